@@ -1,0 +1,255 @@
+/*
+ * gpfvm.h -- C ABI of the GB300-native GP-FVM hot path.
+ *
+ * GP-FVM conditions a Gaussian-process prior on finite-volume observations of
+ * a linear PDE plus initial/boundary data (Weiland, Pfoertner, Hennig,
+ * "Scaling up Probabilistic PDE Simulators with Structured Volumetric
+ * Information").  This library implements, on one GPU:
+ *   - the 1D factor matrices of the tensor-product Matern-5/2 prior under
+ *     interval functionals (Sec. 3.1, Eq. linop-simplified; Sec. 3.2, Eq. LkL);
+ *   - the Kronecker-structured Gram matvec of the volume observations
+ *     (Sec. 4.1, Eq. kronecker-structure) and the point-set blocks;
+ *   - the Cholesky (IC/BC) deflation of Sec. 4.2 and CG with the IterGP
+ *     combined posterior (Sec. 4.1) with full reorthogonalisation (Sec. 5);
+ *   - posterior mean and variance on a tensor prediction grid
+ *     (Sec. 2.1, Eqs. lin-cond-mean / lin-cond-cov).
+ *
+ * Conventions
+ *   - Axes are ordered (t, x, y); ndim is 1, 2 or 3.  Tensors over cells,
+ *     point sets and the prediction grid are row-major in axis order (the
+ *     last axis is contiguous).
+ *   - Pointers in descriptors are HOST pointers; the library copies them in
+ *     gpfvm_create and the caller keeps ownership.  Vector arguments of the
+ *     compute calls are DEVICE pointers unless the name says _host.
+ *   - Every call that takes `stream` enqueues its work on that cudaStream_t
+ *     (NULL = legacy default stream).  Calls that return solver status
+ *     synchronise the stream before returning.
+ *   - Return codes: 0 = success, +1 = iteration budget exhausted before the
+ *     tolerance (a result is still written), negative = error (see
+ *     gpfvm_strerror).  On error nothing is written to outputs.
+ *   - A problem handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef GPFVM_H
+#define GPFVM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPFVM_MAX_DIM 3
+#define GPFVM_MAX_TERMS 8
+#define GPFVM_MAX_SETS 8
+
+enum gpfvm_status {
+  GPFVM_OK = 0,
+  GPFVM_NOT_CONVERGED = 1,
+  GPFVM_ERR_INVALID_ARG = -1,  /* descriptor or argument rejected by validation */
+  GPFVM_ERR_OUT_OF_MEMORY = -2,/* device allocation failed or memory budget exceeded */
+  GPFVM_ERR_NOT_SPD = -3,      /* Cholesky pivot <= 0 in the IC/BC Gram matrix */
+  GPFVM_ERR_BREAKDOWN = -4,    /* CG breakdown: p^T G p <= 0 or not finite */
+  GPFVM_ERR_DEVICE = -5,       /* a CUDA call failed */
+  GPFVM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+  GPFVM_ERR_STATE = -7,        /* call out of order (e.g. solve before assemble) */
+  GPFVM_ERR_NOT_FOUND = -8     /* unknown ticket */
+};
+
+/* One tensor grid of point functionals  d^order u (x)  (Sec. 2.2: initial and
+ * boundary data as linear functionals).  order[i] in {0,1} is the derivative
+ * order along axis i (e.g. order = {1,0,0} observes u_t, a Neumann wall on x
+ * uses {0,1,0}).  The grid has prod n_pts points; `values` lists the
+ * observed values row-major over the per-axis coordinate lists (NULL = all
+ * zero).  noise_var > 0 is the Gaussian noise variance of each value. */
+typedef struct {
+  int order[GPFVM_MAX_DIM];
+  int n_pts[GPFVM_MAX_DIM];
+  const double* coords[GPFVM_MAX_DIM];
+  const double* values;
+  double noise_var;
+} gpfvm_point_set;
+
+/* A linear IBVP discretised by a factorized box scheme (Sec. 4.1, Definition
+ * of factorized structure) under a tensor-product Matern-5/2 prior
+ * (Eq. tensorproduct-cov-def).
+ *   edges[i]       n_cells[i]+1 strictly increasing cell edges of axis i;
+ *                  every cell of the tensor grid is one volume observation
+ *                  int_V D[u] = rhs  (Eq. linop-def).
+ *   alpha, coef    D = sum_k coef[k] d^alpha[k]  (Eq. multi-input-fv), each
+ *                  alpha[k][i] in {0,1,2}.
+ *   lengthscale    per-axis Matern-5/2 lengthscales; outputscale multiplies
+ *                  the product kernel once.
+ *   rhs            N = prod n_cells volume integrals of the forcing f,
+ *                  row-major (NULL = homogeneous PDE).
+ *   jitter         noise variance added to every volume observation.
+ *   sets           initial/boundary point sets (the Cholesky-deflated part).
+ *   pred           per-axis coordinates of the tensor prediction grid. */
+typedef struct {
+  int ndim;
+  int n_cells[GPFVM_MAX_DIM];
+  const double* edges[GPFVM_MAX_DIM];
+  double lengthscale[GPFVM_MAX_DIM];
+  double outputscale;
+  int n_terms;
+  int alpha[GPFVM_MAX_TERMS][GPFVM_MAX_DIM];
+  double coef[GPFVM_MAX_TERMS];
+  const double* rhs;
+  double jitter;
+  int n_sets;
+  gpfvm_point_set sets[GPFVM_MAX_SETS];
+  int n_pred[GPFVM_MAX_DIM];
+  const double* pred[GPFVM_MAX_DIM];
+} gpfvm_desc;
+
+/* Precision of the CG iteration. */
+enum gpfvm_precision {
+  GPFVM_FP64 = 0,       /* every product and vector in FP64 */
+  GPFVM_MIXED_TF32 = 1  /* mode products on tcgen05 tensor cores in TF32 with FP32
+                           accumulation; FP64 scalars, FP64 iterate and periodic
+                           FP64 residual replacement */
+};
+
+typedef struct {
+  int max_iter;        /* iteration budget (>= 1); also sizes the stored directions */
+  double rtol;         /* stop when ||b - G^ x|| / ||b|| <= rtol (recursive residual) */
+  int precision;       /* enum gpfvm_precision */
+  int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions */
+  int want_var;        /* 1 = accumulate the IterGP variance downdate on the grid */
+  int check_every;     /* iterations between host convergence checks (graph replays) */
+  int replace_every;   /* mixed precision: iterations between FP64 residual replacements */
+} gpfvm_solve_opts;
+
+typedef struct {
+  int iterations;      /* CG iterations taken */
+  int status;          /* same code as the return value */
+  double rel_residual; /* recursive ||r||/||b|| at exit */
+  double true_rel_residual; /* FP64 ||b - G^ x||/||b|| recomputed at exit */
+  double t_assemble_ms, t_solve_ms, t_query_ms; /* device time per phase (CUDA events) */
+  double latency_ms;   /* server only: host wall time from submit to result */
+} gpfvm_solve_info;
+
+typedef struct gpfvm_problem gpfvm_problem;
+
+/* Validates and copies the descriptor, allocates device memory for the whole
+ * solve (factors, IC/BC matrices, CG state with room for max_iter stored
+ * directions, prediction outputs).  max_iter <= 0 selects 2000.  Errors:
+ * INVALID_ARG (bad sizes, orders, non-increasing edges, lengthscale <= 0,
+ * total derivative order above 2 in any covariance), OUT_OF_MEMORY. */
+int gpfvm_create(const gpfvm_desc* desc, int max_iter, gpfvm_problem** out);
+
+/* Frees every device and host resource of the problem (NULL is a no-op). */
+void gpfvm_destroy(gpfvm_problem* p);
+
+/* Sizes: out[0] = N volumes, out[1] = M point observations, out[2] = P
+ * prediction points, out[3] = direction capacity. */
+int gpfvm_sizes(const gpfvm_problem* p, int64_t out[4]);
+
+/* Setup (Sec. 4.1 "precompute the 1D factors", Sec. 4.2): assembles all 1D
+ * factor matrices (FP64 closed forms), the dense IC/BC Gram matrix G_BB,
+ * its Cholesky factor and explicit inverse factor L^-1, and the conditioned
+ * right-hand side  b = y_PDE - G_PB G_BB^-1 y_B.  Errors: NOT_SPD, DEVICE. */
+int gpfvm_assemble(gpfvm_problem* p, void* stream);
+
+/* Structured Gram products on device vectors (for parity tests and the
+ * matvec benchmark):
+ *   op 0: out = G_PP v            (N -> N, Eq. kronecker-structure + jitter)
+ *   op 1: out = G^ v = G_PP v - G_PB G_BB^-1 G_BP v   (N -> N, Sec. 4.2)
+ *   op 2: out = G_BP v            (N -> M)
+ *   op 3: out = G_PB v            (M -> N)
+ *   op 4: out = G_PP v in the mixed-precision (TF32 tensor-core) form, FP64 in/out
+ * Requires gpfvm_assemble.  v and out must not overlap. */
+int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);
+
+/* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  All scalars
+ * stay on the device; the iteration is replayed as a CUDA graph and the host
+ * reads the residual every check_every iterations.  Returns OK, NOT_CONVERGED
+ * (budget exhausted; the iterate and variance downdate are kept), BREAKDOWN,
+ * STATE (not assembled) or DEVICE.  info may be NULL. */
+int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info* info,
+                void* stream);
+
+/* Posterior on the prediction grid (device outputs of P doubles each):
+ *   mean = k_B(X*)^T G_BB^-1 (y_B - G_BP x) + L_PDE k(X*)^T x
+ *   var  = k(x,x) - ||L^-1 k_B(x)||^2 - sum_j (Lhat k(x)^T p_j)^2 / eta_j
+ * var may be NULL; a variance needs want_var in the preceding solve. */
+int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream);
+
+/* One call doing assemble + solve + query with HOST input/output buffers:
+ * copies the point-set values (M doubles, may be NULL to keep the
+ * descriptor's) host->device, solves and copies mean/var (P doubles each;
+ * var may be NULL) device->host.  This is the end-to-end path of a user. */
+int gpfvm_solve_host(gpfvm_problem* p, const double* values_host, const gpfvm_solve_opts* opts,
+                     double* mean_host, double* var_host, gpfvm_solve_info* info, void* stream);
+
+/* Replaces the observed values of all point sets (M doubles, DEVICE pointer,
+ * ordered set by set as in the descriptor) and recomputes the conditioned
+ * right-hand side.  Geometry, factors and the IC/BC Cholesky stay valid, so a
+ * new initial condition on the same grid needs no re-assembly.  Requires
+ * gpfvm_assemble. */
+int gpfvm_set_values(gpfvm_problem* p, const double* values, void* stream);
+
+/* Number of kernels this library has launched in the process so far (graph
+ * replays count every kernel node).  Used to report launch counts. */
+int64_t gpfvm_launch_count(void);
+
+/* Copies internal device arrays to a HOST buffer for inspection:
+ *   what 0: conditioned rhs b (N)      what 1: CG iterate x (N)
+ *   what 2: G_BB with noise (M*M)      what 3: L^-1 (M*M, lower)
+ *   what 4: 1D factor (axis, kind_a, ord_a, kind_b, ord_b) -- see gpfvm_factor
+ *   what 5: variance downdate sum (P)  what 6: eta_j (iterations)
+ * Returns the number of doubles written or a negative error. */
+int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream);
+
+/* A 1D covariance factor as assembled on the device (unit output scale):
+ * rows = functional family A, cols = family B on axis `axis`.  kind 0 =
+ * cell family with derivative order ord (0 integral, 1 difference of values,
+ * 2 difference of first derivatives: Eq. linop-simplified); kind 1 = point
+ * set `set` with its order on that axis; kind 2 = prediction points.
+ * Writes rows*cols doubles row-major to host_out. */
+int64_t gpfvm_factor(gpfvm_problem* p, int axis, int kind_a, int arg_a, int kind_b, int arg_b,
+                     double* host_out, int64_t capacity, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched execution: many independent problems of uneven sizes advanced
+ * together.  Each problem must be created and assembled; the iteration of
+ * all unconverged problems runs as one persistent launch per step, captured
+ * in a CUDA graph, with per-problem convergence masks.
+ * ------------------------------------------------------------------------ */
+int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts,
+                      gpfvm_solve_info* infos, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching loop.  Requests are admitted into slots as
+ * device memory and slots free up, their CG state stays resident, and their
+ * iterations are interleaved with those of requests already running.
+ * ------------------------------------------------------------------------ */
+typedef struct gpfvm_server gpfvm_server;
+
+typedef struct {
+  int max_slots;            /* requests resident at once */
+  int64_t memory_budget;    /* bytes of device memory the server may hold (0 = 90% of free) */
+  gpfvm_solve_opts solve;   /* per-request solver options */
+  int steps_per_tick;       /* CG iterations per request per scheduling tick */
+} gpfvm_server_opts;
+
+int gpfvm_server_create(const gpfvm_server_opts* opts, gpfvm_server** out);
+/* Queues a request (descriptor copied); returns its ticket (>= 0) in *ticket. */
+int gpfvm_server_submit(gpfvm_server* s, const gpfvm_desc* desc, int64_t* ticket);
+/* Advances the loop by one scheduling tick (admit, iterate, retire). Returns
+ * the number of requests still queued or running. */
+int gpfvm_server_step(gpfvm_server* s);
+/* If the request is done, copies mean/var (host, P each; var may be NULL) and
+ * its info, returns OK/NOT_CONVERGED or its error; returns 2 if still pending. */
+int gpfvm_server_poll(gpfvm_server* s, int64_t ticket, double* mean_host, double* var_host,
+                      gpfvm_solve_info* info);
+void gpfvm_server_destroy(gpfvm_server* s);
+
+const char* gpfvm_strerror(int code);
+
+/* Library build identification (architecture string and version). */
+const char* gpfvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPFVM_H */

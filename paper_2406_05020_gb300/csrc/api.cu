@@ -1,0 +1,1271 @@
+// C ABI of the GP-FVM hot path: problem setup, assembly, solve, query.
+//
+// Data layout in device memory (all FP64, row-major, axis order t, x, y):
+//   coordinates   cell edges per axis, point-set coordinates, prediction grid
+//   factors       every 1D covariance factor the problem needs (one buffer)
+//   A, L, Linv, LinvT   M x M IC/BC Gram, its Cholesky factor and inverse factor
+//   b, x, r, p, q        N-vectors of the deflated CG
+//   g, t, w              M-vectors (G_BP p, L^-1 g, G_BB^-1 G_BP p)
+//   S, Q                 cap x N stored directions p_j and G^ p_j (reorthogonalisation)
+//   u, down, mean, var, vB   P-vectors on the prediction grid
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <deque>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <tuple>
+
+#include "cg.cuh"
+#include "kron.cuh"
+
+using namespace gpfvm;
+
+namespace gpfvm {
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace gpfvm
+
+namespace {
+
+struct SetC {
+  int order[3] = {0, 0, 0};
+  int n[3] = {1, 1, 1};
+  std::vector<double> coords[3];
+  std::vector<double> values;
+  double noise = 0.0;
+  i64 off = 0, size = 0;
+};
+
+// Factor key: axis, family A (kind, arg), family B (kind, arg).
+// kind 0 = cell family with derivative order arg, 1 = point set arg, 2 = prediction grid.
+typedef std::tuple<int, int, int, int, int> FKey;
+
+struct DevBuf {
+  std::vector<void*> ptrs;
+  i64 bytes = 0;
+  template <typename T>
+  T* alloc(i64 n) {
+    if (n <= 0) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      throw CudaError{cudaErrorMemoryAllocation, "cudaMalloc"};
+    }
+    ptrs.push_back(p);
+    bytes += n * (i64)sizeof(T);
+    return (T*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+int map_error(const CudaError& e) {
+  if (e.err == cudaErrorMemoryAllocation) return GPFVM_ERR_OUT_OF_MEMORY;
+  if (e.err == cudaErrorInvalidValue) return GPFVM_ERR_INVALID_ARG;
+  return GPFVM_ERR_DEVICE;
+}
+
+}  // namespace
+
+struct gpfvm_problem {
+  // ---- descriptor copy
+  int d = 0;
+  int nc[3] = {1, 1, 1};
+  std::vector<double> edges[3];
+  double ell[3] = {1, 1, 1};
+  double s2 = 1.0, jitter = 0.0;
+  int nterms = 0;
+  int alpha[GPFVM_MAX_TERMS][3] = {};
+  double coef[GPFVM_MAX_TERMS] = {};
+  std::vector<double> rhs;
+  int nsets = 0;
+  SetC sets[GPFVM_MAX_SETS];
+  int npred[3] = {1, 1, 1};
+  std::vector<double> pred[3];
+  i64 N = 0, M = 0, P = 0;
+  int cap = 0;
+
+  // ---- device memory
+  DevBuf mem;
+  double* d_coords = nullptr;
+  i64 off_edges[3] = {0, 0, 0}, off_pred[3] = {0, 0, 0}, off_set[GPFVM_MAX_SETS][3] = {};
+  double* d_fac = nullptr;
+  std::map<FKey, i64> fac_off;
+  std::vector<FactorJob> jobs;
+  FactorJob* d_jobs = nullptr;
+  i64 max_entries = 0;
+  double *d_A = nullptr, *d_L = nullptr, *d_Linv = nullptr, *d_LinvT = nullptr, *d_cscr = nullptr;
+  double *d_yB = nullptr, *d_rhs = nullptr, *d_b = nullptr;
+  double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr;
+  double *d_g = nullptr, *d_t = nullptr, *d_w = nullptr, *d_g2 = nullptr;
+  double *d_u = nullptr, *d_down = nullptr, *d_mean = nullptr, *d_var = nullptr, *d_vB = nullptr;
+  double *d_S = nullptr, *d_Q = nullptr, *d_eta = nullptr, *d_part2 = nullptr, *d_coef = nullptr;
+  double *d_vin = nullptr, *d_vout = nullptr, *d_win = nullptr, *d_wout = nullptr;
+  double *d_vbchunk = nullptr, *d_vbY = nullptr;
+  double* d_scratch = nullptr;
+  i64 scratch_cap = 0;
+  int vb_rows = 0;
+  CGState* d_st = nullptr;
+  CGState* h_st = nullptr;  // pinned mirror of the scalar header
+
+  // ---- plans
+  Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB;
+  Plan p_op[4];
+  int modeprods_pp = 0;
+
+  // ---- state
+  bool assembled = false, solved = false, vB_ready = false, want_var_last = false;
+  cudaGraphExec_t graph = nullptr;
+  int graph_key = -1;
+  long long graph_kernels = 0;
+  gpfvm_solve_info last{};
+
+  ~gpfvm_problem() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (h_st) cudaFreeHost(h_st);
+    mem.release();
+  }
+};
+
+namespace {
+
+
+i64 fam_n(const gpfvm_problem* p, int ax, int kind, int arg) {
+  if (kind == 0) return p->nc[ax];
+  if (kind == 1) return p->sets[arg].n[ax];
+  return p->npred[ax];
+}
+
+void need_factor(gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab) {
+  FKey key(ax, ka, aa, kb, ab);
+  if (p->fac_off.count(key)) return;
+  FactorJob J{};
+  J.kind_a = ka == 0 ? 0 : 1;
+  J.kind_b = kb == 0 ? 0 : 1;
+  J.ord_a = ka == 0 ? aa : (ka == 1 ? p->sets[aa].order[ax] : 0);
+  J.ord_b = kb == 0 ? ab : (kb == 1 ? p->sets[ab].order[ax] : 0);
+  J.n_a = (int)fam_n(p, ax, ka, aa);
+  J.n_b = (int)fam_n(p, ax, kb, ab);
+  J.ell = p->ell[ax];
+  i64 off = 0;
+  for (auto& j : p->jobs) off += (i64)j.n_a * j.n_b;
+  p->fac_off[key] = off;
+  // coordinate pointers are patched once the coordinate buffer exists
+  J.ca = (const double*)(intptr_t)(ka * 1000 + aa);
+  J.cb = (const double*)(intptr_t)(kb * 1000 + ab);
+  J.out = (double*)(intptr_t)off;
+  p->jobs.push_back(J);
+  p->max_entries = std::max(p->max_entries, (i64)J.n_a * J.n_b);
+}
+
+MatRef fac_ref(const gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab, bool transpose) {
+  const i64 off = p->fac_off.at(FKey(ax, ka, aa, kb, ab));
+  const i64 nb = fam_n(p, ax, kb, ab);
+  MatRef m{p->d_fac + off, nb, 1};
+  if (transpose) std::swap(m.rs, m.cs);
+  return m;
+}
+
+// Terms of G_PP: pairs of operator terms, factor per axis A_i^{a_i b_i}.
+std::vector<KTerm> pp_terms(const gpfvm_problem* p) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b) {
+      KTerm t{};
+      t.c = p->coef[a] * p->coef[b];
+      for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 0, p->alpha[b][i], false);
+      ts.push_back(t);
+    }
+  return ts;
+}
+
+// cells -> set s (transpose=true) or set s -> cells (transpose=false)
+std::vector<KTerm> pb_terms(const gpfvm_problem* p, int s, bool to_set) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a) {
+    KTerm t{};
+    t.c = p->coef[a];
+    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 1, s, to_set);
+    ts.push_back(t);
+  }
+  return ts;
+}
+
+std::vector<KTerm> ppred_terms(const gpfvm_problem* p) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a) {
+    KTerm t{};
+    t.c = p->coef[a];
+    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 2, 0, true);
+    ts.push_back(t);
+  }
+  return ts;
+}
+
+std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s) {
+  KTerm t{};
+  t.c = 1.0;
+  for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 1, s, 2, 0, true);
+  return {t};
+}
+
+void dims_cells(const gpfvm_problem* p, int* o) { for (int i = 0; i < p->d; ++i) o[i] = p->nc[i]; }
+void dims_set(const gpfvm_problem* p, int s, int* o) { for (int i = 0; i < p->d; ++i) o[i] = p->sets[s].n[i]; }
+void dims_pred(const gpfvm_problem* p, int* o) { for (int i = 0; i < p->d; ++i) o[i] = p->npred[i]; }
+
+}  // namespace
+
+namespace {
+
+struct Builder {
+  gpfvm_problem* p;
+  Scratch scr;
+  i64 peak = 0;
+  void kron(Plan& plan, const int* din, const int* dout, i64 batch, const std::vector<KTerm>& terms, double scale,
+            const double* in, double* out, double beta, const double* D, double gamma, int* count = nullptr) {
+    scr.used = 0;
+    plan_kron(plan, scr, p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count);
+    peak = std::max(peak, scr.used);
+  }
+
+  // out = G_BP in (cells -> all sets), into g (M)
+  void bp(Plan& plan, const double* in, double* g) {
+    int dc[3], ds[3];
+    dims_cells(p, dc);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(plan, dc, ds, 1, pb_terms(p, s, true), p->s2, in, g + p->sets[s].off, 0.0, nullptr, 0.0);
+    }
+  }
+  // out (+)= scale * G_PB w
+  void pb(Plan& plan, const double* w, double* out, double scale, bool accumulate) {
+    int dc[3], ds[3];
+    dims_cells(p, dc);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(plan, ds, dc, 1, pb_terms(p, s, false), scale * p->s2, w + p->sets[s].off, out,
+           (accumulate || s > 0) ? 1.0 : 0.0, nullptr, 0.0);
+    }
+  }
+  // w = G_BB^-1 g via the explicit inverse factor
+  void hsolve(Plan& plan, const double* g, double* t, double* w) {
+    const int M = (int)p->M;
+    plan.gemv(M, M, p->d_Linv, M, g, t, 1.0, 0.0, 1);
+    plan.gemv(M, M, p->d_LinvT, M, t, w, 1.0, 0.0, 2);
+  }
+  void pp(Plan& plan, const double* in, double* out, int* count) {
+    int dc[3];
+    dims_cells(p, dc);
+    kron(plan, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
+  }
+  // out = G^ in = G_PP in - G_PB G_BB^-1 G_BP in ; leaves w = G_BB^-1 G_BP in
+  void ghat(Plan& plan, const double* in, double* out, double* g, double* t, double* w, int* count) {
+    if (p->M > 0) {
+      bp(plan, in, g);
+      hsolve(plan, g, t, w);
+    }
+    pp(plan, in, out, count);
+    if (p->M > 0) pb(plan, w, out, -1.0, true);
+  }
+  // u (+)= scale * (L_PDE k(X*))^T v
+  void to_pred_cells(Plan& plan, const double* v, double* u, double scale, bool acc) {
+    int dc[3], dp[3];
+    dims_cells(p, dc);
+    dims_pred(p, dp);
+    kron(plan, dc, dp, 1, ppred_terms(p), scale * p->s2, v, u, acc ? 1.0 : 0.0, nullptr, 0.0);
+  }
+  void to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc) {
+    int ds[3], dp[3];
+    dims_pred(p, dp);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(plan, ds, dp, 1, bpred_terms(p, s), scale * p->s2, w + p->sets[s].off, u, (acc || s > 0) ? 1.0 : 0.0,
+           nullptr, 0.0);
+    }
+  }
+};
+
+void build_plans(gpfvm_problem* p, Builder& B) {
+  const i64 N = p->N, M = p->M, P = p->P;
+  gpfvm_problem* pp_ = p;
+  // ---- setup: factors + G_BB
+  p->p_setup = Plan();
+  {
+    FactorJob* dj = p->d_jobs;
+    const int nj = (int)p->jobs.size();
+    const i64 me = p->max_entries;
+    p->p_setup.func([=](cudaStream_t st) { launch_factors(dj, nj, me, st); });
+    if (M > 0) {
+      GbbParams G{};
+      G.M = (int)M;
+      G.ndim = p->d;
+      G.n_sets = p->nsets;
+      G.outputscale = p->s2;
+      for (int s = 0; s < p->nsets; ++s) {
+        G.off[s] = (int)p->sets[s].off;
+        G.noise[s] = p->sets[s].noise;
+        for (int i = 0; i < p->d; ++i) G.dims[s][i] = p->sets[s].n[i];
+        for (int s2 = 0; s2 < p->nsets; ++s2)
+          for (int i = 0; i < p->d; ++i)
+            G.fac[s][s2][i] = p->d_fac ? p->d_fac + p->fac_off.at(FKey(i, 1, s, 1, s2)) : nullptr;
+      }
+      G.off[p->nsets] = (int)M;
+      double* A = p->d_A;
+      p->p_setup.func([=](cudaStream_t st) { launch_gbb(G, A, st); });
+    }
+  }
+  // ---- IC/BC Cholesky + inverse
+  p->p_chol = Plan();
+  if (M > 0) {
+    int* status = p->d_st ? &p->d_st->pad[0] : nullptr;
+    p->p_chol.func([=](cudaStream_t st) {
+      GPFVM_CUDA(cudaMemsetAsync(pp_->d_L, 0, sizeof(double) * M * M, st));
+      GPFVM_CUDA(cudaMemsetAsync(pp_->d_Linv, 0, sizeof(double) * M * M, st));
+    });
+    plan_chol_inverse(p->p_chol, p->d_A, p->d_L, p->d_Linv, (int)M, M, p->d_cscr, status);
+    double* Li = p->d_Linv;
+    double* LiT = p->d_LinvT;
+    p->p_chol.func([=](cudaStream_t st) { transpose(Li, LiT, (int)M, (int)M, st); });
+  }
+  // ---- conditioned right-hand side b = y_P - G_PB G_BB^-1 y_B
+  p->p_rhs = Plan();
+  {
+    double* b = p->d_b;
+    const double* rhs = p->d_rhs;
+    p->p_rhs.func([=](cudaStream_t st) {
+      if (rhs) GPFVM_CUDA(cudaMemcpyAsync(b, rhs, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      else GPFVM_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * N, st));
+    });
+    if (M > 0) {
+      B.hsolve(p->p_rhs, p->d_yB, p->d_t, p->d_w);
+      B.pb(p->p_rhs, p->d_w, b, -1.0, true);
+    }
+  }
+  // ---- CG iteration plans
+  p->p_mv_cg = Plan();
+  p->modeprods_pp = 0;
+  B.ghat(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_t, p->d_w, &p->modeprods_pp);
+  p->p_var_cg = Plan();
+  B.to_pred_cells(p->p_var_cg, p->d_p, p->d_u, 1.0, false);
+  if (M > 0) B.to_pred_sets(p->p_var_cg, p->d_w, p->d_u, -1.0, true);
+  // ---- operator plans for gpfvm_gram_matvec / true residual
+  for (int k = 0; k < 4; ++k) p->p_op[k] = Plan();
+  B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
+  B.ghat(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_t, p->d_wout, nullptr);
+  if (M > 0) {
+    B.bp(p->p_op[2], p->d_vin, p->d_wout);
+    B.pb(p->p_op[3], p->d_win, p->d_vout, 1.0, false);
+  }
+  // ---- posterior mean
+  p->p_mean = Plan();
+  if (M > 0) {
+    B.bp(p->p_mean, p->d_x, p->d_g);
+    double *g = p->d_g, *g2 = p->d_g2;
+    const double* yB = p->d_yB;
+    p->p_mean.func([=](cudaStream_t st) { axpby(yB, g, g2, 1.0, -1.0, M, st); });
+    B.hsolve(p->p_mean, p->d_g2, p->d_t, p->d_w);
+    B.to_pred_sets(p->p_mean, p->d_w, p->d_mean, 1.0, false);
+  }
+  B.to_pred_cells(p->p_mean, p->d_x, p->d_mean, 1.0, M > 0);
+  // ---- Cholesky-stage variance term vB[p] = || L^-1 k_B(x_p) ||^2 in row chunks
+  p->p_vB = Plan();
+  {
+    double* vB = p->d_vB;
+    p->p_vB.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemsetAsync(vB, 0, sizeof(double) * P, st)); });
+    const int R = p->vb_rows;
+    int dp[3], ds[3];
+    dims_pred(p, dp);
+    for (i64 m0 = 0; m0 < M && R > 0; m0 += R) {
+      const int rows = (int)std::min<i64>(R, M - m0);
+      bool first = true;
+      for (int s = 0; s < p->nsets; ++s) {
+        const i64 off = p->sets[s].off, ms = p->sets[s].size;
+        if (off > m0 + rows - 1) continue;  // L^-1 is lower triangular: these columns are zero
+        const double* src = p->d_Linv + m0 * M + off;
+        double* dst = p->d_vbchunk;
+        p->p_vB.func([=](cudaStream_t st) {
+          GPFVM_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ms, src, sizeof(double) * M, sizeof(double) * ms, rows,
+                                       cudaMemcpyDeviceToDevice, st));
+        });
+        dims_set(p, s, ds);
+        B.kron(p->p_vB, ds, dp, rows, bpred_terms(p, s), p->s2, p->d_vbchunk, p->d_vbY, first ? 0.0 : 1.0, nullptr,
+               0.0);
+        first = false;
+      }
+      const double* Y = p->d_vbY;
+      p->p_vB.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
+    }
+  }
+}
+
+void finalize_plans(gpfvm_problem* p) {
+  p->p_mv_cg.skip = &p->d_st->done;
+  p->p_var_cg.skip = &p->d_st->done;
+  Plan* all[] = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
+                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3]};
+  for (Plan* pl : all) pl->finalize();
+}
+
+int validate(const gpfvm_desc* D) {
+  if (!D) return GPFVM_ERR_INVALID_ARG;
+  if (D->ndim < 1 || D->ndim > 3) return GPFVM_ERR_INVALID_ARG;
+  if (D->n_terms < 1 || D->n_terms > GPFVM_MAX_TERMS) return GPFVM_ERR_INVALID_ARG;
+  if (D->n_sets < 0 || D->n_sets > GPFVM_MAX_SETS) return GPFVM_ERR_INVALID_ARG;
+  if (!(D->outputscale > 0) || !(D->jitter >= 0) || !std::isfinite(D->outputscale) || !std::isfinite(D->jitter))
+    return GPFVM_ERR_INVALID_ARG;
+  i64 N = 1, P = 1;
+  for (int i = 0; i < D->ndim; ++i) {
+    if (D->n_cells[i] < 1 || D->n_cells[i] > 65536 || !D->edges[i]) return GPFVM_ERR_INVALID_ARG;
+    if (!(D->lengthscale[i] > 0) || !std::isfinite(D->lengthscale[i])) return GPFVM_ERR_INVALID_ARG;
+    for (int j = 0; j < D->n_cells[i]; ++j)
+      if (!(D->edges[i][j + 1] > D->edges[i][j]) || !std::isfinite(D->edges[i][j + 1])) return GPFVM_ERR_INVALID_ARG;
+    if (D->n_pred[i] < 1 || D->n_pred[i] > 65536 || !D->pred[i]) return GPFVM_ERR_INVALID_ARG;
+    for (int j = 0; j < D->n_pred[i]; ++j)
+      if (!std::isfinite(D->pred[i][j])) return GPFVM_ERR_INVALID_ARG;
+    N *= D->n_cells[i];
+    P *= D->n_pred[i];
+  }
+  if (N > (i64)1 << 28 || P > (i64)1 << 28) return GPFVM_ERR_INVALID_ARG;
+  bool any = false;
+  for (int k = 0; k < D->n_terms; ++k) {
+    if (!std::isfinite(D->coef[k])) return GPFVM_ERR_INVALID_ARG;
+    any = any || D->coef[k] != 0.0;
+    for (int i = 0; i < D->ndim; ++i)
+      if (D->alpha[k][i] < 0 || D->alpha[k][i] > 2) return GPFVM_ERR_INVALID_ARG;
+  }
+  if (!any) return GPFVM_ERR_INVALID_ARG;
+  i64 M = 0;
+  for (int s = 0; s < D->n_sets; ++s) {
+    const gpfvm_point_set& S = D->sets[s];
+    if (!(S.noise_var >= 0) || !std::isfinite(S.noise_var)) return GPFVM_ERR_INVALID_ARG;
+    i64 n = 1;
+    for (int i = 0; i < D->ndim; ++i) {
+      if (S.order[i] < 0 || S.order[i] > 1) return GPFVM_ERR_INVALID_ARG;
+      if (S.n_pts[i] < 1 || S.n_pts[i] > 65536 || !S.coords[i]) return GPFVM_ERR_INVALID_ARG;
+      for (int j = 0; j < S.n_pts[i]; ++j)
+        if (!std::isfinite(S.coords[i][j])) return GPFVM_ERR_INVALID_ARG;
+      n *= S.n_pts[i];
+    }
+    if (S.values)
+      for (i64 j = 0; j < n; ++j)
+        if (!std::isfinite(S.values[j])) return GPFVM_ERR_INVALID_ARG;
+    M += n;
+  }
+  if (M > 65536) return GPFVM_ERR_INVALID_ARG;
+  if (D->rhs)
+    for (i64 j = 0; j < N; ++j)
+      if (!std::isfinite(D->rhs[j])) return GPFVM_ERR_INVALID_ARG;
+  return GPFVM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+cudaStream_t pick_stream(gpfvm_problem* p, void* s);
+
+}  // namespace
+
+static std::map<const gpfvm_problem*, cudaStream_t>& own_streams() {
+  static std::map<const gpfvm_problem*, cudaStream_t> m;
+  return m;
+}
+
+namespace {
+
+cudaStream_t pick_stream(gpfvm_problem* p, void* s) {
+  if (s) return (cudaStream_t)s;
+  auto& m = own_streams();
+  auto it = m.find(p);
+  if (it != m.end()) return it->second;
+  cudaStream_t st;
+  GPFVM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  m[p] = st;
+  return st;
+}
+
+void alloc_all(gpfvm_problem* p) {
+  const i64 N = p->N, M = p->M, P = p->P;
+  DevBuf& m = p->mem;
+  // coordinates
+  std::vector<double> coords;
+  for (int i = 0; i < p->d; ++i) {
+    p->off_edges[i] = (i64)coords.size();
+    coords.insert(coords.end(), p->edges[i].begin(), p->edges[i].end());
+  }
+  for (int s = 0; s < p->nsets; ++s)
+    for (int i = 0; i < p->d; ++i) {
+      p->off_set[s][i] = (i64)coords.size();
+      coords.insert(coords.end(), p->sets[s].coords[i].begin(), p->sets[s].coords[i].end());
+    }
+  for (int i = 0; i < p->d; ++i) {
+    p->off_pred[i] = (i64)coords.size();
+    coords.insert(coords.end(), p->pred[i].begin(), p->pred[i].end());
+  }
+  p->d_coords = m.alloc<double>((i64)coords.size());
+  GPFVM_CUDA(cudaMemcpy(p->d_coords, coords.data(), coords.size() * sizeof(double), cudaMemcpyHostToDevice));
+  // factors
+  i64 nfac = 0;
+  for (auto& j : p->jobs) nfac += (i64)j.n_a * j.n_b;
+  p->d_fac = m.alloc<double>(std::max<i64>(nfac, 1));
+  for (auto& key_off : p->fac_off) {
+    int ax, ka, aa, kb, ab;
+    std::tie(ax, ka, aa, kb, ab) = key_off.first;
+    for (auto& J : p->jobs)
+      if ((i64)(intptr_t)J.out == key_off.second && (intptr_t)J.ca == ka * 1000 + aa && (intptr_t)J.cb == kb * 1000 + ab) {
+        auto cptr = [&](int k, int a) -> const double* {
+          if (k == 0) return p->d_coords + p->off_edges[ax];
+          if (k == 1) return p->d_coords + p->off_set[a][ax];
+          return p->d_coords + p->off_pred[ax];
+        };
+        J.ca = cptr(ka, aa);
+        J.cb = cptr(kb, ab);
+        J.out = p->d_fac + key_off.second;
+        break;
+      }
+  }
+  p->d_jobs = m.alloc<FactorJob>((i64)p->jobs.size());
+  GPFVM_CUDA(cudaMemcpy(p->d_jobs, p->jobs.data(), p->jobs.size() * sizeof(FactorJob), cudaMemcpyHostToDevice));
+  // IC/BC matrices
+  if (M > 0) {
+    p->d_A = m.alloc<double>(M * M);
+    p->d_L = m.alloc<double>(M * M);
+    p->d_Linv = m.alloc<double>(M * M);
+    p->d_LinvT = m.alloc<double>(M * M);
+    p->d_cscr = m.alloc<double>(M * M / 4 + 64 * M + 64);
+    p->d_yB = m.alloc<double>(M);
+    p->d_g = m.alloc<double>(M);
+    p->d_t = m.alloc<double>(M);
+    p->d_w = m.alloc<double>(M);
+    p->d_g2 = m.alloc<double>(M);
+    p->d_win = m.alloc<double>(M);
+    p->d_wout = m.alloc<double>(M);
+    std::vector<double> y;
+    for (int s = 0; s < p->nsets; ++s) y.insert(y.end(), p->sets[s].values.begin(), p->sets[s].values.end());
+    GPFVM_CUDA(cudaMemcpy(p->d_yB, y.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!p->rhs.empty()) {
+    p->d_rhs = m.alloc<double>(N);
+    GPFVM_CUDA(cudaMemcpy(p->d_rhs, p->rhs.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  p->d_b = m.alloc<double>(N);
+  p->d_x = m.alloc<double>(N);
+  p->d_r = m.alloc<double>(N);
+  p->d_p = m.alloc<double>(N);
+  p->d_q = m.alloc<double>(N);
+  p->d_vin = m.alloc<double>(N);
+  p->d_vout = m.alloc<double>(N);
+  p->d_u = m.alloc<double>(P);
+  p->d_down = m.alloc<double>(P);
+  p->d_mean = m.alloc<double>(P);
+  p->d_var = m.alloc<double>(P);
+  p->d_vB = m.alloc<double>(P);
+  const int cap = p->cap;
+  p->d_S = m.alloc<double>((i64)cap * N);
+  p->d_Q = m.alloc<double>((i64)cap * N);
+  p->d_eta = m.alloc<double>(cap);
+  p->d_part2 = m.alloc<double>((i64)cap * reorth_chunks(N));
+  p->d_coef = m.alloc<double>(cap);
+  if (M > 0) {
+    i64 R = std::max<i64>(1, std::min<i64>(M, ((i64)1 << 25) / std::max<i64>(P, 1)));
+    p->vb_rows = (int)R;
+    i64 maxms = 0;
+    for (int s = 0; s < p->nsets; ++s) maxms = std::max(maxms, p->sets[s].size);
+    p->d_vbchunk = m.alloc<double>(R * maxms);
+    p->d_vbY = m.alloc<double>(R * P);
+  }
+  p->d_st = m.alloc<CGState>(1);
+  GPFVM_CUDA(cudaMemset(p->d_st, 0, sizeof(CGState)));
+  GPFVM_CUDA(cudaMallocHost(&p->h_st, sizeof(CGState)));
+  std::memset(p->h_st, 0, sizeof(CGState));
+  GPFVM_CUDA(cudaMemset(p->d_down, 0, P * sizeof(double)));
+  // plans: count scratch, allocate, build for real
+  Builder B0{p};
+  B0.scr.base = nullptr;
+  B0.scr.cap = (i64)1 << 62;
+  build_plans(p, B0);
+  p->scratch_cap = std::max<i64>(B0.peak, 64);
+  p->d_scratch = m.alloc<double>(p->scratch_cap);
+  Builder B{p};
+  B.scr.base = p->d_scratch;
+  B.scr.cap = p->scratch_cap;
+  build_plans(p, B);
+  finalize_plans(p);
+}
+
+void copy_header_to_host(gpfvm_problem* p, cudaStream_t st) {
+  GPFVM_CUDA(cudaMemcpyAsync(p->h_st, p->d_st, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+}
+
+int run_assemble(gpfvm_problem* p, cudaStream_t st) {
+  GPFVM_CUDA(cudaMemsetAsync(p->d_st, 0, offsetof(CGState, part), st));
+  p->p_setup.run(st);
+  if (p->M > 0) {
+    p->p_chol.run(st);
+    copy_header_to_host(p, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (p->h_st->pad[0] & DEV_NOT_SPD) return GPFVM_ERR_NOT_SPD;
+  }
+  p->p_rhs.run(st);
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  p->assembled = true;
+  p->solved = false;
+  p->vB_ready = false;
+  return GPFVM_OK;
+}
+
+void cg_iteration(gpfvm_problem* p, bool reorth, bool want_var, cudaStream_t st) {
+  const i64 N = p->N;
+  p->p_mv_cg.run(st);
+  cg_dot_eta(p->d_p, p->d_q, N, p->d_st, p->d_eta, st);
+  if (want_var) {
+    p->p_var_cg.run(st);
+    cg_downdate(p->d_u, p->d_down, p->P, p->d_st, st);
+  }
+  cg_update(p->d_x, p->d_r, p->d_p, p->d_q, N, p->d_st, reorth ? p->d_S : nullptr, reorth ? p->d_Q : nullptr, st);
+  cg_pupdate(p->d_r, p->d_p, N, p->d_st, st);
+  if (reorth) cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
+}
+
+double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
+  GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, x, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, st));
+  p->p_op[1].run(st);
+  axpby(p->d_b, p->d_vout, p->d_vout, 1.0, -1.0, p->N, st);
+  norm2(p->d_vout, p->N, &p->d_st->aux[0], p->d_st, st);
+  copy_header_to_host(p, st);
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  const double b2 = p->h_st->bnorm2;
+  return b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
+}
+
+int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st);
+
+struct SolveRun {
+  gpfvm_solve_opts o{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int launched = 0;
+  bool active = false;
+};
+std::map<const gpfvm_problem*, SolveRun>& runs() {
+  static std::map<const gpfvm_problem*, SolveRun> m;
+  return m;
+}
+
+int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
+  if (o->precision != GPFVM_FP64 && o->precision != GPFVM_MIXED_TF32) return GPFVM_ERR_INVALID_ARG;
+  const bool reorth = o->reorth != 0, want_var = o->want_var != 0;
+  if (reorth && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
+  SolveRun& R = runs()[p];
+  R.o = *o;
+  R.launched = 0;
+  R.active = true;
+  if (!R.e0) {
+    GPFVM_CUDA(cudaEventCreate(&R.e0));
+    GPFVM_CUDA(cudaEventCreate(&R.e1));
+  }
+  GPFVM_CUDA(cudaEventRecord(R.e0, st));
+  p->h_st->rtol2 = o->rtol * o->rtol;
+  p->h_st->max_iter = o->max_iter;
+  p->h_st->cap = p->cap;
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->rtol2, &p->h_st->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->max_iter, &p->h_st->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  cg_init(p->d_b, p->d_x, p->d_r, p->d_p, p->N, p->d_st, st);
+  const int key = (reorth ? 1 : 0) + (want_var ? 2 : 0);
+  if (!p->graph || p->graph_key != key) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    cudaGraph_t g;
+    const long long before = g_launches.load();
+    GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cg_iteration(p, reorth, want_var, st);
+    GPFVM_CUDA(cudaStreamEndCapture(st, &g));
+    p->graph_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(p->graph_kernels);  // captured, not launched
+    GPFVM_CUDA(cudaGraphInstantiate(&p->graph, g, 0));
+    cudaGraphDestroy(g);
+    p->graph_key = key;
+  }
+  return GPFVM_OK;
+}
+
+// Enqueues up to n more iterations (graph replays) and a copy of the scalar header.
+void solve_launch(gpfvm_problem* p, int n, cudaStream_t st) {
+  SolveRun& R = runs()[p];
+  n = std::min(n, R.o.max_iter - R.launched);
+  for (int i = 0; i < n; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph, st));
+  count_launch((long long)n * p->graph_kernels);
+  R.launched += n;
+  copy_header_to_host(p, st);
+}
+
+// True once the device reports done (or the budget is spent); needs the stream to be synchronised.
+bool solve_finished(gpfvm_problem* p) {
+  SolveRun& R = runs()[p];
+  return p->h_st->done || R.launched >= R.o.max_iter;
+}
+
+int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
+  SolveRun& R = runs()[p];
+  GPFVM_CUDA(cudaEventRecord(R.e1, st));
+  GPFVM_CUDA(cudaEventSynchronize(R.e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, R.e0, R.e1);
+  R.active = false;
+  const CGState& h = *p->h_st;
+  int status = GPFVM_NOT_CONVERGED;
+  if (h.status & DEV_BREAKDOWN) status = GPFVM_ERR_BREAKDOWN;
+  else if (h.converged) status = GPFVM_OK;
+  gpfvm_solve_info I = p->last;
+  I.iterations = h.k;
+  I.status = status;
+  I.rel_residual = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+  I.t_solve_ms = ms;
+  I.true_rel_residual = true_rel_residual(p, p->d_x, st);
+  p->last = I;
+  if (info) *info = I;
+  p->solved = status >= 0;
+  p->want_var_last = R.o.want_var != 0;
+  return status;
+}
+
+int run_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+  if (o && o->precision == GPFVM_MIXED_TF32) return mixed_solve(p, o, info, st);
+  const int b = solve_begin(p, o, st);
+  if (b != GPFVM_OK) return b;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  while (true) {
+    solve_launch(p, chunk, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (solve_finished(p)) break;
+  }
+  return solve_end(p, info, st);
+}
+
+int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
+  if (!p->solved) return GPFVM_ERR_STATE;
+  if (var && !p->want_var_last) return GPFVM_ERR_STATE;
+  p->p_mean.run(st);
+  if (mean) GPFVM_CUDA(cudaMemcpyAsync(mean, p->d_mean, sizeof(double) * p->P, cudaMemcpyDeviceToDevice, st));
+  if (var) {
+    if (p->M > 0 && !p->vB_ready) {
+      p->p_vB.run(st);
+      p->vB_ready = true;
+    }
+    var_final(p->M > 0 ? p->d_vB : nullptr, p->d_down, p->d_var, p->s2, p->P, st);
+    GPFVM_CUDA(cudaMemcpyAsync(var, p->d_var, sizeof(double) * p->P, cudaMemcpyDeviceToDevice, st));
+  }
+  return GPFVM_OK;
+}
+
+}  // namespace
+
+namespace {
+int mixed_solve(gpfvm_problem*, const gpfvm_solve_opts*, gpfvm_solve_info*, cudaStream_t) {
+  return GPFVM_ERR_INVALID_ARG;  // replaced by the tensor-core path
+}
+}  // namespace
+
+#define GPFVM_GUARD_BEGIN try {
+#define GPFVM_GUARD_END                  \
+  }                                      \
+  catch (const CudaError& e) {           \
+    return map_error(e);                 \
+  }                                      \
+  catch (const std::bad_alloc&) {        \
+    return GPFVM_ERR_OUT_OF_MEMORY;      \
+  }                                      \
+  catch (...) {                          \
+    return GPFVM_ERR_DEVICE;             \
+  }
+
+extern "C" {
+
+int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
+  if (!out) return GPFVM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int v = validate(D);
+  if (v != GPFVM_OK) return v;
+  std::unique_ptr<gpfvm_problem> p(new gpfvm_problem());
+  GPFVM_GUARD_BEGIN
+  p->d = D->ndim;
+  p->N = 1;
+  p->P = 1;
+  for (int i = 0; i < p->d; ++i) {
+    p->nc[i] = D->n_cells[i];
+    p->edges[i].assign(D->edges[i], D->edges[i] + D->n_cells[i] + 1);
+    p->ell[i] = D->lengthscale[i];
+    p->npred[i] = D->n_pred[i];
+    p->pred[i].assign(D->pred[i], D->pred[i] + D->n_pred[i]);
+    p->N *= p->nc[i];
+    p->P *= p->npred[i];
+  }
+  p->s2 = D->outputscale;
+  p->jitter = D->jitter;
+  p->nterms = D->n_terms;
+  for (int k = 0; k < p->nterms; ++k) {
+    p->coef[k] = D->coef[k];
+    for (int i = 0; i < p->d; ++i) p->alpha[k][i] = D->alpha[k][i];
+  }
+  if (D->rhs) p->rhs.assign(D->rhs, D->rhs + p->N);
+  p->nsets = D->n_sets;
+  i64 off = 0;
+  for (int s = 0; s < p->nsets; ++s) {
+    SetC& S = p->sets[s];
+    S.size = 1;
+    for (int i = 0; i < p->d; ++i) {
+      S.order[i] = D->sets[s].order[i];
+      S.n[i] = D->sets[s].n_pts[i];
+      S.coords[i].assign(D->sets[s].coords[i], D->sets[s].coords[i] + S.n[i]);
+      S.size *= S.n[i];
+    }
+    if (D->sets[s].values) S.values.assign(D->sets[s].values, D->sets[s].values + S.size);
+    else S.values.assign(S.size, 0.0);
+    S.noise = D->sets[s].noise_var;
+    S.off = off;
+    off += S.size;
+  }
+  p->M = off;
+  p->cap = max_iter > 0 ? max_iter : 2000;
+  // register the 1D factors the problem needs
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b)
+      for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 0, p->alpha[a][i], 0, p->alpha[b][i]);
+  for (int s = 0; s < p->nsets; ++s) {
+    for (int a = 0; a < p->nterms; ++a)
+      for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 0, p->alpha[a][i], 1, s);
+    for (int s2 = 0; s2 < p->nsets; ++s2)
+      for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 1, s, 1, s2);
+    for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 1, s, 2, 0);
+  }
+  for (int a = 0; a < p->nterms; ++a)
+    for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 0, p->alpha[a][i], 2, 0);
+  alloc_all(p.get());
+  *out = p.release();
+  return GPFVM_OK;
+  GPFVM_GUARD_END
+}
+
+void gpfvm_destroy(gpfvm_problem* p) {
+  if (!p) return;
+  auto& m = own_streams();
+  auto it = m.find(p);
+  if (it != m.end()) {
+    cudaStreamSynchronize(it->second);
+    cudaStreamDestroy(it->second);
+    m.erase(it);
+  }
+  delete p;
+}
+
+int gpfvm_sizes(const gpfvm_problem* p, int64_t out[4]) {
+  if (!p || !out) return GPFVM_ERR_INVALID_ARG;
+  out[0] = p->N;
+  out[1] = p->M;
+  out[2] = p->P;
+  out[3] = p->cap;
+  return GPFVM_OK;
+}
+
+int gpfvm_assemble(gpfvm_problem* p, void* stream) {
+  if (!p) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  cudaEvent_t e0, e1;
+  GPFVM_CUDA(cudaEventCreate(&e0));
+  GPFVM_CUDA(cudaEventCreate(&e1));
+  GPFVM_CUDA(cudaEventRecord(e0, st));
+  const int r = run_assemble(p, st);
+  GPFVM_CUDA(cudaEventRecord(e1, st));
+  GPFVM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  p->last.t_assemble_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream) {
+  if (!p || !v || !out || op < 0 || op > 4) return GPFVM_ERR_INVALID_ARG;
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
+  if (op == 4) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  const i64 nin = (op == 3) ? p->M : p->N;
+  const i64 nout = (op == 2) ? p->M : p->N;
+  double* in = (op == 3) ? p->d_win : p->d_vin;
+  double* res = (op == 2) ? p->d_wout : p->d_vout;
+  GPFVM_CUDA(cudaMemcpyAsync(in, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
+  p->p_op[op].run(st);
+  GPFVM_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * nout, cudaMemcpyDeviceToDevice, st));
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  return GPFVM_OK;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info* info, void* stream) {
+  if (!p) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  return run_solve(p, opts, info, pick_stream(p, stream));
+  GPFVM_GUARD_END
+}
+
+int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream) {
+  if (!p || (!mean && !var)) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  const int r = run_query(p, mean, var, st);
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  return r;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_solve_host(gpfvm_problem* p, const double* values_host, const gpfvm_solve_opts* opts, double* mean_host,
+                     double* var_host, gpfvm_solve_info* info, void* stream) {
+  if (!p || !opts || !mean_host) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  if (values_host && p->M > 0)
+    GPFVM_CUDA(cudaMemcpyAsync(p->d_yB, values_host, sizeof(double) * p->M, cudaMemcpyHostToDevice, st));
+  int r;
+  if (!p->assembled) {
+    r = run_assemble(p, st);
+    if (r != GPFVM_OK) return r;
+  } else {
+    p->p_rhs.run(st);
+  }
+  r = run_solve(p, opts, info, st);
+  if (r < 0) return r;
+  const int q = run_query(p, p->d_mean, var_host ? p->d_var : nullptr, st);
+  if (q != GPFVM_OK) return q;
+  GPFVM_CUDA(cudaMemcpyAsync(mean_host, p->d_mean, sizeof(double) * p->P, cudaMemcpyDeviceToHost, st));
+  if (var_host) GPFVM_CUDA(cudaMemcpyAsync(var_host, p->d_var, sizeof(double) * p->P, cudaMemcpyDeviceToHost, st));
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  return r;
+  GPFVM_GUARD_END
+}
+
+int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream) {
+  if (!p || !host_out) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  const double* src = nullptr;
+  i64 n = 0;
+  switch (what) {
+    case 0: src = p->d_b; n = p->N; break;
+    case 1: src = p->d_x; n = p->N; break;
+    case 2: src = p->d_A; n = p->M * p->M; break;
+    case 3: src = p->d_Linv; n = p->M * p->M; break;
+    case 5: src = p->d_down; n = p->P; break;
+    case 6: src = p->d_eta; n = p->last.iterations; break;
+    default: return GPFVM_ERR_INVALID_ARG;
+  }
+  if (n > capacity) return GPFVM_ERR_INVALID_ARG;
+  if (what == 2) {
+    // G_BB is overwritten by the Cholesky recursion: rebuild it
+    p->p_setup.run(st);
+  }
+  if (n > 0) GPFVM_CUDA(cudaMemcpyAsync(host_out, src, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  return n;
+  GPFVM_GUARD_END
+}
+
+int64_t gpfvm_factor(gpfvm_problem* p, int axis, int kind_a, int arg_a, int kind_b, int arg_b, double* host_out,
+                     int64_t capacity, void* stream) {
+  if (!p || !host_out || axis < 0 || axis >= p->d) return GPFVM_ERR_INVALID_ARG;
+  auto it = p->fac_off.find(FKey(axis, kind_a, arg_a, kind_b, arg_b));
+  if (it == p->fac_off.end()) return GPFVM_ERR_NOT_FOUND;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  const i64 n = fam_n(p, axis, kind_a, arg_a) * fam_n(p, axis, kind_b, arg_b);
+  if (n > capacity) return GPFVM_ERR_INVALID_ARG;
+  p->p_setup.run(st);
+  GPFVM_CUDA(cudaMemcpyAsync(host_out, p->d_fac + it->second, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  return n;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_set_values(gpfvm_problem* p, const double* values, void* stream) {
+  if (!p || (!values && p->M > 0)) return GPFVM_ERR_INVALID_ARG;
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  if (p->M > 0) GPFVM_CUDA(cudaMemcpyAsync(p->d_yB, values, sizeof(double) * p->M, cudaMemcpyDeviceToDevice, st));
+  p->p_rhs.run(st);
+  p->solved = false;
+  return GPFVM_OK;
+  GPFVM_GUARD_END
+}
+
+int64_t gpfvm_launch_count(void) { return g_launches.load(); }
+
+const char* gpfvm_strerror(int code) {
+  switch (code) {
+    case GPFVM_OK: return "ok";
+    case GPFVM_NOT_CONVERGED: return "iteration budget exhausted before the tolerance";
+    case GPFVM_ERR_INVALID_ARG: return "invalid argument";
+    case GPFVM_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case GPFVM_ERR_NOT_SPD: return "IC/BC Gram matrix not positive definite (Cholesky pivot <= 0)";
+    case GPFVM_ERR_BREAKDOWN: return "CG breakdown (p^T G p <= 0 or not finite)";
+    case GPFVM_ERR_DEVICE: return "CUDA error";
+    case GPFVM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GPFVM_ERR_STATE: return "call out of order";
+    case GPFVM_ERR_NOT_FOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* gpfvm_version(void) { return "gpfvm 0.1 sm_103a"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solves: every problem iterates on its own stream; chunks of graph
+// replays are issued round-robin so that the problems' kernels overlap on the
+// device, and converged problems drop out (their kernels become no-ops).
+// ---------------------------------------------------------------------------
+extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts, gpfvm_solve_info* infos,
+                                 void* stream) {
+  if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
+  if (opts->precision == GPFVM_MIXED_TF32) {
+    int worst = GPFVM_OK;
+    for (int i = 0; i < n; ++i) {
+      const int r = gpfvm_solve(ps[i], opts, infos ? &infos[i] : nullptr, nullptr);
+      if (r < worst || (worst == GPFVM_OK && r != GPFVM_OK)) worst = r;
+    }
+    return worst;
+  }
+  GPFVM_GUARD_BEGIN
+  cudaEvent_t ev;
+  GPFVM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (stream) GPFVM_CUDA(cudaEventRecord(ev, (cudaStream_t)stream));
+  std::vector<cudaStream_t> sts(n);
+  std::vector<int> active(n, 1);
+  int worst = GPFVM_OK;
+  for (int i = 0; i < n; ++i) {
+    sts[i] = pick_stream(ps[i], nullptr);
+    if (stream) GPFVM_CUDA(cudaStreamWaitEvent(sts[i], ev, 0));
+    const int b = solve_begin(ps[i], opts, sts[i]);
+    if (b != GPFVM_OK) {
+      active[i] = 0;
+      worst = std::min(worst, b);
+      if (infos) infos[i].status = b;
+    }
+  }
+  const int chunk = opts->check_every > 0 ? opts->check_every : 16;
+  int left = 0;
+  for (int i = 0; i < n; ++i) left += active[i];
+  while (left > 0) {
+    for (int i = 0; i < n; ++i)
+      if (active[i]) solve_launch(ps[i], chunk, sts[i]);
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      GPFVM_CUDA(cudaStreamSynchronize(sts[i]));
+      if (solve_finished(ps[i])) {
+        const int r = solve_end(ps[i], infos ? &infos[i] : nullptr, sts[i]);
+        if (r < 0) worst = std::min(worst, r);
+        else if (r == GPFVM_NOT_CONVERGED && worst == GPFVM_OK) worst = r;
+        active[i] = 0;
+        --left;
+      }
+    }
+  }
+  cudaEventDestroy(ev);
+  return worst;
+  GPFVM_GUARD_END
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop with continuous batching.
+// ---------------------------------------------------------------------------
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  int64_t ticket = 0;
+  gpfvm_desc desc{};
+  std::vector<std::vector<double>> store;  // owned copies of every descriptor array
+  gpfvm_problem* p = nullptr;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  int code = 0;
+  std::vector<double> mean, var;
+  gpfvm_solve_info info{};
+  double t_submit = 0;
+};
+
+const double* own_copy(Request& R, const double* src, i64 n) {
+  if (!src) return nullptr;
+  R.store.emplace_back(src, src + n);
+  return R.store.back().data();
+}
+
+}  // namespace
+
+struct gpfvm_server {
+  gpfvm_server_opts o{};
+  std::deque<Request*> queue;
+  std::vector<Request*> running;
+  std::map<int64_t, std::unique_ptr<Request>> all;
+  int64_t next = 0;
+  int64_t used = 0, budget = 0;
+};
+
+extern "C" int gpfvm_server_create(const gpfvm_server_opts* o, gpfvm_server** out) {
+  if (!o || !out || o->max_slots < 1 || o->steps_per_tick < 1 || o->solve.max_iter < 1) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  auto* s = new gpfvm_server();
+  s->o = *o;
+  s->budget = o->memory_budget;
+  if (s->budget <= 0) {
+    size_t fr = 0, tot = 0;
+    GPFVM_CUDA(cudaMemGetInfo(&fr, &tot));
+    s->budget = (int64_t)(0.9 * (double)fr);
+  }
+  *out = s;
+  return GPFVM_OK;
+  GPFVM_GUARD_END
+}
+
+extern "C" int gpfvm_server_submit(gpfvm_server* s, const gpfvm_desc* d, int64_t* ticket) {
+  if (!s || !d || !ticket) return GPFVM_ERR_INVALID_ARG;
+  const int v = validate(d);
+  if (v != GPFVM_OK) return v;
+  auto R = std::make_unique<Request>();
+  R->desc = *d;
+  R->store.reserve(4 + 3 * GPFVM_MAX_SETS + 8);
+  i64 N = 1;
+  for (int i = 0; i < d->ndim; ++i) {
+    R->desc.edges[i] = own_copy(*R, d->edges[i], d->n_cells[i] + 1);
+    R->desc.pred[i] = own_copy(*R, d->pred[i], d->n_pred[i]);
+    N *= d->n_cells[i];
+  }
+  R->desc.rhs = own_copy(*R, d->rhs, N);
+  for (int k = 0; k < d->n_sets; ++k) {
+    i64 n = 1;
+    for (int i = 0; i < d->ndim; ++i) {
+      R->desc.sets[k].coords[i] = own_copy(*R, d->sets[k].coords[i], d->sets[k].n_pts[i]);
+      n *= d->sets[k].n_pts[i];
+    }
+    R->desc.sets[k].values = own_copy(*R, d->sets[k].values, n);
+  }
+  R->ticket = s->next++;
+  R->t_submit = now_ms();
+  *ticket = R->ticket;
+  s->queue.push_back(R.get());
+  s->all[R->ticket] = std::move(R);
+  return GPFVM_OK;
+}
+
+static void finish_request(gpfvm_server* s, Request* R, int code) {
+  R->code = code;
+  R->state = 2;
+  R->info.latency_ms = now_ms() - R->t_submit;
+  if (R->p) {
+    s->used -= R->p->mem.bytes;
+    gpfvm_destroy(R->p);
+    R->p = nullptr;
+  }
+}
+
+extern "C" int gpfvm_server_step(gpfvm_server* s) {
+  if (!s) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  // admit queued requests while slots and memory allow (FIFO)
+  while (!s->queue.empty() && (int)s->running.size() < s->o.max_slots) {
+    Request* R = s->queue.front();
+    gpfvm_problem* p = nullptr;
+    int r = gpfvm_create(&R->desc, s->o.solve.max_iter, &p);
+    if (r == GPFVM_ERR_OUT_OF_MEMORY || (r == GPFVM_OK && s->used + p->mem.bytes > s->budget)) {
+      if (p) gpfvm_destroy(p);
+      if (s->running.empty()) {  // can never fit: fail it rather than stall the queue
+        s->queue.pop_front();
+        finish_request(s, R, GPFVM_ERR_OUT_OF_MEMORY);
+        continue;
+      }
+      break;
+    }
+    s->queue.pop_front();
+    if (r != GPFVM_OK) {
+      finish_request(s, R, r);
+      continue;
+    }
+    R->p = p;
+    s->used += p->mem.bytes;
+    cudaStream_t st = pick_stream(p, nullptr);
+    r = run_assemble(p, st);
+    if (r == GPFVM_OK) r = solve_begin(p, &s->o.solve, st);
+    if (r != GPFVM_OK) {
+      finish_request(s, R, r);
+      continue;
+    }
+    R->state = 1;
+    s->running.push_back(R);
+  }
+  // one tick of iterations for every resident request, overlapped across streams
+  for (Request* R : s->running) solve_launch(R->p, s->o.steps_per_tick, pick_stream(R->p, nullptr));
+  std::vector<Request*> still;
+  for (Request* R : s->running) {
+    cudaStream_t st = pick_stream(R->p, nullptr);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (!solve_finished(R->p)) {
+      still.push_back(R);
+      continue;
+    }
+    int r = solve_end(R->p, &R->info, st);
+    if (r >= 0) {
+      R->mean.resize(R->p->P);
+      if (s->o.solve.want_var) R->var.resize(R->p->P);
+      const int q = run_query(R->p, R->p->d_mean, s->o.solve.want_var ? R->p->d_var : nullptr, st);
+      if (q == GPFVM_OK) {
+        GPFVM_CUDA(cudaMemcpyAsync(R->mean.data(), R->p->d_mean, sizeof(double) * R->p->P, cudaMemcpyDeviceToHost, st));
+        if (s->o.solve.want_var)
+          GPFVM_CUDA(cudaMemcpyAsync(R->var.data(), R->p->d_var, sizeof(double) * R->p->P, cudaMemcpyDeviceToHost, st));
+        GPFVM_CUDA(cudaStreamSynchronize(st));
+      } else {
+        r = q;
+      }
+    }
+    finish_request(s, R, r);
+  }
+  s->running.swap(still);
+  return (int)(s->queue.size() + s->running.size());
+  GPFVM_GUARD_END
+}
+
+extern "C" int gpfvm_server_poll(gpfvm_server* s, int64_t ticket, double* mean, double* var, gpfvm_solve_info* info) {
+  if (!s) return GPFVM_ERR_INVALID_ARG;
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return GPFVM_ERR_NOT_FOUND;
+  Request* R = it->second.get();
+  if (R->state != 2) return 2;
+  if (info) *info = R->info;
+  if (R->code >= 0) {
+    if (mean) std::memcpy(mean, R->mean.data(), R->mean.size() * sizeof(double));
+    if (var && !R->var.empty()) std::memcpy(var, R->var.data(), R->var.size() * sizeof(double));
+  }
+  return R->code;
+}
+
+extern "C" void gpfvm_server_destroy(gpfvm_server* s) {
+  if (!s) return;
+  for (auto& kv : s->all)
+    if (kv.second->p) gpfvm_destroy(kv.second->p);
+  delete s;
+}

@@ -1,0 +1,339 @@
+// CG / IterGP iteration kernels (Sec. 4.1 "Iterative techniques", Sec. 4.2).
+//
+// Per iteration j (x0 = 0, r0 = p0 = b):
+//   q = G^ p                           (structured matvec plan, also w = G_BB^-1 G_BP p)
+//   eta_j = p.q                        (k_dot_eta)
+//   u = Lhat k(X*)^T p,  down += u^2/eta_j   (IterGP combined-posterior downdate)
+//   alpha = r.r/eta, x += alpha p, r -= alpha q, beta = r'.r'/r.r   (k_update)
+//   p = r' + beta p                    (k_pupdate)
+//   p -= sum_i (q_i.p / eta_i) p_i     (full reorthogonalisation, Sec. 5)
+// All scalars live in device memory (CGState), so an iteration is a fixed
+// launch sequence that a CUDA graph replays; reductions use a fixed-order
+// "last block" sum so results do not depend on block scheduling.
+#include "cg.cuh"
+
+namespace gpfvm {
+
+constexpr int RT = 256;  // threads per reduction block
+
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return am_last;
+}
+
+__device__ double sum_partials(const double* part, int n, double* smem) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += ((volatile const double*)part)[i];
+  return block_sum<RT>(v, smem);
+}
+
+__global__ void __launch_bounds__(RT) k_init(const double* __restrict__ b, double* __restrict__ x,
+                                              double* __restrict__ r, double* __restrict__ p, i64 n,
+                                              CGState* st) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const double v = b[i];
+    x[i] = 0.0;
+    r[i] = v;
+    p[i] = v;
+    acc += v * v;
+  }
+  acc = block_sum<RT>(acc, red);
+  if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
+  if (last_block(&st->ticket[0])) {
+    const double s = sum_partials(st->part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->rr = s;
+      st->bnorm2 = s;
+      st->k = 0;
+      st->status = 0;
+      st->converged = (s == 0.0);
+      st->done = (s == 0.0) || (st->max_iter <= 0);
+      st->ticket[0] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_dot_eta(const double* __restrict__ p, const double* __restrict__ q, i64 n,
+                                                 CGState* st, double* __restrict__ eta_hist) {
+  if (st->done) return;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) acc = fma(p[i], q[i], acc);
+  acc = block_sum<RT>(acc, red);
+  if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
+  if (last_block(&st->ticket[1])) {
+    const double s = sum_partials(st->part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->eta = s;
+      if (!(s > 0.0) || !isfinite(s)) {
+        st->status |= DEV_BREAKDOWN;
+        st->done = 1;
+      } else if (st->k < st->cap) {
+        eta_hist[st->k] = s;
+      }
+      st->ticket[1] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_downdate(const double* __restrict__ u, double* __restrict__ down, i64 n,
+                                                  const CGState* st) {
+  if (st->done) return;
+  const double inv = 1.0 / st->eta;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const double v = u[i];
+    down[i] = fma(v * v, inv, down[i]);
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_update(double* __restrict__ x, double* __restrict__ r,
+                                                const double* __restrict__ p, const double* __restrict__ q, i64 n,
+                                                CGState* st, double* __restrict__ S, double* __restrict__ Q) {
+  if (st->done) return;
+  __shared__ double red[32];
+  const double alpha = st->rr / st->eta;
+  const int k = st->k;
+  const bool keep = (S != nullptr) && (k < st->cap);
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const double pi = p[i], qi = q[i];
+    x[i] = fma(alpha, pi, x[i]);
+    const double ri = fma(-alpha, qi, r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+    if (keep) {
+      S[(i64)k * n + i] = pi;
+      Q[(i64)k * n + i] = qi;
+    }
+  }
+  acc = block_sum<RT>(acc, red);
+  if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
+  if (last_block(&st->ticket[2])) {
+    const double s = sum_partials(st->part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->alpha = alpha;
+      st->beta = s / st->rr;
+      st->rr = s;
+      st->k = k + 1;
+      if (!isfinite(s)) {
+        st->status |= DEV_BREAKDOWN;
+        st->done = 1;
+      }
+      if (s <= st->rtol2 * st->bnorm2) {
+        st->converged = 1;
+        st->done = 1;
+      }
+      if (k + 1 >= st->max_iter) st->done = 1;
+      st->ticket[2] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_pupdate(const double* __restrict__ r, double* __restrict__ p, i64 n,
+                                                 const CGState* st) {
+  if (st->done) return;
+  const double beta = st->beta;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) p[i] = fma(beta, p[i], r[i]);
+}
+
+// partial dots part2[j * nchunk + c] = sum_{i in chunk c} Q[j][i] p[i] for j < k
+__global__ void __launch_bounds__(RT) k_reorth_dots(const double* __restrict__ Q, const double* __restrict__ p, i64 n,
+                                                     int chunk, const CGState* st, double* __restrict__ part2) {
+  if (st->done) return;
+  const int k = min(st->k, st->cap);
+  const int c = blockIdx.x, nchunk = gridDim.x;
+  const i64 lo = (i64)c * chunk;
+  const i64 hi = min(n, lo + chunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = blockIdx.y * (RT / 32) + warp; j < k; j += gridDim.y * (RT / 32)) {
+    const double* qj = Q + (i64)j * n;
+    double s = 0.0;
+    for (i64 i = lo + lane; i < hi; i += 32) s = fma(qj[i], p[i], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part2[(i64)j * nchunk + c] = s;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_reorth_coef(const double* __restrict__ part2, int nchunk,
+                                                     const double* __restrict__ eta_hist, const CGState* st,
+                                                     double* __restrict__ coef) {
+  if (st->done) return;
+  const int k = min(st->k, st->cap);
+  const int j = blockIdx.x * RT + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part2[(i64)j * nchunk + c];
+  coef[j] = s / eta_hist[j];
+}
+
+__global__ void __launch_bounds__(RT) k_reorth_apply(const double* __restrict__ S, double* __restrict__ p, i64 n,
+                                                      const CGState* st, const double* __restrict__ coef) {
+  if (st->done) return;
+  __shared__ double cs[1024];
+  const int k = min(st->k, st->cap);
+  const i64 i = (i64)blockIdx.x * RT + threadIdx.x;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int j0 = 0; j0 < k; j0 += 1024) {
+    const int jn = min(1024, k - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < jn; t += RT) cs[t] = coef[j0 + t];
+    __syncthreads();
+    if (i < n) {
+      int j = 0;
+      for (; j + 1 < jn; j += 2) {
+        acc0 = fma(S[(i64)(j0 + j) * n + i], cs[j], acc0);
+        acc1 = fma(S[(i64)(j0 + j + 1) * n + i], cs[j + 1], acc1);
+      }
+      if (j < jn) acc0 = fma(S[(i64)(j0 + j) * n + i], cs[j], acc0);
+    }
+  }
+  if (i < n) p[i] -= acc0 + acc1;
+}
+
+// ---------------------------------------------------------------------------
+int reduce_grid(i64 n) {
+  int g = ceil_div(n, RT * 4);
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  return g;
+}
+
+void cg_init(const double* b, double* x, double* r, double* p, i64 n, CGState* st, cudaStream_t s) {
+  k_init<<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st);
+  GPFVM_LAUNCH_CHECK();
+}
+void cg_dot_eta(const double* p, const double* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
+  k_dot_eta<<<reduce_grid(n), RT, 0, s>>>(p, q, n, st, eta_hist);
+  GPFVM_LAUNCH_CHECK();
+}
+void cg_downdate(const double* u, double* down, i64 n, const CGState* st, cudaStream_t s) {
+  k_downdate<<<ceil_div(n, RT), RT, 0, s>>>(u, down, n, st);
+  GPFVM_LAUNCH_CHECK();
+}
+void cg_update(double* x, double* r, const double* p, const double* q, i64 n, CGState* st, double* S, double* Q,
+               cudaStream_t s) {
+  k_update<<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q);
+  GPFVM_LAUNCH_CHECK();
+}
+void cg_pupdate(const double* r, double* p, i64 n, const CGState* st, cudaStream_t s) {
+  k_pupdate<<<ceil_div(n, RT), RT, 0, s>>>(r, p, n, st);
+  GPFVM_LAUNCH_CHECK();
+}
+int reorth_chunks(i64 n) {
+  int c = ceil_div(n, 4096);
+  return c < 1 ? 1 : c;
+}
+void cg_reorth(const double* S, const double* Q, double* p, i64 n, int cap, const CGState* st, double* part2,
+               double* coef, const double* eta_hist, cudaStream_t s) {
+  const int nchunk = reorth_chunks(n);
+  const int chunk = (int)((n + nchunk - 1) / nchunk);
+  int gy = ceil_div(cap, RT / 32);
+  const int target = 4 * 152;
+  if ((i64)gy * nchunk > target) gy = (target + nchunk - 1) / nchunk;
+  if (gy < 1) gy = 1;
+  k_reorth_dots<<<dim3(nchunk, gy), RT, 0, s>>>(Q, p, n, chunk, st, part2);
+  GPFVM_LAUNCH_CHECK();
+  k_reorth_coef<<<ceil_div(cap, RT), RT, 0, s>>>(part2, nchunk, eta_hist, st, coef);
+  GPFVM_LAUNCH_CHECK();
+  k_reorth_apply<<<ceil_div(n, RT), RT, 0, s>>>(S, p, n, st, coef);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// ---- small vector helpers -------------------------------------------------
+__global__ void k_axpby(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                        double sa, double sb, i64 n) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) out[i] = sa * a[i] + sb * b[i];
+}
+void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  k_axpby<<<g, RT, 0, s>>>(a, b, out, sa, sb, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+__global__ void k_norm2(const double* __restrict__ v, i64 n, double* out, double* part, unsigned int* ticket) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) acc = fma(v[i], v[i], acc);
+  acc = block_sum<RT>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (last_block(ticket)) {
+    const double s = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      *out = s;
+      *ticket = 0;
+    }
+  }
+}
+void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s) {
+  k_norm2<<<reduce_grid(n), RT, 0, s>>>(v, n, out, st->part, &st->ticket[3]);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// var = outputscale - vB - down
+__global__ void k_var_final(const double* __restrict__ vB, const double* __restrict__ down, double* __restrict__ var,
+                            double s2, i64 n) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT)
+    var[i] = s2 - (vB ? vB[i] : 0.0) - (down ? down[i] : 0.0);
+}
+void var_final(const double* vB, const double* down, double* var, double s2, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  k_var_final<<<g, RT, 0, s>>>(vB, down, var, s2, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// acc[j] += sum_{i < rows} Y[i][j]^2   (column sums of squares, fixed order over i)
+__global__ void k_colsumsq(const double* __restrict__ Y, int rows, i64 cols, double* __restrict__ acc) {
+  const i64 j = (i64)blockIdx.x * RT + threadIdx.x;
+  if (j >= cols) return;
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  for (; i + 1 < rows; i += 2) {
+    const double a = Y[(i64)i * cols + j], b = Y[(i64)(i + 1) * cols + j];
+    s0 = fma(a, a, s0);
+    s1 = fma(b, b, s1);
+  }
+  if (i < rows) {
+    const double a = Y[(i64)i * cols + j];
+    s0 = fma(a, a, s0);
+  }
+  acc[j] += s0 + s1;
+}
+void colsumsq(const double* Y, int rows, i64 cols, double* acc, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  k_colsumsq<<<ceil_div(cols, RT), RT, 0, s>>>(Y, rows, cols, acc);
+  GPFVM_LAUNCH_CHECK();
+}
+
+__global__ void k_transpose(const double* __restrict__ A, double* __restrict__ B, int m, int n) {
+  __shared__ double t[32][33];
+  const int x = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8)
+    if (x < n && y0 + yy < m) t[yy][threadIdx.x] = A[(i64)(y0 + yy) * n + x];
+  __syncthreads();
+  const int xo = y0 + threadIdx.x;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int yo = blockIdx.x * 32 + yy;
+    if (xo < m && yo < n) B[(i64)yo * m + xo] = t[threadIdx.x][yy];
+  }
+}
+void transpose(const double* A, double* B, int m, int n, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return;
+  k_transpose<<<dim3(ceil_div(n, 32), ceil_div(m, 32)), dim3(32, 8), 0, s>>>(A, B, m, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+}  // namespace gpfvm

@@ -1,0 +1,34 @@
+// CG / IterGP device state and launch helpers (see cg.cu).
+#pragma once
+#include "common.cuh"
+
+namespace gpfvm {
+
+constexpr int CG_MAX_PART = 1024;
+
+struct CGState {
+  double rr, bnorm2, rtol2, eta, alpha, beta;
+  double aux[8];
+  int k, done, converged, status, max_iter, cap;
+  int pad[2];
+  unsigned int ticket[8];
+  double part[CG_MAX_PART];
+};
+
+int reduce_grid(i64 n);
+int reorth_chunks(i64 n);
+void cg_init(const double* b, double* x, double* r, double* p, i64 n, CGState* st, cudaStream_t s);
+void cg_dot_eta(const double* p, const double* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
+void cg_downdate(const double* u, double* down, i64 n, const CGState* st, cudaStream_t s);
+void cg_update(double* x, double* r, const double* p, const double* q, i64 n, CGState* st, double* S, double* Q,
+               cudaStream_t s);
+void cg_pupdate(const double* r, double* p, i64 n, const CGState* st, cudaStream_t s);
+void cg_reorth(const double* S, const double* Q, double* p, i64 n, int cap, const CGState* st, double* part2,
+               double* coef, const double* eta_hist, cudaStream_t s);
+void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s);
+void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s);
+void var_final(const double* vB, const double* down, double* var, double s2, i64 n, cudaStream_t s);
+void colsumsq(const double* Y, int rows, i64 cols, double* acc, cudaStream_t s);
+void transpose(const double* A, double* B, int m, int n, cudaStream_t s);
+
+}  // namespace gpfvm

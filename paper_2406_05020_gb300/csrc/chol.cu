@@ -1,0 +1,137 @@
+// IC/BC stage of the Cholesky deflation (Sec. 4.2): G_BB = L L^T and the
+// explicit inverse factor L^-1, so that every CG iteration applies
+// G_BB^-1 = L^-T L^-1 with two parallel triangular GEMVs instead of two
+// sequential triangular solves.
+//
+// Recursive 2x2 block form (all blocks aligned to 64):
+//   L11, L11^-1 = chol_inv(A11)
+//   L21 = A21 L11^-T
+//   A22 <- A22 - L21 L21^T                     (lower tiles only)
+//   L22, L22^-1 = chol_inv(A22)
+//   (L^-1)21 = -L22^-1 (L21 L11^-1)
+// The base case (n <= 64) runs in one CTA from shared memory.
+#include "plan.cuh"
+
+namespace gpfvm {
+
+__global__ void __launch_bounds__(256) chol_base_kernel(const double* __restrict__ A, double* __restrict__ L,
+                                                        double* __restrict__ Linv, int n, i64 lda,
+                                                        int* status) {
+  extern __shared__ double sm[];
+  constexpr int LD = 65;
+  double* Ls = sm;            // 64 x 65
+  double* Xs = sm + 64 * LD;  // 64 x 65
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < 64 * 64; e += blockDim.x) {
+    const int i = e / 64, j = e % 64;
+    Ls[i * LD + j] = (i < n && j <= i) ? A[(i64)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double d = Ls[j * LD + j];
+      if (!(d > 0.0)) {
+        bad = 1;
+        Ls[j * LD + j] = 1.0;
+      } else {
+        Ls[j * LD + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double piv = Ls[j * LD + j];
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) Ls[i * LD + j] /= piv;
+    __syncthreads();
+    const int w = n - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int ii = j + 1 + e / w, ll = j + 1 + e % w;
+      if (ll <= ii) Ls[ii * LD + ll] -= Ls[ii * LD + j] * Ls[ll * LD + j];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower factor, one column per thread (forward substitution)
+  if (tid < n) {
+    const int c = tid;
+    for (int i = 0; i < c; ++i) Xs[i * LD + c] = 0.0;
+    for (int i = c; i < n; ++i) {
+      double s0 = (i == c) ? 1.0 : 0.0, s1 = 0.0;
+      int l = c;
+      for (; l + 1 < i; l += 2) {
+        s0 -= Ls[i * LD + l] * Xs[l * LD + c];
+        s1 -= Ls[i * LD + l + 1] * Xs[(l + 1) * LD + c];
+      }
+      if (l < i) s0 -= Ls[i * LD + l] * Xs[l * LD + c];
+      Xs[i * LD + c] = (s0 + s1) / Ls[i * LD + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    L[(i64)i * lda + j] = (j <= i) ? Ls[i * LD + j] : 0.0;
+    Linv[(i64)i * lda + j] = (j <= i) ? Xs[i * LD + j] : 0.0;
+  }
+  if (tid == 0 && bad) atomicOr(status, (int)DEV_NOT_SPD);
+}
+
+void launch_chol_base(const double* A, double* L, double* Linv, int n, i64 lda, int* status,
+                      cudaStream_t st) {
+  const int smem = 2 * 64 * 65 * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    GPFVM_CUDA(cudaFuncSetAttribute(chol_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  chol_base_kernel<<<1, 256, smem, st>>>(A, L, Linv, n, lda, status);
+  GPFVM_LAUNCH_CHECK();
+}
+
+static GemmDesc gdesc(int m, int n, int k, i64 a_rs, i64 a_cs, i64 b_rs, i64 b_cs, i64 c_rs, int tri) {
+  GemmDesc g{};
+  g.m = m; g.n = n; g.k = k;
+  g.a_rs = a_rs; g.a_cs = a_cs; g.b_rs = b_rs; g.b_cs = b_cs; g.c_rs = c_rs; g.d_rs = 0;
+  g.batch = 1; g.tri = tri; g.tile = 0;
+  return g;
+}
+
+void plan_chol_inverse(Plan& plan, double* A, double* L, double* Linv, int n, i64 lda,
+                       double* scratch, int* status) {
+  if (n <= 0) return;
+  if (n <= 64) {
+    plan.func([=](cudaStream_t st) { launch_chol_base(A, L, Linv, n, lda, status, st); });
+    return;
+  }
+  const int nb = (n + 63) / 64;
+  const int n1 = 64 * ((nb + 1) / 2);
+  const int n2 = n - n1;
+  double* A21 = A + (i64)n1 * lda;
+  double* A22 = A21 + n1;
+  double* L21 = L + (i64)n1 * lda;
+  double* L22 = L21 + n1;
+  double* Li21 = Linv + (i64)n1 * lda;
+  double* Li22 = Li21 + n1;
+  plan_chol_inverse(plan, A, L, Linv, n1, lda, scratch, status);
+  // L21 = A21 * Linv11^T ; B(kk, j) = Linv11[j][kk] is upper triangular in (kk, j)
+  {
+    GemmGroup G{L21, nullptr, 0.0, 0.0, 0, 0};
+    plan.gemm(gdesc(n2, n1, n1, lda, 1, 1, lda, lda, TRI_B_UPPER), {{G, {GemmSeg{A21, Linv, 1.0}}}});
+  }
+  // A22 -= L21 * L21^T (lower tiles)
+  {
+    GemmGroup G{A22, nullptr, 1.0, 0.0, 0, 0};
+    plan.gemm(gdesc(n2, n2, n1, lda, 1, 1, lda, lda, TRI_C_LOWER), {{G, {GemmSeg{L21, L21, -1.0}}}});
+  }
+  plan_chol_inverse(plan, A22, L22, Li22, n2, lda, scratch, status);
+  // T = L21 * Linv11 (Linv11 lower: B(kk, j) = 0 for kk < j)
+  {
+    GemmGroup G{scratch, nullptr, 0.0, 0.0, 0, 0};
+    plan.gemm(gdesc(n2, n1, n1, lda, 1, lda, 1, n1, TRI_B_LOWER), {{G, {GemmSeg{L21, Linv, 1.0}}}});
+  }
+  // Linv21 = -Linv22 * T (Linv22 lower: A(i, kk) = 0 for kk > i)
+  {
+    GemmGroup G{Li21, nullptr, 0.0, 0.0, 0, 0};
+    plan.gemm(gdesc(n2, n1, n2, lda, 1, n1, 1, lda, TRI_A_LOWER), {{G, {GemmSeg{Li22, scratch, -1.0}}}});
+  }
+}
+
+}  // namespace gpfvm

@@ -1,0 +1,75 @@
+// Kernel interfaces of the GP-FVM GPU library.
+#pragma once
+#include "common.cuh"
+
+namespace gpfvm {
+
+// ---- 1D factor assembly (factors.cu) -------------------------------------
+// kind 0: cell family over edges ca[0..n] with derivative order ord (0..2);
+// kind 1: point family at ca[0..n) with derivative order ord (0..1).
+struct FactorJob {
+  int kind_a, ord_a, n_a;
+  int kind_b, ord_b, n_b;
+  const double* ca;
+  const double* cb;
+  double ell;
+  double* out;  // n_a x n_b row-major
+};
+void launch_factors(const FactorJob* d_jobs, int n_jobs, i64 max_entries, cudaStream_t st);
+
+struct GbbParams {
+  int M, ndim, n_sets;
+  int off[GPFVM_MAX_SETS + 1];
+  int dims[GPFVM_MAX_SETS][GPFVM_MAX_DIM];
+  double noise[GPFVM_MAX_SETS];
+  double outputscale;
+  const double* fac[GPFVM_MAX_SETS][GPFVM_MAX_SETS][GPFVM_MAX_DIM];
+};
+void launch_gbb(const GbbParams& P, double* G, cudaStream_t st);
+
+// ---- grouped, segmented, batched, strided FP64 GEMM (gemm64.cu) -----------
+// For every group g and batch entry b:
+//   C_g[b](i,j) = beta_g C_g[b](i,j) + gamma_g D_g[b](i,j)
+//               + sum_{s in segs of g} alpha_s sum_kk A_s[b](i,kk) B_s[b](kk,j)
+// with A(i,kk) at A + b*a_bs + i*a_rs + kk*a_cs, B(kk,j) at B + b*b_bs +
+// kk*b_rs + j*b_cs, C(i,j) at C + b*c_bs + i*c_rs + j, D likewise with d_rs.
+struct GemmSeg {
+  const double* A;
+  const double* B;
+  double alpha;
+};
+struct GemmGroup {
+  double* C;
+  const double* D;
+  double beta, gamma;
+  int seg0, nseg;
+};
+enum GemmTri {
+  TRI_A_LOWER = 1,  // A(i,kk) = 0 for kk > i
+  TRI_A_UPPER = 2,  // A(i,kk) = 0 for kk < i
+  TRI_B_UPPER = 4,  // B(kk,j) = 0 for kk > j
+  TRI_B_LOWER = 8,  // B(kk,j) = 0 for kk < j
+  TRI_C_LOWER = 16  // only tiles touching the lower triangle of C are computed
+};
+struct GemmDesc {
+  int m, n, k;
+  i64 a_rs, a_cs, b_rs, b_cs, c_rs, d_rs;
+  i64 a_bs, b_bs, c_bs, d_bs;
+  int batch, n_groups, tri, tile;  // tile: 0 = 64x64, 1 = 32x64, 2 = 16x64 (rows x cols)
+  const GemmSeg* segs;
+  const GemmGroup* groups;
+  const int* skip;  // if non-null and *skip != 0 the launch does nothing (converged CG)
+};
+void launch_gemm64(const GemmDesc& g, cudaStream_t st);
+
+// y(i) = alpha * sum_{j in tri range} A(i,j) x(j) + beta y(i); A row-major lda.
+// tri: 0 full, 1 lower (j <= i), 2 upper (j >= i).
+void launch_gemv64(int m, int n, const double* A, i64 lda, const double* x, double* y, double alpha,
+                   double beta, int tri, cudaStream_t st, const int* skip = nullptr);
+
+// ---- IC/BC stage base case (chol.cu) ---------------------------------------
+// One CTA factorises an n <= 64 diagonal block: L = chol(A) and Linv = L^-1.
+void launch_chol_base(const double* A, double* L, double* Linv, int n, i64 lda, int* status,
+                      cudaStream_t st);
+
+}  // namespace gpfvm

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libgpfvm (include/gpfvm.h).
+
+Argument marshalling only: every step of the GP-FVM path runs in the CUDA
+library.  Device buffers are torch tensors (float64, cuda), passed by pointer;
+the CUDA stream is torch's current stream unless one is given.  If the library
+has not been built the import of this module fails loudly -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgpfvm.so")
+
+MAX_DIM, MAX_TERMS, MAX_SETS = 3, 8, 8
+OK, NOT_CONVERGED = 0, 1
+FP64, MIXED_TF32 = 0, 1
+
+_lib = None
+
+
+def lib():
+    """Loads libgpfvm.so; raises if it is missing (build with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgpfvm.so not found at {LIB_PATH}: run paper_2406_05020_gb300.build.build()")
+        _lib = C.CDLL(LIB_PATH)
+        _declare(_lib)
+    return _lib
+
+
+class PointSet(C.Structure):
+    _fields_ = [("order", C.c_int * MAX_DIM), ("n_pts", C.c_int * MAX_DIM),
+                ("coords", C.POINTER(C.c_double) * MAX_DIM), ("values", C.POINTER(C.c_double)),
+                ("noise_var", C.c_double)]
+
+
+class Desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n_cells", C.c_int * MAX_DIM), ("edges", C.POINTER(C.c_double) * MAX_DIM),
+                ("lengthscale", C.c_double * MAX_DIM), ("outputscale", C.c_double), ("n_terms", C.c_int),
+                ("alpha", (C.c_int * MAX_DIM) * MAX_TERMS), ("coef", C.c_double * MAX_TERMS),
+                ("rhs", C.POINTER(C.c_double)), ("jitter", C.c_double), ("n_sets", C.c_int),
+                ("sets", PointSet * MAX_SETS), ("n_pred", C.c_int * MAX_DIM),
+                ("pred", C.POINTER(C.c_double) * MAX_DIM)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("precision", C.c_int), ("reorth", C.c_int),
+                ("want_var", C.c_int), ("check_every", C.c_int), ("replace_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double), ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("t_query_ms", C.c_double), ("latency_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("memory_budget", C.c_int64), ("solve", SolveOpts),
+                ("steps_per_tick", C.c_int)]
+
+
+P = C.c_void_p
+D = C.POINTER(C.c_double)
+
+# name -> (restype, argtypes); every symbol declared in include/gpfvm.h
+SIGNATURES = {
+    "gpfvm_create": (C.c_int, [C.POINTER(Desc), C.c_int, C.POINTER(P)]),
+    "gpfvm_destroy": (None, [P]),
+    "gpfvm_sizes": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "gpfvm_assemble": (C.c_int, [P, P]),
+    "gpfvm_gram_matvec": (C.c_int, [P, C.c_int, P, P, P]),
+    "gpfvm_solve": (C.c_int, [P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "gpfvm_query": (C.c_int, [P, P, P, P]),
+    "gpfvm_solve_host": (C.c_int, [P, D, C.POINTER(SolveOpts), D, D, C.POINTER(SolveInfo), P]),
+    "gpfvm_export": (C.c_int64, [P, C.c_int, D, C.c_int64, P]),
+    "gpfvm_factor": (C.c_int64, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, D, C.c_int64, P]),
+    "gpfvm_solve_batch": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "gpfvm_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(P)]),
+    "gpfvm_server_submit": (C.c_int, [P, C.POINTER(Desc), C.POINTER(C.c_int64)]),
+    "gpfvm_server_step": (C.c_int, [P]),
+    "gpfvm_server_poll": (C.c_int, [P, C.c_int64, D, D, C.POINTER(SolveInfo)]),
+    "gpfvm_server_destroy": (None, [P]),
+    "gpfvm_set_values": (C.c_int, [P, P, P]),
+    "gpfvm_launch_count": (C.c_int64, []),
+    "gpfvm_strerror": (C.c_char_p, [C.c_int]),
+    "gpfvm_version": (C.c_char_p, []),
+}
+
+
+def _declare(L):
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+class GpfvmError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {lib().gpfvm_strerror(code).decode()} ({code})")
+
+
+def _check(code, where):
+    if code < 0:
+        raise GpfvmError(code, where)
+    return code
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(D)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_desc(prob):
+    """Builds a gpfvm_desc from a problem statement (gpfvm_workloads.Problem or
+    any object with the same attributes).  Returns (desc, keepalive)."""
+    keep = []
+
+    def arr(x):
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        keep.append(a)
+        return _dptr(a)
+
+    d = Desc()
+    d.ndim = prob.ndim
+    for i in range(prob.ndim):
+        d.n_cells[i] = len(prob.edges[i]) - 1
+        d.edges[i] = arr(prob.edges[i])
+        d.lengthscale[i] = float(prob.lengthscale[i])
+        d.n_pred[i] = len(prob.pred[i])
+        d.pred[i] = arr(prob.pred[i])
+    d.outputscale = float(prob.outputscale)
+    if len(prob.terms) > MAX_TERMS:
+        raise ValueError("too many operator terms")
+    d.n_terms = len(prob.terms)
+    for k, (alpha, c) in enumerate(prob.terms):
+        for i in range(prob.ndim):
+            d.alpha[k][i] = int(alpha[i])
+        d.coef[k] = float(c)
+    d.rhs = arr(np.ravel(prob.rhs)) if prob.rhs is not None else None
+    d.jitter = float(prob.jitter)
+    if len(prob.sets) > MAX_SETS:
+        raise ValueError("too many point sets")
+    d.n_sets = len(prob.sets)
+    for s, ps in enumerate(prob.sets):
+        for i in range(prob.ndim):
+            d.sets[s].order[i] = int(ps.order[i])
+            d.sets[s].n_pts[i] = len(ps.coords[i])
+            d.sets[s].coords[i] = arr(ps.coords[i])
+        d.sets[s].values = arr(np.ravel(ps.values))
+        d.sets[s].noise_var = float(ps.noise_var)
+    return d, keep
+
+
+def solve_opts(max_iter=2000, rtol=1e-10, precision=FP64, reorth=True, want_var=True, check_every=16,
+               replace_every=50):
+    o = SolveOpts()
+    o.max_iter, o.rtol, o.precision = int(max_iter), float(rtol), int(precision)
+    o.reorth, o.want_var, o.check_every, o.replace_every = int(reorth), int(want_var), int(check_every), int(
+        replace_every)
+    return o
+
+
+class Problem:
+    """One GP-FVM problem resident on the GPU (create/assemble/solve/query)."""
+
+    def __init__(self, prob, max_iter: int = 2000):
+        self.prob = prob
+        self.desc, self._keep = make_desc(prob)
+        h = P()
+        _check(lib().gpfvm_create(C.byref(self.desc), int(max_iter), C.byref(h)), "gpfvm_create")
+        self.h = h
+        sz = (C.c_int64 * 4)()
+        _check(lib().gpfvm_sizes(self.h, sz), "gpfvm_sizes")
+        self.N, self.M, self.P, self.cap = (int(v) for v in sz)
+        self.info = SolveInfo()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpfvm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def assemble(self, stream=None):
+        return _check(lib().gpfvm_assemble(self.h, _stream(stream)), "gpfvm_assemble")
+
+    def matvec(self, op: int, v, out, stream=None):
+        """out = op(v) on device tensors (see gpfvm_gram_matvec)."""
+        return _check(lib().gpfvm_gram_matvec(self.h, int(op), C.c_void_p(v.data_ptr()),
+                                              C.c_void_p(out.data_ptr()), _stream(stream)), "gpfvm_gram_matvec")
+
+    def solve(self, opts: Optional[SolveOpts] = None, stream=None, **kw):
+        opts = opts or solve_opts(**kw)
+        self.info = SolveInfo()
+        code = _check(lib().gpfvm_solve(self.h, C.byref(opts), C.byref(self.info), _stream(stream)), "gpfvm_solve")
+        return code, self.info
+
+    def query(self, mean, var=None, stream=None):
+        return _check(lib().gpfvm_query(self.h, C.c_void_p(mean.data_ptr()),
+                                        C.c_void_p(var.data_ptr()) if var is not None else None,
+                                        _stream(stream)), "gpfvm_query")
+
+    def solve_host(self, values: Optional[np.ndarray], opts: SolveOpts, mean: np.ndarray,
+                   var: Optional[np.ndarray] = None, stream=None):
+        vals = None if values is None else np.ascontiguousarray(values, dtype=np.float64)
+        self.info = SolveInfo()
+        code = _check(lib().gpfvm_solve_host(self.h, _dptr(vals) if vals is not None else None, C.byref(opts),
+                                             _dptr(mean), _dptr(var) if var is not None else None,
+                                             C.byref(self.info), _stream(stream)), "gpfvm_solve_host")
+        return code, self.info
+
+    def set_values(self, values_dev, stream=None):
+        """New point-set values (device tensor of M doubles) on the assembled problem."""
+        return _check(lib().gpfvm_set_values(self.h, C.c_void_p(values_dev.data_ptr()), _stream(stream)),
+                      "gpfvm_set_values")
+
+    def export(self, what: int, n: int) -> np.ndarray:
+        out = np.empty(max(n, 1))
+        k = _check(lib().gpfvm_export(self.h, int(what), _dptr(out), out.size, _stream(None)), "gpfvm_export")
+        return out[:k]
+
+    def factor(self, axis, kind_a, arg_a, kind_b, arg_b, shape) -> np.ndarray:
+        out = np.empty(int(np.prod(shape)))
+        k = _check(lib().gpfvm_factor(self.h, axis, kind_a, arg_a, kind_b, arg_b, _dptr(out), out.size,
+                                      _stream(None)), "gpfvm_factor")
+        return out[:k].reshape(shape)
+
+
+def solve_batch(problems, opts: SolveOpts, stream=None):
+    arr = (P * len(problems))(*[p.h for p in problems])
+    infos = (SolveInfo * len(problems))()
+    code = _check(lib().gpfvm_solve_batch(arr, len(problems), C.byref(opts), infos, _stream(stream)),
+                  "gpfvm_solve_batch")
+    return code, list(infos)
+
+
+def launch_count() -> int:
+    return int(lib().gpfvm_launch_count())
+
+
+def version() -> str:
+    return lib().gpfvm_version().decode()
