@@ -52,7 +52,8 @@ enum gpfvm_status {
   GPFVM_ERR_DEVICE = -5,       /* a CUDA call failed */
   GPFVM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
   GPFVM_ERR_STATE = -7,        /* call out of order (e.g. solve before assemble) */
-  GPFVM_ERR_NOT_FOUND = -8     /* unknown ticket */
+  GPFVM_ERR_NOT_FOUND = -8,    /* unknown ticket */
+  GPFVM_ERR_TOO_LARGE = -9     /* request exceeds the fixed capacity of gpfvm_kron_matvec_noalloc */
 };
 
 /* One tensor grid of point functionals  d^order u (x)  (Sec. 2.2: initial and
@@ -243,6 +244,34 @@ int gpfvm_server_step(gpfvm_server* s);
 int gpfvm_server_poll(gpfvm_server* s, int64_t ticket, double* mean_host, double* var_host,
                       gpfvm_solve_info* info);
 void gpfvm_server_destroy(gpfvm_server* s);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free Kronecker Gram matvec.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need the product -- code running while a CUDA graph is being captured,
+ * frameworks whose allocator owns the whole device, real-time loops that must
+ * not enter the driver's allocator.  It computes
+ *   out = scale * sum_k coef[k] (F[k][0] (x) ... (x) F[k][ndim-1]) v + diag * v
+ * for a row-major tensor of dims n[0..ndim) (ndim 1..3), where F[k][i] =
+ * factors[k*ndim + i] is a DEVICE pointer to an n[i] x n[i] row-major matrix
+ * (e.g. the 1D factors of Eq. kronecker-structure exported by gpfvm_factor),
+ * coef is a HOST array of n_terms (<= 64) coefficients, and v, out are DEVICE
+ * vectors of prod n doubles that must not overlap.
+ * Memory: it calls no cudaMalloc/cudaFree or allocating routine.  The
+ * intermediates (at most 4,194,304 doubles = 32 MiB; a three-axis product
+ * needs (distinct last-axis factors + distinct first-axis factors) * prod n
+ * doubles) and the argument tables live in file-scope device arrays that
+ * every GPU loading the library keeps until the process exits; larger
+ * requests return GPFVM_ERR_TOO_LARGE without launching anything.
+ * The first call on a device looks up those arrays' device addresses with
+ * that device current; make that first call before any stream capture.
+ * All calls share the arrays and leave the last call's contents behind
+ * (nothing in them needs to start at zero); calls that overlap on the GPU
+ * (different streams, or host threads racing) race on them.  The work is
+ * enqueued on `stream`; the call returns without synchronising. */
+int gpfvm_kron_matvec_noalloc(int ndim, const int* n, int n_terms, const double* const* factors,
+                              const double* coef, double scale, double diag, const double* v, double* out,
+                              void* stream);
 
 const char* gpfvm_strerror(int code);
 

@@ -1023,6 +1023,7 @@ const char* gpfvm_strerror(int code) {
     case GPFVM_ERR_TIMEOUT: return "bounded device wait timed out";
     case GPFVM_ERR_STATE: return "call out of order";
     case GPFVM_ERR_NOT_FOUND: return "not found";
+    case GPFVM_ERR_TOO_LARGE: return "request exceeds the static scratch capacity of the allocation-free path";
     default: return "unknown status";
   }
 }

@@ -92,6 +92,8 @@ SIGNATURES = {
     "gpfvm_server_destroy": (None, [P]),
     "gpfvm_set_values": (C.c_int, [P, P, P]),
     "gpfvm_launch_count": (C.c_int64, []),
+    "gpfvm_kron_matvec_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_void_p), D,
+                                            C.c_double, C.c_double, P, P, P]),
     "gpfvm_strerror": (C.c_char_p, [C.c_int]),
     "gpfvm_version": (C.c_char_p, []),
 }
@@ -253,6 +255,18 @@ def solve_batch(problems, opts: SolveOpts, stream=None):
     code = _check(lib().gpfvm_solve_batch(arr, len(problems), C.byref(opts), infos, _stream(stream)),
                   "gpfvm_solve_batch")
     return code, list(infos)
+
+
+def kron_matvec_noalloc(dims, terms, scale, diag, v, out, stream=None):
+    """out = scale * sum_k c_k (F_k0 (x) ...) v + diag * v without any device
+    allocation; terms = [(c_k, [F_k0, F_k1, ...])] with device tensors F."""
+    ndim = len(dims)
+    n = (C.c_int * ndim)(*dims)
+    ptrs = (C.c_void_p * (len(terms) * ndim))(*[f.data_ptr() for _, fs in terms for f in fs])
+    coef = np.ascontiguousarray([c for c, _ in terms], dtype=np.float64)
+    return _check(lib().gpfvm_kron_matvec_noalloc(ndim, n, len(terms), ptrs, _dptr(coef), float(scale),
+                                                  float(diag), C.c_void_p(v.data_ptr()), C.c_void_p(out.data_ptr()),
+                                                  _stream(stream)), "gpfvm_kron_matvec_noalloc")
 
 
 def launch_count() -> int:
