@@ -104,10 +104,12 @@ typedef struct {
 
 /* Precision of the CG iteration. */
 enum gpfvm_precision {
-  GPFVM_FP64 = 0,       /* every product and vector in FP64 */
-  GPFVM_MIXED_TF32 = 1  /* mode products on tcgen05 tensor cores in TF32 with FP32
-                           accumulation; FP64 scalars, FP64 iterate and periodic
-                           FP64 residual replacement */
+  GPFVM_FP64 = 0,        /* every product and vector in FP64 */
+  GPFVM_MIXED_FP32 = 1,  /* iterative refinement: FP64 residual b - G^ x with the FP64
+                            operator; inner CG on an FP32 operator (FP32 SIMT mode
+                            products, FP32 vectors) with FP64 scalars and reductions */
+  GPFVM_MIXED_TF32X3 = 2 /* as MIXED_FP32, with the G_PP mode products on tcgen05 tensor
+                            cores in split TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulate) */
 };
 
 typedef struct {
@@ -117,7 +119,8 @@ typedef struct {
   int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions */
   int want_var;        /* 1 = accumulate the IterGP variance downdate on the grid */
   int check_every;     /* iterations between host convergence checks (graph replays) */
-  int replace_every;   /* mixed precision: iterations between FP64 residual replacements */
+  int inner_max_iter;  /* mixed: iteration cap of one inner CG (<= 0: no cap beyond max_iter) */
+  double inner_rtol;   /* mixed: residual reduction of one inner CG (<= 0: 1e-2) */
 } gpfvm_solve_opts;
 
 typedef struct {
@@ -157,15 +160,20 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream);
  *   op 1: out = G^ v = G_PP v - G_PB G_BB^-1 G_BP v   (N -> N, Sec. 4.2)
  *   op 2: out = G_BP v            (N -> M)
  *   op 3: out = G_PB v            (M -> N)
- *   op 4: out = G_PP v in the mixed-precision (TF32 tensor-core) form, FP64 in/out
+ *   op 4: out = G_PP v in the FP32 form of the mixed solver (FP64 in/out)
+ *   op 5: out = G_PP v in the split-TF32 tensor-core form (FP64 in/out)
  * Requires gpfvm_assemble.  v and out must not overlap. */
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);
 
-/* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  All scalars
+/* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  max_iter
+ * counts CG iterations (for the mixed precisions: inner iterations).  All scalars
  * stay on the device; the iteration is replayed as a CUDA graph and the host
  * reads the residual every check_every iterations.  Returns OK, NOT_CONVERGED
  * (budget exhausted; the iterate and variance downdate are kept), BREAKDOWN,
- * STATE (not assembled) or DEVICE.  info may be NULL. */
+ * STATE (not assembled) or DEVICE.  info may be NULL.  Mixed precisions: the
+ * stopping test is the FP64 residual of the refined iterate, and the IterGP
+ * variance downdate uses the directions of the first inner CG (a valid
+ * combined posterior for those actions, which are conjugate within one run). */
 int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info* info,
                 void* stream);
 
@@ -198,6 +206,8 @@ int64_t gpfvm_launch_count(void);
  *   what 2: G_BB with noise (M*M)      what 3: L^-1 (M*M, lower)
  *   what 4: 1D factor (axis, kind_a, ord_a, kind_b, ord_b) -- see gpfvm_factor
  *   what 5: variance downdate sum (P)  what 6: eta_j (iterations)
+ *   what 7: device time (ms) of the last assemble, solve and query (3 values)
+ *   what 8: refinement steps of the last mixed-precision solve (1 value)
  * Returns the number of doubles written or a negative error. */
 int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream);
 

@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <tuple>
+#include <type_traits>
 
 #include "cg.cuh"
 #include "kron.cuh"
@@ -44,6 +45,7 @@ typedef std::tuple<int, int, int, int, int> FKey;
 
 struct DevBuf {
   std::vector<void*> ptrs;
+  std::vector<i64> sizes;
   i64 bytes = 0;
   template <typename T>
   T* alloc(i64 n) {
@@ -54,15 +56,60 @@ struct DevBuf {
       throw CudaError{cudaErrorMemoryAllocation, "cudaMalloc"};
     }
     ptrs.push_back(p);
+    sizes.push_back(n * (i64)sizeof(T));
     bytes += n * (i64)sizeof(T);
     return (T*)p;
+  }
+  // true if [p, p + len) lies inside one allocation
+  bool contains(const void* p, i64 len) const {
+    const char* c = (const char*)p;
+    for (size_t i = 0; i < ptrs.size(); ++i) {
+      const char* b = (const char*)ptrs[i];
+      if (c >= b && c + len <= b + sizes[i]) return true;
+    }
+    return false;
   }
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+    sizes.clear();
     bytes = 0;
   }
 };
+
+// Host-side bounds check of every GEMM/GEMV operand of a plan against the
+// problem's allocations, done once when the plan is built (before any launch).
+void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
+  auto need = [&](const void* p, i64 len, const char* what) {
+    if (!p || len <= 0) return;
+    if (!mem.contains(p, len)) {
+      fprintf(stderr, "gpfvm: plan %s: %s operand out of bounds\n", name, what);
+      throw CudaError{cudaErrorInvalidValue, "plan operand out of bounds"};
+    }
+  };
+  for (const PlanOp& op : plan.ops) {
+    if (op.kind == PlanOp::GEMM) {
+      const GemmDesc& g = op.g;
+      const i64 e = g.f32 ? 4 : 8;
+      const i64 nb = (i64)g.batch - 1;
+      for (int gi = 0; gi < g.n_groups; ++gi) {
+        const GemmGroup& G = plan.groups[op.group0 + gi];
+        need(G.C, e * (nb * g.c_bs + (i64)(g.m - 1) * g.c_rs + g.n), "C");
+        need(G.D, e * (nb * g.d_bs + (i64)(g.m - 1) * g.d_rs + g.n), "D");
+        for (int si = 0; si < G.nseg; ++si) {
+          const GemmSeg& S = plan.segs[G.seg0 + si];
+          need(S.A, e * (nb * g.a_bs + (i64)(g.m - 1) * g.a_rs + (i64)(g.k - 1) * g.a_cs + 1), "A");
+          need(S.B, e * (nb * g.b_bs + (i64)(g.k - 1) * g.b_rs + (i64)(g.n - 1) * g.b_cs + 1), "B");
+        }
+      }
+    } else if (op.kind == PlanOp::GEMV || op.kind == PlanOp::GEMV32) {
+      const i64 e = op.kind == PlanOp::GEMV32 ? 4 : 8;
+      need(op.A, e * ((i64)(op.m - 1) * op.lda + op.n), "gemv A");
+      need(op.x, e * op.n, "gemv x");
+      need(op.y, e * op.m, "gemv y");
+    }
+  }
+}
 
 int map_error(const CudaError& e) {
   if (e.err == cudaErrorMemoryAllocation) return GPFVM_ERR_OUT_OF_MEMORY;
@@ -107,6 +154,15 @@ struct gpfvm_problem {
   double *d_S = nullptr, *d_Q = nullptr, *d_eta = nullptr, *d_part2 = nullptr, *d_coef = nullptr;
   double *d_vin = nullptr, *d_vout = nullptr, *d_win = nullptr, *d_wout = nullptr;
   double *d_vbchunk = nullptr, *d_vbY = nullptr;
+  // mixed precision (FP32 inner operator)
+  float *f_fac = nullptr, *f_Linv = nullptr, *f_LinvT = nullptr;
+  float *f_p = nullptr, *f_q = nullptr, *f_r = nullptr, *f_d = nullptr, *f_g = nullptr, *f_t = nullptr,
+        *f_w = nullptr, *f_u = nullptr, *f_S = nullptr, *f_Q = nullptr, *f_vin = nullptr, *f_vout = nullptr;
+  double* d_eta32 = nullptr;
+  CGState* d_st32 = nullptr;
+  CGState* h_st32 = nullptr;
+  i64 nfac = 0;
+  bool building_f32 = false;
   double* d_scratch = nullptr;
   i64 scratch_cap = 0;
   int vb_rows = 0;
@@ -116,6 +172,7 @@ struct gpfvm_problem {
   // ---- plans
   Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB;
   Plan p_op[4];
+  Plan p_mv32, p_var32, p_pp32;
   int modeprods_pp = 0;
 
   // ---- state
@@ -123,11 +180,17 @@ struct gpfvm_problem {
   cudaGraphExec_t graph = nullptr;
   int graph_key = -1;
   long long graph_kernels = 0;
+  cudaGraphExec_t graph32 = nullptr;
+  int graph32_key = -1;
+  long long graph32_kernels = 0;
   gpfvm_solve_info last{};
+  int last_outer = 0;
 
   ~gpfvm_problem() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph32) cudaGraphExecDestroy(graph32);
     if (h_st) cudaFreeHost(h_st);
+    if (h_st32) cudaFreeHost(h_st32);
     mem.release();
   }
 };
@@ -166,7 +229,7 @@ void need_factor(gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab) {
 MatRef fac_ref(const gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab, bool transpose) {
   const i64 off = p->fac_off.at(FKey(ax, ka, aa, kb, ab));
   const i64 nb = fam_n(p, ax, kb, ab);
-  MatRef m{p->d_fac + off, nb, 1};
+  MatRef m{p->building_f32 ? (const double*)(p->f_fac + off) : p->d_fac + off, nb, 1};
   if (transpose) std::swap(m.rs, m.cs);
   return m;
 }
@@ -226,10 +289,19 @@ struct Builder {
   gpfvm_problem* p;
   Scratch scr;
   i64 peak = 0;
+  bool f32 = false;  // build FP32 plans (pointers below then address float data)
+  // `base` advanced by n elements of the plan's element type
+  template <typename P>
+  P at(P base, i64 n) const {
+    if (!f32) return base + n;
+    typedef typename std::conditional<std::is_const<typename std::remove_pointer<P>::type>::value, const float*,
+                                      float*>::type FP;
+    return (P)((FP)base + n);
+  }
   void kron(Plan& plan, const int* din, const int* dout, i64 batch, const std::vector<KTerm>& terms, double scale,
             const double* in, double* out, double beta, const double* D, double gamma, int* count = nullptr) {
     scr.used = 0;
-    plan_kron(plan, scr, p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count);
+    plan_kron(plan, scr, p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count, f32);
     peak = std::max(peak, scr.used);
   }
 
@@ -239,7 +311,7 @@ struct Builder {
     dims_cells(p, dc);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, dc, ds, 1, pb_terms(p, s, true), p->s2, in, g + p->sets[s].off, 0.0, nullptr, 0.0);
+      kron(plan, dc, ds, 1, pb_terms(p, s, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
     }
   }
   // out (+)= scale * G_PB w
@@ -248,13 +320,18 @@ struct Builder {
     dims_cells(p, dc);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, ds, dc, 1, pb_terms(p, s, false), scale * p->s2, w + p->sets[s].off, out,
+      kron(plan, ds, dc, 1, pb_terms(p, s, false), scale * p->s2, at(w, p->sets[s].off), out,
            (accumulate || s > 0) ? 1.0 : 0.0, nullptr, 0.0);
     }
   }
   // w = G_BB^-1 g via the explicit inverse factor
   void hsolve(Plan& plan, const double* g, double* t, double* w) {
     const int M = (int)p->M;
+    if (f32) {
+      plan.gemv32(M, M, p->f_Linv, M, (const float*)g, (float*)t, 1);
+      plan.gemv32(M, M, p->f_LinvT, M, (const float*)t, (float*)w, 2);
+      return;
+    }
     plan.gemv(M, M, p->d_Linv, M, g, t, 1.0, 0.0, 1);
     plan.gemv(M, M, p->d_LinvT, M, t, w, 1.0, 0.0, 2);
   }
@@ -284,7 +361,7 @@ struct Builder {
     dims_pred(p, dp);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, ds, dp, 1, bpred_terms(p, s), scale * p->s2, w + p->sets[s].off, u, (acc || s > 0) ? 1.0 : 0.0,
+      kron(plan, ds, dp, 1, bpred_terms(p, s), scale * p->s2, at(w, p->sets[s].off), u, (acc || s > 0) ? 1.0 : 0.0,
            nullptr, 0.0);
     }
   }
@@ -403,11 +480,32 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   }
 }
 
+// FP32 plans of the mixed solver's inner operator.
+void build_plans32(gpfvm_problem* p, Builder& B) {
+  B.f32 = true;
+  p->building_f32 = true;
+  auto D = [](float* f) { return (double*)f; };
+  p->p_mv32 = Plan();
+  B.ghat(p->p_mv32, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_t), D(p->f_w), nullptr);
+  p->p_var32 = Plan();
+  B.to_pred_cells(p->p_var32, D(p->f_p), D(p->f_u), 1.0, false);
+  if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true);
+  p->p_pp32 = Plan();
+  B.pp(p->p_pp32, D(p->f_vin), D(p->f_vout), nullptr);
+  p->building_f32 = false;
+  B.f32 = false;
+}
+
 void finalize_plans(gpfvm_problem* p) {
   p->p_mv_cg.skip = &p->d_st->done;
   p->p_var_cg.skip = &p->d_st->done;
+  p->p_mv32.skip = &p->d_st32->done;
+  p->p_var32.skip = &p->d_st32->done;
   Plan* all[] = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
-                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3]};
+                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32};
+  const char* names[] = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2", "op3",
+                         "mv32", "var32", "pp32"};
+  for (int i = 0; i < 14; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
   for (Plan* pl : all) pl->finalize();
 }
 
@@ -579,22 +677,48 @@ void alloc_all(gpfvm_problem* p) {
     p->d_vbchunk = m.alloc<double>(R * maxms);
     p->d_vbY = m.alloc<double>(R * P);
   }
+  // mixed-precision buffers
+  p->nfac = std::max<i64>(nfac, 1);
+  p->f_fac = m.alloc<float>(p->nfac);
+  if (M > 0) {
+    p->f_Linv = m.alloc<float>(M * M);
+    p->f_LinvT = m.alloc<float>(M * M);
+    p->f_g = m.alloc<float>(M);
+    p->f_t = m.alloc<float>(M);
+    p->f_w = m.alloc<float>(M);
+  }
+  p->f_p = m.alloc<float>(N);
+  p->f_q = m.alloc<float>(N);
+  p->f_r = m.alloc<float>(N);
+  p->f_d = m.alloc<float>(N);
+  p->f_vin = m.alloc<float>(N);
+  p->f_vout = m.alloc<float>(N);
+  p->f_u = m.alloc<float>(P);
+  p->f_S = m.alloc<float>((i64)cap * N);
+  p->f_Q = m.alloc<float>((i64)cap * N);
+  p->d_eta32 = m.alloc<double>(cap);
   p->d_st = m.alloc<CGState>(1);
+  p->d_st32 = m.alloc<CGState>(1);
   GPFVM_CUDA(cudaMemset(p->d_st, 0, sizeof(CGState)));
+  GPFVM_CUDA(cudaMemset(p->d_st32, 0, sizeof(CGState)));
   GPFVM_CUDA(cudaMallocHost(&p->h_st, sizeof(CGState)));
+  GPFVM_CUDA(cudaMallocHost(&p->h_st32, sizeof(CGState)));
   std::memset(p->h_st, 0, sizeof(CGState));
+  std::memset(p->h_st32, 0, sizeof(CGState));
   GPFVM_CUDA(cudaMemset(p->d_down, 0, P * sizeof(double)));
   // plans: count scratch, allocate, build for real
   Builder B0{p};
   B0.scr.base = nullptr;
   B0.scr.cap = (i64)1 << 62;
   build_plans(p, B0);
+  build_plans32(p, B0);
   p->scratch_cap = std::max<i64>(B0.peak, 64);
   p->d_scratch = m.alloc<double>(p->scratch_cap);
   Builder B{p};
   B.scr.base = p->d_scratch;
   B.scr.cap = p->scratch_cap;
   build_plans(p, B);
+  build_plans32(p, B);
   finalize_plans(p);
 }
 
@@ -612,6 +736,11 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
     if (p->h_st->pad[0] & DEV_NOT_SPD) return GPFVM_ERR_NOT_SPD;
   }
   p->p_rhs.run(st);
+  convert_d2f(p->d_fac, p->f_fac, p->nfac, st);
+  if (p->M > 0) {
+    convert_d2f(p->d_Linv, p->f_Linv, p->M * p->M, st);
+    convert_d2f(p->d_LinvT, p->f_LinvT, p->M * p->M, st);
+  }
   GPFVM_CUDA(cudaStreamSynchronize(st));
   p->assembled = true;
   p->solved = false;
@@ -659,7 +788,8 @@ std::map<const gpfvm_problem*, SolveRun>& runs() {
 int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
-  if (o->precision != GPFVM_FP64 && o->precision != GPFVM_MIXED_TF32) return GPFVM_ERR_INVALID_ARG;
+  if (o->precision != GPFVM_FP64 && o->precision != GPFVM_MIXED_FP32 && o->precision != GPFVM_MIXED_TF32X3)
+    return GPFVM_ERR_INVALID_ARG;
   const bool reorth = o->reorth != 0, want_var = o->want_var != 0;
   if (reorth && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
   SolveRun& R = runs()[p];
@@ -737,7 +867,7 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
 }
 
 int run_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
-  if (o && o->precision == GPFVM_MIXED_TF32) return mixed_solve(p, o, info, st);
+  if (o && (o->precision == GPFVM_MIXED_FP32 || o->precision == GPFVM_MIXED_TF32X3)) return mixed_solve(p, o, info, st);
   const int b = solve_begin(p, o, st);
   if (b != GPFVM_OK) return b;
   const int chunk = o->check_every > 0 ? o->check_every : 16;
@@ -765,12 +895,116 @@ int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
   return GPFVM_OK;
 }
 
-}  // namespace
-
-namespace {
-int mixed_solve(gpfvm_problem*, const gpfvm_solve_opts*, gpfvm_solve_info*, cudaStream_t) {
-  return GPFVM_ERR_INVALID_ARG;  // replaced by the tensor-core path
+// One inner CG iteration of the mixed solver (FP32 operator and vectors, FP64 scalars).
+void cg_iteration32(gpfvm_problem* p, bool want_var, cudaStream_t st) {
+  const i64 N = p->N;
+  p->p_mv32.run(st);
+  cg_dot_eta<float>(p->f_p, p->f_q, N, p->d_st32, p->d_eta32, st);
+  if (want_var) {
+    p->p_var32.run(st);
+    cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
+  }
+  cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, p->f_S, p->f_Q, st);
+  cg_pupdate<float>(p->f_r, p->f_p, N, p->d_st32, st);
+  cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
 }
+
+// Iterative refinement (mixed precision, Sec. 4.1 CG as the inner solver):
+//   r = b - G^ x            FP64 operator, FP64 vectors
+//   solve G^_32 d ~= r      inner CG: FP32 operator/vectors, FP64 scalars, reorthogonalised
+//   x += d
+// until ||r|| / ||b|| <= rtol.  The IterGP variance downdate is accumulated
+// during the first inner CG (whose right-hand side is b and whose directions
+// are conjugate within the run).
+int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
+  const bool want_var = o->want_var != 0;
+  const i64 N = p->N;
+  const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
+  cudaEvent_t e0, e1;
+  GPFVM_CUDA(cudaEventCreate(&e0));
+  GPFVM_CUDA(cudaEventCreate(&e1));
+  GPFVM_CUDA(cudaEventRecord(e0, st));
+  GPFVM_CUDA(cudaMemsetAsync(p->d_x, 0, sizeof(double) * N, st));
+  if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  norm2(p->d_b, N, &p->d_st->aux[1], p->d_st, st);
+  int total = 0, outer = 0, status = GPFVM_NOT_CONVERGED;
+  double rel = 1.0;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  for (;; ++outer) {
+    // FP64 residual of the refined iterate
+    GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, p->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    p->p_op[1].run(st);
+    axpby(p->d_b, p->d_vout, p->d_r, 1.0, -1.0, N, st);
+    norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
+    copy_header_to_host(p, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    const double b2 = p->h_st->aux[1];
+    rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
+    if (!(rel <= o->rtol) && !std::isfinite(rel)) { status = GPFVM_ERR_BREAKDOWN; break; }
+    if (rel <= o->rtol) { status = GPFVM_OK; break; }
+    if (total >= o->max_iter) break;
+    // inner CG on the FP32 operator
+    const bool var_now = want_var && outer == 0;
+    p->h_st32->rtol2 = itol * itol;
+    p->h_st32->max_iter = std::min(icap, o->max_iter - total);
+    p->h_st32->cap = p->cap;
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->rtol2, &p->h_st32->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->max_iter, &p->h_st32->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st);
+    const int key = var_now ? 1 : 0;
+    if (!p->graph32 || p->graph32_key != key) {
+      if (p->graph32) cudaGraphExecDestroy(p->graph32);
+      p->graph32 = nullptr;
+      cudaGraph_t g;
+      const long long before = gpfvm_launch_count();
+      GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cg_iteration32(p, var_now, st);
+      GPFVM_CUDA(cudaStreamEndCapture(st, &g));
+      p->graph32_kernels = gpfvm_launch_count() - before;
+      count_launch(-p->graph32_kernels);
+      GPFVM_CUDA(cudaGraphInstantiate(&p->graph32, g, 0));
+      cudaGraphDestroy(g);
+      p->graph32_key = key;
+    }
+    int launched = 0;
+    const int lim = p->h_st32->max_iter;
+    while (true) {
+      const int n = std::min(chunk, lim - launched);
+      for (int i = 0; i < n; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));
+      count_launch((long long)n * p->graph32_kernels);
+      launched += n;
+      GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+      GPFVM_CUDA(cudaStreamSynchronize(st));
+      if (p->h_st32->done || launched >= lim) break;
+    }
+    const int k = p->h_st32->k;
+    total += k;
+    if (k == 0) { status = GPFVM_ERR_BREAKDOWN; break; }  // not even one inner step
+    add_f2d(p->d_x, p->f_d, N, st);
+  }
+  GPFVM_CUDA(cudaEventRecord(e1, st));
+  GPFVM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  gpfvm_solve_info I = p->last;
+  I.iterations = total;
+  I.status = status;
+  I.rel_residual = rel;
+  I.true_rel_residual = rel;
+  I.t_solve_ms = ms;
+  p->last = I;
+  p->last_outer = outer;
+  if (info) *info = I;
+  p->solved = status >= 0;
+  p->want_var_last = want_var;
+  return status;
+}
+
 }  // namespace
 
 #define GPFVM_GUARD_BEGIN try {
@@ -895,12 +1129,19 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream) {
 }
 
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream) {
-  if (!p || !v || !out || op < 0 || op > 4) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || op < 0 || op > 5) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
-  if (op == 4) return GPFVM_ERR_INVALID_ARG;
+  if (op == 5) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
+  if (op == 4) {
+    convert_d2f(v, p->f_vin, p->N, st);
+    p->p_pp32.run(st);
+    f2d(p->f_vout, out, p->N, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    return GPFVM_OK;
+  }
   const i64 nin = (op == 3) ? p->M : p->N;
   const i64 nout = (op == 2) ? p->M : p->N;
   double* in = (op == 3) ? p->d_win : p->d_vin;
@@ -924,8 +1165,18 @@ int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream) {
   if (!p || (!mean && !var)) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
+  cudaEvent_t e0, e1;
+  GPFVM_CUDA(cudaEventCreate(&e0));
+  GPFVM_CUDA(cudaEventCreate(&e1));
+  GPFVM_CUDA(cudaEventRecord(e0, st));
   const int r = run_query(p, mean, var, st);
-  GPFVM_CUDA(cudaStreamSynchronize(st));
+  GPFVM_CUDA(cudaEventRecord(e1, st));
+  GPFVM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  p->last.t_query_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return r;
   GPFVM_GUARD_END
 }
@@ -968,6 +1219,17 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
     case 3: src = p->d_Linv; n = p->M * p->M; break;
     case 5: src = p->d_down; n = p->P; break;
     case 6: src = p->d_eta; n = p->last.iterations; break;
+    case 8: {  // refinement steps of the last mixed-precision solve
+      host_out[0] = p->last_outer;
+      return 1;
+    }
+    case 7: {  // timing of the last assemble / solve / query (ms)
+      if (capacity < 3) return GPFVM_ERR_INVALID_ARG;
+      host_out[0] = p->last.t_assemble_ms;
+      host_out[1] = p->last.t_solve_ms;
+      host_out[2] = p->last.t_query_ms;
+      return 3;
+    }
     default: return GPFVM_ERR_INVALID_ARG;
   }
   if (n > capacity) return GPFVM_ERR_INVALID_ARG;
@@ -1042,7 +1304,7 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
   if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
-  if (opts->precision == GPFVM_MIXED_TF32) {
+  if (opts->precision != GPFVM_FP64) {
     int worst = GPFVM_OK;
     for (int i = 0; i < n; ++i) {
       const int r = gpfvm_solve(ps[i], opts, infos ? &infos[i] : nullptr, nullptr);

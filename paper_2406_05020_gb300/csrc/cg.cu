@@ -34,17 +34,17 @@ __device__ double sum_partials(const double* part, int n, double* smem) {
   return block_sum<RT>(v, smem);
 }
 
-__global__ void __launch_bounds__(RT) k_init(const double* __restrict__ b, double* __restrict__ x,
-                                              double* __restrict__ r, double* __restrict__ p, i64 n,
-                                              CGState* st) {
+template <typename TB, typename T>
+__global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                                              T* __restrict__ p, i64 n, CGState* st) {
   __shared__ double red[32];
   double acc = 0.0;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
-    const double v = b[i];
-    x[i] = 0.0;
+    const T v = (T)b[i];
+    x[i] = T(0);
     r[i] = v;
     p[i] = v;
-    acc += v * v;
+    acc += (double)v * (double)v;
   }
   acc = block_sum<RT>(acc, red);
   if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
@@ -62,12 +62,14 @@ __global__ void __launch_bounds__(RT) k_init(const double* __restrict__ b, doubl
   }
 }
 
-__global__ void __launch_bounds__(RT) k_dot_eta(const double* __restrict__ p, const double* __restrict__ q, i64 n,
+template <typename T>
+__global__ void __launch_bounds__(RT) k_dot_eta(const T* __restrict__ p, const T* __restrict__ q, i64 n,
                                                  CGState* st, double* __restrict__ eta_hist) {
   if (st->done) return;
   __shared__ double red[32];
   double acc = 0.0;
-  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) acc = fma(p[i], q[i], acc);
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT)
+    acc = fma((double)p[i], (double)q[i], acc);
   acc = block_sum<RT>(acc, red);
   if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
   if (last_block(&st->ticket[1])) {
@@ -85,19 +87,21 @@ __global__ void __launch_bounds__(RT) k_dot_eta(const double* __restrict__ p, co
   }
 }
 
-__global__ void __launch_bounds__(RT) k_downdate(const double* __restrict__ u, double* __restrict__ down, i64 n,
+template <typename T>
+__global__ void __launch_bounds__(RT) k_downdate(const T* __restrict__ u, double* __restrict__ down, i64 n,
                                                   const CGState* st) {
   if (st->done) return;
   const double inv = 1.0 / st->eta;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
-    const double v = u[i];
+    const double v = (double)u[i];
     down[i] = fma(v * v, inv, down[i]);
   }
 }
 
-__global__ void __launch_bounds__(RT) k_update(double* __restrict__ x, double* __restrict__ r,
-                                                const double* __restrict__ p, const double* __restrict__ q, i64 n,
-                                                CGState* st, double* __restrict__ S, double* __restrict__ Q) {
+template <typename T>
+__global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                const T* __restrict__ q, i64 n, CGState* st, T* __restrict__ S,
+                                                T* __restrict__ Q) {
   if (st->done) return;
   __shared__ double red[32];
   const double alpha = st->rr / st->eta;
@@ -105,10 +109,10 @@ __global__ void __launch_bounds__(RT) k_update(double* __restrict__ x, double* _
   const bool keep = (S != nullptr) && (k < st->cap);
   double acc = 0.0;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
-    const double pi = p[i], qi = q[i];
-    x[i] = fma(alpha, pi, x[i]);
-    const double ri = fma(-alpha, qi, r[i]);
-    r[i] = ri;
+    const T pi = p[i], qi = q[i];
+    x[i] = (T)fma(alpha, (double)pi, (double)x[i]);
+    const double ri = fma(-alpha, (double)qi, (double)r[i]);
+    r[i] = (T)ri;
     acc = fma(ri, ri, acc);
     if (keep) {
       S[(i64)k * n + i] = pi;
@@ -138,15 +142,18 @@ __global__ void __launch_bounds__(RT) k_update(double* __restrict__ x, double* _
   }
 }
 
-__global__ void __launch_bounds__(RT) k_pupdate(const double* __restrict__ r, double* __restrict__ p, i64 n,
+template <typename T>
+__global__ void __launch_bounds__(RT) k_pupdate(const T* __restrict__ r, T* __restrict__ p, i64 n,
                                                  const CGState* st) {
   if (st->done) return;
   const double beta = st->beta;
-  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) p[i] = fma(beta, p[i], r[i]);
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT)
+    p[i] = (T)fma(beta, (double)p[i], (double)r[i]);
 }
 
 // partial dots part2[j * nchunk + c] = sum_{i in chunk c} Q[j][i] p[i] for j < k
-__global__ void __launch_bounds__(RT) k_reorth_dots(const double* __restrict__ Q, const double* __restrict__ p, i64 n,
+template <typename T>
+__global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ p, i64 n,
                                                      int chunk, const CGState* st, double* __restrict__ part2) {
   if (st->done) return;
   const int k = min(st->k, st->cap);
@@ -155,9 +162,9 @@ __global__ void __launch_bounds__(RT) k_reorth_dots(const double* __restrict__ Q
   const i64 hi = min(n, lo + chunk);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = blockIdx.y * (RT / 32) + warp; j < k; j += gridDim.y * (RT / 32)) {
-    const double* qj = Q + (i64)j * n;
+    const T* qj = Q + (i64)j * n;
     double s = 0.0;
-    for (i64 i = lo + lane; i < hi; i += 32) s = fma(qj[i], p[i], s);
+    for (i64 i = lo + lane; i < hi; i += 32) s = fma((double)qj[i], (double)p[i], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) part2[(i64)j * nchunk + c] = s;
@@ -176,7 +183,8 @@ __global__ void __launch_bounds__(RT) k_reorth_coef(const double* __restrict__ p
   coef[j] = s / eta_hist[j];
 }
 
-__global__ void __launch_bounds__(RT) k_reorth_apply(const double* __restrict__ S, double* __restrict__ p, i64 n,
+template <typename T>
+__global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, T* __restrict__ p, i64 n,
                                                       const CGState* st, const double* __restrict__ coef) {
   if (st->done) return;
   __shared__ double cs[1024];
@@ -191,13 +199,13 @@ __global__ void __launch_bounds__(RT) k_reorth_apply(const double* __restrict__ 
     if (i < n) {
       int j = 0;
       for (; j + 1 < jn; j += 2) {
-        acc0 = fma(S[(i64)(j0 + j) * n + i], cs[j], acc0);
-        acc1 = fma(S[(i64)(j0 + j + 1) * n + i], cs[j + 1], acc1);
+        acc0 = fma((double)S[(i64)(j0 + j) * n + i], cs[j], acc0);
+        acc1 = fma((double)S[(i64)(j0 + j + 1) * n + i], cs[j + 1], acc1);
       }
-      if (j < jn) acc0 = fma(S[(i64)(j0 + j) * n + i], cs[j], acc0);
+      if (j < jn) acc0 = fma((double)S[(i64)(j0 + j) * n + i], cs[j], acc0);
     }
   }
-  if (i < n) p[i] -= acc0 + acc1;
+  if (i < n) p[i] = (T)((double)p[i] - (acc0 + acc1));
 }
 
 // ---------------------------------------------------------------------------
@@ -208,46 +216,63 @@ int reduce_grid(i64 n) {
   return g;
 }
 
-void cg_init(const double* b, double* x, double* r, double* p, i64 n, CGState* st, cudaStream_t s) {
-  k_init<<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st);
+template <typename TB, typename T>
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s) {
+  k_init<TB, T><<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st);
   GPFVM_LAUNCH_CHECK();
 }
-void cg_dot_eta(const double* p, const double* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
-  k_dot_eta<<<reduce_grid(n), RT, 0, s>>>(p, q, n, st, eta_hist);
+template <typename T>
+void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
+  k_dot_eta<T><<<reduce_grid(n), RT, 0, s>>>(p, q, n, st, eta_hist);
   GPFVM_LAUNCH_CHECK();
 }
-void cg_downdate(const double* u, double* down, i64 n, const CGState* st, cudaStream_t s) {
-  k_downdate<<<ceil_div(n, RT), RT, 0, s>>>(u, down, n, st);
+template <typename T>
+void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_t s) {
+  k_downdate<T><<<ceil_div(n, RT), RT, 0, s>>>(u, down, n, st);
   GPFVM_LAUNCH_CHECK();
 }
-void cg_update(double* x, double* r, const double* p, const double* q, i64 n, CGState* st, double* S, double* Q,
-               cudaStream_t s) {
-  k_update<<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q);
+template <typename T>
+void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s) {
+  k_update<T><<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q);
   GPFVM_LAUNCH_CHECK();
 }
-void cg_pupdate(const double* r, double* p, i64 n, const CGState* st, cudaStream_t s) {
-  k_pupdate<<<ceil_div(n, RT), RT, 0, s>>>(r, p, n, st);
+template <typename T>
+void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s) {
+  k_pupdate<T><<<ceil_div(n, RT), RT, 0, s>>>(r, p, n, st);
   GPFVM_LAUNCH_CHECK();
 }
 int reorth_chunks(i64 n) {
   int c = ceil_div(n, 4096);
   return c < 1 ? 1 : c;
 }
-void cg_reorth(const double* S, const double* Q, double* p, i64 n, int cap, const CGState* st, double* part2,
-               double* coef, const double* eta_hist, cudaStream_t s) {
+template <typename T>
+void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, double* part2, double* coef,
+               const double* eta_hist, cudaStream_t s) {
   const int nchunk = reorth_chunks(n);
   const int chunk = (int)((n + nchunk - 1) / nchunk);
   int gy = ceil_div(cap, RT / 32);
   const int target = 4 * 152;
   if ((i64)gy * nchunk > target) gy = (target + nchunk - 1) / nchunk;
   if (gy < 1) gy = 1;
-  k_reorth_dots<<<dim3(nchunk, gy), RT, 0, s>>>(Q, p, n, chunk, st, part2);
+  k_reorth_dots<T><<<dim3(nchunk, gy), RT, 0, s>>>(Q, p, n, chunk, st, part2);
   GPFVM_LAUNCH_CHECK();
   k_reorth_coef<<<ceil_div(cap, RT), RT, 0, s>>>(part2, nchunk, eta_hist, st, coef);
   GPFVM_LAUNCH_CHECK();
-  k_reorth_apply<<<ceil_div(n, RT), RT, 0, s>>>(S, p, n, st, coef);
+  k_reorth_apply<T><<<ceil_div(n, RT), RT, 0, s>>>(S, p, n, st, coef);
   GPFVM_LAUNCH_CHECK();
 }
+
+#define GPFVM_CG_INST(T)                                                                                    \
+  template void cg_dot_eta<T>(const T*, const T*, i64, CGState*, double*, cudaStream_t);                   \
+  template void cg_downdate<T>(const T*, double*, i64, const CGState*, cudaStream_t);                      \
+  template void cg_update<T>(T*, T*, const T*, const T*, i64, CGState*, T*, T*, cudaStream_t);             \
+  template void cg_pupdate<T>(const T*, T*, i64, const CGState*, cudaStream_t);                            \
+  template void cg_reorth<T>(const T*, const T*, T*, i64, int, const CGState*, double*, double*, const double*, \
+                             cudaStream_t);
+GPFVM_CG_INST(double)
+GPFVM_CG_INST(float)
+template void cg_init<double, double>(const double*, double*, double*, double*, i64, CGState*, cudaStream_t);
+template void cg_init<double, float>(const double*, float*, float*, float*, i64, CGState*, cudaStream_t);
 
 // ---- small vector helpers -------------------------------------------------
 __global__ void k_axpby(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
@@ -278,6 +303,28 @@ __global__ void k_norm2(const double* __restrict__ v, i64 n, double* out, double
 }
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s) {
   k_norm2<<<reduce_grid(n), RT, 0, s>>>(v, n, out, st->part, &st->ticket[3]);
+  GPFVM_LAUNCH_CHECK();
+}
+
+__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] += (double)d[i];
+}
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  k_add_f2d<<<g, RT, 0, s>>>(x, d, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, i64 n) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) b[i] = (double)a[i];
+}
+void f2d(const float* a, double* b, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  k_f2d<<<g, RT, 0, s>>>(a, b, n);
   GPFVM_LAUNCH_CHECK();
 }
 

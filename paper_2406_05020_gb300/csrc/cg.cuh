@@ -17,14 +17,21 @@ struct CGState {
 
 int reduce_grid(i64 n);
 int reorth_chunks(i64 n);
-void cg_init(const double* b, double* x, double* r, double* p, i64 n, CGState* st, cudaStream_t s);
-void cg_dot_eta(const double* p, const double* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
-void cg_downdate(const double* u, double* down, i64 n, const CGState* st, cudaStream_t s);
-void cg_update(double* x, double* r, const double* p, const double* q, i64 n, CGState* st, double* S, double* Q,
-               cudaStream_t s);
-void cg_pupdate(const double* r, double* p, i64 n, const CGState* st, cudaStream_t s);
-void cg_reorth(const double* S, const double* Q, double* p, i64 n, int cap, const CGState* st, double* part2,
-               double* coef, const double* eta_hist, cudaStream_t s);
+template <typename TB, typename T>
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s);
+template <typename T>
+void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
+template <typename T>
+void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_t s);
+template <typename T>
+void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s);
+template <typename T>
+void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s);
+template <typename T>
+void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, double* part2, double* coef,
+               const double* eta_hist, cudaStream_t s);
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s);
+void f2d(const float* a, double* b, i64 n, cudaStream_t s);
 void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s);
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s);
 void var_final(const double* vB, const double* down, double* var, double s2, i64 n, cudaStream_t s);

@@ -59,6 +59,7 @@ struct GemmDesc {
   const GemmSeg* segs;
   const GemmGroup* groups;
   const int* skip;  // if non-null and *skip != 0 the launch does nothing (converged CG)
+  int f32;          // 1: every A/B/C/D pointer of the launch addresses float data (FP32 FFMA)
 };
 void launch_gemm64(const GemmDesc& g, cudaStream_t st);
 
@@ -66,6 +67,11 @@ void launch_gemm64(const GemmDesc& g, cudaStream_t st);
 // tri: 0 full, 1 lower (j <= i), 2 upper (j >= i).
 void launch_gemv64(int m, int n, const double* A, i64 lda, const double* x, double* y, double alpha,
                    double beta, int tri, cudaStream_t st, const int* skip = nullptr);
+// FP32 variant (float A, x, y; FP32 accumulation)
+void launch_gemv32(int m, int n, const float* A, i64 lda, const float* x, float* y, float alpha, float beta, int tri,
+                   cudaStream_t st, const int* skip = nullptr);
+// float <-> double conversions
+void convert_d2f(const double* in, float* out, i64 n, cudaStream_t st);
 
 // ---- IC/BC stage base case (chol.cu) ---------------------------------------
 // One CTA factorises an n <= 64 diagonal block: L = chol(A) and Linv = L^-1.

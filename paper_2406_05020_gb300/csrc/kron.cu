@@ -30,7 +30,8 @@ static int pick_tile(int m, i64 ctas_per_rowtile) {
 
 // out (dims with `ax` replaced by n_out) = sum over segs of alpha F x_ax in (+ beta out + gamma D)
 void add_mode_gemm(Plan& plan, int d, const int* dims, int ax, int n_out, i64 batch,
-                   const std::vector<std::pair<GemmGroup, std::vector<std::pair<MatRef, std::pair<const double*, double>>>>>& groups) {
+                   const std::vector<std::pair<GemmGroup, std::vector<std::pair<MatRef, std::pair<const double*, double>>>>>& groups,
+                   bool f32) {
   i64 pre = batch;
   for (int i = 0; i < ax; ++i) pre *= dims[i];
   const int n_in = dims[ax];
@@ -75,6 +76,7 @@ void add_mode_gemm(Plan& plan, int d, const int* dims, int ax, int n_out, i64 ba
     }
   }
   g.tri = 0;
+  g.f32 = f32 ? 1 : 0;
   plan.gemm(g, gs);
 }
 
@@ -82,7 +84,7 @@ static bool same(const MatRef& a, const MatRef& b) { return a.p == b.p && a.rs =
 
 void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* dout, i64 batch,
                const std::vector<KTerm>& terms, double scale, const double* in, double* out, double beta,
-               const double* D, double gamma, int* n_modeprods) {
+               const double* D, double gamma, int* n_modeprods, bool f32) {
   if (terms.empty()) throw CudaError{cudaErrorInvalidValue, "kron: no terms"};
   // axis order: most shrinking first
   int order[3] = {0, 1, 2};
@@ -95,7 +97,7 @@ void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* d
     std::vector<std::pair<MatRef, std::pair<const double*, double>>> segs;
     for (auto& t : terms) segs.push_back({t.f[0], {in, scale * t.c}});
     int dims[1] = {din[0]};
-    add_mode_gemm(plan, 1, dims, 0, dout[0], batch, {{G, segs}});
+    add_mode_gemm(plan, 1, dims, 0, dout[0], batch, {{G, segs}}, f32);
     count = 1;
   } else {
     const int p0 = order[0], plast = order[d - 1];
@@ -122,7 +124,7 @@ void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* d
         Y.push_back(y);
         gs.push_back({GemmGroup{y, nullptr, 0.0, 0.0, 0, 0}, {{U[u], {in, 1.0}}}});
       }
-      add_mode_gemm(plan, 3, din, p0, dout[p0], batch, gs);
+      add_mode_gemm(plan, 3, din, p0, dout[p0], batch, gs, f32);
       count += (int)U.size();
     }
     // level 2: axis pm (middle for d == 3, first for d == 2), grouped by the factor on plast
@@ -153,11 +155,11 @@ void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* d
       gs2.push_back({GemmGroup{z, nullptr, 0.0, 0.0, 0, 0}, wsegs[w]});
       count += (int)wsegs[w].size();
     }
-    add_mode_gemm(plan, d, dims1, pm, dout[pm], batch, gs2);
+    add_mode_gemm(plan, d, dims1, pm, dout[pm], batch, gs2, f32);
     // level 3: last axis, one group summing over the distinct factors
     std::vector<std::pair<MatRef, std::pair<const double*, double>>> segs3;
     for (size_t w = 0; w < Wf.size(); ++w) segs3.push_back({Wf[w], {Z[w], scale}});
-    add_mode_gemm(plan, d, dims2, plast, dout[plast], batch, {{GemmGroup{out, D, beta, gamma, 0, 0}, segs3}});
+    add_mode_gemm(plan, d, dims2, plast, dout[plast], batch, {{GemmGroup{out, D, beta, gamma, 0, 0}, segs3}}, f32);
     count += (int)Wf.size();
   }
   if (n_modeprods) *n_modeprods += count;

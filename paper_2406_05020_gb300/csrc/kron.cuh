@@ -33,9 +33,10 @@ struct Scratch {
 //   out = scale * sum_t c_t (F_t0 (x) ... ) in  + beta*out + gamma*D
 // for `batch` contiguous tensors (in: prod din, out: prod dout doubles each).
 // Intermediates come from `scratch`.  n_modeprods (optional) accumulates the
-// number of mode products issued.
+// number of mode products issued.  With f32 every pointer (factors, in, out,
+// D) addresses float data and the GEMMs run in FP32.
 void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* dout, i64 batch,
                const std::vector<KTerm>& terms, double scale, const double* in, double* out, double beta,
-               const double* D, double gamma, int* n_modeprods);
+               const double* D, double gamma, int* n_modeprods, bool f32 = false);
 
 }  // namespace gpfvm

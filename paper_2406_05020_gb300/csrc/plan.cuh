@@ -9,7 +9,7 @@
 namespace gpfvm {
 
 struct PlanOp {
-  enum Kind { GEMM, GEMV, FUNC } kind;
+  enum Kind { GEMM, GEMV, GEMV32, FUNC } kind;
   GemmDesc g;
   int seg0 = 0, group0 = 0;
   // GEMV
@@ -62,6 +62,13 @@ class Plan {
     op.alpha = alpha; op.beta = beta; op.tri = tri;
     ops.push_back(op);
   }
+  void gemv32(int m, int n, const float* A, i64 lda, const float* x, float* y, int tri) {
+    PlanOp op;
+    op.kind = PlanOp::GEMV32;
+    op.m = m; op.n = n; op.A = (const double*)A; op.lda = lda; op.x = (const double*)x; op.y = (double*)y;
+    op.alpha = 1.0; op.beta = 0.0; op.tri = tri;
+    ops.push_back(op);
+  }
   void func(std::function<void(cudaStream_t)> f) {
     PlanOp op;
     op.kind = PlanOp::FUNC;
@@ -97,6 +104,9 @@ class Plan {
       if (op.kind == PlanOp::GEMM) launch_gemm64(op.g, st);
       else if (op.kind == PlanOp::GEMV)
         launch_gemv64(op.m, op.n, op.A, op.lda, op.x, op.y, op.alpha, op.beta, op.tri, st, skip);
+      else if (op.kind == PlanOp::GEMV32)
+        launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, 1.0f, 0.0f, op.tri,
+                      st, skip);
       else op.fn(st);
     }
   }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libgpfvm.so")
 
 MAX_DIM, MAX_TERMS, MAX_SETS = 3, 8, 8
 OK, NOT_CONVERGED = 0, 1
-FP64, MIXED_TF32 = 0, 1
+FP64, MIXED_FP32, MIXED_TF32X3 = 0, 1, 2
 
 _lib = None
 
@@ -52,7 +52,8 @@ class Desc(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("precision", C.c_int), ("reorth", C.c_int),
-                ("want_var", C.c_int), ("check_every", C.c_int), ("replace_every", C.c_int)]
+                ("want_var", C.c_int), ("check_every", C.c_int), ("inner_max_iter", C.c_int),
+                ("inner_rtol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -171,11 +172,11 @@ def make_desc(prob):
 
 
 def solve_opts(max_iter=2000, rtol=1e-10, precision=FP64, reorth=True, want_var=True, check_every=16,
-               replace_every=50):
+               inner_max_iter=0, inner_rtol=1e-2):
     o = SolveOpts()
     o.max_iter, o.rtol, o.precision = int(max_iter), float(rtol), int(precision)
-    o.reorth, o.want_var, o.check_every, o.replace_every = int(reorth), int(want_var), int(check_every), int(
-        replace_every)
+    o.reorth, o.want_var, o.check_every = int(reorth), int(want_var), int(check_every)
+    o.inner_max_iter, o.inner_rtol = int(inner_max_iter), float(inner_rtol)
     return o
 
 
