@@ -159,6 +159,17 @@ struct gpfvm_problem {
   float *f_p = nullptr, *f_q = nullptr, *f_r = nullptr, *f_d = nullptr, *f_g = nullptr, *f_t = nullptr,
         *f_w = nullptr, *f_u = nullptr, *f_S = nullptr, *f_Q = nullptr, *f_vin = nullptr, *f_vout = nullptr;
   double* d_eta32 = nullptr;
+  // structured IC/BC stage: set 0 inverted through its Kronecker eigen-structure,
+  // the other sets through the Schur complement S (see icbc.cu)
+  bool sicbc = false;
+  int MK = 0, MR = 0, nK[3] = {1, 1, 1};
+  double *d_QK[3] = {}, *d_lam[3] = {}, *d_lt = nullptr, *d_ltinv = nullptr;
+  double *d_BT = nullptr, *d_Et = nullptr, *d_E1 = nullptr, *d_Sc = nullptr, *d_LS = nullptr, *d_LSinv = nullptr,
+         *d_LSinvT = nullptr, *d_sscr = nullptr, *d_Ft = nullptr, *d_F = nullptr, *d_R = nullptr;
+  double *d_hK = nullptr, *d_tR = nullptr, *d_uR = nullptr, *d_H[3] = {}, *d_Hsq[3] = {};
+  float *f_QK[3] = {}, *f_Ft = nullptr, *f_F = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_hK = nullptr,
+        *f_tR = nullptr, *f_uR = nullptr;
+  JacobiJob* d_jac = nullptr;
   CGState* d_st32 = nullptr;
   CGState* h_st32 = nullptr;
   i64 nfac = 0;
@@ -325,8 +336,54 @@ struct Builder {
     }
   }
   // w = G_BB^-1 g via the explicit inverse factor
+  // w = G_BB^-1 g with set 0 through its eigen-structure and the rest through S:
+  //   h = A^-1 g_K ;  t_R = g_R - F^T g_K ;  w_R = S^-1 t_R ;  w_K = h - F w_R
+  void hsolve_struct(Plan& plan, const double* g, double* w) {
+    const int MK = p->MK, MR = p->MR;
+    int dK[3];
+    dims_set(p, 0, dK);
+    KTerm QT{}, Qn{};
+    QT.c = Qn.c = 1.0;
+    for (int i = 0; i < p->d; ++i) {
+      const double* q = f32 ? (const double*)p->f_QK[i] : p->d_QK[i];
+      QT.f[i] = MatRef{q, 1, p->nK[i]};
+      Qn.f[i] = MatRef{q, p->nK[i], 1};
+    }
+    double* hK = f32 ? (double*)p->f_hK : p->d_hK;
+    kron(plan, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0);
+    const double* lt = p->d_lt;
+    const bool F32 = f32;
+    plan.func([=](cudaStream_t st) {
+      if (F32) scale_cols32((float*)hK, 1, MK, lt, -1.0, st);
+      else scale_cols(hK, 1, MK, lt, -1.0, st);
+    });
+    kron(plan, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0);
+    if (MR > 0) {
+      const size_t es = f32 ? sizeof(float) : sizeof(double);
+      double* tR = f32 ? (double*)p->f_tR : p->d_tR;
+      double* uR = f32 ? (double*)p->f_uR : p->d_uR;
+      const double* gR = at(g, MK);
+      double* wR = at(w, MK);
+      plan.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemcpyAsync(tR, gR, es * MR, cudaMemcpyDeviceToDevice, st)); });
+      if (f32) {
+        plan.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
+        plan.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
+        plan.gemv32(MR, MR, p->f_LSinvT, MR, (const float*)uR, (float*)wR, 2);
+        plan.gemv32(MK, MR, p->f_F, MR, (const float*)wR, (float*)w, 0, -1.0, 1.0);
+      } else {
+        plan.gemv(MR, MK, p->d_Ft, MK, g, tR, -1.0, 1.0, 0);
+        plan.gemv(MR, MR, p->d_LSinv, MR, tR, uR, 1.0, 0.0, 1);
+        plan.gemv(MR, MR, p->d_LSinvT, MR, uR, wR, 1.0, 0.0, 2);
+        plan.gemv(MK, MR, p->d_F, MR, wR, w, -1.0, 1.0, 0);
+      }
+    }
+  }
   void hsolve(Plan& plan, const double* g, double* t, double* w) {
     const int M = (int)p->M;
+    if (p->sicbc) {
+      hsolve_struct(plan, g, w);
+      return;
+    }
     if (f32) {
       plan.gemv32(M, M, p->f_Linv, M, (const float*)g, (float*)t, 1);
       plan.gemv32(M, M, p->f_LinvT, M, (const float*)t, (float*)w, 2);
@@ -367,6 +424,129 @@ struct Builder {
   }
 };
 
+// Structured IC/BC assembly (see icbc.cu): eigen-decompose set 0's 1D
+// factors, form the Schur complement of the other sets and factorise it.
+void build_sicbc(gpfvm_problem* p, Builder& B) {
+  Plan& pl = p->p_chol;
+  const int M = (int)p->M, MK = p->MK, MR = p->MR, d = p->d;
+  int dK[3];
+  dims_set(p, 0, dK);
+  KTerm QT{}, Qn{};
+  QT.c = Qn.c = 1.0;
+  int maxn = 1;
+  for (int i = 0; i < d; ++i) {
+    QT.f[i] = MatRef{p->d_QK[i], 1, p->nK[i]};
+    Qn.f[i] = MatRef{p->d_QK[i], p->nK[i], 1};
+    maxn = std::max(maxn, p->nK[i]);
+  }
+  gpfvm_problem* pp = p;
+  pl.func([=](cudaStream_t st) {
+    launch_jacobi(pp->d_jac, pp->d, maxn, st);
+    lambda_tensor(pp->d_lam[0], d >= 2 ? pp->d_lam[1] : nullptr, d >= 3 ? pp->d_lam[2] : nullptr, pp->nK[0],
+                  d >= 2 ? pp->nK[1] : 1, d >= 3 ? pp->nK[2] : 1, pp->s2, pp->sets[0].noise, pp->d_lt, st);
+    recip(pp->d_lt, pp->d_ltinv, MK, st);
+  });
+  if (MR > 0) {
+    pl.func([=](cudaStream_t st) {
+      GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_BT, sizeof(double) * MK, pp->d_A + (i64)MK * M, sizeof(double) * M,
+                                   sizeof(double) * MK, MR, cudaMemcpyDeviceToDevice, st));
+    });
+    B.kron(pl, dK, dK, MR, {QT}, 1.0, p->d_BT, p->d_Et, 0.0, nullptr, 0.0);
+    pl.func([=](cudaStream_t st) {
+      GPFVM_CUDA(cudaMemcpyAsync(pp->d_E1, pp->d_Et, sizeof(double) * MR * MK, cudaMemcpyDeviceToDevice, st));
+      scale_cols(pp->d_E1, MR, MK, pp->d_lt, -0.5, st);
+      GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_Sc, sizeof(double) * MR, pp->d_A + (i64)MK * M + MK, sizeof(double) * M,
+                                   sizeof(double) * MR, MR, cudaMemcpyDeviceToDevice, st));
+      GPFVM_CUDA(cudaMemsetAsync(pp->d_LS, 0, sizeof(double) * MR * MR, st));
+      GPFVM_CUDA(cudaMemsetAsync(pp->d_LSinv, 0, sizeof(double) * MR * MR, st));
+    });
+    {
+      GemmDesc g{};
+      g.m = MR; g.n = MR; g.k = MK;
+      g.a_rs = MK; g.a_cs = 1; g.b_rs = 1; g.b_cs = MK; g.c_rs = MR;
+      g.batch = 1; g.tri = TRI_C_LOWER; g.tile = 0;
+      pl.gemm(g, {{GemmGroup{p->d_Sc, nullptr, 1.0, 0.0, 0, 0}, {GemmSeg{p->d_E1, p->d_E1, -1.0}}}});
+    }
+    plan_chol_inverse(pl, p->d_Sc, p->d_LS, p->d_LSinv, MR, MR, p->d_sscr, p->d_st ? &p->d_st->pad[0] : nullptr);
+    pl.func([=](cudaStream_t st) {
+      transpose(pp->d_LSinv, pp->d_LSinvT, MR, MR, st);
+      scale_cols(pp->d_Et, MR, MK, pp->d_lt, -1.0, st);
+    });
+    B.kron(pl, dK, dK, MR, {Qn}, 1.0, p->d_Et, p->d_Ft, 0.0, nullptr, 0.0);
+    pl.func([=](cudaStream_t st) { transpose(pp->d_Ft, pp->d_F, MR, MK, st); });
+  }
+  pl.func([=](cudaStream_t st) {
+    for (int i = 0; i < d; ++i) convert_d2f(pp->d_QK[i], pp->f_QK[i], (i64)pp->nK[i] * pp->nK[i], st);
+    if (MR > 0) {
+      convert_d2f(pp->d_Ft, pp->f_Ft, (i64)MR * MK, st);
+      convert_d2f(pp->d_F, pp->f_F, (i64)MR * MK, st);
+      convert_d2f(pp->d_LSinv, pp->f_LSinv, (i64)MR * MR, st);
+      convert_d2f(pp->d_LSinvT, pp->f_LSinvT, (i64)MR * MR, st);
+    }
+  });
+}
+
+// Cholesky-stage variance with the structured IC/BC stage:
+//   k_B^T G_BB^-1 k_B = k_K^T A^-1 k_K + || L_S^-1 (k_R - F^T k_K) ||^2
+// term 1 = sigma^4 sum_m prod_i H_i[m_i,p_i]^2 / lambda~[m] with H_i = Q_i^T F_{K,i}
+// is itself a Kronecker product applied to the tensor 1/lambda~; term 2 uses
+// R = L_S^-1 F^T and runs over row chunks.
+void build_sicbc_var(gpfvm_problem* p, Builder& B) {
+  Plan& pl = p->p_vB;
+  const int MK = p->MK, MR = p->MR, d = p->d;
+  const i64 P = p->P;
+  int dK[3], dP[3], ds[3];
+  dims_set(p, 0, dK);
+  dims_pred(p, dP);
+  KTerm T1{};
+  T1.c = 1.0;
+  for (int i = 0; i < d; ++i) {
+    const int n = p->nK[i], pi = p->npred[i];
+    GemmDesc g{};
+    g.m = n; g.n = pi; g.k = n;
+    g.a_rs = 1; g.a_cs = n; g.b_rs = pi; g.b_cs = 1; g.c_rs = pi;
+    g.batch = 1; g.tile = 2;
+    const double* FK = p->d_fac + p->fac_off.at(FKey(i, 1, 0, 2, 0));
+    pl.gemm(g, {{GemmGroup{p->d_H[i], nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_QK[i], FK, 1.0}}}});
+    double* H = p->d_H[i];
+    double* Hs = p->d_Hsq[i];
+    pl.func([=](cudaStream_t st) { square(H, Hs, (i64)n * pi, st); });
+    T1.f[i] = MatRef{p->d_Hsq[i], 1, pi};
+  }
+  B.kron(pl, dK, dP, 1, {T1}, p->s2 * p->s2, p->d_ltinv, p->d_vB, 0.0, nullptr, 0.0);
+  if (MR == 0) return;
+  {
+    GemmDesc g{};
+    g.m = MR; g.n = MK; g.k = MR;
+    g.a_rs = MR; g.a_cs = 1; g.b_rs = MK; g.b_cs = 1; g.c_rs = MK;
+    g.batch = 1; g.tri = TRI_A_LOWER; g.tile = 0;
+    pl.gemm(g, {{GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_LSinv, p->d_Ft, 1.0}}}});
+  }
+  const int Rrows = p->vb_rows;
+  double* vB = p->d_vB;
+  for (int m0 = 0; m0 < MR; m0 += Rrows) {
+    const int rows = std::min(Rrows, MR - m0);
+    bool first = true;
+    for (int s = 1; s < p->nsets; ++s) {
+      const i64 offR = p->sets[s].off - MK, ms = p->sets[s].size;
+      if (offR > m0 + rows - 1) continue;  // L_S^-1 is lower triangular
+      const double* src = p->d_LSinv + (i64)m0 * MR + offR;
+      double* dst = p->d_vbchunk;
+      pl.func([=](cudaStream_t st) {
+        GPFVM_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ms, src, sizeof(double) * MR, sizeof(double) * ms, rows,
+                                     cudaMemcpyDeviceToDevice, st));
+      });
+      dims_set(p, s, ds);
+      B.kron(pl, ds, dP, rows, bpred_terms(p, s), p->s2, p->d_vbchunk, p->d_vbY, first ? 0.0 : 1.0, nullptr, 0.0);
+      first = false;
+    }
+    B.kron(pl, dK, dP, rows, bpred_terms(p, 0), -p->s2, p->d_R + (i64)m0 * MK, p->d_vbY, first ? 0.0 : 1.0, nullptr,
+           0.0);
+    const double* Y = p->d_vbY;
+    pl.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
+  }
+}
+
 void build_plans(gpfvm_problem* p, Builder& B) {
   const i64 N = p->N, M = p->M, P = p->P;
   gpfvm_problem* pp_ = p;
@@ -398,7 +578,9 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   }
   // ---- IC/BC Cholesky + inverse
   p->p_chol = Plan();
-  if (M > 0) {
+  if (M > 0 && p->sicbc) {
+    build_sicbc(p, B);
+  } else if (M > 0) {
     int* status = p->d_st ? &p->d_st->pad[0] : nullptr;
     p->p_chol.func([=](cudaStream_t st) {
       GPFVM_CUDA(cudaMemsetAsync(pp_->d_L, 0, sizeof(double) * M * M, st));
@@ -451,7 +633,9 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   B.to_pred_cells(p->p_mean, p->d_x, p->d_mean, 1.0, M > 0);
   // ---- Cholesky-stage variance term vB[p] = || L^-1 k_B(x_p) ||^2 in row chunks
   p->p_vB = Plan();
-  {
+  if (M > 0 && p->sicbc) {
+    build_sicbc_var(p, B);
+  } else {
     double* vB = p->d_vB;
     p->p_vB.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemsetAsync(vB, 0, sizeof(double) * P, st)); });
     const int R = p->vb_rows;
@@ -629,13 +813,69 @@ void alloc_all(gpfvm_problem* p) {
   }
   p->d_jobs = m.alloc<FactorJob>((i64)p->jobs.size());
   GPFVM_CUDA(cudaMemcpy(p->d_jobs, p->jobs.data(), p->jobs.size() * sizeof(FactorJob), cudaMemcpyHostToDevice));
-  // IC/BC matrices
+  // IC/BC matrices: the structured stage needs set 0 to be the largest set,
+  // to carry noise, and to have at most 96 points per axis (Jacobi in shared
+  // memory); GPFVM_ICBC=dense forces the dense Cholesky of all of G_BB.
+  p->sicbc = false;
   if (M > 0) {
+    const char* env = getenv("GPFVM_ICBC");
+    bool ok = !(env && std::strcmp(env, "dense") == 0) && p->sets[0].noise > 0;
+    for (int s = 1; s < p->nsets; ++s) ok = ok && p->sets[s].size <= p->sets[0].size;
+    for (int i = 0; i < p->d; ++i) ok = ok && p->sets[0].n[i] <= 96;
+    p->sicbc = ok;
+  }
+  if (M > 0 && p->sicbc) {
+    p->MK = (int)p->sets[0].size;
+    p->MR = (int)(M - p->MK);
+    const i64 MK = p->MK, MR = p->MR;
     p->d_A = m.alloc<double>(M * M);
-    p->d_L = m.alloc<double>(M * M);
-    p->d_Linv = m.alloc<double>(M * M);
-    p->d_LinvT = m.alloc<double>(M * M);
-    p->d_cscr = m.alloc<double>(M * M / 4 + 64 * M + 64);
+    std::vector<JacobiJob> jobs(p->d);
+    for (int i = 0; i < p->d; ++i) {
+      const int n = p->sets[0].n[i];
+      p->nK[i] = n;
+      p->d_QK[i] = m.alloc<double>((i64)n * n);
+      p->d_lam[i] = m.alloc<double>(n);
+      p->f_QK[i] = m.alloc<float>((i64)n * n);
+      p->d_H[i] = m.alloc<double>((i64)n * p->npred[i]);
+      p->d_Hsq[i] = m.alloc<double>((i64)n * p->npred[i]);
+      jobs[i] = JacobiJob{p->d_fac + p->fac_off.at(FKey(i, 1, 0, 1, 0)), p->d_QK[i], p->d_lam[i], n, 1e-14};
+    }
+    p->d_jac = m.alloc<JacobiJob>(p->d);
+    GPFVM_CUDA(cudaMemcpy(p->d_jac, jobs.data(), sizeof(JacobiJob) * p->d, cudaMemcpyHostToDevice));
+    p->d_lt = m.alloc<double>(MK);
+    p->d_ltinv = m.alloc<double>(MK);
+    p->d_hK = m.alloc<double>(MK);
+    p->f_hK = m.alloc<float>(MK);
+    if (MR > 0) {
+      p->d_BT = m.alloc<double>(MR * MK);
+      p->d_Et = m.alloc<double>(MR * MK);
+      p->d_E1 = m.alloc<double>(MR * MK);
+      p->d_Ft = m.alloc<double>(MR * MK);
+      p->d_F = m.alloc<double>(MR * MK);
+      p->d_R = m.alloc<double>(MR * MK);
+      p->d_Sc = m.alloc<double>(MR * MR);
+      p->d_LS = m.alloc<double>(MR * MR);
+      p->d_LSinv = m.alloc<double>(MR * MR);
+      p->d_LSinvT = m.alloc<double>(MR * MR);
+      p->d_sscr = m.alloc<double>(MR * MR / 4 + 64 * MR + 64);
+      p->d_tR = m.alloc<double>(MR);
+      p->d_uR = m.alloc<double>(MR);
+      p->f_Ft = m.alloc<float>(MR * MK);
+      p->f_F = m.alloc<float>(MR * MK);
+      p->f_LSinv = m.alloc<float>(MR * MR);
+      p->f_LSinvT = m.alloc<float>(MR * MR);
+      p->f_tR = m.alloc<float>(MR);
+      p->f_uR = m.alloc<float>(MR);
+    }
+  }
+  if (M > 0) {
+    if (!p->sicbc) {
+      p->d_A = m.alloc<double>(M * M);
+      p->d_L = m.alloc<double>(M * M);
+      p->d_Linv = m.alloc<double>(M * M);
+      p->d_LinvT = m.alloc<double>(M * M);
+      p->d_cscr = m.alloc<double>(M * M / 4 + 64 * M + 64);
+    }
     p->d_yB = m.alloc<double>(M);
     p->d_g = m.alloc<double>(M);
     p->d_t = m.alloc<double>(M);
@@ -681,8 +921,10 @@ void alloc_all(gpfvm_problem* p) {
   p->nfac = std::max<i64>(nfac, 1);
   p->f_fac = m.alloc<float>(p->nfac);
   if (M > 0) {
-    p->f_Linv = m.alloc<float>(M * M);
-    p->f_LinvT = m.alloc<float>(M * M);
+    if (!p->sicbc) {
+      p->f_Linv = m.alloc<float>(M * M);
+      p->f_LinvT = m.alloc<float>(M * M);
+    }
     p->f_g = m.alloc<float>(M);
     p->f_t = m.alloc<float>(M);
     p->f_w = m.alloc<float>(M);
@@ -737,7 +979,7 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
   }
   p->p_rhs.run(st);
   convert_d2f(p->d_fac, p->f_fac, p->nfac, st);
-  if (p->M > 0) {
+  if (p->M > 0 && !p->sicbc) {
     convert_d2f(p->d_Linv, p->f_Linv, p->M * p->M, st);
     convert_d2f(p->d_LinvT, p->f_LinvT, p->M * p->M, st);
   }
@@ -1233,6 +1475,7 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
     default: return GPFVM_ERR_INVALID_ARG;
   }
   if (n > capacity) return GPFVM_ERR_INVALID_ARG;
+  if (n > 0 && !src) return GPFVM_ERR_STATE;  // e.g. L^-1 under the structured IC/BC stage
   if (what == 2) {
     // G_BB is overwritten by the Cholesky recursion: rebuild it
     p->p_setup.run(st);

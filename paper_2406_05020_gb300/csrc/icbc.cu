@@ -1,0 +1,190 @@
+// Structured IC/BC stage: the exact inverse of G_BB through the Kronecker
+// structure of its largest point set.
+//
+// The first point set K (e.g. the initial condition on a tensor grid at
+// t = 0) has the self-covariance  A = sigma^2 (D_0 (x) D_1 (x) D_2) + nu I,
+// where D_i are its 1D point-point factors.  With D_i = Q_i diag(lam_i) Q_i^T,
+//   A^-1 = (x)Q_i  diag(1 / (sigma^2 prod_i lam_i + nu))  (x)Q_i^T ,
+// so A needs no factorisation.  The remaining sets R enter through the Schur
+// complement S = G_RR - G_RK A^-1 G_KR (block elimination, exact), which is
+// small (the boundary points) and factorised by the recursive Cholesky +
+// inverse of chol.cu.  This file holds the kernels: a one-sided Jacobi
+// eigensolver for the small symmetric factors D_i, and the eigenvalue-tensor
+// scalings.
+#include "kernels.cuh"
+
+namespace gpfvm {
+
+constexpr int JAC_MAX_N = 96;
+
+// One-sided (Hestenes) Jacobi on a symmetric positive semidefinite n x n
+// matrix: rotate column pairs of U = A until they are orthogonal; then
+// U = Q diag(lam) with Q = V, lam_j = ||U_j||.  Pairs follow the round-robin
+// (circle) schedule, so the n/2 rotations of a round touch disjoint columns.
+// The sweep count is bounded; convergence (largest |cos| between a rotated
+// column pair below tol) or the bound ends the loop.
+__global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict__ jobs) {
+  extern __shared__ double sm[];
+  const JacobiJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  const int np = (n + 1) & ~1;  // even number of players (one dummy if n is odd)
+  double* U = sm;               // column-major: U[j * n + i]
+  double* V = sm + n * n;
+  __shared__ double maxrot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    U[e] = 0.5 * (J.A[(i64)i * n + j] + J.A[(i64)j * n + i]);
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) maxrot = 0.0;
+    __syncthreads();
+    double local_max = 0.0;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = warp; k < np / 2; k += nw) {
+        int p, q;
+        if (k == 0) { p = r; q = np - 1; }
+        else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const double up = U[p * n + i], uq = U[q * n + i];
+          a += up * up;
+          b += uq * uq;
+          c += up * uq;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (c == 0.0 || a == 0.0 || b == 0.0) continue;
+        const double rot = fabs(c) / sqrt(a * b);
+        local_max = fmax(local_max, rot);
+        if (rot < 1e-15) continue;
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = lane; i < n; i += 32) {
+          const double up = U[p * n + i], uq = U[q * n + i];
+          U[p * n + i] = cs * up - sn * uq;
+          U[q * n + i] = sn * up + cs * uq;
+          const double vp = V[p * n + i], vq = V[q * n + i];
+          V[p * n + i] = cs * vp - sn * vq;
+          V[q * n + i] = sn * vp + cs * vq;
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0) {
+      // fold the warps' maxima (benign: max of non-negative doubles via integer compare)
+      atomicMax((unsigned long long*)&maxrot, __double_as_longlong(local_max));
+    }
+    __syncthreads();
+    const bool done = maxrot < J.tol;
+    __syncthreads();
+    if (done) break;
+  }
+  // eigenvalues = column norms of U, eigenvectors = columns of V
+  for (int j = warp; j < n; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += U[j * n + i] * U[j * n + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) J.lam[j] = sqrt(s);
+  }
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    J.Q[(i64)i * n + j] = V[j * n + i];  // Q row-major, column j = eigenvector j
+  }
+}
+
+void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st) {
+  if (n_jobs <= 0) return;
+  if (max_n > JAC_MAX_N) throw CudaError{cudaErrorInvalidValue, "jacobi: matrix too large"};
+  const int smem = 2 * max_n * max_n * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    GPFVM_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    2 * JAC_MAX_N * JAC_MAX_N * (int)sizeof(double)));
+    attr = true;
+  }
+  jacobi_kernel<<<n_jobs, 256, smem, st>>>(d_jobs);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// lt[m] = sigma^2 prod_i lam_i[m_i] + nu  over the row-major multi-index m of (n0, n1, n2)
+__global__ void k_lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2,
+                                double s2, double nu, double* __restrict__ lt) {
+  const i64 tot = (i64)n0 * n1 * n2;
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
+    const int i2 = (int)(e % n2), i1 = (int)((e / n2) % n1), i0 = (int)(e / ((i64)n1 * n2));
+    lt[e] = s2 * (l0 ? l0[i0] : 1.0) * (l1 ? l1[i1] : 1.0) * (l2 ? l2[i2] : 1.0) + nu;
+  }
+}
+void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,
+                   double* lt, cudaStream_t st) {
+  const i64 tot = (i64)n0 * n1 * n2;
+  int g = ceil_div(tot, 256);
+  if (g > 2048) g = 2048;
+  k_lambda_tensor<<<g, 256, 0, st>>>(l0, l1, l2, n0, n1, n2, s2, nu, lt);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// X[r][m] *= lt[m]^pw for rows r < rows (pw = -1 or -1/2); also a float copy if Xf
+template <typename T>
+__global__ void k_scale_cols(T* __restrict__ X, int rows, i64 cols, const double* __restrict__ lt, double pw) {
+  const i64 tot = (i64)rows * cols;
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
+    const double l = lt[e % cols];
+    const double f = (pw == -1.0) ? 1.0 / l : 1.0 / sqrt(l);
+    X[e] = (T)((double)X[e] * f);
+  }
+}
+void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st) {
+  const i64 tot = (i64)rows * cols;
+  if (tot <= 0) return;
+  int g = ceil_div(tot, 256);
+  if (g > 8192) g = 8192;
+  k_scale_cols<double><<<g, 256, 0, st>>>(X, rows, cols, lt, pw);
+  GPFVM_LAUNCH_CHECK();
+}
+void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st) {
+  const i64 tot = (i64)rows * cols;
+  if (tot <= 0) return;
+  int g = ceil_div(tot, 256);
+  if (g > 8192) g = 8192;
+  k_scale_cols<float><<<g, 256, 0, st>>>(X, rows, cols, lt, pw);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// out[m] = 1/lt[m] (the weight tensor of the A^-1 quadratic form)
+__global__ void k_recip(const double* __restrict__ lt, double* __restrict__ out, i64 n) {
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x)
+    out[e] = 1.0 / lt[e];
+}
+void recip(const double* lt, double* out, i64 n, cudaStream_t st) {
+  if (n <= 0) return;
+  int g = ceil_div(n, 256);
+  if (g > 2048) g = 2048;
+  k_recip<<<g, 256, 0, st>>>(lt, out, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// out[i][j] = in[i][j]^2 (squared factors for the A^-1 quadratic form on the grid)
+__global__ void k_square(const double* __restrict__ in, double* __restrict__ out, i64 n) {
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x)
+    out[e] = in[e] * in[e];
+}
+void square(const double* in, double* out, i64 n, cudaStream_t st) {
+  if (n <= 0) return;
+  int g = ceil_div(n, 256);
+  if (g > 2048) g = 2048;
+  k_square<<<g, 256, 0, st>>>(in, out, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
+}  // namespace gpfvm

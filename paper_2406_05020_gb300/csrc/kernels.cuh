@@ -78,4 +78,20 @@ void convert_d2f(const double* in, float* out, i64 n, cudaStream_t st);
 void launch_chol_base(const double* A, double* L, double* Linv, int n, i64 lda, int* status,
                       cudaStream_t st);
 
+// ---- structured IC/BC stage (icbc.cu) ---------------------------------------
+struct JacobiJob {
+  const double* A;  // n x n symmetric PSD, row-major
+  double* Q;        // n x n eigenvectors (columns), row-major
+  double* lam;      // n eigenvalues
+  int n;
+  double tol;
+};
+void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st);
+void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,
+                   double* lt, cudaStream_t st);
+void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
+void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
+void recip(const double* lt, double* out, i64 n, cudaStream_t st);
+void square(const double* in, double* out, i64 n, cudaStream_t st);
+
 }  // namespace gpfvm

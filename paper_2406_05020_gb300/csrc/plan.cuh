@@ -62,11 +62,12 @@ class Plan {
     op.alpha = alpha; op.beta = beta; op.tri = tri;
     ops.push_back(op);
   }
-  void gemv32(int m, int n, const float* A, i64 lda, const float* x, float* y, int tri) {
+  void gemv32(int m, int n, const float* A, i64 lda, const float* x, float* y, int tri, double alpha = 1.0,
+              double beta = 0.0) {
     PlanOp op;
     op.kind = PlanOp::GEMV32;
     op.m = m; op.n = n; op.A = (const double*)A; op.lda = lda; op.x = (const double*)x; op.y = (double*)y;
-    op.alpha = 1.0; op.beta = 0.0; op.tri = tri;
+    op.alpha = alpha; op.beta = beta; op.tri = tri;
     ops.push_back(op);
   }
   void func(std::function<void(cudaStream_t)> f) {
@@ -105,8 +106,8 @@ class Plan {
       else if (op.kind == PlanOp::GEMV)
         launch_gemv64(op.m, op.n, op.A, op.lda, op.x, op.y, op.alpha, op.beta, op.tri, st, skip);
       else if (op.kind == PlanOp::GEMV32)
-        launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, 1.0f, 0.0f, op.tri,
-                      st, skip);
+        launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, (float)op.alpha,
+                      (float)op.beta, op.tri, st, skip);
       else op.fn(st);
     }
   }
