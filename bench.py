@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gpfvm", choices=["gpfvm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=50)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling mode: one assemble, solves of this many CG iterations per path, one query")
     return ap.parse_args()
 
 
@@ -365,8 +367,38 @@ def run_gpfvm(args):
     return 0
 
 
+def run_profile(args):
+    """Short fixed-work run for launch lists: assemble, an FP64 solve and a
+    mixed solve of --profile-iters CG iterations each, query, and 3 Gram matvecs."""
+    import torch
+
+    from paper_2406_05020_gb300 import build, gpfvm
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    s_ptr = stream.cuda_stream
+    pb = gpfvm.Problem(workload(0), max_iter=max(args.profile_iters, 8))
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    pb.assemble(stream=s_ptr)
+    for prec in (gpfvm.FP64, gpfvm.MIXED_FP32):
+        opts = gpfvm.solve_opts(max_iter=args.profile_iters, rtol=0.0, precision=prec, reorth=True, want_var=True,
+                                inner_max_iter=args.profile_iters)
+        pb.solve(opts, stream=s_ptr)
+        pb.query(mean, var, stream=s_ptr)
+    v = torch.randn(pb.N, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    for op in (0, 1, 4):
+        pb.matvec(op, v, out, stream=s_ptr)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_iters": args.profile_iters, "launches": gpfvm.launch_count()}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_iters > 0:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpfvm(args)

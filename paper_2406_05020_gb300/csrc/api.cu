@@ -183,7 +183,7 @@ struct gpfvm_problem {
   // ---- plans
   Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB;
   Plan p_op[4];
-  Plan p_mv32, p_var32, p_pp32;
+  Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32;
   int modeprods_pp = 0;
 
   // ---- state
@@ -309,10 +309,17 @@ struct Builder {
                                       float*>::type FP;
     return (P)((FP)base + n);
   }
-  void kron(Plan& plan, const int* din, const int* dout, i64 batch, const std::vector<KTerm>& terms, double scale,
-            const double* in, double* out, double beta, const double* D, double gamma, int* count = nullptr) {
+  bool keep = false;  // inside a stage of zipped chains: intermediates must not overlap
+  void stage_begin() {
     scr.used = 0;
-    plan_kron(plan, scr, p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count, f32);
+    keep = true;
+  }
+  void stage_end() { keep = false; }
+  void kron(Plan& plan, const int* din, const int* dout, i64 batch, const std::vector<KTerm>& terms, double scale,
+            const double* in, double* out, double beta, const double* D, double gamma, int* count = nullptr,
+            int dd = 0) {
+    if (!keep) scr.used = 0;
+    plan_kron(plan, scr, dd > 0 ? dd : p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count, f32);
     peak = std::max(peak, scr.used);
   }
 
@@ -392,6 +399,114 @@ struct Builder {
     plan.gemv(M, M, p->d_Linv, M, g, t, 1.0, 0.0, 1);
     plan.gemv(M, M, p->d_LinvT, M, t, w, 1.0, 0.0, 2);
   }
+  // The structured G_BB^-1 apply as two zipped chains: the A^-1 transforms of
+  // g_K (singleton axes of set 0 dropped) and the Schur-complement GEMVs.
+  void hsolve_phased(Plan& plan, const double* g, double* w) {
+    if (!p->sicbc) {
+      double* t = f32 ? (double*)p->f_t : p->d_t;
+      hsolve(plan, g, t, w);
+      return;
+    }
+    const int MK = p->MK, MR = p->MR;
+    int dK[3], nd = 0;
+    KTerm QT{}, Qn{};
+    QT.c = Qn.c = 1.0;
+    for (int i = 0; i < p->d; ++i) {
+      if (p->nK[i] == 1 && !(i == p->d - 1 && nd == 0)) continue;  // Q = [1] on a singleton axis
+      const double* q = f32 ? (const double*)p->f_QK[i] : p->d_QK[i];
+      QT.f[nd] = MatRef{q, 1, p->nK[i]};
+      Qn.f[nd] = MatRef{q, p->nK[i], 1};
+      dK[nd++] = p->nK[i];
+    }
+    Plan c1, c2;
+    double* hK = f32 ? (double*)p->f_hK : p->d_hK;
+    kron(c1, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0, nullptr, nd);
+    const double* lt = p->d_lt;
+    const bool F32 = f32;
+    c1.func([=](cudaStream_t st) {
+      if (F32) scale_cols32((float*)hK, 1, MK, lt, -1.0, st);
+      else scale_cols(hK, 1, MK, lt, -1.0, st);
+    });
+    kron(c1, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0, nullptr, nd);
+    if (MR > 0) {
+      const size_t es = f32 ? sizeof(float) : sizeof(double);
+      double* tR = f32 ? (double*)p->f_tR : p->d_tR;
+      double* uR = f32 ? (double*)p->f_uR : p->d_uR;
+      const double* gR = at(g, MK);
+      double* wR = at(w, MK);
+      c2.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemcpyAsync(tR, gR, es * MR, cudaMemcpyDeviceToDevice, st)); });
+      if (f32) {
+        c2.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
+        c2.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
+        c2.gemv32(MR, MR, p->f_LSinvT, MR, (const float*)uR, (float*)wR, 2);
+      } else {
+        c2.gemv(MR, MK, p->d_Ft, MK, g, tR, -1.0, 1.0, 0);
+        c2.gemv(MR, MR, p->d_LSinv, MR, tR, uR, 1.0, 0.0, 1);
+        c2.gemv(MR, MR, p->d_LSinvT, MR, uR, wR, 1.0, 0.0, 2);
+      }
+      plan.zip({&c1, &c2});
+      Plan c3;
+      if (f32) c3.gemv32(MK, MR, p->f_F, MR, (const float*)wR, (float*)w, 0, -1.0, 1.0);
+      else c3.gemv(MK, MR, p->d_F, MR, wR, w, -1.0, 1.0, 0);
+      plan.append(c3);
+    } else {
+      plan.zip({&c1});
+    }
+  }
+
+  // out = G^ in as zipped stages; with u != null also u = Lhat k(X*)^T in.
+  //   stage A (reads in):  G_PP in, G_BP in (each set), L_PDE k(X*)^T in
+  //   stage B:             w = G_BB^-1 g
+  //   stage C (reads w):   out -= G_PB w, u -= k_B(X*)^T w  (last levels paired)
+  void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count) {
+    int dc[3], ds[3], dp[3];
+    dims_cells(p, dc);
+    dims_pred(p, dp);
+    stage_begin();
+    std::vector<Plan> A(1 + p->nsets + (u ? 1 : 0));
+    kron(A[0], dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(A[1 + s], dc, ds, 1, pb_terms(p, s, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+    }
+    if (u) kron(A.back(), dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
+    {
+      std::vector<const Plan*> c;
+      for (auto& x : A) c.push_back(&x);
+      plan.zip(c);
+    }
+    stage_end();
+    if (p->M == 0) return;
+    stage_begin();
+    hsolve_phased(plan, g, w);
+    stage_end();
+    stage_begin();
+    std::vector<Plan> PB(p->nsets), VS(u ? p->nsets : 0);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(PB[s], ds, dc, 1, pb_terms(p, s, false), -p->s2, at(w, p->sets[s].off), out, 1.0, nullptr, 0.0);
+      if (u) kron(VS[s], ds, dp, 1, bpred_terms(p, s), -p->s2, at(w, p->sets[s].off), u, 1.0, nullptr, 0.0);
+    }
+    stage_end();
+    std::vector<Plan> heads;
+    std::vector<const Plan*> hp;
+    std::vector<Plan> tpb, tvs;
+    for (int s = 0; s < p->nsets; ++s) {
+      heads.push_back(PB[s].slice(0, PB[s].ops.size() - 1));
+      tpb.push_back(PB[s].slice(PB[s].ops.size() - 1, PB[s].ops.size()));
+      if (u) {
+        heads.push_back(VS[s].slice(0, VS[s].ops.size() - 1));
+        tvs.push_back(VS[s].slice(VS[s].ops.size() - 1, VS[s].ops.size()));
+      }
+    }
+    for (auto& x : heads) hp.push_back(&x);
+    plan.zip(hp);
+    std::vector<const Plan*> a, b;
+    for (auto& x : tpb) a.push_back(&x);
+    for (auto& x : tvs) b.push_back(&x);
+    plan.zip_pairs(a, b);
+  }
+
   void pp(Plan& plan, const double* in, double* out, int* count) {
     int dc[3];
     dims_cells(p, dc);
@@ -605,17 +720,19 @@ void build_plans(gpfvm_problem* p, Builder& B) {
       B.pb(p->p_rhs, p->d_w, b, -1.0, true);
     }
   }
-  // ---- CG iteration plans
+  // ---- CG iteration plans (phased: independent mode products share launches)
   p->p_mv_cg = Plan();
   p->modeprods_pp = 0;
-  B.ghat(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_t, p->d_w, &p->modeprods_pp);
+  B.ghat_phased(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_w, nullptr, &p->modeprods_pp);
+  p->p_mvv_cg = Plan();
+  B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr);
   p->p_var_cg = Plan();
   B.to_pred_cells(p->p_var_cg, p->d_p, p->d_u, 1.0, false);
   if (M > 0) B.to_pred_sets(p->p_var_cg, p->d_w, p->d_u, -1.0, true);
   // ---- operator plans for gpfvm_gram_matvec / true residual
   for (int k = 0; k < 4; ++k) p->p_op[k] = Plan();
   B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
-  B.ghat(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_t, p->d_wout, nullptr);
+  B.ghat_phased(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
   if (M > 0) {
     B.bp(p->p_op[2], p->d_vin, p->d_wout);
     B.pb(p->p_op[3], p->d_win, p->d_vout, 1.0, false);
@@ -670,7 +787,9 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
   p->building_f32 = true;
   auto D = [](float* f) { return (double*)f; };
   p->p_mv32 = Plan();
-  B.ghat(p->p_mv32, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_t), D(p->f_w), nullptr);
+  B.ghat_phased(p->p_mv32, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), nullptr, nullptr);
+  p->p_mvv32 = Plan();
+  B.ghat_phased(p->p_mvv32, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), D(p->f_u), nullptr);
   p->p_var32 = Plan();
   B.to_pred_cells(p->p_var32, D(p->f_p), D(p->f_u), 1.0, false);
   if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true);
@@ -682,14 +801,17 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
 
 void finalize_plans(gpfvm_problem* p) {
   p->p_mv_cg.skip = &p->d_st->done;
+  p->p_mvv_cg.skip = &p->d_st->done;
   p->p_var_cg.skip = &p->d_st->done;
   p->p_mv32.skip = &p->d_st32->done;
+  p->p_mvv32.skip = &p->d_st32->done;
   p->p_var32.skip = &p->d_st32->done;
   Plan* all[] = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
-                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32};
+                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
+                 &p->p_mvv_cg, &p->p_mvv32};
   const char* names[] = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2", "op3",
-                         "mv32", "var32", "pp32"};
-  for (int i = 0; i < 14; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
+                         "mv32", "var32", "pp32", "mvv_cg", "mvv32"};
+  for (int i = 0; i < 16; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
   for (Plan* pl : all) pl->finalize();
 }
 
@@ -992,12 +1114,9 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
 
 void cg_iteration(gpfvm_problem* p, bool reorth, bool want_var, cudaStream_t st) {
   const i64 N = p->N;
-  p->p_mv_cg.run(st);
+  (want_var ? p->p_mvv_cg : p->p_mv_cg).run(st);
   cg_dot_eta(p->d_p, p->d_q, N, p->d_st, p->d_eta, st);
-  if (want_var) {
-    p->p_var_cg.run(st);
-    cg_downdate(p->d_u, p->d_down, p->P, p->d_st, st);
-  }
+  if (want_var) cg_downdate(p->d_u, p->d_down, p->P, p->d_st, st);
   cg_update(p->d_x, p->d_r, p->d_p, p->d_q, N, p->d_st, reorth ? p->d_S : nullptr, reorth ? p->d_Q : nullptr, st);
   cg_pupdate(p->d_r, p->d_p, N, p->d_st, st);
   if (reorth) cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
@@ -1140,12 +1259,9 @@ int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
 // One inner CG iteration of the mixed solver (FP32 operator and vectors, FP64 scalars).
 void cg_iteration32(gpfvm_problem* p, bool want_var, cudaStream_t st) {
   const i64 N = p->N;
-  p->p_mv32.run(st);
+  (want_var ? p->p_mvv32 : p->p_mv32).run(st);
   cg_dot_eta<float>(p->f_p, p->f_q, N, p->d_st32, p->d_eta32, st);
-  if (want_var) {
-    p->p_var32.run(st);
-    cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
-  }
+  if (want_var) cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
   cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, p->f_S, p->f_Q, st);
   cg_pupdate<float>(p->f_r, p->f_p, N, p->d_st32, st);
   cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);

@@ -8,23 +8,24 @@
 // smaller) register tile per thread, operands staged through shared memory in
 // K-chunks of 16, and no more than a few bytes of shared-memory traffic per
 // DFMA.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace gpfvm {
 
+// One output tile (BM x 64) of one (batch, group) entry; all threads of the
+// CTA must call it together (it synchronises through shared memory).
 template <typename T, int BM>
-__global__ void __launch_bounds__(256) gemm64_kernel(GemmDesc g) {
+__device__ __forceinline__ void gemm_tile(const GemmDesc& g, int bx, int by, i64 zb, T (*As)[BM + 1],
+                                          T (*Bs)[65]) {
   constexpr int BN = 64, BK = 16;
   constexpr int RM = BM / 16;  // rows per thread (4, 2, 1)
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
-
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int j0 = blockIdx.x * BN, i0 = blockIdx.y * BM;
+  const int j0 = bx * BN, i0 = by * BM;
   if ((g.tri & TRI_C_LOWER) && j0 > i0 + BM - 1) return;
-  if (g.skip && *g.skip) return;
-  for (i64 zb = blockIdx.z; zb < (i64)g.batch * g.n_groups; zb += gridDim.z) {
+  {
   const int grp = (int)(zb % g.n_groups);
   const int b = (int)(zb / g.n_groups);
   const GemmGroup G = g.groups[grp];
@@ -107,7 +108,98 @@ __global__ void __launch_bounds__(256) gemm64_kernel(GemmDesc g) {
       C[(i64)gi * g.c_rs + gj] = v;
     }
   }
-  }  // zb
+  }
+}
+
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) gemm64_kernel(GemmDesc g) {
+  __shared__ T As[16][BM + 1];
+  __shared__ T Bs[16][65];
+  if (g.skip && *g.skip) return;
+  for (i64 zb = blockIdx.z; zb < (i64)g.batch * g.n_groups; zb += gridDim.z)
+    gemm_tile<T, BM>(g, blockIdx.x, blockIdx.y, zb, As, Bs);
+}
+
+// Many GEMM ops (different shapes and operands, same element type and row
+// tile) in one launch: CTA t works on tile t - ops[o].tile_begin of op o.
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) multi_gemm_kernel(const MOp* __restrict__ ops, int nops, i64 total) {
+  __shared__ T As[16][BM + 1];
+  __shared__ T Bs[16][65];
+  for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nops - 1;
+    while (lo < hi) {  // last op with tile_begin <= t
+      const int mid = (lo + hi + 1) >> 1;
+      if (ops[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const MOp& op = ops[lo];
+    if (op.g.skip && *op.g.skip) continue;
+    const i64 r = t - op.tile_begin;
+    const int bx = (int)(r % op.tiles_x);
+    const int by = (int)((r / op.tiles_x) % op.tiles_y);
+    const i64 zb = r / ((i64)op.tiles_x * op.tiles_y);
+    gemm_tile<T, BM>(op.g, bx, by, zb, As, Bs);
+  }
+}
+
+void launch_multi_gemm(const MOp* d_ops, int nops, i64 total, int f32, int bm, cudaStream_t st) {
+  if (nops <= 0 || total <= 0) return;
+  const int grid = (int)std::min<i64>(total, 152 * 16);
+  if (f32) {
+    if (bm == 64) multi_gemm_kernel<float, 64><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    else if (bm == 32) multi_gemm_kernel<float, 32><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    else multi_gemm_kernel<float, 16><<<grid, 256, 0, st>>>(d_ops, nops, total);
+  } else {
+    if (bm == 64) multi_gemm_kernel<double, 64><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    else if (bm == 32) multi_gemm_kernel<double, 32><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    else multi_gemm_kernel<double, 16><<<grid, 256, 0, st>>>(d_ops, nops, total);
+  }
+  GPFVM_LAUNCH_CHECK();
+}
+
+// Many GEMV ops in one launch, one warp per output row over all ops:
+// y = alpha * A x + beta * z  (z may alias y).
+template <typename T>
+__global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict__ ops, int nops, i64 total_rows) {
+  const i64 w = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total_rows) return;
+  int lo = 0, hi = nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ops[mid].row_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  const MGemv& op = ops[lo];
+  if (op.skip && *op.skip) return;
+  const int i = (int)(w - op.row_begin);
+  int jlo = 0, jhi = op.n;
+  if (op.tri == 1) jhi = min(op.n, i + 1);
+  if (op.tri == 2) jlo = i;
+  const T* row = reinterpret_cast<const T*>(op.A) + (i64)i * op.lda;
+  const T* x = reinterpret_cast<const T*>(op.x);
+  T s0 = T(0), s1 = T(0);
+  int j = jlo + lane;
+  for (; j + 32 < jhi; j += 64) {
+    s0 = fma(row[j], x[j], s0);
+    s1 = fma(row[j + 32], x[j + 32], s1);
+  }
+  if (j < jhi) s0 = fma(row[j], x[j], s0);
+  T s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    T v = (T)op.alpha * s;
+    if (op.beta != 0.0) v += (T)op.beta * reinterpret_cast<const T*>(op.z)[i];
+    reinterpret_cast<T*>(op.y)[i] = v;
+  }
+}
+
+void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st) {
+  if (nops <= 0 || total_rows <= 0) return;
+  const int grid = ceil_div(total_rows * 32, 256);
+  if (f32) multi_gemv_kernel<float><<<grid, 256, 0, st>>>(d_ops, nops, total_rows);
+  else multi_gemv_kernel<double><<<grid, 256, 0, st>>>(d_ops, nops, total_rows);
+  GPFVM_LAUNCH_CHECK();
 }
 
 void launch_gemm64(const GemmDesc& g, cudaStream_t st) {

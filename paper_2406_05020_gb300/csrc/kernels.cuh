@@ -63,6 +63,27 @@ struct GemmDesc {
 };
 void launch_gemm64(const GemmDesc& g, cudaStream_t st);
 
+// A GEMM op inside a multi-op launch (tile grid of the op and its first tile).
+struct MOp {
+  GemmDesc g;
+  int tiles_x, tiles_y;
+  i64 tile_begin;
+};
+void launch_multi_gemm(const MOp* d_ops, int nops, i64 total_tiles, int f32, int bm, cudaStream_t st);
+
+// A GEMV op inside a multi-op launch: y = alpha A x + beta z (tri as launch_gemv64).
+struct MGemv {
+  const void* A;
+  const void* x;
+  const void* z;
+  void* y;
+  i64 lda, row_begin;
+  int m, n, tri, pad;
+  double alpha, beta;
+  const int* skip;
+};
+void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st);
+
 // y(i) = alpha * sum_{j in tri range} A(i,j) x(j) + beta y(i); A row-major lda.
 // tri: 0 full, 1 lower (j <= i), 2 upper (j >= i).
 void launch_gemv64(int m, int n, const double* A, i64 lda, const double* x, double* y, double alpha,

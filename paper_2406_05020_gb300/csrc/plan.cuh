@@ -2,6 +2,8 @@
 // in device memory.  Plans are built once per problem (at create/assemble)
 // and replayed every CG iteration, so they can be captured in CUDA graphs.
 #pragma once
+#include <algorithm>
+#include <cstring>
 #include <functional>
 
 #include "kernels.cuh"
@@ -10,6 +12,7 @@ namespace gpfvm {
 
 struct PlanOp {
   enum Kind { GEMM, GEMV, GEMV32, FUNC } kind;
+  int phase = -1;  // ops sharing a phase id (>= 0, consecutive) are independent: merged launches
   GemmDesc g;
   int seg0 = 0, group0 = 0;
   // GEMV
@@ -22,6 +25,15 @@ struct PlanOp {
   std::function<void(cudaStream_t)> fn;
 };
 
+// One merged launch of a phase: a table of GEMM ops (same element type and
+// row tile) or of GEMV ops (same element type).
+struct LaunchUnit {
+  int kind;  // 0 multi-GEMM, 1 multi-GEMV
+  int f32, bm, nops;
+  i64 total;
+  size_t offset;  // byte offset of the op table in the plan's table buffer
+};
+
 class Plan {
  public:
   std::vector<GemmSeg> segs;
@@ -29,14 +41,37 @@ class Plan {
   std::vector<PlanOp> ops;
   GemmSeg* d_segs = nullptr;
   GemmGroup* d_groups = nullptr;
+  char* d_tables = nullptr;
+  std::vector<std::vector<LaunchUnit>> phase_units;  // indexed by phase id
+  int n_phases = 0;
   const int* skip = nullptr;  // device flag: when set, every GEMM/GEMV of the plan is a no-op
 
   ~Plan() { release(); }
   void release() {
     if (d_segs) cudaFree(d_segs);
     if (d_groups) cudaFree(d_groups);
+    if (d_tables) cudaFree(d_tables);
     d_segs = nullptr;
     d_groups = nullptr;
+    d_tables = nullptr;
+  }
+  Plan() = default;
+  Plan(const Plan&) = delete;
+  Plan& operator=(const Plan&) = delete;
+  Plan(Plan&& o) noexcept { *this = std::move(o); }
+  Plan& operator=(Plan&& o) noexcept {
+    if (this != &o) {
+      release();
+      segs = std::move(o.segs);
+      groups = std::move(o.groups);
+      ops = std::move(o.ops);
+      phase_units = std::move(o.phase_units);
+      n_phases = o.n_phases;
+      skip = o.skip;
+      d_segs = o.d_segs; d_groups = o.d_groups; d_tables = o.d_tables;
+      o.d_segs = nullptr; o.d_groups = nullptr; o.d_tables = nullptr;
+    }
+    return *this;
   }
   // Adds a GEMM; `gs` lists the groups, each with its segments.
   void gemm(GemmDesc g, const std::vector<std::pair<GemmGroup, std::vector<GemmSeg>>>& gs) {
@@ -80,10 +115,88 @@ class Plan {
     const int s0 = (int)segs.size(), g0 = (int)groups.size();
     for (auto s : o.segs) segs.push_back(s);
     for (auto G : o.groups) { G.seg0 += s0; groups.push_back(G); }
-    for (auto op : o.ops) { op.group0 += g0; ops.push_back(op); }
+    for (auto op : o.ops) { op.group0 += g0; op.phase = -1; ops.push_back(op); }
+  }
+  // Appends independent chains level by level: op l of every chain shares one
+  // phase (they read only what earlier levels or earlier plan ops wrote).
+  void zip(const std::vector<const Plan*>& chains, size_t max_levels = (size_t)-1) {
+    const int s0 = (int)segs.size(), g0 = (int)groups.size();
+    std::vector<int> sbase, gbase;
+    int so = s0, go = g0;
+    for (const Plan* c : chains) {
+      sbase.push_back(so);
+      gbase.push_back(go);
+      for (auto x : c->segs) segs.push_back(x);
+      for (auto G : c->groups) { G.seg0 += so - s0 + s0; groups.push_back(G); }
+      so += (int)c->segs.size();
+      go += (int)c->groups.size();
+    }
+    // fix the group seg0 offsets (each chain's groups index its own segs)
+    {
+      int gi = g0;
+      for (size_t c = 0; c < chains.size(); ++c)
+        for (size_t k = 0; k < chains[c]->groups.size(); ++k, ++gi)
+          groups[gi].seg0 = chains[c]->groups[k].seg0 + sbase[c];
+    }
+    size_t maxlen = 0;
+    for (const Plan* c : chains) maxlen = std::max(maxlen, c->ops.size());
+    const size_t zl = std::min(maxlen, max_levels);
+    for (size_t l = 0; l < zl; ++l) {
+      const int ph = n_phases++;
+      for (size_t c = 0; c < chains.size(); ++c) {
+        if (l >= chains[c]->ops.size()) continue;
+        PlanOp op = chains[c]->ops[l];
+        op.group0 += gbase[c];
+        op.phase = ph;
+        ops.push_back(op);
+      }
+    }
+    // levels beyond max_levels: one phase per level and chain pair (a, b) of
+    // `pairs`, i.e. chains that write the same output never share a phase
+    for (size_t c = 0; c < chains.size(); ++c)
+      for (size_t l = zl; l < chains[c]->ops.size(); ++l) {
+        PlanOp op = chains[c]->ops[l];
+        op.group0 += gbase[c];
+        op.phase = -1;
+        ops.push_back(op);
+      }
+  }
+  // Copy of ops [from, to) with the argument tables they use.
+  Plan slice(size_t from, size_t to) const {
+    Plan r;
+    to = std::min(to, ops.size());
+    for (size_t i = from; i < to; ++i) {
+      PlanOp op = ops[i];
+      op.phase = -1;
+      if (op.kind == PlanOp::GEMM) {
+        const int g0 = (int)r.groups.size();
+        for (int k = 0; k < op.g.n_groups; ++k) {
+          GemmGroup G = groups[op.group0 + k];
+          const int s0 = (int)r.segs.size();
+          for (int j = 0; j < G.nseg; ++j) r.segs.push_back(segs[G.seg0 + j]);
+          G.seg0 = s0;
+          r.groups.push_back(G);
+        }
+        op.group0 = g0;
+      }
+      r.ops.push_back(op);
+    }
+    return r;
+  }
+  // Like zip, but chain i of `a` and chain i of `b` (different outputs) share
+  // one phase per level; used for the conflicting last levels.
+  void zip_pairs(const std::vector<const Plan*>& a, const std::vector<const Plan*>& b) {
+    const size_t n = std::max(a.size(), b.size());
+    for (size_t i = 0; i < n; ++i) {
+      std::vector<const Plan*> c;
+      if (i < a.size()) c.push_back(a[i]);
+      if (i < b.size()) c.push_back(b[i]);
+      zip(c);
+    }
   }
   void finalize() {
     release();
+    phase_units.assign(n_phases, {});
     if (!segs.empty()) {
       GPFVM_CUDA(cudaMalloc(&d_segs, segs.size() * sizeof(GemmSeg)));
       GPFVM_CUDA(cudaMemcpy(d_segs, segs.data(), segs.size() * sizeof(GemmSeg), cudaMemcpyHostToDevice));
@@ -99,9 +212,75 @@ class Plan {
         op.g.groups = d_groups + op.group0;
         op.g.skip = skip;
       }
+    // merged launch tables for phased ops
+    std::vector<char> blob;
+    auto put = [&](const void* p, size_t n) {
+      size_t off = (blob.size() + 255) / 256 * 256;
+      blob.resize(off + n);
+      std::memcpy(blob.data() + off, p, n);
+      return off;
+    };
+    for (int ph = 0; ph < n_phases; ++ph) {
+      for (int f32 = 0; f32 < 2; ++f32) {
+        for (int tile = 0; tile < 3; ++tile) {
+          std::vector<MOp> mops;
+          i64 total = 0;
+          for (auto& op : ops) {
+            if (op.phase != ph || op.kind != PlanOp::GEMM || op.g.f32 != f32 || op.g.tile != tile) continue;
+            const int bm = tile == 2 ? 16 : (tile == 1 ? 32 : 64);
+            MOp m{};
+            m.g = op.g;
+            m.tiles_x = (op.g.n + 63) / 64;
+            m.tiles_y = (op.g.m + bm - 1) / bm;
+            m.tile_begin = total;
+            total += (i64)m.tiles_x * m.tiles_y * op.g.batch * op.g.n_groups;
+            mops.push_back(m);
+          }
+          if (mops.empty()) continue;
+          LaunchUnit u{0, f32, tile == 2 ? 16 : (tile == 1 ? 32 : 64), (int)mops.size(), total, 0};
+          u.offset = put(mops.data(), mops.size() * sizeof(MOp));
+          phase_units[ph].push_back(u);
+        }
+        std::vector<MGemv> gops;
+        i64 rows = 0;
+        for (auto& op : ops) {
+          const bool is32 = op.kind == PlanOp::GEMV32;
+          if (op.phase != ph || !(op.kind == PlanOp::GEMV || is32) || (int)is32 != f32) continue;
+          MGemv m{};
+          m.A = op.A; m.x = op.x; m.z = op.y; m.y = op.y;
+          m.lda = op.lda; m.row_begin = rows; m.m = op.m; m.n = op.n; m.tri = op.tri;
+          m.alpha = op.alpha; m.beta = op.beta; m.skip = skip;
+          rows += op.m;
+          gops.push_back(m);
+        }
+        if (!gops.empty()) {
+          LaunchUnit u{1, f32, 0, (int)gops.size(), rows, 0};
+          u.offset = put(gops.data(), gops.size() * sizeof(MGemv));
+          phase_units[ph].push_back(u);
+        }
+      }
+    }
+    if (!blob.empty()) {
+      GPFVM_CUDA(cudaMalloc(&d_tables, blob.size()));
+      GPFVM_CUDA(cudaMemcpy(d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    }
   }
   void run(cudaStream_t st) const {
+    int done_phase = -1;
     for (auto& op : ops) {
+      if (op.phase >= 0) {
+        if (op.phase == done_phase) {
+          if (op.kind == PlanOp::FUNC) op.fn(st);
+          continue;
+        }
+        done_phase = op.phase;
+        for (const LaunchUnit& u : phase_units[op.phase]) {
+          if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
+          else launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
+        }
+        if (op.kind == PlanOp::FUNC) op.fn(st);
+        continue;
+      }
       if (op.kind == PlanOp::GEMM) launch_gemm64(op.g, st);
       else if (op.kind == PlanOp::GEMV)
         launch_gemv64(op.m, op.n, op.A, op.lda, op.x, op.y, op.alpha, op.beta, op.tri, st, skip);
