@@ -223,6 +223,8 @@ def run_gpfvm(args):
                               check_every=32)
     opts_mx = gpfvm.solve_opts(max_iter=MAX_ITER_MIXED, rtol=RTOL, precision=gpfvm.MIXED_FP32, reorth=True,
                                want_var=True, check_every=32, inner_rtol=1e-2)
+    opts_tc = gpfvm.solve_opts(max_iter=MAX_ITER_MIXED, rtol=RTOL, precision=gpfvm.MIXED_TF32X3, reorth=True,
+                               want_var=True, check_every=32, inner_rtol=1e-2)
     s_ptr = stream.cuda_stream
 
     def step(i, opts):
@@ -266,12 +268,30 @@ def run_gpfvm(args):
     t64, it64, res64, ph64 = timed(opts64)
     launches64 = gpfvm.launch_count() - launches0
     launches0 = gpfvm.launch_count()
-    tmx, itmx, resmx, phmx = timed(opts_mx)
-    launches = gpfvm.launch_count() - launches0
+    tfp, itfp, resfp, phfp = timed(opts_mx)
+    launches_fp = gpfvm.launch_count() - launches0
+    launches0 = gpfvm.launch_count()
+    ttc, ittc, restc, phtc = timed(opts_tc)
+    launches_tc = gpfvm.launch_count() - launches0
     clk = clocks.stop()
-    err_mean = max(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]) for a, b in zip(resmx, res64))
-    err_var = max(float(np.max(np.abs(a[1] - b[1]))) / base.outputscale for a, b in zip(resmx, res64))
-    mixed_ok = err_mean <= ACCURACY_BAR
+
+    def errs(res):
+        em = max(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]) for a, b in zip(res, res64))
+        ev = max(float(np.max(np.abs(a[1] - b[1]))) / base.outputscale for a, b in zip(res, res64))
+        return em, ev
+    err_fp = errs(resfp)
+    err_tc = errs(restc)
+    # headline: the fastest mixed path whose mean is within 1e-6 of the FP64 path
+    cands = [(sum(tfp), "mixed_fp32", tfp, itfp, resfp, phfp, launches_fp, opts_mx, err_fp),
+             (sum(ttc), "mixed_tf32x3", ttc, ittc, restc, phtc, launches_tc, opts_tc, err_tc)]
+    cands = [c for c in cands if c[8][0] <= ACCURACY_BAR]
+    mixed_ok = bool(cands)
+    if mixed_ok:
+        best = min(cands, key=lambda c: c[0])
+        _, best_name, tmx, itmx, resmx, phmx, launches, opts_best, (err_mean, err_var) = best
+    else:
+        best_name, tmx, itmx, resmx, phmx, launches, opts_best = "fp64", t64, it64, res64, ph64, launches64, opts64
+        err_mean, err_var = 0.0, 0.0
     times = tmx if mixed_ok else t64
     total_ms = sum(times)
     if ws > 1:
@@ -285,7 +305,7 @@ def run_gpfvm(args):
     phases = phmx if mixed_ok else ph64
 
     # ---- end to end through the C ABI with host buffers
-    opts_e2e = opts_mx if mixed_ok else opts64
+    opts_e2e = opts_best
     mean_h = np.empty(P)
     var_h = np.empty(P)
     torch.cuda.synchronize()
@@ -338,7 +358,7 @@ def run_gpfvm(args):
             "vs_baseline": None, "dtype": "f32+f64" if mixed_ok else "f64", "data": "synthetic",
             "config": {"workload": "heat2d_64x64x64_M5120_P32768 (2D+time heat, 64^3 cells, IC 64x64, "
                                    "walls 4x16x16, grid 32^3)",
-                       "precision": "mixed_fp32 (FP32 inner CG, FP64 refinement)" if mixed_ok else "fp64",
+                       "precision": best_name,
                        "cg": {"rtol": RTOL, "reorth": "full", "iters_mean": statistics.mean(iters)},
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}"},
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * pb.M,
@@ -353,10 +373,16 @@ def run_gpfvm(args):
                 "fp64": {"solves_per_s": fp64_value, "ms_per_step": sum(t64) / args.steps,
                          "cg_iters_mean": statistics.mean(it64), "gpu_launches": int(launches64),
                          "phases_ms_last_step": list(ph64)},
-                "mixed_fp32": {"solves_per_s": ws * args.steps / (sum(tmx) / 1e3),
-                               "ms_per_step": sum(tmx) / args.steps, "inner_iters_mean": statistics.mean(itmx),
-                               "mean_rel_err_vs_fp64_max": err_mean, "var_abs_err_vs_fp64_max": err_var,
-                               "meets_1e-6": bool(mixed_ok), "phases_ms_last_step": list(phmx)},
+                "mixed_fp32": {"solves_per_s": ws * args.steps / (sum(tfp) / 1e3),
+                               "ms_per_step": sum(tfp) / args.steps, "inner_iters_mean": statistics.mean(itfp),
+                               "mean_rel_err_vs_fp64_max": err_fp[0], "var_abs_err_vs_fp64_max": err_fp[1],
+                               "meets_1e-6": bool(err_fp[0] <= ACCURACY_BAR), "phases_ms_last_step": list(phfp),
+                               "gpu_launches": int(launches_fp)},
+                "mixed_tf32x3": {"solves_per_s": ws * args.steps / (sum(ttc) / 1e3),
+                                 "ms_per_step": sum(ttc) / args.steps, "inner_iters_mean": statistics.mean(ittc),
+                                 "mean_rel_err_vs_fp64_max": err_tc[0], "var_abs_err_vs_fp64_max": err_tc[1],
+                                 "meets_1e-6": bool(err_tc[0] <= ACCURACY_BAR), "phases_ms_last_step": list(phtc),
+                                 "gpu_launches": int(launches_tc)},
             },
             "clocks": clk,
             "cpu_baseline": cpu,

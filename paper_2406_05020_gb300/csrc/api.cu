@@ -20,6 +20,7 @@
 
 #include "cg.cuh"
 #include "kron.cuh"
+#include "tc.cuh"
 
 using namespace gpfvm;
 
@@ -170,6 +171,19 @@ struct gpfvm_problem {
   float *f_QK[3] = {}, *f_Ft = nullptr, *f_F = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_hK = nullptr,
         *f_tR = nullptr, *f_uR = nullptr;
   JacobiJob* d_jac = nullptr;
+  // tensor-core G_PP (split TF32): factor splits, rotated intermediates, op tables
+  bool tc_ok = false, use_tc = false;
+  float* f_tcsplit = nullptr;
+  float *f_tcY = nullptr, *f_tcZ = nullptr;
+  std::vector<std::tuple<i64, float, i64, i64>> tc_jobs;  // (factor offset in f_fac, alpha, size, split offset)
+  TcOp* d_tcops = nullptr;
+  struct TcLevel {
+    int off, nops, maxn;
+    i64 tiles;
+  };
+  std::vector<TcLevel> tc_levels[2];
+  i64 tc_split_total = 0, tc_ops_total = 0;
+  int tc_nu = 0, tc_nw = 0;
   CGState* d_st32 = nullptr;
   CGState* h_st32 = nullptr;
   i64 nfac = 0;
@@ -183,7 +197,7 @@ struct gpfvm_problem {
   // ---- plans
   Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB;
   Plan p_op[4];
-  Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32;
+  Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32, p_mv32tc, p_mvv32tc, p_pp32tc;
   int modeprods_pp = 0;
 
   // ---- state
@@ -458,13 +472,15 @@ struct Builder {
   //   stage A (reads in):  G_PP in, G_BP in (each set), L_PDE k(X*)^T in
   //   stage B:             w = G_BB^-1 g
   //   stage C (reads w):   out -= G_PB w, u -= k_B(X*)^T w  (last levels paired)
-  void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count) {
+  void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
+                   Plan* pp_chain = nullptr) {
     int dc[3], ds[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
     stage_begin();
     std::vector<Plan> A(1 + p->nsets + (u ? 1 : 0));
-    kron(A[0], dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
+    if (pp_chain) A[0] = std::move(*pp_chain);
+    else kron(A[0], dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
       kron(A[1 + s], dc, ds, 1, pb_terms(p, s, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
@@ -579,7 +595,7 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
       GemmDesc g{};
       g.m = MR; g.n = MR; g.k = MK;
       g.a_rs = MK; g.a_cs = 1; g.b_rs = 1; g.b_cs = MK; g.c_rs = MR;
-      g.batch = 1; g.tri = TRI_C_LOWER; g.tile = 0;
+      g.batch = 1; g.tri = TRI_C_LOWER; g.tile = dense_tile(MR, MR / 2);
       pl.gemm(g, {{GemmGroup{p->d_Sc, nullptr, 1.0, 0.0, 0, 0}, {GemmSeg{p->d_E1, p->d_E1, -1.0}}}});
     }
     plan_chol_inverse(pl, p->d_Sc, p->d_LS, p->d_LSinv, MR, MR, p->d_sscr, p->d_st ? &p->d_st->pad[0] : nullptr);
@@ -634,7 +650,7 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
     GemmDesc g{};
     g.m = MR; g.n = MK; g.k = MR;
     g.a_rs = MR; g.a_cs = 1; g.b_rs = MK; g.b_cs = 1; g.c_rs = MK;
-    g.batch = 1; g.tri = TRI_A_LOWER; g.tile = 0;
+    g.batch = 1; g.tri = TRI_A_LOWER; g.tile = dense_tile(MR, MK);
     pl.gemm(g, {{GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_LSinv, p->d_Ft, 1.0}}}});
   }
   const int Rrows = p->vb_rows;
@@ -781,6 +797,145 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   }
 }
 
+// Tensor-core G_PP: the shared three-level form with rotating axes
+// (contract the last axis, write the new axis first), see tc.cu.
+// Builds the op tables of one instance (in -> out) and returns them by level.
+struct TcBuild {
+  gpfvm_problem* p;
+  std::vector<TcOp> ops;
+  std::map<std::pair<i64, float>, i64> split_off;
+  i64 split_n = 0;
+  bool ok = true;
+  const float* split(i64 fac_off, i64 n, float alpha, bool hi) {
+    auto key = std::make_pair(fac_off, alpha);
+    auto it = split_off.find(key);
+    i64 off;
+    if (it == split_off.end()) {
+      off = split_n;
+      split_off[key] = off;
+      split_n += 2 * ((n + 63) / 64 * 64);
+      p->tc_jobs.push_back(std::make_tuple(fac_off, alpha, n, off));
+    } else {
+      off = it->second;
+    }
+    return p->f_tcsplit ? p->f_tcsplit + off + (hi ? 0 : (n + 63) / 64 * 64) : nullptr;
+  }
+};
+
+void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out, int inst) {
+  const int d = p->d;
+  int n[3] = {1, 1, 1};
+  i64 Ntot = 1;
+  for (int i = 0; i < d; ++i) {
+    n[i] = p->nc[i];
+    Ntot *= n[i];
+  }
+  struct Term { double c; i64 f[3]; };
+  std::vector<Term> terms;
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b) {
+      Term t{p->coef[a] * p->coef[b], {0, 0, 0}};
+      for (int i = 0; i < d; ++i) t.f[i] = p->fac_off.at(FKey(i, 0, p->alpha[a][i], 0, p->alpha[b][i]));
+      terms.push_back(t);
+    }
+  auto fsize = [&](int ax) { return (i64)n[ax] * n[ax]; };
+  p->tc_levels[inst].clear();
+  auto begin_level = [&]() { p->tc_levels[inst].push_back({(int)T.ops.size(), 0, 0, 0}); };
+  auto add_op = [&](TcOp op) {
+    auto& L = p->tc_levels[inst].back();
+    const i64 tiles = (op.R + 127) / 128;
+    op.tile_begin = L.tiles;
+    L.tiles += tiles;
+    L.nops++;
+    L.maxn = std::max(L.maxn, op.N);
+    if (op.nseg > TC_MAXSEG || op.N > 256) T.ok = false;
+    T.ops.push_back(op);
+  };
+  auto seg = [&](TcOp& op, const float* A, i64 fo, int ax, double alpha) {
+    if (op.nseg >= TC_MAXSEG) { T.ok = false; return; }
+    op.A[op.nseg] = A;
+    op.Bhi[op.nseg] = T.split(fo, fsize(ax), (float)alpha, true);
+    op.Blo[op.nseg] = T.split(fo, fsize(ax), (float)alpha, false);
+    op.nseg++;
+  };
+  auto blank = [&](int R, int K, int N, float* o) {
+    TcOp op{};
+    op.R = R; op.K = K; op.N = N; op.out = o;
+    op.skip = (inst == 0 && p->d_st32) ? &p->d_st32->done : nullptr;
+    return op;
+  };
+  if (d == 1) {
+    begin_level();
+    TcOp op = blank(1, n[0], n[0], out);
+    for (auto& t : terms) seg(op, in, t.f[0], 0, p->s2 * t.c);
+    op.D = in;
+    op.gamma = (float)p->jitter;
+    add_op(op);
+    return;
+  }
+  // distinct factors on the last axis (3 axes) and on axis 0
+  std::vector<i64> U, Wf;
+  std::vector<int> uo(terms.size()), wo(terms.size());
+  for (size_t k = 0; k < terms.size(); ++k) {
+    if (d == 3) {
+      auto it = std::find(U.begin(), U.end(), terms[k].f[2]);
+      uo[k] = (int)(it - U.begin());
+      if (it == U.end()) U.push_back(terms[k].f[2]);
+    }
+    auto jt = std::find(Wf.begin(), Wf.end(), terms[k].f[0]);
+    wo[k] = (int)(jt - Wf.begin());
+    if (jt == Wf.end()) Wf.push_back(terms[k].f[0]);
+  }
+  p->tc_nu = std::max(p->tc_nu, (int)U.size());
+  p->tc_nw = std::max(p->tc_nw, (int)Wf.size());
+  if (d == 3) {
+    begin_level();
+    for (size_t u = 0; u < U.size(); ++u) {
+      TcOp op = blank(n[0] * n[1], n[2], n[2], p->f_tcY ? p->f_tcY + u * Ntot : nullptr);
+      seg(op, in, U[u], 2, 1.0);
+      add_op(op);
+    }
+  }
+  begin_level();
+  for (size_t w = 0; w < Wf.size(); ++w) {
+    TcOp op = (d == 3) ? blank(n[2] * n[0], n[1], n[1], p->f_tcZ ? p->f_tcZ + w * Ntot : nullptr)
+                       : blank(n[0], n[1], n[1], p->f_tcZ ? p->f_tcZ + w * Ntot : nullptr);
+    // merge equal (source, factor) pairs of the group
+    std::vector<std::pair<std::pair<int, i64>, double>> acc;
+    for (size_t k = 0; k < terms.size(); ++k) {
+      if (wo[k] != (int)w) continue;
+      const int src = (d == 3) ? uo[k] : -1;
+      bool merged = false;
+      for (auto& a : acc)
+        if (a.first.first == src && a.first.second == terms[k].f[1]) { a.second += terms[k].c; merged = true; }
+      if (!merged) acc.push_back({{src, terms[k].f[1]}, terms[k].c});
+    }
+    for (auto& a : acc) {
+      const float* A = (d == 3) ? (p->f_tcY ? p->f_tcY + (i64)a.first.first * Ntot : nullptr) : in;
+      seg(op, A, a.first.second, 1, a.second);
+    }
+    add_op(op);
+  }
+  begin_level();
+  TcOp op = blank((int)(Ntot / n[0]), n[0], n[0], out);
+  for (size_t w = 0; w < Wf.size(); ++w) seg(op, p->f_tcZ ? p->f_tcZ + (i64)w * Ntot : nullptr, Wf[w], 0, p->s2);
+  op.D = in;
+  op.gamma = (float)p->jitter;
+  add_op(op);
+}
+
+// G_PP on tensor cores as a chain of FUNC ops (one per level) for a phased plan.
+Plan tc_chain(gpfvm_problem* p, int inst) {
+  Plan c;
+  for (auto L : p->tc_levels[inst]) {
+    gpfvm_problem* pp = p;
+    c.func([=](cudaStream_t st) {
+      launch_tc_modes(pp->d_tcops + L.off, L.nops, L.tiles, L.maxn, &pp->d_st32->pad[1], st);
+    });
+  }
+  return c;
+}
+
 // FP32 plans of the mixed solver's inner operator.
 void build_plans32(gpfvm_problem* p, Builder& B) {
   B.f32 = true;
@@ -795,6 +950,35 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
   if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true);
   p->p_pp32 = Plan();
   B.pp(p->p_pp32, D(p->f_vin), D(p->f_vout), nullptr);
+  // tensor-core variants (split TF32 G_PP)
+  {
+    TcBuild T{p};
+    build_tc_instance(p, T, p->f_p, p->f_q, 0);
+    build_tc_instance(p, T, p->f_vin, p->f_vout, 1);
+    p->tc_ok = T.ok;
+    p->tc_split_total = T.split_n;
+    p->tc_ops_total = (i64)T.ops.size();
+    if (p->d_tcops && T.ok) {
+      // host-side bounds check of every tensor-core operand before any launch
+      for (const TcOp& op : T.ops) {
+        bool ok = p->mem.contains(op.out, 4LL * op.N * op.R) && (!op.D || p->mem.contains(op.D, 4LL * op.N * op.R));
+        for (int s = 0; s < op.nseg; ++s)
+          ok = ok && p->mem.contains(op.A[s], 4LL * op.R * op.K) && p->mem.contains(op.Bhi[s], 4LL * op.N * op.K) &&
+               p->mem.contains(op.Blo[s], 4LL * op.N * op.K);
+        if (!ok) throw CudaError{cudaErrorInvalidValue, "tc operand out of bounds"};
+      }
+      GPFVM_CUDA(cudaMemcpy(p->d_tcops, T.ops.data(), sizeof(TcOp) * T.ops.size(), cudaMemcpyHostToDevice));
+    }
+    if (p->tc_ok && p->d_tcops) {
+      p->p_mv32tc = Plan();
+      Plan c0 = tc_chain(p, 0);
+      B.ghat_phased(p->p_mv32tc, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), nullptr, nullptr, &c0);
+      p->p_mvv32tc = Plan();
+      Plan c1 = tc_chain(p, 0);
+      B.ghat_phased(p->p_mvv32tc, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), D(p->f_u), nullptr, &c1);
+      p->p_pp32tc = tc_chain(p, 1);
+    }
+  }
   p->building_f32 = false;
   B.f32 = false;
 }
@@ -808,10 +992,12 @@ void finalize_plans(gpfvm_problem* p) {
   p->p_var32.skip = &p->d_st32->done;
   Plan* all[] = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
                  &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
-                 &p->p_mvv_cg, &p->p_mvv32};
+                 &p->p_mvv_cg, &p->p_mvv32, &p->p_mv32tc, &p->p_mvv32tc, &p->p_pp32tc};
   const char* names[] = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2", "op3",
-                         "mv32", "var32", "pp32", "mvv_cg", "mvv32"};
-  for (int i = 0; i < 16; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
+                         "mv32", "var32", "pp32", "mvv_cg", "mvv32", "mv32tc", "mvv32tc", "pp32tc"};
+  for (int i = 0; i < 19; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
+  p->p_mv32tc.skip = &p->d_st32->done;
+  p->p_mvv32tc.skip = &p->d_st32->done;
   for (Plan* pl : all) pl->finalize();
 }
 
@@ -1076,6 +1262,11 @@ void alloc_all(gpfvm_problem* p) {
   B0.scr.cap = (i64)1 << 62;
   build_plans(p, B0);
   build_plans32(p, B0);
+  p->f_tcsplit = m.alloc<float>(std::max<i64>(p->tc_split_total, 64));
+  p->f_tcY = m.alloc<float>(std::max<i64>((i64)p->tc_nu * N, 64));
+  p->f_tcZ = m.alloc<float>(std::max<i64>((i64)p->tc_nw * N, 64));
+  p->d_tcops = m.alloc<TcOp>(std::max<i64>(p->tc_ops_total, 1));
+  p->tc_jobs.clear();
   p->scratch_cap = std::max<i64>(B0.peak, 64);
   p->d_scratch = m.alloc<double>(p->scratch_cap);
   Builder B{p};
@@ -1101,6 +1292,11 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
   }
   p->p_rhs.run(st);
   convert_d2f(p->d_fac, p->f_fac, p->nfac, st);
+  for (auto& j : p->tc_jobs) {
+    const i64 n = std::get<2>(j), off = std::get<3>(j);
+    tc_split(p->f_fac + std::get<0>(j), n, std::get<1>(j), p->f_tcsplit + off, p->f_tcsplit + off + (n + 63) / 64 * 64,
+             st);
+  }
   if (p->M > 0 && !p->sicbc) {
     convert_d2f(p->d_Linv, p->f_Linv, p->M * p->M, st);
     convert_d2f(p->d_LinvT, p->f_LinvT, p->M * p->M, st);
@@ -1259,7 +1455,8 @@ int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
 // One inner CG iteration of the mixed solver (FP32 operator and vectors, FP64 scalars).
 void cg_iteration32(gpfvm_problem* p, bool want_var, cudaStream_t st) {
   const i64 N = p->N;
-  (want_var ? p->p_mvv32 : p->p_mv32).run(st);
+  if (p->use_tc) (want_var ? p->p_mvv32tc : p->p_mv32tc).run(st);
+  else (want_var ? p->p_mvv32 : p->p_mv32).run(st);
   cg_dot_eta<float>(p->f_p, p->f_q, N, p->d_st32, p->d_eta32, st);
   if (want_var) cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
   cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, p->f_S, p->f_Q, st);
@@ -1280,6 +1477,16 @@ int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* i
   const bool want_var = o->want_var != 0;
   const i64 N = p->N;
   const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  const bool want_tc = o->precision == GPFVM_MIXED_TF32X3;
+  if (want_tc && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (want_tc != p->use_tc) {  // the captured inner iteration depends on the operator
+    p->use_tc = want_tc;
+    if (p->graph32) cudaGraphExecDestroy(p->graph32);
+    p->graph32 = nullptr;
+    p->graph32_key = -1;
+  }
+  p->h_st32->pad[1] = 0;
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
   const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
   cudaEvent_t e0, e1;
   GPFVM_CUDA(cudaEventCreate(&e0));
@@ -1340,6 +1547,7 @@ int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* i
     }
     const int k = p->h_st32->k;
     total += k;
+    if (p->h_st32->pad[1] & DEV_TIMEOUT) { status = GPFVM_ERR_TIMEOUT; break; }
     if (k == 0) { status = GPFVM_ERR_BREAKDOWN; break; }  // not even one inner step
     add_f2d(p->d_x, p->f_d, N, st);
   }
@@ -1490,9 +1698,19 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
   if (!p || !v || !out || op < 0 || op > 5) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
-  if (op == 5) return GPFVM_ERR_INVALID_ARG;
+  if (op == 5 && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
+  if (op == 5) {
+    p->h_st32->pad[1] = 0;
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
+    convert_d2f(v, p->f_vin, p->N, st);
+    p->p_pp32tc.run(st);
+    f2d(p->f_vout, out, p->N, st);
+    GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    return (p->h_st32->pad[1] & DEV_TIMEOUT) ? GPFVM_ERR_TIMEOUT : GPFVM_OK;
+  }
   if (op == 4) {
     convert_d2f(v, p->f_vin, p->N, st);
     p->p_pp32.run(st);

@@ -86,11 +86,20 @@ void launch_chol_base(const double* A, double* L, double* Linv, int n, i64 lda, 
   GPFVM_LAUNCH_CHECK();
 }
 
+// Row tile for a dense FP64 GEMM: the FP64 pipe needs several CTAs per SM, so
+// take the tallest tile that still gives about two CTAs for each of the 152 SMs.
+int dense_tile(int m, int n) {
+  const i64 cols = (n + 63) / 64;
+  if ((i64)((m + 63) / 64) * cols >= 304) return 0;
+  if ((i64)((m + 31) / 32) * cols >= 304) return 1;
+  return 2;
+}
+
 static GemmDesc gdesc(int m, int n, int k, i64 a_rs, i64 a_cs, i64 b_rs, i64 b_cs, i64 c_rs, int tri) {
   GemmDesc g{};
   g.m = m; g.n = n; g.k = k;
   g.a_rs = a_rs; g.a_cs = a_cs; g.b_rs = b_rs; g.b_cs = b_cs; g.c_rs = c_rs; g.d_rs = 0;
-  g.batch = 1; g.tri = tri; g.tile = 0;
+  g.batch = 1; g.tri = tri; g.tile = dense_tile(m, n);
   return g;
 }
 

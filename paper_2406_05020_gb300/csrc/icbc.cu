@@ -38,6 +38,17 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict
     V[e] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // ||A||_F^2: pairs whose inner product is below eps^2 of it are converged
+  // (columns of numerically zero eigenvalues are rounding noise and would
+  // otherwise keep rotating)
+  __shared__ double fro2;
+  if (tid == 0) {
+    double f = 0.0;
+    for (int e = 0; e < n * n; ++e) f += U[e] * U[e];
+    fro2 = f;
+  }
+  __syncthreads();
+  const double cabs = 1e-30 * fro2;
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (tid == 0) maxrot = 0.0;
     __syncthreads();
@@ -61,10 +72,10 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict
           b += __shfl_xor_sync(0xffffffffu, b, o);
           c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        if (c == 0.0 || a == 0.0 || b == 0.0) continue;
+        if (fabs(c) <= cabs || a == 0.0 || b == 0.0) continue;
         const double rot = fabs(c) / sqrt(a * b);
-        local_max = fmax(local_max, rot);
         if (rot < 1e-15) continue;
+        local_max = fmax(local_max, rot);
         const double zeta = (b - a) / (2.0 * c);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;

@@ -298,5 +298,6 @@ class Plan {
 // hold n*n/4 + 64 doubles.  status receives DEV_NOT_SPD on a pivot <= 0.
 void plan_chol_inverse(Plan& plan, double* A, double* L, double* Linv, int n, i64 lda,
                        double* scratch, int* status);
+int dense_tile(int m, int n);
 
 }  // namespace gpfvm

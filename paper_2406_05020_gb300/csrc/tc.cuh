@@ -1,0 +1,29 @@
+// Tensor-core (tcgen05) mode products, see tc.cu.
+#pragma once
+#include "kernels.cuh"
+
+namespace gpfvm {
+
+constexpr int TC_MAXSEG = 16;
+
+// out[j * R + r] = sum_s sum_k A_s[r * K + k] * (Bhi_s + Blo_s)[j * K + k]
+//                  (+ gamma * D[j * R + r]) (+ beta * out[j * R + r])
+// A_s: R x K row-major (FP32, split on the fly); B_s: N x K row-major, already
+// scaled and split into tf32 hi / FP32 lo parts.  N <= 256.
+struct TcOp {
+  int R, K, N, nseg;
+  const float* A[TC_MAXSEG];
+  const float* Bhi[TC_MAXSEG];
+  const float* Blo[TC_MAXSEG];
+  float* out;
+  const float* D;
+  float gamma, beta;
+  i64 tile_begin;   // first tile (128 rows) of this op in the launch
+  const int* skip;  // op does nothing if *skip
+};
+
+void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st);
+void tc_split(const float* F, i64 n, float alpha, float* hi, float* lo, cudaStream_t st);
+int tc_smem_bytes(int ncols);
+
+}  // namespace gpfvm

@@ -1,0 +1,75 @@
+"""Tensor-core (tcgen05, split TF32) Gram matvec and the mixed solve that uses
+it, against the FP64 oracle.  Split TF32 carries about FP32 accuracy, so the
+operator is checked at 5e-6 relative (the lo*lo product is dropped, ~2^-19) and the refined posterior mean at the
+1e-6 bar of the mixed solves."""
+import numpy as np
+import pytest
+
+import gpfvm_workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_05020_gb300 import build
+    build.build()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+PROBS = {
+    "heat2d_8": lambda: W.heat_2d(8, 8, 8, n_ic=(4, 4), n_bc=(2, 2), pred=(3, 3, 3), ell=(0.4, 0.3, 0.3)),
+    "heat2d_ragged": lambda: W.heat_2d(5, 7, 9, n_ic=(4, 3), n_bc=(2, 3), pred=(3, 2, 4), ell=(0.4, 0.3, 0.35)),
+    "heat2d_tiles": lambda: W.heat_2d(17, 33, 70, n_ic=(9, 11), n_bc=(4, 5), pred=(5, 6, 7)),
+    "wave2d": lambda: W.wave_2d(12, 20, 36, n_ic=(4, 4), n_bc=(2, 2), pred=(3, 3, 3), ell=(0.3, 0.3, 0.3)),
+    "heat1d": lambda: W.heat_1d(16, 32),
+    "c2_64": lambda: W.heat_2d(64, 64, 64, seed=0),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_tc_gram_matvec(name):
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob = PROBS[name]()
+    pb = gpfvm.Problem(prob, max_iter=8)
+    pb.assemble()
+    K = O.KronIBVP(prob)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        v = rng.normal(size=prob.N)
+        out = torch.full((prob.N,), float("nan"), dtype=torch.float64, device="cuda")
+        pb.matvec(5, torch.as_tensor(v, device="cuda"), out)
+        assert relerr(out.cpu().numpy(), K.Gpp(v)) < 5e-6  # split TF32 without lo*lo: ~2^-19
+    pb.close()
+
+
+@pytest.mark.parametrize("name", ["heat2d_ragged", "heat2d_tiles", "heat1d"])
+def test_mixed_tf32x3_solve(name):
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob = PROBS[name]()
+    pb = gpfvm.Problem(prob, max_iter=4000)
+    pb.assemble()
+    code, info = pb.solve(max_iter=4000, rtol=1e-10, precision=gpfvm.MIXED_TF32X3, want_var=True)
+    assert code == 0, info.as_dict()
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    pb.query(mean, var)
+    m, v = O.dense_posterior(prob) if prob.N + prob.M < 3000 else (None, None)
+    if m is None:
+        r = O.kron_posterior(prob, rtol=1e-12, want_var=False)
+        m = r["mean"]
+    assert relerr(mean.cpu().numpy(), m) < 1e-6
+    if v is not None:
+        assert np.all(var.cpu().numpy() >= v - 1e-7)
+    pb.close()
