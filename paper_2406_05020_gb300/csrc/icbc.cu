@@ -18,39 +18,24 @@ namespace gpfvm {
 constexpr int JAC_MAX_N = 96;
 
 // One-sided (Hestenes) Jacobi on a symmetric positive semidefinite n x n
-// matrix: rotate column pairs of U = A until they are orthogonal; then
-// U = Q diag(lam) with Q = V, lam_j = ||U_j||.  Pairs follow the round-robin
-// (circle) schedule, so the n/2 rotations of a round touch disjoint columns.
-// The sweep count is bounded; convergence (largest |cos| between a rotated
-// column pair below tol) or the bound ends the loop.
-__global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict__ jobs) {
-  extern __shared__ double sm[];
-  const JacobiJob J = jobs[blockIdx.x];
-  const int n = J.n;
-  const int np = (n + 1) & ~1;  // even number of players (one dummy if n is odd)
-  double* U = sm;               // column-major: U[j * n + i]
-  double* V = sm + n * n;
-  __shared__ double maxrot;
+// matrix: rotate column pairs of U = A V until they are orthogonal; then
+// A V = U = Q diag(lam) with Q = V, lam_j = ||U_j||.  Pairs follow the
+// round-robin (circle) schedule, so the n/2 rotations of a round touch
+// disjoint columns (one warp per pair).  The bulk of the sweeps runs in FP32
+// (the FP64 pipe of one SM is slow); V is then re-orthonormalised in FP64
+// (modified Gram-Schmidt), U = A V is recomputed in FP64 and FP64 sweeps
+// polish to the rounding level.  A pair counts as converged when its cosine
+// is below 1e-15 or its inner product is at the rounding level of the largest
+// column, |c| <= 4e-16 ||A||_F (|u_p| + |u_q|): columns of tiny eigenvalues
+// carry rounding noise of that size and would otherwise keep rotating.
+// Sweeps are bounded in both phases.
+template <typename T>
+__device__ void jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, double tol_abs, int max_sweeps,
+                              double* maxrot) {
+  const int np = (n + 1) & ~1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    U[e] = 0.5 * (J.A[(i64)i * n + j] + J.A[(i64)j * n + i]);
-    V[e] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  // ||A||_F^2: pairs whose inner product is below eps^2 of it are converged
-  // (columns of numerically zero eigenvalues are rounding noise and would
-  // otherwise keep rotating)
-  __shared__ double fro2;
-  if (tid == 0) {
-    double f = 0.0;
-    for (int e = 0; e < n * n; ++e) f += U[e] * U[e];
-    fro2 = f;
-  }
-  __syncthreads();
-  const double cabs = 1e-30 * fro2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) maxrot = 0.0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *maxrot = 0.0;
     __syncthreads();
     double local_max = 0.0;
     for (int r = 0; r < np - 1; ++r) {
@@ -59,9 +44,9 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict
         if (k == 0) { p = r; q = np - 1; }
         else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
         if (p >= n || q >= n) continue;
-        double a = 0.0, b = 0.0, c = 0.0;
+        T a = 0, b = 0, c = 0;
         for (int i = lane; i < n; i += 32) {
-          const double up = U[p * n + i], uq = U[q * n + i];
+          const T up = U[p * n + i], uq = U[q * n + i];
           a += up * up;
           b += uq * uq;
           c += up * uq;
@@ -72,33 +57,93 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict
           b += __shfl_xor_sync(0xffffffffu, b, o);
           c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        if (fabs(c) <= cabs || a == 0.0 || b == 0.0) continue;
-        const double rot = fabs(c) / sqrt(a * b);
-        if (rot < 1e-15) continue;
-        local_max = fmax(local_max, rot);
-        const double zeta = (b - a) / (2.0 * c);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        if (a == T(0) || b == T(0) || fabs((double)c) <= tol_abs * fro * (sqrt((double)a) + sqrt((double)b)))
+          continue;
+        const T rot = fabs(c) / sqrt(a * b);
+        if ((double)rot < tol_rot) continue;
+        local_max = fmax(local_max, (double)rot);
+        const T zeta = (b - a) / (T(2) * c);
+        const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
         for (int i = lane; i < n; i += 32) {
-          const double up = U[p * n + i], uq = U[q * n + i];
+          const T up = U[p * n + i], uq = U[q * n + i];
           U[p * n + i] = cs * up - sn * uq;
           U[q * n + i] = sn * up + cs * uq;
-          const double vp = V[p * n + i], vq = V[q * n + i];
+          const T vp = V[p * n + i], vq = V[q * n + i];
           V[p * n + i] = cs * vp - sn * vq;
           V[q * n + i] = sn * vp + cs * vq;
         }
       }
       __syncthreads();
     }
-    if (lane == 0) {
-      // fold the warps' maxima (benign: max of non-negative doubles via integer compare)
-      atomicMax((unsigned long long*)&maxrot, __double_as_longlong(local_max));
-    }
+    if (lane == 0) atomicMax((unsigned long long*)maxrot, __double_as_longlong(local_max));
     __syncthreads();
-    const bool done = maxrot < J.tol;
+    const bool done = *maxrot < tol_rot * 10.0;
     __syncthreads();
     if (done) break;
   }
+}
+
+__global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restrict__ jobs) {
+  extern __shared__ double sm[];
+  const JacobiJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  double* U = sm;  // FP64 column-major U[j * n + i]
+  double* V = sm + n * n;
+  float* Uf = (float*)(sm + 2 * n * n);
+  float* Vf = Uf + n * n;
+  __shared__ double maxrot, fro2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    const double a = 0.5 * (J.A[(i64)i * n + j] + J.A[(i64)j * n + i]);
+    U[e] = a;
+    Uf[e] = (float)a;
+    Vf[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int e = 0; e < n * n; ++e) f += U[e] * U[e];
+    fro2 = f;
+  }
+  __syncthreads();
+  const double fro = sqrt(fro2);
+  // phase 1: FP32 sweeps to about single precision
+  jacobi_sweeps<float>(Uf, Vf, n, fro, 1e-6, 4e-8, 30, &maxrot);
+  // re-orthonormalise V in FP64 (modified Gram-Schmidt over its columns)
+  for (int e = tid; e < n * n; e += blockDim.x) V[e] = (double)Vf[e];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    // normalise column j (warp 0), then remove it from the later columns (all warps)
+    if (warp == 0) {
+      double s = 0.0;
+      for (int i = lane; i < n; i += 32) s += V[j * n + i] * V[j * n + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const double inv = 1.0 / sqrt(s);
+      for (int i = lane; i < n; i += 32) V[j * n + i] *= inv;
+    }
+    __syncthreads();
+    for (int k = j + 1 + warp; k < n; k += nw) {
+      double s = 0.0;
+      for (int i = lane; i < n; i += 32) s += V[j * n + i] * V[k * n + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      for (int i = lane; i < n; i += 32) V[k * n + i] -= s * V[j * n + i];
+    }
+    __syncthreads();
+  }
+  // U = A V in FP64 (A row-major, symmetric)
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += 0.5 * (J.A[(i64)i * n + l] + J.A[(i64)l * n + i]) * V[j * n + l];
+    U[e] = s;
+  }
+  __syncthreads();
+  // phase 2: FP64 polish
+  jacobi_sweeps<double>(U, V, n, fro, 1e-15, 4e-16, 12, &maxrot);
   // eigenvalues = column norms of U, eigenvectors = columns of V
   for (int j = warp; j < n; j += nw) {
     double s = 0.0;
@@ -116,14 +161,14 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const JacobiJob* __restrict
 void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st) {
   if (n_jobs <= 0) return;
   if (max_n > JAC_MAX_N) throw CudaError{cudaErrorInvalidValue, "jacobi: matrix too large"};
-  const int smem = 2 * max_n * max_n * (int)sizeof(double);
+  const int smem = 3 * max_n * max_n * (int)sizeof(double);
   static bool attr = false;
   if (!attr) {
     GPFVM_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    2 * JAC_MAX_N * JAC_MAX_N * (int)sizeof(double)));
+                                    3 * JAC_MAX_N * JAC_MAX_N * (int)sizeof(double)));
     attr = true;
   }
-  jacobi_kernel<<<n_jobs, 256, smem, st>>>(d_jobs);
+  jacobi_kernel<<<n_jobs, 1024, smem, st>>>(d_jobs);
   GPFVM_LAUNCH_CHECK();
 }
 
