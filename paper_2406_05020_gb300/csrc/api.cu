@@ -848,7 +848,7 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
     L.tiles += tiles;
     L.nops++;
     L.maxn = std::max(L.maxn, op.N);
-    if (op.nseg > TC_MAXSEG || op.N > 256) T.ok = false;
+    if (op.nseg > TC_MAXSEG || op.N > 128) T.ok = false;
     T.ops.push_back(op);
   };
   auto seg = [&](TcOp& op, const float* A, i64 fo, int ax, double alpha) {

@@ -29,6 +29,7 @@ namespace gpfvm {
 constexpr int TC_ROWS = 128;
 constexpr int TC_KB = 32;                    // floats per K block (128 bytes)
 constexpr int TC_A_BYTES = TC_ROWS * 128;    // 16 KB per A slice
+constexpr int TC_BREG = 32;                  // B rows per thread / 4: npad <= 128 in registers
 constexpr long long TC_SPIN_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -133,57 +134,80 @@ __global__ void __launch_bounds__(128, 1) tc_mode_kernel(const TcOp* __restrict_
     const int npad = (N + 15) & ~15;
     const uint32_t idesc = idesc_tf32(npad);
     uint32_t acc = 0;
-    for (int s = 0; s < op.nseg && !abort_flag; ++s) {
-      const float* A = op.A[s];
-      const float* Bh = op.Bhi[s];
-      const float* Bl = op.Blo[s];
-      for (int k0 = 0; k0 < K; k0 += TC_KB) {
-        // stage A (split on the fly) and B (pre-split) slices
-        for (int e = tid; e < TC_ROWS * TC_KB; e += 128) {
-          const int r = e >> 5, c = e & 31;
-          const int gr = row0 + r, gc = k0 + c;
-          const float v = (gr < R && gc < K) ? A[(i64)gr * K + gc] : 0.0f;
-          const float vh = tf32_rna(v);
-          const uint32_t off = sw128(r, c);
-          *(float*)(sAhi + off) = vh;
-          *(float*)(sAlo + off) = v - vh;
-        }
-        for (int e = tid; e < npad * TC_KB; e += 128) {
-          const int r = e >> 5, c = e & 31;
-          const int gc = k0 + c;
-          const bool in = (r < N && gc < K);
-          const uint32_t off = sw128(r, c);
-          *(float*)(sBhi + off) = in ? Bh[(i64)r * K + gc] : 0.0f;
-          *(float*)(sBlo + off) = in ? Bl[(i64)r * K + gc] : 0.0f;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int ksteps = min(TC_KB, K - k0) / 8 + ((min(TC_KB, K - k0) % 8) ? 1 : 0);
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
-            const uint64_t ah = desc_sw128(smem_u32(sAhi) + koff), al = desc_sw128(smem_u32(sAlo) + koff);
-            const uint64_t bh = desc_sw128(smem_u32(sBhi) + koff), bl = desc_sw128(smem_u32(sBlo) + koff);
-            mma_tf32(tmem, ah, bh, idesc, acc);
-            acc = 1;
-            mma_tf32(tmem, ah, bl, idesc, 1);
-            mma_tf32(tmem, al, bh, idesc, 1);
-          }
-          mma_commit(&bar);
-        }
-        const bool ok = mbar_wait(&bar, phase);
-        phase ^= 1;
-        if (!ok) {
-          if (tid == 0) {
-            atomicOr(status, (int)DEV_TIMEOUT);
-            abort_flag = 1;
-          }
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (abort_flag) break;
+    // Stage (segment, K block) pairs in order; the next pair's global loads
+    // are issued into registers while the tensor cores work on the current one.
+    const int nkb = (K + TC_KB - 1) / TC_KB;
+    const int nstage = op.nseg * nkb;
+    float ra[TC_ROWS * TC_KB / 128];  // 32 A values per thread
+    float rbh[TC_BREG], rbl[TC_BREG];  // B slice (npad <= 128 rows)
+    auto load_stage = [&](int st) {
+      const int s = st / nkb, k0 = (st % nkb) * TC_KB;
+      const float* __restrict__ A = op.A[s];
+      const float* __restrict__ Bh = op.Bhi[s];
+      const float* __restrict__ Bl = op.Blo[s];
+      const int c = tid & 31, rb = tid >> 5;
+      const int gc = k0 + c;
+#pragma unroll
+      for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
+        const int gr = row0 + rb + 4 * q;
+        ra[q] = (gr < R && gc < K) ? __ldg(&A[(i64)gr * K + gc]) : 0.0f;
       }
+#pragma unroll
+      for (int q = 0; q < TC_BREG; ++q) {
+        const int r = rb + 4 * q;
+        const bool in = (r < N && gc < K && r < npad);
+        rbh[q] = in ? __ldg(&Bh[(i64)r * K + gc]) : 0.0f;
+        rbl[q] = in ? __ldg(&Bl[(i64)r * K + gc]) : 0.0f;
+      }
+    };
+    load_stage(0);
+    for (int st = 0; st < nstage && !abort_flag; ++st) {
+      const int k0 = (st % nkb) * TC_KB;
+      const int c = tid & 31, rb = tid >> 5;
+      // registers -> shared (split A into hi / lo), previous MMAs have completed
+#pragma unroll
+      for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
+        const int r = rb + 4 * q;
+        const float v = ra[q], vh = tf32_rna(v);
+        const uint32_t off = sw128(r, c);
+        *(float*)(sAhi + off) = vh;
+        *(float*)(sAlo + off) = v - vh;
+      }
+#pragma unroll
+      for (int q = 0; q < TC_BREG; ++q) {
+        const int r = rb + 4 * q;
+        if (r < npad) {
+          const uint32_t off = sw128(r, c);
+          *(float*)(sBhi + off) = rbh[q];
+          *(float*)(sBlo + off) = rbl[q];
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int kk = min(TC_KB, K - k0);
+        const int ksteps = (kk + 7) / 8;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
+          const uint64_t ah = desc_sw128(smem_u32(sAhi) + koff), al = desc_sw128(smem_u32(sAlo) + koff);
+          const uint64_t bh = desc_sw128(smem_u32(sBhi) + koff), bl = desc_sw128(smem_u32(sBlo) + koff);
+          mma_tf32(tmem, ah, bh, idesc, acc);
+          acc = 1;
+          mma_tf32(tmem, ah, bl, idesc, 1);
+          mma_tf32(tmem, al, bh, idesc, 1);
+        }
+        mma_commit(&bar);
+      }
+      if (st + 1 < nstage) load_stage(st + 1);  // overlaps the MMAs
+      const bool ok = mbar_wait(&bar, phase);
+      phase ^= 1;
+      if (!ok && tid == 0) {
+        atomicOr(status, (int)DEV_TIMEOUT);
+        abort_flag = 1;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      __syncthreads();
     }
     if (abort_flag) break;
     // epilogue: row = row0 + tid, columns j < N, rotated store out[j * R + row]
@@ -226,14 +250,14 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
   const int npad = (max_n + 15) & ~15;
   int ncols = 32;
   while (ncols < npad) ncols <<= 1;
-  if (ncols > 256) throw CudaError{cudaErrorInvalidValue, "tc: output size above 256"};
+  if (npad > 4 * TC_BREG) throw CudaError{cudaErrorInvalidValue, "tc: output size above 128"};
   const int smem = tc_smem_bytes(ncols);
   static int attr_set = 0;
   if (attr_set < smem) {
     GPFVM_CUDA(cudaFuncSetAttribute(tc_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(256)));
     attr_set = tc_smem_bytes(256);
   }
-  const int grid = (int)std::min<i64>(total_tiles, 152);
+  const int grid = (int)std::min<i64>(total_tiles, 2 * 152);
   tc_mode_kernel<<<grid, 128, smem, st>>>(d_ops, nops, total_tiles, ncols, status);
   GPFVM_LAUNCH_CHECK();
 }
