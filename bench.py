@@ -407,7 +407,7 @@ def run_profile(args):
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
     var = torch.empty_like(mean)
     pb.assemble(stream=s_ptr)
-    for prec in (gpfvm.FP64, gpfvm.MIXED_FP32):
+    for prec in (gpfvm.FP64, gpfvm.MIXED_FP32, gpfvm.MIXED_TF32X3):
         opts = gpfvm.solve_opts(max_iter=args.profile_iters, rtol=0.0, precision=prec, reorth=True, want_var=True,
                                 inner_max_iter=args.profile_iters)
         pb.solve(opts, stream=s_ptr)

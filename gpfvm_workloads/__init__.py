@@ -262,8 +262,9 @@ def serving_wave_stream(rate: float = 500.0, duration: float = 1.0, lo: int = 32
     """Poisson request stream of 2D+time wave IBVPs: arrival times (s) and problems.
 
     Per-axis sizes uniform in {lo..hi}, c ~ U(0.5, 2), one random bump as
-    displacement; IC (Ns/4)^2 grids for displacement and velocity, reflecting
-    walls on (Nt/8)(Ns/8) grids per face."""
+    displacement; IC grids of max(N/4, 3) points per axis for displacement and
+    velocity, reflecting walls on (Nt/8)(Ns/8) grids per face.  The bump is at
+    least half an IC grid spacing wide, so that small requests still observe it."""
     rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
     while True:
@@ -273,8 +274,9 @@ def serving_wave_stream(rate: float = 500.0, duration: float = 1.0, lo: int = 32
         nt, nx, ny = (int(v) for v in rng.integers(lo, hi + 1, 3))
         c = float(rng.uniform(0.5, 2.0))
         ns = max(nx, ny)
-        p = wave_2d(nt, nx, ny, c=c, seed=int(rng.integers(0, 2 ** 31 - 1)),
-                    n_ic=(max(nx // 4, 2), max(ny // 4, 2)),
+        n_ic = (max(nx // 4, 3), max(ny // 4, 3))
+        p = wave_2d(nt, nx, ny, c=c, seed=int(rng.integers(0, 2 ** 31 - 1)), n_ic=n_ic,
+                    width=max(0.05, 0.5 / (min(n_ic) - 1)),
                     n_bc=(max(nt // 8, 1), max(ns // 8, 1)),
                     pred=(nt // 2, nx // 2, ny // 2), ic_noise=0.0, ell=ell, jitter=jitter)
         reqs.append((t, p))

@@ -162,7 +162,10 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream);
  *   op 3: out = G_PB v            (M -> N)
  *   op 4: out = G_PP v in the FP32 form of the mixed solver (FP64 in/out)
  *   op 5: out = G_PP v in the split-TF32 tensor-core form (FP64 in/out)
- * Requires gpfvm_assemble.  v and out must not overlap. */
+ *   op 6: out = G^ v, the inner operator of GPFVM_MIXED_FP32 (FP32, FP64 in/out)
+ *   op 7: out = G^ v, the inner operator of GPFVM_MIXED_TF32X3 (FP64 in/out)
+ * Ops 6 and 7 use the mixed solver's FP32 work vectors: not between the
+ * begin and end of a solve on the same problem.  Requires gpfvm_assemble.  v and out must not overlap. */
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);
 
 /* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  max_iter

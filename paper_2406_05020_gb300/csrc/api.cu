@@ -184,6 +184,7 @@ struct gpfvm_problem {
   std::vector<TcLevel> tc_levels[2];
   i64 tc_split_total = 0, tc_ops_total = 0;
   int tc_nu = 0, tc_nw = 0;
+  int cap64 = 0, cap32 = 0;  // directions the allocated stores hold
   CGState* d_st32 = nullptr;
   CGState* h_st32 = nullptr;
   i64 nfac = 0;
@@ -216,6 +217,10 @@ struct gpfvm_problem {
     if (graph32) cudaGraphExecDestroy(graph32);
     if (h_st) cudaFreeHost(h_st);
     if (h_st32) cudaFreeHost(h_st32);
+    if (d_S) cudaFree(d_S);
+    if (d_Q) cudaFree(d_Q);
+    if (f_S) cudaFree(f_S);
+    if (f_Q) cudaFree(f_Q);
     mem.release();
   }
 };
@@ -1212,8 +1217,7 @@ void alloc_all(gpfvm_problem* p) {
   p->d_var = m.alloc<double>(P);
   p->d_vB = m.alloc<double>(P);
   const int cap = p->cap;
-  p->d_S = m.alloc<double>((i64)cap * N);
-  p->d_Q = m.alloc<double>((i64)cap * N);
+  // the direction stores S, Q (FP64 and FP32) are allocated on first use, sized by need
   p->d_eta = m.alloc<double>(cap);
   p->d_part2 = m.alloc<double>((i64)cap * reorth_chunks(N));
   p->d_coef = m.alloc<double>(cap);
@@ -1244,8 +1248,6 @@ void alloc_all(gpfvm_problem* p) {
   p->f_vin = m.alloc<float>(N);
   p->f_vout = m.alloc<float>(N);
   p->f_u = m.alloc<float>(P);
-  p->f_S = m.alloc<float>((i64)cap * N);
-  p->f_Q = m.alloc<float>((i64)cap * N);
   p->d_eta32 = m.alloc<double>(cap);
   p->d_st = m.alloc<CGState>(1);
   p->d_st32 = m.alloc<CGState>(1);
@@ -1308,6 +1310,42 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
   return GPFVM_OK;
 }
 
+// Direction stores for the reorthogonalisation, allocated on first use.
+void ensure_store64(gpfvm_problem* p, int need) {
+  need = std::min(need, p->cap);
+  if (p->cap64 >= need) return;
+  if (p->d_S) { cudaFree(p->d_S); cudaFree(p->d_Q); p->mem.bytes -= 16LL * p->cap64 * p->N; }
+  p->d_S = p->d_Q = nullptr;
+  p->cap64 = 0;
+  if (cudaMalloc(&p->d_S, sizeof(double) * (size_t)need * p->N) != cudaSuccess ||
+      cudaMalloc(&p->d_Q, sizeof(double) * (size_t)need * p->N) != cudaSuccess) {
+    cudaGetLastError();
+    if (p->d_S) cudaFree(p->d_S);
+    p->d_S = p->d_Q = nullptr;
+    throw CudaError{cudaErrorMemoryAllocation, "direction store"};
+  }
+  p->cap64 = need;
+  p->mem.bytes += 16LL * need * p->N;
+  if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; p->graph_key = -1; }
+}
+void ensure_store32(gpfvm_problem* p, int need) {
+  need = std::min(need, p->cap);
+  if (p->cap32 >= need) return;
+  if (p->f_S) { cudaFree(p->f_S); cudaFree(p->f_Q); p->mem.bytes -= 8LL * p->cap32 * p->N; }
+  p->f_S = p->f_Q = nullptr;
+  p->cap32 = 0;
+  if (cudaMalloc(&p->f_S, sizeof(float) * (size_t)need * p->N) != cudaSuccess ||
+      cudaMalloc(&p->f_Q, sizeof(float) * (size_t)need * p->N) != cudaSuccess) {
+    cudaGetLastError();
+    if (p->f_S) cudaFree(p->f_S);
+    p->f_S = p->f_Q = nullptr;
+    throw CudaError{cudaErrorMemoryAllocation, "direction store"};
+  }
+  p->cap32 = need;
+  p->mem.bytes += 8LL * need * p->N;
+  if (p->graph32) { cudaGraphExecDestroy(p->graph32); p->graph32 = nullptr; p->graph32_key = -1; }
+}
+
 void cg_iteration(gpfvm_problem* p, bool reorth, bool want_var, cudaStream_t st) {
   const i64 N = p->N;
   (want_var ? p->p_mvv_cg : p->p_mv_cg).run(st);
@@ -1315,7 +1353,7 @@ void cg_iteration(gpfvm_problem* p, bool reorth, bool want_var, cudaStream_t st)
   if (want_var) cg_downdate(p->d_u, p->d_down, p->P, p->d_st, st);
   cg_update(p->d_x, p->d_r, p->d_p, p->d_q, N, p->d_st, reorth ? p->d_S : nullptr, reorth ? p->d_Q : nullptr, st);
   cg_pupdate(p->d_r, p->d_p, N, p->d_st, st);
-  if (reorth) cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
+  if (reorth) cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap64, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
 }
 
 double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
@@ -1358,9 +1396,10 @@ int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
     GPFVM_CUDA(cudaEventCreate(&R.e1));
   }
   GPFVM_CUDA(cudaEventRecord(R.e0, st));
+  if (reorth) ensure_store64(p, o->max_iter);
   p->h_st->rtol2 = o->rtol * o->rtol;
   p->h_st->max_iter = o->max_iter;
-  p->h_st->cap = p->cap;
+  p->h_st->cap = reorth ? p->cap64 : 0;
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->rtol2, &p->h_st->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->max_iter, &p->h_st->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
   if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
@@ -1461,64 +1500,105 @@ void cg_iteration32(gpfvm_problem* p, bool want_var, cudaStream_t st) {
   if (want_var) cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
   cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, p->f_S, p->f_Q, st);
   cg_pupdate<float>(p->f_r, p->f_p, N, p->d_st32, st);
-  cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
+  cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
 }
 
 // Iterative refinement (mixed precision, Sec. 4.1 CG as the inner solver):
 //   r = b - G^ x            FP64 operator, FP64 vectors
-//   solve G^_32 d ~= r      inner CG: FP32 operator/vectors, FP64 scalars, reorthogonalised
-//   x += d
+//   solve G^_32 d ~= r/|r|  inner CG: FP32 operator/vectors, FP64 scalars, reorthogonalised
+//   x += |r| d              (the unit right-hand side keeps FP32 in range for any data scale)
 // until ||r|| / ||b|| <= rtol.  The IterGP variance downdate is accumulated
 // during the first inner CG (whose right-hand side is b and whose directions
-// are conjugate within the run).
-int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+// are conjugate within the run).  The solve is a resumable state machine so
+// that batched and served execution can interleave many problems:
+//   0 residual wanted -> 1 residual enqueued -> 2 inner CG running -> 0 ... -> 3 done
+struct MixedRun {
+  gpfvm_solve_opts o{};
+  int mstate = 3, outer = 0, total = 0, launched = 0, lim = 0, status = 0;
+  double rel = 1.0, itol = 1e-2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+std::map<const gpfvm_problem*, MixedRun>& mruns() {
+  static std::map<const gpfvm_problem*, MixedRun> m;
+  return m;
+}
+
+int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
-  const bool want_var = o->want_var != 0;
-  const i64 N = p->N;
-  const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  MixedRun& R = mruns()[p];
+  R.o = *o;
+  R.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
   const bool want_tc = o->precision == GPFVM_MIXED_TF32X3;
   if (want_tc && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  ensure_store32(p, icap);
   if (want_tc != p->use_tc) {  // the captured inner iteration depends on the operator
     p->use_tc = want_tc;
     if (p->graph32) cudaGraphExecDestroy(p->graph32);
     p->graph32 = nullptr;
     p->graph32_key = -1;
   }
+  if (!R.e0) {
+    GPFVM_CUDA(cudaEventCreate(&R.e0));
+    GPFVM_CUDA(cudaEventCreate(&R.e1));
+  }
+  GPFVM_CUDA(cudaEventRecord(R.e0, st));
   p->h_st32->pad[1] = 0;
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
-  const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
-  cudaEvent_t e0, e1;
-  GPFVM_CUDA(cudaEventCreate(&e0));
-  GPFVM_CUDA(cudaEventCreate(&e1));
-  GPFVM_CUDA(cudaEventRecord(e0, st));
-  GPFVM_CUDA(cudaMemsetAsync(p->d_x, 0, sizeof(double) * N, st));
-  if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
-  norm2(p->d_b, N, &p->d_st->aux[1], p->d_st, st);
-  int total = 0, outer = 0, status = GPFVM_NOT_CONVERGED;
-  double rel = 1.0;
-  const int chunk = o->check_every > 0 ? o->check_every : 16;
-  for (;; ++outer) {
-    // FP64 residual of the refined iterate
+  GPFVM_CUDA(cudaMemsetAsync(p->d_x, 0, sizeof(double) * p->N, st));
+  if (o->want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  norm2(p->d_b, p->N, &p->d_st->aux[1], p->d_st, st);
+  R.mstate = 0;
+  R.outer = 0;
+  R.total = 0;
+  R.status = GPFVM_NOT_CONVERGED;
+  R.rel = 1.0;
+  return GPFVM_OK;
+}
+
+// Enqueues the next piece of work (the FP64 residual, or up to n inner iterations).
+void mixed_launch(gpfvm_problem* p, int n, cudaStream_t st) {
+  MixedRun& R = mruns()[p];
+  const i64 N = p->N;
+  if (R.mstate == 0) {
     GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, p->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     p->p_op[1].run(st);
     axpby(p->d_b, p->d_vout, p->d_r, 1.0, -1.0, N, st);
     norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
     copy_header_to_host(p, st);
-    GPFVM_CUDA(cudaStreamSynchronize(st));
+    R.mstate = 1;
+  } else if (R.mstate == 2) {
+    const int k = std::min(n, R.lim - R.launched);
+    for (int i = 0; i < k; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));
+    count_launch((long long)k * p->graph32_kernels);
+    R.launched += k;
+    GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+  }
+}
+
+// Advances the state machine after the stream has been synchronised; may enqueue work.
+void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
+  MixedRun& R = mruns()[p];
+  const gpfvm_solve_opts* o = &R.o;
+  const i64 N = p->N;
+  if (R.mstate == 1) {
     const double b2 = p->h_st->aux[1];
-    rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
-    if (!(rel <= o->rtol) && !std::isfinite(rel)) { status = GPFVM_ERR_BREAKDOWN; break; }
-    if (rel <= o->rtol) { status = GPFVM_OK; break; }
-    if (total >= o->max_iter) break;
-    // inner CG on the FP32 operator
-    const bool var_now = want_var && outer == 0;
-    p->h_st32->rtol2 = itol * itol;
-    p->h_st32->max_iter = std::min(icap, o->max_iter - total);
-    p->h_st32->cap = p->cap;
+    R.rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
+    if (!std::isfinite(R.rel)) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }
+    if (R.rel <= o->rtol) { R.status = GPFVM_OK; R.mstate = 3; return; }
+    if (R.total >= o->max_iter) { R.status = GPFVM_NOT_CONVERGED; R.mstate = 3; return; }
+    const bool var_now = o->want_var && R.outer == 0;
+    const int icap = std::min(p->cap32, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap32);
+    p->h_st32->rtol2 = R.itol * R.itol;
+    p->h_st32->max_iter = std::min(icap, o->max_iter - R.total);
+    p->h_st32->cap = p->cap32;
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->rtol2, &p->h_st32->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
-    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->max_iter, &p->h_st32->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
-    cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st);
+    GPFVM_CUDA(
+        cudaMemcpyAsync(&p->d_st32->max_iter, &p->h_st32->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    // the inner run solves for the normalised residual r / ||r||: FP32 then
+    // sees unit-norm data whatever the scale of y (no under- or overflow)
+    cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st, &p->d_st->aux[0]);
     const int key = var_now ? 1 : 0;
     if (!p->graph32 || p->graph32_key != key) {
       if (p->graph32) cudaGraphExecDestroy(p->graph32);
@@ -1534,41 +1614,73 @@ int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* i
       cudaGraphDestroy(g);
       p->graph32_key = key;
     }
-    int launched = 0;
-    const int lim = p->h_st32->max_iter;
-    while (true) {
-      const int n = std::min(chunk, lim - launched);
-      for (int i = 0; i < n; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));
-      count_launch((long long)n * p->graph32_kernels);
-      launched += n;
-      GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
-      GPFVM_CUDA(cudaStreamSynchronize(st));
-      if (p->h_st32->done || launched >= lim) break;
-    }
+    R.launched = 0;
+    R.lim = p->h_st32->max_iter;
+    R.mstate = 2;
+  } else if (R.mstate == 2) {
+    if (!(p->h_st32->done || R.launched >= R.lim)) return;
     const int k = p->h_st32->k;
-    total += k;
-    if (p->h_st32->pad[1] & DEV_TIMEOUT) { status = GPFVM_ERR_TIMEOUT; break; }
-    if (k == 0) { status = GPFVM_ERR_BREAKDOWN; break; }  // not even one inner step
-    add_f2d(p->d_x, p->f_d, N, st);
+    R.total += k;
+    if (p->h_st32->pad[1] & DEV_TIMEOUT) { R.status = GPFVM_ERR_TIMEOUT; R.mstate = 3; return; }
+    if (k == 0) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }  // not even one inner step
+    add_f2d(p->d_x, p->f_d, N, st, &p->d_st32->aux[7]);
+    R.outer++;
+    R.mstate = 0;
   }
-  GPFVM_CUDA(cudaEventRecord(e1, st));
-  GPFVM_CUDA(cudaEventSynchronize(e1));
+}
+
+bool mixed_finished(gpfvm_problem* p) { return mruns()[p].mstate == 3; }
+
+int mixed_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
+  MixedRun& R = mruns()[p];
+  GPFVM_CUDA(cudaEventRecord(R.e1, st));
+  GPFVM_CUDA(cudaEventSynchronize(R.e1));
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, R.e0, R.e1);
   gpfvm_solve_info I = p->last;
-  I.iterations = total;
-  I.status = status;
-  I.rel_residual = rel;
-  I.true_rel_residual = rel;
+  I.iterations = R.total;
+  I.status = R.status;
+  I.rel_residual = R.rel;
+  I.true_rel_residual = R.rel;
   I.t_solve_ms = ms;
   p->last = I;
-  p->last_outer = outer;
+  p->last_outer = R.outer;
   if (info) *info = I;
-  p->solved = status >= 0;
-  p->want_var_last = want_var;
-  return status;
+  p->solved = R.status >= 0;
+  p->want_var_last = R.o.want_var != 0;
+  return R.status;
+}
+
+int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+  const int b = mixed_begin(p, o, st);
+  if (b != GPFVM_OK) return b;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  while (!mixed_finished(p)) {
+    mixed_launch(p, chunk, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    mixed_poll(p, st);
+  }
+  return mixed_end(p, info, st);
+}
+
+// Precision-independent resumable solve, used by the batch and server drivers.
+bool is_mixed(const gpfvm_solve_opts* o) { return o && o->precision != GPFVM_FP64; }
+int any_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
+  return is_mixed(o) ? mixed_begin(p, o, st) : solve_begin(p, o, st);
+}
+void any_launch(gpfvm_problem* p, const gpfvm_solve_opts* o, int n, cudaStream_t st) {
+  if (is_mixed(o)) mixed_launch(p, n, st);
+  else solve_launch(p, n, st);
+}
+bool any_poll_finished(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
+  if (is_mixed(o)) {
+    mixed_poll(p, st);
+    return mixed_finished(p);
+  }
+  return solve_finished(p);
+}
+int any_end(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+  return is_mixed(o) ? mixed_end(p, info, st) : solve_end(p, info, st);
 }
 
 }  // namespace
@@ -1655,6 +1767,20 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
 
 void gpfvm_destroy(gpfvm_problem* p) {
   if (!p) return;
+  {
+    auto it = runs().find(p);
+    if (it != runs().end()) {
+      if (it->second.e0) cudaEventDestroy(it->second.e0);
+      if (it->second.e1) cudaEventDestroy(it->second.e1);
+      runs().erase(it);
+    }
+    auto jt = mruns().find(p);
+    if (jt != mruns().end()) {
+      if (jt->second.e0) cudaEventDestroy(jt->second.e0);
+      if (jt->second.e1) cudaEventDestroy(jt->second.e1);
+      mruns().erase(jt);
+    }
+  }
   auto& m = own_streams();
   auto it = m.find(p);
   if (it != m.end()) {
@@ -1695,12 +1821,24 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream) {
 }
 
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream) {
-  if (!p || !v || !out || op < 0 || op > 5) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || op < 0 || op > 7) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
-  if (op == 5 && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if ((op == 5 || op == 7) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
+  if (op == 6 || op == 7) {  // the inner CG operator: f_p -> f_q, gated by the inner "done" flag
+    p->h_st32->done = 0;
+    p->h_st32->pad[1] = 0;
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->done, &p->h_st32->done, sizeof(int), cudaMemcpyHostToDevice, st));
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
+    convert_d2f(v, p->f_p, p->N, st);
+    (op == 6 ? p->p_mv32 : p->p_mv32tc).run(st);
+    f2d(p->f_q, out, p->N, st);
+    GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    return (p->h_st32->pad[1] & DEV_TIMEOUT) ? GPFVM_ERR_TIMEOUT : GPFVM_OK;
+  }
   if (op == 5) {
     p->h_st32->pad[1] = 0;
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1881,14 +2019,6 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
   if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
-  if (opts->precision != GPFVM_FP64) {
-    int worst = GPFVM_OK;
-    for (int i = 0; i < n; ++i) {
-      const int r = gpfvm_solve(ps[i], opts, infos ? &infos[i] : nullptr, nullptr);
-      if (r < worst || (worst == GPFVM_OK && r != GPFVM_OK)) worst = r;
-    }
-    return worst;
-  }
   GPFVM_GUARD_BEGIN
   cudaEvent_t ev;
   GPFVM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1899,7 +2029,7 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
   for (int i = 0; i < n; ++i) {
     sts[i] = pick_stream(ps[i], nullptr);
     if (stream) GPFVM_CUDA(cudaStreamWaitEvent(sts[i], ev, 0));
-    const int b = solve_begin(ps[i], opts, sts[i]);
+    const int b = any_begin(ps[i], opts, sts[i]);
     if (b != GPFVM_OK) {
       active[i] = 0;
       worst = std::min(worst, b);
@@ -1911,12 +2041,12 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
   for (int i = 0; i < n; ++i) left += active[i];
   while (left > 0) {
     for (int i = 0; i < n; ++i)
-      if (active[i]) solve_launch(ps[i], chunk, sts[i]);
+      if (active[i]) any_launch(ps[i], opts, chunk, sts[i]);
     for (int i = 0; i < n; ++i) {
       if (!active[i]) continue;
       GPFVM_CUDA(cudaStreamSynchronize(sts[i]));
-      if (solve_finished(ps[i])) {
-        const int r = solve_end(ps[i], infos ? &infos[i] : nullptr, sts[i]);
+      if (any_poll_finished(ps[i], opts, sts[i])) {
+        const int r = any_end(ps[i], opts, infos ? &infos[i] : nullptr, sts[i]);
         if (r < 0) worst = std::min(worst, r);
         else if (r == GPFVM_NOT_CONVERGED && worst == GPFVM_OK) worst = r;
         active[i] = 0;
@@ -2032,7 +2162,14 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
     Request* R = s->queue.front();
     gpfvm_problem* p = nullptr;
     int r = gpfvm_create(&R->desc, s->o.solve.max_iter, &p);
-    if (r == GPFVM_ERR_OUT_OF_MEMORY || (r == GPFVM_OK && s->used + p->mem.bytes > s->budget)) {
+    // admission counts the direction stores the solve will allocate
+    i64 store = 0;
+    if (r == GPFVM_OK) {
+      const gpfvm_solve_opts& so = s->o.solve;
+      if (so.precision == GPFVM_FP64) store = so.reorth ? 16LL * p->N * std::min(so.max_iter, p->cap) : 0;
+      else store = 8LL * p->N * std::min(p->cap, so.inner_max_iter > 0 ? so.inner_max_iter : p->cap);
+    }
+    if (r == GPFVM_ERR_OUT_OF_MEMORY || (r == GPFVM_OK && s->used + p->mem.bytes + store > s->budget)) {
       if (p) gpfvm_destroy(p);
       if (s->running.empty()) {  // can never fit: fail it rather than stall the queue
         s->queue.pop_front();
@@ -2047,10 +2184,10 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
       continue;
     }
     R->p = p;
-    s->used += p->mem.bytes;
     cudaStream_t st = pick_stream(p, nullptr);
     r = run_assemble(p, st);
-    if (r == GPFVM_OK) r = solve_begin(p, &s->o.solve, st);
+    if (r == GPFVM_OK) r = any_begin(p, &s->o.solve, st);
+    s->used += p->mem.bytes;
     if (r != GPFVM_OK) {
       finish_request(s, R, r);
       continue;
@@ -2059,16 +2196,16 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
     s->running.push_back(R);
   }
   // one tick of iterations for every resident request, overlapped across streams
-  for (Request* R : s->running) solve_launch(R->p, s->o.steps_per_tick, pick_stream(R->p, nullptr));
+  for (Request* R : s->running) any_launch(R->p, &s->o.solve, s->o.steps_per_tick, pick_stream(R->p, nullptr));
   std::vector<Request*> still;
   for (Request* R : s->running) {
     cudaStream_t st = pick_stream(R->p, nullptr);
     GPFVM_CUDA(cudaStreamSynchronize(st));
-    if (!solve_finished(R->p)) {
+    if (!any_poll_finished(R->p, &s->o.solve, st)) {
       still.push_back(R);
       continue;
     }
-    int r = solve_end(R->p, &R->info, st);
+    int r = any_end(R->p, &s->o.solve, &R->info, st);
     if (r >= 0) {
       R->mean.resize(R->p->P);
       if (s->o.solve.want_var) R->var.resize(R->p->P);

@@ -36,11 +36,17 @@ __device__ double sum_partials(const double* part, int n, double* smem) {
 
 template <typename TB, typename T>
 __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                                              T* __restrict__ p, i64 n, CGState* st) {
+                                              T* __restrict__ p, i64 n, CGState* st, const double* nrm2) {
   __shared__ double red[32];
+  // optional normalisation to a unit right-hand side (x0 = 0): b / ||b||
+  double sc = 1.0;
+  if (nrm2) {
+    const double s = *nrm2;
+    if (s > 0.0 && isfinite(s)) sc = 1.0 / sqrt(s);
+  }
   double acc = 0.0;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
-    const T v = (T)b[i];
+    const T v = (T)(sc * (double)b[i]);
     x[i] = T(0);
     r[i] = v;
     p[i] = v;
@@ -53,6 +59,7 @@ __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __rest
     if (threadIdx.x == 0) {
       st->rr = s;
       st->bnorm2 = s;
+      st->aux[7] = 1.0 / sc;  // undoes the normalisation of the solution
       st->k = 0;
       st->status = 0;
       st->converged = (s == 0.0);
@@ -217,8 +224,8 @@ int reduce_grid(i64 n) {
 }
 
 template <typename TB, typename T>
-void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s) {
-  k_init<TB, T><<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st);
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2) {
+  k_init<TB, T><<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st, nrm2);
   GPFVM_LAUNCH_CHECK();
 }
 template <typename T>
@@ -271,8 +278,10 @@ void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, 
                              cudaStream_t);
 GPFVM_CG_INST(double)
 GPFVM_CG_INST(float)
-template void cg_init<double, double>(const double*, double*, double*, double*, i64, CGState*, cudaStream_t);
-template void cg_init<double, float>(const double*, float*, float*, float*, i64, CGState*, cudaStream_t);
+template void cg_init<double, double>(const double*, double*, double*, double*, i64, CGState*, cudaStream_t,
+                                      const double*);
+template void cg_init<double, float>(const double*, float*, float*, float*, i64, CGState*, cudaStream_t,
+                                     const double*);
 
 // ---- small vector helpers -------------------------------------------------
 __global__ void k_axpby(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
@@ -306,14 +315,15 @@ void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s) {
   GPFVM_LAUNCH_CHECK();
 }
 
-__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n) {
-  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] += (double)d[i];
+__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n, const double* scale) {
+  const double a = scale ? *scale : 1.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] = fma(a, (double)d[i], x[i]);
 }
-void add_f2d(double* x, const float* d, i64 n, cudaStream_t s) {
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale) {
   if (n <= 0) return;
   int g = ceil_div(n, RT);
   if (g > 4096) g = 4096;
-  k_add_f2d<<<g, RT, 0, s>>>(x, d, n);
+  k_add_f2d<<<g, RT, 0, s>>>(x, d, n, scale);
   GPFVM_LAUNCH_CHECK();
 }
 

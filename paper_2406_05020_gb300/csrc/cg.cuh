@@ -17,8 +17,10 @@ struct CGState {
 
 int reduce_grid(i64 n);
 int reorth_chunks(i64 n);
+// r = p = b (scaled by 1/sqrt(*nrm2) when nrm2 is given; st->aux[7] keeps the
+// inverse factor), x = 0, and the scalar header reset for a new run.
 template <typename TB, typename T>
-void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s);
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2 = nullptr);
 template <typename T>
 void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
 template <typename T>
@@ -30,7 +32,8 @@ void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s);
 template <typename T>
 void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, double* part2, double* coef,
                const double* eta_hist, cudaStream_t s);
-void add_f2d(double* x, const float* d, i64 n, cudaStream_t s);
+// x += (*scale) d  (scale defaults to 1)
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale = nullptr);
 void f2d(const float* a, double* b, i64 n, cudaStream_t s);
 void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s);
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s);

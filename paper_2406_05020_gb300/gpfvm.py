@@ -270,6 +270,52 @@ def kron_matvec_noalloc(dims, terms, scale, diag, v, out, stream=None):
                                                   _stream(stream)), "gpfvm_kron_matvec_noalloc")
 
 
+class Server:
+    """Continuous-batching serving loop (gpfvm_server_*)."""
+
+    def __init__(self, max_slots=8, memory_budget=0, steps_per_tick=16, **solve_kw):
+        o = ServerOpts()
+        o.max_slots, o.memory_budget, o.steps_per_tick = int(max_slots), int(memory_budget), int(steps_per_tick)
+        o.solve = solve_opts(**solve_kw)
+        self.opts = o
+        h = P()
+        _check(lib().gpfvm_server_create(C.byref(o), C.byref(h)), "gpfvm_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, prob) -> int:
+        d, keep = make_desc(prob)
+        t = C.c_int64()
+        _check(lib().gpfvm_server_submit(self.h, C.byref(d), C.byref(t)), "gpfvm_server_submit")
+        self._keep[t.value] = (d, keep, prob)
+        return t.value
+
+    def step(self) -> int:
+        return _check(lib().gpfvm_server_step(self.h), "gpfvm_server_step")
+
+    def poll(self, ticket: int, want_var: bool = True):
+        """(code, mean, var, info); code 2 = still pending."""
+        prob = self._keep[ticket][2]
+        P_ = int(np.prod([len(x) for x in prob.pred]))
+        mean = np.empty(P_)
+        var = np.empty(P_) if want_var else None
+        info = SolveInfo()
+        code = lib().gpfvm_server_poll(self.h, int(ticket), _dptr(mean), _dptr(var) if var is not None else None,
+                                       C.byref(info))
+        return code, mean, var, info
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpfvm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def launch_count() -> int:
     return int(lib().gpfvm_launch_count())
 
