@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--matvec-reps", type=int, default=50)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling mode: one assemble, solves of this many CG iterations per path, one query")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling mode: exactly one timed-region step (assemble, set values, solve to the "
+                         "benchmark tolerance, query) of --profile-precision (default: mixed TF32x3)")
+    ap.add_argument("--profile-precision", type=int, default=-1,
+                    help="profiling mode: only this precision (0 FP64, 1 mixed FP32, 2 mixed TF32x3)")
     return ap.parse_args()
 
 
@@ -407,7 +412,10 @@ def run_profile(args):
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
     var = torch.empty_like(mean)
     pb.assemble(stream=s_ptr)
-    for prec in (gpfvm.FP64, gpfvm.MIXED_FP32, gpfvm.MIXED_TF32X3):
+    precs = (gpfvm.FP64, gpfvm.MIXED_FP32, gpfvm.MIXED_TF32X3)
+    if args.profile_precision >= 0:
+        precs = (args.profile_precision,)
+    for prec in precs:
         opts = gpfvm.solve_opts(max_iter=args.profile_iters, rtol=0.0, precision=prec, reorth=True, want_var=True,
                                 inner_max_iter=args.profile_iters)
         pb.solve(opts, stream=s_ptr)
@@ -421,8 +429,37 @@ def run_profile(args):
     return 0
 
 
+def run_profile_step(args):
+    """One step of the timed region, for launch lists and kernel shares."""
+    import torch
+
+    from paper_2406_05020_gb300 import build, gpfvm
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    s_ptr = stream.cuda_stream
+    prec = args.profile_precision if args.profile_precision >= 0 else gpfvm.MIXED_TF32X3
+    pb = gpfvm.Problem(workload(0), max_iter=MAX_ITER_MIXED)
+    prob = workload(1)
+    vals = torch.as_tensor(np.concatenate([np.ravel(s.values) for s in prob.sets]), device="cuda")
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    opts = gpfvm.solve_opts(max_iter=MAX_ITER if prec == gpfvm.FP64 else MAX_ITER_MIXED, rtol=RTOL, precision=prec,
+                            reorth=True, want_var=True, check_every=32, inner_rtol=1e-2)
+    pb.assemble(stream=s_ptr)
+    pb.set_values(vals, stream=s_ptr)
+    code, info = pb.solve(opts, stream=s_ptr)
+    pb.query(mean, var, stream=s_ptr)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": True, "precision": prec, "code": code, "iterations": info.iterations,
+                      "launches": gpfvm.launch_count()}))
+    return 0 if code == 0 else 1
+
+
 def main():
     args = parse()
+    if args.profile_step:
+        return run_profile_step(args)
     if args.profile_iters > 0:
         return run_profile(args)
     if args.impl == "reference":

@@ -118,7 +118,7 @@ typedef struct {
   int precision;       /* enum gpfvm_precision */
   int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions */
   int want_var;        /* 1 = accumulate the IterGP variance downdate on the grid */
-  int check_every;     /* iterations between host convergence checks (graph replays) */
+  int check_every;     /* unused (kept for layout): every CG run is one device-side loop */
   int inner_max_iter;  /* mixed: iteration cap of one inner CG (<= 0: no cap beyond max_iter) */
   double inner_rtol;   /* mixed: residual reduction of one inner CG (<= 0: 1e-2) */
 } gpfvm_solve_opts;
@@ -170,8 +170,10 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
 
 /* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  max_iter
  * counts CG iterations (for the mixed precisions: inner iterations).  All scalars
- * stay on the device; the iteration is replayed as a CUDA graph and the host
- * reads the residual every check_every iterations.  Returns OK, NOT_CONVERGED
+ * stay on the device; a whole CG run is one CUDA graph launch whose WHILE node
+ * repeats the captured iteration until the device state reports convergence,
+ * breakdown or max_iter (bounded by max_iter + 2 passes in any case), so the
+ * host reads the state once per run.  Returns OK, NOT_CONVERGED
  * (budget exhausted; the iterate and variance downdate are kept), BREAKDOWN,
  * STATE (not assembled) or DEVICE.  info may be NULL.  Mixed precisions: the
  * stopping test is the FP64 residual of the refined iterate, and the IterGP
@@ -225,9 +227,11 @@ int64_t gpfvm_factor(gpfvm_problem* p, int axis, int kind_a, int arg_a, int kind
 
 /* ------------------------------------------------------------------------
  * Batched execution: many independent problems of uneven sizes advanced
- * together.  Each problem must be created and assembled; the iteration of
- * all unconverged problems runs as one persistent launch per step, captured
- * in a CUDA graph, with per-problem convergence masks.
+ * together.  Each problem must be created and assembled.  Every problem runs
+ * on its own stream, each CG run as one device-side loop (graph WHILE node),
+ * so the problems overlap on the device; the host only advances the
+ * refinement steps of problems whose streams are idle.  Returns the worst
+ * status; infos (may be NULL) receives one entry per problem.
  * ------------------------------------------------------------------------ */
 int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts,
                       gpfvm_solve_info* infos, void* stream);
@@ -235,7 +239,7 @@ int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts,
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching loop.  Requests are admitted into slots as
  * device memory and slots free up, their CG state stays resident, and their
- * iterations are interleaved with those of requests already running.
+ * device-side CG loops overlap with those of requests already running.
  * ------------------------------------------------------------------------ */
 typedef struct gpfvm_server gpfvm_server;
 
@@ -243,14 +247,16 @@ typedef struct {
   int max_slots;            /* requests resident at once */
   int64_t memory_budget;    /* bytes of device memory the server may hold (0 = 90% of free) */
   gpfvm_solve_opts solve;   /* per-request solver options */
-  int steps_per_tick;       /* CG iterations per request per scheduling tick */
+  int steps_per_tick;       /* unused (kept for layout): CG runs are device-side loops */
 } gpfvm_server_opts;
 
 int gpfvm_server_create(const gpfvm_server_opts* opts, gpfvm_server** out);
 /* Queues a request (descriptor copied); returns its ticket (>= 0) in *ticket. */
 int gpfvm_server_submit(gpfvm_server* s, const gpfvm_desc* desc, int64_t* ticket);
-/* Advances the loop by one scheduling tick (admit, iterate, retire). Returns
- * the number of requests still queued or running. */
+/* One scheduling pass: admits queued requests, advances every request whose
+ * stream is idle (next refinement step, or retire with its result) and
+ * returns without waiting for running loops (it sleeps ~50 us when nothing
+ * advanced).  Returns the number of requests still queued or running. */
 int gpfvm_server_step(gpfvm_server* s);
 /* If the request is done, copies mean/var (host, P each; var may be NULL) and
  * its info, returns OK/NOT_CONVERGED or its error; returns 2 if still pending. */

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <thread>
 #include <deque>
 #include <cstring>
 #include <map>
@@ -200,6 +201,7 @@ struct gpfvm_problem {
   Plan p_op[4];
   Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32, p_mv32tc, p_mvv32tc, p_pp32tc;
   int modeprods_pp = 0;
+  Fan fan;  // side streams for the independent launches of a plan phase
 
   // ---- state
   bool assembled = false, solved = false, vB_ready = false, want_var_last = false;
@@ -213,6 +215,7 @@ struct gpfvm_problem {
   int last_outer = 0;
 
   ~gpfvm_problem() {
+    fan.destroy();
     if (graph) cudaGraphExecDestroy(graph);
     if (graph32) cudaGraphExecDestroy(graph32);
     if (h_st) cudaFreeHost(h_st);
@@ -1003,7 +1006,11 @@ void finalize_plans(gpfvm_problem* p) {
   for (int i = 0; i < 19; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
   p->p_mv32tc.skip = &p->d_st32->done;
   p->p_mvv32tc.skip = &p->d_st32->done;
-  for (Plan* pl : all) pl->finalize();
+  if (!p->fan.fork) p->fan.create();
+  for (Plan* pl : all) {
+    pl->finalize();
+    pl->fan = &p->fan;
+  }
 }
 
 int validate(const gpfvm_desc* D) {
@@ -1314,35 +1321,37 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
 void ensure_store64(gpfvm_problem* p, int need) {
   need = std::min(need, p->cap);
   if (p->cap64 >= need) return;
-  if (p->d_S) { cudaFree(p->d_S); cudaFree(p->d_Q); p->mem.bytes -= 16LL * p->cap64 * p->N; }
+  const i64 ld = store_ld(p->N);
+  if (p->d_S) { cudaFree(p->d_S); cudaFree(p->d_Q); p->mem.bytes -= 16LL * p->cap64 * ld; }
   p->d_S = p->d_Q = nullptr;
   p->cap64 = 0;
-  if (cudaMalloc(&p->d_S, sizeof(double) * (size_t)need * p->N) != cudaSuccess ||
-      cudaMalloc(&p->d_Q, sizeof(double) * (size_t)need * p->N) != cudaSuccess) {
+  if (cudaMalloc(&p->d_S, sizeof(double) * (size_t)need * ld) != cudaSuccess ||
+      cudaMalloc(&p->d_Q, sizeof(double) * (size_t)need * ld) != cudaSuccess) {
     cudaGetLastError();
     if (p->d_S) cudaFree(p->d_S);
     p->d_S = p->d_Q = nullptr;
     throw CudaError{cudaErrorMemoryAllocation, "direction store"};
   }
   p->cap64 = need;
-  p->mem.bytes += 16LL * need * p->N;
+  p->mem.bytes += 16LL * need * ld;
   if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; p->graph_key = -1; }
 }
 void ensure_store32(gpfvm_problem* p, int need) {
   need = std::min(need, p->cap);
   if (p->cap32 >= need) return;
-  if (p->f_S) { cudaFree(p->f_S); cudaFree(p->f_Q); p->mem.bytes -= 8LL * p->cap32 * p->N; }
+  const i64 ld = store_ld(p->N);
+  if (p->f_S) { cudaFree(p->f_S); cudaFree(p->f_Q); p->mem.bytes -= 8LL * p->cap32 * ld; }
   p->f_S = p->f_Q = nullptr;
   p->cap32 = 0;
-  if (cudaMalloc(&p->f_S, sizeof(float) * (size_t)need * p->N) != cudaSuccess ||
-      cudaMalloc(&p->f_Q, sizeof(float) * (size_t)need * p->N) != cudaSuccess) {
+  if (cudaMalloc(&p->f_S, sizeof(float) * (size_t)need * ld) != cudaSuccess ||
+      cudaMalloc(&p->f_Q, sizeof(float) * (size_t)need * ld) != cudaSuccess) {
     cudaGetLastError();
     if (p->f_S) cudaFree(p->f_S);
     p->f_S = p->f_Q = nullptr;
     throw CudaError{cudaErrorMemoryAllocation, "direction store"};
   }
   p->cap32 = need;
-  p->mem.bytes += 8LL * need * p->N;
+  p->mem.bytes += 8LL * need * ld;
   if (p->graph32) { cudaGraphExecDestroy(p->graph32); p->graph32 = nullptr; p->graph32_key = -1; }
 }
 
@@ -1365,6 +1374,51 @@ double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
   GPFVM_CUDA(cudaStreamSynchronize(st));
   const double b2 = p->h_st->bnorm2;
   return b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
+}
+
+// A graph whose only node is a WHILE loop over one captured CG iteration:
+// the iteration kernels plus loop_ctl, which ends the loop once the device
+// state reports done (or after max_iter + 2 passes).  One launch runs a whole
+// CG run with no host round trips.  *body_kernels receives the kernels of one
+// pass (the control kernel included).
+cudaGraphExec_t make_loop_graph(CGState* st_dev, cudaStream_t st, const std::function<void()>& body,
+                                long long* body_kernels) {
+  cudaGraph_t g = nullptr;
+  GPFVM_CUDA(cudaGraphCreate(&g, 0));
+  try {
+    cudaGraphConditionalHandle h;
+    GPFVM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    GPFVM_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    const long long before = g_launches.load();
+    GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      body();
+      loop_ctl(st_dev, h, st);
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(st, &dummy);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t captured;
+    GPFVM_CUDA(cudaStreamEndCapture(st, &captured));
+    *body_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(*body_kernels);  // captured, not launched
+    cudaGraphExec_t ex = nullptr;
+    GPFVM_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    return ex;
+  } catch (...) {
+    cudaGraphDestroy(g);
+    throw;
+  }
 }
 
 int mixed_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st);
@@ -1408,34 +1462,25 @@ int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->graph || p->graph_key != key) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
-    cudaGraph_t g;
-    const long long before = g_launches.load();
-    GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cg_iteration(p, reorth, want_var, st);
-    GPFVM_CUDA(cudaStreamEndCapture(st, &g));
-    p->graph_kernels = g_launches.load() - before;
-    g_launches.fetch_sub(p->graph_kernels);  // captured, not launched
-    GPFVM_CUDA(cudaGraphInstantiate(&p->graph, g, 0));
-    cudaGraphDestroy(g);
+    p->graph = make_loop_graph(p->d_st, st, [&] { cg_iteration(p, reorth, want_var, st); }, &p->graph_kernels);
     p->graph_key = key;
   }
   return GPFVM_OK;
 }
 
-// Enqueues up to n more iterations (graph replays) and a copy of the scalar header.
-void solve_launch(gpfvm_problem* p, int n, cudaStream_t st) {
+// Enqueues the device-side CG loop (all iterations) and a copy of the scalar header.
+void solve_launch(gpfvm_problem* p, int, cudaStream_t st) {
   SolveRun& R = runs()[p];
-  n = std::min(n, R.o.max_iter - R.launched);
-  for (int i = 0; i < n; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph, st));
-  count_launch((long long)n * p->graph_kernels);
-  R.launched += n;
+  if (R.launched > 0) return;
+  GPFVM_CUDA(cudaGraphLaunch(p->graph, st));
+  R.launched = R.o.max_iter;
   copy_header_to_host(p, st);
 }
 
-// True once the device reports done (or the budget is spent); needs the stream to be synchronised.
+// True once the launched loop has ended; needs the stream to be synchronised.
 bool solve_finished(gpfvm_problem* p) {
   SolveRun& R = runs()[p];
-  return p->h_st->done || R.launched >= R.o.max_iter;
+  return R.launched > 0;
 }
 
 int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
@@ -1446,6 +1491,7 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   cudaEventElapsedTime(&ms, R.e0, R.e1);
   R.active = false;
   const CGState& h = *p->h_st;
+  count_launch((long long)h.loops * p->graph_kernels);
   int status = GPFVM_NOT_CONVERGED;
   if (h.status & DEV_BREAKDOWN) status = GPFVM_ERR_BREAKDOWN;
   else if (h.converged) status = GPFVM_OK;
@@ -1466,12 +1512,8 @@ int run_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* inf
   if (o && (o->precision == GPFVM_MIXED_FP32 || o->precision == GPFVM_MIXED_TF32X3)) return mixed_solve(p, o, info, st);
   const int b = solve_begin(p, o, st);
   if (b != GPFVM_OK) return b;
-  const int chunk = o->check_every > 0 ? o->check_every : 16;
-  while (true) {
-    solve_launch(p, chunk, st);
-    GPFVM_CUDA(cudaStreamSynchronize(st));
-    if (solve_finished(p)) break;
-  }
+  solve_launch(p, 0, st);
+  GPFVM_CUDA(cudaStreamSynchronize(st));
   return solve_end(p, info, st);
 }
 
@@ -1558,7 +1600,7 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
 }
 
 // Enqueues the next piece of work (the FP64 residual, or up to n inner iterations).
-void mixed_launch(gpfvm_problem* p, int n, cudaStream_t st) {
+void mixed_launch(gpfvm_problem* p, int, cudaStream_t st) {
   MixedRun& R = mruns()[p];
   const i64 N = p->N;
   if (R.mstate == 0) {
@@ -1568,11 +1610,9 @@ void mixed_launch(gpfvm_problem* p, int n, cudaStream_t st) {
     norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
     copy_header_to_host(p, st);
     R.mstate = 1;
-  } else if (R.mstate == 2) {
-    const int k = std::min(n, R.lim - R.launched);
-    for (int i = 0; i < k; ++i) GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));
-    count_launch((long long)k * p->graph32_kernels);
-    R.launched += k;
+  } else if (R.mstate == 2 && R.launched == 0) {
+    GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));  // the whole inner run
+    R.launched = R.lim;
     GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
   }
 }
@@ -1603,22 +1643,15 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     if (!p->graph32 || p->graph32_key != key) {
       if (p->graph32) cudaGraphExecDestroy(p->graph32);
       p->graph32 = nullptr;
-      cudaGraph_t g;
-      const long long before = gpfvm_launch_count();
-      GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cg_iteration32(p, var_now, st);
-      GPFVM_CUDA(cudaStreamEndCapture(st, &g));
-      p->graph32_kernels = gpfvm_launch_count() - before;
-      count_launch(-p->graph32_kernels);
-      GPFVM_CUDA(cudaGraphInstantiate(&p->graph32, g, 0));
-      cudaGraphDestroy(g);
+      p->graph32 = make_loop_graph(p->d_st32, st, [&] { cg_iteration32(p, var_now, st); }, &p->graph32_kernels);
       p->graph32_key = key;
     }
     R.launched = 0;
     R.lim = p->h_st32->max_iter;
     R.mstate = 2;
   } else if (R.mstate == 2) {
-    if (!(p->h_st32->done || R.launched >= R.lim)) return;
+    if (R.launched == 0) return;  // the inner run has not been launched yet
+    count_launch((long long)p->h_st32->loops * p->graph32_kernels);
     const int k = p->h_st32->k;
     R.total += k;
     if (p->h_st32->pad[1] & DEV_TIMEOUT) { R.status = GPFVM_ERR_TIMEOUT; R.mstate = 3; return; }
@@ -2010,9 +2043,10 @@ const char* gpfvm_version(void) { return "gpfvm 0.1 sm_103a"; }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batched solves: every problem iterates on its own stream; chunks of graph
-// replays are issued round-robin so that the problems' kernels overlap on the
-// device, and converged problems drop out (their kernels become no-ops).
+// Batched solves: every problem runs on its own stream, each CG run as one
+// device-side loop (a graph WHILE node), so the problems' kernels overlap on
+// the device; the host only advances the mixed-precision refinement steps of
+// problems whose streams have gone idle.
 // ---------------------------------------------------------------------------
 extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts, gpfvm_solve_info* infos,
                                  void* stream) {
@@ -2036,15 +2070,24 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
       if (infos) infos[i].status = b;
     }
   }
-  const int chunk = opts->check_every > 0 ? opts->check_every : 16;
+  // every problem runs its own device-side loops on its own stream; the host
+  // advances whichever problem's stream has gone idle
   int left = 0;
   for (int i = 0; i < n; ++i) left += active[i];
+  std::vector<char> pending(n, 0);
   while (left > 0) {
-    for (int i = 0; i < n; ++i)
-      if (active[i]) any_launch(ps[i], opts, chunk, sts[i]);
+    bool progressed = false;
     for (int i = 0; i < n; ++i) {
       if (!active[i]) continue;
-      GPFVM_CUDA(cudaStreamSynchronize(sts[i]));
+      if (!pending[i]) {
+        any_launch(ps[i], opts, 0, sts[i]);
+        pending[i] = 1;
+      }
+      const cudaError_t q = cudaStreamQuery(sts[i]);
+      if (q == cudaErrorNotReady) continue;
+      GPFVM_CUDA(q);
+      pending[i] = 0;
+      progressed = true;
       if (any_poll_finished(ps[i], opts, sts[i])) {
         const int r = any_end(ps[i], opts, infos ? &infos[i] : nullptr, sts[i]);
         if (r < 0) worst = std::min(worst, r);
@@ -2053,6 +2096,7 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
         --left;
       }
     }
+    if (!progressed) std::this_thread::yield();
   }
   cudaEventDestroy(ev);
   return worst;
@@ -2074,6 +2118,7 @@ struct Request {
   std::vector<std::vector<double>> store;  // owned copies of every descriptor array
   gpfvm_problem* p = nullptr;
   int state = 0;  // 0 queued, 1 running, 2 done
+  bool pending = false;  // work enqueued on the request's stream and not yet polled
   int code = 0;
   std::vector<double> mean, var;
   gpfvm_solve_info info{};
@@ -2166,8 +2211,9 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
     i64 store = 0;
     if (r == GPFVM_OK) {
       const gpfvm_solve_opts& so = s->o.solve;
-      if (so.precision == GPFVM_FP64) store = so.reorth ? 16LL * p->N * std::min(so.max_iter, p->cap) : 0;
-      else store = 8LL * p->N * std::min(p->cap, so.inner_max_iter > 0 ? so.inner_max_iter : p->cap);
+      const i64 ld = store_ld(p->N);
+      if (so.precision == GPFVM_FP64) store = so.reorth ? 16LL * ld * std::min(so.max_iter, p->cap) : 0;
+      else store = 8LL * ld * std::min(p->cap, so.inner_max_iter > 0 ? so.inner_max_iter : p->cap);
     }
     if (r == GPFVM_ERR_OUT_OF_MEMORY || (r == GPFVM_OK && s->used + p->mem.bytes + store > s->budget)) {
       if (p) gpfvm_destroy(p);
@@ -2195,12 +2241,24 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
     R->state = 1;
     s->running.push_back(R);
   }
-  // one tick of iterations for every resident request, overlapped across streams
-  for (Request* R : s->running) any_launch(R->p, &s->o.solve, s->o.steps_per_tick, pick_stream(R->p, nullptr));
+  // advance every resident request whose stream is idle; the device-side
+  // loops of the others keep running meanwhile
+  bool progressed = false;
   std::vector<Request*> still;
   for (Request* R : s->running) {
     cudaStream_t st = pick_stream(R->p, nullptr);
-    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (!R->pending) {
+      any_launch(R->p, &s->o.solve, 0, st);
+      R->pending = true;
+    }
+    const cudaError_t q = cudaStreamQuery(st);
+    if (q == cudaErrorNotReady) {
+      still.push_back(R);
+      continue;
+    }
+    GPFVM_CUDA(q);
+    R->pending = false;
+    progressed = true;
     if (!any_poll_finished(R->p, &s->o.solve, st)) {
       still.push_back(R);
       continue;
@@ -2209,18 +2267,19 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
     if (r >= 0) {
       R->mean.resize(R->p->P);
       if (s->o.solve.want_var) R->var.resize(R->p->P);
-      const int q = run_query(R->p, R->p->d_mean, s->o.solve.want_var ? R->p->d_var : nullptr, st);
-      if (q == GPFVM_OK) {
+      const int q2 = run_query(R->p, R->p->d_mean, s->o.solve.want_var ? R->p->d_var : nullptr, st);
+      if (q2 == GPFVM_OK) {
         GPFVM_CUDA(cudaMemcpyAsync(R->mean.data(), R->p->d_mean, sizeof(double) * R->p->P, cudaMemcpyDeviceToHost, st));
         if (s->o.solve.want_var)
           GPFVM_CUDA(cudaMemcpyAsync(R->var.data(), R->p->d_var, sizeof(double) * R->p->P, cudaMemcpyDeviceToHost, st));
         GPFVM_CUDA(cudaStreamSynchronize(st));
       } else {
-        r = q;
+        r = q2;
       }
     }
     finish_request(s, R, r);
   }
+  if (!progressed && !still.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
   s->running.swap(still);
   return (int)(s->queue.size() + s->running.size());
   GPFVM_GUARD_END

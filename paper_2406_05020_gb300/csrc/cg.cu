@@ -10,6 +10,8 @@
 // All scalars live in device memory (CGState), so an iteration is a fixed
 // launch sequence that a CUDA graph replays; reductions use a fixed-order
 // "last block" sum so results do not depend on block scheduling.
+#include <algorithm>
+
 #include "cg.cuh"
 
 namespace gpfvm {
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __rest
       st->bnorm2 = s;
       st->aux[7] = 1.0 / sc;  // undoes the normalisation of the solution
       st->k = 0;
+      st->loops = 0;
       st->status = 0;
       st->converged = (s == 0.0);
       st->done = (s == 0.0) || (st->max_iter <= 0);
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(RT) k_downdate(const T* __restrict__ u, double
 template <typename T>
 __global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                 const T* __restrict__ q, i64 n, CGState* st, T* __restrict__ S,
-                                                T* __restrict__ Q) {
+                                                T* __restrict__ Q, i64 ld) {
   if (st->done) return;
   __shared__ double red[32];
   const double alpha = st->rr / st->eta;
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict_
     r[i] = (T)ri;
     acc = fma(ri, ri, acc);
     if (keep) {
-      S[(i64)k * n + i] = pi;
-      Q[(i64)k * n + i] = qi;
+      S[(i64)k * ld + i] = pi;
+      Q[(i64)k * ld + i] = qi;
     }
   }
   acc = block_sum<RT>(acc, red);
@@ -158,61 +161,130 @@ __global__ void __launch_bounds__(RT) k_pupdate(const T* __restrict__ r, T* __re
     p[i] = (T)fma(beta, (double)p[i], (double)r[i]);
 }
 
-// partial dots part2[j * nchunk + c] = sum_{i in chunk c} Q[j][i] p[i] for j < k
+// ---- full reorthogonalisation  p -= sum_j (q_j . p / eta_j) s_j  (Sec. 5)
+// The direction stores hold one row of ld = store_ld(n) elements per
+// direction (rows 16-byte aligned), so both kernels read them with 16-byte
+// vector loads.  Chunk c of RCH elements of p stays in registers while each
+// warp sweeps its share of the directions; per-lane partial dots are formed in
+// the working precision, reduced across the warp and over chunks in FP64 in a
+// fixed order (deterministic), and the last block turns the sums into the
+// coefficients q_j.p / eta_j.
+constexpr int RCH = 1024;  // elements of p per dots chunk
+
 template <typename T>
-__global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ p, i64 n,
-                                                     int chunk, const CGState* st, double* __restrict__ part2) {
-  if (st->done) return;
-  const int k = min(st->k, st->cap);
-  const int c = blockIdx.x, nchunk = gridDim.x;
-  const i64 lo = (i64)c * chunk;
-  const i64 hi = min(n, lo + chunk);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = blockIdx.y * (RT / 32) + warp; j < k; j += gridDim.y * (RT / 32)) {
-    const T* qj = Q + (i64)j * n;
-    double s = 0.0;
-    for (i64 i = lo + lane; i < hi; i += 32) s = fma((double)qj[i], (double)p[i], s);
+__device__ __forceinline__ void ldv(const T* __restrict__ a, i64 e, i64 lim, T (&o)[16 / sizeof(T)]) {
+  constexpr int W = 16 / sizeof(T);
+  if (e + W <= lim) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(a + e);
+      o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(a + e);
+      o[0] = v.x; o[1] = v.y;
+    }
+  } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) part2[(i64)j * nchunk + c] = s;
+    for (int w = 0; w < W; ++w) o[w] = (e + w < lim) ? a[e + w] : T(0);
   }
 }
 
-__global__ void __launch_bounds__(RT) k_reorth_coef(const double* __restrict__ part2, int nchunk,
-                                                     const double* __restrict__ eta_hist, const CGState* st,
-                                                     double* __restrict__ coef) {
+template <typename T>
+__global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64 ld, const T* __restrict__ p, i64 n,
+                                                     CGState* st, double* __restrict__ part2,
+                                                     const double* __restrict__ eta_hist, double* __restrict__ coef) {
   if (st->done) return;
+  constexpr int W = 16 / sizeof(T);
+  constexpr int NV = RCH / (32 * W);  // vectors per lane
   const int k = min(st->k, st->cap);
-  const int j = blockIdx.x * RT + threadIdx.x;
-  if (j >= k) return;
-  double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part2[(i64)j * nchunk + c];
-  coef[j] = s / eta_hist[j];
+  const int c = blockIdx.x, nchunk = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const i64 base = (i64)c * RCH;
+  T pv[NV][W];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ldv(p, base + (i64)(v * 32 + lane) * W, n, pv[v]);
+  const int wstride = gridDim.y * (RT / 32);
+  for (int j = blockIdx.y * (RT / 32) + warp; j < k; j += wstride) {
+    const T* __restrict__ qj = Q + (i64)j * ld;
+    T a0 = T(0), a1 = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T qv[W];
+      ldv(qj, base + (i64)(v * 32 + lane) * W, n, qv);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        if (w & 1) a1 = fma(qv[w], pv[v][w], a1);
+        else a0 = fma(qv[w], pv[v][w], a0);
+      }
+    }
+    double sum = (double)a0 + (double)a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) part2[(i64)j * nchunk + c] = sum;
+  }
+  // the last block to finish forms the coefficients (one warp per direction)
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(&st->ticket[4], 1u) == gridDim.x * gridDim.y - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int j = warp; j < k; j += RT / 32) {
+    const volatile double* row = part2 + (i64)j * nchunk;
+    double sum = 0.0;
+    for (int cc = lane; cc < nchunk; cc += 32) sum += row[cc];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) coef[j] = sum / eta_hist[j];
+  }
+  if (threadIdx.x == 0) st->ticket[4] = 0;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, T* __restrict__ p, i64 n,
+__global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, i64 ld, T* __restrict__ p, i64 n,
                                                       const CGState* st, const double* __restrict__ coef) {
   if (st->done) return;
-  __shared__ double cs[1024];
+  constexpr int W = 16 / sizeof(T);
+  __shared__ T cs[1024];
   const int k = min(st->k, st->cap);
-  const i64 i = (i64)blockIdx.x * RT + threadIdx.x;
-  double acc0 = 0.0, acc1 = 0.0;
+  const i64 e = ((i64)blockIdx.x * RT + threadIdx.x) * W;
+  T acc0[W], acc1[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc0[w] = acc1[w] = T(0);
   for (int j0 = 0; j0 < k; j0 += 1024) {
     const int jn = min(1024, k - j0);
     __syncthreads();
-    for (int t = threadIdx.x; t < jn; t += RT) cs[t] = coef[j0 + t];
+    for (int t = threadIdx.x; t < jn; t += RT) cs[t] = (T)coef[j0 + t];
     __syncthreads();
-    if (i < n) {
+    if (e < n) {
+      const T* __restrict__ Sj = S + (i64)j0 * ld;
       int j = 0;
       for (; j + 1 < jn; j += 2) {
-        acc0 = fma((double)S[(i64)(j0 + j) * n + i], cs[j], acc0);
-        acc1 = fma((double)S[(i64)(j0 + j + 1) * n + i], cs[j + 1], acc1);
+        T s0[W], s1[W];
+        ldv(Sj + (i64)j * ld, e, n, s0);
+        ldv(Sj + (i64)(j + 1) * ld, e, n, s1);
+        const T c0 = cs[j], c1 = cs[j + 1];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          acc0[w] = fma(s0[w], c0, acc0[w]);
+          acc1[w] = fma(s1[w], c1, acc1[w]);
+        }
       }
-      if (j < jn) acc0 = fma((double)S[(i64)(j0 + j) * n + i], cs[j], acc0);
+      if (j < jn) {
+        T s0[W];
+        ldv(Sj + (i64)j * ld, e, n, s0);
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc0[w] = fma(s0[w], cs[j], acc0[w]);
+      }
     }
   }
-  if (i < n) p[i] = (T)((double)p[i] - (acc0 + acc1));
+  if (e < n) {
+    T pv[W];
+    ldv(p, e, n, pv);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (e + w < n) p[e + w] = pv[w] - (acc0[w] + acc1[w]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +312,7 @@ void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_
 }
 template <typename T>
 void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s) {
-  k_update<T><<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q);
+  k_update<T><<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q, store_ld(n));
   GPFVM_LAUNCH_CHECK();
 }
 template <typename T>
@@ -248,24 +320,22 @@ void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s) {
   k_pupdate<T><<<ceil_div(n, RT), RT, 0, s>>>(r, p, n, st);
   GPFVM_LAUNCH_CHECK();
 }
+i64 store_ld(i64 n) { return (n + 31) / 32 * 32; }
 int reorth_chunks(i64 n) {
-  int c = ceil_div(n, 4096);
-  return c < 1 ? 1 : c;
+  const i64 c = (n + RCH - 1) / RCH;
+  return c < 1 ? 1 : (int)c;
 }
 template <typename T>
-void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, double* part2, double* coef,
+void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
                const double* eta_hist, cudaStream_t s) {
+  const i64 ld = store_ld(n);
   const int nchunk = reorth_chunks(n);
-  const int chunk = (int)((n + nchunk - 1) / nchunk);
-  int gy = ceil_div(cap, RT / 32);
-  const int target = 4 * 152;
-  if ((i64)gy * nchunk > target) gy = (target + nchunk - 1) / nchunk;
-  if (gy < 1) gy = 1;
-  k_reorth_dots<T><<<dim3(nchunk, gy), RT, 0, s>>>(Q, p, n, chunk, st, part2);
+  // split the directions over blockIdx.y until about four CTAs per SM are busy
+  int gy = (4 * 152 + nchunk - 1) / nchunk;
+  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
+  k_reorth_dots<T><<<dim3(nchunk, gy), RT, 0, s>>>(Q, ld, p, n, st, part2, eta_hist, coef);
   GPFVM_LAUNCH_CHECK();
-  k_reorth_coef<<<ceil_div(cap, RT), RT, 0, s>>>(part2, nchunk, eta_hist, st, coef);
-  GPFVM_LAUNCH_CHECK();
-  k_reorth_apply<T><<<ceil_div(n, RT), RT, 0, s>>>(S, p, n, st, coef);
+  k_reorth_apply<T><<<ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s>>>(S, ld, p, n, st, coef);
   GPFVM_LAUNCH_CHECK();
 }
 
@@ -274,7 +344,7 @@ void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, 
   template void cg_downdate<T>(const T*, double*, i64, const CGState*, cudaStream_t);                      \
   template void cg_update<T>(T*, T*, const T*, const T*, i64, CGState*, T*, T*, cudaStream_t);             \
   template void cg_pupdate<T>(const T*, T*, i64, const CGState*, cudaStream_t);                            \
-  template void cg_reorth<T>(const T*, const T*, T*, i64, int, const CGState*, double*, double*, const double*, \
+  template void cg_reorth<T>(const T*, const T*, T*, i64, int, CGState*, double*, double*, const double*,       \
                              cudaStream_t);
 GPFVM_CG_INST(double)
 GPFVM_CG_INST(float)
@@ -312,6 +382,16 @@ __global__ void k_norm2(const double* __restrict__ v, i64 n, double* out, double
 }
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s) {
   k_norm2<<<reduce_grid(n), RT, 0, s>>>(v, n, out, st->part, &st->ticket[3]);
+  GPFVM_LAUNCH_CHECK();
+}
+
+__global__ void k_loop_ctl(CGState* st, cudaGraphConditionalHandle h) {
+  const int n = ++st->loops;
+  const int lim = min(max(st->max_iter, 0), 1 << 24) + 2;  // bounded whatever the CG state holds
+  cudaGraphSetConditional(h, (!st->done && n < lim) ? 1u : 0u);
+}
+void loop_ctl(CGState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_ctl<<<1, 1, 0, s>>>(st, h);
   GPFVM_LAUNCH_CHECK();
 }
 

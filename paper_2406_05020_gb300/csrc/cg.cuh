@@ -11,12 +11,16 @@ struct CGState {
   double aux[8];
   int k, done, converged, status, max_iter, cap;
   int pad[2];
+  int loops, pad2;  // passes of the device-side iteration loop (reset by cg_init)
   unsigned int ticket[8];
   double part[CG_MAX_PART];
 };
 
 int reduce_grid(i64 n);
+// chunks of the reorthogonalisation dots (the partial-sum buffer holds cap x chunks)
 int reorth_chunks(i64 n);
+// row stride (elements) of the direction stores S and Q: n rounded up to 32
+i64 store_ld(i64 n);
 // r = p = b (scaled by 1/sqrt(*nrm2) when nrm2 is given; st->aux[7] keeps the
 // inverse factor), x = 0, and the scalar header reset for a new run.
 template <typename TB, typename T>
@@ -30,9 +34,12 @@ void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* 
 template <typename T>
 void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s);
 template <typename T>
-void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, const CGState* st, double* part2, double* coef,
+void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
                const double* eta_hist, cudaStream_t s);
 // x += (*scale) d  (scale defaults to 1)
+// Control node of a device-side CG loop (a graph WHILE node): one more pass
+// while the CG state is not done, and never more than max_iter + 2 passes.
+void loop_ctl(CGState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale = nullptr);
 void f2d(const float* a, double* b, i64 n, cudaStream_t s);
 void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s);

@@ -34,6 +34,32 @@ struct LaunchUnit {
   size_t offset;  // byte offset of the op table in the plan's table buffer
 };
 
+// Auxiliary streams on which the independent launches of one phase run
+// side by side (fork from the plan's stream at the phase start, join at its
+// end); under stream capture they become parallel graph branches.
+struct Fan {
+  static constexpr int NAUX = 3;
+  cudaStream_t aux[NAUX] = {};
+  cudaEvent_t fork = nullptr, join[NAUX] = {};
+  void create() {
+    for (int a = 0; a < NAUX; ++a) {
+      GPFVM_CUDA(cudaStreamCreateWithFlags(&aux[a], cudaStreamNonBlocking));
+      GPFVM_CUDA(cudaEventCreateWithFlags(&join[a], cudaEventDisableTiming));
+    }
+    GPFVM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  }
+  void destroy() {
+    for (int a = 0; a < NAUX; ++a) {
+      if (aux[a]) cudaStreamDestroy(aux[a]);
+      if (join[a]) cudaEventDestroy(join[a]);
+      aux[a] = nullptr;
+      join[a] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+  }
+};
+
 class Plan {
  public:
   std::vector<GemmSeg> segs;
@@ -45,6 +71,7 @@ class Plan {
   std::vector<std::vector<LaunchUnit>> phase_units;  // indexed by phase id
   int n_phases = 0;
   const int* skip = nullptr;  // device flag: when set, every GEMM/GEMV of the plan is a no-op
+  const Fan* fan = nullptr;    // optional: run the independent launches of a phase concurrently
 
   ~Plan() { release(); }
   void release() {
@@ -68,6 +95,7 @@ class Plan {
       phase_units = std::move(o.phase_units);
       n_phases = o.n_phases;
       skip = o.skip;
+      fan = o.fan;
       d_segs = o.d_segs; d_groups = o.d_groups; d_tables = o.d_tables;
       o.d_segs = nullptr; o.d_groups = nullptr; o.d_tables = nullptr;
     }
@@ -265,29 +293,62 @@ class Plan {
       GPFVM_CUDA(cudaMemcpy(d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice));
     }
   }
+  void run_op(const PlanOp& op, cudaStream_t st) const {
+    if (op.kind == PlanOp::GEMM) launch_gemm64(op.g, st);
+    else if (op.kind == PlanOp::GEMV)
+      launch_gemv64(op.m, op.n, op.A, op.lda, op.x, op.y, op.alpha, op.beta, op.tri, st, skip);
+    else if (op.kind == PlanOp::GEMV32)
+      launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, (float)op.alpha,
+                    (float)op.beta, op.tri, st, skip);
+    else op.fn(st);
+  }
+  void run_unit(const LaunchUnit& u, cudaStream_t st) const {
+    if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
+    else launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
+  }
+  // Ops of one phase are consecutive; its merged launch units and FUNC ops
+  // are mutually independent.  Without a fan they run in order on st.
   void run(cudaStream_t st) const {
-    int done_phase = -1;
-    for (auto& op : ops) {
-      if (op.phase >= 0) {
-        if (op.phase == done_phase) {
-          if (op.kind == PlanOp::FUNC) op.fn(st);
-          continue;
-        }
-        done_phase = op.phase;
-        for (const LaunchUnit& u : phase_units[op.phase]) {
-          if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
-          else launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
-        }
-        if (op.kind == PlanOp::FUNC) op.fn(st);
+    size_t i = 0;
+    while (i < ops.size()) {
+      const PlanOp& op = ops[i];
+      if (op.phase < 0) {
+        run_op(op, st);
+        ++i;
         continue;
       }
-      if (op.kind == PlanOp::GEMM) launch_gemm64(op.g, st);
-      else if (op.kind == PlanOp::GEMV)
-        launch_gemv64(op.m, op.n, op.A, op.lda, op.x, op.y, op.alpha, op.beta, op.tri, st, skip);
-      else if (op.kind == PlanOp::GEMV32)
-        launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, (float)op.alpha,
-                      (float)op.beta, op.tri, st, skip);
-      else op.fn(st);
+      const int ph = op.phase;
+      size_t j = i;
+      while (j < ops.size() && ops[j].phase == ph) ++j;
+      int lanes = (int)phase_units[ph].size();
+      for (size_t t = i; t < j; ++t) lanes += ops[t].kind == PlanOp::FUNC;
+      if (!fan || lanes <= 1) {
+        for (const LaunchUnit& u : phase_units[ph]) run_unit(u, st);
+        for (size_t t = i; t < j; ++t)
+          if (ops[t].kind == PlanOp::FUNC) ops[t].fn(st);
+      } else {
+        GPFVM_CUDA(cudaEventRecord(fan->fork, st));
+        bool used[Fan::NAUX] = {};
+        int lane = 0;
+        auto lane_stream = [&](int l) {
+          if (l == 0) return st;
+          const int a = (l - 1) % Fan::NAUX;
+          if (!used[a]) {
+            GPFVM_CUDA(cudaStreamWaitEvent(fan->aux[a], fan->fork, 0));
+            used[a] = true;
+          }
+          return fan->aux[a];
+        };
+        for (const LaunchUnit& u : phase_units[ph]) run_unit(u, lane_stream(lane++));
+        for (size_t t = i; t < j; ++t)
+          if (ops[t].kind == PlanOp::FUNC) ops[t].fn(lane_stream(lane++));
+        for (int a = 0; a < Fan::NAUX; ++a)
+          if (used[a]) {
+            GPFVM_CUDA(cudaEventRecord(fan->join[a], fan->aux[a]));
+            GPFVM_CUDA(cudaStreamWaitEvent(st, fan->join[a], 0));
+          }
+      }
+      i = j;
     }
   }
   int launches() const { return (int)ops.size(); }
