@@ -13,6 +13,7 @@
 #include <chrono>
 #include <thread>
 #include <deque>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -202,6 +203,10 @@ struct gpfvm_problem {
   Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32, p_mv32tc, p_mvv32tc, p_pp32tc;
   int modeprods_pp = 0;
   Fan fan;  // side streams for the independent launches of a plan phase
+  // GPFVM_HOST_LOOP=1: the host replays the captured iteration pass by pass
+  // instead of a device-side WHILE loop (same kernels; for per-kernel profilers,
+  // which see kernels inside conditional graph bodies only as one workload)
+  bool host_loop = false;
 
   // ---- state
   bool assembled = false, solved = false, vB_ready = false, want_var_last = false;
@@ -1382,7 +1387,27 @@ double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
 // CG run with no host round trips.  *body_kernels receives the kernels of one
 // pass (the control kernel included).
 cudaGraphExec_t make_loop_graph(CGState* st_dev, cudaStream_t st, const std::function<void()>& body,
-                                long long* body_kernels) {
+                                long long* body_kernels, bool host_loop) {
+  if (host_loop) {  // one pass per launch; the host repeats it
+    cudaGraph_t g = nullptr;
+    const long long before = g_launches.load();
+    GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      body();
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(st, &dummy);
+      cudaGetLastError();
+      throw;
+    }
+    GPFVM_CUDA(cudaStreamEndCapture(st, &g));
+    *body_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(*body_kernels);
+    cudaGraphExec_t ex = nullptr;
+    GPFVM_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    return ex;
+  }
   cudaGraph_t g = nullptr;
   GPFVM_CUDA(cudaGraphCreate(&g, 0));
   try {
@@ -1462,16 +1487,36 @@ int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->graph || p->graph_key != key) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
-    p->graph = make_loop_graph(p->d_st, st, [&] { cg_iteration(p, reorth, want_var, st); }, &p->graph_kernels);
+    p->graph = make_loop_graph(p->d_st, st, [&] { cg_iteration(p, reorth, want_var, st); }, &p->graph_kernels,
+                               p->host_loop);
     p->graph_key = key;
   }
   return GPFVM_OK;
+}
+
+// Host-driven form of a CG run (GPFVM_HOST_LOOP): replays the one-pass graph
+// until the device state reports done; leaves the header copied to hst.
+void host_loop_run(cudaGraphExec_t g, long long kernels, CGState* dst, CGState* hst, cudaStream_t st) {
+  const int lim = std::max(dst ? hst->max_iter : 0, 0) + 2;
+  for (int pass = 0; pass < lim; ++pass) {
+    GPFVM_CUDA(cudaGraphLaunch(g, st));
+    count_launch(kernels);
+    GPFVM_CUDA(cudaMemcpyAsync(hst, dst, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (hst->done) break;
+  }
+  hst->loops = 0;  // launches already counted
 }
 
 // Enqueues the device-side CG loop (all iterations) and a copy of the scalar header.
 void solve_launch(gpfvm_problem* p, int, cudaStream_t st) {
   SolveRun& R = runs()[p];
   if (R.launched > 0) return;
+  if (p->host_loop) {
+    host_loop_run(p->graph, p->graph_kernels, p->d_st, p->h_st, st);
+    R.launched = R.o.max_iter;
+    return;
+  }
   GPFVM_CUDA(cudaGraphLaunch(p->graph, st));
   R.launched = R.o.max_iter;
   copy_header_to_host(p, st);
@@ -1610,6 +1655,9 @@ void mixed_launch(gpfvm_problem* p, int, cudaStream_t st) {
     norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
     copy_header_to_host(p, st);
     R.mstate = 1;
+  } else if (R.mstate == 2 && R.launched == 0 && p->host_loop) {
+    host_loop_run(p->graph32, p->graph32_kernels, p->d_st32, p->h_st32, st);
+    R.launched = R.lim;
   } else if (R.mstate == 2 && R.launched == 0) {
     GPFVM_CUDA(cudaGraphLaunch(p->graph32, st));  // the whole inner run
     R.launched = R.lim;
@@ -1643,7 +1691,8 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     if (!p->graph32 || p->graph32_key != key) {
       if (p->graph32) cudaGraphExecDestroy(p->graph32);
       p->graph32 = nullptr;
-      p->graph32 = make_loop_graph(p->d_st32, st, [&] { cg_iteration32(p, var_now, st); }, &p->graph32_kernels);
+      p->graph32 = make_loop_graph(p->d_st32, st, [&] { cg_iteration32(p, var_now, st); }, &p->graph32_kernels,
+                                   p->host_loop);
       p->graph32_key = key;
     }
     R.launched = 0;
@@ -1792,6 +1841,10 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
   }
   for (int a = 0; a < p->nterms; ++a)
     for (int i = 0; i < p->d; ++i) need_factor(p.get(), i, 0, p->alpha[a][i], 2, 0);
+  {
+    const char* e = std::getenv("GPFVM_HOST_LOOP");
+    p->host_loop = e && std::atoi(e) != 0;
+  }
   alloc_all(p.get());
   *out = p.release();
   return GPFVM_OK;
