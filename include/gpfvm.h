@@ -213,6 +213,8 @@ int64_t gpfvm_launch_count(void);
  *   what 5: variance downdate sum (P)  what 6: eta_j (iterations)
  *   what 7: device time (ms) of the last assemble, solve and query (3 values)
  *   what 8: refinement steps of the last mixed-precision solve (1 value)
+ *   what 9: eigensolver sweeps of the structured IC/BC stage, (FP32, FP64)
+ *           per axis (2 * ndim values; 0 written without that stage)
  * Returns the number of doubles written or a negative error. */
 int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream);
 

@@ -173,6 +173,7 @@ struct gpfvm_problem {
   float *f_QK[3] = {}, *f_Ft = nullptr, *f_F = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_hK = nullptr,
         *f_tR = nullptr, *f_uR = nullptr;
   JacobiJob* d_jac = nullptr;
+  int* d_jac_sweeps = nullptr;  // 2 per axis: FP32 and FP64 sweeps of the last assembly
   // tensor-core G_PP (split TF32): factor splits, rotated intermediates, op tables
   bool tc_ok = false, use_tc = false;
   float* f_tcsplit = nullptr;
@@ -1155,6 +1156,8 @@ void alloc_all(gpfvm_problem* p) {
     const i64 MK = p->MK, MR = p->MR;
     p->d_A = m.alloc<double>(M * M);
     std::vector<JacobiJob> jobs(p->d);
+    p->d_jac_sweeps = m.alloc<int>(2 * p->d);
+    GPFVM_CUDA(cudaMemset(p->d_jac_sweeps, 0, sizeof(int) * 2 * p->d));
     for (int i = 0; i < p->d; ++i) {
       const int n = p->sets[0].n[i];
       p->nK[i] = n;
@@ -1163,7 +1166,8 @@ void alloc_all(gpfvm_problem* p) {
       p->f_QK[i] = m.alloc<float>((i64)n * n);
       p->d_H[i] = m.alloc<double>((i64)n * p->npred[i]);
       p->d_Hsq[i] = m.alloc<double>((i64)n * p->npred[i]);
-      jobs[i] = JacobiJob{p->d_fac + p->fac_off.at(FKey(i, 1, 0, 1, 0)), p->d_QK[i], p->d_lam[i], n, 1e-14};
+      jobs[i] = JacobiJob{p->d_fac + p->fac_off.at(FKey(i, 1, 0, 1, 0)), p->d_QK[i], p->d_lam[i], n, 1e-14,
+                          p->d_jac_sweeps + 2 * i};
     }
     p->d_jac = m.alloc<JacobiJob>(p->d);
     GPFVM_CUDA(cudaMemcpy(p->d_jac, jobs.data(), sizeof(JacobiJob) * p->d, cudaMemcpyHostToDevice));
@@ -2022,6 +2026,15 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
     case 8: {  // refinement steps of the last mixed-precision solve
       host_out[0] = p->last_outer;
       return 1;
+    }
+    case 9: {  // eigensolver sweeps (FP32, FP64) per axis of the structured IC/BC stage
+      if (!p->d_jac_sweeps) return 0;
+      if (capacity < 2 * p->d) return GPFVM_ERR_INVALID_ARG;
+      int sw[2 * GPFVM_MAX_DIM] = {};
+      GPFVM_CUDA(cudaMemcpyAsync(sw, p->d_jac_sweeps, sizeof(int) * 2 * p->d, cudaMemcpyDeviceToHost, st));
+      GPFVM_CUDA(cudaStreamSynchronize(st));
+      for (int i = 0; i < 2 * p->d; ++i) host_out[i] = sw[i];
+      return 2 * p->d;
     }
     case 7: {  // timing of the last assemble / solve / query (ms)
       if (capacity < 3) return GPFVM_ERR_INVALID_ARG;

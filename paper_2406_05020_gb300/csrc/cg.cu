@@ -39,6 +39,7 @@ __device__ double sum_partials(const double* part, int n, double* smem) {
 template <typename TB, typename T>
 __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                                               T* __restrict__ p, i64 n, CGState* st, const double* nrm2) {
+  pdl_wait();
   __shared__ double red[32];
   // optional normalisation to a unit right-hand side (x0 = 0): b / ||b||
   double sc = 1.0;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __rest
 template <typename T>
 __global__ void __launch_bounds__(RT) k_dot_eta(const T* __restrict__ p, const T* __restrict__ q, i64 n,
                                                  CGState* st, double* __restrict__ eta_hist) {
+  pdl_wait();
   if (st->done) return;
   __shared__ double red[32];
   double acc = 0.0;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(RT) k_dot_eta(const T* __restrict__ p, const T
 template <typename T>
 __global__ void __launch_bounds__(RT) k_downdate(const T* __restrict__ u, double* __restrict__ down, i64 n,
                                                   const CGState* st) {
+  pdl_wait();
   if (st->done) return;
   const double inv = 1.0 / st->eta;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
@@ -112,6 +115,7 @@ template <typename T>
 __global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                 const T* __restrict__ q, i64 n, CGState* st, T* __restrict__ S,
                                                 T* __restrict__ Q, i64 ld) {
+  pdl_wait();
   if (st->done) return;
   __shared__ double red[32];
   const double alpha = st->rr / st->eta;
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(RT) k_pupdate(const T* __restrict__ r, T* __restrict__ p, i64 n,
                                                  const CGState* st) {
+  pdl_wait();
   if (st->done) return;
   const double beta = st->beta;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT)
@@ -192,6 +197,7 @@ template <typename T>
 __global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64 ld, const T* __restrict__ p, i64 n,
                                                      CGState* st, double* __restrict__ part2,
                                                      const double* __restrict__ eta_hist, double* __restrict__ coef) {
+  pdl_wait();
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   constexpr int NV = RCH / (32 * W);  // vectors per lane
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64
 template <typename T>
 __global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, i64 ld, T* __restrict__ p, i64 n,
                                                       const CGState* st, const double* __restrict__ coef) {
+  pdl_wait();
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   __shared__ T cs[1024];
@@ -297,28 +304,23 @@ int reduce_grid(i64 n) {
 
 template <typename TB, typename T>
 void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2) {
-  k_init<TB, T><<<reduce_grid(n), RT, 0, s>>>(b, x, r, p, n, st, nrm2);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_init<TB, T>, reduce_grid(n), RT, 0, s, b, x, r, p, n, st, nrm2);
 }
 template <typename T>
 void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
-  k_dot_eta<T><<<reduce_grid(n), RT, 0, s>>>(p, q, n, st, eta_hist);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_dot_eta<T>, reduce_grid(n), RT, 0, s, p, q, n, st, eta_hist);
 }
 template <typename T>
 void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_t s) {
-  k_downdate<T><<<ceil_div(n, RT), RT, 0, s>>>(u, down, n, st);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_downdate<T>, ceil_div(n, RT), RT, 0, s, u, down, n, st);
 }
 template <typename T>
 void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s) {
-  k_update<T><<<reduce_grid(n), RT, 0, s>>>(x, r, p, q, n, st, S, Q, store_ld(n));
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_update<T>, reduce_grid(n), RT, 0, s, x, r, p, q, n, st, S, Q, store_ld(n));
 }
 template <typename T>
 void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s) {
-  k_pupdate<T><<<ceil_div(n, RT), RT, 0, s>>>(r, p, n, st);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_pupdate<T>, ceil_div(n, RT), RT, 0, s, r, p, n, st);
 }
 i64 store_ld(i64 n) { return (n + 31) / 32 * 32; }
 int reorth_chunks(i64 n) {
@@ -333,10 +335,8 @@ void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double
   // split the directions over blockIdx.y until about four CTAs per SM are busy
   int gy = (4 * 152 + nchunk - 1) / nchunk;
   gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
-  k_reorth_dots<T><<<dim3(nchunk, gy), RT, 0, s>>>(Q, ld, p, n, st, part2, eta_hist, coef);
-  GPFVM_LAUNCH_CHECK();
-  k_reorth_apply<T><<<ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s>>>(S, ld, p, n, st, coef);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, Q, ld, p, n, st, part2, eta_hist, coef);
+  launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, S, ld, p, n, st, coef);
 }
 
 #define GPFVM_CG_INST(T)                                                                                    \
@@ -356,17 +356,18 @@ template void cg_init<double, float>(const double*, float*, float*, float*, i64,
 // ---- small vector helpers -------------------------------------------------
 __global__ void k_axpby(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
                         double sa, double sb, i64 n) {
+  pdl_wait();
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) out[i] = sa * a[i] + sb * b[i];
 }
 void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s) {
   if (n <= 0) return;
   int g = ceil_div(n, RT);
   if (g > 4096) g = 4096;
-  k_axpby<<<g, RT, 0, s>>>(a, b, out, sa, sb, n);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_axpby, g, RT, 0, s, a, b, out, sa, sb, n);
 }
 
 __global__ void k_norm2(const double* __restrict__ v, i64 n, double* out, double* part, unsigned int* ticket) {
+  pdl_wait();
   __shared__ double red[32];
   double acc = 0.0;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) acc = fma(v[i], v[i], acc);
@@ -381,21 +382,21 @@ __global__ void k_norm2(const double* __restrict__ v, i64 n, double* out, double
   }
 }
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s) {
-  k_norm2<<<reduce_grid(n), RT, 0, s>>>(v, n, out, st->part, &st->ticket[3]);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_norm2, reduce_grid(n), RT, 0, s, v, n, out, st->part, &st->ticket[3]);
 }
 
 __global__ void k_loop_ctl(CGState* st, cudaGraphConditionalHandle h) {
+  pdl_wait();
   const int n = ++st->loops;
   const int lim = min(max(st->max_iter, 0), 1 << 24) + 2;  // bounded whatever the CG state holds
   cudaGraphSetConditional(h, (!st->done && n < lim) ? 1u : 0u);
 }
 void loop_ctl(CGState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
-  k_loop_ctl<<<1, 1, 0, s>>>(st, h);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_loop_ctl, 1, 1, 0, s, st, h);
 }
 
 __global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n, const double* scale) {
+  pdl_wait();
   const double a = scale ? *scale : 1.0;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] = fma(a, (double)d[i], x[i]);
 }
@@ -403,8 +404,7 @@ void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* sca
   if (n <= 0) return;
   int g = ceil_div(n, RT);
   if (g > 4096) g = 4096;
-  k_add_f2d<<<g, RT, 0, s>>>(x, d, n, scale);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_add_f2d, g, RT, 0, s, x, d, n, scale);
 }
 
 __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, i64 n) {

@@ -43,6 +43,30 @@ void count_launch(long long n = 1);
     ::gpfvm::count_launch();             \
   } while (0)
 
+// Launch with programmatic dependent launch allowed: the grid may be scheduled
+// while its stream predecessor drains.  Every kernel launched this way calls
+// pdl_wait() before it touches memory that an earlier kernel writes.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  GPFVM_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+  count_launch();
+}
+// Waits until the grids this one depends on have completed and their memory
+// operations are visible (a no-op for a grid launched without that dependency).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+
 inline int ceil_div(i64 a, i64 b) { return (int)((a + b - 1) / b); }
 
 // Fixed-order block reduction of doubles (deterministic for a fixed blockDim).

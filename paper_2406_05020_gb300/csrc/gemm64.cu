@@ -14,18 +14,44 @@
 
 namespace gpfvm {
 
-// One output tile (BM x 64) of one (batch, group) entry; all threads of the
-// CTA must call it together (it synchronises through shared memory).
+// cp.async (global -> shared, bypassing registers) of one element; src_bytes
+// = 0 zero-fills the destination without reading the source.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// pipeline depth: shared memory per CTA stays below the 48 KB static limit
 template <typename T, int BM>
-__device__ __forceinline__ void gemm_tile(const GemmDesc& g, int bx, int by, i64 zb, T (*As)[BM + 1],
-                                          T (*Bs)[65]) {
+struct GemmStages {
+  static constexpr int value = sizeof(T) == 8 ? (BM == 64 ? 2 : (BM == 32 ? 3 : 4)) : 4;
+};
+
+// One output tile (BM x 64) of one (batch, group) entry; all threads of the
+// CTA must call it together (it synchronises through shared memory).  The
+// (segment, 16-wide K chunk) pairs form one sequence of stages that cp.async
+// streams into a ring of STAGES shared-memory buffers, so up to STAGES - 1
+// chunks are in flight while one is multiplied: a short tile pays the
+// global-load latency about once instead of once per chunk.  The arithmetic
+// order (per segment: chunks in K order, then acc += alpha * part) is fixed.
+template <typename T, int BM>
+__device__ __forceinline__ void gemm_tile(const GemmDesc& g, int bx, int by, i64 zb, T (*As)[16][BM + 1],
+                                          T (*Bs)[16][65]) {
   constexpr int BN = 64, BK = 16;
   constexpr int RM = BM / 16;  // rows per thread (4, 2, 1)
+  constexpr int STAGES = GemmStages<T, BM>::value;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int j0 = bx * BN, i0 = by * BM;
   if ((g.tri & TRI_C_LOWER) && j0 > i0 + BM - 1) return;
-  {
   const int grp = (int)(zb % g.n_groups);
   const int b = (int)(zb / g.n_groups);
   const GemmGroup G = g.groups[grp];
@@ -35,62 +61,76 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& g, int bx, int by, i64
   if (g.tri & TRI_A_UPPER) k_lo = max(k_lo, i0);
   if (g.tri & TRI_B_UPPER) k_hi = min(k_hi, j0 + BN);
   if (g.tri & TRI_B_LOWER) k_lo = max(k_lo, j0);
-
-  T acc[RM][4];
-#pragma unroll
-  for (int r = 0; r < RM; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+  const int nkc = k_hi > k_lo ? (k_hi - k_lo + BK - 1) / BK : 0;
+  const int nst = G.nseg * nkc;
 
   const bool a_kfast = (g.a_cs == 1);
   const bool b_jfast = (g.b_cs == 1);
 
-  for (int s = 0; s < G.nseg; ++s) {
-    const GemmSeg S = g.segs[G.seg0 + s];
+  // issue the copies of stage st into ring buffer buf
+  auto issue = [&](int st, int buf) {
+    const int sg = st / nkc, k0 = k_lo + (st % nkc) * BK;
+    const GemmSeg S = g.segs[G.seg0 + sg];
     const T* __restrict__ A = reinterpret_cast<const T*>(S.A) + (i64)b * g.a_bs;
     const T* __restrict__ B = reinterpret_cast<const T*>(S.B) + (i64)b * g.b_bs;
-    const T alpha = (T)S.alpha;
-    T part[RM][4];
-#pragma unroll
-    for (int r = 0; r < RM; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) part[r][c] = T(0);
-
-    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
-      // stage A tile (BM x BK)
-      for (int e = tid; e < BM * BK; e += 256) {
-        int ii, kk;
-        if (a_kfast) { ii = e / BK; kk = e % BK; } else { ii = e % BM; kk = e / BM; }
-        const int gi = i0 + ii, gk = k0 + kk;
-        As[kk][ii] = (gi < g.m && gk < k_hi) ? A[(i64)gi * g.a_rs + (i64)gk * g.a_cs] : T(0);
-      }
-      // stage B tile (BK x BN)
-      for (int e = tid; e < BK * BN; e += 256) {
-        int kk, jj;
-        if (b_jfast) { kk = e / BN; jj = e % BN; } else { kk = e % BK; jj = e / BK; }
-        const int gk = k0 + kk, gj = j0 + jj;
-        Bs[kk][jj] = (gj < g.n && gk < k_hi) ? B[(i64)gk * g.b_rs + (i64)gj * g.b_cs] : T(0);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        T a[RM], bb[4];
-#pragma unroll
-        for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + 16 * r];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bb[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-        for (int r = 0; r < RM; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) part[r][c] = fma(a[r], bb[c], part[r][c]);
-      }
-      __syncthreads();
+    for (int e = tid; e < BM * BK; e += 256) {
+      int ii, kk;
+      if (a_kfast) { ii = e / BK; kk = e % BK; } else { ii = e % BM; kk = e / BM; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      const bool ok = gi < g.m && gk < k_hi;
+      cp_async_el(&As[buf][kk][ii], ok ? A + (i64)gi * g.a_rs + (i64)gk * g.a_cs : A, ok);
     }
+    for (int e = tid; e < BK * BN; e += 256) {
+      int kk, jj;
+      if (b_jfast) { kk = e / BN; jj = e % BN; } else { kk = e % BK; jj = e / BK; }
+      const int gk = k0 + kk, gj = j0 + jj;
+      const bool ok = gj < g.n && gk < k_hi;
+      cp_async_el(&Bs[buf][kk][jj], ok ? B + (i64)gk * g.b_rs + (i64)gj * g.b_cs : B, ok);
+    }
+  };
+
+  T acc[RM][4], part[RM][4];
 #pragma unroll
-    for (int r = 0; r < RM; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = fma(alpha, part[r][c], acc[r][c]);
+    for (int c = 0; c < 4; ++c) acc[r][c] = part[r][c] = T(0);
+
+#pragma unroll
+  for (int st = 0; st < STAGES - 1; ++st) {
+    if (st < nst) issue(st, st);
+    cp_async_commit();
   }
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait<STAGES - 2>();  // stage st has landed (for this thread)
+    __syncthreads();              // ... for all threads; buffer (st - 1) % STAGES is free again
+    if (st + STAGES - 1 < nst) issue(st + STAGES - 1, (st + STAGES - 1) % STAGES);
+    cp_async_commit();
+    const int buf = st % STAGES;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[RM], bb[4];
+#pragma unroll
+      for (int r = 0; r < RM; ++r) a[r] = As[buf][kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bb[c] = Bs[buf][kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[r][c] = fma(a[r], bb[c], part[r][c]);
+    }
+    if (st % nkc == nkc - 1) {  // last chunk of segment st / nkc
+      const T alpha = (T)g.segs[G.seg0 + st / nkc].alpha;
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][c] = fma(alpha, part[r][c], acc[r][c]);
+          part[r][c] = T(0);
+        }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();  // the ring is reused by the CTA's next tile
 
   T* __restrict__ C = reinterpret_cast<T*>(G.C) + (i64)b * g.c_bs;
   const T* __restrict__ D = G.D ? reinterpret_cast<const T*>(G.D) + (i64)b * g.d_bs : nullptr;
@@ -108,13 +148,13 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& g, int bx, int by, i64
       C[(i64)gi * g.c_rs + gj] = v;
     }
   }
-  }
 }
 
 template <typename T, int BM>
 __global__ void __launch_bounds__(256) gemm64_kernel(GemmDesc g) {
-  __shared__ T As[16][BM + 1];
-  __shared__ T Bs[16][65];
+  pdl_wait();
+  __shared__ T As[GemmStages<T, BM>::value][16][BM + 1];
+  __shared__ T Bs[GemmStages<T, BM>::value][16][65];
   if (g.skip && *g.skip) return;
   for (i64 zb = blockIdx.z; zb < (i64)g.batch * g.n_groups; zb += gridDim.z)
     gemm_tile<T, BM>(g, blockIdx.x, blockIdx.y, zb, As, Bs);
@@ -124,37 +164,43 @@ __global__ void __launch_bounds__(256) gemm64_kernel(GemmDesc g) {
 // tile) in one launch: CTA t works on tile t - ops[o].tile_begin of op o.
 template <typename T, int BM>
 __global__ void __launch_bounds__(256) multi_gemm_kernel(const MOp* __restrict__ ops, int nops, i64 total) {
-  __shared__ T As[16][BM + 1];
-  __shared__ T Bs[16][65];
+  __shared__ T As[GemmStages<T, BM>::value][16][BM + 1];
+  __shared__ T Bs[GemmStages<T, BM>::value][16][65];
+  bool waited = false;
   for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
+    // the op tables are written at plan build time: look them up before waiting
     int lo = 0, hi = nops - 1;
     while (lo < hi) {  // last op with tile_begin <= t
       const int mid = (lo + hi + 1) >> 1;
       if (ops[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
     const MOp& op = ops[lo];
-    if (op.g.skip && *op.g.skip) continue;
     const i64 r = t - op.tile_begin;
     const int bx = (int)(r % op.tiles_x);
     const int by = (int)((r / op.tiles_x) % op.tiles_y);
     const i64 zb = r / ((i64)op.tiles_x * op.tiles_y);
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+    }
+    if (op.g.skip && *op.g.skip) continue;
     gemm_tile<T, BM>(op.g, bx, by, zb, As, Bs);
   }
+  if (!waited) pdl_wait();
 }
 
 void launch_multi_gemm(const MOp* d_ops, int nops, i64 total, int f32, int bm, cudaStream_t st) {
   if (nops <= 0 || total <= 0) return;
   const int grid = (int)std::min<i64>(total, 152 * 16);
   if (f32) {
-    if (bm == 64) multi_gemm_kernel<float, 64><<<grid, 256, 0, st>>>(d_ops, nops, total);
-    else if (bm == 32) multi_gemm_kernel<float, 32><<<grid, 256, 0, st>>>(d_ops, nops, total);
-    else multi_gemm_kernel<float, 16><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    if (bm == 64) launch_pdl(multi_gemm_kernel<float, 64>, grid, 256, 0, st, d_ops, nops, total);
+    else if (bm == 32) launch_pdl(multi_gemm_kernel<float, 32>, grid, 256, 0, st, d_ops, nops, total);
+    else launch_pdl(multi_gemm_kernel<float, 16>, grid, 256, 0, st, d_ops, nops, total);
   } else {
-    if (bm == 64) multi_gemm_kernel<double, 64><<<grid, 256, 0, st>>>(d_ops, nops, total);
-    else if (bm == 32) multi_gemm_kernel<double, 32><<<grid, 256, 0, st>>>(d_ops, nops, total);
-    else multi_gemm_kernel<double, 16><<<grid, 256, 0, st>>>(d_ops, nops, total);
+    if (bm == 64) launch_pdl(multi_gemm_kernel<double, 64>, grid, 256, 0, st, d_ops, nops, total);
+    else if (bm == 32) launch_pdl(multi_gemm_kernel<double, 32>, grid, 256, 0, st, d_ops, nops, total);
+    else launch_pdl(multi_gemm_kernel<double, 16>, grid, 256, 0, st, d_ops, nops, total);
   }
-  GPFVM_LAUNCH_CHECK();
 }
 
 // Many GEMV ops in one launch, one warp per output row over all ops:
@@ -169,7 +215,8 @@ __global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict
     const int mid = (lo + hi + 1) >> 1;
     if (ops[mid].row_begin <= w) lo = mid; else hi = mid - 1;
   }
-  const MGemv& op = ops[lo];
+  const MGemv op = ops[lo];  // copied to registers before the wait
+  pdl_wait();
   if (op.skip && *op.skip) return;
   const int i = (int)(w - op.row_begin);
   int jlo = 0, jhi = op.n;
@@ -197,9 +244,8 @@ __global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict
 void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st) {
   if (nops <= 0 || total_rows <= 0) return;
   const int grid = ceil_div(total_rows * 32, 256);
-  if (f32) multi_gemv_kernel<float><<<grid, 256, 0, st>>>(d_ops, nops, total_rows);
-  else multi_gemv_kernel<double><<<grid, 256, 0, st>>>(d_ops, nops, total_rows);
-  GPFVM_LAUNCH_CHECK();
+  if (f32) launch_pdl(multi_gemv_kernel<float>, grid, 256, 0, st, d_ops, nops, total_rows);
+  else launch_pdl(multi_gemv_kernel<double>, grid, 256, 0, st, d_ops, nops, total_rows);
 }
 
 void launch_gemm64(const GemmDesc& g, cudaStream_t st) {
@@ -209,15 +255,14 @@ void launch_gemm64(const GemmDesc& g, cudaStream_t st) {
   if (z > 65535) z = 65535;  // the kernel strides over the remaining (batch, group) pairs
   dim3 grid(ceil_div(g.n, 64), ceil_div(g.m, BM), (unsigned)z);
   if (g.f32) {
-    if (BM == 64) gemm64_kernel<float, 64><<<grid, 256, 0, st>>>(g);
-    else if (BM == 32) gemm64_kernel<float, 32><<<grid, 256, 0, st>>>(g);
-    else gemm64_kernel<float, 16><<<grid, 256, 0, st>>>(g);
+    if (BM == 64) launch_pdl(gemm64_kernel<float, 64>, grid, 256, 0, st, g);
+    else if (BM == 32) launch_pdl(gemm64_kernel<float, 32>, grid, 256, 0, st, g);
+    else launch_pdl(gemm64_kernel<float, 16>, grid, 256, 0, st, g);
   } else {
-    if (BM == 64) gemm64_kernel<double, 64><<<grid, 256, 0, st>>>(g);
-    else if (BM == 32) gemm64_kernel<double, 32><<<grid, 256, 0, st>>>(g);
-    else gemm64_kernel<double, 16><<<grid, 256, 0, st>>>(g);
+    if (BM == 64) launch_pdl(gemm64_kernel<double, 64>, grid, 256, 0, st, g);
+    else if (BM == 32) launch_pdl(gemm64_kernel<double, 32>, grid, 256, 0, st, g);
+    else launch_pdl(gemm64_kernel<double, 16>, grid, 256, 0, st, g);
   }
-  GPFVM_LAUNCH_CHECK();
 }
 
 // One warp per row: y(i) = alpha * sum_j A(i,j) x(j) + beta y(i).
@@ -225,6 +270,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) gemv_kernel(int m, int n, const T* __restrict__ A, i64 lda,
                                                    const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
                                                    int tri, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -250,15 +296,13 @@ __global__ void __launch_bounds__(256) gemv_kernel(int m, int n, const T* __rest
 void launch_gemv64(int m, int n, const double* A, i64 lda, const double* x, double* y, double alpha,
                    double beta, int tri, cudaStream_t st, const int* skip) {
   if (m <= 0) return;
-  gemv_kernel<double><<<ceil_div((i64)m * 32, 256), 256, 0, st>>>(m, n, A, lda, x, y, alpha, beta, tri, skip);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(gemv_kernel<double>, ceil_div((i64)m * 32, 256), 256, 0, st, m, n, A, lda, x, y, alpha, beta, tri, skip);
 }
 
 void launch_gemv32(int m, int n, const float* A, i64 lda, const float* x, float* y, float alpha, float beta, int tri,
                    cudaStream_t st, const int* skip) {
   if (m <= 0) return;
-  gemv_kernel<float><<<ceil_div((i64)m * 32, 256), 256, 0, st>>>(m, n, A, lda, x, y, alpha, beta, tri, skip);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(gemv_kernel<float>, ceil_div((i64)m * 32, 256), 256, 0, st, m, n, A, lda, x, y, alpha, beta, tri, skip);
 }
 
 __global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, i64 n) {

@@ -25,16 +25,20 @@ constexpr int JAC_MAX_N = 96;
 // (the FP64 pipe of one SM is slow); V is then re-orthonormalised in FP64
 // (modified Gram-Schmidt), U = A V is recomputed in FP64 and FP64 sweeps
 // polish to the rounding level.  A pair counts as converged when its cosine
-// is below 1e-15 or its inner product is at the rounding level of the largest
-// column, |c| <= 4e-16 ||A||_F (|u_p| + |u_q|): columns of tiny eigenvalues
-// carry rounding noise of that size and would otherwise keep rotating.
+// is below the phase's target (about the rounding level of n-term dot
+// products), or its inner product is at the rounding level of the largest
+// column, |c| <= 4 eps ||A||_F (|u_p| + |u_q|), or both columns are below the
+// rounding floor n eps ||A||_F of U = A V: such columns hold noise whose
+// mutual angle is meaningless, and rotating them kept sweeps from converging.
 // Sweeps are bounded in both phases.
 template <typename T>
-__device__ void jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, double tol_abs, int max_sweeps,
-                              double* maxrot) {
+__device__ int jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, double tol_abs, double noise,
+                             int max_sweeps, double* maxrot) {
   const int np = (n + 1) & ~1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  const double noise2 = noise * noise * fro * fro;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *maxrot = 0.0;
     __syncthreads();
     double local_max = 0.0;
@@ -59,6 +63,8 @@ __device__ void jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, dou
         }
         if (a == T(0) || b == T(0) || fabs((double)c) <= tol_abs * fro * (sqrt((double)a) + sqrt((double)b)))
           continue;
+        // both columns at the rounding floor of U = A V: their mutual angle is noise
+        if ((double)a <= noise2 && (double)b <= noise2) continue;
         const T rot = fabs(c) / sqrt(a * b);
         if ((double)rot < tol_rot) continue;
         local_max = fmax(local_max, (double)rot);
@@ -80,8 +86,9 @@ __device__ void jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, dou
     __syncthreads();
     const bool done = *maxrot < tol_rot * 10.0;
     __syncthreads();
-    if (done) break;
+    if (done) return sweep + 1;
   }
+  return sweep;
 }
 
 __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restrict__ jobs) {
@@ -109,8 +116,10 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
   }
   __syncthreads();
   const double fro = sqrt(fro2);
-  // phase 1: FP32 sweeps to about single precision
-  jacobi_sweeps<float>(Uf, Vf, n, fro, 1e-6, 4e-8, 30, &maxrot);
+  // phase 1: FP32 sweeps until the largest rotation of a sweep is below 1e-4
+  // (FP32 dot products carry ~n * 6e-8 of rounding, so tighter targets only
+  // rotate on noise); the FP64 polish converges quadratically from there
+  const int sw32 = jacobi_sweeps<float>(Uf, Vf, n, fro, 1e-5, 4e-8, n * 6e-8, 30, &maxrot);
   // re-orthonormalise V in FP64 (modified Gram-Schmidt over its columns)
   for (int e = tid; e < n * n; e += blockDim.x) V[e] = (double)Vf[e];
   __syncthreads();
@@ -142,8 +151,14 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
     U[e] = s;
   }
   __syncthreads();
-  // phase 2: FP64 polish
-  jacobi_sweeps<double>(U, V, n, fro, 1e-15, 4e-16, 12, &maxrot);
+  // phase 2: FP64 polish to the rounding level of n-term FP64 dot products
+  // (~n * 1.1e-16): smaller rotations are noise, and chasing them made every
+  // polish run all of its sweeps
+  const int sw64 = jacobi_sweeps<double>(U, V, n, fro, 2e-14, 4e-16, n * 1.2e-16, 12, &maxrot);
+  if (J.sweeps && tid == 0) {
+    J.sweeps[0] = sw32;
+    J.sweeps[1] = sw64;
+  }
   // eigenvalues = column norms of U, eigenvectors = columns of V
   for (int j = warp; j < n; j += nw) {
     double s = 0.0;
@@ -193,6 +208,7 @@ void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0,
 // X[r][m] *= lt[m]^pw for rows r < rows (pw = -1 or -1/2); also a float copy if Xf
 template <typename T>
 __global__ void k_scale_cols(T* __restrict__ X, int rows, i64 cols, const double* __restrict__ lt, double pw) {
+  pdl_wait();
   const i64 tot = (i64)rows * cols;
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
     const double l = lt[e % cols];
@@ -205,16 +221,14 @@ void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cuda
   if (tot <= 0) return;
   int g = ceil_div(tot, 256);
   if (g > 8192) g = 8192;
-  k_scale_cols<double><<<g, 256, 0, st>>>(X, rows, cols, lt, pw);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_scale_cols<double>, g, 256, 0, st, X, rows, cols, lt, pw);
 }
 void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st) {
   const i64 tot = (i64)rows * cols;
   if (tot <= 0) return;
   int g = ceil_div(tot, 256);
   if (g > 8192) g = 8192;
-  k_scale_cols<float><<<g, 256, 0, st>>>(X, rows, cols, lt, pw);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(k_scale_cols<float>, g, 256, 0, st, X, rows, cols, lt, pw);
 }
 
 // out[m] = 1/lt[m] (the weight tensor of the A^-1 quadratic form)

@@ -106,6 +106,7 @@ struct JacobiJob {
   double* lam;      // n eigenvalues
   int n;
   double tol;
+  int* sweeps;      // out: sweeps of the FP32 and of the FP64 phase (may be null)
 };
 void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st);
 void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(128, 1) tc_mode_kernel(const TcOp* __restrict_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   uint32_t phase = 0;
+  pdl_wait();  // TMEM and the barrier are set up while the previous kernel drains
 
   for (i64 t = blockIdx.x; t < total && !abort_flag; t += gridDim.x) {
     int lo = 0, hi = nops - 1;
@@ -258,8 +259,7 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
     attr_set = tc_smem_bytes(256);
   }
   const int grid = (int)std::min<i64>(total_tiles, 2 * 152);
-  tc_mode_kernel<<<grid, 128, smem, st>>>(d_ops, nops, total_tiles, ncols, status);
-  GPFVM_LAUNCH_CHECK();
+  launch_pdl(tc_mode_kernel, grid, 128, smem, st, d_ops, nops, total_tiles, ncols, status);
 }
 
 // hi = tf32(alpha * F), lo = alpha * F - hi for an n x k row-major factor

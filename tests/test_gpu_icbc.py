@@ -40,6 +40,7 @@ def _run(prob, mode, iters):
         else:
             os.environ["GPFVM_ICBC"] = old
     pb.assemble()
+    sweeps = pb.export(9, 6)
     b = pb.export(0, prob.N)
     code, info = pb.solve(max_iter=iters, rtol=0.0, reorth=True, want_var=True)
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
@@ -48,7 +49,7 @@ def _run(prob, mode, iters):
     v = np.random.default_rng(2).normal(size=prob.N)
     out = torch.empty(prob.N, dtype=torch.float64, device="cuda")
     pb.matvec(1, torch.as_tensor(v, device="cuda"), out)
-    res = dict(b=b, mean=mean.cpu().numpy(), var=var.cpu().numpy(), ghat=out.cpu().numpy(), v=v)
+    res = dict(b=b, mean=mean.cpu().numpy(), var=var.cpu().numpy(), ghat=out.cpu().numpy(), v=v, sweeps=sweeps)
     pb.close()
     return res
 
@@ -88,3 +89,18 @@ def test_structured_icbc_c2_full_size():
     assert relerr(s["ghat"], d["ghat"]) < 1e-10
     assert relerr(s["mean"], d["mean"]) < 1e-10
     np.testing.assert_allclose(s["var"], d["var"], atol=1e-10, rtol=0)
+
+
+def test_eigensolver_sweeps_converge_before_their_caps():
+    """Both Jacobi phases stop on their convergence test (FP32 cap 30 sweeps,
+    FP64 cap 12) on the full-size 2D+time heat IC grid (64 x 64 points) and on
+    the 1D+time IC line."""
+    for prob in (W.heat_2d(seed=4), W.heat_1d(16, 32, n_ic=33)):
+        sw = _run(prob, "structured", 2)["sweeps"]
+        assert len(sw) == 2 * prob.ndim
+        for a in range(prob.ndim):
+            s32, s64 = sw[2 * a], sw[2 * a + 1]
+            if prob.sets[0].coords[a].size == 1:
+                continue
+            assert 1 <= s32 < 30, sw
+            assert 1 <= s64 < 12, sw
