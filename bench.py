@@ -11,6 +11,14 @@ CG with full reorthogonalisation and the IterGP variance downdate to a relative
 residual of 1e-10, and posterior mean + variance on a 32^3 grid.  A new seeded
 initial condition is used every step.
 
+The three precisions (FP64, mixed FP32, mixed TF32x3) are timed on the same
+steps; the headline is the fastest mixed path whose posterior mean is within
+1e-6 of the FP64 path.  Beside it: the roofline of one application of that
+path's Gram operator (device time of CUDA-graph replays), the end-to-end rate
+through the C ABI with host buffers, a batched solve of the uneven heat batch
+(--batch / --batch-fp64 problems) and a served Poisson stream of wave IBVPs
+(--serve requests), both in mixed TF32x3 and FP64 with the means compared.
+
 Output: one JSON line (rank 0).  Multi-GPU runs are independent replicas
 (weak scaling: each rank solves its own IBVPs).
 """
@@ -46,8 +54,14 @@ def parse():
     ap.add_argument("--impl", default="gpfvm", choices=["gpfvm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=50)
+    ap.add_argument("--batch", type=int, default=64, help="problems of the uneven heat batch (mixed path; 0: skip)")
+    ap.add_argument("--batch-fp64", type=int, default=16, help="problems of the batch solved by the FP64 path")
+    ap.add_argument("--serve", type=int, default=6, help="requests of the served wave stream (0: skip)")
+    ap.add_argument("--slots", type=int, default=4, help="resident request slots of the server")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling mode: one assemble, solves of this many CG iterations per path, one query")
+    ap.add_argument("--profile-gram", action="store_true",
+                    help="profiling mode: one application of the inner Gram operator in an NVTX range")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling mode: exactly one timed-region step (assemble, set values, solve to the "
                          "benchmark tolerance, query) of --profile-precision (default: mixed TF32x3)")
@@ -65,6 +79,34 @@ def dist_env():
 
 def workload(seed):
     return W.heat_2d(64, 64, 64, nu=0.05, seed=seed)
+
+
+def source_digest():
+    """sha256 over the CUDA sources (which kernels a recorded profile belongs to)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2406_05020_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(name):
+    """DRAM bytes per application from a committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    try:
+        rec = dict(line.split(":", 1) for line in open(path) if line.startswith(("csrc_sha256:", "dram_bytes_per_application:")))
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_sha256", "").strip() != source_digest():
+        return None
+    try:
+        return float(rec["dram_bytes_per_application"])
+    except (KeyError, ValueError):
+        return None
 
 
 def load_peaks():
@@ -198,6 +240,111 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched and served execution (uneven heat batch; Poisson stream of wave IBVPs)
+# ---------------------------------------------------------------------------
+MAX_ITER_BATCH = 8000
+
+
+def bench_batch(gpfvm, torch, n_mixed: int, n_fp64: int):
+    """The first n problems of the seeded 256-problem batch of 2D+time heat
+    IBVPs (axis sizes U{16..64}).  A batched solve = assemble + solve_batch +
+    query of every problem, wall time between device synchronisations.  The
+    mixed path runs on n_mixed problems, the FP64 path (plain CG, no stored
+    directions: memory O(N) per problem) on the first n_fp64 of them, and the
+    posterior means of the common problems are compared."""
+    probs = W.batch_heat(256, lo=16, hi=64, seed=0)
+    out = {}
+    means = {}
+    for name, prec, reorth, n in (("mixed_tf32x3", gpfvm.MIXED_TF32X3, True, n_mixed),
+                                  ("fp64", gpfvm.FP64, False, n_fp64)):
+        if n <= 0:
+            continue
+        sub = probs[:n]
+        opts = gpfvm.solve_opts(max_iter=MAX_ITER_BATCH, rtol=RTOL, precision=prec, reorth=reorth, want_var=True,
+                                inner_max_iter=400, inner_rtol=1e-2)
+        pbs = [gpfvm.Problem(q, max_iter=MAX_ITER_BATCH) for q in sub]
+        outs = [(torch.empty(pb.P, dtype=torch.float64, device="cuda"),
+                 torch.empty(pb.P, dtype=torch.float64, device="cuda")) for pb in pbs]
+        torch.cuda.synchronize()
+        l0 = gpfvm.launch_count()
+        t0 = time.perf_counter()
+        for pb in pbs:
+            pb.assemble()
+        t1 = time.perf_counter()
+        code, infos = gpfvm.solve_batch(pbs, opts)
+        t2 = time.perf_counter()
+        for pb, (m, v) in zip(pbs, outs):
+            pb.query(m, v)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        launches = gpfvm.launch_count() - l0
+        its = [i.iterations for i in infos]
+        means[name] = [m.cpu().numpy() for m, _ in outs]
+        out[name] = {"problems": n, "status": int(code), "solves_per_s": n / (t3 - t0), "wall_s": t3 - t0,
+                     "assemble_s": t1 - t0, "solve_s": t2 - t1, "query_s": t3 - t2,
+                     "iters_min_mean_max": [min(its), float(np.mean(its)), max(its)],
+                     "unknowns_total": int(sum(q.N for q in sub)), "gpu_launches": int(launches)}
+        for pb in pbs:
+            pb.close()
+    if "fp64" in means and "mixed_tf32x3" in means:
+        k = min(len(means["fp64"]), len(means["mixed_tf32x3"]))
+        errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in
+                zip(means["mixed_tf32x3"][:k], means["fp64"][:k])]
+        out["mixed_mean_rel_err_vs_fp64_max"] = max(errs)
+        out["meets_1e-6"] = bool(max(errs) <= ACCURACY_BAR)
+    out["workload"] = ("batch of 2D+time heat IBVPs, axis sizes U{16..64}, nu~U(0.01,0.1), 5-bump IC on "
+                       "(Nx/2)(Ny/2), walls ceil(Nt/4) x ceil(Ns/4), grid (Nt/2)(Nx/2)(Ny/2), seed 0; "
+                       "first n of the 256-problem set")
+    return out
+
+
+def bench_serving(gpfvm, torch, n_req: int, slots: int):
+    """The first n_req requests of the seeded Poisson stream (500 req/s) of
+    2D+time wave IBVPs (axis sizes U{32..128}, c ~ U(0.5, 2)), submitted at
+    their arrival times to a continuous-batching server.  Latency = submit to
+    result on the host; throughput = requests / (last completion - first
+    arrival).  The same stream is served in mixed TF32x3 and in FP64 (plain
+    CG), and the means are compared request by request."""
+    reqs = W.serving_wave_stream(rate=500.0, duration=60.0, lo=32, hi=128, seed=0, n_max=n_req)
+    out, means = {}, {}
+    for name, prec, reorth in (("mixed_tf32x3", gpfvm.MIXED_TF32X3, True), ("fp64", gpfvm.FP64, False)):
+        srv = gpfvm.Server(max_slots=slots, max_iter=MAX_ITER_BATCH, rtol=RTOL, precision=prec, reorth=reorth,
+                           want_var=True, inner_max_iter=400, inner_rtol=1e-2)
+        torch.cuda.synchronize()
+        l0 = gpfvm.launch_count()
+        t0 = time.perf_counter()
+        pending = list(reqs)
+        tickets = []
+        while True:
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                tickets.append(srv.submit(pending.pop(0)[1]))
+            left = srv.step()
+            if not pending and left == 0:
+                break
+        t1 = time.perf_counter()
+        lat, codes, ms = [], [], []
+        for t in tickets:
+            code, mean, var, info = srv.poll(t)
+            codes.append(int(code))
+            lat.append(info.latency_ms)
+            ms.append(mean)
+        srv.close()
+        means[name] = ms
+        out[name] = {"requests": len(tickets), "codes": sorted(set(codes)),
+                     "solves_per_s": len(tickets) / (t1 - t0), "makespan_s": t1 - t0,
+                     "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                     "gpu_launches": int(gpfvm.launch_count() - l0)}
+    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(means["mixed_tf32x3"], means["fp64"])]
+    out["mixed_mean_rel_err_vs_fp64_max"] = max(errs)
+    out["meets_1e-6"] = bool(max(errs) <= ACCURACY_BAR)
+    out["workload"] = (f"first {n_req} requests of a seeded Poisson stream (500 req/s) of 2D+time wave IBVPs, "
+                       f"axis sizes U{{32..128}}, c~U(0.5,2), bump IC; {slots} resident slots")
+    out["sizes"] = [list(q.n_cells) for _, q in reqs]
+    return out
+
+
+# ---------------------------------------------------------------------------
 def l2_flush(buf):
     buf.add_(1.0)  # 256 MB write: evicts the 129 MB L2 between timed steps
 
@@ -327,27 +474,58 @@ def run_gpfvm(args):
         e2e_val = ws * args.steps / float(t.item())
     e2e_err = float(np.linalg.norm(mean_h - means[-1]) / np.linalg.norm(means[-1]))
 
-    # ---- dominant kernel: the Kronecker Gram matvec (G_PP, FP64 mode products)
-    N = pb.N
+    # ---- roofline: one application of the Gram operator of the headline path
+    # (the inner operator G^ of the mixed solve: G_PP mode products + the
+    # IC/BC deflation), device time of CUDA-graph replays on the solver stream
+    N, M = pb.N, pb.M
     nt, nx, ny = base.n_cells
-    flops_mv = 2.0 * N * (4 * ny + 9 * nx + 4 * nt)  # 17 shared mode products (4 y, 9 x, 4 t)
-    bytes_mv = 16.0 * N
+    lay = pb.export(10, 3)
+    structured, MK, MR = int(lay[0]), int(lay[1]), int(lay[2])
+    op_head = {"mixed_tf32x3": 7, "mixed_fp32": 6}.get(best_name, 1)
+    es = 4 if op_head in (6, 7) else 8
+    dense_icbc = (2 * MR * MK + MR * MR) if structured else M * M  # dense IC/BC operator entries read
+    bytes_op = float(es * (2 * N + dense_icbc))
+    flops_pp = 2.0 * N * (4 * ny + 9 * nx + 4 * nt)  # 17 shared mode products (4 y, 9 x, 4 t)
     v = torch.randn(N, dtype=torch.float64, device=dev)
     out = torch.empty_like(v)
-    for _ in range(5):
-        pb.matvec(0, v, out, stream=s_ptr)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     reps = args.matvec_reps
-    e0.record(stream)
-    for _ in range(reps):
-        pb.matvec(0, v, out, stream=s_ptr)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    mv_ms = e0.elapsed_time(e1) / reps
-    peak_alu = 152 * 4 * 2.07e9 / 1e12  # FP64: 2 DFMA/clk/SM at the 2070 MHz maximum clock
-    achieved = flops_mv / (mv_ms / 1e3) / 1e12
+    ms_op = pb.matvec_bench(op_head, v, out, reps=reps, stream=s_ptr)
+    ms_pp64 = pb.matvec_bench(0, v, out, reps=reps, stream=s_ptr)
+    ms_pptc = pb.matvec_bench(5, v, out, reps=reps, stream=s_ptr) if op_head == 7 else None
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else "of fallback (6800 GB/s)"
+    hbm_peak = hbm_peak or 6800.0
+    achieved = bytes_op / (ms_op / 1e3) / 1e9
+    traffic = recorded_traffic("gram_operator_heat2d_64x64x64")
+    peak_fp64 = 152 * 4 * 2.07e9 / 1e12  # 2 DFMA/clk/SM at the 2070 MHz maximum clock
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    tf32_split_peak = bf16 * (1.1 / 2.25) / 3.0  # TF32 = bf16 x nominal ratio; split TF32 issues 3 products
+    roofline = {
+        "kernel": ("G^ inner operator, one application (tcgen05 split-TF32 G_PP mode products + FP32 IC/BC "
+                   "products; 2D+time heat 64^3, M = 5120)" if op_head == 7 else f"G^ operator op {op_head}"),
+        "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+        "peak_source": peak_src, "traffic": traffic,
+        "algorithmic_bytes_per_application": bytes_op, "ms_per_application": ms_op,
+        "algorithmic_flops_per_application_gpp": flops_pp,
+        "secondary": {
+            "gpp_fp64_modeproducts": {"bound": "alu", "ms": ms_pp64, "achieved_tflops": flops_pp / (ms_pp64 / 1e3) / 1e12,
+                                      "peak_tflops": peak_fp64, "frac": flops_pp / (ms_pp64 / 1e3) / 1e12 / peak_fp64,
+                                      "peak_source": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz"},
+        },
+    }
+    if ms_pptc is not None:
+        roofline["secondary"]["gpp_tcgen05_split_tf32"] = {
+            "bound": "tensor", "ms": ms_pptc, "achieved_tflops": flops_pp / (ms_pptc / 1e3) / 1e12,
+            "peak_tflops": tf32_split_peak, "frac": flops_pp / (ms_pptc / 1e3) / 1e12 / tf32_split_peak,
+            "peak_source": "of measured bf16 x (1.1/2.25 nominal TF32 ratio) / 3 split products"}
+
+    # ---- batched and served execution (rank 0 only: bounded samples)
+    batch = serving = None
+    if rank == 0 and args.batch > 0:
+        batch = bench_batch(gpfvm, torch, args.batch, args.batch_fp64)
+    if rank == 0 and args.serve > 0:
+        serving = bench_serving(gpfvm, torch, args.serve, args.slots)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -369,10 +547,10 @@ def run_gpfvm(args):
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * pb.M,
                     "d2h_bytes_per_step": 16 * P, "mean_rel_diff_vs_device_path": e2e_err},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "gram_matvec_fp64 (gemm64_kernel x3 levels)", "bound": "alu",
-                         "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s", "frac": achieved / peak_alu,
-                         "peak_source": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz (recipe nominal 1.25 TFLOP/s)",
-                         "traffic": None, "ms_per_launch": mv_ms, "gram_mvm_gbs": bytes_mv / (mv_ms / 1e3) / 1e9},
+            "roofline": roofline,
+            "gram_mvm_gbs": achieved,
+            "batch": batch,
+            "serving": serving,
             "phases_ms_last_step": {"assemble": phases[0], "solve": phases[1], "query": phases[2]},
             "paths": {
                 "fp64": {"solves_per_s": fp64_value, "ms_per_step": sum(t64) / args.steps,
@@ -456,8 +634,32 @@ def run_profile_step(args):
     return 0 if code == 0 else 1
 
 
+def run_profile_gram(args):
+    """One application of the inner Gram operator (mixed TF32x3) inside the
+    NVTX range "gram_op7", for DRAM-traffic captures of that range."""
+    import torch
+
+    from paper_2406_05020_gb300 import build, gpfvm
+    build.build()
+    torch.cuda.set_device(0)
+    pb = gpfvm.Problem(workload(0), max_iter=64)
+    pb.assemble()
+    v = torch.randn(pb.N, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    pb.matvec(7, v, out)  # warm-up (first-use set-up outside the range)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("gram_op7")
+    pb.matvec(7, v, out)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_gram": True, "csrc_sha256": source_digest(), "N": pb.N, "M": pb.M}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_gram:
+        return run_profile_gram(args)
     if args.profile_step:
         return run_profile_step(args)
     if args.profile_iters > 0:

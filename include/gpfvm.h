@@ -168,6 +168,14 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream);
  * begin and end of a solve on the same problem.  Requires gpfvm_assemble.  v and out must not overlap. */
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);
 
+/* As gpfvm_gram_matvec (same ops, device pointers), for measurement: the
+ * op's launch sequence is captured once as a CUDA graph, replayed 2 + reps
+ * times, and *ms_per_application receives the device time of one application
+ * (CUDA events around the reps replays on the problem's stream).  out holds
+ * the result.  reps >= 1.  Errors as gpfvm_gram_matvec. */
+int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* out, int reps, void* stream,
+                            double* ms_per_application);
+
 /* CG / IterGP on the deflated system (Sec. 4.1, 4.2), x0 = 0.  max_iter
  * counts CG iterations (for the mixed precisions: inner iterations).  All scalars
  * stay on the device; a whole CG run is one CUDA graph launch whose WHILE node
@@ -215,6 +223,8 @@ int64_t gpfvm_launch_count(void);
  *   what 8: refinement steps of the last mixed-precision solve (1 value)
  *   what 9: eigensolver sweeps of the structured IC/BC stage, (FP32, FP64)
  *           per axis (2 * ndim values; 0 written without that stage)
+ *   what 10: IC/BC stage layout: (structured 1 / dense 0, rows of the set
+ *           inverted through its eigen-structure, rows of the Schur block)
  * Returns the number of doubles written or a negative error. */
 int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream);
 

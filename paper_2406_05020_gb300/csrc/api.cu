@@ -1958,6 +1958,85 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
   GPFVM_GUARD_END
 }
 
+int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* out, int reps, void* stream,
+                            double* ms_per_application) {
+  if (!p || !v || !out || !ms_per_application || reps < 1 || op < 0 || op > 7) return GPFVM_ERR_INVALID_ARG;
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
+  if ((op == 5 || op == 7) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  const Plan* plan = nullptr;
+  if (op >= 4) {
+    p->h_st32->done = 0;
+    p->h_st32->pad[1] = 0;
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->done, &p->h_st32->done, sizeof(int), cudaMemcpyHostToDevice, st));
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  const i64 nin = (op == 3) ? p->M : p->N;
+  const i64 nout = (op == 2) ? p->M : p->N;
+  switch (op) {
+    case 4: convert_d2f(v, p->f_vin, p->N, st); plan = &p->p_pp32; break;
+    case 5: convert_d2f(v, p->f_vin, p->N, st); plan = &p->p_pp32tc; break;
+    case 6: convert_d2f(v, p->f_p, p->N, st); plan = &p->p_mv32; break;
+    case 7: convert_d2f(v, p->f_p, p->N, st); plan = &p->p_mv32tc; break;
+    default:
+      GPFVM_CUDA(cudaMemcpyAsync(op == 3 ? p->d_win : p->d_vin, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
+      plan = &p->p_op[op];
+  }
+  // one application as a CUDA graph, replayed reps times between events
+  cudaGraph_t g = nullptr;
+  const long long before = g_launches.load();
+  GPFVM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  try {
+    plan->run(st);
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(st, &dummy);
+    cudaGetLastError();
+    throw;
+  }
+  GPFVM_CUDA(cudaStreamEndCapture(st, &g));
+  const long long kernels = g_launches.load() - before;
+  g_launches.fetch_sub(kernels);
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  GPFVM_CUDA(e);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    GPFVM_CUDA(cudaEventCreate(&e0));
+    GPFVM_CUDA(cudaEventCreate(&e1));
+    for (int i = 0; i < 2; ++i) GPFVM_CUDA(cudaGraphLaunch(ex, st));  // warm-up
+    GPFVM_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; ++i) GPFVM_CUDA(cudaGraphLaunch(ex, st));
+    GPFVM_CUDA(cudaEventRecord(e1, st));
+    count_launch((long long)(reps + 2) * kernels);
+    GPFVM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    GPFVM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_per_application = (double)ms / reps;
+    switch (op) {
+      case 4: case 5: f2d(p->f_vout, out, p->N, st); break;
+      case 6: case 7: f2d(p->f_q, out, p->N, st); break;
+      default:
+        GPFVM_CUDA(cudaMemcpyAsync(out, op == 2 ? p->d_wout : p->d_vout, sizeof(double) * nout,
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ex);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ex);
+  return GPFVM_OK;
+  GPFVM_GUARD_END
+}
+
 int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info* info, void* stream) {
   if (!p) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
@@ -2026,6 +2105,13 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
     case 8: {  // refinement steps of the last mixed-precision solve
       host_out[0] = p->last_outer;
       return 1;
+    }
+    case 10: {  // IC/BC stage: structured (1) or dense (0), rows of the structured set, other rows
+      if (capacity < 3) return GPFVM_ERR_INVALID_ARG;
+      host_out[0] = p->sicbc ? 1.0 : 0.0;
+      host_out[1] = p->sicbc ? p->MK : 0;
+      host_out[2] = p->sicbc ? p->MR : (double)p->M;
+      return 3;
     }
     case 9: {  // eigensolver sweeps (FP32, FP64) per axis of the structured IC/BC stage
       if (!p->d_jac_sweeps) return 0;

@@ -80,6 +80,7 @@ SIGNATURES = {
     "gpfvm_sizes": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "gpfvm_assemble": (C.c_int, [P, P]),
     "gpfvm_gram_matvec": (C.c_int, [P, C.c_int, P, P, P]),
+    "gpfvm_gram_matvec_bench": (C.c_int, [P, C.c_int, P, P, C.c_int, P, D]),
     "gpfvm_solve": (C.c_int, [P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
     "gpfvm_query": (C.c_int, [P, P, P, P]),
     "gpfvm_solve_host": (C.c_int, [P, D, C.POINTER(SolveOpts), D, D, C.POINTER(SolveInfo), P]),
@@ -212,6 +213,13 @@ class Problem:
         """out = op(v) on device tensors (see gpfvm_gram_matvec)."""
         return _check(lib().gpfvm_gram_matvec(self.h, int(op), C.c_void_p(v.data_ptr()),
                                               C.c_void_p(out.data_ptr()), _stream(stream)), "gpfvm_gram_matvec")
+
+    def matvec_bench(self, op: int, v, out, reps: int = 50, stream=None) -> float:
+        """Device ms of one application of op (graph replays; see gpfvm_gram_matvec_bench)."""
+        ms = C.c_double(0.0)
+        _check(lib().gpfvm_gram_matvec_bench(self.h, int(op), C.c_void_p(v.data_ptr()), C.c_void_p(out.data_ptr()),
+                                             int(reps), _stream(stream), C.byref(ms)), "gpfvm_gram_matvec_bench")
+        return ms.value
 
     def solve(self, opts: Optional[SolveOpts] = None, stream=None, **kw):
         opts = opts or solve_opts(**kw)
