@@ -10,7 +10,7 @@
  *   - the Kronecker-structured Gram matvec of the volume observations
  *     (Sec. 4.1, Eq. kronecker-structure) and the point-set blocks;
  *   - the Cholesky (IC/BC) deflation of Sec. 4.2 and CG with the IterGP
- *     combined posterior (Sec. 4.1) with full reorthogonalisation (Sec. 5);
+ *     combined posterior (Sec. 4.1) with full reorthogonalisation (Sec. 7);
  *   - posterior mean and variance on a tensor prediction grid
  *     (Sec. 2.1, Eqs. lin-cond-mean / lin-cond-cov).
  *

@@ -403,7 +403,7 @@ def cg_itergp(K: KronIBVP, max_iter: int, rtol: float = 0.0, want_var: bool = Tr
     posterior variance removes sum_j (Lhat k(x)^T p_j)^2 / eta_j, where
     Lhat k = L_PDE k - G_PB G_BB^-1 L_IC,BC k is the cross-covariance under the
     IC/BC-conditioned prior.  That sum presumes G^-conjugate directions, which
-    finite precision loses; following the paper's stabilisation (Sec. 5, full
+    finite precision loses; following the paper's stabilisation (Sec. 7, full
     reorthogonalisation) each new direction is made G^-conjugate to all
     previous ones: p <- p - sum_j (q_j.p / eta_j) p_j with q_j = G^ p_j.
     Stops when ||r||/||b|| <= rtol or after max_iter iterations."""

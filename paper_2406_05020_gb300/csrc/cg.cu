@@ -6,7 +6,7 @@
 //   u = Lhat k(X*)^T p,  down += u^2/eta_j   (IterGP combined-posterior downdate)
 //   alpha = r.r/eta, x += alpha p, r -= alpha q, beta = r'.r'/r.r   (k_update)
 //   p = r' + beta p                    (k_pupdate)
-//   p -= sum_i (q_i.p / eta_i) p_i     (full reorthogonalisation, Sec. 5)
+//   p -= sum_i (q_i.p / eta_i) p_i     (full reorthogonalisation, Sec. 7)
 // All scalars live in device memory (CGState), so an iteration is a fixed
 // launch sequence that a CUDA graph replays; reductions use a fixed-order
 // "last block" sum so results do not depend on block scheduling.
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(RT) k_pupdate(const T* __restrict__ r, T* __re
     p[i] = (T)fma(beta, (double)p[i], (double)r[i]);
 }
 
-// ---- full reorthogonalisation  p -= sum_j (q_j . p / eta_j) s_j  (Sec. 5)
+// ---- full reorthogonalisation  p -= sum_j (q_j . p / eta_j) s_j  (Sec. 7)
 // The direction stores hold one row of ld = store_ld(n) elements per
 // direction (rows 16-byte aligned), so both kernels read them with 16-byte
 // vector loads.  Chunk c of RCH elements of p stays in registers while each

@@ -1,7 +1,7 @@
 """The solves are scale-free in the data.
 
 The posterior mean is linear in the observations and the variance does not
-depend on them (Sec. 2, Eq. posterior), so scaling every observation by a
+depend on them (Sec. 2.1, Eqs. lin-cond-mean and lin-cond-cov), so scaling every observation by a
 power of two must scale the mean by exactly that factor and leave the
 variance unchanged, at every precision.  With factors 2^-100 and 2^+100 the
 late residuals of the mixed-precision refinement lie far outside the normal

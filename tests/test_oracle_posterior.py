@@ -259,7 +259,7 @@ def test_itergp_variance_bounds_and_monotone():
 
 def test_no_reorth_variance_breaks_down():
     """Without reorthogonalisation the sum over directions overshoots (the
-    reason for the paper's stabilisation, Sec. 5); with it the bound holds."""
+    reason for the paper's stabilisation, Sec. 7); with it the bound holds."""
     p = W.heat_1d()
     m, v = O.dense_posterior(p)
     bad = O.kron_posterior(p, max_iter=300, rtol=0.0, reorth=False)
