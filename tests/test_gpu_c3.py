@@ -1,0 +1,115 @@
+"""Full-size 2D+time wave IBVP (128^3 cells, N = 2,097,152; IC displacement
+with noise 0.01^2 and zero velocity on 64 x 64 grids; Neumann walls on 32 x 32
+midpoint grids per face, M = 12,288; grid 32 x 64 x 64), the early-terminated
+CG configuration with computational-uncertainty variance.
+
+The operators and the first CG iterates are compared with the oracle's same
+recurrence (reorthogonalised CG, Sec. 4.1/4.2, Sec. 7).  The variance is
+compared at sampled grid points (the dense cross-covariance of all 131,072
+grid points would be 12.9 GB on the host).  The 200-iteration run is checked
+through properties that hold at any size: positive curvatures, a variance
+within [0, sigma^2], and a variance that does not grow with more actions."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import gpfvm_workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_05020_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def c3():
+    prob = W.wave_2d(128, 128, 128, c=1.0, seed=0)
+    assert prob.N == 2_097_152 and prob.M == 12_288
+    return prob, O.KronIBVP(prob)
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _probe_variance(K, prob, down, idx):
+    """Oracle variance at grid points idx (flat indices of the prediction grid):
+    sigma^2 - ||L_BB^-1 k_B(x)||^2 - down(x)."""
+    shape = tuple(len(g) for g in prob.pred)
+    out = []
+    for f in idx:
+        m = np.unravel_index(f, shape)
+        pt = W.PointSet((0, 0, 0), [np.array([prob.pred[i][m[i]]]) for i in range(3)], np.zeros(1), 0.0, "probe")
+        probe = O.point_block(pt)
+        kB = np.concatenate([O.block_cov(X, probe, K.ell, K.s2)[:, 0] for X in K.sets])
+        v = sla.solve_triangular(K.Lbb, kB, lower=True)
+        out.append(K.s2 - v @ v - down[f])
+    return np.array(out)
+
+
+def test_c3_full_size_operators_and_first_iterations(c3):
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob, K = c3
+    pb = gpfvm.Problem(prob, max_iter=200)
+    pb.assemble()
+    v = np.random.default_rng(5).normal(size=prob.N)
+    vt = torch.as_tensor(v, device="cuda")
+    out = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    pb.matvec(0, vt, out)
+    assert relerr(out.cpu().numpy(), K.Gpp(v)) < 1e-12
+    g = torch.empty(prob.M, dtype=torch.float64, device="cuda")
+    pb.matvec(2, vt, g)
+    assert relerr(g.cpu().numpy(), K.Gbp(v)) < 1e-12
+    pb.matvec(1, vt, out)
+    assert relerr(out.cpu().numpy(), K.Ghat(v)) < RTOL
+    assert relerr(pb.export(0, prob.N), K.rhs_hat()) < RTOL
+
+    iters = 12
+    code, info = pb.solve(max_iter=iters, rtol=0.0, reorth=True, want_var=True)
+    assert info.iterations == iters
+    x, down, it, hist = O.cg_itergp(K, iters, 0.0, True, True)
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    pb.query(mean, var)
+    m_o = K.KBx(K.Hsolve(K.yB - K.Gbp(x))) + K.KPx(x)
+    assert relerr(mean.cpu().numpy(), m_o) < RTOL
+    assert relerr(pb.export(1, prob.N), x) < 1e-8
+    np.testing.assert_allclose(pb.export(5, pb.P), down, rtol=0, atol=RTOL)
+    idx = np.random.default_rng(6).choice(pb.P, size=8, replace=False)
+    np.testing.assert_allclose(var.cpu().numpy()[idx], _probe_variance(K, prob, down, idx), rtol=0, atol=RTOL)
+    pb.close()
+
+
+def test_c3_200_iterations_properties(c3):
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob, _ = c3
+    pb = gpfvm.Problem(prob, max_iter=200)
+    pb.assemble()
+    res = {}
+    for iters in (12, 200):
+        code, info = pb.solve(max_iter=iters, rtol=0.0, reorth=True, want_var=True)
+        assert code in (0, 1) and info.iterations == iters
+        mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+        var = torch.empty_like(mean)
+        pb.query(mean, var)
+        res[iters] = (mean.cpu().numpy(), var.cpu().numpy(), pb.export(6, iters))
+    m, v, eta = res[200]
+    assert np.all(np.isfinite(m))
+    assert np.all(eta > 0)
+    assert v.min() >= -RTOL and v.max() <= prob.outputscale + RTOL
+    # more CG actions can only lower the combined-posterior variance
+    assert np.all(v <= res[12][1] + 1e-12)
+    pb.close()
