@@ -552,6 +552,7 @@ def run_gpfvm(args):
             "batch": batch,
             "serving": serving,
             "phases_ms_last_step": {"assemble": phases[0], "solve": phases[1], "query": phases[2]},
+            "eigensolver_sweeps_fp32_fp64_per_axis": [int(x) for x in pb.export(9, 6)],
             "paths": {
                 "fp64": {"solves_per_s": fp64_value, "ms_per_step": sum(t64) / args.steps,
                          "cg_iters_mean": statistics.mean(it64), "gpu_launches": int(launches64),

@@ -9,6 +9,8 @@
 // K-chunks of 16, and no more than a few bytes of shared-memory traffic per
 // DFMA.
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -203,6 +205,50 @@ void launch_multi_gemm(const MOp* d_ops, int nops, i64 total, int f32, int bm, c
   }
 }
 
+// sum_{j in [jlo, jhi)} row[j] x[j] over one warp (result in every lane):
+// 16-byte vector loads over the aligned interior (four independent
+// accumulators, so that many loads are in flight), scalar head and tail.
+template <typename T>
+__device__ __forceinline__ T warp_row_dot(const T* __restrict__ row, const T* __restrict__ x, int jlo, int jhi,
+                                          int lane) {
+  constexpr int W = 16 / sizeof(T);
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
+  T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+  const bool vec = (((uintptr_t)row | (uintptr_t)x) & 15) == 0;
+  const int va = vec ? min(jhi, (jlo + W - 1) / W * W) : jhi;
+  const int vb = vec ? max(va, jhi / W * W) : jhi;
+  for (int j = jlo + lane; j < va; j += 32) acc0 = fma(row[j], x[j], acc0);
+  for (int j = vb + lane; j < jhi; j += 32) acc1 = fma(row[j], x[j], acc1);
+  const int nv = (vb - va) / W;
+  const V* __restrict__ rv = reinterpret_cast<const V*>(row + va);
+  const V* __restrict__ xv = reinterpret_cast<const V*>(x + va);
+  auto dot = [](const V& a, const V& b, T acc) {
+    if constexpr (sizeof(T) == 4) {
+      acc = fma(a.x, b.x, acc);
+      acc = fma(a.y, b.y, acc);
+      acc = fma(a.z, b.z, acc);
+      return fma(a.w, b.w, acc);
+    } else {
+      acc = fma(a.x, b.x, acc);
+      return fma(a.y, b.y, acc);
+    }
+  };
+  int v = lane;
+  for (; v + 96 < nv; v += 128) {
+    const V a0 = rv[v], a1 = rv[v + 32], a2 = rv[v + 64], a3 = rv[v + 96];
+    const V b0 = xv[v], b1 = xv[v + 32], b2 = xv[v + 64], b3 = xv[v + 96];
+    acc0 = dot(a0, b0, acc0);
+    acc1 = dot(a1, b1, acc1);
+    acc2 = dot(a2, b2, acc2);
+    acc3 = dot(a3, b3, acc3);
+  }
+  for (; v < nv; v += 32) acc2 = dot(rv[v], xv[v], acc2);
+  T s = (acc0 + acc1) + (acc2 + acc3);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 // Many GEMV ops in one launch, one warp per output row over all ops:
 // y = alpha * A x + beta * z  (z may alias y).
 template <typename T>
@@ -224,16 +270,7 @@ __global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict
   if (op.tri == 2) jlo = i;
   const T* row = reinterpret_cast<const T*>(op.A) + (i64)i * op.lda;
   const T* x = reinterpret_cast<const T*>(op.x);
-  T s0 = T(0), s1 = T(0);
-  int j = jlo + lane;
-  for (; j + 32 < jhi; j += 64) {
-    s0 = fma(row[j], x[j], s0);
-    s1 = fma(row[j + 32], x[j + 32], s1);
-  }
-  if (j < jhi) s0 = fma(row[j], x[j], s0);
-  T s = s0 + s1;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const T s = warp_row_dot(row, x, jlo, jhi, lane);
   if (lane == 0) {
     T v = (T)op.alpha * s;
     if (op.beta != 0.0) v += (T)op.beta * reinterpret_cast<const T*>(op.z)[i];
@@ -280,16 +317,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(int m, int n, const T* __rest
   if (tri == 1) hi = min(n, i + 1);
   if (tri == 2) lo = i;
   const T* row = A + (i64)i * lda;
-  T s0 = T(0), s1 = T(0);
-  int j = lo + lane;
-  for (; j + 32 < hi; j += 64) {
-    s0 = fma(row[j], x[j], s0);
-    s1 = fma(row[j + 32], x[j + 32], s1);
-  }
-  if (j < hi) s0 = fma(row[j], x[j], s0);
-  T s = s0 + s1;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const T s = warp_row_dot(row, x, lo, hi, lane);
   if (lane == 0) y[i] = alpha * s + (beta != T(0) ? beta * y[i] : T(0));
 }
 

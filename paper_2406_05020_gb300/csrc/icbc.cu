@@ -31,47 +31,70 @@ constexpr int JAC_MAX_N = 96;
 // rounding floor n eps ||A||_F of U = A V: such columns hold noise whose
 // mutual angle is meaningless, and rotating them kept sweeps from converging.
 // Sweeps are bounded in both phases.
+// One pair per 8 lanes (4 pairs per warp): the per-pair scalar work (FP64 on
+// the polish sweeps, where one SM's DFMA rate is the bound) is repeated by 8
+// lanes instead of 32.  Column norms are carried in nrm[] (recomputed at
+// every sweep start, updated exactly for the applied rotation), so a pair
+// needs one inner product.  The angle is formed in FP32; its cosine is
+// normalised in T by two Newton steps, so the applied rotation is orthogonal
+// to T's rounding.  Shuffles run in warp-uniform loops.
 template <typename T>
-__device__ int jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, double tol_abs, double noise,
-                             int max_sweeps, double* maxrot) {
+__device__ int jacobi_sweeps(T* U, T* V, T* nrm, int n, double fro, double tol_rot, double tol_abs, double noise,
+                             int max_sweeps, double* maxrot, int extra = 0) {
   const int np = (n + 1) & ~1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int oct = lane >> 3, sl = lane & 7;
   const double noise2 = noise * noise * fro * fro;
+  const double tol2 = tol_rot * tol_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    for (int j0 = warp * 4; j0 < n; j0 += nw * 4) {
+      const int j = j0 + oct;
+      T a = T(0);
+      if (j < n)
+        for (int i = sl; i < n; i += 8) a = fma(U[j * n + i], U[j * n + i], a);
+      a += __shfl_xor_sync(0xffffffffu, a, 4);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      if (j < n && sl == 0) nrm[j] = a;
+    }
     if (tid == 0) *maxrot = 0.0;
     __syncthreads();
-    double local_max = 0.0;
+    double local_max2 = 0.0;
     for (int r = 0; r < np - 1; ++r) {
-      for (int k = warp; k < np / 2; k += nw) {
-        int p, q;
-        if (k == 0) { p = r; q = np - 1; }
-        else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
-        if (p >= n || q >= n) continue;
-        T a = 0, b = 0, c = 0;
-        for (int i = lane; i < n; i += 32) {
-          const T up = U[p * n + i], uq = U[q * n + i];
-          a += up * up;
-          b += uq * uq;
-          c += up * uq;
+      for (int k0 = warp * 4; k0 < np / 2; k0 += nw * 4) {
+        const int k = k0 + oct;
+        int p = n, q = n;
+        if (k < np / 2) {
+          if (k == 0) { p = r; q = np - 1; }
+          else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          c += __shfl_xor_sync(0xffffffffu, c, o);
-        }
-        if (a == T(0) || b == T(0) || fabs((double)c) <= tol_abs * fro * (sqrt((double)a) + sqrt((double)b)))
+        const bool valid = p < n && q < n;
+        T c = T(0);
+        if (valid)
+          for (int i = sl; i < n; i += 8) c = fma(U[p * n + i], U[q * n + i], c);
+        c += __shfl_xor_sync(0xffffffffu, c, 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        if (!valid) continue;
+        const T a = nrm[p], b = nrm[q];
+        const double cd = (double)c;
+        if (a == T(0) || b == T(0) ||
+            fabs(cd) <= tol_abs * fro * ((double)sqrtf((float)a) + (double)sqrtf((float)b)))
           continue;
         // both columns at the rounding floor of U = A V: their mutual angle is noise
         if ((double)a <= noise2 && (double)b <= noise2) continue;
-        const T rot = fabs(c) / sqrt(a * b);
-        if ((double)rot < tol_rot) continue;
-        local_max = fmax(local_max, (double)rot);
-        const T zeta = (b - a) / (T(2) * c);
-        const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-        for (int i = lane; i < n; i += 32) {
+        const double rot2 = cd * cd / ((double)a * (double)b);
+        if (rot2 < tol2) continue;
+        local_max2 = fmax(local_max2, rot2);
+        const float zeta = (float)(b - a) / (2.0f * (float)c);
+        const float tf = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+        const T t = (T)tf, h = T(1) + t * t;
+        T cs = (T)rsqrtf((float)h);
+        cs = cs * (T(1.5) - T(0.5) * h * cs * cs);
+        cs = cs * (T(1.5) - T(0.5) * h * cs * cs);
+        const T sn = cs * t;
+        for (int i = sl; i < n; i += 8) {
           const T up = U[p * n + i], uq = U[q * n + i];
           U[p * n + i] = cs * up - sn * uq;
           U[q * n + i] = sn * up + cs * uq;
@@ -79,14 +102,25 @@ __device__ int jacobi_sweeps(T* U, T* V, int n, double fro, double tol_rot, doub
           V[p * n + i] = cs * vp - sn * vq;
           V[q * n + i] = sn * vp + cs * vq;
         }
+        if (sl == 0) {
+          const T cs2 = cs * cs, tc2 = T(2) * t * c, tt = t * t;
+          nrm[p] = cs2 * (a - tc2 + tt * b);
+          nrm[q] = cs2 * (b + tc2 + tt * a);
+        }
       }
       __syncthreads();
     }
-    if (lane == 0) atomicMax((unsigned long long*)maxrot, __double_as_longlong(local_max));
+    double m2 = local_max2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    if (lane == 0) atomicMax((unsigned long long*)maxrot, __double_as_longlong(sqrt(m2)));
     __syncthreads();
     const bool done = *maxrot < tol_rot * 10.0;
     __syncthreads();
-    if (done) return sweep + 1;
+    if (done) {
+      if (extra-- > 0) continue;  // quadratic convergence: one more sweep reaches the rounding level
+      return sweep + 1;
+    }
   }
   return sweep;
 }
@@ -99,6 +133,8 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
   double* V = sm + n * n;
   float* Uf = (float*)(sm + 2 * n * n);
   float* Vf = Uf + n * n;
+  double* nrm = sm + 3 * n * n;       // column norms of U (FP64 phase)
+  float* nrmf = (float*)(nrm + n);    // ... of Uf (FP32 phase)
   __shared__ double maxrot, fro2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < n * n; e += blockDim.x) {
@@ -119,7 +155,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
   // phase 1: FP32 sweeps until the largest rotation of a sweep is below 1e-4
   // (FP32 dot products carry ~n * 6e-8 of rounding, so tighter targets only
   // rotate on noise); the FP64 polish converges quadratically from there
-  const int sw32 = jacobi_sweeps<float>(Uf, Vf, n, fro, 1e-5, 4e-8, n * 6e-8, 30, &maxrot);
+  const int sw32 = jacobi_sweeps<float>(Uf, Vf, nrmf, n, fro, 1e-5, 4e-8, n * 6e-8, 30, &maxrot);
   // re-orthonormalise V in FP64 (modified Gram-Schmidt over its columns)
   for (int e = tid; e < n * n; e += blockDim.x) V[e] = (double)Vf[e];
   __syncthreads();
@@ -151,10 +187,12 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
     U[e] = s;
   }
   __syncthreads();
-  // phase 2: FP64 polish to the rounding level of n-term FP64 dot products
-  // (~n * 1.1e-16): smaller rotations are noise, and chasing them made every
-  // polish run all of its sweeps
-  const int sw64 = jacobi_sweeps<double>(U, V, n, fro, 2e-14, 4e-16, n * 1.2e-16, 12, &maxrot);
+  // phase 2: FP64 polish: rotations down to 1e-15 are applied (eigenvectors of
+  // eigenvalues near the noise term are weighted by 1/noise in G_BB^-1, so
+  // their angles matter); once a sweep's largest rotation is below 1e-14
+  // (reachable thanks to the noise-floor skip) one more sweep is run, which
+  // takes the angles to the rounding level
+  const int sw64 = jacobi_sweeps<double>(U, V, nrm, n, fro, 1e-15, 4e-16, n * 1.2e-16, 12, &maxrot, 1);
   if (J.sweeps && tid == 0) {
     J.sweeps[0] = sw32;
     J.sweeps[1] = sw64;
@@ -173,14 +211,17 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* __restric
   }
 }
 
+// U, V (FP64), Uf, Vf (FP32) and the column norms of both phases
+static int jacobi_smem_bytes(int n) { return 3 * n * n * (int)sizeof(double) + n * (int)(sizeof(double) + sizeof(float)); }
+
 void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st) {
   if (n_jobs <= 0) return;
   if (max_n > JAC_MAX_N) throw CudaError{cudaErrorInvalidValue, "jacobi: matrix too large"};
-  const int smem = 3 * max_n * max_n * (int)sizeof(double);
+  const int smem = jacobi_smem_bytes(max_n);
   static bool attr = false;
   if (!attr) {
     GPFVM_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    3 * JAC_MAX_N * JAC_MAX_N * (int)sizeof(double)));
+                                    jacobi_smem_bytes(JAC_MAX_N)));
     attr = true;
   }
   jacobi_kernel<<<n_jobs, 1024, smem, st>>>(d_jobs);

@@ -81,7 +81,7 @@ def test_structured_icbc_matches_dense_and_oracle(name):
 
 
 def test_structured_icbc_c2_full_size():
-    """configs[1] geometry (M = 5120): structured vs dense GPU stages."""
+    """2D+time heat 64^3 geometry (M = 5120): structured vs dense GPU stages."""
     prob = W.heat_2d(seed=4)
     s = _run(prob, "structured", 6)
     d = _run(prob, "dense", 6)

@@ -70,7 +70,7 @@ def test_fp32_gram_operator_accuracy(name):
 
 
 def test_mixed_c2_full_size_against_fp64_path():
-    """configs[1] at full size: the mixed solve's mean is within 1e-6 of the
+    """2D+time heat 64^3 at full size: the mixed solve's mean is within 1e-6 of the
     plain FP64 GPU solve (itself pinned to the oracle by the parity tests)."""
     import torch
 

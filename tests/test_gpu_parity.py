@@ -105,7 +105,11 @@ def test_fixed_iterations_match_oracle(name):
     """The same recurrence for a fixed number of iterations: iterate, IterGP
     downdate and posterior agree with the oracle's CG."""
     prob = PROBS[name]()
-    iters = min(12, prob.N // 2)  # stay clear of the fully converged (rounding-noise) regime
+    # Stay clear of the regime where the Krylov recurrence is decided by rounding:
+    # on the 35-unknown 1D+t problem the downdate moves by 1e-14 under a change of
+    # summation order after 9 iterations but by 3e-11 after 12, while the larger
+    # problems stay at 1e-16 through 12.  At most N/4 iterations are compared.
+    iters = min(12, max(prob.N // 4, 2))
     pb = _gpu(prob)
     code, info = pb.solve(max_iter=iters, rtol=0.0, reorth=True, want_var=True)
     assert info.iterations == iters
@@ -141,7 +145,7 @@ def test_converged_posterior_matches_dense_cholesky(name):
 
 
 def test_c1_heat_1d_full_config():
-    """configs[0]-shaped workload: 16x32 cells, 32 IC + 32 BC points, 64x64 grid."""
+    """1D+time heat at full size: 16x32 cells, 32 IC + 32 BC points, 64x64 grid."""
     prob = W.heat_1d()
     pb = _gpu(prob)
     code, info = pb.solve(max_iter=2000, rtol=1e-12, reorth=True, want_var=True)
@@ -182,7 +186,7 @@ def test_solve_before_assemble_is_state_error():
 
 
 def test_c2_full_size_matvec_and_iterations():
-    """configs[1] (2D+time heat, 64^3 cells, M = 5120) at full size: one
+    """2D+time heat at full size (64^3 cells, M = 5120): one
     deflated Gram matvec and 10 CG iterations against the oracle."""
     prob = W.heat_2d(seed=0)
     pb = _gpu(prob, max_iter=64)
