@@ -110,6 +110,12 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       need(op.A, e * ((i64)(op.m - 1) * op.lda + op.n), "gemv A");
       need(op.x, e * op.n, "gemv x");
       need(op.y, e * op.m, "gemv y");
+    } else if (op.kind == PlanOp::SCALE) {
+      need(op.sc_X, (op.sc_f32 ? 4 : 8) * (i64)op.sc_rows * op.sc_cols, "scale X");
+      need(op.sc_lt, 8 * op.sc_cols, "scale lt");
+    } else if (op.kind == PlanOp::COPY) {
+      need(op.cp_dst, op.cp_bytes, "copy dst");
+      need(op.cp_src, op.cp_bytes, "copy src");
     }
   }
 }
@@ -173,6 +179,7 @@ struct gpfvm_problem {
   float *f_QK[3] = {}, *f_Ft = nullptr, *f_F = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_hK = nullptr,
         *f_tR = nullptr, *f_uR = nullptr;
   JacobiJob* d_jac = nullptr;
+  unsigned int* d_psync = nullptr;  // grid-barrier words of the persistent plan kernel
   int* d_jac_sweeps = nullptr;  // 2 per axis: FP32 and FP64 sweeps of the last assembly
   // tensor-core G_PP (split TF32): factor splits, rotated intermediates, op tables
   bool tc_ok = false, use_tc = false;
@@ -388,10 +395,7 @@ struct Builder {
     kron(plan, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0);
     const double* lt = p->d_lt;
     const bool F32 = f32;
-    plan.func([=](cudaStream_t st) {
-      if (F32) scale_cols32((float*)hK, 1, MK, lt, -1.0, st);
-      else scale_cols(hK, 1, MK, lt, -1.0, st);
-    });
+    plan.scale(hK, 1, MK, lt, -1.0, F32);
     kron(plan, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0);
     if (MR > 0) {
       const size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -399,7 +403,7 @@ struct Builder {
       double* uR = f32 ? (double*)p->f_uR : p->d_uR;
       const double* gR = at(g, MK);
       double* wR = at(w, MK);
-      plan.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemcpyAsync(tR, gR, es * MR, cudaMemcpyDeviceToDevice, st)); });
+      plan.copy(tR, gR, (i64)es * MR);
       if (f32) {
         plan.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
         plan.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
@@ -451,10 +455,7 @@ struct Builder {
     kron(c1, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0, nullptr, nd);
     const double* lt = p->d_lt;
     const bool F32 = f32;
-    c1.func([=](cudaStream_t st) {
-      if (F32) scale_cols32((float*)hK, 1, MK, lt, -1.0, st);
-      else scale_cols(hK, 1, MK, lt, -1.0, st);
-    });
+    c1.scale(hK, 1, MK, lt, -1.0, F32);
     kron(c1, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0, nullptr, nd);
     if (MR > 0) {
       const size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -462,7 +463,7 @@ struct Builder {
       double* uR = f32 ? (double*)p->f_uR : p->d_uR;
       const double* gR = at(g, MK);
       double* wR = at(w, MK);
-      c2.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemcpyAsync(tR, gR, es * MR, cudaMemcpyDeviceToDevice, st)); });
+      c2.copy(tR, gR, (i64)es * MR);
       if (f32) {
         c2.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
         c2.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
@@ -941,12 +942,7 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
 // G_PP on tensor cores as a chain of FUNC ops (one per level) for a phased plan.
 Plan tc_chain(gpfvm_problem* p, int inst) {
   Plan c;
-  for (auto L : p->tc_levels[inst]) {
-    gpfvm_problem* pp = p;
-    c.func([=](cudaStream_t st) {
-      launch_tc_modes(pp->d_tcops + L.off, L.nops, L.tiles, L.maxn, &pp->d_st32->pad[1], st);
-    });
-  }
+  for (auto L : p->tc_levels[inst]) c.tc(p->d_tcops + L.off, L.nops, L.tiles, L.maxn, &p->d_st32->pad[1]);
   return c;
 }
 
@@ -1017,6 +1013,11 @@ void finalize_plans(gpfvm_problem* p) {
     pl->finalize();
     pl->fan = &p->fan;
   }
+  // persistent forms of the iteration operators (used when GPFVM_PERSIST=1)
+  Plan* fp64_plans[] = {&p->p_mv_cg, &p->p_mvv_cg, &p->p_op[0], &p->p_op[1]};
+  Plan* fp32_plans[] = {&p->p_mv32, &p->p_mvv32, &p->p_mv32tc, &p->p_mvv32tc, &p->p_pp32, &p->p_pp32tc};
+  for (Plan* pl : fp64_plans) pl->prog = persist_build(*pl, p->d_psync, &p->d_st->status);
+  for (Plan* pl : fp32_plans) pl->prog = persist_build(*pl, p->d_psync, &p->d_st32->pad[1]);
 }
 
 int validate(const gpfvm_desc* D) {
@@ -1267,6 +1268,8 @@ void alloc_all(gpfvm_problem* p) {
   p->d_eta32 = m.alloc<double>(cap);
   p->d_st = m.alloc<CGState>(1);
   p->d_st32 = m.alloc<CGState>(1);
+  p->d_psync = m.alloc<unsigned int>(2);
+  GPFVM_CUDA(cudaMemset(p->d_psync, 0, 2 * sizeof(unsigned int)));
   GPFVM_CUDA(cudaMemset(p->d_st, 0, sizeof(CGState)));
   GPFVM_CUDA(cudaMemset(p->d_st32, 0, sizeof(CGState)));
   GPFVM_CUDA(cudaMallocHost(&p->h_st, sizeof(CGState)));
@@ -1542,7 +1545,8 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   const CGState& h = *p->h_st;
   count_launch((long long)h.loops * p->graph_kernels);
   int status = GPFVM_NOT_CONVERGED;
-  if (h.status & DEV_BREAKDOWN) status = GPFVM_ERR_BREAKDOWN;
+  if (h.status & DEV_TIMEOUT) status = GPFVM_ERR_TIMEOUT;
+  else if (h.status & DEV_BREAKDOWN) status = GPFVM_ERR_BREAKDOWN;
   else if (h.converged) status = GPFVM_OK;
   gpfvm_solve_info I = p->last;
   I.iterations = h.k;
@@ -1637,6 +1641,7 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   GPFVM_CUDA(cudaEventRecord(R.e0, st));
   p->h_st32->pad[1] = 0;
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
+  GPFVM_CUDA(cudaMemsetAsync(&p->d_st->status, 0, sizeof(int), st));
   GPFVM_CUDA(cudaMemsetAsync(p->d_x, 0, sizeof(double) * p->N, st));
   if (o->want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
   norm2(p->d_b, p->N, &p->d_st->aux[1], p->d_st, st);
@@ -1675,6 +1680,7 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
   const gpfvm_solve_opts* o = &R.o;
   const i64 N = p->N;
   if (R.mstate == 1) {
+    if (p->h_st->status & DEV_TIMEOUT) { R.status = GPFVM_ERR_TIMEOUT; R.mstate = 3; return; }
     const double b2 = p->h_st->aux[1];
     R.rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
     if (!std::isfinite(R.rel)) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }

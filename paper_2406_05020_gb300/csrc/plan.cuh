@@ -7,11 +7,15 @@
 #include <functional>
 
 #include "kernels.cuh"
+#include "persist.cuh"
+#include "tc.cuh"
 
 namespace gpfvm {
 
 struct PlanOp {
-  enum Kind { GEMM, GEMV, GEMV32, FUNC } kind;
+  // FUNC runs a host callback; TC, SCALE and COPY are typed device ops that
+  // the persistent plan kernel can also execute (they run like FUNC ops in run()).
+  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY } kind;
   int phase = -1;  // ops sharing a phase id (>= 0, consecutive) are independent: merged launches
   GemmDesc g;
   int seg0 = 0, group0 = 0;
@@ -23,6 +27,22 @@ struct PlanOp {
   double* y = nullptr;
   double alpha = 1.0, beta = 0.0;
   std::function<void(cudaStream_t)> fn;
+  // TC: tensor-core mode products of one level (see tc.cu)
+  const TcOp* tc_ops = nullptr;
+  int tc_nops = 0, tc_maxn = 0;
+  i64 tc_tiles = 0;
+  int* tc_status = nullptr;
+  // SCALE: X (rows x cols, FP64 or FP32) column j times lt[j]^pw (pw = -1 or -0.5)
+  void* sc_X = nullptr;
+  int sc_rows = 0, sc_f32 = 0;
+  i64 sc_cols = 0;
+  const double* sc_lt = nullptr;
+  double sc_pw = -1.0;
+  // COPY: device to device
+  void* cp_dst = nullptr;
+  const void* cp_src = nullptr;
+  i64 cp_bytes = 0;
+  bool func_like() const { return kind == FUNC || kind == TC || kind == SCALE || kind == COPY; }
 };
 
 // One merged launch of a phase: a table of GEMM ops (same element type and
@@ -72,9 +92,12 @@ class Plan {
   int n_phases = 0;
   const int* skip = nullptr;  // device flag: when set, every GEMM/GEMV of the plan is a no-op
   const Fan* fan = nullptr;    // optional: run the independent launches of a phase concurrently
+  PersistProg* prog = nullptr; // optional: the whole plan as one cooperative launch (persist.cu)
 
   ~Plan() { release(); }
   void release() {
+    persist_free(prog);
+    prog = nullptr;
     if (d_segs) cudaFree(d_segs);
     if (d_groups) cudaFree(d_groups);
     if (d_tables) cudaFree(d_tables);
@@ -96,6 +119,8 @@ class Plan {
       n_phases = o.n_phases;
       skip = o.skip;
       fan = o.fan;
+      prog = o.prog;
+      o.prog = nullptr;
       d_segs = o.d_segs; d_groups = o.d_groups; d_tables = o.d_tables;
       o.d_segs = nullptr; o.d_groups = nullptr; o.d_tables = nullptr;
     }
@@ -137,6 +162,24 @@ class Plan {
     PlanOp op;
     op.kind = PlanOp::FUNC;
     op.fn = std::move(f);
+    ops.push_back(op);
+  }
+  void tc(const TcOp* d_ops, int nops, i64 tiles, int maxn, int* status) {
+    PlanOp op;
+    op.kind = PlanOp::TC;
+    op.tc_ops = d_ops; op.tc_nops = nops; op.tc_tiles = tiles; op.tc_maxn = maxn; op.tc_status = status;
+    ops.push_back(op);
+  }
+  void scale(void* X, int rows, i64 cols, const double* lt, double pw, bool f32) {
+    PlanOp op;
+    op.kind = PlanOp::SCALE;
+    op.sc_X = X; op.sc_rows = rows; op.sc_cols = cols; op.sc_lt = lt; op.sc_pw = pw; op.sc_f32 = f32 ? 1 : 0;
+    ops.push_back(op);
+  }
+  void copy(void* dst, const void* src, i64 bytes) {
+    PlanOp op;
+    op.kind = PlanOp::COPY;
+    op.cp_dst = dst; op.cp_src = src; op.cp_bytes = bytes;
     ops.push_back(op);
   }
   void append(const Plan& o) {
@@ -300,7 +343,13 @@ class Plan {
     else if (op.kind == PlanOp::GEMV32)
       launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, (float)op.alpha,
                     (float)op.beta, op.tri, st, skip);
-    else op.fn(st);
+    else if (op.kind == PlanOp::TC) launch_tc_modes(op.tc_ops, op.tc_nops, op.tc_tiles, op.tc_maxn, op.tc_status, st);
+    else if (op.kind == PlanOp::SCALE) {
+      if (op.sc_f32) scale_cols32((float*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
+      else scale_cols((double*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
+    } else if (op.kind == PlanOp::COPY) {
+      if (op.cp_bytes > 0) GPFVM_CUDA(cudaMemcpyAsync(op.cp_dst, op.cp_src, op.cp_bytes, cudaMemcpyDeviceToDevice, st));
+    } else op.fn(st);
   }
   void run_unit(const LaunchUnit& u, cudaStream_t st) const {
     if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
@@ -309,6 +358,7 @@ class Plan {
   // Ops of one phase are consecutive; its merged launch units and FUNC ops
   // are mutually independent.  Without a fan they run in order on st.
   void run(cudaStream_t st) const {
+    if (prog && persist_enabled() && persist_run(prog, st)) return;
     size_t i = 0;
     while (i < ops.size()) {
       const PlanOp& op = ops[i];
@@ -321,11 +371,11 @@ class Plan {
       size_t j = i;
       while (j < ops.size() && ops[j].phase == ph) ++j;
       int lanes = (int)phase_units[ph].size();
-      for (size_t t = i; t < j; ++t) lanes += ops[t].kind == PlanOp::FUNC;
+      for (size_t t = i; t < j; ++t) lanes += ops[t].func_like();
       if (!fan || lanes <= 1) {
         for (const LaunchUnit& u : phase_units[ph]) run_unit(u, st);
         for (size_t t = i; t < j; ++t)
-          if (ops[t].kind == PlanOp::FUNC) ops[t].fn(st);
+          if (ops[t].func_like()) run_op(ops[t], st);
       } else {
         GPFVM_CUDA(cudaEventRecord(fan->fork, st));
         bool used[Fan::NAUX] = {};
@@ -341,7 +391,7 @@ class Plan {
         };
         for (const LaunchUnit& u : phase_units[ph]) run_unit(u, lane_stream(lane++));
         for (size_t t = i; t < j; ++t)
-          if (ops[t].kind == PlanOp::FUNC) ops[t].fn(lane_stream(lane++));
+          if (ops[t].func_like()) run_op(ops[t], lane_stream(lane++));
         for (int a = 0; a < Fan::NAUX; ++a)
           if (used[a]) {
             GPFVM_CUDA(cudaEventRecord(fan->join[a], fan->aux[a]));

@@ -1,0 +1,211 @@
+// Device building blocks of the tcgen05 mode-product kernel (tc.cu), shared
+// with the persistent plan kernel (persist.cu).  See tc.cu for the method.
+#pragma once
+#include "tc.cuh"
+
+namespace gpfvm {
+
+constexpr int TC_ROWS = 128;
+constexpr int TC_KB = 32;                    // floats per K block (128 bytes)
+constexpr int TC_A_BYTES = TC_ROWS * 128;    // 16 KB per A slice
+constexpr int TC_BREG = 32;                  // B rows per thread / 4: npad <= 128 in registers
+constexpr long long TC_SPIN_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (r, c) (c < 32) in a K-major, 128-byte-swizzled slice
+__device__ __forceinline__ uint32_t sw128(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + (c & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                    // leading byte offset: unused for swizzled K-major
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8-row groups 1024 B apart
+  d |= (uint64_t)1 << 46;                    // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                    // layout: 128-byte swizzle
+  return d;
+}
+
+// kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Per-CTA state for running tensor-core tiles (set up by the kernel: shared
+// operand buffers, the MMA-completion mbarrier, the TMEM accumulator, the
+// barrier phase, an abort flag in shared memory and the status word).
+struct TcCtx {
+  unsigned char *sAhi, *sAlo, *sBhi, *sBlo;
+  uint64_t* bar;
+  uint32_t tmem;
+  uint32_t phase;
+  int* abort_flag;
+  int* status;
+};
+
+// One 128-row output tile t of the op table.  Every thread of the CTA calls
+// it (it synchronises the CTA); threads 0..127 stage the operands and read
+// the accumulator (one row each), the others only join the barriers.
+__device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, i64 t, TcCtx& cx) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const bool act = tid < 128;
+  int lo = 0, hi = nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ops[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const TcOp& op = ops[lo];
+  if (op.skip && *op.skip) return;
+  const int row0 = (int)(t - op.tile_begin) * TC_ROWS;
+  const int K = op.K, N = op.N, R = op.R;
+  const int npad = (N + 15) & ~15;
+  const uint32_t idesc = idesc_tf32(npad);
+  uint32_t acc = 0;
+  // Stage (segment, K block) pairs in order; the next pair's global loads
+  // are issued into registers while the tensor cores work on the current one.
+  const int nkb = (K + TC_KB - 1) / TC_KB;
+  const int nstage = op.nseg * nkb;
+  float ra[TC_ROWS * TC_KB / 128];  // 32 A values per thread
+  float rbh[TC_BREG], rbl[TC_BREG];  // B slice (npad <= 128 rows)
+  const int c = tid & 31, rb = (tid >> 5) & 3;
+  auto load_stage = [&](int st) {
+    if (!act) return;
+    const int s = st / nkb, k0 = (st % nkb) * TC_KB;
+    const float* __restrict__ A = op.A[s];
+    const float* __restrict__ Bh = op.Bhi[s];
+    const float* __restrict__ Bl = op.Blo[s];
+    const int gc = k0 + c;
+#pragma unroll
+    for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
+      const int gr = row0 + rb + 4 * q;
+      ra[q] = (gr < R && gc < K) ? __ldg(&A[(i64)gr * K + gc]) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < TC_BREG; ++q) {
+      const int r = rb + 4 * q;
+      const bool in = (r < N && gc < K && r < npad);
+      rbh[q] = in ? __ldg(&Bh[(i64)r * K + gc]) : 0.0f;
+      rbl[q] = in ? __ldg(&Bl[(i64)r * K + gc]) : 0.0f;
+    }
+  };
+  load_stage(0);
+  for (int st = 0; st < nstage && !*cx.abort_flag; ++st) {
+    const int k0 = (st % nkb) * TC_KB;
+    // registers -> shared (split A into hi / lo), previous MMAs have completed
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
+        const int r = rb + 4 * q;
+        const float v = ra[q], vh = tf32_rna(v);
+        const uint32_t off = sw128(r, c);
+        *(float*)(cx.sAhi + off) = vh;
+        *(float*)(cx.sAlo + off) = v - vh;
+      }
+#pragma unroll
+      for (int q = 0; q < TC_BREG; ++q) {
+        const int r = rb + 4 * q;
+        if (r < npad) {
+          const uint32_t off = sw128(r, c);
+          *(float*)(cx.sBhi + off) = rbh[q];
+          *(float*)(cx.sBlo + off) = rbl[q];
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int kk = min(TC_KB, K - k0);
+      const int ksteps = (kk + 7) / 8;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
+        const uint64_t ah = desc_sw128(smem_u32(cx.sAhi) + koff), al = desc_sw128(smem_u32(cx.sAlo) + koff);
+        const uint64_t bh = desc_sw128(smem_u32(cx.sBhi) + koff), bl = desc_sw128(smem_u32(cx.sBlo) + koff);
+        mma_tf32(cx.tmem, ah, bh, idesc, acc);
+        acc = 1;
+        mma_tf32(cx.tmem, ah, bl, idesc, 1);
+        mma_tf32(cx.tmem, al, bh, idesc, 1);
+      }
+      mma_commit(cx.bar);
+    }
+    if (st + 1 < nstage) load_stage(st + 1);  // overlaps the MMAs
+    const bool ok = mbar_wait(cx.bar, cx.phase);
+    cx.phase ^= 1;
+    if (!ok && tid == 0) {
+      atomicOr(cx.status, (int)DEV_TIMEOUT);
+      *cx.abort_flag = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (*cx.abort_flag) return;
+  // epilogue: row = row0 + tid, columns j < N, rotated store out[j * R + row]
+  if (act) {
+    const int row = row0 + tid;
+    for (int j0 = 0; j0 < npad; j0 += 8) {
+      uint32_t v[8];
+      const uint32_t taddr = cx.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < R) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + q;
+          if (j >= N) break;
+          const i64 o = (i64)j * R + row;
+          float val = __uint_as_float(v[q]);
+          if (op.D) val += op.gamma * op.D[o];
+          if (op.beta != 0.0f) val += op.beta * op.out[o];
+          op.out[o] = val;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+}  // namespace gpfvm
