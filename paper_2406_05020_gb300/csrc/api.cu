@@ -185,11 +185,14 @@ struct gpfvm_problem {
   bool tc_ok = false, use_tc = false;
   float* f_tcsplit = nullptr;
   float *f_tcY = nullptr, *f_tcZ = nullptr;
+  float* f_tcpart = nullptr;  // partial sums of split tensor-core tiles
+  i64 tc_part_total = 0;      // floats f_tcpart needs (largest level)
   std::vector<std::tuple<i64, float, i64, i64>> tc_jobs;  // (factor offset in f_fac, alpha, size, split offset)
   TcOp* d_tcops = nullptr;
   struct TcLevel {
     int off, nops, maxn;
     i64 tiles;
+    int any_split;
   };
   std::vector<TcLevel> tc_levels[2];
   i64 tc_split_total = 0, tc_ops_total = 0;
@@ -837,6 +840,37 @@ struct TcBuild {
   }
 };
 
+// Tiles of the tensor-core levels.  A tile runs its (segment, K block) stages
+// one after the other, so a level with few row tiles and several segments per
+// op (the t level: 32 row tiles x 4 segments on 64^3 cells) is a long chain on
+// a few SMs.  Such ops split their segments into groups, one tile per
+// (row tile, group), as long as the level stays within about two resident
+// CTAs per SM; the groups' partial sums are added in order by tc_sum.
+void tc_group_levels(gpfvm_problem* p, TcBuild& T, int inst) {
+  const i64 slots = 2 * 152;
+  for (auto& L : p->tc_levels[inst]) {
+    i64 rows = 0;
+    for (int o = L.off; o < L.off + L.nops; ++o) rows += (T.ops[o].R + 127) / 128;
+    const i64 per = std::max<i64>(1, slots / std::max<i64>(rows, 1));
+    L.tiles = 0;
+    L.any_split = 0;
+    i64 part = 0;
+    for (int o = L.off; o < L.off + L.nops; ++o) {
+      TcOp& op = T.ops[o];
+      op.sgroups = (int)std::max<i64>(1, std::min<i64>(per, op.nseg));
+      op.tile_begin = L.tiles;
+      L.tiles += (i64)((op.R + 127) / 128) * op.sgroups;
+      op.part = nullptr;
+      if (op.sgroups > 1) {
+        op.part = p->f_tcpart ? p->f_tcpart + part : nullptr;
+        part += (i64)op.sgroups * op.N * op.R;
+        L.any_split = 1;
+      }
+    }
+    p->tc_part_total = std::max(p->tc_part_total, part);
+  }
+}
+
 void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out, int inst) {
   const int d = p->d;
   int n[3] = {1, 1, 1};
@@ -855,12 +889,9 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
     }
   auto fsize = [&](int ax) { return (i64)n[ax] * n[ax]; };
   p->tc_levels[inst].clear();
-  auto begin_level = [&]() { p->tc_levels[inst].push_back({(int)T.ops.size(), 0, 0, 0}); };
+  auto begin_level = [&]() { p->tc_levels[inst].push_back({(int)T.ops.size(), 0, 0, 0, 0}); };
   auto add_op = [&](TcOp op) {
     auto& L = p->tc_levels[inst].back();
-    const i64 tiles = (op.R + 127) / 128;
-    op.tile_begin = L.tiles;
-    L.tiles += tiles;
     L.nops++;
     L.maxn = std::max(L.maxn, op.N);
     if (op.nseg > TC_MAXSEG || op.N > 128) T.ok = false;
@@ -876,6 +907,7 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
   auto blank = [&](int R, int K, int N, float* o) {
     TcOp op{};
     op.R = R; op.K = K; op.N = N; op.out = o;
+    op.sgroups = 1;
     op.skip = (inst == 0 && p->d_st32) ? &p->d_st32->done : nullptr;
     return op;
   };
@@ -886,6 +918,7 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
     op.D = in;
     op.gamma = (float)p->jitter;
     add_op(op);
+    tc_group_levels(p, T, inst);
     return;
   }
   // distinct factors on the last axis (3 axes) and on axis 0
@@ -937,12 +970,14 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
   op.D = in;
   op.gamma = (float)p->jitter;
   add_op(op);
+  tc_group_levels(p, T, inst);
 }
 
 // G_PP on tensor cores as a chain of FUNC ops (one per level) for a phased plan.
 Plan tc_chain(gpfvm_problem* p, int inst) {
   Plan c;
-  for (auto L : p->tc_levels[inst]) c.tc(p->d_tcops + L.off, L.nops, L.tiles, L.maxn, &p->d_st32->pad[1]);
+  for (auto L : p->tc_levels[inst])
+    c.tc(p->d_tcops + L.off, L.nops, L.tiles, L.maxn, &p->d_st32->pad[1], L.any_split);
   return c;
 }
 
@@ -972,6 +1007,8 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
       // host-side bounds check of every tensor-core operand before any launch
       for (const TcOp& op : T.ops) {
         bool ok = p->mem.contains(op.out, 4LL * op.N * op.R) && (!op.D || p->mem.contains(op.D, 4LL * op.N * op.R));
+        ok = ok && op.sgroups >= 1 && op.sgroups <= op.nseg &&
+             (op.sgroups == 1 || p->mem.contains(op.part, 4LL * op.sgroups * op.N * op.R));
         for (int s = 0; s < op.nseg; ++s)
           ok = ok && p->mem.contains(op.A[s], 4LL * op.R * op.K) && p->mem.contains(op.Bhi[s], 4LL * op.N * op.K) &&
                p->mem.contains(op.Blo[s], 4LL * op.N * op.K);
@@ -1286,6 +1323,7 @@ void alloc_all(gpfvm_problem* p) {
   p->f_tcsplit = m.alloc<float>(std::max<i64>(p->tc_split_total, 64));
   p->f_tcY = m.alloc<float>(std::max<i64>((i64)p->tc_nu * N, 64));
   p->f_tcZ = m.alloc<float>(std::max<i64>((i64)p->tc_nw * N, 64));
+  p->f_tcpart = m.alloc<float>(std::max<i64>(p->tc_part_total, 64));
   p->d_tcops = m.alloc<TcOp>(std::max<i64>(p->tc_ops_total, 1));
   p->tc_jobs.clear();
   p->scratch_cap = std::max<i64>(B0.peak, 64);

@@ -22,7 +22,8 @@
 
 namespace gpfvm {
 
-enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV };
+enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM };
+constexpr int P_SUM_CHUNKS = 64;  // items per op of a segment-group reduction
 
 constexpr int P_THREADS = 256;
 constexpr int P_GEMV_ROWS = P_THREADS / 32;  // one warp per row
@@ -256,6 +257,20 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
           p_gemm_dispatch(u.g, u.f32, u.bm, bx, by, zb, sm);
           break;
         }
+        case PU_TCSUM: {
+          // out = sum of the segment groups in order (+ gamma D + beta out), as tc_sum_kernel
+          const TcOp& op = static_cast<const TcOp*>(u.table)[local / P_SUM_CHUNKS];
+          if (op.sgroups <= 1 || (op.skip && *op.skip)) break;
+          const i64 n = (i64)op.N * op.R;
+          for (i64 e = (local % P_SUM_CHUNKS) * P_THREADS + tid; e < n; e += (i64)P_SUM_CHUNKS * P_THREADS) {
+            float v = 0.0f;
+            for (int g = 0; g < op.sgroups; ++g) v += op.part[(i64)g * n + e];
+            if (op.D) v += op.gamma * op.D[e];
+            if (op.beta != 0.0f) v += op.beta * op.out[e];
+            op.out[e] = v;
+          }
+          break;
+        }
         case PU_GEMV: {
           if (u.skip && *u.skip) break;
           const i64 i = local * P_GEMV_ROWS + warp;
@@ -368,8 +383,20 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
   };
   size_t i = 0;
   const auto& ops = plan.ops;
+  std::vector<PUnit> sums;  // reductions of split tensor-core levels of the current phase
+  auto unit_of_sum = [&](const PlanOp& op) {
+    if (op.kind == PlanOp::TC && op.tc_split) {
+      PUnit u{};
+      u.kind = PU_TCSUM;
+      u.table = op.tc_ops;
+      u.nops = op.tc_nops;
+      u.items = (i64)op.tc_nops * P_SUM_CHUNKS;
+      sums.push_back(u);
+    }
+  };
   while (i < ops.size()) {
     PPhase P{(int)units.size(), 0, 0};
+    sums.clear();
     auto push = [&](PUnit u) {
       u.item_begin = P.items;
       P.items += u.items;
@@ -380,6 +407,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
       PUnit u;
       if (!unit_of(ops[i], u)) return nullptr;
       if (u.items > 0) push(u);
+      unit_of_sum(ops[i]);
       ++i;
     } else {
       const int ph = ops[i].phase;
@@ -409,10 +437,21 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
         PUnit u;
         if (!unit_of(ops[t], u)) return nullptr;
         if (u.items > 0) push(u);
+        unit_of_sum(ops[t]);
       }
       i = j;
     }
     if (P.nunits > 0) phases.push_back(P);
+    if (!sums.empty()) {  // the next phase may read what the split levels wrote
+      PPhase S{(int)units.size(), 0, 0};
+      for (PUnit u : sums) {
+        u.item_begin = S.items;
+        S.items += u.items;
+        units.push_back(u);
+        S.nunits++;
+      }
+      phases.push_back(S);
+    }
   }
   if (phases.empty()) return nullptr;
   auto* pr = new PersistProg();

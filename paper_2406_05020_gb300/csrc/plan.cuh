@@ -32,6 +32,7 @@ struct PlanOp {
   int tc_nops = 0, tc_maxn = 0;
   i64 tc_tiles = 0;
   int* tc_status = nullptr;
+  int tc_split = 0;  // some op of the level sums segment groups (second launch)
   // SCALE: X (rows x cols, FP64 or FP32) column j times lt[j]^pw (pw = -1 or -0.5)
   void* sc_X = nullptr;
   int sc_rows = 0, sc_f32 = 0;
@@ -164,10 +165,11 @@ class Plan {
     op.fn = std::move(f);
     ops.push_back(op);
   }
-  void tc(const TcOp* d_ops, int nops, i64 tiles, int maxn, int* status) {
+  void tc(const TcOp* d_ops, int nops, i64 tiles, int maxn, int* status, int split = 0) {
     PlanOp op;
     op.kind = PlanOp::TC;
     op.tc_ops = d_ops; op.tc_nops = nops; op.tc_tiles = tiles; op.tc_maxn = maxn; op.tc_status = status;
+    op.tc_split = split;
     ops.push_back(op);
   }
   void scale(void* X, int rows, i64 cols, const double* lt, double pw, bool f32) {
@@ -343,7 +345,8 @@ class Plan {
     else if (op.kind == PlanOp::GEMV32)
       launch_gemv32(op.m, op.n, (const float*)op.A, op.lda, (const float*)op.x, (float*)op.y, (float)op.alpha,
                     (float)op.beta, op.tri, st, skip);
-    else if (op.kind == PlanOp::TC) launch_tc_modes(op.tc_ops, op.tc_nops, op.tc_tiles, op.tc_maxn, op.tc_status, st);
+    else if (op.kind == PlanOp::TC)
+      launch_tc_modes(op.tc_ops, op.tc_nops, op.tc_tiles, op.tc_maxn, op.tc_status, st, op.tc_split);
     else if (op.kind == PlanOp::SCALE) {
       if (op.sc_f32) scale_cols32((float*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
       else scale_cols((double*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);

@@ -59,9 +59,25 @@ __global__ void __launch_bounds__(128, 1) tc_mode_kernel(const TcOp* __restrict_
   }
 }
 
+// out = sum_g part[g] (groups in order) + gamma D + beta out, for the split ops
+__global__ void __launch_bounds__(256) tc_sum_kernel(const TcOp* __restrict__ ops) {
+  pdl_wait();
+  const TcOp& op = ops[blockIdx.y];
+  if (op.sgroups <= 1 || (op.skip && *op.skip)) return;
+  const i64 n = (i64)op.N * op.R;
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int g = 0; g < op.sgroups; ++g) v += op.part[(i64)g * n + e];
+    if (op.D) v += op.gamma * op.D[e];
+    if (op.beta != 0.0f) v += op.beta * op.out[e];
+    op.out[e] = v;
+  }
+}
+
 int tc_smem_bytes(int ncols) { return 2 * TC_A_BYTES + 2 * ncols * 128 + 1024; }
 
-void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st) {
+void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st,
+                     int any_split) {
   if (nops <= 0 || total_tiles <= 0) return;
   const int npad = (max_n + 15) & ~15;
   int ncols = 32;
@@ -75,6 +91,7 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
   }
   const int grid = (int)std::min<i64>(total_tiles, 2 * 152);
   launch_pdl(tc_mode_kernel, grid, 128, smem, st, d_ops, nops, total_tiles, ncols, status);
+  if (any_split) launch_pdl(tc_sum_kernel, dim3(2 * 152, nops), 256, 0, st, d_ops);
 }
 
 // hi = tf32(alpha * F), lo = alpha * F - hi for an n x k row-major factor

@@ -18,11 +18,20 @@ struct TcOp {
   float* out;
   const float* D;
   float gamma, beta;
-  i64 tile_begin;   // first tile (128 rows) of this op in the launch
+  i64 tile_begin;   // first tile of this op in the launch
   const int* skip;  // op does nothing if *skip
+  // Segment groups: with sgroups > 1 the segments are split into sgroups
+  // contiguous groups, one tile per (128 rows, group), each writing its
+  // partial sum to part + group * N * R; tc_sum then adds the groups in order
+  // (and gamma D, beta out) into out.
+  int sgroups;
+  float* part;
 };
 
-void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st);
+// Runs the tiles of one level; with any_split the partial sums of split ops
+// are then reduced (a second, elementwise launch).
+void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st,
+                     int any_split = 0);
 void tc_split(const float* F, i64 n, float alpha, float* hi, float* lo, cudaStream_t st);
 int tc_smem_bytes(int ncols);
 

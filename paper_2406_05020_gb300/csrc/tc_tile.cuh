@@ -95,7 +95,11 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
   }
   const TcOp& op = ops[lo];
   if (op.skip && *op.skip) return;
-  const int row0 = (int)(t - op.tile_begin) * TC_ROWS;
+  const int sg = op.sgroups;
+  const i64 local = t - op.tile_begin;
+  const int grp = (int)(local % sg);
+  const int row0 = (int)(local / sg) * TC_ROWS;
+  const int s_lo = grp * op.nseg / sg;
   const int K = op.K, N = op.N, R = op.R;
   const int npad = (N + 15) & ~15;
   const uint32_t idesc = idesc_tf32(npad);
@@ -103,13 +107,13 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
   // Stage (segment, K block) pairs in order; the next pair's global loads
   // are issued into registers while the tensor cores work on the current one.
   const int nkb = (K + TC_KB - 1) / TC_KB;
-  const int nstage = op.nseg * nkb;
+  const int nstage = ((grp + 1) * op.nseg / sg - s_lo) * nkb;
   float ra[TC_ROWS * TC_KB / 128];  // 32 A values per thread
   float rbh[TC_BREG], rbl[TC_BREG];  // B slice (npad <= 128 rows)
   const int c = tid & 31, rb = (tid >> 5) & 3;
   auto load_stage = [&](int st) {
     if (!act) return;
-    const int s = st / nkb, k0 = (st % nkb) * TC_KB;
+    const int s = s_lo + st / nkb, k0 = (st % nkb) * TC_KB;
     const float* __restrict__ A = op.A[s];
     const float* __restrict__ Bh = op.Bhi[s];
     const float* __restrict__ Bl = op.Blo[s];
@@ -179,7 +183,10 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
   }
   if (*cx.abort_flag) return;
   // epilogue: row = row0 + tid, columns j < N, rotated store out[j * R + row]
+  // (a partial sum of a segment group goes to its slice of op.part)
   if (act) {
+    const bool fin = sg == 1;
+    float* __restrict__ dst = fin ? op.out : op.part + (i64)grp * N * R;
     const int row = row0 + tid;
     for (int j0 = 0; j0 < npad; j0 += 8) {
       uint32_t v[8];
@@ -196,9 +203,11 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
           if (j >= N) break;
           const i64 o = (i64)j * R + row;
           float val = __uint_as_float(v[q]);
-          if (op.D) val += op.gamma * op.D[o];
-          if (op.beta != 0.0f) val += op.beta * op.out[o];
-          op.out[o] = val;
+          if (fin) {
+            if (op.D) val += op.gamma * op.D[o];
+            if (op.beta != 0.0f) val += op.beta * op.out[o];
+          }
+          dst[o] = val;
         }
       }
     }
