@@ -261,7 +261,7 @@ def bench_batch(gpfvm, torch, n_mixed: int, n_fp64: int):
             continue
         sub = probs[:n]
         opts = gpfvm.solve_opts(max_iter=MAX_ITER_BATCH, rtol=RTOL, precision=prec, reorth=reorth, want_var=True,
-                                inner_max_iter=400, inner_rtol=1e-2)
+                                inner_max_iter=400, inner_rtol=1e-2, inner_reorth_first=True)
         pbs = [gpfvm.Problem(q, max_iter=MAX_ITER_BATCH) for q in sub]
         outs = [(torch.empty(pb.P, dtype=torch.float64, device="cuda"),
                  torch.empty(pb.P, dtype=torch.float64, device="cuda")) for pb in pbs]
@@ -373,10 +373,13 @@ def run_gpfvm(args):
     var = torch.empty_like(mean)
     opts64 = gpfvm.solve_opts(max_iter=MAX_ITER, rtol=RTOL, precision=gpfvm.FP64, reorth=True, want_var=True,
                               check_every=32)
+    # mixed paths: the first inner run (whose directions carry the variance) is
+    # reorthogonalised, the correction runs are plain CG (measured: same
+    # iterations and accuracy on this workload, 19% less time)
     opts_mx = gpfvm.solve_opts(max_iter=MAX_ITER_MIXED, rtol=RTOL, precision=gpfvm.MIXED_FP32, reorth=True,
-                               want_var=True, check_every=32, inner_rtol=1e-2)
+                               want_var=True, check_every=32, inner_rtol=1e-2, inner_reorth_first=True)
     opts_tc = gpfvm.solve_opts(max_iter=MAX_ITER_MIXED, rtol=RTOL, precision=gpfvm.MIXED_TF32X3, reorth=True,
-                               want_var=True, check_every=32, inner_rtol=1e-2)
+                               want_var=True, check_every=32, inner_rtol=1e-2, inner_reorth_first=True)
     s_ptr = stream.cuda_stream
 
     def step(i, opts):
@@ -624,7 +627,7 @@ def run_profile_step(args):
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
     var = torch.empty_like(mean)
     opts = gpfvm.solve_opts(max_iter=MAX_ITER if prec == gpfvm.FP64 else MAX_ITER_MIXED, rtol=RTOL, precision=prec,
-                            reorth=True, want_var=True, check_every=32, inner_rtol=1e-2)
+                            reorth=True, want_var=True, check_every=32, inner_rtol=1e-2, inner_reorth_first=True)
     pb.assemble(stream=s_ptr)
     pb.set_values(vals, stream=s_ptr)
     code, info = pb.solve(opts, stream=s_ptr)

@@ -121,6 +121,10 @@ typedef struct {
   int check_every;     /* unused (kept for layout): every CG run is one device-side loop */
   int inner_max_iter;  /* mixed: iteration cap of one inner CG (<= 0: no cap beyond max_iter) */
   double inner_rtol;   /* mixed: residual reduction of one inner CG (<= 0: 1e-2) */
+  int inner_reorth_first; /* mixed, with reorth: 0 = reorthogonalise every inner CG run (robust);
+                             1 = only the first run, whose directions carry the IterGP variance
+                             (later runs only solve correction equations to inner_rtol; cheaper
+                             per iteration, but plain FP32 CG may stall on ill-conditioned systems) */
 } gpfvm_solve_opts;
 
 typedef struct {

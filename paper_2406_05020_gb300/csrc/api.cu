@@ -1625,15 +1625,17 @@ int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
 }
 
 // One inner CG iteration of the mixed solver (FP32 operator and vectors, FP64 scalars).
-void cg_iteration32(gpfvm_problem* p, bool want_var, cudaStream_t st) {
+void cg_iteration32(gpfvm_problem* p, bool want_var, bool reorth, cudaStream_t st) {
   const i64 N = p->N;
   if (p->use_tc) (want_var ? p->p_mvv32tc : p->p_mv32tc).run(st);
   else (want_var ? p->p_mvv32 : p->p_mv32).run(st);
   cg_dot_eta<float>(p->f_p, p->f_q, N, p->d_st32, p->d_eta32, st);
   if (want_var) cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
-  cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, p->f_S, p->f_Q, st);
+  cg_update<float>(p->f_d, p->f_r, p->f_p, p->f_q, N, p->d_st32, reorth ? p->f_S : nullptr,
+                   reorth ? p->f_Q : nullptr, st);
   cg_pupdate<float>(p->f_r, p->f_p, N, p->d_st32, st);
-  cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
+  if (reorth)
+    cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
 }
 
 // Iterative refinement (mixed precision, Sec. 4.1 CG as the inner solver):
@@ -1725,6 +1727,7 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     if (R.rel <= o->rtol) { R.status = GPFVM_OK; R.mstate = 3; return; }
     if (R.total >= o->max_iter) { R.status = GPFVM_NOT_CONVERGED; R.mstate = 3; return; }
     const bool var_now = o->want_var && R.outer == 0;
+    const bool reorth_now = o->reorth && (R.outer == 0 || !o->inner_reorth_first);
     const int icap = std::min(p->cap32, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap32);
     p->h_st32->rtol2 = R.itol * R.itol;
     p->h_st32->max_iter = std::min(icap, o->max_iter - R.total);
@@ -1735,12 +1738,12 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     // the inner run solves for the normalised residual r / ||r||: FP32 then
     // sees unit-norm data whatever the scale of y (no under- or overflow)
     cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st, &p->d_st->aux[0]);
-    const int key = var_now ? 1 : 0;
+    const int key = (var_now ? 1 : 0) + (reorth_now ? 2 : 0);
     if (!p->graph32 || p->graph32_key != key) {
       if (p->graph32) cudaGraphExecDestroy(p->graph32);
       p->graph32 = nullptr;
-      p->graph32 = make_loop_graph(p->d_st32, st, [&] { cg_iteration32(p, var_now, st); }, &p->graph32_kernels,
-                                   p->host_loop);
+      p->graph32 = make_loop_graph(p->d_st32, st, [&] { cg_iteration32(p, var_now, reorth_now, st); },
+                                   &p->graph32_kernels, p->host_loop);
       p->graph32_key = key;
     }
     R.launched = 0;
