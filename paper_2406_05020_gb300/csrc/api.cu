@@ -110,6 +110,8 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       need(op.A, e * ((i64)(op.m - 1) * op.lda + op.n), "gemv A");
       need(op.x, e * op.n, "gemv x");
       need(op.y, e * op.m, "gemv y");
+      need(op.z, e * op.m, "gemv z");
+      need(op.zs, 8 * op.m, "gemv zs");
     } else if (op.kind == PlanOp::SCALE) {
       need(op.sc_X, (op.sc_f32 ? 4 : 8) * (i64)op.sc_rows * op.sc_cols, "scale X");
       need(op.sc_lt, 8 * op.sc_cols, "scale lt");
@@ -173,11 +175,19 @@ struct gpfvm_problem {
   bool sicbc = false;
   int MK = 0, MR = 0, nK[3] = {1, 1, 1};
   double *d_QK[3] = {}, *d_lam[3] = {}, *d_lt = nullptr, *d_ltinv = nullptr;
-  double *d_BT = nullptr, *d_Et = nullptr, *d_E1 = nullptr, *d_Sc = nullptr, *d_LS = nullptr, *d_LSinv = nullptr,
-         *d_LSinvT = nullptr, *d_sscr = nullptr, *d_Ft = nullptr, *d_F = nullptr, *d_R = nullptr;
-  double *d_hK = nullptr, *d_tR = nullptr, *d_uR = nullptr, *d_H[3] = {}, *d_Hsq[3] = {};
-  float *f_QK[3] = {}, *f_Ft = nullptr, *f_F = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_hK = nullptr,
-        *f_tR = nullptr, *f_uR = nullptr;
+  // E~ = G_RK (x)Q Lambda~^-1 (MR x MK) and its transpose; set 0's parts of the
+  // solve vectors are coordinates in the eigenbasis (x)Q_i
+  double *d_BT = nullptr, *d_Et = nullptr, *d_EtT = nullptr, *d_E1 = nullptr, *d_Sc = nullptr, *d_LS = nullptr,
+         *d_LSinv = nullptr, *d_LSinvT = nullptr, *d_sscr = nullptr, *d_R = nullptr;
+  double *d_tR = nullptr, *d_uR = nullptr, *d_Hsq[3] = {}, *d_yBt = nullptr;
+  float *f_QK[3] = {}, *f_Et = nullptr, *f_EtT = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_tR = nullptr,
+        *f_uR = nullptr;
+  // set-0 factors with the eigenbasis multiplied in: F_i Q_i (cells x set 0)
+  // under the key of F_i, Q_i^T C_i (set 0 x prediction grid) under that of C_i
+  std::map<FKey, i64> facq_off;
+  double* d_facq = nullptr;
+  float* f_facq = nullptr;
+  i64 nfacq = 0;
   JacobiJob* d_jac = nullptr;
   unsigned int* d_psync = nullptr;  // grid-barrier words of the persistent plan kernel
   int* d_jac_sweeps = nullptr;  // 2 per axis: FP32 and FP64 sweeps of the last assembly
@@ -296,13 +306,26 @@ std::vector<KTerm> pp_terms(const gpfvm_problem* p) {
   return ts;
 }
 
-// cells -> set s (transpose=true) or set s -> cells (transpose=false)
-std::vector<KTerm> pb_terms(const gpfvm_problem* p, int s, bool to_set) {
+// Factors of set 0 with its eigenbasis multiplied in (structured IC/BC stage):
+// F_i Q_i for cells x set 0, Q_i^T C_i for set 0 x prediction grid.
+MatRef facq_ref(const gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab, bool transpose) {
+  const i64 off = p->facq_off.at(FKey(ax, ka, aa, kb, ab));
+  const i64 nb = fam_n(p, ax, kb, ab);
+  MatRef m{p->building_f32 ? (const double*)(p->f_facq + off) : p->d_facq + off, nb, 1};
+  if (transpose) std::swap(m.rs, m.cs);
+  return m;
+}
+
+// cells -> set s (transpose=true) or set s -> cells (transpose=false); with
+// fold, set 0 of the structured stage in its eigenbasis
+std::vector<KTerm> pb_terms(const gpfvm_problem* p, int s, bool to_set, bool fold = false) {
+  const bool q = fold && s == 0 && p->sicbc;
   std::vector<KTerm> ts;
   for (int a = 0; a < p->nterms; ++a) {
     KTerm t{};
     t.c = p->coef[a];
-    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 1, s, to_set);
+    for (int i = 0; i < p->d; ++i)
+      t.f[i] = q ? facq_ref(p, i, 0, p->alpha[a][i], 1, s, to_set) : fac_ref(p, i, 0, p->alpha[a][i], 1, s, to_set);
     ts.push_back(t);
   }
   return ts;
@@ -319,10 +342,11 @@ std::vector<KTerm> ppred_terms(const gpfvm_problem* p) {
   return ts;
 }
 
-std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s) {
+std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s, bool fold = false) {
+  const bool q = fold && s == 0 && p->sicbc;
   KTerm t{};
   t.c = 1.0;
-  for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 1, s, 2, 0, true);
+  for (int i = 0; i < p->d; ++i) t.f[i] = q ? facq_ref(p, i, 1, s, 2, 0, true) : fac_ref(p, i, 1, s, 2, 0, true);
   return {t};
 }
 
@@ -361,69 +385,71 @@ struct Builder {
     peak = std::max(peak, scr.used);
   }
 
-  // out = G_BP in (cells -> all sets), into g (M)
-  void bp(Plan& plan, const double* in, double* g) {
+  // out = G_BP in (cells -> all sets), into g (M); fold: set 0 in its eigenbasis
+  void bp(Plan& plan, const double* in, double* g, bool fold = false) {
     int dc[3], ds[3];
     dims_cells(p, dc);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, dc, ds, 1, pb_terms(p, s, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+      kron(plan, dc, ds, 1, pb_terms(p, s, true, fold), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
     }
   }
-  // out (+)= scale * G_PB w
-  void pb(Plan& plan, const double* w, double* out, double scale, bool accumulate) {
+  // out (+)= scale * G_PB w; fold: the set-0 part of w in its eigenbasis
+  void pb(Plan& plan, const double* w, double* out, double scale, bool accumulate, bool fold = false) {
     int dc[3], ds[3];
     dims_cells(p, dc);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, ds, dc, 1, pb_terms(p, s, false), scale * p->s2, at(w, p->sets[s].off), out,
+      kron(plan, ds, dc, 1, pb_terms(p, s, false, fold), scale * p->s2, at(w, p->sets[s].off), out,
            (accumulate || s > 0) ? 1.0 : 0.0, nullptr, 0.0);
     }
   }
-  // w = G_BB^-1 g via the explicit inverse factor
-  // w = G_BB^-1 g with set 0 through its eigen-structure and the rest through S:
-  //   h = A^-1 g_K ;  t_R = g_R - F^T g_K ;  w_R = S^-1 t_R ;  w_K = h - F w_R
-  void hsolve_struct(Plan& plan, const double* g, double* w) {
+  // G_BB^-1 with the structured IC/BC stage, in the eigenbasis of set 0: the
+  // set-0 parts g~_K, w~_K of g and w are coordinates in (x)Q_i (the folded
+  // G_BP / G_PB / prediction factors produce and consume them), so
+  //   t_R  = g_R - E~ g~_K            (E~ = G_RK (x)Q Lambda~^-1)
+  //   w_R  = L_S^-T L_S^-1 t_R       (S = G_RR - G_RK A^-1 G_KR = L_S L_S^T)
+  //   w~_K = Lambda~^-1 g~_K - E~^T w_R
+  // is a chain of four GEMVs (one phase each).
+  void hsolve_eig(Plan& plan, const double* g, double* w) {
     const int MK = p->MK, MR = p->MR;
-    int dK[3];
-    dims_set(p, 0, dK);
-    KTerm QT{}, Qn{};
-    QT.c = Qn.c = 1.0;
-    for (int i = 0; i < p->d; ++i) {
-      const double* q = f32 ? (const double*)p->f_QK[i] : p->d_QK[i];
-      QT.f[i] = MatRef{q, 1, p->nK[i]};
-      Qn.f[i] = MatRef{q, p->nK[i], 1};
-    }
-    double* hK = f32 ? (double*)p->f_hK : p->d_hK;
-    kron(plan, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0);
-    const double* lt = p->d_lt;
-    const bool F32 = f32;
-    plan.scale(hK, 1, MK, lt, -1.0, F32);
-    kron(plan, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0);
+    const bool F = f32;
+    Plan c;
     if (MR > 0) {
-      const size_t es = f32 ? sizeof(float) : sizeof(double);
-      double* tR = f32 ? (double*)p->f_tR : p->d_tR;
-      double* uR = f32 ? (double*)p->f_uR : p->d_uR;
-      const double* gR = at(g, MK);
-      double* wR = at(w, MK);
-      plan.copy(tR, gR, (i64)es * MR);
-      if (f32) {
-        plan.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
-        plan.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
-        plan.gemv32(MR, MR, p->f_LSinvT, MR, (const float*)uR, (float*)wR, 2);
-        plan.gemv32(MK, MR, p->f_F, MR, (const float*)wR, (float*)w, 0, -1.0, 1.0);
-      } else {
-        plan.gemv(MR, MK, p->d_Ft, MK, g, tR, -1.0, 1.0, 0);
-        plan.gemv(MR, MR, p->d_LSinv, MR, tR, uR, 1.0, 0.0, 1);
-        plan.gemv(MR, MR, p->d_LSinvT, MR, uR, wR, 1.0, 0.0, 2);
-        plan.gemv(MK, MR, p->d_F, MR, wR, w, -1.0, 1.0, 0);
-      }
+      double* tR = F ? (double*)p->f_tR : p->d_tR;
+      double* uR = F ? (double*)p->f_uR : p->d_uR;
+      const void* Et = F ? (const void*)p->f_Et : (const void*)p->d_Et;
+      const void* EtT = F ? (const void*)p->f_EtT : (const void*)p->d_EtT;
+      const void* LSi = F ? (const void*)p->f_LSinv : (const void*)p->d_LSinv;
+      const void* LSiT = F ? (const void*)p->f_LSinvT : (const void*)p->d_LSinvT;
+      c.gemvz(F, MR, MK, Et, MK, g, tR, -1.0, 1.0, at(g, MK), nullptr);
+      c.gemvz(F, MR, MR, LSi, MR, tR, uR, 1.0, 0.0, nullptr, nullptr, 1);
+      c.gemvz(F, MR, MR, LSiT, MR, uR, at(w, MK), 1.0, 0.0, nullptr, nullptr, 2);
+      c.gemvz(F, MK, MR, EtT, MR, at(w, MK), w, -1.0, 1.0, g, p->d_ltinv);
+    } else {
+      c.gemvz(F, MK, 0, g, 0, g, w, 0.0, 1.0, g, p->d_ltinv);
     }
+    plan.zip({&c});
   }
+  // y~ (set 0 in its eigenbasis, the other sets as they are) from y (FP64)
+  void to_eigenbasis(Plan& plan, const double* y, double* yt) {
+    const int MK = p->MK, MR = p->MR;
+    int dK[3], nd = 0;
+    KTerm QT{};
+    QT.c = 1.0;
+    for (int i = 0; i < p->d; ++i) {
+      if (p->nK[i] == 1 && !(i == p->d - 1 && nd == 0)) continue;  // Q = [1] on a singleton axis
+      QT.f[nd] = MatRef{p->d_QK[i], 1, p->nK[i]};
+      dK[nd++] = p->nK[i];
+    }
+    kron(plan, dK, dK, 1, {QT}, 1.0, y, yt, 0.0, nullptr, 0.0, nullptr, nd);
+    if (MR > 0) plan.copy(yt + MK, y + MK, (i64)sizeof(double) * MR);
+  }
+  // w = G_BB^-1 g (w~ / g~ in the eigenbasis of set 0 with the structured stage)
   void hsolve(Plan& plan, const double* g, double* t, double* w) {
     const int M = (int)p->M;
     if (p->sicbc) {
-      hsolve_struct(plan, g, w);
+      hsolve_eig(plan, g, w);
       return;
     }
     if (f32) {
@@ -434,56 +460,9 @@ struct Builder {
     plan.gemv(M, M, p->d_Linv, M, g, t, 1.0, 0.0, 1);
     plan.gemv(M, M, p->d_LinvT, M, t, w, 1.0, 0.0, 2);
   }
-  // The structured G_BB^-1 apply as two zipped chains: the A^-1 transforms of
-  // g_K (singleton axes of set 0 dropped) and the Schur-complement GEMVs.
   void hsolve_phased(Plan& plan, const double* g, double* w) {
-    if (!p->sicbc) {
-      double* t = f32 ? (double*)p->f_t : p->d_t;
-      hsolve(plan, g, t, w);
-      return;
-    }
-    const int MK = p->MK, MR = p->MR;
-    int dK[3], nd = 0;
-    KTerm QT{}, Qn{};
-    QT.c = Qn.c = 1.0;
-    for (int i = 0; i < p->d; ++i) {
-      if (p->nK[i] == 1 && !(i == p->d - 1 && nd == 0)) continue;  // Q = [1] on a singleton axis
-      const double* q = f32 ? (const double*)p->f_QK[i] : p->d_QK[i];
-      QT.f[nd] = MatRef{q, 1, p->nK[i]};
-      Qn.f[nd] = MatRef{q, p->nK[i], 1};
-      dK[nd++] = p->nK[i];
-    }
-    Plan c1, c2;
-    double* hK = f32 ? (double*)p->f_hK : p->d_hK;
-    kron(c1, dK, dK, 1, {QT}, 1.0, g, hK, 0.0, nullptr, 0.0, nullptr, nd);
-    const double* lt = p->d_lt;
-    const bool F32 = f32;
-    c1.scale(hK, 1, MK, lt, -1.0, F32);
-    kron(c1, dK, dK, 1, {Qn}, 1.0, hK, w, 0.0, nullptr, 0.0, nullptr, nd);
-    if (MR > 0) {
-      const size_t es = f32 ? sizeof(float) : sizeof(double);
-      double* tR = f32 ? (double*)p->f_tR : p->d_tR;
-      double* uR = f32 ? (double*)p->f_uR : p->d_uR;
-      const double* gR = at(g, MK);
-      double* wR = at(w, MK);
-      c2.copy(tR, gR, (i64)es * MR);
-      if (f32) {
-        c2.gemv32(MR, MK, p->f_Ft, MK, (const float*)g, (float*)tR, 0, -1.0, 1.0);
-        c2.gemv32(MR, MR, p->f_LSinv, MR, (const float*)tR, (float*)uR, 1);
-        c2.gemv32(MR, MR, p->f_LSinvT, MR, (const float*)uR, (float*)wR, 2);
-      } else {
-        c2.gemv(MR, MK, p->d_Ft, MK, g, tR, -1.0, 1.0, 0);
-        c2.gemv(MR, MR, p->d_LSinv, MR, tR, uR, 1.0, 0.0, 1);
-        c2.gemv(MR, MR, p->d_LSinvT, MR, uR, wR, 1.0, 0.0, 2);
-      }
-      plan.zip({&c1, &c2});
-      Plan c3;
-      if (f32) c3.gemv32(MK, MR, p->f_F, MR, (const float*)wR, (float*)w, 0, -1.0, 1.0);
-      else c3.gemv(MK, MR, p->d_F, MR, wR, w, -1.0, 1.0, 0);
-      plan.append(c3);
-    } else {
-      plan.zip({&c1});
-    }
+    double* t = f32 ? (double*)p->f_t : p->d_t;
+    hsolve(plan, g, t, w);
   }
 
   // out = G^ in as zipped stages; with u != null also u = Lhat k(X*)^T in.
@@ -501,7 +480,7 @@ struct Builder {
     else kron(A[0], dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(A[1 + s], dc, ds, 1, pb_terms(p, s, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+      kron(A[1 + s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
     }
     if (u) kron(A.back(), dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
     {
@@ -518,8 +497,8 @@ struct Builder {
     std::vector<Plan> PB(p->nsets), VS(u ? p->nsets : 0);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(PB[s], ds, dc, 1, pb_terms(p, s, false), -p->s2, at(w, p->sets[s].off), out, 1.0, nullptr, 0.0);
-      if (u) kron(VS[s], ds, dp, 1, bpred_terms(p, s), -p->s2, at(w, p->sets[s].off), u, 1.0, nullptr, 0.0);
+      kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), out, 1.0, nullptr, 0.0);
+      if (u) kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), u, 1.0, nullptr, 0.0);
     }
     stage_end();
     std::vector<Plan> heads;
@@ -546,15 +525,6 @@ struct Builder {
     dims_cells(p, dc);
     kron(plan, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
   }
-  // out = G^ in = G_PP in - G_PB G_BB^-1 G_BP in ; leaves w = G_BB^-1 G_BP in
-  void ghat(Plan& plan, const double* in, double* out, double* g, double* t, double* w, int* count) {
-    if (p->M > 0) {
-      bp(plan, in, g);
-      hsolve(plan, g, t, w);
-    }
-    pp(plan, in, out, count);
-    if (p->M > 0) pb(plan, w, out, -1.0, true);
-  }
   // u (+)= scale * (L_PDE k(X*))^T v
   void to_pred_cells(Plan& plan, const double* v, double* u, double scale, bool acc) {
     int dc[3], dp[3];
@@ -562,13 +532,13 @@ struct Builder {
     dims_pred(p, dp);
     kron(plan, dc, dp, 1, ppred_terms(p), scale * p->s2, v, u, acc ? 1.0 : 0.0, nullptr, 0.0);
   }
-  void to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc) {
+  void to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc, bool fold = false) {
     int ds[3], dp[3];
     dims_pred(p, dp);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
-      kron(plan, ds, dp, 1, bpred_terms(p, s), scale * p->s2, at(w, p->sets[s].off), u, (acc || s > 0) ? 1.0 : 0.0,
-           nullptr, 0.0);
+      kron(plan, ds, dp, 1, bpred_terms(p, s, fold), scale * p->s2, at(w, p->sets[s].off), u,
+           (acc || s > 0) ? 1.0 : 0.0, nullptr, 0.0);
     }
   }
 };
@@ -580,12 +550,11 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
   const int M = (int)p->M, MK = p->MK, MR = p->MR, d = p->d;
   int dK[3];
   dims_set(p, 0, dK);
-  KTerm QT{}, Qn{};
-  QT.c = Qn.c = 1.0;
+  KTerm QT{};
+  QT.c = 1.0;
   int maxn = 1;
   for (int i = 0; i < d; ++i) {
     QT.f[i] = MatRef{p->d_QK[i], 1, p->nK[i]};
-    Qn.f[i] = MatRef{p->d_QK[i], p->nK[i], 1};
     maxn = std::max(maxn, p->nK[i]);
   }
   gpfvm_problem* pp = p;
@@ -620,15 +589,35 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
     pl.func([=](cudaStream_t st) {
       transpose(pp->d_LSinv, pp->d_LSinvT, MR, MR, st);
       scale_cols(pp->d_Et, MR, MK, pp->d_lt, -1.0, st);
+      transpose(pp->d_Et, pp->d_EtT, MR, MK, st);
     });
-    B.kron(pl, dK, dK, MR, {Qn}, 1.0, p->d_Et, p->d_Ft, 0.0, nullptr, 0.0);
-    pl.func([=](cudaStream_t st) { transpose(pp->d_Ft, pp->d_F, MR, MK, st); });
+  }
+  // fold the eigenbasis into set 0's cell and prediction factors
+  for (auto& ko : p->facq_off) {
+    int ax, ka, aa, kb, ab;
+    std::tie(ax, ka, aa, kb, ab) = ko.first;
+    const int n = p->nK[ax];
+    const double* src = p->d_fac + p->fac_off.at(ko.first);
+    GemmDesc g{};
+    g.batch = 1;
+    if (ka == 0) {  // F_i Q_i: (cells x n) (n x n)
+      g.m = p->nc[ax]; g.n = n; g.k = n;
+      g.a_rs = n; g.a_cs = 1; g.b_rs = n; g.b_cs = 1; g.c_rs = n;
+      g.tile = dense_tile(g.m, g.n);
+      pl.gemm(g, {{GemmGroup{p->d_facq + ko.second, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{src, p->d_QK[ax], 1.0}}}});
+    } else {  // Q_i^T C_i: (n x n) (n x pred)
+      g.m = n; g.n = p->npred[ax]; g.k = n;
+      g.a_rs = 1; g.a_cs = n; g.b_rs = g.n; g.b_cs = 1; g.c_rs = g.n;
+      g.tile = dense_tile(g.m, g.n);
+      pl.gemm(g, {{GemmGroup{p->d_facq + ko.second, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_QK[ax], src, 1.0}}}});
+    }
   }
   pl.func([=](cudaStream_t st) {
     for (int i = 0; i < d; ++i) convert_d2f(pp->d_QK[i], pp->f_QK[i], (i64)pp->nK[i] * pp->nK[i], st);
+    convert_d2f(pp->d_facq, pp->f_facq, pp->nfacq, st);
     if (MR > 0) {
-      convert_d2f(pp->d_Ft, pp->f_Ft, (i64)MR * MK, st);
-      convert_d2f(pp->d_F, pp->f_F, (i64)MR * MK, st);
+      convert_d2f(pp->d_Et, pp->f_Et, (i64)MR * MK, st);
+      convert_d2f(pp->d_EtT, pp->f_EtT, (i64)MR * MK, st);
       convert_d2f(pp->d_LSinv, pp->f_LSinv, (i64)MR * MR, st);
       convert_d2f(pp->d_LSinvT, pp->f_LSinvT, (i64)MR * MR, st);
     }
@@ -637,9 +626,11 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
 
 // Cholesky-stage variance with the structured IC/BC stage:
 //   k_B^T G_BB^-1 k_B = k_K^T A^-1 k_K + || L_S^-1 (k_R - F^T k_K) ||^2
-// term 1 = sigma^4 sum_m prod_i H_i[m_i,p_i]^2 / lambda~[m] with H_i = Q_i^T F_{K,i}
-// is itself a Kronecker product applied to the tensor 1/lambda~; term 2 uses
-// R = L_S^-1 F^T and runs over row chunks.
+// with F = A^-1 G_KR.  Term 1 = sigma^4 sum_m prod_i H_i[m_i,p_i]^2 / lambda~[m]
+// with H_i = Q_i^T C_i (the folded prediction factor of set 0) is itself a
+// Kronecker product applied to the tensor 1/lambda~; in term 2,
+// F^T k_K = E~ (x)H_i k, so R = L_S^-1 E~ meets the folded factors; it runs
+// over row chunks.
 void build_sicbc_var(gpfvm_problem* p, Builder& B) {
   Plan& pl = p->p_vB;
   const int MK = p->MK, MR = p->MR, d = p->d;
@@ -651,13 +642,7 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
   T1.c = 1.0;
   for (int i = 0; i < d; ++i) {
     const int n = p->nK[i], pi = p->npred[i];
-    GemmDesc g{};
-    g.m = n; g.n = pi; g.k = n;
-    g.a_rs = 1; g.a_cs = n; g.b_rs = pi; g.b_cs = 1; g.c_rs = pi;
-    g.batch = 1; g.tile = 2;
-    const double* FK = p->d_fac + p->fac_off.at(FKey(i, 1, 0, 2, 0));
-    pl.gemm(g, {{GemmGroup{p->d_H[i], nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_QK[i], FK, 1.0}}}});
-    double* H = p->d_H[i];
+    const double* H = p->d_facq + p->facq_off.at(FKey(i, 1, 0, 2, 0));
     double* Hs = p->d_Hsq[i];
     pl.func([=](cudaStream_t st) { square(H, Hs, (i64)n * pi, st); });
     T1.f[i] = MatRef{p->d_Hsq[i], 1, pi};
@@ -669,7 +654,7 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
     g.m = MR; g.n = MK; g.k = MR;
     g.a_rs = MR; g.a_cs = 1; g.b_rs = MK; g.b_cs = 1; g.c_rs = MK;
     g.batch = 1; g.tri = TRI_A_LOWER; g.tile = dense_tile(MR, MK);
-    pl.gemm(g, {{GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_LSinv, p->d_Ft, 1.0}}}});
+    pl.gemm(g, {{GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_LSinv, p->d_Et, 1.0}}}});
   }
   const int Rrows = p->vb_rows;
   double* vB = p->d_vB;
@@ -689,8 +674,8 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
       B.kron(pl, ds, dP, rows, bpred_terms(p, s), p->s2, p->d_vbchunk, p->d_vbY, first ? 0.0 : 1.0, nullptr, 0.0);
       first = false;
     }
-    B.kron(pl, dK, dP, rows, bpred_terms(p, 0), -p->s2, p->d_R + (i64)m0 * MK, p->d_vbY, first ? 0.0 : 1.0, nullptr,
-           0.0);
+    B.kron(pl, dK, dP, rows, bpred_terms(p, 0, true), -p->s2, p->d_R + (i64)m0 * MK, p->d_vbY, first ? 0.0 : 1.0,
+           nullptr, 0.0);
     const double* Y = p->d_vbY;
     pl.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
   }
@@ -749,7 +734,11 @@ void build_plans(gpfvm_problem* p, Builder& B) {
       if (rhs) GPFVM_CUDA(cudaMemcpyAsync(b, rhs, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
       else GPFVM_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * N, st));
     });
-    if (M > 0) {
+    if (M > 0 && p->sicbc) {
+      B.to_eigenbasis(p->p_rhs, p->d_yB, p->d_yBt);
+      B.hsolve(p->p_rhs, p->d_yBt, p->d_t, p->d_w);
+      B.pb(p->p_rhs, p->d_w, b, -1.0, true, true);
+    } else if (M > 0) {
       B.hsolve(p->p_rhs, p->d_yB, p->d_t, p->d_w);
       B.pb(p->p_rhs, p->d_w, b, -1.0, true);
     }
@@ -762,7 +751,7 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr);
   p->p_var_cg = Plan();
   B.to_pred_cells(p->p_var_cg, p->d_p, p->d_u, 1.0, false);
-  if (M > 0) B.to_pred_sets(p->p_var_cg, p->d_w, p->d_u, -1.0, true);
+  if (M > 0) B.to_pred_sets(p->p_var_cg, p->d_w, p->d_u, -1.0, true, true);
   // ---- operator plans for gpfvm_gram_matvec / true residual
   for (int k = 0; k < 4; ++k) p->p_op[k] = Plan();
   B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
@@ -774,12 +763,13 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   // ---- posterior mean
   p->p_mean = Plan();
   if (M > 0) {
-    B.bp(p->p_mean, p->d_x, p->d_g);
+    // with the structured stage, g and y~_B hold set 0 in its eigenbasis
+    B.bp(p->p_mean, p->d_x, p->d_g, true);
     double *g = p->d_g, *g2 = p->d_g2;
-    const double* yB = p->d_yB;
+    const double* yB = p->sicbc ? p->d_yBt : p->d_yB;
     p->p_mean.func([=](cudaStream_t st) { axpby(yB, g, g2, 1.0, -1.0, M, st); });
     B.hsolve(p->p_mean, p->d_g2, p->d_t, p->d_w);
-    B.to_pred_sets(p->p_mean, p->d_w, p->d_mean, 1.0, false);
+    B.to_pred_sets(p->p_mean, p->d_w, p->d_mean, 1.0, false, true);
   }
   B.to_pred_cells(p->p_mean, p->d_x, p->d_mean, 1.0, M > 0);
   // ---- Cholesky-stage variance term vB[p] = || L^-1 k_B(x_p) ||^2 in row chunks
@@ -992,7 +982,7 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
   B.ghat_phased(p->p_mvv32, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), D(p->f_u), nullptr);
   p->p_var32 = Plan();
   B.to_pred_cells(p->p_var32, D(p->f_p), D(p->f_u), 1.0, false);
-  if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true);
+  if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true, true);
   p->p_pp32 = Plan();
   B.pp(p->p_pp32, D(p->f_vin), D(p->f_vout), nullptr);
   // tensor-core variants (split TF32 G_PP)
@@ -1202,7 +1192,6 @@ void alloc_all(gpfvm_problem* p) {
       p->d_QK[i] = m.alloc<double>((i64)n * n);
       p->d_lam[i] = m.alloc<double>(n);
       p->f_QK[i] = m.alloc<float>((i64)n * n);
-      p->d_H[i] = m.alloc<double>((i64)n * p->npred[i]);
       p->d_Hsq[i] = m.alloc<double>((i64)n * p->npred[i]);
       jobs[i] = JacobiJob{p->d_fac + p->fac_off.at(FKey(i, 1, 0, 1, 0)), p->d_QK[i], p->d_lam[i], n, 1e-14,
                           p->d_jac_sweeps + 2 * i};
@@ -1211,14 +1200,25 @@ void alloc_all(gpfvm_problem* p) {
     GPFVM_CUDA(cudaMemcpy(p->d_jac, jobs.data(), sizeof(JacobiJob) * p->d, cudaMemcpyHostToDevice));
     p->d_lt = m.alloc<double>(MK);
     p->d_ltinv = m.alloc<double>(MK);
-    p->d_hK = m.alloc<double>(MK);
-    p->f_hK = m.alloc<float>(MK);
+    p->d_yBt = m.alloc<double>(M);
+    p->facq_off.clear();
+    i64 nq = 0;
+    auto add_q = [&](const FKey& k, i64 size) {
+      if (p->facq_off.count(k)) return;
+      p->facq_off[k] = nq;
+      nq += size;
+    };
+    for (int a = 0; a < p->nterms; ++a)
+      for (int i = 0; i < p->d; ++i) add_q(FKey(i, 0, p->alpha[a][i], 1, 0), (i64)p->nc[i] * p->sets[0].n[i]);
+    for (int i = 0; i < p->d; ++i) add_q(FKey(i, 1, 0, 2, 0), (i64)p->sets[0].n[i] * p->npred[i]);
+    p->nfacq = std::max<i64>(nq, 1);
+    p->d_facq = m.alloc<double>(p->nfacq);
+    p->f_facq = m.alloc<float>(p->nfacq);
     if (MR > 0) {
       p->d_BT = m.alloc<double>(MR * MK);
       p->d_Et = m.alloc<double>(MR * MK);
+      p->d_EtT = m.alloc<double>(MR * MK);
       p->d_E1 = m.alloc<double>(MR * MK);
-      p->d_Ft = m.alloc<double>(MR * MK);
-      p->d_F = m.alloc<double>(MR * MK);
       p->d_R = m.alloc<double>(MR * MK);
       p->d_Sc = m.alloc<double>(MR * MR);
       p->d_LS = m.alloc<double>(MR * MR);
@@ -1227,8 +1227,8 @@ void alloc_all(gpfvm_problem* p) {
       p->d_sscr = m.alloc<double>(MR * MR / 4 + 64 * MR + 64);
       p->d_tR = m.alloc<double>(MR);
       p->d_uR = m.alloc<double>(MR);
-      p->f_Ft = m.alloc<float>(MR * MK);
-      p->f_F = m.alloc<float>(MR * MK);
+      p->f_Et = m.alloc<float>(MR * MK);
+      p->f_EtT = m.alloc<float>(MR * MK);
       p->f_LSinv = m.alloc<float>(MR * MR);
       p->f_LSinvT = m.alloc<float>(MR * MR);
       p->f_tR = m.alloc<float>(MR);

@@ -93,7 +93,10 @@ __global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict
   const T s = warp_row_dot(row, x, jlo, jhi, lane);
   if (lane == 0) {
     T v = (T)op.alpha * s;
-    if (op.beta != 0.0) v += (T)op.beta * reinterpret_cast<const T*>(op.z)[i];
+    if (op.beta != 0.0) {
+      const T zi = reinterpret_cast<const T*>(op.z)[i];
+      v += (T)op.beta * (op.zs ? (T)op.zs[i] * zi : zi);
+    }
     reinterpret_cast<T*>(op.y)[i] = v;
   }
 }

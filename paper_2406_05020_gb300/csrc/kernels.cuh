@@ -81,6 +81,7 @@ struct MGemv {
   int m, n, tri, pad;
   double alpha, beta;
   const int* skip;
+  const double* zs;  // optional per-row scale of z: y = alpha A x + beta zs .* z
 };
 void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st);
 

@@ -137,7 +137,10 @@ __device__ __forceinline__ void p_mgemv_row(const PUnit& u, i64 w, int lane) {
   const T s = warp_row_dot(row, reinterpret_cast<const T*>(op.x), jlo, jhi, lane);
   if (lane == 0) {
     T v = (T)op.alpha * s;
-    if (op.beta != 0.0) v += (T)op.beta * reinterpret_cast<const T*>(op.z)[i];
+    if (op.beta != 0.0) {
+      const T zi = reinterpret_cast<const T*>(op.z)[i];
+      v += (T)op.beta * (op.zs ? (T)op.zs[i] * zi : zi);
+    }
     reinterpret_cast<T*>(op.y)[i] = v;
   }
 }

@@ -25,6 +25,8 @@ struct PlanOp {
   i64 lda = 0;
   const double* x = nullptr;
   double* y = nullptr;
+  const double* z = nullptr;   // phased GEMV only: y = alpha A x + beta zs .* z (z = y if null)
+  const double* zs = nullptr;  // phased GEMV only: per-row scale of z (FP64)
   double alpha = 1.0, beta = 0.0;
   std::function<void(cudaStream_t)> fn;
   // TC: tensor-core mode products of one level (see tc.cu)
@@ -159,6 +161,16 @@ class Plan {
     op.alpha = alpha; op.beta = beta; op.tri = tri;
     ops.push_back(op);
   }
+  // y = alpha A x + beta zs .* z (zs may be null), FP64 or FP32 (f32) data; only inside zipped chains
+  void gemvz(bool f32, int m, int n, const void* A, i64 lda, const void* x, void* y, double alpha, double beta,
+             const void* z, const double* zs, int tri = 0) {
+    PlanOp op;
+    op.kind = f32 ? PlanOp::GEMV32 : PlanOp::GEMV;
+    op.m = m; op.n = n; op.A = (const double*)A; op.lda = lda; op.x = (const double*)x; op.y = (double*)y;
+    op.alpha = alpha; op.beta = beta; op.tri = tri;
+    op.z = (const double*)z; op.zs = zs;
+    ops.push_back(op);
+  }
   void func(std::function<void(cudaStream_t)> f) {
     PlanOp op;
     op.kind = PlanOp::FUNC;
@@ -269,6 +281,9 @@ class Plan {
   }
   void finalize() {
     release();
+    for (auto& op : ops)
+      if ((op.kind == PlanOp::GEMV || op.kind == PlanOp::GEMV32) && op.phase < 0 && (op.z || op.zs))
+        throw CudaError{cudaErrorInvalidValue, "plan: a GEMV with z or zs must be part of a zipped chain"};
     phase_units.assign(n_phases, {});
     if (!segs.empty()) {
       GPFVM_CUDA(cudaMalloc(&d_segs, segs.size() * sizeof(GemmSeg)));
@@ -320,7 +335,7 @@ class Plan {
           const bool is32 = op.kind == PlanOp::GEMV32;
           if (op.phase != ph || !(op.kind == PlanOp::GEMV || is32) || (int)is32 != f32) continue;
           MGemv m{};
-          m.A = op.A; m.x = op.x; m.z = op.y; m.y = op.y;
+          m.A = op.A; m.x = op.x; m.z = op.z ? op.z : op.y; m.y = op.y; m.zs = op.zs;
           m.lda = op.lda; m.row_begin = rows; m.m = op.m; m.n = op.n; m.tri = op.tri;
           m.alpha = op.alpha; m.beta = op.beta; m.skip = skip;
           rows += op.m;
