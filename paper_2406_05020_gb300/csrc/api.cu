@@ -83,6 +83,7 @@ struct DevBuf {
 // Host-side bounds check of every GEMM/GEMV operand of a plan against the
 // problem's allocations, done once when the plan is built (before any launch).
 void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
+  for (auto& b : plan.bgs) check_plan_ranges(*b, mem, name);
   auto need = [&](const void* p, i64 len, const char* what) {
     if (!p || len <= 0) return;
     if (!mem.contains(p, len)) {
@@ -117,7 +118,10 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       need(op.sc_lt, 8 * op.sc_cols, "scale lt");
     } else if (op.kind == PlanOp::COPY) {
       need(op.cp_dst, op.cp_bytes, "copy dst");
-      need(op.cp_src, op.cp_bytes, "copy src");
+      need(op.cp_src, op.cp_bytes, "copy src");    } else if (op.kind == PlanOp::ADD) {
+      const i64 e = op.ad_f32 ? 4 : 8;
+      need(op.ad_X, e * op.ad_n, "add X");
+      need(op.ad_P, e * ((i64)(op.ad_np - 1) * op.ad_stride + op.ad_n), "add parts");
     }
   }
 }
@@ -410,12 +414,21 @@ struct Builder {
   //   t_R  = g_R - E~ g~_K            (E~ = G_RK (x)Q Lambda~^-1)
   //   w_R  = L_S^-T L_S^-1 t_R       (S = G_RR - G_RK A^-1 G_KR = L_S L_S^T)
   //   w~_K = Lambda~^-1 g~_K - E~^T w_R
-  // is a chain of four GEMVs (one phase each).
-  void hsolve_eig(Plan& plan, const double* g, double* w) {
-    const int MK = p->MK, MR = p->MR;
+  // is a chain of four dependent GEMVs; without the structured stage it is
+  // w = L^-T L^-1 g.  Appends the chain to c (one op per level) and returns in
+  // ready[0] / ready[1] the number of levels after which the part of w of set 0
+  // / of the other sets is final.
+  void hsolve_chain(Plan& c, const double* g, double* w, int* ready) {
+    const int M = (int)p->M, MK = p->MK, MR = p->MR;
     const bool F = f32;
-    Plan c;
-    if (MR > 0) {
+    if (!p->sicbc) {
+      double* t = F ? (double*)p->f_t : p->d_t;
+      const void* Li = F ? (const void*)p->f_Linv : (const void*)p->d_Linv;
+      const void* LiT = F ? (const void*)p->f_LinvT : (const void*)p->d_LinvT;
+      c.gemvz(F, M, M, Li, M, g, t, 1.0, 0.0, nullptr, nullptr, 1);
+      c.gemvz(F, M, M, LiT, M, t, w, 1.0, 0.0, nullptr, nullptr, 2);
+      ready[0] = ready[1] = 2;
+    } else if (MR > 0) {
       double* tR = F ? (double*)p->f_tR : p->d_tR;
       double* uR = F ? (double*)p->f_uR : p->d_uR;
       const void* Et = F ? (const void*)p->f_Et : (const void*)p->d_Et;
@@ -426,10 +439,12 @@ struct Builder {
       c.gemvz(F, MR, MR, LSi, MR, tR, uR, 1.0, 0.0, nullptr, nullptr, 1);
       c.gemvz(F, MR, MR, LSiT, MR, uR, at(w, MK), 1.0, 0.0, nullptr, nullptr, 2);
       c.gemvz(F, MK, MR, EtT, MR, at(w, MK), w, -1.0, 1.0, g, p->d_ltinv);
+      ready[0] = 4;
+      ready[1] = 3;
     } else {
       c.gemvz(F, MK, 0, g, 0, g, w, 0.0, 1.0, g, p->d_ltinv);
+      ready[0] = ready[1] = 1;
     }
-    plan.zip({&c});
   }
   // y~ (set 0 in its eigenbasis, the other sets as they are) from y (FP64)
   void to_eigenbasis(Plan& plan, const double* y, double* yt) {
@@ -446,78 +461,91 @@ struct Builder {
     if (MR > 0) plan.copy(yt + MK, y + MK, (i64)sizeof(double) * MR);
   }
   // w = G_BB^-1 g (w~ / g~ in the eigenbasis of set 0 with the structured stage)
-  void hsolve(Plan& plan, const double* g, double* t, double* w) {
-    const int M = (int)p->M;
-    if (p->sicbc) {
-      hsolve_eig(plan, g, w);
-      return;
-    }
-    if (f32) {
-      plan.gemv32(M, M, p->f_Linv, M, (const float*)g, (float*)t, 1);
-      plan.gemv32(M, M, p->f_LinvT, M, (const float*)t, (float*)w, 2);
-      return;
-    }
-    plan.gemv(M, M, p->d_Linv, M, g, t, 1.0, 0.0, 1);
-    plan.gemv(M, M, p->d_LinvT, M, t, w, 1.0, 0.0, 2);
+  void hsolve(Plan& plan, const double* g, double* w) {
+    Plan c;
+    int ready[2];
+    hsolve_chain(c, g, w, ready);
+    plan.zip({&c});
   }
-  void hsolve_phased(Plan& plan, const double* g, double* w) {
-    double* t = f32 ? (double*)p->f_t : p->d_t;
-    hsolve(plan, g, t, w);
+  // n elements of the plan's element type from the scratch pool
+  double* take(i64 n) {
+    double* r = scr.take(f32 ? (n + 1) / 2 : n);
+    peak = std::max(peak, scr.used);
+    return r;
   }
 
-  // out = G^ in as zipped stages; with u != null also u = Lhat k(X*)^T in.
-  //   stage A (reads in):  G_PP in, G_BP in (each set), L_PDE k(X*)^T in
-  //   stage B:             w = G_BB^-1 g
-  //   stage C (reads w):   out -= G_PB w, u -= k_B(X*)^T w  (last levels paired)
+  // out = G^ in = G_PP in - G_PB G_BB^-1 G_BP in; with u != null also
+  // u = Lhat k(X*)^T in.  Every product is a chain of dependent launches; the
+  // chains are placed by phase so that each starts as soon as its input is final:
+  //   phase 0..        G_PP in (into out), G_BP in (each set, into g), L k(X*)^T in (into u)
+  //   after G_BP:      w = G_BB^-1 g (hsolve_chain)
+  //   after w_s final: -G_PB w_s and -k_s(X*)^T w_s per set s, into separate buffers
+  //   last:            out += sum of the G_PB parts, u += sum of the k(X*) parts
+  // (sets in order, so the result does not depend on the concurrency).  With
+  // IC/BC sets, G_PP runs beside all of it as a background chain.
   void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
                    Plan* pp_chain = nullptr) {
     int dc[3], ds[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
-    stage_begin();
-    std::vector<Plan> A(1 + p->nsets + (u ? 1 : 0));
-    if (pp_chain) A[0] = std::move(*pp_chain);
-    else kron(A[0], dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
-    for (int s = 0; s < p->nsets; ++s) {
-      dims_set(p, s, ds);
-      kron(A[1 + s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
-    }
-    if (u) kron(A.back(), dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
-    {
-      std::vector<const Plan*> c;
-      for (auto& x : A) c.push_back(&x);
-      plan.zip(c);
-    }
-    stage_end();
-    if (p->M == 0) return;
-    stage_begin();
-    hsolve_phased(plan, g, w);
-    stage_end();
-    stage_begin();
-    std::vector<Plan> PB(p->nsets), VS(u ? p->nsets : 0);
-    for (int s = 0; s < p->nsets; ++s) {
-      dims_set(p, s, ds);
-      kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), out, 1.0, nullptr, 0.0);
-      if (u) kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), u, 1.0, nullptr, 0.0);
-    }
-    stage_end();
-    std::vector<Plan> heads;
-    std::vector<const Plan*> hp;
-    std::vector<Plan> tpb, tvs;
-    for (int s = 0; s < p->nsets; ++s) {
-      heads.push_back(PB[s].slice(0, PB[s].ops.size() - 1));
-      tpb.push_back(PB[s].slice(PB[s].ops.size() - 1, PB[s].ops.size()));
-      if (u) {
-        heads.push_back(VS[s].slice(0, VS[s].ops.size() - 1));
-        tvs.push_back(VS[s].slice(VS[s].ops.size() - 1, VS[s].ops.size()));
+    const int ns = p->nsets;
+    stage_begin();  // one stage: every intermediate below is distinct
+    Plan PP, PR;
+    if (pp_chain) PP = std::move(*pp_chain);
+    else kron(PP, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
+    if (u) kron(PR, dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
+    std::vector<const Plan*> cs;
+    std::vector<int> st;
+    auto put = [&](const Plan& c, int s0) {
+      if (c.ops.empty()) return;
+      cs.push_back(&c);
+      st.push_back(s0);
+    };
+    // G_PP (the longest chain) runs as the plan's background chain; only the
+    // final sum waits for it
+    const bool bgpp = p->M > 0 && !PP.ops.empty();
+    if (!bgpp) put(PP, 0);
+    if (u) put(PR, 0);
+    std::vector<Plan> BP(ns), PB(ns), VS(ns);
+    Plan H, SO, SU;
+    if (p->M > 0) {
+      int lbp = 0;
+      for (int s = 0; s < ns; ++s) {
+        dims_set(p, s, ds);
+        kron(BP[s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+        lbp = std::max(lbp, (int)BP[s].ops.size());
+        put(BP[s], 0);
       }
+      int ready[2];
+      hsolve_chain(H, g, w, ready);
+      put(H, lbp);
+      const i64 sN = (p->N + 31) / 32 * 32, sP = (p->P + 31) / 32 * 32;
+      double* T = take(ns * sN);
+      double* V = u ? take(ns * sP) : nullptr;
+      for (int s = 0; s < ns; ++s) {
+        dims_set(p, s, ds);
+        const int r = lbp + ready[s == 0 ? 0 : 1];
+        kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), at(T, s * sN), 0.0,
+             nullptr, 0.0);
+        put(PB[s], r);
+        if (u) {
+          kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, s * sP), 0.0,
+               nullptr, 0.0);
+          put(VS[s], r);
+        }
+      }
+      SO.add(out, T, ns, sN, p->N, f32);
+      if (u) SU.add(u, V, ns, sP, p->P, f32);
     }
-    for (auto& x : heads) hp.push_back(&x);
-    plan.zip(hp);
-    std::vector<const Plan*> a, b;
-    for (auto& x : tpb) a.push_back(&x);
-    for (auto& x : tvs) b.push_back(&x);
-    plan.zip_pairs(a, b);
+    if (bgpp) plan.fork(std::move(PP));
+    plan.zip_at(cs, st);
+    if (bgpp) plan.join();
+    if (!SO.ops.empty()) {
+      std::vector<const Plan*> last{&SO};
+      if (!SU.ops.empty()) last.push_back(&SU);
+      plan.zip(last);
+    }
+    stage_end();
   }
 
   void pp(Plan& plan, const double* in, double* out, int* count) {
@@ -736,10 +764,10 @@ void build_plans(gpfvm_problem* p, Builder& B) {
     });
     if (M > 0 && p->sicbc) {
       B.to_eigenbasis(p->p_rhs, p->d_yB, p->d_yBt);
-      B.hsolve(p->p_rhs, p->d_yBt, p->d_t, p->d_w);
+      B.hsolve(p->p_rhs, p->d_yBt, p->d_w);
       B.pb(p->p_rhs, p->d_w, b, -1.0, true, true);
     } else if (M > 0) {
-      B.hsolve(p->p_rhs, p->d_yB, p->d_t, p->d_w);
+      B.hsolve(p->p_rhs, p->d_yB, p->d_w);
       B.pb(p->p_rhs, p->d_w, b, -1.0, true);
     }
   }
@@ -768,7 +796,7 @@ void build_plans(gpfvm_problem* p, Builder& B) {
     double *g = p->d_g, *g2 = p->d_g2;
     const double* yB = p->sicbc ? p->d_yBt : p->d_yB;
     p->p_mean.func([=](cudaStream_t st) { axpby(yB, g, g2, 1.0, -1.0, M, st); });
-    B.hsolve(p->p_mean, p->d_g2, p->d_t, p->d_w);
+    B.hsolve(p->p_mean, p->d_g2, p->d_w);
     B.to_pred_sets(p->p_mean, p->d_w, p->d_mean, 1.0, false, true);
   }
   B.to_pred_cells(p->p_mean, p->d_x, p->d_mean, 1.0, M > 0);

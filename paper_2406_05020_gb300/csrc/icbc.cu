@@ -272,6 +272,23 @@ void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cud
   launch_pdl(k_scale_cols<float>, g, 256, 0, st, X, rows, cols, lt, pw);
 }
 
+template <typename T>
+__global__ void k_add_parts(T* __restrict__ X, const T* __restrict__ P, int np, i64 stride, i64 n) {
+  pdl_wait();
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
+    T v = X[e];
+    for (int k = 0; k < np; ++k) v += P[(i64)k * stride + e];
+    X[e] = v;
+  }
+}
+void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaStream_t st) {
+  if (n <= 0 || np <= 0) return;
+  int g = ceil_div(n, 256);
+  if (g > 8192) g = 8192;
+  if (f32) launch_pdl(k_add_parts<float>, g, 256, 0, st, (float*)X, (const float*)P, np, stride, n);
+  else launch_pdl(k_add_parts<double>, g, 256, 0, st, (double*)X, (const double*)P, np, stride, n);
+}
+
 // out[m] = 1/lt[m] (the weight tensor of the A^-1 quadratic form)
 __global__ void k_recip(const double* __restrict__ lt, double* __restrict__ out, i64 n) {
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x)

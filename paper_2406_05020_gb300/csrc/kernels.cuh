@@ -114,6 +114,9 @@ void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0,
                    double* lt, cudaStream_t st);
 void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
 void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
+// X[i] += P[i] + P[stride + i] + ... + P[(np-1) stride + i] for i < n, added
+// in that order (FP64, or FP32 when f32)
+void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaStream_t st);
 void recip(const double* lt, double* out, i64 n, cudaStream_t st);
 void square(const double* in, double* out, i64 n, cudaStream_t st);
 

@@ -17,17 +17,19 @@
 
 #include "gemm_tiles.cuh"
 #include "persist.cuh"
+#include <functional>
+
 #include "plan.cuh"
 #include "tc_tile.cuh"
 
 namespace gpfvm {
 
-enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM };
+enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM, PU_ADD };
 constexpr int P_SUM_CHUNKS = 64;  // items per op of a segment-group reduction
 
 constexpr int P_THREADS = 256;
 constexpr int P_GEMV_ROWS = P_THREADS / 32;  // one warp per row
-constexpr int P_ELEMS = 4 * P_THREADS;       // elements per SCALE / COPY item
+constexpr int P_ELEMS = 4 * P_THREADS;       // elements per SCALE / COPY / ADD item
 
 struct PUnit {
   int kind, f32, bm, nops;
@@ -39,10 +41,12 @@ struct PUnit {
   i64 cols, elems;
   const double* lt;
   double pw;
-  // COPY (4-byte words)
+  // COPY (4-byte words); ADD: dst[e] += sum_k src[k stride + e], e < words
   void* dst;
   const void* src;
   i64 words;
+  int np;
+  i64 stride;
   // single GEMM
   GemmDesc g;
   int tiles_x, tiles_y;
@@ -167,6 +171,18 @@ __device__ __forceinline__ void p_scale_item(const PUnit& u, i64 item) {
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void p_add_item(const PUnit& u, i64 item) {
+  T* X = static_cast<T*>(u.dst);
+  const T* P = static_cast<const T*>(u.src);
+  const i64 e0 = item * P_ELEMS;
+  for (i64 e = e0 + threadIdx.x; e < e0 + P_ELEMS && e < u.words; e += P_THREADS) {
+    T v = X[e];
+    for (int k = 0; k < u.np; ++k) v += P[(i64)k * u.stride + e];
+    X[e] = v;
+  }
+}
+
 // Returns false if the barrier gave up (then *abort is set for the CTA).
 __device__ __forceinline__ bool grid_barrier(unsigned int* sync, int* status, int* abort_sm) {
   __syncthreads();
@@ -244,6 +260,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
         case PU_SCALE:
           if (u.f32) p_scale_item<float>(u, local);
           else p_scale_item<double>(u, local);
+          break;
+        case PU_ADD:
+          if (u.f32) p_add_item<float>(u, local);
+          else p_add_item<double>(u, local);
           break;
         case PU_COPY: {
           const i64 w0 = local * P_ELEMS;
@@ -326,7 +346,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
   std::vector<PPhase> phases;
   std::vector<PUnit> units;
   int tc_maxn = 0;
-  auto unit_of = [&](const PlanOp& op, PUnit& u) -> bool {
+  auto unit_of = [&](const Plan& plan, const PlanOp& op, PUnit& u) -> bool {
     u = PUnit{};
     switch (op.kind) {
       case PlanOp::TC:
@@ -352,6 +372,16 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
         u.dst = op.cp_dst;
         u.src = op.cp_src;
         u.words = op.cp_bytes / 4;
+        u.items = (u.words + P_ELEMS - 1) / P_ELEMS;
+        return true;
+      case PlanOp::ADD:
+        u.kind = PU_ADD;
+        u.f32 = op.ad_f32;
+        u.dst = op.ad_X;
+        u.src = op.ad_P;
+        u.np = op.ad_np;
+        u.stride = op.ad_stride;
+        u.words = op.ad_n;
         u.items = (u.words + P_ELEMS - 1) / P_ELEMS;
         return true;
       case PlanOp::GEMM: {
@@ -384,8 +414,6 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
         return false;  // host callbacks cannot run inside the kernel
     }
   };
-  size_t i = 0;
-  const auto& ops = plan.ops;
   std::vector<PUnit> sums;  // reductions of split tensor-core levels of the current phase
   auto unit_of_sum = [&](const PlanOp& op) {
     if (op.kind == PlanOp::TC && op.tc_split) {
@@ -397,7 +425,20 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
       sums.push_back(u);
     }
   };
+  // a background chain (FORK) runs in place: the kernel executes phases in order
+  std::function<bool(const Plan&)> emit = [&](const Plan& plan) -> bool {
+  const auto& ops = plan.ops;
+  size_t i = 0;
   while (i < ops.size()) {
+    if (ops[i].kind == PlanOp::FORK) {
+      if (!emit(*plan.bgs[ops[i].bg])) return false;
+      ++i;
+      continue;
+    }
+    if (ops[i].kind == PlanOp::JOIN) {
+      ++i;
+      continue;
+    }
     PPhase P{(int)units.size(), 0, 0};
     sums.clear();
     auto push = [&](PUnit u) {
@@ -408,7 +449,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
     };
     if (ops[i].phase < 0) {
       PUnit u;
-      if (!unit_of(ops[i], u)) return nullptr;
+      if (!unit_of(plan, ops[i], u)) return false;
       if (u.items > 0) push(u);
       unit_of_sum(ops[i]);
       ++i;
@@ -438,7 +479,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
       for (size_t t = i; t < j; ++t) {
         if (!ops[t].func_like()) continue;
         PUnit u;
-        if (!unit_of(ops[t], u)) return nullptr;
+        if (!unit_of(plan, ops[t], u)) return false;
         if (u.items > 0) push(u);
         unit_of_sum(ops[t]);
       }
@@ -456,7 +497,9 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
       phases.push_back(S);
     }
   }
-  if (phases.empty()) return nullptr;
+  return true;
+  };
+  if (!emit(plan) || phases.empty()) return nullptr;
   auto* pr = new PersistProg();
   int tc_cols = 0;
   if (tc_maxn > 0) {

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <functional>
+#include <memory>
 
 #include "kernels.cuh"
 #include "persist.cuh"
@@ -13,9 +14,11 @@
 namespace gpfvm {
 
 struct PlanOp {
-  // FUNC runs a host callback; TC, SCALE and COPY are typed device ops that
-  // the persistent plan kernel can also execute (they run like FUNC ops in run()).
-  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY } kind;
+  // FUNC runs a host callback; TC, SCALE, COPY and ADD are typed device ops
+  // that the persistent plan kernel can also execute (they run like FUNC ops in run()).
+  // FORK starts background chain `bg` of the plan on its own stream; JOIN
+  // makes the plan's stream wait for it.
+  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY, ADD, FORK, JOIN } kind;
   int phase = -1;  // ops sharing a phase id (>= 0, consecutive) are independent: merged launches
   GemmDesc g;
   int seg0 = 0, group0 = 0;
@@ -45,7 +48,13 @@ struct PlanOp {
   void* cp_dst = nullptr;
   const void* cp_src = nullptr;
   i64 cp_bytes = 0;
-  bool func_like() const { return kind == FUNC || kind == TC || kind == SCALE || kind == COPY; }
+  // ADD: ad_X[i] += sum_k ad_P[k ad_stride + i] (k ascending), i < ad_n
+  void* ad_X = nullptr;
+  const void* ad_P = nullptr;
+  int ad_np = 0, ad_f32 = 0;
+  i64 ad_stride = 0, ad_n = 0;
+  int bg = -1;  // FORK: index into Plan::bgs
+  bool func_like() const { return kind == FUNC || kind == TC || kind == SCALE || kind == COPY || kind == ADD; }
 };
 
 // One merged launch of a phase: a table of GEMM ops (same element type and
@@ -64,12 +73,18 @@ struct Fan {
   static constexpr int NAUX = 3;
   cudaStream_t aux[NAUX] = {};
   cudaEvent_t fork = nullptr, join[NAUX] = {};
+  // the background chain of a plan (FORK .. JOIN) runs on bgs
+  cudaStream_t bgs = nullptr;
+  cudaEvent_t bg_fork = nullptr, bg_join = nullptr;
   void create() {
     for (int a = 0; a < NAUX; ++a) {
       GPFVM_CUDA(cudaStreamCreateWithFlags(&aux[a], cudaStreamNonBlocking));
       GPFVM_CUDA(cudaEventCreateWithFlags(&join[a], cudaEventDisableTiming));
     }
     GPFVM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    GPFVM_CUDA(cudaStreamCreateWithFlags(&bgs, cudaStreamNonBlocking));
+    GPFVM_CUDA(cudaEventCreateWithFlags(&bg_fork, cudaEventDisableTiming));
+    GPFVM_CUDA(cudaEventCreateWithFlags(&bg_join, cudaEventDisableTiming));
   }
   void destroy() {
     for (int a = 0; a < NAUX; ++a) {
@@ -79,7 +94,12 @@ struct Fan {
       join[a] = nullptr;
     }
     if (fork) cudaEventDestroy(fork);
+    if (bgs) cudaStreamDestroy(bgs);
+    if (bg_fork) cudaEventDestroy(bg_fork);
+    if (bg_join) cudaEventDestroy(bg_join);
     fork = nullptr;
+    bgs = nullptr;
+    bg_fork = bg_join = nullptr;
   }
 };
 
@@ -96,6 +116,7 @@ class Plan {
   const int* skip = nullptr;  // device flag: when set, every GEMM/GEMV of the plan is a no-op
   const Fan* fan = nullptr;    // optional: run the independent launches of a phase concurrently
   PersistProg* prog = nullptr; // optional: the whole plan as one cooperative launch (persist.cu)
+  std::vector<std::shared_ptr<Plan>> bgs;  // background chains (FORK / JOIN)
 
   ~Plan() { release(); }
   void release() {
@@ -119,6 +140,7 @@ class Plan {
       groups = std::move(o.groups);
       ops = std::move(o.ops);
       phase_units = std::move(o.phase_units);
+      bgs = std::move(o.bgs);
       n_phases = o.n_phases;
       skip = o.skip;
       fan = o.fan;
@@ -196,6 +218,26 @@ class Plan {
     op.cp_dst = dst; op.cp_src = src; op.cp_bytes = bytes;
     ops.push_back(op);
   }
+  void add(void* X, const void* P, int np, i64 stride, i64 n, bool f32) {
+    PlanOp op;
+    op.kind = PlanOp::ADD;
+    op.ad_X = X; op.ad_P = P; op.ad_np = np; op.ad_stride = stride; op.ad_n = n; op.ad_f32 = f32 ? 1 : 0;
+    ops.push_back(op);
+  }
+  // Runs `chain` concurrently with the ops that follow, up to the next join():
+  // they must neither write what the chain reads nor touch what it writes.
+  void fork(Plan&& chain) {
+    bgs.push_back(std::make_shared<Plan>(std::move(chain)));
+    PlanOp op;
+    op.kind = PlanOp::FORK;
+    op.bg = (int)bgs.size() - 1;
+    ops.push_back(op);
+  }
+  void join() {
+    PlanOp op;
+    op.kind = PlanOp::JOIN;
+    ops.push_back(op);
+  }
   void append(const Plan& o) {
     const int s0 = (int)segs.size(), g0 = (int)groups.size();
     for (auto s : o.segs) segs.push_back(s);
@@ -246,6 +288,36 @@ class Plan {
         ops.push_back(op);
       }
   }
+  // Appends chains placed by phase: op l of chain c joins the (start[c] + l)-th
+  // new phase.  The caller guarantees that the ops sharing a phase are
+  // independent (each reads only what earlier phases or plan ops wrote).
+  void zip_at(const std::vector<const Plan*>& chains, const std::vector<int>& start) {
+    const int s0 = (int)segs.size();
+    std::vector<int> sbase, gbase;
+    int so = s0, go = (int)groups.size();
+    for (const Plan* c : chains) {
+      sbase.push_back(so);
+      gbase.push_back(go);
+      for (auto x : c->segs) segs.push_back(x);
+      for (auto G : c->groups) { G.seg0 += so; groups.push_back(G); }
+      so += (int)c->segs.size();
+      go += (int)c->groups.size();
+    }
+    int nl = 0;
+    for (size_t c = 0; c < chains.size(); ++c) nl = std::max(nl, start[c] + (int)chains[c]->ops.size());
+    for (int l = 0; l < nl; ++l) {
+      int ph = -1;
+      for (size_t c = 0; c < chains.size(); ++c) {
+        const int k = l - start[c];
+        if (k < 0 || k >= (int)chains[c]->ops.size()) continue;
+        if (ph < 0) ph = n_phases++;
+        PlanOp op = chains[c]->ops[k];
+        op.group0 += gbase[c];
+        op.phase = ph;
+        ops.push_back(op);
+      }
+    }
+  }
   // Copy of ops [from, to) with the argument tables they use.
   Plan slice(size_t from, size_t to) const {
     Plan r;
@@ -281,6 +353,17 @@ class Plan {
   }
   void finalize() {
     release();
+    bool open = false;
+    for (auto& op : ops) {
+      if (op.kind == PlanOp::FORK && open) throw CudaError{cudaErrorInvalidValue, "plan: nested background chain"};
+      if (op.kind == PlanOp::FORK) open = true;
+      if (op.kind == PlanOp::JOIN) open = false;
+    }
+    if (open) throw CudaError{cudaErrorInvalidValue, "plan: background chain without join"};
+    for (auto& b : bgs) {
+      b->skip = skip;
+      b->finalize();
+    }
     for (auto& op : ops)
       if ((op.kind == PlanOp::GEMV || op.kind == PlanOp::GEMV32) && op.phase < 0 && (op.z || op.zs))
         throw CudaError{cudaErrorInvalidValue, "plan: a GEMV with z or zs must be part of a zipped chain"};
@@ -367,6 +450,19 @@ class Plan {
       else scale_cols((double*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
     } else if (op.kind == PlanOp::COPY) {
       if (op.cp_bytes > 0) GPFVM_CUDA(cudaMemcpyAsync(op.cp_dst, op.cp_src, op.cp_bytes, cudaMemcpyDeviceToDevice, st));
+    } else if (op.kind == PlanOp::ADD) {
+      add_parts(op.ad_X, op.ad_P, op.ad_np, op.ad_stride, op.ad_n, op.ad_f32, st);
+    } else if (op.kind == PlanOp::FORK) {
+      if (!fan) {
+        bgs[op.bg]->run(st);  // no side stream: in place
+      } else {
+        GPFVM_CUDA(cudaEventRecord(fan->bg_fork, st));
+        GPFVM_CUDA(cudaStreamWaitEvent(fan->bgs, fan->bg_fork, 0));
+        bgs[op.bg]->run(fan->bgs);
+        GPFVM_CUDA(cudaEventRecord(fan->bg_join, fan->bgs));
+      }
+    } else if (op.kind == PlanOp::JOIN) {
+      if (fan) GPFVM_CUDA(cudaStreamWaitEvent(st, fan->bg_join, 0));
     } else op.fn(st);
   }
   void run_unit(const LaunchUnit& u, cudaStream_t st) const {
