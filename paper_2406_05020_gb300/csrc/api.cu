@@ -446,18 +446,23 @@ struct Builder {
       ready[0] = ready[1] = 1;
     }
   }
-  // y~ (set 0 in its eigenbasis, the other sets as they are) from y (FP64)
-  void to_eigenbasis(Plan& plan, const double* y, double* yt) {
-    const int MK = p->MK, MR = p->MR;
+  // rows x <- rows x (x)Q_i^T over set 0's axes (FP64); singleton axes
+  // (Q = [1]) are dropped
+  void eig_rows(Plan& plan, i64 rows, const double* x, double* xt) {
     int dK[3], nd = 0;
     KTerm QT{};
     QT.c = 1.0;
     for (int i = 0; i < p->d; ++i) {
-      if (p->nK[i] == 1 && !(i == p->d - 1 && nd == 0)) continue;  // Q = [1] on a singleton axis
+      if (p->nK[i] == 1 && !(i == p->d - 1 && nd == 0)) continue;
       QT.f[nd] = MatRef{p->d_QK[i], 1, p->nK[i]};
       dK[nd++] = p->nK[i];
     }
-    kron(plan, dK, dK, 1, {QT}, 1.0, y, yt, 0.0, nullptr, 0.0, nullptr, nd);
+    kron(plan, dK, dK, rows, {QT}, 1.0, x, xt, 0.0, nullptr, 0.0, nullptr, nd);
+  }
+  // y~ (set 0 in its eigenbasis, the other sets as they are) from y (FP64)
+  void to_eigenbasis(Plan& plan, const double* y, double* yt) {
+    const int MK = p->MK, MR = p->MR;
+    eig_rows(plan, 1, y, yt);
     if (MR > 0) plan.copy(yt + MK, y + MK, (i64)sizeof(double) * MR);
   }
   // w = G_BB^-1 g (w~ / g~ in the eigenbasis of set 0 with the structured stage)
@@ -576,15 +581,8 @@ struct Builder {
 void build_sicbc(gpfvm_problem* p, Builder& B) {
   Plan& pl = p->p_chol;
   const int M = (int)p->M, MK = p->MK, MR = p->MR, d = p->d;
-  int dK[3];
-  dims_set(p, 0, dK);
-  KTerm QT{};
-  QT.c = 1.0;
   int maxn = 1;
-  for (int i = 0; i < d; ++i) {
-    QT.f[i] = MatRef{p->d_QK[i], 1, p->nK[i]};
-    maxn = std::max(maxn, p->nK[i]);
-  }
+  for (int i = 0; i < d; ++i) maxn = std::max(maxn, p->nK[i]);
   gpfvm_problem* pp = p;
   pl.func([=](cudaStream_t st) {
     launch_jacobi(pp->d_jac, pp->d, maxn, st);
@@ -597,7 +595,7 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
       GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_BT, sizeof(double) * MK, pp->d_A + (i64)MK * M, sizeof(double) * M,
                                    sizeof(double) * MK, MR, cudaMemcpyDeviceToDevice, st));
     });
-    B.kron(pl, dK, dK, MR, {QT}, 1.0, p->d_BT, p->d_Et, 0.0, nullptr, 0.0);
+    B.eig_rows(pl, MR, p->d_BT, p->d_Et);
     pl.func([=](cudaStream_t st) {
       GPFVM_CUDA(cudaMemcpyAsync(pp->d_E1, pp->d_Et, sizeof(double) * MR * MK, cudaMemcpyDeviceToDevice, st));
       scale_cols(pp->d_E1, MR, MK, pp->d_lt, -0.5, st);
@@ -1304,7 +1302,8 @@ void alloc_all(gpfvm_problem* p) {
   p->d_part2 = m.alloc<double>((i64)cap * reorth_chunks(N));
   p->d_coef = m.alloc<double>(cap);
   if (M > 0) {
-    i64 R = std::max<i64>(1, std::min<i64>(M, ((i64)1 << 25) / std::max<i64>(P, 1)));
+    // row chunks of the Cholesky-stage variance: rows x P FP64 (32 MB) stays in L2
+    i64 R = std::max<i64>(1, std::min<i64>(M, ((i64)1 << 22) / std::max<i64>(P, 1)));
     p->vb_rows = (int)R;
     i64 maxms = 0;
     for (int s = 0; s < p->nsets; ++s) maxms = std::max(maxms, p->sets[s].size);
@@ -1726,9 +1725,13 @@ void mixed_launch(gpfvm_problem* p, int, cudaStream_t st) {
   MixedRun& R = mruns()[p];
   const i64 N = p->N;
   if (R.mstate == 0) {
-    GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, p->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    p->p_op[1].run(st);
-    axpby(p->d_b, p->d_vout, p->d_r, 1.0, -1.0, N, st);
+    if (R.outer == 0) {  // x = 0 (mixed_begin): r = b
+      GPFVM_CUDA(cudaMemcpyAsync(p->d_r, p->d_b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    } else {
+      GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, p->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      p->p_op[1].run(st);
+      axpby(p->d_b, p->d_vout, p->d_r, 1.0, -1.0, N, st);
+    }
     norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
     copy_header_to_host(p, st);
     R.mstate = 1;

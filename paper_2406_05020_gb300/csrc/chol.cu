@@ -22,13 +22,18 @@ __global__ void __launch_bounds__(256) chol_base_kernel(const double* __restrict
   double* Ls = sm;            // 64 x 65
   double* Xs = sm + 64 * LD;  // 64 x 65
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) bad = 0;
   for (int e = tid; e < 64 * 64; e += blockDim.x) {
     const int i = e / 64, j = e % 64;
     Ls[i * LD + j] = (i < n && j <= i) ? A[(i64)i * lda + j] : 0.0;
+    Xs[i * LD + j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // Right-looking Cholesky; X = L^-1 is eliminated alongside: X starts as I,
+  // and once column j of L is final, row j of X is divided by L[j][j] and
+  // X[i][c] -= L[i][j] X[j][c] for the rows i > j (columns c <= j; X stays
+  // lower triangular).  Rows go to warps, columns to lanes.
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
       const double d = Ls[j * LD + j];
@@ -42,30 +47,15 @@ __global__ void __launch_bounds__(256) chol_base_kernel(const double* __restrict
     __syncthreads();
     const double piv = Ls[j * LD + j];
     for (int i = j + 1 + tid; i < n; i += blockDim.x) Ls[i * LD + j] /= piv;
+    for (int c = tid; c <= j; c += blockDim.x) Xs[j * LD + c] /= piv;
     __syncthreads();
-    const int w = n - j - 1;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int ii = j + 1 + e / w, ll = j + 1 + e % w;
-      if (ll <= ii) Ls[ii * LD + ll] -= Ls[ii * LD + j] * Ls[ll * LD + j];
+    for (int i = j + 1 + warp; i < n; i += nw) {
+      const double lij = Ls[i * LD + j];
+      for (int l = j + 1 + lane; l <= i; l += 32) Ls[i * LD + l] -= lij * Ls[l * LD + j];
+      for (int c = lane; c <= j; c += 32) Xs[i * LD + c] -= lij * Xs[j * LD + c];
     }
     __syncthreads();
   }
-  // inverse of the lower factor, one column per thread (forward substitution)
-  if (tid < n) {
-    const int c = tid;
-    for (int i = 0; i < c; ++i) Xs[i * LD + c] = 0.0;
-    for (int i = c; i < n; ++i) {
-      double s0 = (i == c) ? 1.0 : 0.0, s1 = 0.0;
-      int l = c;
-      for (; l + 1 < i; l += 2) {
-        s0 -= Ls[i * LD + l] * Xs[l * LD + c];
-        s1 -= Ls[i * LD + l + 1] * Xs[(l + 1) * LD + c];
-      }
-      if (l < i) s0 -= Ls[i * LD + l] * Xs[l * LD + c];
-      Xs[i * LD + c] = (s0 + s1) / Ls[i * LD + i];
-    }
-  }
-  __syncthreads();
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     L[(i64)i * lda + j] = (j <= i) ? Ls[i * LD + j] : 0.0;
