@@ -121,7 +121,44 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       need(op.cp_src, op.cp_bytes, "copy src");    } else if (op.kind == PlanOp::ADD) {
       const i64 e = op.ad_f32 ? 4 : 8;
       need(op.ad_X, e * op.ad_n, "add X");
-      need(op.ad_P, e * ((i64)(op.ad_np - 1) * op.ad_stride + op.ad_n), "add parts");
+      need(op.ad_P, e * ((i64)(op.ad_np - 1) * op.ad_stride + op.ad_n), "add parts");    } else if (op.kind == PlanOp::CONTR) {
+      const ContrOp& o = op.fco;
+      const i64 e = op.fc_f32 ? 4 : 8;
+      need(o.in, e * o.pre * o.na * o.post, "contr in");
+      for (int k = 0; k < o.nf; ++k) {
+        need(o.f[k], e * ((i64)(o.na - 1) * o.fs + 1), "contr f");
+        need(o.out[k], e * o.pre * o.post, "contr out");
+      }
+    } else if (op.kind == PlanOp::BILIN) {
+      const BilOp& o = op.fbo;
+      const i64 e = op.fc_f32 ? 4 : 8;
+      if (o.R > FACE_MAXN || o.C > FACE_MAXN || o.K1 > FACE_MAXN || o.K2 > FACE_MAXN || o.nt > FACE_MAXT)
+        throw CudaError{cudaErrorInvalidValue, "plan: bilinear form too large"};
+      need(o.out, e * ((i64)(o.R - 1) * o.ldo + (i64)(o.C - 1) * o.ocs + 1), "bilin out");
+      if (o.nA > FACE_MAXO || o.nX > FACE_MAXO || o.nB > FACE_MAXO)
+        throw CudaError{cudaErrorInvalidValue, "plan: bilinear form too large"};
+      for (int k = 0; k < o.nA; ++k)
+        need(o.A[k].p, e * ((i64)(o.R - 1) * o.A[k].rs + (i64)(o.K1 - 1) * o.A[k].cs + 1), "bilin A");
+      for (int k = 0; k < o.nX; ++k)
+        need(o.X[k].p, e * ((i64)(o.K1 - 1) * o.X[k].rs + (i64)(o.K2 - 1) * o.X[k].cs + 1), "bilin X");
+      for (int k = 0; k < o.nB; ++k)
+        need(o.B[k].p, e * ((i64)(o.C - 1) * o.B[k].rs + (i64)(o.K2 - 1) * o.B[k].cs + 1), "bilin B");
+      for (int k = 0; k < o.nt; ++k)
+        if (o.ta[k] < 0 || o.ta[k] >= o.nA || o.tx[k] < 0 || o.tx[k] >= o.nX || o.tb[k] < 0 || o.tb[k] >= o.nB)
+          throw CudaError{cudaErrorInvalidValue, "plan: bilinear term operand out of range"};
+    } else if (op.kind == PlanOp::EXPADD) {
+      const ExpAddOp& o = op.feo;
+      const i64 e = op.fc_f32 ? 4 : 8;
+      if (o.nj > FACE_MAXJ) throw CudaError{cudaErrorInvalidValue, "plan: too many expansion terms"};
+      need(o.dst, e * o.n, "expadd dst");
+      need(o.P, e * ((i64)(o.np - 1) * o.pstride + o.n), "expadd parts");
+      const i64 d0 = o.n / ((i64)o.d1 * o.d2);
+      for (int k = 0; k < o.nj; ++k) {
+        const ExpTerm& t = o.j[k];
+        const i64 na = t.axis == 0 ? d0 : (t.axis == 1 ? o.d1 : o.d2);
+        need(t.f, e * ((na - 1) * t.fs + 1), "expadd f");
+        need(t.Z, e * (o.n / na), "expadd Z");
+      }
     }
   }
 }
@@ -479,15 +516,181 @@ struct Builder {
     return r;
   }
 
+  // ---- sets on faces of the box (face.cuh)
+  // The axis on which set s has its fewest coordinates (at most FACE_MAXF:
+  // faces), when its other dimensions and those of the grid dt fit the
+  // bilinear kernel; else -1.
+  int face_axis(int s, const int* dt) const {
+    if (p->d != 3 || p->nterms > FACE_MAXT) return -1;
+    int a = 0;
+    for (int i = 1; i < 3; ++i)
+      if (p->sets[s].n[i] < p->sets[s].n[a]) a = i;
+    if (p->sets[s].n[a] > FACE_MAXF) return -1;
+    for (int i = 0; i < 3; ++i)
+      if (i != a && (p->sets[s].n[i] > FACE_MAXN || dt[i] > FACE_MAXN)) return -1;
+    if ((i64)dt[0] * dt[1] * dt[2] >= ((i64)1 << 31)) return -1;  // 32-bit element indices
+    return a;
+  }
+  // strides of set s's flattened layout (row-major over the three axes)
+  void set_strides(int s, i64* st) const {
+    st[2] = 1;
+    st[1] = p->sets[s].n[2];
+    st[0] = (i64)p->sets[s].n[1] * p->sets[s].n[2];
+  }
+  // distinct factors on axis a of a term list
+  static void distinct_on(const std::vector<KTerm>& ts, int a, std::vector<MatRef>& U, std::vector<int>& ui) {
+    U.clear();
+    ui.assign(ts.size(), -1);
+    for (size_t t = 0; t < ts.size(); ++t) {
+      for (size_t k = 0; k < U.size(); ++k)
+        if (U[k].p == ts[t].f[a].p && U[k].rs == ts[t].f[a].rs && U[k].cs == ts[t].f[a].cs) ui[t] = (int)k;
+      if (ui[t] < 0) {
+        ui[t] = (int)U.size();
+        U.push_back(ts[t].f[a]);
+      }
+    }
+  }
+  // G_BP of a face set s into gs: a CONTR chain (level 0) and one BILIN
+  // chain per face (level 1), appended to `chains` with their levels in
+  // `lv`; false if s does not qualify
+  bool bp_face(std::deque<Plan>& chains, std::vector<int>& lv, int s, const double* in, double* gs) {
+    int dc[3];
+    dims_cells(p, dc);
+    const int a = face_axis(s, dc);
+    if (a < 0) return false;
+    const std::vector<KTerm> ts = pb_terms(p, s, true, true);
+    std::vector<MatRef> U;
+    std::vector<int> ui;
+    distinct_on(ts, a, U, ui);
+    const int na = p->sets[s].n[a];
+    if ((int)U.size() * na > FACE_MAXF) return false;
+    for (auto& f : U)
+      if (f.cs != U[0].cs) return false;
+    const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+    const i64 Nb = dc[b], Nc = dc[cc];
+    i64 sst[3];
+    set_strides(s, sst);
+    // the bilinear forms of the faces (Y_u,m are placed below; take() only
+    // after every check has passed)
+    std::vector<BilOp> bos(na);
+    for (int m = 0; m < na; ++m) {
+      BilOp& bo = bos[m];
+      bo = BilOp{};
+      bo.out = at(gs, m * sst[a]);
+      bo.ldo = sst[b];
+      bo.ocs = sst[cc];
+      bo.R = p->sets[s].n[b];
+      bo.C = p->sets[s].n[cc];
+      bo.K1 = (int)Nb;
+      bo.K2 = (int)Nc;
+      for (size_t k = 0; k < ts.size(); ++k) {
+        const KTerm& t = ts[k];
+        // X is patched to Y_u,m once it exists; the slot index keeps operands apart
+        const BilMat X{(const void*)(intptr_t)(1 + ui[k] * na + m), Nc, 1};
+        if (!bil_add(bo, BilMat{t.f[b].p, t.f[b].rs, t.f[b].cs}, X, BilMat{t.f[cc].p, t.f[cc].rs, t.f[cc].cs},
+                     t.c * p->s2))
+          return false;
+      }
+      if (bilin_smem_elems(bo.C, bo.K1, bo.K2, bo.nA, bo.nX, bo.nB, bo.nt) * (f32 ? 4 : 8) > FACE_SMEM_MAX)
+        return false;
+    }
+    // the factor on a is na x N_a: row m is f(m, k) = p[m rs + k cs]
+    ContrOp co{};
+    co.in = in;
+    co.nf = (int)U.size() * na;
+    co.na = dc[a];
+    co.fs = U[0].cs;
+    co.pre = 1;
+    co.post = 1;
+    for (int i = 0; i < a; ++i) co.pre *= dc[i];
+    for (int i = a + 1; i < 3; ++i) co.post *= dc[i];
+    co.alpha = 1.0;
+    double* Y[FACE_MAXF];
+    for (size_t k = 0; k < U.size(); ++k)
+      for (int m = 0; m < na; ++m) {
+        const int j = (int)k * na + m;
+        Y[j] = take(Nb * Nc);
+        co.f[j] = at(U[k].p, m * U[k].rs);
+        co.out[j] = Y[j];
+      }
+    chains.emplace_back();
+    chains.back().contr(co, f32);
+    lv.push_back(0);
+    for (int m = 0; m < na; ++m) {
+      BilOp bo = bos[m];
+      for (int k = 0; k < bo.nX; ++k) bo.X[k].p = Y[(intptr_t)bo.X[k].p - 1];
+      chains.emplace_back();
+      chains.back().bilin(bo, f32);
+      lv.push_back(1);
+    }
+    return true;
+  }
+  // -s2 (G_PB w_s) (pred = false, grid = cells) or -s2 k_s(X*)^T w_s (pred =
+  // true) of a face set s: one BILIN chain per distinct factor on the face
+  // axis and face (appended to `chains`), expansion terms appended to `xt`
+  bool pb_face(std::deque<Plan>& chains, int s, const double* ws, bool pred, std::vector<ExpTerm>& xt) {
+    int dt[3];
+    if (pred) dims_pred(p, dt);
+    else dims_cells(p, dt);
+    const int a = face_axis(s, dt);
+    if (a < 0) return false;
+    const std::vector<KTerm> ts = pred ? bpred_terms(p, s, true) : pb_terms(p, s, false, true);
+    std::vector<MatRef> U;
+    std::vector<int> ui;
+    distinct_on(ts, a, U, ui);
+    const int na = p->sets[s].n[a];
+    if ((int)(xt.size() + U.size() * na) > FACE_MAXJ) return false;
+    const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+    const i64 Nb = dt[b], Nc = dt[cc];
+    const int nb = p->sets[s].n[b], nc = p->sets[s].n[cc];
+    i64 sst[3];
+    set_strides(s, sst);
+    std::vector<BilOp> bos;
+    for (size_t k = 0; k < U.size(); ++k)
+      for (int m = 0; m < na; ++m) {
+        BilOp bo{};
+        bo.ldo = Nc;
+        bo.ocs = 1;
+        bo.R = (int)Nb;
+        bo.C = (int)Nc;
+        bo.K1 = nb;
+        bo.K2 = nc;
+        for (size_t t = 0; t < ts.size(); ++t) {
+          if (ui[t] != (int)k) continue;
+          const KTerm& x = ts[t];
+          if (!bil_add(bo, BilMat{x.f[b].p, x.f[b].rs, x.f[b].cs}, BilMat{at(ws, m * sst[a]), sst[b], sst[cc]},
+                       BilMat{x.f[cc].p, x.f[cc].rs, x.f[cc].cs}, -x.c * p->s2))
+            return false;
+        }
+        if (bilin_smem_elems(bo.C, bo.K1, bo.K2, bo.nA, bo.nX, bo.nB, bo.nt) * (f32 ? 4 : 8) > FACE_SMEM_MAX)
+          return false;
+        bos.push_back(bo);
+      }
+    for (size_t k = 0; k < U.size(); ++k)
+      for (int m = 0; m < na; ++m) {
+        double* Z = take(Nb * Nc);
+        BilOp bo = bos[k * na + m];
+        bo.out = Z;
+        chains.emplace_back();
+        chains.back().bilin(bo, f32);
+        // the factor on a is N_a x na: column m is f(k, m) = p[k rs + m cs]
+        xt.push_back(ExpTerm{at(U[k].p, m * U[k].cs), U[k].rs, Z, a, 1.0});
+      }
+    return true;
+  }
+
   // out = G^ in = G_PP in - G_PB G_BB^-1 G_BP in; with u != null also
   // u = Lhat k(X*)^T in.  Every product is a chain of dependent launches; the
   // chains are placed by phase so that each starts as soon as its input is final:
   //   phase 0..        G_PP in (into out), G_BP in (each set, into g), L k(X*)^T in (into u)
   //   after G_BP:      w = G_BB^-1 g (hsolve_chain)
-  //   after w_s final: -G_PB w_s and -k_s(X*)^T w_s per set s, into separate buffers
-  //   last:            out += sum of the G_PB parts, u += sum of the k(X*) parts
-  // (sets in order, so the result does not depend on the concurrency).  With
-  // IC/BC sets, G_PP runs beside all of it as a background chain.
+  //   after w_s final: -G_PB w_s and -k_s(X*)^T w_s per set s
+  //   last:            out += the G_PB parts, u += the k(X*) parts (EXPADD;
+  //                    sets in order, so the result does not depend on the concurrency)
+  // Sets on a face of the box take the CONTR / BILIN / EXPADD form (two
+  // launches per direction instead of three); the others take Kronecker chains
+  // into separate buffers.  With IC/BC sets, G_PP runs beside all of it as a
+  // background chain.
   void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
                    Plan* pp_chain = nullptr) {
     int dc[3], ds[3], dp[3];
@@ -512,35 +715,81 @@ struct Builder {
     if (!bgpp) put(PP, 0);
     if (u) put(PR, 0);
     std::vector<Plan> BP(ns), PB(ns), VS(ns);
+    std::deque<Plan> FC;  // bilinear chains of face sets
     Plan H, SO, SU;
     if (p->M > 0) {
       int lbp = 0;
       for (int s = 0; s < ns; ++s) {
         dims_set(p, s, ds);
-        kron(BP[s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
-        lbp = std::max(lbp, (int)BP[s].ops.size());
-        put(BP[s], 0);
+        const size_t f0 = FC.size();
+        std::vector<int> lv;
+        if (bp_face(FC, lv, s, in, at(g, p->sets[s].off))) {
+          for (size_t k = f0; k < FC.size(); ++k) {
+            put(FC[k], lv[k - f0]);
+            lbp = std::max(lbp, lv[k - f0] + 1);
+          }
+        } else {
+          kron(BP[s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+          lbp = std::max(lbp, (int)BP[s].ops.size());
+          put(BP[s], 0);
+        }
       }
       int ready[2];
       hsolve_chain(H, g, w, ready);
       put(H, lbp);
       const i64 sN = (p->N + 31) / 32 * 32, sP = (p->P + 31) / 32 * 32;
-      double* T = take(ns * sN);
-      double* V = u ? take(ns * sP) : nullptr;
+      std::vector<ExpTerm> xo, xu;
+      std::vector<int> gen_o, gen_u;  // sets with Kronecker chains (dense parts)
+      std::vector<int> r_of(ns);
       for (int s = 0; s < ns; ++s) {
-        dims_set(p, s, ds);
-        const int r = lbp + ready[s == 0 ? 0 : 1];
-        kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), at(T, s * sN), 0.0,
-             nullptr, 0.0);
-        put(PB[s], r);
+        r_of[s] = lbp + ready[s == 0 ? 0 : 1];
+        const size_t f0 = FC.size();
+        if (pb_face(FC, s, at(w, p->sets[s].off), false, xo)) {
+          for (size_t k = f0; k < FC.size(); ++k) put(FC[k], r_of[s]);
+        } else {
+          gen_o.push_back(s);
+        }
         if (u) {
-          kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, s * sP), 0.0,
-               nullptr, 0.0);
-          put(VS[s], r);
+          const size_t f1 = FC.size();
+          if (pb_face(FC, s, at(w, p->sets[s].off), true, xu)) {
+            for (size_t k = f1; k < FC.size(); ++k) put(FC[k], r_of[s]);
+          } else {
+            gen_u.push_back(s);
+          }
         }
       }
-      SO.add(out, T, ns, sN, p->N, f32);
-      if (u) SU.add(u, V, ns, sP, p->P, f32);
+      double* T = gen_o.empty() ? nullptr : take((i64)gen_o.size() * sN);
+      double* V = gen_u.empty() ? nullptr : take((i64)gen_u.size() * sP);
+      for (size_t k = 0; k < gen_o.size(); ++k) {
+        const int s = gen_o[k];
+        dims_set(p, s, ds);
+        kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), at(T, (i64)k * sN), 0.0,
+             nullptr, 0.0);
+        put(PB[s], r_of[s]);
+      }
+      for (size_t k = 0; k < gen_u.size(); ++k) {
+        const int s = gen_u[k];
+        dims_set(p, s, ds);
+        kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, (i64)k * sP), 0.0,
+             nullptr, 0.0);
+        put(VS[s], r_of[s]);
+      }
+      auto expadd = [&](Plan& pl, double* dst, i64 n, const int* dt, const double* parts, int np, i64 stride,
+                        const std::vector<ExpTerm>& xt) {
+        ExpAddOp eo{};
+        eo.dst = dst;
+        eo.n = n;
+        eo.d1 = p->d == 3 ? dt[1] : 1;
+        eo.d2 = p->d == 3 ? dt[2] : 1;
+        eo.P = parts;
+        eo.np = np;
+        eo.pstride = stride;
+        eo.nj = (int)xt.size();
+        for (size_t j = 0; j < xt.size(); ++j) eo.j[j] = xt[j];
+        pl.expadd(eo, f32);
+      };
+      expadd(SO, out, p->N, dc, T, (int)gen_o.size(), sN, xo);
+      if (u) expadd(SU, u, p->P, dp, V, (int)gen_u.size(), sP, xu);
     }
     if (bgpp) plan.fork(std::move(PP));
     plan.zip_at(cs, st);

@@ -117,6 +117,9 @@ void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cud
 // X[i] += P[i] + P[stride + i] + ... + P[(np-1) stride + i] for i < n, added
 // in that order (FP64, or FP32 when f32)
 void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaStream_t st);
+// One launch of a merged table of face-set ops (face.cuh): kind 0 ContrOp,
+// 1 BilOp, 2 ExpAddOp; `items` CTAs in total, `smem` dynamic shared bytes.
+void launch_face(int kind, const void* table, int nops, i64 items, int f32, int smem, cudaStream_t st);
 void recip(const double* lt, double* out, i64 n, cudaStream_t st);
 void square(const double* in, double* out, i64 n, cudaStream_t st);
 

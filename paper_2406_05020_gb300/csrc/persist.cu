@@ -19,12 +19,15 @@
 #include "persist.cuh"
 #include <functional>
 
+#include "face.cuh"
 #include "plan.cuh"
 #include "tc_tile.cuh"
 
 namespace gpfvm {
 
-enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM, PU_ADD };
+enum PUnitKind {
+  PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM, PU_ADD, PU_CONTR, PU_BILIN, PU_EXPADD
+};
 constexpr int P_SUM_CHUNKS = 64;  // items per op of a segment-group reduction
 
 constexpr int P_THREADS = 256;
@@ -265,6 +268,27 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
           if (u.f32) p_add_item<float>(u, local);
           else p_add_item<double>(u, local);
           break;
+        case PU_CONTR: {
+          const ContrOp& op = face_find(static_cast<const ContrOp*>(u.table), u.nops, local);
+          if (op.skip && *op.skip) break;
+          if (u.f32) contr_item<float>(op, local - op.item_begin, reinterpret_cast<float*>(sm));
+          else contr_item<double>(op, local - op.item_begin, reinterpret_cast<double*>(sm));
+          break;
+        }
+        case PU_BILIN: {
+          const BilOp& op = face_find(static_cast<const BilOp*>(u.table), u.nops, local);
+          if (op.skip && *op.skip) break;
+          if (u.f32) bilin_item<float>(op, local - op.item_begin, reinterpret_cast<float*>(sm));
+          else bilin_item<double>(op, local - op.item_begin, reinterpret_cast<double*>(sm));
+          break;
+        }
+        case PU_EXPADD: {
+          const ExpAddOp& op = face_find(static_cast<const ExpAddOp*>(u.table), u.nops, local);
+          if (op.skip && *op.skip) break;
+          if (u.f32) expadd_item<float>(op, local - op.item_begin);
+          else expadd_item<double>(op, local - op.item_begin);
+          break;
+        }
         case PU_COPY: {
           const i64 w0 = local * P_ELEMS;
           const unsigned int* s = static_cast<const unsigned int*>(u.src);
@@ -346,6 +370,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
   std::vector<PPhase> phases;
   std::vector<PUnit> units;
   int tc_maxn = 0;
+  int face_smem = 0;  // largest bilinear item
   auto unit_of = [&](const Plan& plan, const PlanOp& op, PUnit& u) -> bool {
     u = PUnit{};
     switch (op.kind) {
@@ -466,6 +491,13 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
           u.nops = lu.nops;
           u.table = plan.d_tables + lu.offset;
           u.items = lu.total;
+        } else if (lu.kind >= 2) {
+          u.kind = lu.kind == 2 ? PU_CONTR : (lu.kind == 3 ? PU_BILIN : PU_EXPADD);
+          face_smem = std::max(face_smem, lu.smem);
+          u.f32 = lu.f32;
+          u.nops = lu.nops;
+          u.table = plan.d_tables + lu.offset;
+          u.items = lu.total;
         } else {
           u.kind = PU_MGEMV;
           u.f32 = lu.f32;
@@ -508,7 +540,7 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
     while (tc_cols < npad) tc_cols <<= 1;
   }
   const int tc_smem = tc_cols > 0 ? 2 * TC_A_BYTES + 2 * tc_cols * 128 : 0;
-  pr->smem = std::max(gemm_smem_bytes(), tc_smem) + 1024;
+  pr->smem = std::max(std::max(gemm_smem_bytes(), tc_smem), face_smem) + 1024;
   GPFVM_CUDA(cudaMalloc(&pr->d_phases, sizeof(PPhase) * phases.size()));
   GPFVM_CUDA(cudaMalloc(&pr->d_units, sizeof(PUnit) * units.size()));
   GPFVM_CUDA(cudaMemcpy(pr->d_phases, phases.data(), sizeof(PPhase) * phases.size(), cudaMemcpyHostToDevice));

@@ -7,6 +7,7 @@
 #include <functional>
 #include <memory>
 
+#include "face.cuh"
 #include "kernels.cuh"
 #include "persist.cuh"
 #include "tc.cuh"
@@ -18,7 +19,9 @@ struct PlanOp {
   // that the persistent plan kernel can also execute (they run like FUNC ops in run()).
   // FORK starts background chain `bg` of the plan on its own stream; JOIN
   // makes the plan's stream wait for it.
-  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY, ADD, FORK, JOIN } kind;
+  // CONTR, BILIN and EXPADD are the face-set ops of face.cuh (phased only:
+  // merged into one launch per kind, element type and phase).
+  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY, ADD, FORK, JOIN, CONTR, BILIN, EXPADD } kind;
   int phase = -1;  // ops sharing a phase id (>= 0, consecutive) are independent: merged launches
   GemmDesc g;
   int seg0 = 0, group0 = 0;
@@ -54,16 +57,22 @@ struct PlanOp {
   int ad_np = 0, ad_f32 = 0;
   i64 ad_stride = 0, ad_n = 0;
   int bg = -1;  // FORK: index into Plan::bgs
+  int fc_f32 = 0;  // face ops: element type
+  ContrOp fco{};
+  BilOp fbo{};
+  ExpAddOp feo{};
+  bool face() const { return kind == CONTR || kind == BILIN || kind == EXPADD; }
   bool func_like() const { return kind == FUNC || kind == TC || kind == SCALE || kind == COPY || kind == ADD; }
 };
 
 // One merged launch of a phase: a table of GEMM ops (same element type and
 // row tile) or of GEMV ops (same element type).
 struct LaunchUnit {
-  int kind;  // 0 multi-GEMM, 1 multi-GEMV
+  int kind;  // 0 multi-GEMM, 1 multi-GEMV, 2 / 3 / 4 face CONTR / BILIN / EXPADD
   int f32, bm, nops;
   i64 total;
   size_t offset;  // byte offset of the op table in the plan's table buffer
+  int smem = 0;   // dynamic shared memory of the launch (face BILIN)
 };
 
 // Auxiliary streams on which the independent launches of one phase run
@@ -218,6 +227,27 @@ class Plan {
     op.cp_dst = dst; op.cp_src = src; op.cp_bytes = bytes;
     ops.push_back(op);
   }
+  void contr(const ContrOp& o, bool f32) {
+    PlanOp op;
+    op.kind = PlanOp::CONTR;
+    op.fco = o;
+    op.fc_f32 = f32 ? 1 : 0;
+    ops.push_back(op);
+  }
+  void bilin(const BilOp& o, bool f32) {
+    PlanOp op;
+    op.kind = PlanOp::BILIN;
+    op.fbo = o;
+    op.fc_f32 = f32 ? 1 : 0;
+    ops.push_back(op);
+  }
+  void expadd(const ExpAddOp& o, bool f32) {
+    PlanOp op;
+    op.kind = PlanOp::EXPADD;
+    op.feo = o;
+    op.fc_f32 = f32 ? 1 : 0;
+    ops.push_back(op);
+  }
   void add(void* X, const void* P, int np, i64 stride, i64 n, bool f32) {
     PlanOp op;
     op.kind = PlanOp::ADD;
@@ -364,9 +394,12 @@ class Plan {
       b->skip = skip;
       b->finalize();
     }
-    for (auto& op : ops)
+    for (auto& op : ops) {
       if ((op.kind == PlanOp::GEMV || op.kind == PlanOp::GEMV32) && op.phase < 0 && (op.z || op.zs))
         throw CudaError{cudaErrorInvalidValue, "plan: a GEMV with z or zs must be part of a zipped chain"};
+      if (op.face() && op.phase < 0)
+        throw CudaError{cudaErrorInvalidValue, "plan: face-set ops must be part of a zipped chain"};
+    }
     phase_units.assign(n_phases, {});
     if (!segs.empty()) {
       GPFVM_CUDA(cudaMalloc(&d_segs, segs.size() * sizeof(GemmSeg)));
@@ -429,6 +462,57 @@ class Plan {
           u.offset = put(gops.data(), gops.size() * sizeof(MGemv));
           phase_units[ph].push_back(u);
         }
+        // face-set ops: one table per kind
+        {
+          std::vector<ContrOp> co;
+          std::vector<BilOp> bo;
+          std::vector<ExpAddOp> eo;
+          i64 ic = 0, ib = 0, ie = 0;
+          for (auto& op : ops) {
+            if (op.phase != ph || !op.face() || op.fc_f32 != f32) continue;
+            if (op.kind == PlanOp::CONTR) {
+              ContrOp o = op.fco;
+              o.items = contr_items(o.pre, o.post);
+              o.item_begin = ic;
+              o.skip = skip;
+              ic += o.items;
+              co.push_back(o);
+            } else if (op.kind == PlanOp::BILIN) {
+              BilOp o = op.fbo;
+              o.items = (o.R + FACE_RB - 1) / FACE_RB;
+              o.item_begin = ib;
+              o.skip = skip;
+              ib += o.items;
+              bo.push_back(o);
+            } else {
+              ExpAddOp o = op.feo;
+              o.items = (o.n + FACE_EXP_ELEMS - 1) / FACE_EXP_ELEMS;
+              o.item_begin = ie;
+              o.skip = skip;
+              ie += o.items;
+              eo.push_back(o);
+            }
+          }
+          if (!co.empty()) {
+            LaunchUnit u{2, f32, 0, (int)co.size(), ic, 0};
+            u.offset = put(co.data(), co.size() * sizeof(ContrOp));
+            phase_units[ph].push_back(u);
+          }
+          if (!bo.empty()) {
+            LaunchUnit u{3, f32, 0, (int)bo.size(), ib, 0};
+            u.offset = put(bo.data(), bo.size() * sizeof(BilOp));
+            i64 sm = 0;
+            for (auto& o : bo) sm = std::max(sm, bilin_smem_elems(o.C, o.K1, o.K2, o.nA, o.nX, o.nB, o.nt));
+            u.smem = (int)(sm * (f32 ? 4 : 8));
+            if (u.smem > FACE_SMEM_MAX) throw CudaError{cudaErrorInvalidValue, "plan: bilinear form too large"};
+            phase_units[ph].push_back(u);
+          }
+          if (!eo.empty()) {
+            LaunchUnit u{4, f32, 0, (int)eo.size(), ie, 0};
+            u.offset = put(eo.data(), eo.size() * sizeof(ExpAddOp));
+            phase_units[ph].push_back(u);
+          }
+        }
       }
     }
     if (!blob.empty()) {
@@ -467,7 +551,8 @@ class Plan {
   }
   void run_unit(const LaunchUnit& u, cudaStream_t st) const {
     if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
-    else launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
+    else if (u.kind == 1) launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
+    else launch_face(u.kind - 2, d_tables + u.offset, u.nops, u.total, u.f32, u.smem, st);
   }
   // Ops of one phase are consecutive; its merged launch units and FUNC ops
   // are mutually independent.  Without a fan they run in order on st.
