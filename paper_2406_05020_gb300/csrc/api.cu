@@ -786,6 +786,10 @@ struct Builder {
         eo.pstride = stride;
         eo.nj = (int)xt.size();
         for (size_t j = 0; j < xt.size(); ++j) eo.j[j] = xt[j];
+        auto al16 = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
+        bool vec = p->d == 3 && eo.d2 % 4 == 0 && al16(dst) && (np == 0 || (al16(parts) && stride % 4 == 0));
+        for (auto& x : xt) vec = vec && (x.axis == 2 || al16(x.Z));
+        eo.vec = vec ? 1 : 0;
         pl.expadd(eo, f32);
       };
       expadd(SO, out, p->N, dc, T, (int)gen_o.size(), sN, xo);

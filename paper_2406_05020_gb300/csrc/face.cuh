@@ -76,6 +76,7 @@ struct ExpAddOp {
   void* dst;
   i64 n;
   int d1, d2;
+  int vec;  // d2 % 4 == 0, dst, P, the Z of axes 0 / 1 16-byte aligned, pstride % 4 == 0
   const void* P;
   i64 pstride;
   int np, nj;
@@ -307,7 +308,7 @@ __device__ __forceinline__ void bilin_item(const BilOp& op, i64 item, T* sm) {
 }
 
 template <typename T>
-__device__ __forceinline__ void expadd_item(const ExpAddOp& op, i64 item) {
+__device__ __forceinline__ void expadd_item_scalar(const ExpAddOp& op, i64 item) {
   T* __restrict__ dst = static_cast<T*>(op.dst);
   const T* __restrict__ P = static_cast<const T*>(op.P);
   const unsigned n = (unsigned)op.n, d1 = (unsigned)op.d1, d2 = (unsigned)op.d2;
@@ -347,6 +348,71 @@ __device__ __forceinline__ void expadd_item(const ExpAddOp& op, i64 item) {
 #pragma unroll
   for (int q = 0; q < FACE_EXP_EPT; ++q)
     if (e[q] < n) dst[e[q]] = v[q];
+}
+
+template <typename T>
+__device__ __forceinline__ void face_ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void face_st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+// Four consecutive elements of one innermost row per thread, vector loads;
+// every element is summed in the order of expadd_item_scalar.
+template <typename T>
+__device__ __forceinline__ void expadd_item_vec(const ExpAddOp& op, i64 item) {
+  const unsigned n = (unsigned)op.n, d1 = (unsigned)op.d1, d2 = (unsigned)op.d2;
+  const unsigned e0 = (unsigned)(item * FACE_EXP_ELEMS) + 4 * threadIdx.x;
+  if (e0 >= n) return;
+  T* __restrict__ dst = static_cast<T*>(op.dst);
+  const T* __restrict__ P = static_cast<const T*>(op.P);
+  const unsigned c01 = e0 / d2, c2 = e0 - c01 * d2;
+  const unsigned c0 = c01 / d1, c1 = c01 - c0 * d1;
+  T v[4];
+  face_ld4(dst + e0, v);
+  for (int k = 0; k < op.np; ++k) {
+    T w[4];
+    face_ld4(P + (i64)k * op.pstride + e0, w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += w[q];
+  }
+  for (int j = 0; j < op.nj; ++j) {
+    const ExpTerm x = op.j[j];
+    const T al = (T)x.alpha;
+    const T* __restrict__ f = static_cast<const T*>(x.f);
+    const T* __restrict__ Z = static_cast<const T*>(x.Z);
+    if (x.axis == 2) {
+      const T z = Z[c0 * d1 + c1];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = fma(al * f[(i64)(c2 + q) * x.fs], z, v[q]);
+    } else {
+      const T fa = al * f[(i64)(x.axis == 0 ? c0 : c1) * x.fs];
+      T z[4];
+      face_ld4(Z + (x.axis == 0 ? c1 : c0) * d2 + c2, z);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = fma(fa, z[q], v[q]);
+    }
+  }
+  face_st4(dst + e0, v);
+}
+
+template <typename T>
+__device__ __forceinline__ void expadd_item(const ExpAddOp& op, i64 item) {
+  if (op.vec) expadd_item_vec<T>(op, item);
+  else expadd_item_scalar<T>(op, item);
 }
 
 }  // namespace gpfvm

@@ -69,43 +69,19 @@ void launch_multi_gemm(const MOp* d_ops, int nops, i64 total, int f32, int bm, c
   }
 }
 
-// Many GEMV ops in one launch, one warp per output row over all ops:
-// y = alpha * A x + beta * z  (z may alias y).
+// Many GEMV ops in one launch (mgemv_item): S warps per output row.
 template <typename T>
-__global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict__ ops, int nops, i64 total_rows) {
-  const i64 w = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= total_rows) return;
-  int lo = 0, hi = nops - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ops[mid].row_begin <= w) lo = mid; else hi = mid - 1;
-  }
-  const MGemv op = ops[lo];  // copied to registers before the wait
-  pdl_wait();
-  if (op.skip && *op.skip) return;
-  const int i = (int)(w - op.row_begin);
-  int jlo = 0, jhi = op.n;
-  if (op.tri == 1) jhi = min(op.n, i + 1);
-  if (op.tri == 2) jlo = i;
-  const T* row = reinterpret_cast<const T*>(op.A) + (i64)i * op.lda;
-  const T* x = reinterpret_cast<const T*>(op.x);
-  const T s = warp_row_dot(row, x, jlo, jhi, lane);
-  if (lane == 0) {
-    T v = (T)op.alpha * s;
-    if (op.beta != 0.0) {
-      const T zi = reinterpret_cast<const T*>(op.z)[i];
-      v += (T)op.beta * (op.zs ? (T)op.zs[i] * zi : zi);
-    }
-    reinterpret_cast<T*>(op.y)[i] = v;
-  }
+__global__ void __launch_bounds__(256) multi_gemv_kernel(const MGemv* __restrict__ ops, int nops, i64 total_rows,
+                                                         int S) {
+  __shared__ T part[8];
+  mgemv_item<T, true>(ops, nops, total_rows, S, blockIdx.x, part);
 }
 
-void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st) {
+void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, int S, cudaStream_t st) {
   if (nops <= 0 || total_rows <= 0) return;
-  const int grid = ceil_div(total_rows * 32, 256);
-  if (f32) launch_pdl(multi_gemv_kernel<float>, grid, 256, 0, st, d_ops, nops, total_rows);
-  else launch_pdl(multi_gemv_kernel<double>, grid, 256, 0, st, d_ops, nops, total_rows);
+  const int grid = ceil_div(total_rows * S, 8);
+  if (f32) launch_pdl(multi_gemv_kernel<float>, grid, 256, 0, st, d_ops, nops, total_rows, S);
+  else launch_pdl(multi_gemv_kernel<double>, grid, 256, 0, st, d_ops, nops, total_rows, S);
 }
 
 void launch_gemm64(const GemmDesc& g, cudaStream_t st) {

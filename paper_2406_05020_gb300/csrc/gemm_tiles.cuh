@@ -189,4 +189,58 @@ __device__ __forceinline__ T warp_row_dot(const T* __restrict__ row, const T* __
   return s;
 }
 
+// CTA item `item` (8 warps) of a merged multi-GEMV with S warps per output
+// row (S = 1, 2 or 4): y = alpha A x + beta z (z scaled by zs when given).
+// Warp k of a row sums the k-th of S equal column chunks; the row's first
+// warp adds the chunks in order, so the result is fixed for a given S.  All
+// threads of the CTA call this when S > 1 (it synchronises the CTA).  With PDL
+// the op is read before waiting on the previous grid.
+template <typename T, bool PDL>
+__device__ __forceinline__ void mgemv_item(const MGemv* __restrict__ ops, int nops, i64 total_rows, int S, i64 item,
+                                           T* part) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const i64 w = item * 8 + wib;
+  const i64 row = w / S;
+  const int sp = (int)(w - row * S);
+  const bool active = row < total_rows;
+  int lo = 0;
+  if (active) {
+    int hi = nops - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ops[mid].row_begin <= row) lo = mid; else hi = mid - 1;
+    }
+  }
+  const MGemv op = ops[lo];  // in registers before the wait
+  if (PDL) pdl_wait();
+  if (op.skip && *op.skip) return;  // one flag for the whole launch
+  T s = T(0);
+  int i = 0;
+  if (active) {
+    i = (int)(row - op.row_begin);
+    int jlo = 0, jhi = op.n;
+    if (op.tri == 1) jhi = min(op.n, i + 1);
+    if (op.tri == 2) jlo = i;
+    const int len = max(jhi - jlo, 0), ch = (len + S - 1) / S;
+    const int a = jlo + sp * ch, b = max(a, min(jhi, a + ch));
+    s = warp_row_dot(reinterpret_cast<const T*>(op.A) + (i64)i * op.lda, reinterpret_cast<const T*>(op.x), a, b,
+                     lane);
+  }
+  if (S > 1) {
+    if (lane == 0) part[wib] = s;
+    __syncthreads();
+    if (active && sp == 0 && lane == 0)
+      for (int k = 1; k < S; ++k) s += part[wib + k];
+  }
+  if (active && sp == 0 && lane == 0) {
+    T v = (T)op.alpha * s;
+    if (op.beta != 0.0) {
+      const T zi = reinterpret_cast<const T*>(op.z)[i];
+      v += (T)op.beta * (op.zs ? (T)op.zs[i] * zi : zi);
+    }
+    reinterpret_cast<T*>(op.y)[i] = v;
+  }
+  if (S > 1) __syncthreads();  // part is free again
+}
+
 }  // namespace gpfvm

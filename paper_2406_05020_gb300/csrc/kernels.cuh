@@ -83,7 +83,16 @@ struct MGemv {
   const int* skip;
   const double* zs;  // optional per-row scale of z: y = alpha A x + beta zs .* z
 };
-void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, cudaStream_t st);
+// Warps per row of a merged multi-GEMV: split long rows until about 4096
+// warps are in flight (chunks of at least 256 columns).
+inline int mgemv_split(i64 rows, int maxn) {
+  int S = 1;
+  while (S < 4 && rows * S < 4096 && maxn / (2 * S) >= 256) S *= 2;
+  return S;
+}
+
+// S warps per output row (1, 2 or 4; see mgemv_item)
+void launch_multi_gemv(const MGemv* d_ops, int nops, i64 total_rows, int f32, int S, cudaStream_t st);
 
 // y(i) = alpha * sum_{j in tri range} A(i,j) x(j) + beta y(i); A row-major lda.
 // tri: 0 full, 1 lower (j <= i), 2 upper (j >= i).

@@ -127,32 +127,6 @@ __device__ __forceinline__ void p_mgemm_item(const PUnit& u, i64 t, unsigned cha
 }
 
 template <typename T>
-__device__ __forceinline__ void p_mgemv_row(const PUnit& u, i64 w, int lane) {
-  const MGemv* __restrict__ ops = static_cast<const MGemv*>(u.table);
-  int lo = 0, hi = u.nops - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ops[mid].row_begin <= w) lo = mid; else hi = mid - 1;
-  }
-  const MGemv& op = ops[lo];
-  if (op.skip && *op.skip) return;
-  const int i = (int)(w - op.row_begin);
-  int jlo = 0, jhi = op.n;
-  if (op.tri == 1) jhi = min(op.n, i + 1);
-  if (op.tri == 2) jlo = i;
-  const T* row = reinterpret_cast<const T*>(op.A) + (i64)i * op.lda;
-  const T s = warp_row_dot(row, reinterpret_cast<const T*>(op.x), jlo, jhi, lane);
-  if (lane == 0) {
-    T v = (T)op.alpha * s;
-    if (op.beta != 0.0) {
-      const T zi = reinterpret_cast<const T*>(op.z)[i];
-      v += (T)op.beta * (op.zs ? (T)op.zs[i] * zi : zi);
-    }
-    reinterpret_cast<T*>(op.y)[i] = v;
-  }
-}
-
-template <typename T>
 __device__ __forceinline__ void p_gemv_row(const PUnit& u, int i, int lane) {
   int lo = 0, hi = u.n;
   if (u.tri == 1) hi = min(u.n, i + 1);
@@ -249,14 +223,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
         case PU_MGEMM:
           p_mgemm_item(u, local, sm);
           break;
-        case PU_MGEMV: {
-          const i64 w = local * P_GEMV_ROWS + warp;
-          if (w < u.total) {
-            if (u.f32) p_mgemv_row<float>(u, w, lane);
-            else p_mgemv_row<double>(u, w, lane);
-          }
+        case PU_MGEMV:
+          if (u.f32)
+            mgemv_item<float, false>(static_cast<const MGemv*>(u.table), u.nops, u.total, u.bm, local,
+                                     reinterpret_cast<float*>(sm));
+          else
+            mgemv_item<double, false>(static_cast<const MGemv*>(u.table), u.nops, u.total, u.bm, local,
+                                      reinterpret_cast<double*>(sm));
           break;
-        }
         case PU_TC:
           tc_tile(static_cast<const TcOp*>(u.table), u.nops, local, cx);
           break;
@@ -501,10 +475,11 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
         } else {
           u.kind = PU_MGEMV;
           u.f32 = lu.f32;
+          u.bm = lu.bm;  // warps per row
           u.nops = lu.nops;
           u.table = plan.d_tables + lu.offset;
           u.total = lu.total;
-          u.items = (lu.total + P_GEMV_ROWS - 1) / P_GEMV_ROWS;
+          u.items = (lu.total * lu.bm + 7) / 8;
         }
         if (u.items > 0) push(u);
       }

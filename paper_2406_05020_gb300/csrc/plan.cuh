@@ -447,6 +447,7 @@ class Plan {
         }
         std::vector<MGemv> gops;
         i64 rows = 0;
+        int maxn = 0;
         for (auto& op : ops) {
           const bool is32 = op.kind == PlanOp::GEMV32;
           if (op.phase != ph || !(op.kind == PlanOp::GEMV || is32) || (int)is32 != f32) continue;
@@ -455,10 +456,11 @@ class Plan {
           m.lda = op.lda; m.row_begin = rows; m.m = op.m; m.n = op.n; m.tri = op.tri;
           m.alpha = op.alpha; m.beta = op.beta; m.skip = skip;
           rows += op.m;
+          maxn = std::max(maxn, op.n);
           gops.push_back(m);
         }
         if (!gops.empty()) {
-          LaunchUnit u{1, f32, 0, (int)gops.size(), rows, 0};
+          LaunchUnit u{1, f32, mgemv_split(rows, maxn), (int)gops.size(), rows, 0};  // bm: warps per row
           u.offset = put(gops.data(), gops.size() * sizeof(MGemv));
           phase_units[ph].push_back(u);
         }
@@ -551,7 +553,7 @@ class Plan {
   }
   void run_unit(const LaunchUnit& u, cudaStream_t st) const {
     if (u.kind == 0) launch_multi_gemm((const MOp*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
-    else if (u.kind == 1) launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, st);
+    else if (u.kind == 1) launch_multi_gemv((const MGemv*)(d_tables + u.offset), u.nops, u.total, u.f32, u.bm, st);
     else launch_face(u.kind - 2, d_tables + u.offset, u.nops, u.total, u.f32, u.smem, st);
   }
   // Ops of one phase are consecutive; its merged launch units and FUNC ops
