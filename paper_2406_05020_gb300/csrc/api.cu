@@ -134,13 +134,14 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       const i64 e = op.fc_f32 ? 4 : 8;
       if (o.R > FACE_MAXN || o.C > FACE_MAXN || o.K1 > FACE_MAXN || o.K2 > FACE_MAXN || o.nt > FACE_MAXT)
         throw CudaError{cudaErrorInvalidValue, "plan: bilinear form too large"};
-      need(o.out, e * ((i64)(o.R - 1) * o.ldo + (i64)(o.C - 1) * o.ocs + 1), "bilin out");
+      const i64 nb = std::max(o.batch, 1) - 1;
+      need(o.out, e * (nb * o.obs + (i64)(o.R - 1) * o.ldo + (i64)(o.C - 1) * o.ocs + 1), "bilin out");
       if (o.nA > FACE_MAXO || o.nX > FACE_MAXO || o.nB > FACE_MAXO)
         throw CudaError{cudaErrorInvalidValue, "plan: bilinear form too large"};
       for (int k = 0; k < o.nA; ++k)
         need(o.A[k].p, e * ((i64)(o.R - 1) * o.A[k].rs + (i64)(o.K1 - 1) * o.A[k].cs + 1), "bilin A");
       for (int k = 0; k < o.nX; ++k)
-        need(o.X[k].p, e * ((i64)(o.K1 - 1) * o.X[k].rs + (i64)(o.K2 - 1) * o.X[k].cs + 1), "bilin X");
+        need(o.X[k].p, e * (nb * o.xbs + (i64)(o.K1 - 1) * o.X[k].rs + (i64)(o.K2 - 1) * o.X[k].cs + 1), "bilin X");
       for (int k = 0; k < o.nB; ++k)
         need(o.B[k].p, e * ((i64)(o.C - 1) * o.B[k].rs + (i64)(o.K2 - 1) * o.B[k].cs + 1), "bilin B");
       for (int k = 0; k < o.nt; ++k)
@@ -152,12 +153,13 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       if (o.nj > FACE_MAXJ) throw CudaError{cudaErrorInvalidValue, "plan: too many expansion terms"};
       need(o.dst, e * o.n, "expadd dst");
       need(o.P, e * ((i64)(o.np - 1) * o.pstride + o.n), "expadd parts");
-      const i64 d0 = o.n / ((i64)o.d1 * o.d2);
+      if (o.nper <= 0 || o.n % o.nper != 0) throw CudaError{cudaErrorInvalidValue, "plan: expand-add batch"};
+      const i64 d0 = o.nper / ((i64)o.d1 * o.d2), nbz = o.n / o.nper - 1;
       for (int k = 0; k < o.nj; ++k) {
         const ExpTerm& t = o.j[k];
         const i64 na = t.axis == 0 ? d0 : (t.axis == 1 ? o.d1 : o.d2);
         need(t.f, e * ((na - 1) * t.fs + 1), "expadd f");
-        need(t.Z, e * (o.n / na), "expadd Z");
+        need(t.Z, e * (nbz * o.zbs + o.nper / na), "expadd Z");
       }
     }
   }
@@ -576,6 +578,7 @@ struct Builder {
     for (int m = 0; m < na; ++m) {
       BilOp& bo = bos[m];
       bo = BilOp{};
+      bo.batch = 1;
       bo.out = at(gs, m * sst[a]);
       bo.ldo = sst[b];
       bo.ocs = sst[cc];
@@ -649,6 +652,7 @@ struct Builder {
     for (size_t k = 0; k < U.size(); ++k)
       for (int m = 0; m < na; ++m) {
         BilOp bo{};
+        bo.batch = 1;
         bo.ldo = Nc;
         bo.ocs = 1;
         bo.R = (int)Nb;
@@ -676,6 +680,87 @@ struct Builder {
         // the factor on a is N_a x na: column m is f(k, m) = p[k rs + m cs]
         xt.push_back(ExpTerm{at(U[k].p, m * U[k].cs), U[k].rs, Z, a, 1.0});
       }
+    return true;
+  }
+
+  // Rows m0 .. m0 + rows of the Cholesky-stage variance term with the
+  // structured stage, Y = s2 (sum over sets s >= 1 of k_s(X*)^T L_S^-1[rows, s])
+  // - s2 k~_K(X*)^T R[rows] (rows x P into Y), when every set lies on faces of
+  // the box: one batched bilinear form per set and face (over the rows), then
+  // one expansion that writes Y.  False (nothing added) otherwise.
+  bool var_face_chunk(Plan& pl, int m0, int rows, double* Y) {
+    int dp[3];
+    dims_pred(p, dp);
+    const int MK = p->MK, MR = p->MR;
+    struct Part {
+      int s, a;
+      KTerm t;
+    };
+    std::vector<Part> parts;
+    i64 zbs = 0;
+    int nj = 0;
+    for (int s = 0; s < p->nsets; ++s) {
+      const int a = face_axis(s, dp);
+      if (a < 0) return false;
+      const std::vector<KTerm> ts = bpred_terms(p, s, true);
+      if (ts.size() != 1) return false;
+      const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+      if (bilin_smem_elems(dp[cc], p->sets[s].n[b], p->sets[s].n[cc], 1, 1, 1, 1) * 8 > FACE_SMEM_MAX) return false;
+      nj += p->sets[s].n[a];
+      zbs = std::max<i64>(zbs, (i64)dp[b] * dp[cc]);
+      parts.push_back(Part{s, a, ts[0]});
+    }
+    if (nj > FACE_MAXJ) return false;
+    zbs = (zbs + 3) / 4 * 4;  // every row of Z starts 32-byte aligned
+    std::deque<Plan> ch;
+    std::vector<ExpTerm> xt;
+    for (const Part& pt : parts) {
+      const int s = pt.s, a = pt.a, b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+      i64 sst[3];
+      set_strides(s, sst);
+      const double* base = s == 0 ? p->d_R + (i64)m0 * MK : p->d_LSinv + (i64)m0 * MR + (p->sets[s].off - MK);
+      const KTerm& t = pt.t;
+      const double alpha = (s == 0 ? -1.0 : 1.0) * t.c * p->s2;
+      for (int m = 0; m < p->sets[s].n[a]; ++m) {
+        double* Z = take((i64)rows * zbs);
+        BilOp bo{};
+        bo.batch = rows;
+        bo.xbs = s == 0 ? MK : MR;
+        bo.obs = zbs;
+        bo.out = Z;
+        bo.ldo = dp[cc];
+        bo.ocs = 1;
+        bo.R = dp[b];
+        bo.C = dp[cc];
+        bo.K1 = p->sets[s].n[b];
+        bo.K2 = p->sets[s].n[cc];
+        bil_add(bo, BilMat{t.f[b].p, t.f[b].rs, t.f[b].cs}, BilMat{base + m * sst[a], sst[b], sst[cc]},
+                BilMat{t.f[cc].p, t.f[cc].rs, t.f[cc].cs}, alpha);
+        ch.emplace_back();
+        ch.back().bilin(bo, false);
+        // the factor on a is P_a x n_a: column m is f(k, m) = p[k rs + m cs]
+        xt.push_back(ExpTerm{t.f[a].p + m * t.f[a].cs, t.f[a].rs, Z, a, 1.0});
+      }
+    }
+    std::vector<const Plan*> cp;
+    for (auto& c : ch) cp.push_back(&c);
+    pl.zip(cp);
+    ExpAddOp eo{};
+    eo.dst = Y;
+    eo.n = (i64)rows * p->P;
+    eo.nper = p->P;
+    eo.zbs = zbs;
+    eo.zero = 1;
+    eo.d1 = dp[1];
+    eo.d2 = dp[2];
+    eo.nj = (int)xt.size();
+    for (size_t j = 0; j < xt.size(); ++j) eo.j[j] = xt[j];
+    bool vec = dp[2] % 4 == 0 && ((uintptr_t)Y & 15) == 0;
+    for (auto& x : xt) vec = vec && (x.axis == 2 || ((uintptr_t)x.Z & 15) == 0);
+    eo.vec = vec ? 1 : 0;
+    Plan E;
+    E.expadd(eo, false);
+    pl.zip({&E});
     return true;
   }
 
@@ -779,6 +864,7 @@ struct Builder {
         ExpAddOp eo{};
         eo.dst = dst;
         eo.n = n;
+        eo.nper = n;
         eo.d1 = p->d == 3 ? dt[1] : 1;
         eo.d2 = p->d == 3 ? dt[2] : 1;
         eo.P = parts;
@@ -939,6 +1025,14 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
   double* vB = p->d_vB;
   for (int m0 = 0; m0 < MR; m0 += Rrows) {
     const int rows = std::min(Rrows, MR - m0);
+    B.stage_begin();  // this chunk's intermediates (the previous chunk has finished with them)
+    const bool face = B.var_face_chunk(pl, m0, rows, p->d_vbY);
+    B.stage_end();
+    if (face) {
+      const double* Y = p->d_vbY;
+      pl.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
+      continue;
+    }
     bool first = true;
     for (int s = 1; s < p->nsets; ++s) {
       const i64 offR = p->sets[s].off - MK, ms = p->sets[s].size;

@@ -50,11 +50,15 @@ struct BilMat {  // element (r, c) = p[r rs + c cs]
   i64 rs, cs;
 };
 // out[i ldo + j ocs] = sum_t alpha_t (A_ta[t] X_tx[t] B_tb[t]^T)(i, j), with
-// A_k R x K1, X_k K1 x K2, B_k C x K2; items of FACE_RB rows
+// A_k R x K1, X_k K1 x K2, B_k C x K2; items of FACE_RB rows.  With batch > 1
+// the form is repeated for b < batch with every X advanced by b xbs elements
+// and out by b obs.
 struct BilOp {
   void* out;
   i64 ldo, ocs;
   int R, C, K1, K2;
+  int batch;
+  i64 xbs, obs;
   int nA, nX, nB, nt;
   BilMat A[FACE_MAXO], X[FACE_MAXO], B[FACE_MAXO];
   int ta[FACE_MAXT], tx[FACE_MAXT], tb[FACE_MAXT];
@@ -71,10 +75,13 @@ struct ExpTerm {
   double alpha;
 };
 // dst (d0 x d1 x d2 row-major, n elements): dst[e] = dst[e] + P_0[e] + ... +
-// P_{np-1}[e] + sum_j alpha_j f_j[e_a] Z_j[e without a], added in that order
+// P_{np-1}[e] + sum_j alpha_j f_j[e_a] Z_j[e without a], added in that order.
+// With zbs != 0, dst holds n / nper such grids (nper elements each) and grid
+// r reads every Z_j advanced by r zbs; with zero, dst[e] starts from 0.
 struct ExpAddOp {
   void* dst;
-  i64 n;
+  i64 n, nper, zbs;
+  int zero;
   int d1, d2;
   int vec;  // d2 % 4 == 0, dst, P, the Z of axes 0 / 1 16-byte aligned, pstride % 4 == 0
   const void* P;
@@ -250,7 +257,9 @@ __device__ __forceinline__ void face_stage(T* dst, int ld, const BilMat& m, int 
 template <typename T>
 __device__ __forceinline__ void bilin_item(const BilOp& op, i64 item, T* sm) {
   const int tid = threadIdx.x;
-  const int i0 = (int)item * FACE_RB;
+  const int nrb = (op.R + FACE_RB - 1) / FACE_RB;
+  const i64 bt = item / nrb;  // batch index
+  const int i0 = (int)(item - bt * nrb) * FACE_RB;
   const int rows = min(FACE_RB, op.R - i0);
   const int C = op.C, K1 = op.K1, K2 = op.K2, nt = op.nt;
   const int lb = K2 + 1;
@@ -259,7 +268,11 @@ __device__ __forceinline__ void bilin_item(const BilOp& op, i64 item, T* sm) {
   T* As = Bs + op.nB * C * lb;
   T* Ps = As + op.nA * FACE_RB * K1;
   __syncthreads();  // the buffers are free (previous item)
-  for (int k = 0; k < op.nX; ++k) face_stage<T>(Xs + k * K1 * K2, K2, op.X[k], 0, K1, K2);
+  for (int k = 0; k < op.nX; ++k) {
+    BilMat xm = op.X[k];
+    xm.p = static_cast<const T*>(xm.p) + bt * op.xbs;
+    face_stage<T>(Xs + k * K1 * K2, K2, xm, 0, K1, K2);
+  }
   for (int k = 0; k < op.nB; ++k) face_stage<T>(Bs + k * C * lb, lb, op.B[k], 0, C, K2);
   for (int k = 0; k < op.nA; ++k) face_stage<T>(As + k * FACE_RB * K1, K1, op.A[k], i0, rows, K1);
   __syncthreads();
@@ -302,7 +315,7 @@ __device__ __forceinline__ void bilin_item(const BilOp& op, i64 item, T* sm) {
         for (; k2 < K2; ++k2) s0 = fma(pv[k2], bv[k2], s0);
         acc = fma((T)op.alpha[t], (s0 + s1) + (s2 + s3), acc);
       }
-      static_cast<T*>(op.out)[(i64)(i0 + r) * op.ldo + (i64)j * op.ocs] = acc;
+      static_cast<T*>(op.out)[bt * op.obs + (i64)(i0 + r) * op.ldo + (i64)j * op.ocs] = acc;
     }
   }
 }
@@ -313,16 +326,20 @@ __device__ __forceinline__ void expadd_item_scalar(const ExpAddOp& op, i64 item)
   const T* __restrict__ P = static_cast<const T*>(op.P);
   const unsigned n = (unsigned)op.n, d1 = (unsigned)op.d1, d2 = (unsigned)op.d2;
   const unsigned base = (unsigned)(item * FACE_EXP_ELEMS) + threadIdx.x;
+  const unsigned nper = (unsigned)op.nper;
   unsigned e[FACE_EXP_EPT], i0[FACE_EXP_EPT], i1[FACE_EXP_EPT], i2[FACE_EXP_EPT];
+  i64 zo[FACE_EXP_EPT];
   T v[FACE_EXP_EPT];
 #pragma unroll
   for (int q = 0; q < FACE_EXP_EPT; ++q) {
     e[q] = base + q * FACE_THREADS;
-    const unsigned c01 = e[q] / d2;
-    i2[q] = e[q] - c01 * d2;
+    const unsigned r = op.zbs ? e[q] / nper : 0u, el = e[q] - r * nper;
+    zo[q] = (i64)r * op.zbs;
+    const unsigned c01 = el / d2;
+    i2[q] = el - c01 * d2;
     i0[q] = c01 / d1;
     i1[q] = c01 - i0[q] * d1;
-    v[q] = e[q] < n ? dst[e[q]] : T(0);
+    v[q] = (e[q] < n && !op.zero) ? dst[e[q]] : T(0);
   }
   for (int k = 0; k < op.np; ++k) {
     const T* __restrict__ pk = P + (i64)k * op.pstride;
@@ -342,7 +359,7 @@ __device__ __forceinline__ void expadd_item_scalar(const ExpAddOp& op, i64 item)
       if (x.axis == 0) { ia = i0[q]; iz = i1[q] * d2 + i2[q]; }
       else if (x.axis == 1) { ia = i1[q]; iz = i0[q] * d2 + i2[q]; }
       else { ia = i2[q]; iz = i0[q] * d1 + i1[q]; }
-      v[q] = fma(al * f[(i64)ia * x.fs], Z[iz], v[q]);
+      v[q] = fma(al * f[(i64)ia * x.fs], Z[zo[q] + iz], v[q]);
     }
   }
 #pragma unroll
@@ -379,10 +396,16 @@ __device__ __forceinline__ void expadd_item_vec(const ExpAddOp& op, i64 item) {
   if (e0 >= n) return;
   T* __restrict__ dst = static_cast<T*>(op.dst);
   const T* __restrict__ P = static_cast<const T*>(op.P);
-  const unsigned c01 = e0 / d2, c2 = e0 - c01 * d2;
+  const unsigned r = op.zbs ? e0 / (unsigned)op.nper : 0u, el = e0 - r * (unsigned)op.nper;
+  const i64 zo = (i64)r * op.zbs;
+  const unsigned c01 = el / d2, c2 = el - c01 * d2;
   const unsigned c0 = c01 / d1, c1 = c01 - c0 * d1;
   T v[4];
-  face_ld4(dst + e0, v);
+  if (op.zero) {
+    v[0] = v[1] = v[2] = v[3] = T(0);
+  } else {
+    face_ld4(dst + e0, v);
+  }
   for (int k = 0; k < op.np; ++k) {
     T w[4];
     face_ld4(P + (i64)k * op.pstride + e0, w);
@@ -393,7 +416,7 @@ __device__ __forceinline__ void expadd_item_vec(const ExpAddOp& op, i64 item) {
     const ExpTerm x = op.j[j];
     const T al = (T)x.alpha;
     const T* __restrict__ f = static_cast<const T*>(x.f);
-    const T* __restrict__ Z = static_cast<const T*>(x.Z);
+    const T* __restrict__ Z = static_cast<const T*>(x.Z) + zo;
     if (x.axis == 2) {
       const T z = Z[c0 * d1 + c1];
 #pragma unroll

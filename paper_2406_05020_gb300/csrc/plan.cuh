@@ -481,7 +481,7 @@ class Plan {
               co.push_back(o);
             } else if (op.kind == PlanOp::BILIN) {
               BilOp o = op.fbo;
-              o.items = (o.R + FACE_RB - 1) / FACE_RB;
+              o.items = (i64)std::max(o.batch, 1) * ((o.R + FACE_RB - 1) / FACE_RB);
               o.item_begin = ib;
               o.skip = skip;
               ib += o.items;
