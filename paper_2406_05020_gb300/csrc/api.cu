@@ -220,7 +220,7 @@ struct gpfvm_problem {
   double *d_QK[3] = {}, *d_lam[3] = {}, *d_lt = nullptr, *d_ltinv = nullptr;
   // E~ = G_RK (x)Q Lambda~^-1 (MR x MK) and its transpose; set 0's parts of the
   // solve vectors are coordinates in the eigenbasis (x)Q_i
-  double *d_BT = nullptr, *d_Et = nullptr, *d_EtT = nullptr, *d_E1 = nullptr, *d_Sc = nullptr, *d_LS = nullptr,
+  double *d_Tsc = nullptr, *d_Et = nullptr, *d_EtT = nullptr, *d_Sc = nullptr, *d_LS = nullptr,
          *d_LSinv = nullptr, *d_LSinvT = nullptr, *d_sscr = nullptr, *d_R = nullptr;
   double *d_tR = nullptr, *d_uR = nullptr, *d_Hsq[3] = {}, *d_yBt = nullptr;
   float *f_QK[3] = {}, *f_Et = nullptr, *f_EtT = nullptr, *f_LSinv = nullptr, *f_LSinvT = nullptr, *f_tR = nullptr,
@@ -929,35 +929,8 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
                   d >= 2 ? pp->nK[1] : 1, d >= 3 ? pp->nK[2] : 1, pp->s2, pp->sets[0].noise, pp->d_lt, st);
     recip(pp->d_lt, pp->d_ltinv, MK, st);
   });
-  if (MR > 0) {
-    pl.func([=](cudaStream_t st) {
-      GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_BT, sizeof(double) * MK, pp->d_A + (i64)MK * M, sizeof(double) * M,
-                                   sizeof(double) * MK, MR, cudaMemcpyDeviceToDevice, st));
-    });
-    B.eig_rows(pl, MR, p->d_BT, p->d_Et);
-    pl.func([=](cudaStream_t st) {
-      GPFVM_CUDA(cudaMemcpyAsync(pp->d_E1, pp->d_Et, sizeof(double) * MR * MK, cudaMemcpyDeviceToDevice, st));
-      scale_cols(pp->d_E1, MR, MK, pp->d_lt, -0.5, st);
-      GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_Sc, sizeof(double) * MR, pp->d_A + (i64)MK * M + MK, sizeof(double) * M,
-                                   sizeof(double) * MR, MR, cudaMemcpyDeviceToDevice, st));
-      GPFVM_CUDA(cudaMemsetAsync(pp->d_LS, 0, sizeof(double) * MR * MR, st));
-      GPFVM_CUDA(cudaMemsetAsync(pp->d_LSinv, 0, sizeof(double) * MR * MR, st));
-    });
-    {
-      GemmDesc g{};
-      g.m = MR; g.n = MR; g.k = MK;
-      g.a_rs = MK; g.a_cs = 1; g.b_rs = 1; g.b_cs = MK; g.c_rs = MR;
-      g.batch = 1; g.tri = TRI_C_LOWER; g.tile = dense_tile(MR, MR / 2);
-      pl.gemm(g, {{GemmGroup{p->d_Sc, nullptr, 1.0, 0.0, 0, 0}, {GemmSeg{p->d_E1, p->d_E1, -1.0}}}});
-    }
-    plan_chol_inverse(pl, p->d_Sc, p->d_LS, p->d_LSinv, MR, MR, p->d_sscr, p->d_st ? &p->d_st->pad[0] : nullptr);
-    pl.func([=](cudaStream_t st) {
-      transpose(pp->d_LSinv, pp->d_LSinvT, MR, MR, st);
-      scale_cols(pp->d_Et, MR, MK, pp->d_lt, -1.0, st);
-      transpose(pp->d_Et, pp->d_EtT, MR, MK, st);
-    });
-  }
-  // fold the eigenbasis into set 0's cell and prediction factors
+  // fold the eigenbasis into set 0's factors: cells (F_i Q_i), prediction
+  // grid (Q_i^T C_i) and the other sets (F_i(s, 0) Q_i)
   for (auto& ko : p->facq_off) {
     int ax, ka, aa, kb, ab;
     std::tie(ax, ka, aa, kb, ab) = ko.first;
@@ -965,8 +938,8 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
     const double* src = p->d_fac + p->fac_off.at(ko.first);
     GemmDesc g{};
     g.batch = 1;
-    if (ka == 0) {  // F_i Q_i: (cells x n) (n x n)
-      g.m = p->nc[ax]; g.n = n; g.k = n;
+    if (kb == 1) {  // F Q: (rows x n) (n x n)
+      g.m = (int)fam_n(p, ax, ka, aa); g.n = n; g.k = n;
       g.a_rs = n; g.a_cs = 1; g.b_rs = n; g.b_cs = 1; g.c_rs = n;
       g.tile = dense_tile(g.m, g.n);
       pl.gemm(g, {{GemmGroup{p->d_facq + ko.second, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{src, p->d_QK[ax], 1.0}}}});
@@ -976,6 +949,44 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
       g.tile = dense_tile(g.m, g.n);
       pl.gemm(g, {{GemmGroup{p->d_facq + ko.second, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_QK[ax], src, 1.0}}}});
     }
+  }
+  if (MR > 0) {
+    // E~ elementwise from the folded cross factors; S = G_RR - G_RK A^-1 G_KR
+    // with G_RK A^-1 G_KR = sigma^2 E~ ((x)C[s'])^T, a Kronecker product
+    // applied to the rows of E~ for each set s'
+    EtildeSets ES{};
+    ES.ns = p->nsets - 1;
+    for (int s = 1; s < p->nsets; ++s) {
+      ES.off[s - 1] = (int)(p->sets[s].off - MK);
+      for (int i = 0; i < 3; ++i) {
+        ES.n[s - 1][i] = i < d ? p->sets[s].n[i] : 1;
+        ES.c[s - 1][i] = i < d ? p->d_facq + p->facq_off.at(FKey(i, 1, s, 1, 0)) : nullptr;
+      }
+    }
+    const int nk0 = p->nK[0], nk1 = d >= 2 ? p->nK[1] : 1, nk2 = d >= 3 ? p->nK[2] : 1;
+    pl.func([=](cudaStream_t st) {
+      etilde(ES, nk0, nk1, nk2, pp->s2, pp->d_ltinv, pp->d_Et, MR, st);
+      transpose(pp->d_Et, pp->d_EtT, MR, MK, st);
+      GPFVM_CUDA(cudaMemcpy2DAsync(pp->d_Sc, sizeof(double) * MR, pp->d_A + (i64)MK * M + MK, sizeof(double) * M,
+                                   sizeof(double) * MR, MR, cudaMemcpyDeviceToDevice, st));
+      GPFVM_CUDA(cudaMemsetAsync(pp->d_LS, 0, sizeof(double) * MR * MR, st));
+      GPFVM_CUDA(cudaMemsetAsync(pp->d_LSinv, 0, sizeof(double) * MR * MR, st));
+    });
+    int dK[3];
+    dims_set(p, 0, dK);
+    for (int s = 1; s < p->nsets; ++s) {
+      int ds[3];
+      dims_set(p, s, ds);
+      KTerm T{};
+      T.c = 1.0;
+      for (int i = 0; i < d; ++i) T.f[i] = MatRef{p->d_facq + p->facq_off.at(FKey(i, 1, s, 1, 0)), p->nK[i], 1};
+      B.kron(pl, dK, ds, MR, {T}, p->s2, p->d_Et, p->d_Tsc, 0.0, nullptr, 0.0);
+      const i64 offR = p->sets[s].off - MK;
+      const int ms = (int)p->sets[s].size;
+      pl.func([=](cudaStream_t st) { axpy_block(pp->d_Sc + offR, MR, pp->d_Tsc, ms, MR, ms, -1.0, st); });
+    }
+    plan_chol_inverse(pl, p->d_Sc, p->d_LS, p->d_LSinv, MR, MR, p->d_sscr, p->d_st ? &p->d_st->pad[0] : nullptr);
+    pl.func([=](cudaStream_t st) { transpose(pp->d_LSinv, pp->d_LSinvT, MR, MR, st); });
   }
   pl.func([=](cudaStream_t st) {
     for (int i = 0; i < d; ++i) convert_d2f(pp->d_QK[i], pp->f_QK[i], (i64)pp->nK[i] * pp->nK[i], st);
@@ -1584,14 +1595,17 @@ void alloc_all(gpfvm_problem* p) {
     for (int a = 0; a < p->nterms; ++a)
       for (int i = 0; i < p->d; ++i) add_q(FKey(i, 0, p->alpha[a][i], 1, 0), (i64)p->nc[i] * p->sets[0].n[i]);
     for (int i = 0; i < p->d; ++i) add_q(FKey(i, 1, 0, 2, 0), (i64)p->sets[0].n[i] * p->npred[i]);
+    for (int s = 1; s < p->nsets; ++s)
+      for (int i = 0; i < p->d; ++i) add_q(FKey(i, 1, s, 1, 0), (i64)p->sets[s].n[i] * p->sets[0].n[i]);
     p->nfacq = std::max<i64>(nq, 1);
     p->d_facq = m.alloc<double>(p->nfacq);
     p->f_facq = m.alloc<float>(p->nfacq);
     if (MR > 0) {
-      p->d_BT = m.alloc<double>(MR * MK);
       p->d_Et = m.alloc<double>(MR * MK);
       p->d_EtT = m.alloc<double>(MR * MK);
-      p->d_E1 = m.alloc<double>(MR * MK);
+      i64 maxms = 0;
+      for (int s = 1; s < p->nsets; ++s) maxms = std::max<i64>(maxms, p->sets[s].size);
+      p->d_Tsc = m.alloc<double>(MR * maxms);
       p->d_R = m.alloc<double>(MR * MK);
       p->d_Sc = m.alloc<double>(MR * MR);
       p->d_LS = m.alloc<double>(MR * MR);

@@ -289,6 +289,55 @@ void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaS
   else launch_pdl(k_add_parts<double>, g, 256, 0, st, (double*)X, (const double*)P, np, stride, n);
 }
 
+// E~ = G_RK (x)Q Lambda~^-1 from its Kronecker structure: G_RK between set s
+// and set 0 is sigma^2 (x)_i F_i(s, 0), so E~[r][m] = sigma^2 prod_i
+// C_i[s](r_i, m_i) / lt[m] with C_i[s] = F_i(s, 0) Q_i (n_{s,i} x nK_i).
+__global__ void k_etilde(EtildeSets S, int nk0, int nk1, int nk2, double s2, const double* __restrict__ ltinv,
+                         double* __restrict__ Et, int MR) {
+  const i64 MK = (i64)nk0 * nk1 * nk2;
+  const i64 tot = (i64)MR * MK;
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
+    const int r = (int)(e / MK);
+    const int m = (int)(e - (i64)r * MK);
+    int s = 0;
+    while (s + 1 < S.ns && S.off[s + 1] <= r) ++s;
+    const int rl = r - S.off[s];
+    const int r2 = rl % S.n[s][2], r01 = rl / S.n[s][2], r1 = r01 % S.n[s][1], r0 = r01 / S.n[s][1];
+    const int m2 = m % nk2, m01 = m / nk2, m1 = m01 % nk1, m0 = m01 / nk1;
+    double v = s2 * S.c[s][0][r0 * nk0 + m0];
+    if (S.c[s][1]) v *= S.c[s][1][r1 * nk1 + m1];
+    if (S.c[s][2]) v *= S.c[s][2][r2 * nk2 + m2];
+    Et[e] = v * ltinv[m];
+  }
+}
+void etilde(const EtildeSets& S, int nk0, int nk1, int nk2, double s2, const double* ltinv, double* Et, int MR,
+            cudaStream_t st) {
+  const i64 tot = (i64)MR * nk0 * nk1 * nk2;
+  if (tot <= 0) return;
+  int g = ceil_div(tot, 256);
+  if (g > 8192) g = 8192;
+  k_etilde<<<g, 256, 0, st>>>(S, nk0, nk1, nk2, s2, ltinv, Et, MR);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// D[r ldd + c] += alpha S[r lds + c] for r < rows, c < cols
+__global__ void k_axpy_block(double* __restrict__ D, i64 ldd, const double* __restrict__ S, i64 lds, int rows,
+                             int cols, double alpha) {
+  const i64 tot = (i64)rows * cols;
+  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e - (i64)r * cols);
+    D[r * ldd + c] += alpha * S[r * lds + c];
+  }
+}
+void axpy_block(double* D, i64 ldd, const double* S, i64 lds, int rows, int cols, double alpha, cudaStream_t st) {
+  const i64 tot = (i64)rows * cols;
+  if (tot <= 0) return;
+  int g = ceil_div(tot, 256);
+  if (g > 8192) g = 8192;
+  k_axpy_block<<<g, 256, 0, st>>>(D, ldd, S, lds, rows, cols, alpha);
+  GPFVM_LAUNCH_CHECK();
+}
+
 // out[m] = 1/lt[m] (the weight tensor of the A^-1 quadratic form)
 __global__ void k_recip(const double* __restrict__ lt, double* __restrict__ out, i64 n) {
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x)

@@ -130,6 +130,19 @@ void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaS
 // 1 BilOp, 2 ExpAddOp; `items` CTAs in total, `smem` dynamic shared bytes.
 void launch_face(int kind, const void* table, int nops, i64 items, int f32, int smem, cudaStream_t st);
 void recip(const double* lt, double* out, i64 n, cudaStream_t st);
+// Sets 1.. of the structured IC/BC stage (row offsets relative to the first
+// of them, dims, and per axis C_i = F_i(s, 0) Q_i, null for a missing axis)
+struct EtildeSets {
+  int ns;
+  int off[GPFVM_MAX_SETS];
+  int n[GPFVM_MAX_SETS][3];
+  const double* c[GPFVM_MAX_SETS][3];
+};
+// Et (MR x MK) = sigma^2 (x)_i C_i[s] rows, times ltinv per column (k_etilde)
+void etilde(const EtildeSets& S, int nk0, int nk1, int nk2, double s2, const double* ltinv, double* Et, int MR,
+            cudaStream_t st);
+// D[r ldd + c] += alpha S[r lds + c]
+void axpy_block(double* D, i64 ldd, const double* S, i64 lds, int rows, int cols, double alpha, cudaStream_t st);
 void square(const double* in, double* out, i64 n, cudaStream_t st);
 
 }  // namespace gpfvm
