@@ -1819,6 +1819,16 @@ double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
 // state reports done (or after max_iter + 2 passes).  One launch runs a whole
 // CG run with no host round trips.  *body_kernels receives the kernels of one
 // pass (the control kernel included).
+// CG iterations per pass of a device-side loop (GPFVM_LOOP_UNROLL, 1 to 8; default 2)
+int loop_unroll() {
+  static const int u = [] {
+    const char* e = getenv("GPFVM_LOOP_UNROLL");
+    const int v = e ? std::atoi(e) : 2;
+    return std::min(std::max(v, 1), 8);
+  }();
+  return u;
+}
+
 cudaGraphExec_t make_loop_graph(CGState* st_dev, cudaStream_t st, const std::function<void()>& body,
                                 long long* body_kernels, bool host_loop) {
   if (host_loop) {  // one pass per launch; the host repeats it
@@ -1857,7 +1867,10 @@ cudaGraphExec_t make_loop_graph(CGState* st_dev, cudaStream_t st, const std::fun
     const long long before = g_launches.load();
     GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
-      body();
+      // several iterations per pass (every kernel of an iteration does nothing
+      // once the run is done), one condition update per pass
+      const int unroll = loop_unroll();
+      for (int u = 0; u < unroll; ++u) body();
       loop_ctl(st_dev, h, st);
     } catch (...) {
       cudaGraph_t dummy;
