@@ -113,15 +113,10 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
       need(op.y, e * op.m, "gemv y");
       need(op.z, e * op.m, "gemv z");
       need(op.zs, 8 * op.m, "gemv zs");
-    } else if (op.kind == PlanOp::SCALE) {
-      need(op.sc_X, (op.sc_f32 ? 4 : 8) * (i64)op.sc_rows * op.sc_cols, "scale X");
-      need(op.sc_lt, 8 * op.sc_cols, "scale lt");
     } else if (op.kind == PlanOp::COPY) {
       need(op.cp_dst, op.cp_bytes, "copy dst");
-      need(op.cp_src, op.cp_bytes, "copy src");    } else if (op.kind == PlanOp::ADD) {
-      const i64 e = op.ad_f32 ? 4 : 8;
-      need(op.ad_X, e * op.ad_n, "add X");
-      need(op.ad_P, e * ((i64)(op.ad_np - 1) * op.ad_stride + op.ad_n), "add parts");    } else if (op.kind == PlanOp::CONTR) {
+      need(op.cp_src, op.cp_bytes, "copy src");
+    } else if (op.kind == PlanOp::CONTR) {
       const ContrOp& o = op.fco;
       const i64 e = op.fc_f32 ? 4 : 8;
       need(o.in, e * o.pre * o.na * o.post, "contr in");

@@ -246,49 +246,6 @@ void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0,
   GPFVM_LAUNCH_CHECK();
 }
 
-// X[r][m] *= lt[m]^pw for rows r < rows (pw = -1 or -1/2); also a float copy if Xf
-template <typename T>
-__global__ void k_scale_cols(T* __restrict__ X, int rows, i64 cols, const double* __restrict__ lt, double pw) {
-  pdl_wait();
-  const i64 tot = (i64)rows * cols;
-  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
-    const double l = lt[e % cols];
-    const double f = (pw == -1.0) ? 1.0 / l : 1.0 / sqrt(l);
-    X[e] = (T)((double)X[e] * f);
-  }
-}
-void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st) {
-  const i64 tot = (i64)rows * cols;
-  if (tot <= 0) return;
-  int g = ceil_div(tot, 256);
-  if (g > 8192) g = 8192;
-  launch_pdl(k_scale_cols<double>, g, 256, 0, st, X, rows, cols, lt, pw);
-}
-void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st) {
-  const i64 tot = (i64)rows * cols;
-  if (tot <= 0) return;
-  int g = ceil_div(tot, 256);
-  if (g > 8192) g = 8192;
-  launch_pdl(k_scale_cols<float>, g, 256, 0, st, X, rows, cols, lt, pw);
-}
-
-template <typename T>
-__global__ void k_add_parts(T* __restrict__ X, const T* __restrict__ P, int np, i64 stride, i64 n) {
-  pdl_wait();
-  for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
-    T v = X[e];
-    for (int k = 0; k < np; ++k) v += P[(i64)k * stride + e];
-    X[e] = v;
-  }
-}
-void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaStream_t st) {
-  if (n <= 0 || np <= 0) return;
-  int g = ceil_div(n, 256);
-  if (g > 8192) g = 8192;
-  if (f32) launch_pdl(k_add_parts<float>, g, 256, 0, st, (float*)X, (const float*)P, np, stride, n);
-  else launch_pdl(k_add_parts<double>, g, 256, 0, st, (double*)X, (const double*)P, np, stride, n);
-}
-
 // E~ = G_RK (x)Q Lambda~^-1 from its Kronecker structure: G_RK between set s
 // and set 0 is sigma^2 (x)_i F_i(s, 0), so E~[r][m] = sigma^2 prod_i
 // C_i[s](r_i, m_i) / lt[m] with C_i[s] = F_i(s, 0) Q_i (n_{s,i} x nK_i).

@@ -121,11 +121,6 @@ struct JacobiJob {
 void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st);
 void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,
                    double* lt, cudaStream_t st);
-void scale_cols(double* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
-void scale_cols32(float* X, int rows, i64 cols, const double* lt, double pw, cudaStream_t st);
-// X[i] += P[i] + P[stride + i] + ... + P[(np-1) stride + i] for i < n, added
-// in that order (FP64, or FP32 when f32)
-void add_parts(void* X, const void* P, int np, i64 stride, i64 n, int f32, cudaStream_t st);
 // One launch of a merged table of face-set ops (face.cuh): kind 0 ContrOp,
 // 1 BilOp, 2 ExpAddOp; `items` CTAs in total, `smem` dynamic shared bytes.
 void launch_face(int kind, const void* table, int nops, i64 items, int f32, int smem, cudaStream_t st);

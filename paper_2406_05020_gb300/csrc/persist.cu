@@ -25,31 +25,22 @@
 
 namespace gpfvm {
 
-enum PUnitKind {
-  PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_SCALE, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM, PU_ADD, PU_CONTR, PU_BILIN, PU_EXPADD
-};
+enum PUnitKind { PU_MGEMM = 0, PU_MGEMV, PU_TC, PU_COPY, PU_GEMM, PU_GEMV, PU_TCSUM, PU_CONTR, PU_BILIN, PU_EXPADD };
 constexpr int P_SUM_CHUNKS = 64;  // items per op of a segment-group reduction
 
 constexpr int P_THREADS = 256;
 constexpr int P_GEMV_ROWS = P_THREADS / 32;  // one warp per row
-constexpr int P_ELEMS = 4 * P_THREADS;       // elements per SCALE / COPY / ADD item
+constexpr int P_ELEMS = 4 * P_THREADS;       // elements per COPY item
 
 struct PUnit {
   int kind, f32, bm, nops;
   i64 items, item_begin;
   const void* table;  // MOp* / MGemv* / TcOp*
   i64 total;          // MGEMV rows
-  // SCALE
-  void* X;
-  i64 cols, elems;
-  const double* lt;
-  double pw;
-  // COPY (4-byte words); ADD: dst[e] += sum_k src[k stride + e], e < words
+  // COPY (4-byte words)
   void* dst;
   const void* src;
   i64 words;
-  int np;
-  i64 stride;
   // single GEMM
   GemmDesc g;
   int tiles_x, tiles_y;
@@ -137,29 +128,6 @@ __device__ __forceinline__ void p_gemv_row(const PUnit& u, int i, int lane) {
   if (lane == 0) y[i] = (T)u.alpha * s + ((T)u.beta != T(0) ? (T)u.beta * y[i] : T(0));
 }
 
-template <typename T>
-__device__ __forceinline__ void p_scale_item(const PUnit& u, i64 item) {
-  T* X = static_cast<T*>(u.X);
-  const i64 e0 = item * P_ELEMS;
-  for (i64 e = e0 + threadIdx.x; e < e0 + P_ELEMS && e < u.elems; e += P_THREADS) {
-    const double l = u.lt[e % u.cols];
-    const double f = (u.pw == -1.0) ? 1.0 / l : 1.0 / sqrt(l);
-    X[e] = (T)((double)X[e] * f);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void p_add_item(const PUnit& u, i64 item) {
-  T* X = static_cast<T*>(u.dst);
-  const T* P = static_cast<const T*>(u.src);
-  const i64 e0 = item * P_ELEMS;
-  for (i64 e = e0 + threadIdx.x; e < e0 + P_ELEMS && e < u.words; e += P_THREADS) {
-    T v = X[e];
-    for (int k = 0; k < u.np; ++k) v += P[(i64)k * u.stride + e];
-    X[e] = v;
-  }
-}
-
 // Returns false if the barrier gave up (then *abort is set for the CTA).
 __device__ __forceinline__ bool grid_barrier(unsigned int* sync, int* status, int* abort_sm) {
   __syncthreads();
@@ -233,14 +201,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
           break;
         case PU_TC:
           tc_tile(static_cast<const TcOp*>(u.table), u.nops, local, cx);
-          break;
-        case PU_SCALE:
-          if (u.f32) p_scale_item<float>(u, local);
-          else p_scale_item<double>(u, local);
-          break;
-        case PU_ADD:
-          if (u.f32) p_add_item<float>(u, local);
-          else p_add_item<double>(u, local);
           break;
         case PU_CONTR: {
           const ContrOp& op = face_find(static_cast<const ContrOp*>(u.table), u.nops, local);
@@ -355,32 +315,12 @@ PersistProg* persist_build(const Plan& plan, unsigned int* sync, int* status) {
         u.items = op.tc_tiles;
         tc_maxn = std::max(tc_maxn, op.tc_maxn);
         return true;
-      case PlanOp::SCALE:
-        u.kind = PU_SCALE;
-        u.f32 = op.sc_f32;
-        u.X = op.sc_X;
-        u.cols = op.sc_cols;
-        u.elems = (i64)op.sc_rows * op.sc_cols;
-        u.lt = op.sc_lt;
-        u.pw = op.sc_pw;
-        u.items = (u.elems + P_ELEMS - 1) / P_ELEMS;
-        return true;
       case PlanOp::COPY:
         if (op.cp_bytes % 4) return false;
         u.kind = PU_COPY;
         u.dst = op.cp_dst;
         u.src = op.cp_src;
         u.words = op.cp_bytes / 4;
-        u.items = (u.words + P_ELEMS - 1) / P_ELEMS;
-        return true;
-      case PlanOp::ADD:
-        u.kind = PU_ADD;
-        u.f32 = op.ad_f32;
-        u.dst = op.ad_X;
-        u.src = op.ad_P;
-        u.np = op.ad_np;
-        u.stride = op.ad_stride;
-        u.words = op.ad_n;
         u.items = (u.words + P_ELEMS - 1) / P_ELEMS;
         return true;
       case PlanOp::GEMM: {

@@ -15,13 +15,13 @@
 namespace gpfvm {
 
 struct PlanOp {
-  // FUNC runs a host callback; TC, SCALE, COPY and ADD are typed device ops
-  // that the persistent plan kernel can also execute (they run like FUNC ops in run()).
+  // FUNC runs a host callback; TC and COPY are typed device ops that the
+  // persistent plan kernel can also execute (they run like FUNC ops in run()).
   // FORK starts background chain `bg` of the plan on its own stream; JOIN
   // makes the plan's stream wait for it.
   // CONTR, BILIN and EXPADD are the face-set ops of face.cuh (phased only:
   // merged into one launch per kind, element type and phase).
-  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, SCALE, COPY, ADD, FORK, JOIN, CONTR, BILIN, EXPADD } kind;
+  enum Kind { GEMM, GEMV, GEMV32, FUNC, TC, COPY, FORK, JOIN, CONTR, BILIN, EXPADD } kind;
   int phase = -1;  // ops sharing a phase id (>= 0, consecutive) are independent: merged launches
   GemmDesc g;
   int seg0 = 0, group0 = 0;
@@ -41,28 +41,17 @@ struct PlanOp {
   i64 tc_tiles = 0;
   int* tc_status = nullptr;
   int tc_split = 0;  // some op of the level sums segment groups (second launch)
-  // SCALE: X (rows x cols, FP64 or FP32) column j times lt[j]^pw (pw = -1 or -0.5)
-  void* sc_X = nullptr;
-  int sc_rows = 0, sc_f32 = 0;
-  i64 sc_cols = 0;
-  const double* sc_lt = nullptr;
-  double sc_pw = -1.0;
   // COPY: device to device
   void* cp_dst = nullptr;
   const void* cp_src = nullptr;
   i64 cp_bytes = 0;
-  // ADD: ad_X[i] += sum_k ad_P[k ad_stride + i] (k ascending), i < ad_n
-  void* ad_X = nullptr;
-  const void* ad_P = nullptr;
-  int ad_np = 0, ad_f32 = 0;
-  i64 ad_stride = 0, ad_n = 0;
   int bg = -1;  // FORK: index into Plan::bgs
   int fc_f32 = 0;  // face ops: element type
   ContrOp fco{};
   BilOp fbo{};
   ExpAddOp feo{};
   bool face() const { return kind == CONTR || kind == BILIN || kind == EXPADD; }
-  bool func_like() const { return kind == FUNC || kind == TC || kind == SCALE || kind == COPY || kind == ADD; }
+  bool func_like() const { return kind == FUNC || kind == TC || kind == COPY; }
 };
 
 // One merged launch of a phase: a table of GEMM ops (same element type and
@@ -215,12 +204,6 @@ class Plan {
     op.tc_split = split;
     ops.push_back(op);
   }
-  void scale(void* X, int rows, i64 cols, const double* lt, double pw, bool f32) {
-    PlanOp op;
-    op.kind = PlanOp::SCALE;
-    op.sc_X = X; op.sc_rows = rows; op.sc_cols = cols; op.sc_lt = lt; op.sc_pw = pw; op.sc_f32 = f32 ? 1 : 0;
-    ops.push_back(op);
-  }
   void copy(void* dst, const void* src, i64 bytes) {
     PlanOp op;
     op.kind = PlanOp::COPY;
@@ -246,12 +229,6 @@ class Plan {
     op.kind = PlanOp::EXPADD;
     op.feo = o;
     op.fc_f32 = f32 ? 1 : 0;
-    ops.push_back(op);
-  }
-  void add(void* X, const void* P, int np, i64 stride, i64 n, bool f32) {
-    PlanOp op;
-    op.kind = PlanOp::ADD;
-    op.ad_X = X; op.ad_P = P; op.ad_np = np; op.ad_stride = stride; op.ad_n = n; op.ad_f32 = f32 ? 1 : 0;
     ops.push_back(op);
   }
   // Runs `chain` concurrently with the ops that follow, up to the next join():
@@ -531,13 +508,8 @@ class Plan {
                     (float)op.beta, op.tri, st, skip);
     else if (op.kind == PlanOp::TC)
       launch_tc_modes(op.tc_ops, op.tc_nops, op.tc_tiles, op.tc_maxn, op.tc_status, st, op.tc_split);
-    else if (op.kind == PlanOp::SCALE) {
-      if (op.sc_f32) scale_cols32((float*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
-      else scale_cols((double*)op.sc_X, op.sc_rows, op.sc_cols, op.sc_lt, op.sc_pw, st);
-    } else if (op.kind == PlanOp::COPY) {
+    else if (op.kind == PlanOp::COPY) {
       if (op.cp_bytes > 0) GPFVM_CUDA(cudaMemcpyAsync(op.cp_dst, op.cp_src, op.cp_bytes, cudaMemcpyDeviceToDevice, st));
-    } else if (op.kind == PlanOp::ADD) {
-      add_parts(op.ad_X, op.ad_P, op.ad_np, op.ad_stride, op.ad_n, op.ad_f32, st);
     } else if (op.kind == PlanOp::FORK) {
       if (!fan) {
         bgs[op.bg]->run(st);  // no side stream: in place
