@@ -29,17 +29,19 @@
  *     gpfvm_strerror).  On error nothing is written to outputs.
  *   - A problem handle is not thread-safe; distinct handles are independent.
  *
- * Environment (read once per process)
- *   - GPFVM_ICBC=dense: invert G_BB by a dense Cholesky instead of the
- *     structured stage (eigenbasis of the largest IC/BC set + Schur
- *     complement of the others); both give the same posterior.
- *   - GPFVM_HOST_LOOP=1: CG runs are replayed pass by pass from the host
- *     instead of a device-side graph loop (same kernels and results; for
- *     per-kernel profilers).
- *   - GPFVM_LOOP_UNROLL=k (1..8, default 2): CG iterations per pass of a
- *     device-side loop.
- *   - GPFVM_PERSIST=1: Gram operators run as one cooperative launch each
- *     (bit-identical results; slower on the measured workloads).
+ * Environment switches
+ *   - GPFVM_ICBC=dense (read by gpfvm_create): invert G_BB by a dense
+ *     Cholesky instead of the structured stage (eigenbasis of the largest
+ *     IC/BC set + Schur complement of the others); both give the same
+ *     posterior.
+ *   - GPFVM_HOST_LOOP=1 (read by gpfvm_create): CG runs are replayed pass by
+ *     pass from the host instead of a device-side graph loop (same kernels
+ *     and results; for per-kernel profilers).
+ *   - GPFVM_LOOP_UNROLL=k (1..8, default 2; read once per process): CG
+ *     iterations per pass of a device-side loop.
+ *   - GPFVM_PERSIST=1 (read once per process): Gram operators run as one
+ *     cooperative launch each (bit-identical results; slower on the
+ *     measured workloads).
  */
 #ifndef GPFVM_H
 #define GPFVM_H
