@@ -15,6 +15,7 @@
 //   EXPADD  dst += sum_k P_k + sum_j alpha_j f_j (x)_{a_j} Z_j   (in a fixed order)
 #pragma once
 #include "common.cuh"
+#include "gemm_tiles.cuh"
 
 namespace gpfvm {
 
@@ -214,9 +215,10 @@ __host__ __device__ inline i64 bilin_smem_elems(int C, int K1, int K2, int nA, i
 }
 
 // dst[r ld + c] = src(r0 + r, c) for r < rows, c < cols (offsets fit 32
-// bits); FACE_BATCH loads per thread in flight before their stores, the
-// unit-stride index fastest.  A thread's elements are FACE_THREADS apart, so
-// its (r, c) advances by a fixed step (no division per element).
+// bits), as cp.async copies (global -> shared without registers; the caller
+// commits and waits), the unit-stride index fastest.  A thread's elements are
+// FACE_THREADS apart, so its (r, c) advances by a fixed step (no division per
+// element).
 template <typename T>
 __device__ __forceinline__ void face_stage(T* dst, int ld, const BilMat& m, int r0, int rows, int cols) {
   const T* __restrict__ src = static_cast<const T*>(m.p) + (i64)r0 * m.rs;
@@ -228,30 +230,20 @@ __device__ __forceinline__ void face_stage(T* dst, int ld, const BilMat& m, int 
   const int tid = threadIdx.x;
   int slow = tid / nf, fast = tid - slow * nf;
   const int step_s = FACE_THREADS / nf, step_f = FACE_THREADS - step_s * nf;
-  for (int e0 = 0; e0 < n; e0 += FACE_THREADS * FACE_BATCH) {
-    T v[FACE_BATCH];
-    int so[FACE_BATCH], dof[FACE_BATCH];
-#pragma unroll
-    for (int q = 0; q < FACE_BATCH; ++q) {
-      const bool ok = e0 + q * FACE_THREADS + tid < n;
-      so[q] = slow * ss + fast * sf;
-      dof[q] = ok ? slow * ds + fast * df : -1;
-      v[q] = ok ? src[so[q]] : T(0);
-      fast += step_f;
-      slow += step_s;
-      if (fast >= nf) {
-        fast -= nf;
-        ++slow;
-      }
+  for (int e = tid; e < n; e += FACE_THREADS) {
+    cp_async_el(dst + slow * ds + fast * df, src + slow * ss + fast * sf, true);
+    fast += step_f;
+    slow += step_s;
+    if (fast >= nf) {
+      fast -= nf;
+      ++slow;
     }
-#pragma unroll
-    for (int q = 0; q < FACE_BATCH; ++q)
-      if (dof[q] >= 0) dst[dof[q]] = v[q];
   }
 }
 
 // Every thread of the CTA calls this (it synchronises the CTA): stage the
-// distinct operands, form P_t = A_ta[t],rows X_tx[t] for every term, then
+// distinct operands (all copies in flight together), form P_t = A_ta[t],rows
+// X_tx[t] for every term, then
 // out_rows = sum_t alpha_t P_t B_tb[t]^T.  Dot products run on four
 // accumulators (fixed order).
 template <typename T>
@@ -275,6 +267,8 @@ __device__ __forceinline__ void bilin_item(const BilOp& op, i64 item, T* sm) {
   }
   for (int k = 0; k < op.nB; ++k) face_stage<T>(Bs + k * C * lb, lb, op.B[k], 0, C, K2);
   for (int k = 0; k < op.nA; ++k) face_stage<T>(As + k * FACE_RB * K1, K1, op.A[k], i0, rows, K1);
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   // P_t(r, k2) = sum_k1 A(r, k1) X(k1, k2)
   for (int o = tid; o < nt * rows * K2; o += FACE_THREADS) {
