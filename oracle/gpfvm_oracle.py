@@ -386,6 +386,26 @@ class KronIBVP:
             out += mode_apply([A.T for A in mats], W)
         return self.s2 * out.ravel()
 
+    def KPxT(self, beta: np.ndarray) -> np.ndarray:
+        """L_PDE k(X*) beta (prediction grid -> volumes): the adjoint of KPx."""
+        B = beta.reshape(self.pred.shape)
+        out = np.zeros(self.shape)
+        for c, mats in self.pp_pred:
+            out += c * mode_apply(mats, B)
+        return self.s2 * out.ravel()
+
+    def KBxT(self, beta: np.ndarray) -> np.ndarray:
+        """L_IC,BC k(X*) beta (prediction grid -> point sets): the adjoint of KBx."""
+        B = beta.reshape(self.pred.shape)
+        parts = [self.s2 * mode_apply(mats, B).ravel() for mats in self.b_pred]
+        return np.concatenate(parts) if parts else np.zeros(0)
+
+    def Lhat_k(self, beta: np.ndarray) -> np.ndarray:
+        """Lhat k(X*) beta: the cross-covariance of the volume observations with
+        the prediction points under the IC/BC-conditioned prior (Sec. 4.2),
+        L_PDE k(X*) beta - G_PB G_BB^-1 L_IC,BC k(X*) beta."""
+        return self.KPxT(beta) - self.Gpb(self.Hsolve(self.KBxT(beta)))
+
     def KB_dense(self) -> np.ndarray:
         """L_IC,BC k(X*) as a dense M x P matrix (entrywise)."""
         if not self.sets:
@@ -488,6 +508,66 @@ def itergp_actions(K: KronIBVP, S: np.ndarray):
     return mean, base - down
 
 
+def targeted_itergp(K: KronIBVP, max_iter: int, rtol: float, betas, want_var: bool = True):
+    """Targeted uncertainty reduction (appendix "Targeted uncertainty reduction").
+
+    First CG with the IterGP downdate (cg_itergp, reorthogonalised); its
+    directions p_j with eta_j = p_j^T G^ p_j give the inverse approximation
+    C = sum_j p_j p_j^T / eta_j.  Then one more IterGP action per weight vector
+    beta (in the appendix a Dir(1, ..., 1) sample over the target points, zero
+    on the rest of the prediction grid; the caller draws it):
+        t   = Lhat k(X*) beta                 (linear combination of target columns)
+        s_i = t - G^ C t                      (residual w.r.t. the inverse approximation:
+                                               the action is CG on the target system)
+        d_i = s_i - C G^ s_i                  (IterGP: conjugate to every earlier action)
+        eta_i = d_i^T G^ d_i,   C <- C + d_i d_i^T / eta_i
+        x  <- x + d_i (d_i^T r) / eta_i,  r = b - G^ x      (x stays C b)
+        down <- down + (Lhat k(X*)^T d_i)^2 / eta_i
+    Returns (x, down, actions s_i, CG directions as (p, eta) pairs)."""
+    dirs = []
+    x, down, it, hist = cg_itergp(K, max_iter, rtol, want_var, True, dirs)
+    D = [d for d, _ in dirs]
+    E = [e for _, e in dirs]
+    GD = [K.Ghat(d) for d in D]
+    b = K.rhs_hat()
+    r = b - K.Ghat(x)
+    actions = []
+    for beta in betas:
+        t = K.Lhat_k(np.asarray(beta, np.float64))
+        Ct = np.zeros_like(t)
+        for d, e in zip(D, E):
+            Ct += d * (d @ t) / e
+        s = t - K.Ghat(Ct)
+        dv = s.copy()
+        for d, g, e in zip(D, GD, E):
+            dv -= d * (g @ s) / e
+        q = K.Ghat(dv)
+        eta = float(dv @ q)
+        if not eta > 0:
+            raise FloatingPointError("targeted action: d^T G d <= 0")
+        a = float(dv @ r) / eta
+        x = x + a * dv
+        r = r - a * q
+        if want_var:
+            u = K.KPx(dv) - K.KBx(K.Hsolve(K.Gbp(dv)))
+            down = down + u * u / eta
+        D.append(dv)
+        GD.append(q)
+        E.append(eta)
+        actions.append(s)
+    return x, down, actions, dirs
+
+
+def posterior_from(K: KronIBVP, x: np.ndarray, down: np.ndarray):
+    """Posterior mean and IterGP variance on the prediction grid from the
+    representer weights x and the downdate (Eqs. lin-cond-mean, lin-cond-cov)."""
+    wB = K.Hsolve(K.yB - K.Gbp(x))
+    mean = K.KBx(wB) + K.KPx(x)
+    KB = K.KB_dense()
+    base = K.s2 - (np.sum(sla.solve_triangular(K.Lbb, KB, lower=True) ** 2, axis=0) if KB.shape[0] else 0.0)
+    return mean, base - down
+
+
 def true_residual(K: KronIBVP, x: np.ndarray) -> float:
     b = K.rhs_hat()
     return float(np.linalg.norm(b - K.Ghat(x)) / np.linalg.norm(b))
@@ -502,4 +582,8 @@ PINS = {
     "KronIBVP": "equals dense_gram blocks on small grids",
     "cg_itergp/kron_posterior": "deflated == full dense posterior; IterGP at N iterations == "
                                 "Cholesky variance; CG variance >= exact and non-increasing",
+    "KPxT/KBxT/Lhat_k": "adjoint identities against KPx/KBx; entrywise dense cross-covariances (block_cov)",
+    "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
+                                      "on one point is the Cauchy-Schwarz-optimal single-action reduction; "
+                                      "repeated targeted actions reach the exact (Cholesky) variance there",
 }
