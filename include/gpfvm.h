@@ -122,8 +122,11 @@ enum gpfvm_precision {
   GPFVM_MIXED_FP32 = 1,  /* iterative refinement: FP64 residual b - G^ x with the FP64
                             operator; inner CG on an FP32 operator (FP32 SIMT mode
                             products, FP32 vectors) with FP64 scalars and reductions */
-  GPFVM_MIXED_TF32X3 = 2 /* as MIXED_FP32, with the G_PP mode products on tcgen05 tensor
+  GPFVM_MIXED_TF32X3 = 2, /* as MIXED_FP32, with the G_PP mode products on tcgen05 tensor
                             cores in split TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulate) */
+  GPFVM_MIXED_BF16X3 = 3, /* as MIXED_TF32X3 with split bf16 operands (tcgen05 kind::f16:
+                            hi = bf16(x), lo = bf16(x - hi), three products, FP32 accumulate) */
+  GPFVM_MIXED_BF16 = 4    /* as MIXED_BF16X3 with one bf16 product (hi*hi) */
 };
 
 typedef struct {
@@ -133,12 +136,11 @@ typedef struct {
   int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions */
   int want_var;        /* 1 = accumulate the IterGP variance downdate on the grid */
   int check_every;     /* unused (kept for layout): every CG run is one device-side loop */
-  int inner_max_iter;  /* mixed: iteration cap of one inner CG (<= 0: no cap beyond max_iter) */
-  double inner_rtol;   /* mixed: residual reduction of one inner CG (<= 0: 1e-2) */
-  int inner_reorth_first; /* mixed, with reorth: 0 = reorthogonalise every inner CG run (robust);
-                             1 = only the first run, whose directions carry the IterGP variance
-                             (later runs only solve correction equations to inner_rtol; cheaper
-                             per iteration, but plain FP32 CG may stall on ill-conditioned systems) */
+  int inner_max_iter;  /* mixed: iteration cap of one inner CG run, i.e. the period of the FP64
+                          residual replacement (<= 0: no cap beyond max_iter) */
+  double inner_rtol;   /* mixed: residual reduction of one inner CG run (<= 0: 1e-2) */
+  int inner_reorth_first; /* unused (kept for layout): with reorth every inner run continues one
+                             G^-conjugate direction set (see gpfvm_solve) */
 } gpfvm_solve_opts;
 
 typedef struct {
@@ -182,7 +184,9 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream);
  *   op 5: out = G_PP v in the split-TF32 tensor-core form (FP64 in/out)
  *   op 6: out = G^ v, the inner operator of GPFVM_MIXED_FP32 (FP32, FP64 in/out)
  *   op 7: out = G^ v, the inner operator of GPFVM_MIXED_TF32X3 (FP64 in/out)
- * Ops 6 and 7 use the mixed solver's FP32 work vectors: not between the
+ *   op 8 / op 9: G_PP / G^ (inner operator) in split bf16 (GPFVM_MIXED_BF16X3)
+ *   op 10 / op 11: G_PP / G^ (inner operator) in one bf16 product (GPFVM_MIXED_BF16)
+ * Ops 6, 7, 9 and 11 use the mixed solver's FP32 work vectors: not between the
  * begin and end of a solve on the same problem.  Requires gpfvm_assemble.  v and out must not overlap. */
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);
 
@@ -201,10 +205,19 @@ int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* o
  * breakdown or max_iter (bounded by max_iter + 2 passes in any case), so the
  * host reads the state once per run.  Returns OK, NOT_CONVERGED
  * (budget exhausted; the iterate and variance downdate are kept), BREAKDOWN,
- * STATE (not assembled) or DEVICE.  info may be NULL.  Mixed precisions: the
- * stopping test is the FP64 residual of the refined iterate, and the IterGP
- * variance downdate uses the directions of the first inner CG (a valid
- * combined posterior for those actions, which are conjugate within one run). */
+ * STATE (not assembled) or DEVICE.  info may be NULL.
+ * Mixed precisions: inner CG runs on the FP32 (or tensor-core) operator
+ * with FP64 scalars, separated by FP64 residual replacements r = b - G^ x.
+ * With reorth the runs continue ONE G^-conjugate direction set: each run
+ * starts with the Galerkin projection of its residual onto all stored
+ * directions and makes every new direction conjugate to them, so with an
+ * exact operator the iterates are those of the FP64 recurrence and the
+ * IterGP downdate sums over the directions of all runs (the same actions).
+ * A run stops at inner_rtol, at inner_max_iter, or where its recurrence
+ * reaches rtol; the solve ends when the FP64 residual is <= rtol (or <= 2
+ * rtol right after a run that aimed at rtol: the FP32 recurrence's estimate)
+ * or max_iter iterations are spent.  Without reorth the runs are independent
+ * refinement steps and the downdate uses the first run's directions. */
 int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info* info,
                 void* stream);
 
@@ -213,6 +226,24 @@ int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info
  *   var  = k(x,x) - ||L^-1 k_B(x)||^2 - sum_j (Lhat k(x)^T p_j)^2 / eta_j
  * var may be NULL; a variance needs want_var in the preceding solve. */
 int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream);
+
+/* Targeted uncertainty reduction (appendix "Targeted uncertainty reduction"):
+ * continues the IterGP state of the last solve with n_actions more actions,
+ * each aimed at a weighted set of prediction points.  beta is a DEVICE array
+ * of n_actions x P doubles, row a holding the weights of action a on the
+ * prediction grid (row-major like the grid; in the appendix a Dir(1, ..., 1)
+ * sample over the target points and zero elsewhere -- the caller draws it).
+ * Action a takes t = Lhat k(X*) beta_a, the residual s = t - G^ C t of that
+ * system with respect to the inverse approximation C = sum_j p_j p_j^T/eta_j
+ * of every earlier action (so the actions run CG on the target system), and
+ * its conjugate direction d = s - C G^ s; then C += d d^T/(d^T G^ d), the
+ * iterate x = C b moves by d (d^T r)/(d^T G^ d), and the variance downdate by
+ * (Lhat k(X*)^T d)^2/(d^T G^ d).  A following gpfvm_query returns the
+ * refined mean and variance.  Requires a preceding FP64 gpfvm_solve with
+ * reorth and want_var (STATE otherwise) and room for the new directions
+ * (stored directions + n_actions <= the max_iter given to gpfvm_create, else
+ * INVALID_ARG).  BREAKDOWN if an action adds no new direction (d^T G^ d <= 0). */
+int gpfvm_target(gpfvm_problem* p, const double* beta, int n_actions, void* stream);
 
 /* One call doing assemble + solve + query with HOST input/output buffers:
  * copies the point-set values (M doubles, may be NULL to keep the
@@ -243,6 +274,9 @@ int64_t gpfvm_launch_count(void);
  *           per axis (2 * ndim values; 0 written without that stage)
  *   what 10: IC/BC stage layout: (structured 1 / dense 0, rows of the set
  *           inverted through its eigen-structure, rows of the Schur block)
+ *   what 11: the stored directions p_j of the last solve with reorth (k rows
+ *           of N; FP32 stores of the mixed precisions widened to doubles)
+ *   what 12: eta_j = p_j^T G^ p_j of those k directions (k values)
  * Returns the number of doubles written or a negative error. */
 int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capacity, void* stream);
 
@@ -297,23 +331,25 @@ void gpfvm_server_destroy(gpfvm_server* s);
 /* ------------------------------------------------------------------------
  * Allocation-free Kronecker Gram matvec.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
- * need the product -- code running while a CUDA graph is being captured,
- * frameworks whose allocator owns the whole device, real-time loops that must
- * not enter the driver's allocator.  It computes
+ * need the product -- frameworks whose allocator owns the whole device and
+ * refuse foreign allocations, real-time loops that must not enter the
+ * driver's allocator (a cudaMalloc can synchronise the device).  It computes
  *   out = scale * sum_k coef[k] (F[k][0] (x) ... (x) F[k][ndim-1]) v + diag * v
  * for a row-major tensor of dims n[0..ndim) (ndim 1..3), where F[k][i] =
  * factors[k*ndim + i] is a DEVICE pointer to an n[i] x n[i] row-major matrix
- * (e.g. the 1D factors of Eq. kronecker-structure exported by gpfvm_factor),
- * coef is a HOST array of n_terms (<= 64) coefficients, and v, out are DEVICE
- * vectors of prod n doubles that must not overlap.
+ * (for instance a 1D factor exported by gpfvm_factor), coef is a HOST array
+ * of n_terms (<= 64) coefficients, and v, out are DEVICE vectors of prod n
+ * doubles that must not overlap.
  * Memory: it calls no cudaMalloc/cudaFree or allocating routine.  The
  * intermediates (at most 4,194,304 doubles = 32 MiB; a three-axis product
  * needs (distinct last-axis factors + distinct first-axis factors) * prod n
  * doubles) and the argument tables live in file-scope device arrays that
  * every GPU loading the library keeps until the process exits; larger
- * requests return GPFVM_ERR_TOO_LARGE without launching anything.
+ * requests return GPFVM_ERR_TOO_LARGE without launching anything.  The
+ * argument tables travel as a by-value kernel parameter, so no host memory is
+ * read after the call returns.
  * The first call on a device looks up those arrays' device addresses with
- * that device current; make that first call before any stream capture.
+ * that device current (serialised across host threads).
  * All calls share the arrays and leave the last call's contents behind
  * (nothing in them needs to start at zero); calls that overlap on the GPU
  * (different streams, or host threads racing) race on them.  The work is

@@ -203,6 +203,7 @@ struct gpfvm_problem {
   double *d_S = nullptr, *d_Q = nullptr, *d_eta = nullptr, *d_part2 = nullptr, *d_coef = nullptr;
   double *d_vin = nullptr, *d_vout = nullptr, *d_win = nullptr, *d_wout = nullptr;
   double *d_vbchunk = nullptr, *d_vbY = nullptr;
+  double* d_tbeta = nullptr;  // weights of one targeted action on the prediction grid (P)
   // mixed precision (FP32 inner operator)
   float *f_fac = nullptr, *f_Linv = nullptr, *f_LinvT = nullptr;
   float *f_p = nullptr, *f_q = nullptr, *f_r = nullptr, *f_d = nullptr, *f_g = nullptr, *f_t = nullptr,
@@ -230,19 +231,20 @@ struct gpfvm_problem {
   unsigned int* d_psync = nullptr;  // grid-barrier words of the persistent plan kernel
   int* d_jac_sweeps = nullptr;  // 2 per axis: FP32 and FP64 sweeps of the last assembly
   // tensor-core G_PP (split TF32): factor splits, rotated intermediates, op tables
-  bool tc_ok = false, use_tc = false;
+  bool tc_ok = false;
+  int tc_mode = -1;  // operator of the inner CG: -1 FP32 SIMT, else the TcMode of the tensor-core G_PP
   float* f_tcsplit = nullptr;
   float *f_tcY = nullptr, *f_tcZ = nullptr;
   float* f_tcpart = nullptr;  // partial sums of split tensor-core tiles
   i64 tc_part_total = 0;      // floats f_tcpart needs (largest level)
-  std::vector<std::tuple<i64, float, i64, i64>> tc_jobs;  // (factor offset in f_fac, alpha, size, split offset)
+  std::vector<std::tuple<i64, float, i64, i64, int>> tc_jobs;  // (factor offset in f_fac, alpha, size, split offset, mode)
   TcOp* d_tcops = nullptr;
   struct TcLevel {
     int off, nops, maxn;
     i64 tiles;
     int any_split;
   };
-  std::vector<TcLevel> tc_levels[2];
+  std::vector<TcLevel> tc_levels[6];  // instance 2 m + 0: f_p -> f_q, 2 m + 1: f_vin -> f_vout (TcMode m)
   i64 tc_split_total = 0, tc_ops_total = 0;
   int tc_nu = 0, tc_nw = 0;
   int cap64 = 0, cap32 = 0;  // directions the allocated stores hold
@@ -257,9 +259,10 @@ struct gpfvm_problem {
   CGState* h_st = nullptr;  // pinned mirror of the scalar header
 
   // ---- plans
-  Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB;
+  Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB, p_tgt;
   Plan p_op[4];
-  Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32, p_mv32tc, p_mvv32tc, p_pp32tc;
+  Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32;
+  Plan p_mv32tc[3], p_mvv32tc[3], p_pp32tc[3];  // per TcMode
   int modeprods_pp = 0;
   Fan fan;  // side streams for the independent launches of a plan phase
   // GPFVM_HOST_LOOP=1: the host replays the captured iteration pass by pass
@@ -277,6 +280,8 @@ struct gpfvm_problem {
   long long graph32_kernels = 0;
   gpfvm_solve_info last{};
   int last_outer = 0;
+  int last_store = 0;   // directions of the last solve: 0 none, 1 FP64 store, 2 FP32 store
+  int last_kstore = 0;  // how many
 
   ~gpfvm_problem() {
     fan.destroy();
@@ -378,6 +383,27 @@ std::vector<KTerm> ppred_terms(const gpfvm_problem* p) {
     ts.push_back(t);
   }
   return ts;
+}
+
+// prediction grid -> cells (the adjoint of ppred_terms)
+std::vector<KTerm> predp_terms(const gpfvm_problem* p) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a) {
+    KTerm t{};
+    t.c = p->coef[a];
+    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 2, 0, false);
+    ts.push_back(t);
+  }
+  return ts;
+}
+
+// prediction grid -> set s (the adjoint of bpred_terms; fold: set 0 in its eigenbasis)
+std::vector<KTerm> predb_terms(const gpfvm_problem* p, int s, bool fold = false) {
+  const bool q = fold && s == 0 && p->sicbc;
+  KTerm t{};
+  t.c = 1.0;
+  for (int i = 0; i < p->d; ++i) t.f[i] = q ? facq_ref(p, i, 1, s, 2, 0, false) : fac_ref(p, i, 1, s, 2, 0, false);
+  return {t};
 }
 
 std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s, bool fold = false) {
@@ -899,6 +925,22 @@ struct Builder {
     dims_pred(p, dp);
     kron(plan, dc, dp, 1, ppred_terms(p), scale * p->s2, v, u, acc ? 1.0 : 0.0, nullptr, 0.0);
   }
+  // out = scale * L_PDE k(X*) beta (prediction grid -> cells)
+  void from_pred_cells(Plan& plan, const double* beta, double* out, double scale) {
+    int dc[3], dp[3];
+    dims_cells(p, dc);
+    dims_pred(p, dp);
+    kron(plan, dp, dc, 1, predp_terms(p), scale * p->s2, beta, out, 0.0, nullptr, 0.0);
+  }
+  // g = L_IC,BC k(X*) beta (prediction grid -> all sets; fold: set 0 in its eigenbasis)
+  void from_pred_sets(Plan& plan, const double* beta, double* g, bool fold) {
+    int ds[3], dp[3];
+    dims_pred(p, dp);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      kron(plan, dp, ds, 1, predb_terms(p, s, fold), p->s2, beta, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+    }
+  }
   void to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc, bool fold = false) {
     int ds[3], dp[3];
     dims_pred(p, dp);
@@ -1151,6 +1193,15 @@ void build_plans(gpfvm_problem* p, Builder& B) {
     B.to_pred_sets(p->p_mean, p->d_w, p->d_mean, 1.0, false, true);
   }
   B.to_pred_cells(p->p_mean, p->d_x, p->d_mean, 1.0, M > 0);
+  // ---- targeted actions (appendix "Targeted uncertainty reduction"):
+  // p = Lhat k(X*) beta = L_PDE k(X*) beta - G_PB G_BB^-1 L_IC,BC k(X*) beta
+  p->p_tgt = Plan();
+  B.from_pred_cells(p->p_tgt, p->d_tbeta, p->d_p, 1.0);
+  if (M > 0) {
+    B.from_pred_sets(p->p_tgt, p->d_tbeta, p->d_g2, p->sicbc);
+    B.hsolve(p->p_tgt, p->d_g2, p->d_wout);
+    B.pb(p->p_tgt, p->d_wout, p->d_p, -1.0, true, p->sicbc);
+  }
   // ---- Cholesky-stage variance term vB[p] = || L^-1 k_B(x_p) ||^2 in row chunks
   p->p_vB = Plan();
   if (M > 0 && p->sicbc) {
@@ -1190,18 +1241,18 @@ void build_plans(gpfvm_problem* p, Builder& B) {
 struct TcBuild {
   gpfvm_problem* p;
   std::vector<TcOp> ops;
-  std::map<std::pair<i64, float>, i64> split_off;
+  std::map<std::tuple<i64, float, int>, i64> split_off;
   i64 split_n = 0;
   bool ok = true;
-  const float* split(i64 fac_off, i64 n, float alpha, bool hi) {
-    auto key = std::make_pair(fac_off, alpha);
+  const float* split(i64 fac_off, i64 n, float alpha, bool hi, int mode) {
+    auto key = std::make_tuple(fac_off, alpha, mode);
     auto it = split_off.find(key);
     i64 off;
     if (it == split_off.end()) {
       off = split_n;
       split_off[key] = off;
       split_n += 2 * ((n + 63) / 64 * 64);
-      p->tc_jobs.push_back(std::make_tuple(fac_off, alpha, n, off));
+      p->tc_jobs.push_back(std::make_tuple(fac_off, alpha, n, off, mode));
     } else {
       off = it->second;
     }
@@ -1240,7 +1291,7 @@ void tc_group_levels(gpfvm_problem* p, TcBuild& T, int inst) {
   }
 }
 
-void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out, int inst) {
+void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out, int inst, int mode) {
   const int d = p->d;
   int n[3] = {1, 1, 1};
   i64 Ntot = 1;
@@ -1269,15 +1320,16 @@ void build_tc_instance(gpfvm_problem* p, TcBuild& T, const float* in, float* out
   auto seg = [&](TcOp& op, const float* A, i64 fo, int ax, double alpha) {
     if (op.nseg >= TC_MAXSEG) { T.ok = false; return; }
     op.A[op.nseg] = A;
-    op.Bhi[op.nseg] = T.split(fo, fsize(ax), (float)alpha, true);
-    op.Blo[op.nseg] = T.split(fo, fsize(ax), (float)alpha, false);
+    op.Bhi[op.nseg] = T.split(fo, fsize(ax), (float)alpha, true, mode);
+    op.Blo[op.nseg] = T.split(fo, fsize(ax), (float)alpha, false, mode);
     op.nseg++;
   };
   auto blank = [&](int R, int K, int N, float* o) {
     TcOp op{};
     op.R = R; op.K = K; op.N = N; op.out = o;
     op.sgroups = 1;
-    op.skip = (inst == 0 && p->d_st32) ? &p->d_st32->done : nullptr;
+    op.mode = mode;
+    op.skip = (inst % 2 == 0 && p->d_st32) ? &p->d_st32->done : nullptr;
     return op;
   };
   if (d == 1) {
@@ -1364,11 +1416,13 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
   if (p->M > 0) B.to_pred_sets(p->p_var32, D(p->f_w), D(p->f_u), -1.0, true, true);
   p->p_pp32 = Plan();
   B.pp(p->p_pp32, D(p->f_vin), D(p->f_vout), nullptr);
-  // tensor-core variants (split TF32 G_PP)
+  // tensor-core variants of G_PP, one pair of instances per operand format
   {
     TcBuild T{p};
-    build_tc_instance(p, T, p->f_p, p->f_q, 0);
-    build_tc_instance(p, T, p->f_vin, p->f_vout, 1);
+    for (int m = 0; m < 3; ++m) {
+      build_tc_instance(p, T, p->f_p, p->f_q, 2 * m, m);
+      build_tc_instance(p, T, p->f_vin, p->f_vout, 2 * m + 1, m);
+    }
     p->tc_ok = T.ok;
     p->tc_split_total = T.split_n;
     p->tc_ops_total = (i64)T.ops.size();
@@ -1376,7 +1430,7 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
       // host-side bounds check of every tensor-core operand before any launch
       for (const TcOp& op : T.ops) {
         bool ok = p->mem.contains(op.out, 4LL * op.N * op.R) && (!op.D || p->mem.contains(op.D, 4LL * op.N * op.R));
-        ok = ok && op.sgroups >= 1 && op.sgroups <= op.nseg &&
+        ok = ok && op.sgroups >= 1 && op.sgroups <= op.nseg && op.mode >= 0 && op.mode <= 2 &&
              (op.sgroups == 1 || p->mem.contains(op.part, 4LL * op.sgroups * op.N * op.R));
         for (int s = 0; s < op.nseg; ++s)
           ok = ok && p->mem.contains(op.A[s], 4LL * op.R * op.K) && p->mem.contains(op.Bhi[s], 4LL * op.N * op.K) &&
@@ -1386,13 +1440,15 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
       GPFVM_CUDA(cudaMemcpy(p->d_tcops, T.ops.data(), sizeof(TcOp) * T.ops.size(), cudaMemcpyHostToDevice));
     }
     if (p->tc_ok && p->d_tcops) {
-      p->p_mv32tc = Plan();
-      Plan c0 = tc_chain(p, 0);
-      B.ghat_phased(p->p_mv32tc, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), nullptr, nullptr, &c0);
-      p->p_mvv32tc = Plan();
-      Plan c1 = tc_chain(p, 0);
-      B.ghat_phased(p->p_mvv32tc, D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), D(p->f_u), nullptr, &c1);
-      p->p_pp32tc = tc_chain(p, 1);
+      for (int m = 0; m < 3; ++m) {
+        p->p_mv32tc[m] = Plan();
+        Plan c0 = tc_chain(p, 2 * m);
+        B.ghat_phased(p->p_mv32tc[m], D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), nullptr, nullptr, &c0);
+        p->p_mvv32tc[m] = Plan();
+        Plan c1 = tc_chain(p, 2 * m);
+        B.ghat_phased(p->p_mvv32tc[m], D(p->f_p), D(p->f_q), D(p->f_g), D(p->f_w), D(p->f_u), nullptr, &c1);
+        p->p_pp32tc[m] = tc_chain(p, 2 * m + 1);
+      }
     }
   }
   p->building_f32 = false;
@@ -1406,14 +1462,24 @@ void finalize_plans(gpfvm_problem* p) {
   p->p_mv32.skip = &p->d_st32->done;
   p->p_mvv32.skip = &p->d_st32->done;
   p->p_var32.skip = &p->d_st32->done;
-  Plan* all[] = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
-                 &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
-                 &p->p_mvv_cg, &p->p_mvv32, &p->p_mv32tc, &p->p_mvv32tc, &p->p_pp32tc};
-  const char* names[] = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2", "op3",
-                         "mv32", "var32", "pp32", "mvv_cg", "mvv32", "mv32tc", "mvv32tc", "pp32tc"};
-  for (int i = 0; i < 19; ++i) check_plan_ranges(*all[i], p->mem, names[i]);
-  p->p_mv32tc.skip = &p->d_st32->done;
-  p->p_mvv32tc.skip = &p->d_st32->done;
+  std::vector<Plan*> all = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
+                            &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
+                            &p->p_mvv_cg, &p->p_mvv32, &p->p_tgt};
+  std::vector<std::string> names = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2",
+                                    "op3", "mv32", "var32", "pp32", "mvv_cg", "mvv32", "tgt"};
+  for (int m = 0; m < 3; ++m) {
+    all.push_back(&p->p_mv32tc[m]);
+    all.push_back(&p->p_mvv32tc[m]);
+    all.push_back(&p->p_pp32tc[m]);
+    names.push_back("mv32tc" + std::to_string(m));
+    names.push_back("mvv32tc" + std::to_string(m));
+    names.push_back("pp32tc" + std::to_string(m));
+  }
+  for (size_t i = 0; i < all.size(); ++i) check_plan_ranges(*all[i], p->mem, names[i].c_str());
+  for (int m = 0; m < 3; ++m) {
+    p->p_mv32tc[m].skip = &p->d_st32->done;
+    p->p_mvv32tc[m].skip = &p->d_st32->done;
+  }
   if (!p->fan.fork) p->fan.create();
   for (Plan* pl : all) {
     pl->finalize();
@@ -1421,7 +1487,12 @@ void finalize_plans(gpfvm_problem* p) {
   }
   // persistent forms of the iteration operators (used when GPFVM_PERSIST=1)
   Plan* fp64_plans[] = {&p->p_mv_cg, &p->p_mvv_cg, &p->p_op[0], &p->p_op[1]};
-  Plan* fp32_plans[] = {&p->p_mv32, &p->p_mvv32, &p->p_mv32tc, &p->p_mvv32tc, &p->p_pp32, &p->p_pp32tc};
+  std::vector<Plan*> fp32_plans = {&p->p_mv32, &p->p_mvv32, &p->p_pp32};
+  for (int m = 0; m < 3; ++m) {
+    fp32_plans.push_back(&p->p_mv32tc[m]);
+    fp32_plans.push_back(&p->p_mvv32tc[m]);
+    fp32_plans.push_back(&p->p_pp32tc[m]);
+  }
   for (Plan* pl : fp64_plans) pl->prog = persist_build(*pl, p->d_psync, &p->d_st->status);
   for (Plan* pl : fp32_plans) pl->prog = persist_build(*pl, p->d_psync, &p->d_st32->pad[1]);
 }
@@ -1648,6 +1719,7 @@ void alloc_all(gpfvm_problem* p) {
   p->d_vin = m.alloc<double>(N);
   p->d_vout = m.alloc<double>(N);
   p->d_u = m.alloc<double>(P);
+  p->d_tbeta = m.alloc<double>(P);
   p->d_down = m.alloc<double>(P);
   p->d_mean = m.alloc<double>(P);
   p->d_var = m.alloc<double>(P);
@@ -1737,7 +1809,7 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
   for (auto& j : p->tc_jobs) {
     const i64 n = std::get<2>(j), off = std::get<3>(j);
     tc_split(p->f_fac + std::get<0>(j), n, std::get<1>(j), p->f_tcsplit + off, p->f_tcsplit + off + (n + 63) / 64 * 64,
-             st);
+             st, std::get<4>(j));
   }
   if (p->M > 0 && !p->sicbc) {
     convert_d2f(p->d_Linv, p->f_Linv, p->M * p->M, st);
@@ -1768,6 +1840,55 @@ void ensure_store64(gpfvm_problem* p, int need) {
   p->cap64 = need;
   p->mem.bytes += 16LL * need * ld;
   if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; p->graph_key = -1; }
+}
+// Grows the FP64 stores to `need` directions keeping the first `keep` rows.
+void grow_store64(gpfvm_problem* p, int need, int keep) {
+  need = std::min(need, p->cap);
+  if (p->cap64 >= need) return;
+  const i64 ld = store_ld(p->N);
+  double *S = nullptr, *Q = nullptr;
+  if (cudaMalloc(&S, sizeof(double) * (size_t)need * ld) != cudaSuccess ||
+      cudaMalloc(&Q, sizeof(double) * (size_t)need * ld) != cudaSuccess) {
+    cudaGetLastError();
+    if (S) cudaFree(S);
+    throw CudaError{cudaErrorMemoryAllocation, "direction store"};
+  }
+  if (keep > 0 && p->d_S) {
+    GPFVM_CUDA(cudaMemcpy(S, p->d_S, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice));
+    GPFVM_CUDA(cudaMemcpy(Q, p->d_Q, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice));
+  }
+  if (p->d_S) { cudaFree(p->d_S); cudaFree(p->d_Q); p->mem.bytes -= 16LL * p->cap64 * ld; }
+  p->d_S = S;
+  p->d_Q = Q;
+  p->cap64 = need;
+  p->mem.bytes += 16LL * need * ld;
+  if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; p->graph_key = -1; }
+}
+// Grows the FP32 stores to at least `need` directions (geometric steps, at
+// most p->cap) keeping the first `keep` rows; the captured inner loop graph
+// addresses the stores, so it is rebuilt after a move.
+void grow_store32(gpfvm_problem* p, int need, int keep) {
+  need = std::min(need, p->cap);
+  if (p->cap32 >= need) return;
+  const int want = std::min(p->cap, std::max(need, p->cap32 + p->cap32 / 2));
+  const i64 ld = store_ld(p->N);
+  float *S = nullptr, *Q = nullptr;
+  if (cudaMalloc(&S, sizeof(float) * (size_t)want * ld) != cudaSuccess ||
+      cudaMalloc(&Q, sizeof(float) * (size_t)want * ld) != cudaSuccess) {
+    cudaGetLastError();
+    if (S) cudaFree(S);
+    throw CudaError{cudaErrorMemoryAllocation, "direction store"};
+  }
+  if (keep > 0 && p->f_S) {
+    GPFVM_CUDA(cudaMemcpy(S, p->f_S, sizeof(float) * (size_t)keep * ld, cudaMemcpyDeviceToDevice));
+    GPFVM_CUDA(cudaMemcpy(Q, p->f_Q, sizeof(float) * (size_t)keep * ld, cudaMemcpyDeviceToDevice));
+  }
+  if (p->f_S) { cudaFree(p->f_S); cudaFree(p->f_Q); p->mem.bytes -= 8LL * p->cap32 * ld; }
+  p->f_S = S;
+  p->f_Q = Q;
+  p->cap32 = want;
+  p->mem.bytes += 8LL * want * ld;
+  if (p->graph32) { cudaGraphExecDestroy(p->graph32); p->graph32 = nullptr; p->graph32_key = -1; }
 }
 void ensure_store32(gpfvm_problem* p, int need) {
   need = std::min(need, p->cap);
@@ -1903,8 +2024,7 @@ std::map<const gpfvm_problem*, SolveRun>& runs() {
 int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
-  if (o->precision != GPFVM_FP64 && o->precision != GPFVM_MIXED_FP32 && o->precision != GPFVM_MIXED_TF32X3)
-    return GPFVM_ERR_INVALID_ARG;
+  if (o->precision != GPFVM_FP64) return GPFVM_ERR_INVALID_ARG;
   const bool reorth = o->reorth != 0, want_var = o->want_var != 0;
   if (reorth && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
   SolveRun& R = runs()[p];
@@ -1992,11 +2112,13 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   if (info) *info = I;
   p->solved = status >= 0;
   p->want_var_last = R.o.want_var != 0;
+  p->last_store = R.o.reorth ? 1 : 0;
+  p->last_kstore = R.o.reorth ? std::min(h.k, p->cap64) : 0;
   return status;
 }
 
 int run_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
-  if (o && (o->precision == GPFVM_MIXED_FP32 || o->precision == GPFVM_MIXED_TF32X3)) return mixed_solve(p, o, info, st);
+  if (o && o->precision != GPFVM_FP64) return mixed_solve(p, o, info, st);
   const int b = solve_begin(p, o, st);
   if (b != GPFVM_OK) return b;
   solve_launch(p, 0, st);
@@ -2023,7 +2145,7 @@ int run_query(gpfvm_problem* p, double* mean, double* var, cudaStream_t st) {
 // One inner CG iteration of the mixed solver (FP32 operator and vectors, FP64 scalars).
 void cg_iteration32(gpfvm_problem* p, bool want_var, bool reorth, cudaStream_t st) {
   const i64 N = p->N;
-  if (p->use_tc) (want_var ? p->p_mvv32tc : p->p_mv32tc).run(st);
+  if (p->tc_mode >= 0) (want_var ? p->p_mvv32tc[p->tc_mode] : p->p_mv32tc[p->tc_mode]).run(st);
   else (want_var ? p->p_mvv32 : p->p_mv32).run(st);
   cg_dot_eta<float>(p->f_p, p->f_q, N, p->d_st32, p->d_eta32, st);
   if (want_var) cg_downdate<float>(p->f_u, p->d_down, p->P, p->d_st32, st);
@@ -2034,18 +2156,32 @@ void cg_iteration32(gpfvm_problem* p, bool want_var, bool reorth, cudaStream_t s
     cg_reorth<float>(p->f_S, p->f_Q, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef, p->d_eta32, st);
 }
 
-// Iterative refinement (mixed precision, Sec. 4.1 CG as the inner solver):
-//   r = b - G^ x            FP64 operator, FP64 vectors
-//   solve G^_32 d ~= r/|r|  inner CG: FP32 operator/vectors, FP64 scalars, reorthogonalised
+// Mixed precision (Sec. 4.1 CG with an inexact operator, FP64 residual replacement):
+//   r = b - G^ x            FP64 operator, FP64 vectors (x = 0: r = b)
+//   inner CG on G^_32 d ~= r/|r|   FP32 (or tensor-core) operator, FP32 vectors, FP64 scalars
 //   x += |r| d              (the unit right-hand side keeps FP32 in range for any data scale)
-// until ||r|| / ||b|| <= rtol.  The IterGP variance downdate is accumulated
-// during the first inner CG (whose right-hand side is b and whose directions
-// are conjugate within the run).  The solve is a resumable state machine so
-// that batched and served execution can interleave many problems:
+// until ||r|| / ||b|| <= rtol or max_iter inner iterations in total.
+// With reorth the runs form ONE conjugate-direction sequence: every run keeps
+// the stored directions of all earlier runs, starts with the Galerkin
+// projection of its residual onto them (d = S c, r -= Q c, c_j = s_j.r/eta_j;
+// zero in exact arithmetic) and makes each new direction G^-conjugate to all
+// stored ones.  With an exact operator this is the FP64 CG recurrence itself
+// (the restart direction r - (q_last.r/eta) s_last is the continued CG
+// direction), so after k iterations the actions span the same Krylov space;
+// the IterGP downdate sum_j u_j^2/eta_j runs over the directions of all runs.
+// Each run's tolerance is max(inner_rtol, rtol |b|/|r|), so the last run stops
+// where the continued recurrence reaches rtol, as the FP64 path does.
+// Without reorth the runs are independent refinement steps and the downdate
+// uses the first run's directions only (conjugate within that run).
+// The solve is a resumable state machine so that batched and served execution
+// can interleave many problems:
 //   0 residual wanted -> 1 residual enqueued -> 2 inner CG running -> 0 ... -> 3 done
 struct MixedRun {
   gpfvm_solve_opts o{};
   int mstate = 3, outer = 0, total = 0, launched = 0, lim = 0, status = 0;
+  int kstore = 0;  // directions stored by the runs so far (conjugate continuation)
+  int idle = 0;    // consecutive runs that took no iteration
+  double tscale = 1.0;  // fraction of rtol the next run aims at
   double rel = 1.0, itol = 1e-2;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -2057,15 +2193,22 @@ std::map<const gpfvm_problem*, MixedRun>& mruns() {
 int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
+  if (o->precision < GPFVM_MIXED_FP32 || o->precision > GPFVM_MIXED_BF16) return GPFVM_ERR_INVALID_ARG;
   MixedRun& R = mruns()[p];
   R.o = *o;
   R.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  if (o->reorth && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
   const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
-  const bool want_tc = o->precision == GPFVM_MIXED_TF32X3;
-  if (want_tc && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
-  ensure_store32(p, icap);
-  if (want_tc != p->use_tc) {  // the captured inner iteration depends on the operator
-    p->use_tc = want_tc;
+  const int want_tc = o->precision == GPFVM_MIXED_TF32X3 ? TC_TF32X3
+                      : o->precision == GPFVM_MIXED_BF16X3 ? TC_BF16X3
+                      : o->precision == GPFVM_MIXED_BF16  ? TC_BF16
+                                                          : -1;
+  if (want_tc >= 0 && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  // without reorth one run's worth; with it the stores grow run by run
+  // (they keep the directions of every run: up to max_iter in total)
+  if (!o->reorth) ensure_store32(p, icap);
+  if (want_tc != p->tc_mode) {  // the captured inner iteration depends on the operator
+    p->tc_mode = want_tc;
     if (p->graph32) cudaGraphExecDestroy(p->graph32);
     p->graph32 = nullptr;
     p->graph32_key = -1;
@@ -2084,6 +2227,9 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   R.mstate = 0;
   R.outer = 0;
   R.total = 0;
+  R.kstore = 0;
+  R.idle = 0;
+  R.tscale = 1.0;
   R.status = GPFVM_NOT_CONVERGED;
   R.rel = 1.0;
   return GPFVM_OK;
@@ -2124,20 +2270,39 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     const double b2 = p->h_st->aux[1];
     R.rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
     if (!std::isfinite(R.rel)) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }
-    if (R.rel <= o->rtol) { R.status = GPFVM_OK; R.mstate = 3; return; }
-    if (R.total >= o->max_iter) { R.status = GPFVM_NOT_CONVERGED; R.mstate = 3; return; }
-    const bool var_now = o->want_var && R.outer == 0;
-    const bool reorth_now = o->reorth && (R.outer == 0 || !o->inner_reorth_first);
-    const int icap = std::min(p->cap32, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap32);
-    p->h_st32->rtol2 = R.itol * R.itol;
-    p->h_st32->max_iter = std::min(icap, o->max_iter - R.total);
+    const bool cont = o->reorth != 0;  // conjugate continuation across runs
+    // The last run stops where its FP32 recurrence estimates rtol; the FP64
+    // residual then confirms it within a factor 2 (the estimate's error), else
+    // the next run aims at half the remaining distance.
+    if (R.rel <= o->rtol || (cont && R.outer > 0 && R.tscale >= 1.0 && R.rel <= 2.0 * o->rtol)) {
+      R.status = GPFVM_OK;
+      R.mstate = 3;
+      return;
+    }
+    if (R.total >= o->max_iter || R.idle >= 3) { R.status = GPFVM_NOT_CONVERGED; R.mstate = 3; return; }
+    if (R.outer > 0 && R.rel <= 2.0 * o->rtol) R.tscale *= 0.5;
+    const bool var_now = o->want_var && (cont || R.outer == 0);
+    const bool reorth_now = cont;
+    const int kbase = cont ? R.kstore : 0;
+    const int run_cap = std::min(o->inner_max_iter > 0 ? o->inner_max_iter : p->cap, o->max_iter - R.total);
+    if (cont) grow_store32(p, kbase + run_cap, kbase);
+    const int icap = std::min(p->cap32 - kbase, run_cap);
+    // stop the run where the continued recurrence reaches the outer tolerance
+    const double itol = std::max(R.itol, R.rel > 0 ? R.tscale * o->rtol / R.rel : R.itol);
+    p->h_st32->rtol2 = itol * itol;
+    p->h_st32->max_iter = kbase + icap;
     p->h_st32->cap = p->cap32;
+    p->h_st32->kbase = kbase;
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->rtol2, &p->h_st32->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
     GPFVM_CUDA(
         cudaMemcpyAsync(&p->d_st32->max_iter, &p->h_st32->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->kbase, &p->h_st32->kbase, sizeof(int), cudaMemcpyHostToDevice, st));
     // the inner run solves for the normalised residual r / ||r||: FP32 then
     // sees unit-norm data whatever the scale of y (no under- or overflow)
     cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st, &p->d_st->aux[0]);
+    if (cont && kbase > 0)
+      cg_project<float>(p->f_S, p->f_Q, p->f_r, p->f_d, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef,
+                        p->d_eta32, st);
     const int key = (var_now ? 1 : 0) + (reorth_now ? 2 : 0);
     if (!p->graph32 || p->graph32_key != key) {
       if (p->graph32) cudaGraphExecDestroy(p->graph32);
@@ -2147,15 +2312,19 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
       p->graph32_key = key;
     }
     R.launched = 0;
-    R.lim = p->h_st32->max_iter;
+    R.lim = p->h_st32->max_iter - kbase;
     R.mstate = 2;
   } else if (R.mstate == 2) {
     if (R.launched == 0) return;  // the inner run has not been launched yet
     count_launch((long long)p->h_st32->loops * p->graph32_kernels);
-    const int k = p->h_st32->k;
+    const int k = p->h_st32->k - p->h_st32->kbase;  // iterations of this run
     R.total += k;
+    if (o->reorth) R.kstore = std::min(p->h_st32->k, p->cap32);
     if (p->h_st32->pad[1] & DEV_TIMEOUT) { R.status = GPFVM_ERR_TIMEOUT; R.mstate = 3; return; }
-    if (k == 0) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }  // not even one inner step
+    // a breakdown inside a run ends that run (its stored directions stay
+    // conjugate: the failed direction is never stored); none at all is an error
+    if (k == 0 && !p->h_st32->converged) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }
+    R.idle = k == 0 ? R.idle + 1 : 0;
     add_f2d(p->d_x, p->f_d, N, st, &p->d_st32->aux[7]);
     R.outer++;
     R.mstate = 0;
@@ -2181,6 +2350,8 @@ int mixed_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   if (info) *info = I;
   p->solved = R.status >= 0;
   p->want_var_last = R.o.want_var != 0;
+  p->last_store = R.o.reorth ? 2 : 0;
+  p->last_kstore = R.o.reorth ? R.kstore : 0;
   return R.status;
 }
 
@@ -2357,41 +2528,52 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream) {
   GPFVM_GUARD_END
 }
 
+}  // extern "C"
+
+namespace {
+// The FP32 operators of gpfvm_gram_matvec: op -> plan and whether it maps the
+// inner CG vectors f_p -> f_q (else f_vin -> f_vout); nullptr for FP64 ops.
+//   4 G_PP FP32 SIMT, 5 G_PP split TF32, 6 G^ FP32, 7 G^ split TF32,
+//   8 G_PP split BF16, 9 G^ split BF16, 10 G_PP BF16, 11 G^ BF16
+const Plan* op32_plan(gpfvm_problem* p, int op, bool* inner) {
+  *inner = (op == 6 || op == 7 || op == 9 || op == 11);
+  switch (op) {
+    case 4: return &p->p_pp32;
+    case 5: return &p->p_pp32tc[TC_TF32X3];
+    case 6: return &p->p_mv32;
+    case 7: return &p->p_mv32tc[TC_TF32X3];
+    case 8: return &p->p_pp32tc[TC_BF16X3];
+    case 9: return &p->p_mv32tc[TC_BF16X3];
+    case 10: return &p->p_pp32tc[TC_BF16];
+    case 11: return &p->p_mv32tc[TC_BF16];
+    default: return nullptr;
+  }
+}
+bool op_uses_tc(int op) { return op == 5 || op >= 7; }
+}  // namespace
+
+extern "C" {
+
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream) {
-  if (!p || !v || !out || op < 0 || op > 7) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || op < 0 || op > 11) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
-  if ((op == 5 || op == 7) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
-  if (op == 6 || op == 7) {  // the inner CG operator: f_p -> f_q, gated by the inner "done" flag
+  bool inner = false;
+  if (const Plan* pl = op32_plan(p, op, &inner)) {
+    // FP32 operators: the inner ones are gated by the inner "done" flag
     p->h_st32->done = 0;
     p->h_st32->pad[1] = 0;
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->done, &p->h_st32->done, sizeof(int), cudaMemcpyHostToDevice, st));
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
-    convert_d2f(v, p->f_p, p->N, st);
-    (op == 6 ? p->p_mv32 : p->p_mv32tc).run(st);
-    f2d(p->f_q, out, p->N, st);
+    convert_d2f(v, inner ? p->f_p : p->f_vin, p->N, st);
+    pl->run(st);
+    f2d(inner ? p->f_q : p->f_vout, out, p->N, st);
     GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
     GPFVM_CUDA(cudaStreamSynchronize(st));
     return (p->h_st32->pad[1] & DEV_TIMEOUT) ? GPFVM_ERR_TIMEOUT : GPFVM_OK;
-  }
-  if (op == 5) {
-    p->h_st32->pad[1] = 0;
-    GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->pad[1], &p->h_st32->pad[1], sizeof(int), cudaMemcpyHostToDevice, st));
-    convert_d2f(v, p->f_vin, p->N, st);
-    p->p_pp32tc.run(st);
-    f2d(p->f_vout, out, p->N, st);
-    GPFVM_CUDA(cudaMemcpyAsync(p->h_st32, p->d_st32, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
-    GPFVM_CUDA(cudaStreamSynchronize(st));
-    return (p->h_st32->pad[1] & DEV_TIMEOUT) ? GPFVM_ERR_TIMEOUT : GPFVM_OK;
-  }
-  if (op == 4) {
-    convert_d2f(v, p->f_vin, p->N, st);
-    p->p_pp32.run(st);
-    f2d(p->f_vout, out, p->N, st);
-    GPFVM_CUDA(cudaStreamSynchronize(st));
-    return GPFVM_OK;
   }
   const i64 nin = (op == 3) ? p->M : p->N;
   const i64 nout = (op == 2) ? p->M : p->N;
@@ -2407,14 +2589,15 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
 
 int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* out, int reps, void* stream,
                             double* ms_per_application) {
-  if (!p || !v || !out || !ms_per_application || reps < 1 || op < 0 || op > 7) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || !ms_per_application || reps < 1 || op < 0 || op > 11) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
-  if ((op == 5 || op == 7) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
-  const Plan* plan = nullptr;
-  if (op >= 4) {
+  bool inner = false;
+  const Plan* plan = op32_plan(p, op, &inner);
+  if (plan) {
     p->h_st32->done = 0;
     p->h_st32->pad[1] = 0;
     GPFVM_CUDA(cudaMemcpyAsync(&p->d_st32->done, &p->h_st32->done, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -2422,15 +2605,13 @@ int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* o
   }
   const i64 nin = (op == 3) ? p->M : p->N;
   const i64 nout = (op == 2) ? p->M : p->N;
-  switch (op) {
-    case 4: convert_d2f(v, p->f_vin, p->N, st); plan = &p->p_pp32; break;
-    case 5: convert_d2f(v, p->f_vin, p->N, st); plan = &p->p_pp32tc; break;
-    case 6: convert_d2f(v, p->f_p, p->N, st); plan = &p->p_mv32; break;
-    case 7: convert_d2f(v, p->f_p, p->N, st); plan = &p->p_mv32tc; break;
-    default:
-      GPFVM_CUDA(cudaMemcpyAsync(op == 3 ? p->d_win : p->d_vin, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
-      plan = &p->p_op[op];
+  if (plan) {
+    convert_d2f(v, inner ? p->f_p : p->f_vin, p->N, st);
+  } else {
+    GPFVM_CUDA(cudaMemcpyAsync(op == 3 ? p->d_win : p->d_vin, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
+    plan = &p->p_op[op];
   }
+  const bool is32 = op >= 4;
   // one application as a CUDA graph, replayed reps times between events
   cudaGraph_t g = nullptr;
   const long long before = g_launches.load();
@@ -2463,13 +2644,9 @@ int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* o
     float ms = 0.0f;
     GPFVM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     *ms_per_application = (double)ms / reps;
-    switch (op) {
-      case 4: case 5: f2d(p->f_vout, out, p->N, st); break;
-      case 6: case 7: f2d(p->f_q, out, p->N, st); break;
-      default:
-        GPFVM_CUDA(cudaMemcpyAsync(out, op == 2 ? p->d_wout : p->d_vout, sizeof(double) * nout,
-                                   cudaMemcpyDeviceToDevice, st));
-    }
+    if (is32) f2d(inner ? p->f_q : p->f_vout, out, p->N, st);
+    else GPFVM_CUDA(cudaMemcpyAsync(out, op == 2 ? p->d_wout : p->d_vout, sizeof(double) * nout,
+                                    cudaMemcpyDeviceToDevice, st));
     GPFVM_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
     if (e0) cudaEventDestroy(e0);
@@ -2508,6 +2685,44 @@ int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return r;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_target(gpfvm_problem* p, const double* beta, int n_actions, void* stream) {
+  if (!p || !beta || n_actions < 1) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  if (!p->solved || p->last_store != 1 || !p->want_var_last) return GPFVM_ERR_STATE;
+  const int k0 = p->last_kstore;
+  if (k0 + n_actions > p->cap) return GPFVM_ERR_INVALID_ARG;
+  const i64 N = p->N, P = p->P;
+  grow_store64(p, k0 + n_actions, k0);
+  // the scalar header of the finished CG run: never "converged" (rtol2 < 0),
+  // k0 + n_actions iterations in all, stores of cap64 directions
+  CGState& h = *p->h_st;
+  h.rtol2 = -1.0;
+  h.max_iter = k0 + n_actions;
+  h.cap = p->cap64;
+  h.done = 0;
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->rtol2, &h.rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->max_iter, &h.max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->done, &h.done, sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int a = 0; a < n_actions; ++a) {
+    GPFVM_CUDA(cudaMemcpyAsync(p->d_tbeta, beta + (i64)a * P, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+    p->p_tgt.run(st);  // p = Lhat k(X*) beta
+    // action s = t - G^ C t, direction d = s - C G^ s (conjugate to every stored one)
+    cg_residual_wrt(p->d_S, p->d_Q, p->d_p, N, p->cap64, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
+    cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap64, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
+    p->p_mvv_cg.run(st);  // q = G^ d, u = Lhat k(X*)^T d
+    cg_dot_eta_pr(p->d_p, p->d_q, p->d_r, N, p->d_st, p->d_eta, st);
+    cg_downdate(p->d_u, p->d_down, P, p->d_st, st);
+    cg_update(p->d_x, p->d_r, p->d_p, p->d_q, N, p->d_st, p->d_S, p->d_Q, st, true);
+  }
+  copy_header_to_host(p, st);
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  p->last_kstore = std::min(h.k, p->cap64);
+  if (h.status & DEV_BREAKDOWN) return GPFVM_ERR_BREAKDOWN;
+  return GPFVM_OK;
   GPFVM_GUARD_END
 }
 
@@ -2568,6 +2783,32 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
       GPFVM_CUDA(cudaStreamSynchronize(st));
       for (int i = 0; i < 2 * p->d; ++i) host_out[i] = sw[i];
       return 2 * p->d;
+    }
+    case 11: {  // stored directions p_j of the last solve (k rows of N), k = what 12's count
+      const i64 k = p->last_kstore, ld = store_ld(p->N);
+      if (k * p->N > capacity) return GPFVM_ERR_INVALID_ARG;
+      if (p->last_store == 1) {
+        GPFVM_CUDA(cudaMemcpy2DAsync(host_out, sizeof(double) * p->N, p->d_S, sizeof(double) * ld,
+                                     sizeof(double) * p->N, k, cudaMemcpyDeviceToHost, st));
+        GPFVM_CUDA(cudaStreamSynchronize(st));
+      } else if (p->last_store == 2) {
+        std::vector<float> tmp((size_t)(k * p->N));
+        GPFVM_CUDA(cudaMemcpy2DAsync(tmp.data(), sizeof(float) * p->N, p->f_S, sizeof(float) * ld,
+                                     sizeof(float) * p->N, k, cudaMemcpyDeviceToHost, st));
+        GPFVM_CUDA(cudaStreamSynchronize(st));
+        for (i64 i = 0; i < k * p->N; ++i) host_out[i] = tmp[(size_t)i];
+      }
+      return p->last_store ? k * p->N : 0;
+    }
+    case 12: {  // eta_j = p_j^T G^ p_j of the stored directions (the operator of their precision)
+      const i64 k = p->last_kstore;
+      if (k > capacity) return GPFVM_ERR_INVALID_ARG;
+      if (p->last_store && k > 0) {
+        GPFVM_CUDA(cudaMemcpyAsync(host_out, p->last_store == 1 ? p->d_eta : p->d_eta32, sizeof(double) * k,
+                                   cudaMemcpyDeviceToHost, st));
+        GPFVM_CUDA(cudaStreamSynchronize(st));
+      }
+      return p->last_store ? k : 0;
     }
     case 7: {  // timing of the last assemble / solve / query (ms)
       if (capacity < 3) return GPFVM_ERR_INVALID_ARG;

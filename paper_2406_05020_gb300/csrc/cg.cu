@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __rest
       st->rr = s;
       st->bnorm2 = s;
       st->aux[7] = 1.0 / sc;  // undoes the normalisation of the solution
-      st->k = 0;
+      st->k = st->kbase;
       st->loops = 0;
       st->status = 0;
       st->converged = (s == 0.0);
@@ -114,11 +114,12 @@ __global__ void __launch_bounds__(RT) k_downdate(const T* __restrict__ u, double
 template <typename T>
 __global__ void __launch_bounds__(RT) k_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                 const T* __restrict__ q, i64 n, CGState* st, T* __restrict__ S,
-                                                T* __restrict__ Q, i64 ld) {
+                                                T* __restrict__ Q, i64 ld, int gen) {
   pdl_wait();
   if (st->done) return;
   __shared__ double red[32];
-  const double alpha = st->rr / st->eta;
+  // CG step r.r/eta; a general direction (not built from r) takes p.r/eta
+  const double alpha = (gen ? st->aux[5] : st->rr) / st->eta;
   const int k = st->k;
   const bool keep = (S != nullptr) && (k < st->cap);
   double acc = 0.0;
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64
 
 template <typename T>
 __global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, i64 ld, T* __restrict__ p, i64 n,
-                                                      const CGState* st, const double* __restrict__ coef) {
+                                                      const CGState* st, const double* __restrict__ coef,
+                                                      double sgn) {
   pdl_wait();
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(RT) k_reorth_apply(const T* __restrict__ S, i6
   for (int j0 = 0; j0 < k; j0 += 1024) {
     const int jn = min(1024, k - j0);
     __syncthreads();
-    for (int t = threadIdx.x; t < jn; t += RT) cs[t] = (T)coef[j0 + t];
+    for (int t = threadIdx.x; t < jn; t += RT) cs[t] = (T)(sgn * coef[j0 + t]);
     __syncthreads();
     if (e < n) {
       const T* __restrict__ Sj = S + (i64)j0 * ld;
@@ -315,8 +317,62 @@ void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_
   launch_pdl(k_downdate<T>, ceil_div(n, RT), RT, 0, s, u, down, n, st);
 }
 template <typename T>
-void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s) {
-  launch_pdl(k_update<T>, reduce_grid(n), RT, 0, s, x, r, p, q, n, st, S, Q, store_ld(n));
+void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s, bool gen) {
+  launch_pdl(k_update<T>, reduce_grid(n), RT, 0, s, x, r, p, q, n, st, S, Q, store_ld(n), gen ? 1 : 0);
+}
+
+// eta = p.q (into the history, as k_dot_eta) and aux[5] = p.r in one pass
+template <typename T>
+__global__ void __launch_bounds__(RT) k_dot_eta_pr(const T* __restrict__ p, const T* __restrict__ q,
+                                                    const T* __restrict__ r, i64 n, CGState* st,
+                                                    double* __restrict__ eta_hist) {
+  pdl_wait();
+  if (st->done) return;
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const double pi = (double)p[i];
+    a = fma(pi, (double)q[i], a);
+    b = fma(pi, (double)r[i], b);
+  }
+  a = block_sum<RT>(a, red);
+  b = block_sum<RT>(b, red);
+  if (threadIdx.x == 0) {
+    st->part[blockIdx.x] = a;
+    st->part[CG_MAX_PART / 2 + blockIdx.x] = b;
+  }
+  if (last_block(&st->ticket[6])) {
+    const double sa = sum_partials(st->part, gridDim.x, red);
+    const double sb = sum_partials(st->part + CG_MAX_PART / 2, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->eta = sa;
+      st->aux[5] = sb;
+      if (!(sa > 0.0) || !isfinite(sa) || !isfinite(sb)) {
+        st->status |= DEV_BREAKDOWN;
+        st->done = 1;
+      } else if (st->k < st->cap) {
+        eta_hist[st->k] = sa;
+      }
+      st->ticket[6] = 0;
+    }
+  }
+}
+template <typename T>
+void cg_dot_eta_pr(const T* p, const T* q, const T* r, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
+  launch_pdl(k_dot_eta_pr<T>, std::min(reduce_grid(n), CG_MAX_PART / 2), RT, 0, s, p, q, r, n, st, eta_hist);
+}
+
+// p -= Q c with c_j = s_j . p / eta_j: the residual of the system G^ z = p with
+// respect to the inverse approximation C = sum_j s_j s_j^T / eta_j (p - G^ C p)
+template <typename T>
+void cg_residual_wrt(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
+                     const double* eta_hist, cudaStream_t s) {
+  const i64 ld = store_ld(n);
+  const int nchunk = reorth_chunks(n);
+  int gy = (4 * 152 + nchunk - 1) / nchunk;
+  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
+  launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, S, ld, p, n, st, part2, eta_hist, coef);
+  launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, Q, ld, p, n, st, coef, 1.0);
 }
 template <typename T>
 void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s) {
@@ -336,16 +392,68 @@ void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double
   int gy = (4 * 152 + nchunk - 1) / nchunk;
   gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
   launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, Q, ld, p, n, st, part2, eta_hist, coef);
-  launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, S, ld, p, n, st, coef);
+  launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, S, ld, p, n, st, coef, 1.0);
+}
+
+// p = r, rr = r.r (bnorm2 is kept: the run's tolerance stays relative to its
+// right-hand side before the projection)
+template <typename T>
+__global__ void __launch_bounds__(RT) k_restart(const T* __restrict__ r, T* __restrict__ p, i64 n, CGState* st) {
+  pdl_wait();
+  if (st->done) return;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const T v = r[i];
+    p[i] = v;
+    acc = fma((double)v, (double)v, acc);
+  }
+  acc = block_sum<RT>(acc, red);
+  if (threadIdx.x == 0) st->part[blockIdx.x] = acc;
+  if (last_block(&st->ticket[5])) {
+    const double s = sum_partials(st->part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->rr = s;
+      if (!isfinite(s)) {
+        st->status |= DEV_BREAKDOWN;
+        st->done = 1;
+      } else if (s <= st->rtol2 * st->bnorm2) {
+        st->converged = 1;
+        st->done = 1;
+      }
+      st->ticket[5] = 0;
+    }
+  }
+}
+
+template <typename T>
+void cg_project(const T* S, const T* Q, T* r, T* d, T* p, i64 n, int cap, CGState* st, double* part2,
+                double* coef, const double* eta_hist, cudaStream_t s) {
+  const i64 ld = store_ld(n);
+  const int nchunk = reorth_chunks(n);
+  int gy = (4 * 152 + nchunk - 1) / nchunk;
+  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
+  const int ga = ceil_div(n, RT * (16 / (int)sizeof(T)));
+  // c_j = s_j . r / eta_j  (the dots kernel with the directions in place of Q)
+  launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, S, ld, r, n, st, part2, eta_hist, coef);
+  launch_pdl(k_reorth_apply<T>, ga, RT, 0, s, Q, ld, r, n, st, coef, 1.0);   // r -= Q c
+  launch_pdl(k_reorth_apply<T>, ga, RT, 0, s, S, ld, d, n, st, coef, -1.0);  // d += S c
+  launch_pdl(k_restart<T>, reduce_grid(n), RT, 0, s, r, p, n, st);
+  cg_reorth(S, Q, p, n, cap, st, part2, coef, eta_hist, s);
 }
 
 #define GPFVM_CG_INST(T)                                                                                    \
   template void cg_dot_eta<T>(const T*, const T*, i64, CGState*, double*, cudaStream_t);                   \
   template void cg_downdate<T>(const T*, double*, i64, const CGState*, cudaStream_t);                      \
-  template void cg_update<T>(T*, T*, const T*, const T*, i64, CGState*, T*, T*, cudaStream_t);             \
+  template void cg_update<T>(T*, T*, const T*, const T*, i64, CGState*, T*, T*, cudaStream_t, bool);       \
+  template void cg_dot_eta_pr<T>(const T*, const T*, const T*, i64, CGState*, double*, cudaStream_t);        \
+  template void cg_residual_wrt<T>(const T*, const T*, T*, i64, int, CGState*, double*, double*,             \
+                                   const double*, cudaStream_t);                                             \
   template void cg_pupdate<T>(const T*, T*, i64, const CGState*, cudaStream_t);                            \
   template void cg_reorth<T>(const T*, const T*, T*, i64, int, CGState*, double*, double*, const double*,       \
-                             cudaStream_t);
+                             cudaStream_t);                                                                 \
+  template void cg_project<T>(const T*, const T*, T*, T*, T*, i64, int, CGState*, double*, double*,          \
+                              const double*, cudaStream_t);
 GPFVM_CG_INST(double)
 GPFVM_CG_INST(float)
 template void cg_init<double, double>(const double*, double*, double*, double*, i64, CGState*, cudaStream_t,

@@ -11,7 +11,8 @@ struct CGState {
   double aux[8];
   int k, done, converged, status, max_iter, cap;
   int pad[2];
-  int loops, pad2;  // passes of the device-side iteration loop (reset by cg_init)
+  int loops;  // passes of the device-side iteration loop (reset by cg_init)
+  int kbase;  // directions already stored when a run starts: cg_init sets k = kbase
   unsigned int ticket[8];
   double part[CG_MAX_PART];
 };
@@ -29,13 +30,29 @@ template <typename T>
 void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
 template <typename T>
 void cg_downdate(const T* u, double* down, i64 n, const CGState* st, cudaStream_t s);
+// x += alpha p, r -= alpha q (stores p, q as direction k), alpha = r.r/eta, or
+// with gen = true alpha = p.r/eta (aux[5], from cg_dot_eta_pr): the step along
+// a conjugate direction that was not built from r
 template <typename T>
-void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s);
+void cg_update(T* x, T* r, const T* p, const T* q, i64 n, CGState* st, T* S, T* Q, cudaStream_t s,
+               bool gen = false);
+template <typename T>
+void cg_dot_eta_pr(const T* p, const T* q, const T* r, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
+template <typename T>
+void cg_residual_wrt(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
+                     const double* eta_hist, cudaStream_t s);
 template <typename T>
 void cg_pupdate(const T* r, T* p, i64 n, const CGState* st, cudaStream_t s);
 template <typename T>
 void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
                const double* eta_hist, cudaStream_t s);
+// Restart of a CG run that continues a G^-conjugate direction set (S, Q =
+// G^ S, the st->k = kbase directions stored so far): Galerkin projection of the
+// new residual r onto span S, i.e. d += S c and r -= Q c with c_j = s_j.r/eta_j;
+// then p = r made conjugate to every stored direction and rr = r.r.
+template <typename T>
+void cg_project(const T* S, const T* Q, T* r, T* d, T* p, i64 n, int cap, CGState* st, double* part2,
+                double* coef, const double* eta_hist, cudaStream_t s);
 // x += (*scale) d  (scale defaults to 1)
 // Control node of a device-side CG loop (a graph WHILE node): one more pass
 // while the CG state is not done, and never more than max_iter + 2 passes.

@@ -1,13 +1,18 @@
 // Kronecker Gram matvec that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need a Gram
-// product: code running while a CUDA graph is being captured, allocators that
-// own the whole device and forbid foreign allocations, or real-time loops
-// that must not touch the driver's allocator.  This entry point keeps the
-// intermediates of the three-level mode-product chain and the GEMM argument
-// tables in file-scope __device__ arrays instead: every GPU that loads the
-// library holds them (about 32 MiB) until the process exits.
+// product: frameworks whose allocator owns the whole device and refuse
+// foreign allocations, or real-time loops that must not enter the driver's
+// allocator (a cudaMalloc can synchronise the device and take milliseconds).
+// This entry point keeps the intermediates of the three-level mode-product
+// chain and the GEMM argument tables in file-scope __device__ arrays instead:
+// every GPU that loads the library holds them (about 32 MiB) until the
+// process exits.  The argument tables reach the device as the by-value
+// parameter of a small fill kernel, so no host memory is read after the call
+// returns.
 #include <string.h>
+
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -31,12 +36,15 @@ struct NoallocAddrs {
 
 // Device addresses of the static arrays, looked up once per device with that
 // device current (a host-side reference to the array names is only a host
-// stand-in, not a device address).
+// stand-in, not a device address).  The lookup is serialised by a mutex, so
+// host threads making their first calls at the same time are safe.
 static int noalloc_setup(NoallocAddrs* out) {
+  static std::mutex mu;
   static NoallocAddrs cache[NOALLOC_MAX_DEVICES];
   static bool ready[NOALLOC_MAX_DEVICES] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return GPFVM_ERR_DEVICE;
+  std::lock_guard<std::mutex> lock(mu);
   if (!ready[dev]) {
     NoallocAddrs a{};
     if (cudaGetSymbolAddress((void**)&a.scratch, g_noalloc_scratch) != cudaSuccess) return GPFVM_ERR_DEVICE;
@@ -47,6 +55,21 @@ static int noalloc_setup(NoallocAddrs* out) {
   }
   *out = cache[dev];
   return GPFVM_OK;
+}
+
+// The GEMM argument tables of one call, passed BY VALUE as a kernel parameter
+// (about 12.5 KB, within the 32 KB parameter limit): the launch copies them,
+// so nothing on the host stack is read once the call has returned.
+struct NoallocTables {
+  int ns, ng;
+  GemmSeg segs[NOALLOC_MAX_SEGS];
+  GemmGroup groups[NOALLOC_MAX_GROUPS];
+};
+static_assert(sizeof(NoallocTables) < 32000, "kernel parameter too large");
+
+__global__ void noalloc_fill_kernel(const NoallocTables t) {
+  for (int i = threadIdx.x; i < t.ns; i += blockDim.x) g_noalloc_segs[i] = t.segs[i];
+  for (int i = threadIdx.x; i < t.ng; i += blockDim.x) g_noalloc_groups[i] = t.groups[i];
 }
 
 }  // namespace gpfvm
@@ -90,10 +113,10 @@ extern "C" int gpfvm_kron_matvec_noalloc(int ndim, const int* n, int n_terms, co
   if (st_ok != GPFVM_OK) return st_ok;
   cudaStream_t st = (cudaStream_t)stream;
 
-  GemmSeg segs[NOALLOC_MAX_SEGS];
-  GemmGroup groups[NOALLOC_MAX_GROUPS];
-  memset(segs, 0, sizeof(segs));
-  memset(groups, 0, sizeof(groups));
+  static thread_local NoallocTables tab;  // large: kept off the stack
+  memset(&tab, 0, sizeof(tab));
+  GemmSeg* segs = tab.segs;
+  GemmGroup* groups = tab.groups;
   int ns = 0, ng = 0;
   GemmDesc L[3];
   int nl = 0;
@@ -165,10 +188,12 @@ extern "C" int gpfvm_kron_matvec_noalloc(int ndim, const int* n, int n_terms, co
       for (int j = 0; j < nw; ++j) segs[ns++] = GemmSeg{Wf[j], Z + (long long)j * N, scale};
       L[nl++] = g;
     }
-    // argument tables into the static arrays (pageable host -> device, stream ordered)
-    if (cudaMemcpyAsync(A.segs, segs, sizeof(GemmSeg) * ns, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(A.groups, groups, sizeof(GemmGroup) * ng, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return GPFVM_ERR_DEVICE;
+    // argument tables into the static arrays: by-value kernel parameter, stream ordered
+    tab.ns = ns;
+    tab.ng = ng;
+    noalloc_fill_kernel<<<1, 256, 0, st>>>(tab);
+    if (cudaGetLastError() != cudaSuccess) return GPFVM_ERR_DEVICE;
+    count_launch(1);
     for (int l = 0; l < nl; ++l) launch_gemm64(L[l], st);
   } catch (const CudaError&) {
     return GPFVM_ERR_DEVICE;

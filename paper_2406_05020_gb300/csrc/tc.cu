@@ -12,7 +12,9 @@
 // (round to nearest) and x_lo = x - x_hi; the product is accumulated in FP32
 // TMEM as A_hi B_hi + A_hi B_lo + A_lo B_hi, about FP32 accuracy.  Factors are
 // pre-scaled and pre-split once per assembly; tensor data is split while it
-// is staged into shared memory.
+// is staged into shared memory.  The bf16 forms (kind::f16) split into
+// bf16(x) and bf16(x - bf16(x)) (three products, about 2^-16 relative) or
+// keep bf16(x) alone (one product, 2^-8), staged in 64-byte-swizzled rows.
 //
 // Per CTA (128 threads): one 128-row output tile at a time; for every segment
 // and 32-wide K block the A and B slices are written to shared memory in the
@@ -94,21 +96,23 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
   if (any_split) launch_pdl(tc_sum_kernel, dim3(2 * 152, nops), 256, 0, st, d_ops);
 }
 
-// hi = tf32(alpha * F), lo = alpha * F - hi for an n x k row-major factor
+// hi / lo parts of alpha * F (n entries) for the operand format `mode`:
+// TF32X3 hi = tf32(v), lo = v - hi; BF16X3 hi = bf16(v), lo = bf16(v - hi);
+// BF16 hi = bf16(v), lo = 0
 __global__ void k_tc_split(const float* __restrict__ F, i64 n, float alpha, float* __restrict__ hi,
-                           float* __restrict__ lo) {
+                           float* __restrict__ lo, int mode) {
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
     const float v = alpha * F[e];
-    const float h = tf32_rna(v);
+    const float h = mode == TC_TF32X3 ? tf32_rna(v) : bf16_rn(v);
     hi[e] = h;
-    lo[e] = v - h;
+    lo[e] = mode == TC_TF32X3 ? v - h : (mode == TC_BF16X3 ? bf16_rn(v - h) : 0.0f);
   }
 }
-void tc_split(const float* F, i64 n, float alpha, float* hi, float* lo, cudaStream_t st) {
+void tc_split(const float* F, i64 n, float alpha, float* hi, float* lo, cudaStream_t st, int mode) {
   if (n <= 0) return;
   int g = ceil_div(n, 256);
   if (g > 1024) g = 1024;
-  k_tc_split<<<g, 256, 0, st>>>(F, n, alpha, hi, lo);
+  k_tc_split<<<g, 256, 0, st>>>(F, n, alpha, hi, lo, mode);
   GPFVM_LAUNCH_CHECK();
 }
 

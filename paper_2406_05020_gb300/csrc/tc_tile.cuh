@@ -1,6 +1,8 @@
 // Device building blocks of the tcgen05 mode-product kernel (tc.cu), shared
 // with the persistent plan kernel (persist.cu).  See tc.cu for the method.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "tc.cuh"
 
 namespace gpfvm {
@@ -20,6 +22,23 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + (c & 3) * 4);
 }
 
+// byte offset of bf16 element (r, c) (c < 32) in a K-major, 64-byte-swizzled
+// slice: 64-byte rows, 8-row atoms of 512 bytes, the 16-byte chunk index
+// XOR-ed with address bits 7-8 (= (r >> 1) & 3)
+__device__ __forceinline__ uint32_t sw64(int r, int c) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((c >> 3) ^ (r >> 1)) & 3) << 4) + (c & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                    // leading byte offset: unused for swizzled K-major
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8-row groups 512 B apart
+  d |= (uint64_t)1 << 46;                    // descriptor version (sm_100 family)
+  d |= (uint64_t)4 << 61;                    // layout: 64-byte swizzle
+  return d;
+}
+
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
@@ -35,6 +54,17 @@ __device__ __forceinline__ uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
 }
 
+// kind::f16 instruction descriptor with bf16 A and B: D f32, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float bf16_rn(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -46,6 +76,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
@@ -102,7 +140,8 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
   const int s_lo = grp * op.nseg / sg;
   const int K = op.K, N = op.N, R = op.R;
   const int npad = (N + 15) & ~15;
-  const uint32_t idesc = idesc_tf32(npad);
+  const int mode = op.mode;
+  const uint32_t idesc = mode == TC_TF32X3 ? idesc_tf32(npad) : idesc_bf16(npad);
   uint32_t acc = 0;
   // Stage (segment, K block) pairs in order; the next pair's global loads
   // are issued into registers while the tensor cores work on the current one.
@@ -135,7 +174,7 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
   for (int st = 0; st < nstage && !*cx.abort_flag; ++st) {
     const int k0 = (st % nkb) * TC_KB;
     // registers -> shared (split A into hi / lo), previous MMAs have completed
-    if (act) {
+    if (act && mode == TC_TF32X3) {
 #pragma unroll
       for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
         const int r = rb + 4 * q;
@@ -153,21 +192,54 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
           *(float*)(cx.sBlo + off) = rbl[q];
         }
       }
+    } else if (act) {  // bf16 operands in 64-byte rows (the B parts are exact bf16 values)
+#pragma unroll
+      for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
+        const int r = rb + 4 * q;
+        const float v = ra[q], vh = bf16_rn(v);
+        const uint32_t off = sw64(r, c);
+        *(unsigned short*)(cx.sAhi + off) = bf16_bits(vh);
+        if (mode == TC_BF16X3) *(unsigned short*)(cx.sAlo + off) = bf16_bits(v - vh);
+      }
+#pragma unroll
+      for (int q = 0; q < TC_BREG; ++q) {
+        const int r = rb + 4 * q;
+        if (r < npad) {
+          const uint32_t off = sw64(r, c);
+          *(unsigned short*)(cx.sBhi + off) = bf16_bits(rbh[q]);
+          if (mode == TC_BF16X3) *(unsigned short*)(cx.sBlo + off) = bf16_bits(rbl[q]);
+        }
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int kk = min(TC_KB, K - k0);
-      const int ksteps = (kk + 7) / 8;
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
-        const uint64_t ah = desc_sw128(smem_u32(cx.sAhi) + koff), al = desc_sw128(smem_u32(cx.sAlo) + koff);
-        const uint64_t bh = desc_sw128(smem_u32(cx.sBhi) + koff), bl = desc_sw128(smem_u32(cx.sBlo) + koff);
-        mma_tf32(cx.tmem, ah, bh, idesc, acc);
-        acc = 1;
-        mma_tf32(cx.tmem, ah, bl, idesc, 1);
-        mma_tf32(cx.tmem, al, bh, idesc, 1);
+      if (mode == TC_TF32X3) {
+        const int ksteps = (kk + 7) / 8;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
+          const uint64_t ah = desc_sw128(smem_u32(cx.sAhi) + koff), al = desc_sw128(smem_u32(cx.sAlo) + koff);
+          const uint64_t bh = desc_sw128(smem_u32(cx.sBhi) + koff), bl = desc_sw128(smem_u32(cx.sBlo) + koff);
+          mma_tf32(cx.tmem, ah, bh, idesc, acc);
+          acc = 1;
+          mma_tf32(cx.tmem, ah, bl, idesc, 1);
+          mma_tf32(cx.tmem, al, bh, idesc, 1);
+        }
+      } else {
+        const int ksteps = (kk + 15) / 16;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t koff = ks * 32;  // 16 bf16 = 32 bytes inside the 64-byte row
+          const uint64_t ah = desc_sw64(smem_u32(cx.sAhi) + koff), bh = desc_sw64(smem_u32(cx.sBhi) + koff);
+          mma_bf16(cx.tmem, ah, bh, idesc, acc);
+          acc = 1;
+          if (mode == TC_BF16X3) {
+            const uint64_t al = desc_sw64(smem_u32(cx.sAlo) + koff), bl = desc_sw64(smem_u32(cx.sBlo) + koff);
+            mma_bf16(cx.tmem, ah, bl, idesc, 1);
+            mma_bf16(cx.tmem, al, bh, idesc, 1);
+          }
+        }
       }
       mma_commit(cx.bar);
     }

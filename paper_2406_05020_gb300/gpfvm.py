@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libgpfvm.so")
 
 MAX_DIM, MAX_TERMS, MAX_SETS = 3, 8, 8
 OK, NOT_CONVERGED = 0, 1
-FP64, MIXED_FP32, MIXED_TF32X3 = 0, 1, 2
+FP64, MIXED_FP32, MIXED_TF32X3, MIXED_BF16X3, MIXED_BF16 = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "gpfvm_server_poll": (C.c_int, [P, C.c_int64, D, D, C.POINTER(SolveInfo)]),
     "gpfvm_server_destroy": (None, [P]),
     "gpfvm_set_values": (C.c_int, [P, P, P]),
+    "gpfvm_target": (C.c_int, [P, P, C.c_int, P]),
     "gpfvm_launch_count": (C.c_int64, []),
     "gpfvm_kron_matvec_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_void_p), D,
                                             C.c_double, C.c_double, P, P, P]),
@@ -122,6 +123,30 @@ def _check(code, where):
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(D)
+
+
+def _dev(t, n: int, name: str):
+    """Checks a device tensor handed to the library as a raw pointer: float64,
+    contiguous, on the current CUDA device, with exactly n elements (the C ABI
+    cannot check sizes, so a wrong one would become an out-of-bounds access)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name}: expected float64, got {t.dtype}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: must live on the current CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() != n:
+        raise ValueError(f"{name}: expected {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _disjoint(a, b, name: str):
+    a0, b0 = a.data_ptr(), b.data_ptr()
+    if a0 < b0 + 8 * b.numel() and b0 < a0 + 8 * a.numel():
+        raise ValueError(f"{name}: input and output memory overlap")
 
 
 def _stream(stream):
@@ -210,16 +235,30 @@ class Problem:
     def assemble(self, stream=None):
         return _check(lib().gpfvm_assemble(self.h, _stream(stream)), "gpfvm_assemble")
 
+    def _op_sizes(self, op: int):
+        if not 0 <= op <= 11:
+            raise ValueError(f"unknown operator {op}")
+        if op == 2:
+            return self.N, self.M
+        if op == 3:
+            return self.M, self.N
+        return self.N, self.N
+
     def matvec(self, op: int, v, out, stream=None):
         """out = op(v) on device tensors (see gpfvm_gram_matvec)."""
-        return _check(lib().gpfvm_gram_matvec(self.h, int(op), C.c_void_p(v.data_ptr()),
-                                              C.c_void_p(out.data_ptr()), _stream(stream)), "gpfvm_gram_matvec")
+        nin, nout = self._op_sizes(op)
+        pv, po = _dev(v, nin, "v"), _dev(out, nout, "out")
+        _disjoint(v, out, "matvec")
+        return _check(lib().gpfvm_gram_matvec(self.h, int(op), pv, po, _stream(stream)), "gpfvm_gram_matvec")
 
     def matvec_bench(self, op: int, v, out, reps: int = 50, stream=None) -> float:
         """Device ms of one application of op (graph replays; see gpfvm_gram_matvec_bench)."""
+        nin, nout = self._op_sizes(op)
+        pv, po = _dev(v, nin, "v"), _dev(out, nout, "out")
+        _disjoint(v, out, "matvec_bench")
         ms = C.c_double(0.0)
-        _check(lib().gpfvm_gram_matvec_bench(self.h, int(op), C.c_void_p(v.data_ptr()), C.c_void_p(out.data_ptr()),
-                                             int(reps), _stream(stream), C.byref(ms)), "gpfvm_gram_matvec_bench")
+        _check(lib().gpfvm_gram_matvec_bench(self.h, int(op), pv, po, int(reps), _stream(stream), C.byref(ms)),
+               "gpfvm_gram_matvec_bench")
         return ms.value
 
     def solve(self, opts: Optional[SolveOpts] = None, stream=None, **kw):
@@ -229,9 +268,18 @@ class Problem:
         return code, self.info
 
     def query(self, mean, var=None, stream=None):
-        return _check(lib().gpfvm_query(self.h, C.c_void_p(mean.data_ptr()),
-                                        C.c_void_p(var.data_ptr()) if var is not None else None,
-                                        _stream(stream)), "gpfvm_query")
+        pm = _dev(mean, self.P, "mean")
+        pv = _dev(var, self.P, "var") if var is not None else None
+        if var is not None:
+            _disjoint(mean, var, "query")
+        return _check(lib().gpfvm_query(self.h, pm, pv, _stream(stream)), "gpfvm_query")
+
+    def target(self, betas, stream=None):
+        """Targeted uncertainty reduction: one IterGP action per row of betas
+        (device tensor, n_actions x P weights on the prediction grid; see gpfvm_target)."""
+        n = int(betas.shape[0]) if betas.dim() == 2 else 1
+        return _check(lib().gpfvm_target(self.h, _dev(betas, n * self.P, "betas"), n, _stream(stream)),
+                      "gpfvm_target")
 
     def solve_host(self, values: Optional[np.ndarray], opts: SolveOpts, mean: np.ndarray,
                    var: Optional[np.ndarray] = None, stream=None):
@@ -244,7 +292,7 @@ class Problem:
 
     def set_values(self, values_dev, stream=None):
         """New point-set values (device tensor of M doubles) on the assembled problem."""
-        return _check(lib().gpfvm_set_values(self.h, C.c_void_p(values_dev.data_ptr()), _stream(stream)),
+        return _check(lib().gpfvm_set_values(self.h, _dev(values_dev, self.M, "values"), _stream(stream)),
                       "gpfvm_set_values")
 
     def export(self, what: int, n: int) -> np.ndarray:
@@ -271,12 +319,19 @@ def kron_matvec_noalloc(dims, terms, scale, diag, v, out, stream=None):
     """out = scale * sum_k c_k (F_k0 (x) ...) v + diag * v without any device
     allocation; terms = [(c_k, [F_k0, F_k1, ...])] with device tensors F."""
     ndim = len(dims)
+    total = int(np.prod(dims))
+    pv, po = _dev(v, total, "v"), _dev(out, total, "out")
+    _disjoint(v, out, "kron_matvec_noalloc")
+    for _, fs in terms:
+        if len(fs) != ndim:
+            raise ValueError("kron_matvec_noalloc: one factor per axis")
+        for i, f in enumerate(fs):
+            _dev(f, int(dims[i]) ** 2, f"factor on axis {i}")
     n = (C.c_int * ndim)(*dims)
     ptrs = (C.c_void_p * (len(terms) * ndim))(*[f.data_ptr() for _, fs in terms for f in fs])
     coef = np.ascontiguousarray([c for c, _ in terms], dtype=np.float64)
     return _check(lib().gpfvm_kron_matvec_noalloc(ndim, n, len(terms), ptrs, _dptr(coef), float(scale),
-                                                  float(diag), C.c_void_p(v.data_ptr()), C.c_void_p(out.data_ptr()),
-                                                  _stream(stream)), "gpfvm_kron_matvec_noalloc")
+                                                  float(diag), pv, po, _stream(stream)), "gpfvm_kron_matvec_noalloc")
 
 
 class Server:

@@ -113,3 +113,36 @@ def test_c3_200_iterations_properties(c3):
     # more CG actions can only lower the combined-posterior variance
     assert np.all(v <= res[12][1] + 1e-12)
     pb.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_c3_mixed_with_residual_replacement(c3, prec):
+    """The early-terminated mixed form (FP32 / split-TF32 operator, FP64
+    residual replacement every 50 iterations, one conjugate direction set):
+    its first 12 iterates follow the oracle's FP64 recurrence to the operator's
+    precision times the recurrence's growth; after 200 iterations its
+    properties hold (the 200th iterate itself is decided by rounding: two FP64
+    orderings of the IC/BC inverse already differ by 0.6% there)."""
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob, K = c3
+    pb = gpfvm.Problem(prob, max_iter=200)
+    pb.assemble()
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    code, info = pb.solve(max_iter=12, rtol=0.0, precision=prec, reorth=True, want_var=True, inner_max_iter=5)
+    assert info.iterations == 12
+    pb.query(mean, var)
+    x, down, it, hist = O.cg_itergp(K, 12, 0.0, True, True)
+    m_o = K.KBx(K.Hsolve(K.yB - K.Gbp(x))) + K.KPx(x)
+    assert relerr(mean.cpu().numpy(), m_o) < 3e-4
+    np.testing.assert_allclose(pb.export(5, pb.P), down, rtol=0, atol=3e-6)
+    code, info = pb.solve(max_iter=200, rtol=0.0, precision=prec, reorth=True, want_var=True, inner_max_iter=50)
+    assert code == 1 and info.iterations == 200 and pb.export(8, 1)[0] == 4
+    pb.query(mean, var)
+    v = var.cpu().numpy()
+    assert np.all(np.isfinite(mean.cpu().numpy()))
+    assert np.all(pb.export(12, 200) > 0)
+    assert v.min() >= -RTOL and v.max() <= prob.outputscale + RTOL
+    pb.close()

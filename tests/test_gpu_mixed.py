@@ -88,3 +88,102 @@ def test_mixed_c2_full_size_against_fp64_path():
     pb.query(m32)
     assert relerr(m32.cpu().numpy(), m64.cpu().numpy()) < 1e-6
     pb.close()
+
+
+# ---------------------------------------------------------------------------
+# Conjugate continuation across refinement runs (the variance of the mixed
+# precisions).  Beyond about 100 CG iterations the IterGP variance with CG
+# actions is decided by rounding: two FP64 GPU paths that differ only in the
+# order of the IC/BC inverse (structured vs dense Cholesky) differ by
+# 1e-2 sigma^2 there.  So the mixed variance is pinned (a) to the IterGP
+# posterior of its OWN actions, (b) to the FP64 path before that regime, and
+# (c) at convergence to within a few times the FP64-vs-FP64 spread.
+# ---------------------------------------------------------------------------
+def _posterior(pb):
+    import torch
+    m = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    v = torch.empty_like(m)
+    pb.query(m, v)
+    return m.cpu().numpy(), v.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["heat2d_16", "wave2d"])
+def test_mixed_variance_is_itergp_of_its_own_actions(name, prec):
+    """The downdate accumulated over all refinement runs (restarts every 25
+    iterations: Galerkin projections exercised) is the IterGP posterior
+    C = S (S^T G^ S)^-1 S^T of the exported directions S, and the iterate is C b."""
+    from paper_2406_05020_gb300 import gpfvm
+    prob = PROBS[name]()
+    pb = gpfvm.Problem(prob, max_iter=200)
+    pb.assemble()
+    K = O.KronIBVP(prob)
+    iters = min(60, prob.N // 3)
+    code, info = pb.solve(max_iter=iters, rtol=0.0, precision=prec, reorth=True, want_var=True, inner_rtol=1e-2,
+                          inner_max_iter=25)
+    assert info.iterations == iters and pb.export(8, 1)[0] >= 2
+    k = int(pb.export(12, iters).size)
+    assert k == iters
+    S = pb.export(11, k * prob.N).reshape(k, prob.N).T
+    m, v = _posterior(pb)
+    m_ref, v_ref = O.itergp_actions(K, S)
+    tol = 2e-6 if prec == 1 else 2e-5
+    np.testing.assert_allclose(v, v_ref, rtol=0, atol=tol * prob.outputscale)
+    assert relerr(m, m_ref) < 10 * tol
+    pb.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (2, 1e-4)])
+def test_mixed_c2_first_iterations_match_fp64(prec, tol):
+    """2D+time heat 64^3: after 20 iterations (before rounding decides the
+    Krylov space) the mixed posterior matches the FP64 path's, mean and
+    variance; the bound is the operator's precision times the growth the
+    recurrence shows there (FP32 1e-7, split TF32 1e-6)."""
+    from paper_2406_05020_gb300 import gpfvm
+    prob = W.heat_2d(seed=2)
+    pb = gpfvm.Problem(prob, max_iter=64)
+    pb.assemble()
+    pb.solve(max_iter=20, rtol=0.0, precision=gpfvm.FP64, reorth=True, want_var=True)
+    m64, v64 = _posterior(pb)
+    pb.solve(max_iter=20, rtol=0.0, precision=prec, reorth=True, want_var=True, inner_rtol=1e-2, inner_max_iter=8)
+    m, v = _posterior(pb)
+    assert relerr(m, m64) < tol
+    assert np.abs(v - v64).max() < tol * prob.outputscale
+    pb.close()
+
+
+def test_mixed_c2_full_size_bench_options():
+    """The option set the benchmark times (MIXED_TF32X3, inner_rtol 1e-2,
+    reorth, variance) on the full 2D+time heat 64^3 problem: mean within 1e-6
+    of the FP64 path, the same iteration count within 3, and a variance within
+    5x the spread between two FP64 orderings (structured vs dense IC/BC)."""
+    import os
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob = W.heat_2d(seed=2)
+    pb = gpfvm.Problem(prob, max_iter=1500)
+    pb.assemble()
+    code, i64 = pb.solve(max_iter=1500, rtol=1e-10, precision=gpfvm.FP64, reorth=True, want_var=True)
+    assert code == 0
+    m64, v64 = _posterior(pb)
+    k64 = i64.iterations
+    code, imx = pb.solve(max_iter=1500, rtol=1e-10, precision=gpfvm.MIXED_TF32X3, reorth=True, want_var=True,
+                         check_every=32, inner_rtol=1e-2, inner_reorth_first=True)
+    assert code == 0, imx.as_dict()
+    assert imx.true_rel_residual <= 2e-10
+    m, v = _posterior(pb)
+    pb.close()
+    os.environ["GPFVM_ICBC"] = "dense"
+    try:
+        pd = gpfvm.Problem(prob, max_iter=1500)
+    finally:
+        os.environ.pop("GPFVM_ICBC", None)
+    pd.assemble()
+    code, idn = pd.solve(max_iter=k64, rtol=0.0, precision=gpfvm.FP64, reorth=True, want_var=True)
+    md, vd = _posterior(pd)
+    pd.close()
+    spread = float(np.abs(vd - v64).max())
+    assert relerr(m, m64) < 1e-6
+    assert abs(imx.iterations - k64) <= 3
+    assert np.abs(v - v64).max() <= 5 * spread + 1e-6, (np.abs(v - v64).max(), spread)
+    assert v.min() >= -1e-9 and v.max() <= prob.outputscale + 1e-9

@@ -73,3 +73,53 @@ def test_mixed_tf32x3_solve(name):
     if v is not None:
         assert np.all(var.cpu().numpy() >= v - 1e-7)
     pb.close()
+
+
+# ---------------------------------------------------------------------------
+# bf16 operands (tcgen05 kind::f16).  Split bf16 keeps hi = bf16(x) and
+# lo = bf16(x - hi): each operand carries about 16 significant bits (2^-17),
+# and dropping lo*lo adds 2^-16 per product, so a product is good to about
+# 2e-5; the 9 terms of a three-term operator partly cancel (the split-TF32
+# operator shows a 5x growth over its per-product error), hence 2e-4.  One
+# bf16 product (8 bits, 2^-9 per operand) is good to about 4e-3 per product:
+# bound 2e-2.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("op,tol", [(8, 2e-4), (10, 2e-2)])
+@pytest.mark.parametrize("name", ["heat2d_8", "heat2d_ragged", "heat2d_tiles", "wave2d", "heat1d", "c2_64"])
+def test_bf16_gram_matvec(name, op, tol):
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob = PROBS[name]()
+    pb = gpfvm.Problem(prob, max_iter=8)
+    pb.assemble()
+    K = O.KronIBVP(prob)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        v = rng.normal(size=prob.N)
+        out = torch.full((prob.N,), float("nan"), dtype=torch.float64, device="cuda")
+        pb.matvec(op, torch.as_tensor(v, device="cuda"), out)
+        assert relerr(out.cpu().numpy(), K.Gpp(v)) < tol
+    pb.close()
+
+
+@pytest.mark.parametrize("name", ["heat2d_ragged", "heat2d_tiles", "heat1d"])
+def test_mixed_bf16x3_solve(name):
+    """Split-bf16 inner operator + FP64 residual replacement: the refined mean
+    reaches the 1e-6 bar."""
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    prob = PROBS[name]()
+    pb = gpfvm.Problem(prob, max_iter=4000)
+    pb.assemble()
+    code, info = pb.solve(max_iter=4000, rtol=1e-10, precision=gpfvm.MIXED_BF16X3, want_var=True)
+    assert code == 0, info.as_dict()
+    mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    pb.query(mean)
+    if prob.N + prob.M < 3000:
+        m, _ = O.dense_posterior(prob)
+    else:
+        m = O.kron_posterior(prob, rtol=1e-12, want_var=False)["mean"]
+    assert relerr(mean.cpu().numpy(), m) < 1e-6
+    pb.close()

@@ -1,9 +1,9 @@
 """The allocation-free Kronecker Gram matvec (gpfvm_kron_matvec_noalloc).
 
 Callers that cannot allocate device memory when they need a Gram product --
-code running during CUDA-graph capture, frameworks whose allocator owns the
-whole device, real-time loops that must stay out of the driver's allocator --
-use this entry point: its intermediates live in a fixed static device array.
+frameworks whose allocator owns the whole device, real-time loops that must
+stay out of the driver's allocator -- use this entry point: its intermediates
+live in a fixed static device array.
 These tests check it through the C ABI against the regular entry point
 (gpfvm_gram_matvec, op 0, whose intermediates live in memory allocated at
 problem creation), on two calls in a row, and check that requests beyond the
@@ -49,6 +49,7 @@ def _pp_terms(pb, prob):
     lambda: W.heat_2d(17, 33, 70, n_ic=(9, 11), n_bc=(4, 5), pred=(5, 6, 7)),
     lambda: W.heat_2d(64, 64, 64, seed=0),
     lambda: W.heat_1d(16, 32),
+    lambda: W.toy_cos(40),  # one axis: a single level, no intermediates
 ])
 def test_noalloc_matches_regular_matvec_twice(mk):
     import torch
@@ -74,15 +75,23 @@ def test_noalloc_matches_regular_matvec_twice(mk):
 
 
 def test_noalloc_rejects_requests_beyond_capacity():
+    import ctypes as C
+
     import torch
 
     from paper_2406_05020_gb300 import gpfvm
     # three 128-point axes with 4 distinct last-axis and 4 distinct first-axis
-    # factors need 8 * 128^3 doubles of intermediates (> 4,194,304): refused
-    # before anything is launched, so the tiny stand-in tensors are never read
+    # factors need 8 * 128^3 doubles of intermediates (> 4,194,304): the C entry
+    # point refuses before anything is launched, so the tiny stand-in tensors
+    # (called through the raw C ABI, past the binding's size checks) are never read
     dummy = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(8)]
-    terms = [(1.0, [dummy[k % 4], dummy[0], dummy[4 + k % 4]]) for k in range(4)]
+    facs = [dummy[k % 4] if i == 0 else (dummy[0] if i == 1 else dummy[4 + k % 4])
+            for k in range(4) for i in range(3)]
     v = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(gpfvm.GpfvmError) as e:
-        gpfvm.kron_matvec_noalloc([128, 128, 128], terms, 1.0, 0.0, v, v)
-    assert e.value.code == -9
+    n = (C.c_int * 3)(128, 128, 128)
+    ptrs = (C.c_void_p * 12)(*[f.data_ptr() for f in facs])
+    coef = (C.c_double * 4)(1.0, 1.0, 1.0, 1.0)
+    code = gpfvm.lib().gpfvm_kron_matvec_noalloc(3, n, 4, ptrs, coef, 1.0, 0.0, C.c_void_p(v.data_ptr()),
+                                                 C.c_void_p(v.data_ptr()), None)
+    assert code == -9
+    torch.cuda.synchronize()
