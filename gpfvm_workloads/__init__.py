@@ -65,6 +65,9 @@ class Problem:
     rhs: Optional[np.ndarray] = None
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # "fvm": one volume integral of the PDE per cell; "collocation": the PDE
+    # evaluated at each cell centre (rhs then holds point values of the forcing)
+    observe: str = "fvm"
 
     @property
     def ndim(self) -> int:
@@ -225,15 +228,28 @@ def wave_2d_sine(nt: int = 8, nx: int = 8, ny: int = 8, C=None, c: float = 1.0, 
                    name=f"wave_sine_{nt}x{nx}x{ny}", meta={"C": C, "c": c, "T": T})
 
 
-def toy_cos(n: int = 8, ell: float = 1.0, pred: int = 50, jitter: float = 1e-10) -> Problem:
+def toy_cos(n: int = 8, ell: float = 1.0, pred: int = 50, jitter: float = 1e-10,
+            observe: str = "fvm") -> Problem:
     """Sec. 3 toy problem (Fig. 2): du/dx = cos x on [0, 2 pi], u(0)=u(2 pi)=0.
 
-    The right-hand side of the i-th volume observation is int_{a_i}^{b_i} cos x dx."""
+    The right-hand side of the i-th volume observation is int_{a_i}^{b_i} cos x dx;
+    with observe="collocation" it is cos at the centre of cell i."""
     e = uniform_edges(0.0, 2 * np.pi, n)
-    rhs = np.sin(e[1:]) - np.sin(e[:-1])
+    if observe == "collocation":
+        rhs = np.cos(0.5 * (e[1:] + e[:-1]))
+    else:
+        rhs = np.sin(e[1:]) - np.sin(e[:-1])
     bc = PointSet((0,), [np.array([0.0, 2 * np.pi])], np.zeros(2), jitter, "bc")
     return Problem([e], (ell,), 1.0, [((1,), 1.0)], jitter, [bc],
-                   [np.linspace(0, 2 * np.pi, pred)], rhs=rhs, name=f"toy_cos_{n}")
+                   [np.linspace(0, 2 * np.pi, pred)], rhs=rhs, name=f"toy_cos_{observe}_{n}", observe=observe)
+
+
+def collocation(prob: Problem) -> Problem:
+    """The same homogeneous IBVP observed by collocation at the cell centres."""
+    if prob.rhs is not None:
+        raise ValueError("only homogeneous problems: give point values of the forcing instead")
+    from dataclasses import replace
+    return replace(prob, observe="collocation", name=prob.name + "_colloc")
 
 
 def batch_heat(n_problems: int = 256, lo: int = 16, hi: int = 64, seed: int = 0,

@@ -33,6 +33,10 @@ SQRT5 = math.sqrt(5.0)
 # finite differences in tests/test_oracle_closed_forms.py):
 #   k'(r)  = -sgn(r) s z (1 + z)/3 e^-z
 #   k''(r) = -s^2 (1 + z - z^2)/3 e^-z
+#   k^(3)(r) = sgn(r) s^3 z (3 - z)/3 e^-z      (continuous: ~ s^4 r near 0)
+#   k^(4)(r) = s^4 (3 - 5z + z^2)/3 e^-z        (k^(4)(0) = s^4 = 25/ell^4)
+# (the third and fourth derivatives are needed only by collocation
+# observations of second-order operators)
 #   K1(r)  =  sgn(r)/s  [8/3 - (8/3 + 5z/3 + z^2/3) e^-z]
 #   K2(r)  =  s^-2 [8z/3 - 5 + (5 + 7z/3 + z^2/3) e^-z]
 # Near z = 0 both antiderivatives lose digits to cancellation, so their
@@ -69,7 +73,7 @@ def f2(z):
 
 
 def kderiv(r, ell: float, order: int):
-    """k^(order)(r) of the unit-scale 1D Matern-5/2 kernel, order in -2..2."""
+    """k^(order)(r) of the unit-scale 1D Matern-5/2 kernel, order in -2..4."""
     r = np.asarray(r, dtype=np.float64)
     s = SQRT5 / ell
     z = s * np.abs(r)
@@ -81,11 +85,15 @@ def kderiv(r, ell: float, order: int):
         return -sg * s * z * (1.0 + z) / 3.0 * e
     if order == 2:
         return -s * s * (1.0 + z - z * z) / 3.0 * e
+    if order == 3:
+        return sg * s ** 3 * z * (3.0 - z) / 3.0 * e
+    if order == 4:
+        return s ** 4 * (3.0 - 5.0 * z + z * z) / 3.0 * e
     if order == -1:
         return sg * g1(z) / s
     if order == -2:
         return f2(z) / (s * s)
-    raise ValueError(f"derivative order {order} outside -2..2")
+    raise ValueError(f"derivative order {order} outside -2..4")
 
 
 # ----------------------------------------------------------------------------
@@ -99,9 +107,10 @@ def cell_family(a: np.ndarray, b: np.ndarray, alpha: int):
 
 
 def point_family(x: np.ndarray, order: int):
-    """Stacked 1D point functionals d^order u(x_j)."""
-    if order not in (0, 1):
-        raise ValueError("point derivative order must be 0 or 1")
+    """Stacked 1D point functionals d^order u(x_j) (order 2 only for the
+    collocation operator; Matern-5/2 paths are twice differentiable)."""
+    if order not in (0, 1, 2):
+        raise ValueError("point derivative order must be 0, 1 or 2")
     return ("point", np.asarray(x, np.float64), int(order))
 
 
@@ -125,8 +134,8 @@ def cov_1d(F, G, ell: float) -> np.ndarray:
     Taylor series of the full function instead."""
     A, B = _atoms(F), _atoms(G)
     order = A[0][1] + B[0][1]
-    if order > 2:
-        raise ValueError("total derivative order above 2 is not supported by Matern-5/2 paths")
+    if order > 4:
+        raise ValueError("total derivative order above 4 is not supported by Matern-5/2 paths")
     s = SQRT5 / ell
     pairs = []
     for (w1, m, x1) in A:
@@ -178,10 +187,17 @@ class Block:
 
 def pde_block(prob) -> Block:
     """L_PDE of a factorized box scheme (Sec. 4.1): one volume per cell,
-    L_V[u] = sum_alpha c_alpha int_V D^alpha u  (Eq. linop-def, Eq. multi-input-fv)."""
+    L_V[u] = sum_alpha c_alpha int_V D^alpha u  (Eq. linop-def, Eq. multi-input-fv).
+    With collocation observations (Sec. 3: the collocation operator
+    L_x[u] = D[u](x)) the functional of a cell is instead D[u] at its centre:
+    sum_alpha c_alpha D^alpha u (x_V), point families of order alpha_i."""
     terms = []
+    colloc = getattr(prob, "observe", "fvm") == "collocation"
     for alpha, c in prob.terms:
-        fams = [cell_family(e[:-1], e[1:], a) for e, a in zip(prob.edges, alpha)]
+        if colloc:
+            fams = [point_family(0.5 * (e[:-1] + e[1:]), a) for e, a in zip(prob.edges, alpha)]
+        else:
+            fams = [cell_family(e[:-1], e[1:], a) for e, a in zip(prob.edges, alpha)]
         terms.append((float(c), fams))
     return Block(prob.n_cells, terms, "pde")
 
@@ -582,6 +598,10 @@ PINS = {
     "KronIBVP": "equals dense_gram blocks on small grids",
     "cg_itergp/kron_posterior": "deflated == full dense posterior; IterGP at N iterations == "
                                 "Cholesky variance; CG variance >= exact and non-increasing",
+    "kderiv orders 3, 4 / order-2 point families": "finite differences; the spectral moment k^(4)(0) by "
+                                                    "quadrature of the Matern spectral density; collocation "
+                                                    "posteriors of the Fig. 2 toy and the 1D heat equation "
+                                                    "converge to the analytic solutions",
     "KPxT/KBxT/Lhat_k": "adjoint identities against KPx/KBx; entrywise dense cross-covariances (block_cov)",
     "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
                                       "on one point is the Cauchy-Schwarz-optimal single-action reduction; "

@@ -178,4 +178,6 @@ def test_rejects_unsupported_orders():
     with pytest.raises(ValueError):
         O.cell_family(np.zeros(1), np.ones(1), 3)
     with pytest.raises(ValueError):
-        O.point_family(np.zeros(1), 2)
+        O.point_family(np.zeros(1), 3)
+    with pytest.raises(ValueError):
+        O.kderiv(0.5, 1.0, 5)
