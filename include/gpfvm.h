@@ -98,7 +98,12 @@ typedef struct {
  *                  row-major (NULL = homogeneous PDE).
  *   jitter         noise variance added to every volume observation.
  *   sets           initial/boundary point sets (the Cholesky-deflated part).
- *   pred           per-axis coordinates of the tensor prediction grid. */
+ *   pred           per-axis coordinates of the tensor prediction grid.
+ *   observe        0: finite volumes (the PDE integrated over every cell);
+ *                  1: collocation (Sec. 3, the operator D[u](x)): the PDE at
+ *                  the centre of every cell, rhs then holding point values of
+ *                  the forcing; the same Kronecker structure with point
+ *                  factors (kernel derivatives up to order 4). */
 typedef struct {
   int ndim;
   int n_cells[GPFVM_MAX_DIM];
@@ -114,6 +119,7 @@ typedef struct {
   gpfvm_point_set sets[GPFVM_MAX_SETS];
   int n_pred[GPFVM_MAX_DIM];
   const double* pred[GPFVM_MAX_DIM];
+  int observe;
 } gpfvm_desc;
 
 /* Precision of the CG iteration. */
@@ -133,7 +139,10 @@ typedef struct {
   int max_iter;        /* iteration budget (>= 1); also sizes the stored directions */
   double rtol;         /* stop when ||b - G^ x|| / ||b|| <= rtol (recursive residual) */
   int precision;       /* enum gpfvm_precision */
-  int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions */
+  int reorth;          /* 1 = full G^-conjugate reorthogonalisation of directions (mixed: one
+                          conjugate set across all refinement runs, stores for every run);
+                          2 = mixed only: within each run (stores for one run, the variance
+                          from the first run's actions); 0 = none */
   int want_var;        /* 1 = accumulate the IterGP variance downdate on the grid */
   int check_every;     /* unused (kept for layout): every CG run is one device-side loop */
   int inner_max_iter;  /* mixed: iteration cap of one inner CG run, i.e. the period of the FP64
@@ -158,7 +167,7 @@ typedef struct gpfvm_problem gpfvm_problem;
  * solve (factors, IC/BC matrices, CG state with room for max_iter stored
  * directions, prediction outputs).  max_iter <= 0 selects 2000.  Errors:
  * INVALID_ARG (bad sizes, orders, non-increasing edges, lengthscale <= 0,
- * total derivative order above 2 in any covariance), OUT_OF_MEMORY. */
+ * observe not 0 or 1), OUT_OF_MEMORY. */
 int gpfvm_create(const gpfvm_desc* desc, int max_iter, gpfvm_problem** out);
 
 /* Frees every device and host resource of the problem (NULL is a no-op). */
@@ -226,6 +235,21 @@ int gpfvm_solve(gpfvm_problem* p, const gpfvm_solve_opts* opts, gpfvm_solve_info
  *   var  = k(x,x) - ||L^-1 k_B(x)||^2 - sum_j (Lhat k(x)^T p_j)^2 / eta_j
  * var may be NULL; a variance needs want_var in the preceding solve. */
 int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream);
+
+/* Mode-product autotuner (an addition of this library; the paper has no
+ * counterpart).  Times the solver operator of `precision` on this problem
+ * (graph replays on `stream`) under each candidate plan policy -- the row
+ * tile of the SIMT mode-product GEMMs (the size heuristic, or always 64, 32
+ * or 16 rows) and, for the tensor-core precisions, with and without the
+ * segment grouping of idle levels -- rebuilds the problem's plans with the
+ * fastest and caches that choice per (precision, operator terms, axis sizes
+ * rounded up to 16), so that later problems of the same size class take it
+ * without timing.  Results are unchanged up to the summation order of the
+ * split levels.  report (may be NULL) receives up to report_cap doubles: the
+ * ms of each timed candidate, then the choice (3 (tile + 1) + grouping off).
+ * Returns 0 (timed), 1 (taken from the cache) or an error (STATE before
+ * gpfvm_assemble).  Allocates two N-vectors while timing. */
+int gpfvm_autotune(gpfvm_problem* p, int precision, void* stream, double* report, int report_cap);
 
 /* Targeted uncertainty reduction (appendix "Targeted uncertainty reduction"):
  * continues the IterGP state of the last solve with n_actions more actions,

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <tuple>
 #include <type_traits>
@@ -183,13 +184,14 @@ struct gpfvm_problem {
   SetC sets[GPFVM_MAX_SETS];
   int npred[3] = {1, 1, 1};
   std::vector<double> pred[3];
+  bool colloc = false;  // PDE observed at the cell centres (collocation) instead of cell integrals
   i64 N = 0, M = 0, P = 0;
   int cap = 0;
 
   // ---- device memory
   DevBuf mem;
   double* d_coords = nullptr;
-  i64 off_edges[3] = {0, 0, 0}, off_pred[3] = {0, 0, 0}, off_set[GPFVM_MAX_SETS][3] = {};
+  i64 off_edges[3] = {0, 0, 0}, off_pred[3] = {0, 0, 0}, off_set[GPFVM_MAX_SETS][3] = {}, off_mid[3] = {0, 0, 0};
   double* d_fac = nullptr;
   std::map<FKey, i64> fac_off;
   std::vector<FactorJob> jobs;
@@ -280,6 +282,7 @@ struct gpfvm_problem {
   long long graph32_kernels = 0;
   gpfvm_solve_info last{};
   int last_outer = 0;
+  int tuned_tile = -1, tuned_tc = 0;  // plan policies chosen by gpfvm_autotune
   int last_store = 0;   // directions of the last solve: 0 none, 1 FP64 store, 2 FP32 store
   int last_kstore = 0;  // how many
 
@@ -310,8 +313,10 @@ void need_factor(gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab) {
   FKey key(ax, ka, aa, kb, ab);
   if (p->fac_off.count(key)) return;
   FactorJob J{};
-  J.kind_a = ka == 0 ? 0 : 1;
-  J.kind_b = kb == 0 ? 0 : 1;
+  // family kinds of the kernel: 0 = cell integrals, 1 = points (collocation
+  // observes the PDE families at the cell centres, with their derivative order)
+  J.kind_a = (ka == 0 && !p->colloc) ? 0 : 1;
+  J.kind_b = (kb == 0 && !p->colloc) ? 0 : 1;
   J.ord_a = ka == 0 ? aa : (ka == 1 ? p->sets[aa].order[ax] : 0);
   J.ord_b = kb == 0 ? ab : (kb == 1 ? p->sets[ab].order[ax] : 0);
   J.n_a = (int)fam_n(p, ax, ka, aa);
@@ -1266,8 +1271,10 @@ struct TcBuild {
 // a few SMs.  Such ops split their segments into groups, one tile per
 // (row tile, group), as long as the level stays within about two resident
 // CTAs per SM; the groups' partial sums are added in order by tc_sum.
+static thread_local int g_tc_group_policy = 0;  // 0: split idle levels into groups, 1: never
+
 void tc_group_levels(gpfvm_problem* p, TcBuild& T, int inst) {
-  const i64 slots = 2 * 152;
+  const i64 slots = g_tc_group_policy == 1 ? 1 : 2 * 152;
   for (auto& L : p->tc_levels[inst]) {
     i64 rows = 0;
     for (int o = L.off; o < L.off + L.nops; ++o) rows += (T.ops[o].R + 127) / 128;
@@ -1504,6 +1511,7 @@ int validate(const gpfvm_desc* D) {
   if (D->n_sets < 0 || D->n_sets > GPFVM_MAX_SETS) return GPFVM_ERR_INVALID_ARG;
   if (!(D->outputscale > 0) || !(D->jitter >= 0) || !std::isfinite(D->outputscale) || !std::isfinite(D->jitter))
     return GPFVM_ERR_INVALID_ARG;
+  if (D->observe != 0 && D->observe != 1) return GPFVM_ERR_INVALID_ARG;
   i64 N = 1, P = 1;
   for (int i = 0; i < D->ndim; ++i) {
     if (D->n_cells[i] < 1 || D->n_cells[i] > 65536 || !D->edges[i]) return GPFVM_ERR_INVALID_ARG;
@@ -1593,6 +1601,10 @@ void alloc_all(gpfvm_problem* p) {
     p->off_pred[i] = (i64)coords.size();
     coords.insert(coords.end(), p->pred[i].begin(), p->pred[i].end());
   }
+  for (int i = 0; i < p->d; ++i) {  // cell centres (the collocation points)
+    p->off_mid[i] = (i64)coords.size();
+    for (int j = 0; j < p->nc[i]; ++j) coords.push_back(0.5 * (p->edges[i][j] + p->edges[i][j + 1]));
+  }
   p->d_coords = m.alloc<double>((i64)coords.size());
   GPFVM_CUDA(cudaMemcpy(p->d_coords, coords.data(), coords.size() * sizeof(double), cudaMemcpyHostToDevice));
   // factors
@@ -1605,7 +1617,7 @@ void alloc_all(gpfvm_problem* p) {
     for (auto& J : p->jobs)
       if ((i64)(intptr_t)J.out == key_off.second && (intptr_t)J.ca == ka * 1000 + aa && (intptr_t)J.cb == kb * 1000 + ab) {
         auto cptr = [&](int k, int a) -> const double* {
-          if (k == 0) return p->d_coords + p->off_edges[ax];
+          if (k == 0) return p->d_coords + (p->colloc ? p->off_mid[ax] : p->off_edges[ax]);
           if (k == 1) return p->d_coords + p->off_set[a][ax];
           return p->d_coords + p->off_pred[ax];
         };
@@ -1789,6 +1801,32 @@ void alloc_all(gpfvm_problem* p) {
   build_plans(p, B);
   build_plans32(p, B);
   finalize_plans(p);
+}
+
+// Rebuilds every plan under the given mode-product policies (same scratch:
+// intermediates do not depend on tile shapes); captured loops are dropped.
+void rebuild_plans(gpfvm_problem* p, int tile, int tc_group) {
+  set_tile_policy(tile);
+  g_tc_group_policy = tc_group;
+  try {
+    p->tc_jobs.clear();
+    Builder B{p};
+    B.scr.base = p->d_scratch;
+    B.scr.cap = p->scratch_cap;
+    build_plans(p, B);
+    build_plans32(p, B);
+    finalize_plans(p);
+  } catch (...) {
+    set_tile_policy(-1);
+    g_tc_group_policy = 0;
+    throw;
+  }
+  set_tile_policy(-1);
+  g_tc_group_policy = 0;
+  p->tuned_tile = tile;
+  p->tuned_tc = tc_group;
+  if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; p->graph_key = -1; }
+  if (p->graph32) { cudaGraphExecDestroy(p->graph32); p->graph32 = nullptr; p->graph32_key = -1; }
 }
 
 void copy_header_to_host(gpfvm_problem* p, cudaStream_t st) {
@@ -2182,7 +2220,7 @@ struct MixedRun {
   int kstore = 0;  // directions stored by the runs so far (conjugate continuation)
   int idle = 0;    // consecutive runs that took no iteration
   double tscale = 1.0;  // fraction of rtol the next run aims at
-  double rel = 1.0, itol = 1e-2;
+  double rel = 1.0, itol = 1e-2, rel_prev = 1.0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 std::map<const gpfvm_problem*, MixedRun>& mruns() {
@@ -2197,16 +2235,16 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   MixedRun& R = mruns()[p];
   R.o = *o;
   R.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
-  if (o->reorth && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
+  if (o->reorth < 0 || o->reorth > 2 || (o->reorth == 1 && o->max_iter > p->cap)) return GPFVM_ERR_INVALID_ARG;
   const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
   const int want_tc = o->precision == GPFVM_MIXED_TF32X3 ? TC_TF32X3
                       : o->precision == GPFVM_MIXED_BF16X3 ? TC_BF16X3
                       : o->precision == GPFVM_MIXED_BF16  ? TC_BF16
                                                           : -1;
   if (want_tc >= 0 && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
-  // without reorth one run's worth; with it the stores grow run by run
-  // (they keep the directions of every run: up to max_iter in total)
-  if (!o->reorth) ensure_store32(p, icap);
+  // one run's worth unless the runs continue one direction set (reorth 1),
+  // whose stores grow run by run (every run's directions: up to max_iter)
+  if (o->reorth != 1) ensure_store32(p, icap);
   if (want_tc != p->tc_mode) {  // the captured inner iteration depends on the operator
     p->tc_mode = want_tc;
     if (p->graph32) cudaGraphExecDestroy(p->graph32);
@@ -2230,6 +2268,7 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   R.kstore = 0;
   R.idle = 0;
   R.tscale = 1.0;
+  R.rel_prev = 1.0;
   R.status = GPFVM_NOT_CONVERGED;
   R.rel = 1.0;
   return GPFVM_OK;
@@ -2270,7 +2309,19 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     const double b2 = p->h_st->aux[1];
     R.rel = b2 > 0 ? std::sqrt(p->h_st->aux[0] / b2) : 0.0;
     if (!std::isfinite(R.rel)) { R.status = GPFVM_ERR_BREAKDOWN; R.mstate = 3; return; }
-    const bool cont = o->reorth != 0;  // conjugate continuation across runs
+    // divergence guard: a run that raised the FP64 residual tenfold (operator
+    // error times conditioning above one; CG residuals are not monotone, so
+    // smaller rises are left alone) is undone, and the solve stops with the
+    // previous iterate
+    if (R.outer > 0 && R.rel > 10.0 * R.rel_prev) {
+      add_f2d(p->d_x, p->f_d, N, st, &p->d_st32->aux[7], -1.0);
+      R.rel = R.rel_prev;
+      R.status = GPFVM_NOT_CONVERGED;
+      R.mstate = 3;
+      return;
+    }
+    R.rel_prev = R.rel;
+    const bool cont = o->reorth == 1;  // conjugate continuation across runs
     // The last run stops where its FP32 recurrence estimates rtol; the FP64
     // residual then confirms it within a factor 2 (the estimate's error), else
     // the next run aims at half the remaining distance.
@@ -2282,7 +2333,7 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     if (R.total >= o->max_iter || R.idle >= 3) { R.status = GPFVM_NOT_CONVERGED; R.mstate = 3; return; }
     if (R.outer > 0 && R.rel <= 2.0 * o->rtol) R.tscale *= 0.5;
     const bool var_now = o->want_var && (cont || R.outer == 0);
-    const bool reorth_now = cont;
+    const bool reorth_now = o->reorth != 0;  // 2: within each run only
     const int kbase = cont ? R.kstore : 0;
     const int run_cap = std::min(o->inner_max_iter > 0 ? o->inner_max_iter : p->cap, o->max_iter - R.total);
     if (cont) grow_store32(p, kbase + run_cap, kbase);
@@ -2319,7 +2370,7 @@ void mixed_poll(gpfvm_problem* p, cudaStream_t st) {
     count_launch((long long)p->h_st32->loops * p->graph32_kernels);
     const int k = p->h_st32->k - p->h_st32->kbase;  // iterations of this run
     R.total += k;
-    if (o->reorth) R.kstore = std::min(p->h_st32->k, p->cap32);
+    if (o->reorth == 1) R.kstore = std::min(p->h_st32->k, p->cap32);
     if (p->h_st32->pad[1] & DEV_TIMEOUT) { R.status = GPFVM_ERR_TIMEOUT; R.mstate = 3; return; }
     // a breakdown inside a run ends that run (its stored directions stay
     // conjugate: the failed direction is never stored); none at all is an error
@@ -2350,8 +2401,8 @@ int mixed_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   if (info) *info = I;
   p->solved = R.status >= 0;
   p->want_var_last = R.o.want_var != 0;
-  p->last_store = R.o.reorth ? 2 : 0;
-  p->last_kstore = R.o.reorth ? R.kstore : 0;
+  p->last_store = R.o.reorth == 1 ? 2 : 0;
+  p->last_kstore = R.o.reorth == 1 ? R.kstore : 0;
   return R.status;
 }
 
@@ -2425,6 +2476,7 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
   }
   p->s2 = D->outputscale;
   p->jitter = D->jitter;
+  p->colloc = D->observe == 1;
   p->nterms = D->n_terms;
   for (int k = 0; k < p->nterms; ++k) {
     p->coef[k] = D->coef[k];
@@ -2685,6 +2737,68 @@ int gpfvm_query(gpfvm_problem* p, double* mean, double* var, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return r;
+  GPFVM_GUARD_END
+}
+
+int gpfvm_autotune(gpfvm_problem* p, int precision, void* stream, double* report, int report_cap) {
+  if (!p || precision < GPFVM_FP64 || precision > GPFVM_MIXED_BF16) return GPFVM_ERR_INVALID_ARG;
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  static const int op_of[5] = {1, 6, 7, 9, 11};  // the solver's operator of each precision
+  const int op = op_of[precision];
+  const bool tc = precision >= GPFVM_MIXED_TF32X3;
+  if (tc && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  GPFVM_GUARD_BEGIN
+  cudaStream_t st = pick_stream(p, stream);
+  // cache key: precision, operator terms and the axis sizes rounded up to 16
+  auto up16 = [](int n) { return (n + 15) / 16 * 16; };
+  std::vector<int> key = {precision, p->d, p->nterms, p->M > 0, up16(p->nc[0]), p->d > 1 ? up16(p->nc[1]) : 1,
+                          p->d > 2 ? up16(p->nc[2]) : 1};
+  for (int a = 0; a < p->nterms; ++a)
+    for (int i = 0; i < p->d; ++i) key.push_back(p->alpha[a][i]);
+  static std::mutex mu;
+  static std::map<std::vector<int>, std::pair<int, int>> cache;
+  std::pair<int, int> best{-1, 0};
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) { best = it->second; hit = true; }
+  }
+  int nrep = 0;
+  if (!hit) {
+    double *v = nullptr, *out = nullptr;
+    GPFVM_CUDA(cudaMalloc(&v, sizeof(double) * p->N));
+    if (cudaMalloc(&out, sizeof(double) * p->N) != cudaSuccess) {
+      cudaFree(v);
+      return GPFVM_ERR_OUT_OF_MEMORY;
+    }
+    double best_ms = 1e300;
+    try {
+      GPFVM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * p->N, st));
+      for (int tcg = 0; tcg < (tc ? 2 : 1); ++tcg)
+        for (int tile = -1; tile <= 2; ++tile) {
+          rebuild_plans(p, tile, tcg);
+          double ms = 0.0;
+          const int r = gpfvm_gram_matvec_bench(p, op, v, out, 8, stream, &ms);
+          if (r != GPFVM_OK) throw CudaError{cudaErrorUnknown, "autotune timing"};
+          if (report && nrep < report_cap) report[nrep] = ms;
+          ++nrep;
+          if (ms < best_ms) { best_ms = ms; best = {tile, tcg}; }
+        }
+    } catch (...) {
+      cudaFree(v);
+      cudaFree(out);
+      rebuild_plans(p, -1, 0);
+      throw;
+    }
+    cudaFree(v);
+    cudaFree(out);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+  }
+  if (p->tuned_tile != best.first || p->tuned_tc != best.second) rebuild_plans(p, best.first, best.second);
+  if (report && nrep < report_cap) report[nrep] = 3 * (best.first + 1) + best.second;  // the choice
+  return hit ? 1 : 0;
   GPFVM_GUARD_END
 }
 
@@ -3053,6 +3167,7 @@ extern "C" int gpfvm_server_step(gpfvm_server* s) {
       const gpfvm_solve_opts& so = s->o.solve;
       const i64 ld = store_ld(p->N);
       if (so.precision == GPFVM_FP64) store = so.reorth ? 16LL * ld * std::min(so.max_iter, p->cap) : 0;
+      else if (so.reorth == 1) store = 8LL * ld * std::min(so.max_iter, p->cap);  // every run's directions
       else store = 8LL * ld * std::min(p->cap, so.inner_max_iter > 0 ? so.inner_max_iter : p->cap);
     }
     if (r == GPFVM_ERR_OUT_OF_MEMORY || (r == GPFVM_OK && s->used + p->mem.bytes + store > s->budget)) {

@@ -503,16 +503,17 @@ void loop_ctl(CGState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
   launch_pdl(k_loop_ctl, 1, 1, 0, s, st, h);
 }
 
-__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n, const double* scale) {
+__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, i64 n, const double* scale,
+                          double sign) {
   pdl_wait();
-  const double a = scale ? *scale : 1.0;
+  const double a = sign * (scale ? *scale : 1.0);
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] = fma(a, (double)d[i], x[i]);
 }
-void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale) {
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale, double sign) {
   if (n <= 0) return;
   int g = ceil_div(n, RT);
   if (g > 4096) g = 4096;
-  launch_pdl(k_add_f2d, g, RT, 0, s, x, d, n, scale);
+  launch_pdl(k_add_f2d, g, RT, 0, s, x, d, n, scale, sign);
 }
 
 __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, i64 n) {

@@ -53,11 +53,11 @@ void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double
 template <typename T>
 void cg_project(const T* S, const T* Q, T* r, T* d, T* p, i64 n, int cap, CGState* st, double* part2,
                 double* coef, const double* eta_hist, cudaStream_t s);
-// x += (*scale) d  (scale defaults to 1)
 // Control node of a device-side CG loop (a graph WHILE node): one more pass
 // while the CG state is not done, and never more than max_iter + 2 passes.
 void loop_ctl(CGState* st, cudaGraphConditionalHandle h, cudaStream_t s);
-void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale = nullptr);
+// x += sign * (*scale) d  (scale defaults to 1)
+void add_f2d(double* x, const float* d, i64 n, cudaStream_t s, const double* scale = nullptr, double sign = 1.0);
 void f2d(const float* a, double* b, i64 n, cudaStream_t s);
 void axpby(const double* a, const double* b, double* out, double sa, double sb, i64 n, cudaStream_t s);
 void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s);

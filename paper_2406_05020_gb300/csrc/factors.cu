@@ -9,6 +9,8 @@
 //   k    = (1 + z + z^2/3) e^-z
 //   k'   = -sgn(r) s z (1 + z)/3 e^-z
 //   k''  = -s^2 (1 + z - z^2)/3 e^-z
+//   k''' = sgn(r) s^3 z (3 - z)/3 e^-z       (collocation of second-order operators only)
+//   k''''= s^4 (3 - 5z + z^2)/3 e^-z
 //   s K1 = sgn(r) [8/3 - (8/3 + 5z/3 + z^2/3) e^-z]
 //   s^2 K2 = 8z/3 - 5 + (5 + 7z/3 + z^2/3) e^-z
 // Evaluation rules that keep every entry accurate relative to its own size:
@@ -75,7 +77,9 @@ __device__ double factor_entry(const FactorJob& J, int i, int j) {
         double kv;
         if (order == 0) kv = (1.0 + z + z * z * (1.0 / 3.0)) * e;
         else if (order == 1) kv = -sgnd(r) * s * z * (1.0 + z) * (1.0 / 3.0) * e;
-        else kv = -s * s * (1.0 + z - z * z) * (1.0 / 3.0) * e;
+        else if (order == 2) kv = -s * s * (1.0 + z - z * z) * (1.0 / 3.0) * e;
+        else if (order == 3) kv = sgnd(r) * s * s * s * z * (3.0 - z) * (1.0 / 3.0) * e;
+        else kv = s * s * s * s * (3.0 - 5.0 * z + z * z) * (1.0 / 3.0) * e;
         acc += wa[a] * wb[b] * sign_n * kv;
       }
     return acc;

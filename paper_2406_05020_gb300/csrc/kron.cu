@@ -18,7 +18,12 @@
 
 namespace gpfvm {
 
+static thread_local int g_tile_policy = -1;
+void set_tile_policy(int policy) { g_tile_policy = (policy >= 0 && policy <= 2) ? policy : -1; }
+int tile_policy() { return g_tile_policy; }
+
 static int pick_tile(int m, i64 ctas_per_rowtile) {
+  if (g_tile_policy >= 0) return g_tile_policy;
   // row tile 64/32/16: avoid padding waste for short factors, and keep at
   // least two waves of CTAs on the 152 SMs when the output is small
   if (m <= 16) return 2;

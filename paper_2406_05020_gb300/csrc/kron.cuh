@@ -39,4 +39,10 @@ void plan_kron(Plan& plan, Scratch& scratch, int d, const int* din, const int* d
                const std::vector<KTerm>& terms, double scale, const double* in, double* out, double beta,
                const double* D, double gamma, int* n_modeprods, bool f32 = false);
 
+// Row-tile policy of the mode-product GEMMs built by plan_kron on this host
+// thread: -1 = the size heuristic (default), 0/1/2 = always 64/32/16 rows
+// (the autotuner's candidates).
+void set_tile_policy(int policy);
+int tile_policy();
+
 }  // namespace gpfvm

@@ -47,7 +47,7 @@ class Desc(C.Structure):
                 ("alpha", (C.c_int * MAX_DIM) * MAX_TERMS), ("coef", C.c_double * MAX_TERMS),
                 ("rhs", C.POINTER(C.c_double)), ("jitter", C.c_double), ("n_sets", C.c_int),
                 ("sets", PointSet * MAX_SETS), ("n_pred", C.c_int * MAX_DIM),
-                ("pred", C.POINTER(C.c_double) * MAX_DIM)]
+                ("pred", C.POINTER(C.c_double) * MAX_DIM), ("observe", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -94,6 +94,7 @@ SIGNATURES = {
     "gpfvm_server_destroy": (None, [P]),
     "gpfvm_set_values": (C.c_int, [P, P, P]),
     "gpfvm_target": (C.c_int, [P, P, C.c_int, P]),
+    "gpfvm_autotune": (C.c_int, [P, C.c_int, P, D, C.c_int]),
     "gpfvm_launch_count": (C.c_int64, []),
     "gpfvm_kron_matvec_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_void_p), D,
                                             C.c_double, C.c_double, P, P, P]),
@@ -183,6 +184,7 @@ def make_desc(prob):
             d.alpha[k][i] = int(alpha[i])
         d.coef[k] = float(c)
     d.rhs = arr(np.ravel(prob.rhs)) if prob.rhs is not None else None
+    d.observe = 1 if getattr(prob, "observe", "fvm") == "collocation" else 0
     d.jitter = float(prob.jitter)
     if len(prob.sets) > MAX_SETS:
         raise ValueError("too many point sets")
@@ -273,6 +275,16 @@ class Problem:
         if var is not None:
             _disjoint(mean, var, "query")
         return _check(lib().gpfvm_query(self.h, pm, pv, _stream(stream)), "gpfvm_query")
+
+    def autotune(self, precision: int, stream=None):
+        """Picks the fastest mode-product plan policy for this problem's operator
+        (cached per size class; see gpfvm_autotune).  Returns (cached, ms per
+        timed candidate, choice)."""
+        rep = np.full(16, np.nan)
+        code = _check(lib().gpfvm_autotune(self.h, int(precision), _stream(stream), _dptr(rep), rep.size),
+                      "gpfvm_autotune")
+        vals = rep[~np.isnan(rep)]
+        return bool(code == 1), list(vals[:-1]), int(vals[-1]) if vals.size else None
 
     def target(self, betas, stream=None):
         """Targeted uncertainty reduction: one IterGP action per row of betas

@@ -47,7 +47,20 @@ PROBS = {
     "wave2d": lambda: W.wave_2d(6, 9, 5, n_ic=(4, 4), n_bc=(2, 2), pred=(3, 3, 3), ell=(0.3, 0.3, 0.3)),
     "toy1d": lambda: W.toy_cos(9),
     "tiny222": lambda: W.heat_2d(2, 2, 2, n_ic=(2, 2), n_bc=(1, 1), pred=(2, 2, 2), ell=(0.5, 0.5, 0.5)),
+    # collocation observations (the PDE at the cell centres): point factors with
+    # kernel derivatives up to order 4
+    "heat1d_colloc": lambda: W.collocation(W.heat_1d(5, 7, n_ic=6, n_bc=4, pred=6)),
+    "heat2d_colloc": lambda: W.collocation(W.heat_2d(5, 7, 9, n_ic=(4, 3), n_bc=(2, 3), pred=(3, 2, 4),
+                                                     ell=(0.4, 0.3, 0.35))),
+    "wave2d_colloc": lambda: W.collocation(W.wave_2d(6, 9, 5, n_ic=(4, 4), n_bc=(2, 2), pred=(3, 3, 3),
+                                                     ell=(0.3, 0.3, 0.3))),
+    "toy1d_colloc": lambda: W.toy_cos(9, observe="collocation"),
 }
+
+
+def _arg(fam):
+    """The derivative order of a 1D family (cell or point) as gpfvm_factor takes it."""
+    return fam[3] if fam[0] == "cell" else fam[2]
 
 
 @pytest.mark.parametrize("name", list(PROBS))
@@ -61,14 +74,14 @@ def test_factors_match_oracle(name):
         for c2, G in pde.terms:
             for i in range(d):
                 ref = O.cov_1d(F[i], G[i], prob.lengthscale[i])
-                got = pb.factor(i, 0, F[i][3], 0, G[i][3], ref.shape)
+                got = pb.factor(i, 0, _arg(F[i]), 0, _arg(G[i]), ref.shape)
                 np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
     for s, sb in enumerate(K.sets):
         (_, G), = sb.terms
         for c1, F in pde.terms:
             for i in range(d):
                 ref = O.cov_1d(F[i], G[i], prob.lengthscale[i])
-                got = pb.factor(i, 0, F[i][3], 1, s, ref.shape)
+                got = pb.factor(i, 0, _arg(F[i]), 1, s, ref.shape)
                 np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
     pb.close()
 
@@ -100,7 +113,8 @@ def test_gbb_and_operators_match_oracle(name):
     pb.close()
 
 
-@pytest.mark.parametrize("name", ["heat1d", "heat2d_ragged", "wave2d", "toy1d", "tiny222"])
+@pytest.mark.parametrize("name", ["heat1d", "heat2d_ragged", "wave2d", "toy1d", "tiny222", "heat1d_colloc",
+                                  "heat2d_colloc", "wave2d_colloc", "toy1d_colloc"])
 def test_fixed_iterations_match_oracle(name):
     """The same recurrence for a fixed number of iterations: iterate, IterGP
     downdate and posterior agree with the oracle's CG."""
@@ -125,7 +139,8 @@ def test_fixed_iterations_match_oracle(name):
     pb.close()
 
 
-@pytest.mark.parametrize("name", ["heat1d", "heat2d_ragged", "wave2d", "toy1d"])
+@pytest.mark.parametrize("name", ["heat1d", "heat2d_ragged", "wave2d", "toy1d", "heat1d_colloc", "heat2d_colloc",
+                                  "wave2d_colloc", "toy1d_colloc"])
 def test_converged_posterior_matches_dense_cholesky(name):
     prob = PROBS[name]()
     pb = _gpu(prob)
@@ -136,7 +151,10 @@ def test_converged_posterior_matches_dense_cholesky(name):
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
     var = torch.empty_like(mean)
     pb.query(mean, var)
-    assert relerr(mean.cpu().numpy(), m) < 1e-8
+    # both sides solve the same FP64 system: 1e-10, except the Fig. 2 toys,
+    # whose jitter 1e-10 gives cond(G) ~ 8e9 (the dense oracle's own error
+    # is eps * cond ~ 1e-6 there)
+    assert relerr(mean.cpu().numpy(), m) < (1e-7 if name.startswith("toy1d") else RTOL)
     # the IterGP variance never drops below the exact one beyond rounding:
     # eps * cond(G^) (cond ~ 8e9 for the Fig. 2 toy with jitter 1e-10)
     tol = 1e-7 if name == "toy1d" else 1e-9
@@ -156,8 +174,8 @@ def test_c1_heat_1d_full_config():
     mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
     var = torch.empty_like(mean)
     pb.query(mean, var)
-    assert relerr(mean.cpu().numpy(), m) < 1e-9
-    assert relerr(mean.cpu().numpy(), r["mean"]) < 1e-9
+    assert relerr(mean.cpu().numpy(), m) < RTOL
+    assert relerr(mean.cpu().numpy(), r["mean"]) < RTOL
     assert np.all(var.cpu().numpy() >= v - 1e-9)
     pb.close()
 
