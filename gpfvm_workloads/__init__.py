@@ -68,6 +68,10 @@ class Problem:
     # "fvm": one volume integral of the PDE per cell; "collocation": the PDE
     # evaluated at each cell centre (rhs then holds point values of the forcing)
     observe: str = "fvm"
+    # per term: None (constant coefficient) or one value per cell (row-major
+    # over n_cells) multiplying the term's coefficient -- a piecewise-constant
+    # variable coefficient such as a bathymetry-dependent wave speed
+    fields: Optional[List[Optional[np.ndarray]]] = None
 
     @property
     def ndim(self) -> int:
@@ -250,6 +254,47 @@ def collocation(prob: Problem) -> Problem:
         raise ValueError("only homogeneous problems: give point values of the forcing instead")
     from dataclasses import replace
     return replace(prob, observe="collocation", name=prob.name + "_colloc")
+
+
+def heat_1d_varcoef(nt: int = 16, nx: int = 32, pred: int = 33, ell=(0.3, 0.2), jitter: float = 1e-10) -> Problem:
+    """1D+time heat u_t = nu(x) u_xx with nu piecewise constant per cell
+    (nu = 0.05 (1 + x) at the cell centre), built so that
+    u*(t, x) = exp(-t) sin(pi x) satisfies every volume observation exactly:
+    the right-hand side of cell [t0,t1] x [x0,x1] is
+    (nu_V pi^2 - 1) (e^-t0 - e^-t1) (cos pi x0 - cos pi x1) / pi.
+    IC u(0, x) = sin(pi x) on nx + 1 points, zero walls at x = 0, 1."""
+    te, xe = uniform_edges(0, 1, nt), uniform_edges(0, 1, nx)
+    xc = 0.5 * (xe[1:] + xe[:-1])
+    nu = 0.05 * (1.0 + xc)
+    field = np.tile(nu, (nt, 1))
+    It = np.exp(-te[:-1]) - np.exp(-te[1:])
+    Ix = (np.cos(np.pi * xe[:-1]) - np.cos(np.pi * xe[1:])) / np.pi
+    rhs = (field * np.pi ** 2 - 1.0) * np.outer(It, Ix)
+    xs = np.linspace(0, 1, nx + 1)
+    ic = PointSet((0, 0), [np.array([0.0]), xs], np.sin(np.pi * xs), jitter, "ic")
+    tb = np.linspace(0, 1, nt + 1)[1:]
+    bc = PointSet((0, 0), [tb, np.array([0.0, 1.0])], np.zeros(2 * nt), jitter, "bc_x")
+    terms = [((1, 0), 1.0), ((0, 2), -1.0)]
+    grid = [np.linspace(0, 1, pred), np.linspace(0, 1, pred)]
+    return Problem([te, xe], tuple(ell), 1.0, terms, jitter, [ic, bc], grid, rhs=rhs.ravel(),
+                   name=f"heat1d_varcoef_{nt}x{nx}", fields=[None, field.ravel()])
+
+
+def heat_2d_varcoef(nt: int = 16, nx: int = 20, ny: int = 24, seed: int = 0, **kw) -> Problem:
+    """The 2D+time heat problem of heat_2d with a piecewise-constant diffusivity
+    nu(x, y) = 0.02 + 0.08 * (seeded Gaussian bump) per cell (a synthetic
+    stand-in for a depth-dependent coefficient), shared by both second-order terms."""
+    p = heat_2d(nt, nx, ny, seed=seed, **kw)
+    rng = np.random.default_rng(seed + 7)
+    xe, ye = p.edges[1], p.edges[2]
+    X, Y = np.meshgrid(0.5 * (xe[1:] + xe[:-1]), 0.5 * (ye[1:] + ye[:-1]), indexing="ij")
+    cx, cy = rng.uniform(0.3, 0.7, 2)
+    nu = 0.02 + 0.08 * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.2 ** 2))
+    field = np.broadcast_to(nu, (nt, nx, ny)).ravel().copy()
+    p.terms = [((1, 0, 0), 1.0), ((0, 2, 0), -1.0), ((0, 0, 2), -1.0)]
+    p.fields = [None, field, field]
+    p.name = p.name + "_varcoef"
+    return p
 
 
 def batch_heat(n_problems: int = 256, lo: int = 16, hi: int = 64, seed: int = 0,

@@ -173,7 +173,9 @@ class Block:
 
     Every functional of the block is indexed by a multi-index over ``shape``
     (row-major); term t contributes c_t times the product over axes of the
-    1D functional family F_{t,i} evaluated at that index."""
+    1D functional family F_{t,i} evaluated at that index.  c_t is a scalar or,
+    for a piecewise-constant variable coefficient (one value per functional,
+    App. C.4 "Variable bathymetry"), an array over the block."""
 
     def __init__(self, shape: Sequence[int], terms: List[Tuple[float, list]], name: str = ""):
         self.shape = tuple(int(n) for n in shape)
@@ -193,12 +195,15 @@ def pde_block(prob) -> Block:
     sum_alpha c_alpha D^alpha u (x_V), point families of order alpha_i."""
     terms = []
     colloc = getattr(prob, "observe", "fvm") == "collocation"
-    for alpha, c in prob.terms:
+    fields = getattr(prob, "fields", None)
+    for k, (alpha, c) in enumerate(prob.terms):
+        if fields is not None and fields[k] is not None:
+            c = float(c) * np.asarray(fields[k], np.float64).ravel()
         if colloc:
             fams = [point_family(0.5 * (e[:-1] + e[1:]), a) for e, a in zip(prob.edges, alpha)]
         else:
             fams = [cell_family(e[:-1], e[1:], a) for e, a in zip(prob.edges, alpha)]
-        terms.append((float(c), fams))
+        terms.append((c if isinstance(c, np.ndarray) else float(c), fams))
     return Block(prob.n_cells, terms, "pde")
 
 
@@ -221,7 +226,9 @@ def block_cov(X: Block, Y: Block, ell: Sequence[float], outputscale: float) -> n
     out = np.zeros((X.size, Y.size))
     for c1, F in X.terms:
         for c2, G in Y.terms:
-            prod = np.full((X.size, Y.size), c1 * c2)
+            # a variable coefficient makes the term pair a Hadamard product with
+            # the rank-one matrix c1 c2^T (App. C.4)
+            prod = np.outer(np.broadcast_to(c1, (X.size,)), np.broadcast_to(c2, (Y.size,))).copy()
             for ax in range(len(X.shape)):
                 C = cov_1d(F[ax], G[ax], ell[ax])
                 prod *= C[I[ax][:, None], J[ax][None, :]]
@@ -296,7 +303,10 @@ class KronIBVP:
     G_PP = sum_{a,b} c_a c_b (x)_i A_i^{a_i b_i}   (Eq. kronecker-structure)
     with A_i^{pq} = L_{G_i;p} k^(i) L'_{G_i;q}, evaluated naively pair by pair
     (no sharing of mode products); point-set blocks are Kronecker products of
-    rectangular 1D factors; G_BB is assembled densely entrywise."""
+    rectangular 1D factors; G_BB is assembled densely entrywise.  A
+    piecewise-constant variable coefficient c_a (one value per cell) turns
+    each Kronecker term into its Hadamard product with the rank-one matrix
+    c_a c_b^T (App. C.4), applied as diag(c_a) (x)A diag(c_b)."""
 
     def __init__(self, prob):
         self.prob = prob
@@ -307,11 +317,11 @@ class KronIBVP:
         self.pred = pred_block(prob)
         self.shape = prob.n_cells
         d = prob.ndim
-        # PDE x PDE pairs
+        # PDE x PDE pairs (coefficients kept apart: scalars or per-cell arrays)
         self.pp = []
         for c1, F in self.pde.terms:
             for c2, G in self.pde.terms:
-                self.pp.append((c1 * c2, [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)]))
+                self.pp.append(((c1, c2), [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)]))
         # PDE x set s (N_i x n_{s,i} factors per term)
         self.pb = []
         for sb in self.sets:
@@ -342,11 +352,15 @@ class KronIBVP:
         self.offsets = np.cumsum([0] + [s.size for s in self.sets])
 
     # --- blocks -------------------------------------------------------------
+    def _cells(self, c):
+        """A term coefficient as a scalar or a tensor over the cells."""
+        return c.reshape(self.shape) if isinstance(c, np.ndarray) else c
+
     def Gpp(self, v: np.ndarray) -> np.ndarray:
         V = v.reshape(self.shape)
         out = np.zeros(self.shape)
-        for c, mats in self.pp:
-            out += c * mode_apply(mats, V)
+        for (c1, c2), mats in self.pp:
+            out += self._cells(c1) * mode_apply(mats, self._cells(c2) * V)
         return self.s2 * out.ravel() + self.prob.jitter * v
 
     def Gbp(self, v: np.ndarray) -> np.ndarray:
@@ -356,7 +370,7 @@ class KronIBVP:
         for sb, terms in zip(self.sets, self.pb):
             acc = np.zeros(sb.shape)
             for c, mats in terms:
-                acc += c * mode_apply([A.T for A in mats], V)
+                acc += mode_apply([A.T for A in mats], self._cells(c) * V)
             parts.append(self.s2 * acc.ravel())
         return np.concatenate(parts) if parts else np.zeros(0)
 
@@ -366,7 +380,7 @@ class KronIBVP:
         for k, (sb, terms) in enumerate(zip(self.sets, self.pb)):
             W = w[self.offsets[k]:self.offsets[k + 1]].reshape(sb.shape)
             for c, mats in terms:
-                out += c * mode_apply(mats, W)
+                out += self._cells(c) * mode_apply(mats, W)
         return self.s2 * out.ravel()
 
     def Hsolve(self, w: np.ndarray) -> np.ndarray:
@@ -391,7 +405,7 @@ class KronIBVP:
         X = x.reshape(self.shape)
         out = np.zeros(self.pred.shape)
         for c, mats in self.pp_pred:
-            out += c * mode_apply([A.T for A in mats], X)
+            out += mode_apply([A.T for A in mats], self._cells(c) * X)
         return self.s2 * out.ravel()
 
     def KBx(self, w: np.ndarray) -> np.ndarray:
@@ -407,7 +421,7 @@ class KronIBVP:
         B = beta.reshape(self.pred.shape)
         out = np.zeros(self.shape)
         for c, mats in self.pp_pred:
-            out += c * mode_apply(mats, B)
+            out += self._cells(c) * mode_apply(mats, B)
         return self.s2 * out.ravel()
 
     def KBxT(self, beta: np.ndarray) -> np.ndarray:
@@ -602,6 +616,9 @@ PINS = {
                                                     "quadrature of the Matern spectral density; collocation "
                                                     "posteriors of the Fig. 2 toy and the 1D heat equation "
                                                     "converge to the analytic solutions",
+    "variable coefficients (pde_block / block_cov / KronIBVP)": "Kronecker-with-diagonals == entrywise dense "
+                                                                "blocks; constant fields == scalar coefficients; "
+                                                                "manufactured variable-coefficient heat solution",
     "KPxT/KBxT/Lhat_k": "adjoint identities against KPx/KBx; entrywise dense cross-covariances (block_cov)",
     "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
                                       "on one point is the Cauchy-Schwarz-optimal single-action reduction; "
