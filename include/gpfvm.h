@@ -103,7 +103,15 @@ typedef struct {
  *                  1: collocation (Sec. 3, the operator D[u](x)): the PDE at
  *                  the centre of every cell, rhs then holding point values of
  *                  the forcing; the same Kronecker structure with point
- *                  factors (kernel derivatives up to order 4). */
+ *                  factors (kernel derivatives up to order 4).
+ *   coef_field     per term NULL (constant coefficient) or N values, one per
+ *                  cell row-major, multiplying coef[k]: a piecewise-constant
+ *                  variable coefficient (App. C.4, variable bathymetry).
+ *                  Every Kronecker term of the Gram matrix then becomes its
+ *                  Hadamard product with the rank-one matrix of the two terms'
+ *                  coefficients, applied as diagonal scalings.  Terms passing
+ *                  the same pointer share one field.  Such problems run the
+ *                  FP64 and FP32 SIMT operators (no tensor-core precisions). */
 typedef struct {
   int ndim;
   int n_cells[GPFVM_MAX_DIM];
@@ -120,6 +128,7 @@ typedef struct {
   int n_pred[GPFVM_MAX_DIM];
   const double* pred[GPFVM_MAX_DIM];
   int observe;
+  const double* coef_field[GPFVM_MAX_TERMS];
 } gpfvm_desc;
 
 /* Precision of the CG iteration. */
@@ -323,6 +332,21 @@ int64_t gpfvm_factor(gpfvm_problem* p, int axis, int kind_a, int arg_a, int kind
  * ------------------------------------------------------------------------ */
 int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts,
                       gpfvm_solve_info* infos, void* stream);
+
+/* The same batch as ONE graph launch: every problem's whole solve is a
+ * device-driven loop (a WHILE node whose body computes the FP64 residual,
+ * takes the refinement decision on the device, runs the inner CG as a nested
+ * WHILE node and applies the correction; an FP64 problem's body is its CG
+ * iteration), all problems' loops are independent branches of one graph, and
+ * the host only sets them up before and reads their states after.  Results
+ * equal gpfvm_solve_batch's (the same kernels and decisions).  The direction
+ * stores cannot grow inside a graph, so they are allocated up front: for
+ * every run (up to max_iter directions) with reorth 1, for one run
+ * (inner_max_iter) with reorth 0 or 2 -- use reorth 2 when max_iter directions
+ * of every problem do not fit.  *launches_out (may be NULL) receives the
+ * kernels executed.  Problems must be distinct. */
+int gpfvm_solve_batch_graph(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts, gpfvm_solve_info* infos,
+                            void* stream, int64_t* launches_out);
 
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching loop.  Requests are admitted into slots as

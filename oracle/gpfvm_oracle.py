@@ -588,6 +588,80 @@ def targeted_itergp(K: KronIBVP, max_iter: int, rtol: float, betas, want_var: bo
     return x, down, actions, dirs
 
 
+def restriction(shape, factor: int) -> np.ndarray:
+    """W (N x N_c): column c is the indicator of the fine cells inside coarse
+    cell c, the axes coarsened by `factor` (each axis size divisible by it).
+    A coarse volume is the disjoint union of its fine volumes, so its FVM
+    observation is the sum of theirs (appendix "Multigrid preconditioners",
+    Eq. subdomain-partition): y_coarse = W^T y_fine."""
+    shape = tuple(int(n) for n in shape)
+    cshape = tuple(n // factor for n in shape)
+    if any(n % factor for n in shape):
+        raise ValueError("axis sizes must be divisible by the coarsening factor")
+    fine = np.indices(shape).reshape(len(shape), -1) // factor
+    cidx = np.ravel_multi_index(tuple(fine), cshape)
+    W = np.zeros((int(np.prod(shape)), int(np.prod(cshape))))
+    W[np.arange(W.shape[0]), cidx] = 1.0
+    return W
+
+
+def multigrid_itergp(K: KronIBVP, factor: int, max_iter: int, rtol: float = 0.0, want_var: bool = True):
+    """Multigrid warm start (appendix "Multigrid preconditioners"): the
+    IC/BC-conditioned prior is conditioned further, exactly, on the coarse FVM
+    observations W^T y (by a Cholesky factorisation), and IterGP continues with
+    CG actions on the fine observations.
+      A_c = W^T G^ W = L_c L_c^T                 (the coarse observations' Gram)
+      x0  = W A_c^-1 W^T b,  r0 = b - G^ x0      (exact solve on the coarse scheme)
+      down0 = diag(U^T A_c^-1 U),  U = Lhat k(X*)^T W
+    then CG from r0 whose every direction is made G^-conjugate to span W
+    (p <- p - W A_c^-1 (G^ W)^T p) and to the earlier directions (Sec. 7), with
+    the downdate of each CG action added to down0.
+    Returns (x, down, CG iterations, W, directions as (p, eta) pairs)."""
+    W = restriction(K.shape, factor)
+    b = K.rhs_hat()
+    GW = np.column_stack([K.Ghat(W[:, c]) for c in range(W.shape[1])])
+    Ac = W.T @ GW
+    Lc = sla.cholesky(0.5 * (Ac + Ac.T), lower=True)
+    x = W @ sla.cho_solve((Lc, True), W.T @ b)
+    r = b - K.Ghat(x)
+    down = np.zeros(K.pred.size)
+    if want_var:
+        U = np.column_stack([K.KPx(W[:, c]) - K.KBx(K.Hsolve(K.Gbp(W[:, c]))) for c in range(W.shape[1])])
+        Z = sla.solve_triangular(Lc, U.T, lower=True)
+        down = np.sum(Z * Z, axis=0)
+
+    def deflate(v):
+        return v - W @ sla.cho_solve((Lc, True), GW.T @ v)
+
+    p = deflate(r.copy())
+    rr = float(r @ r)
+    bnorm = math.sqrt(float(b @ b))
+    S, Q, E, dirs = [], [], [], []
+    it = 0
+    while it < max_iter and bnorm > 0 and math.sqrt(rr) > rtol * bnorm:
+        q = K.Ghat(p)
+        eta = float(p @ q)
+        if not eta > 0:
+            raise FloatingPointError("CG breakdown: p^T G p <= 0")
+        if want_var:
+            u = K.KPx(p) - K.KBx(K.Hsolve(K.Gbp(p)))
+            down += u * u / eta
+        a = float(p @ r) / eta
+        x += a * p
+        r -= a * q
+        rr_new = float(r @ r)
+        S.append(p)
+        Q.append(q)
+        E.append(eta)
+        dirs.append((p.copy(), eta))
+        p = deflate(r + (rr_new / rr) * p)
+        c = (np.array(Q) @ p) / np.array(E)
+        p = p - np.array(S).T @ c
+        rr = rr_new
+        it += 1
+    return x, down, it, W, dirs
+
+
 def posterior_from(K: KronIBVP, x: np.ndarray, down: np.ndarray):
     """Posterior mean and IterGP variance on the prediction grid from the
     representer weights x and the downdate (Eqs. lin-cond-mean, lin-cond-cov)."""
@@ -619,6 +693,9 @@ PINS = {
     "variable coefficients (pde_block / block_cov / KronIBVP)": "Kronecker-with-diagonals == entrywise dense "
                                                                 "blocks; constant fields == scalar coefficients; "
                                                                 "manufactured variable-coefficient heat solution",
+    "restriction/multigrid_itergp": "equals itergp_actions on [W | CG directions]; with no CG step it is the "
+                                    "dense posterior of the same IBVP on the coarse cells; converged, the dense "
+                                    "fine posterior",
     "KPxT/KBxT/Lhat_k": "adjoint identities against KPx/KBx; entrywise dense cross-covariances (block_cov)",
     "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
                                       "on one point is the Cauchy-Schwarz-optimal single-action reduction; "

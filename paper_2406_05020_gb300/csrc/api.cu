@@ -162,6 +162,11 @@ void check_plan_ranges(const Plan& plan, const DevBuf& mem, const char* name) {
 }
 
 int map_error(const CudaError& e) {
+  static const bool trace = [] {
+    const char* v = getenv("GPFVM_DEBUG");
+    return v && std::atoi(v) != 0;
+  }();
+  if (trace) fprintf(stderr, "gpfvm: %s failed: %s\n", e.where ? e.where : "?", cudaGetErrorString(e.err));
   if (e.err == cudaErrorMemoryAllocation) return GPFVM_ERR_OUT_OF_MEMORY;
   if (e.err == cudaErrorInvalidValue) return GPFVM_ERR_INVALID_ARG;
   return GPFVM_ERR_DEVICE;
@@ -185,6 +190,13 @@ struct gpfvm_problem {
   int npred[3] = {1, 1, 1};
   std::vector<double> pred[3];
   bool colloc = false;  // PDE observed at the cell centres (collocation) instead of cell integrals
+  // variable coefficients: term a's coefficient is coef[a] * field[fclass[a]] per cell (fclass -1:
+  // constant); the distinct fields live in d_field / f_field (nfield x N)
+  int nfield = 0;
+  int fclass[GPFVM_MAX_TERMS] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  std::vector<double> fields;
+  double* d_field = nullptr;
+  float* f_field = nullptr;
   i64 N = 0, M = 0, P = 0;
   int cap = 0;
 
@@ -259,9 +271,12 @@ struct gpfvm_problem {
   int vb_rows = 0;
   CGState* d_st = nullptr;
   CGState* h_st = nullptr;  // pinned mirror of the scalar header
+  MixedCtl* d_mctl = nullptr;  // device-driven refinement state (batch graph)
+  MixedCtl* h_mctl = nullptr;  // its pinned mirror
 
   // ---- plans
   Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB, p_tgt;
+  Plan p_res;  // G^ x for the FP64 residual of the device-driven refinement (skipped on its first pass)
   Plan p_op[4];
   Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32;
   Plan p_mv32tc[3], p_mvv32tc[3], p_pp32tc[3];  // per TcMode
@@ -292,6 +307,7 @@ struct gpfvm_problem {
     if (graph32) cudaGraphExecDestroy(graph32);
     if (h_st) cudaFreeHost(h_st);
     if (h_st32) cudaFreeHost(h_st32);
+    if (h_mctl) cudaFreeHost(h_mctl);
     if (d_S) cudaFree(d_S);
     if (d_Q) cudaFree(d_Q);
     if (f_S) cudaFree(f_S);
@@ -411,6 +427,35 @@ std::vector<KTerm> predb_terms(const gpfvm_problem* p, int s, bool fold = false)
   return {t};
 }
 
+// ---- variable coefficients: terms grouped by field class (-1 = constant)
+std::vector<int> field_classes(const gpfvm_problem* p) {
+  std::vector<int> c;
+  for (int a = 0; a < p->nterms; ++a)
+    if (std::find(c.begin(), c.end(), p->fclass[a]) == c.end()) c.push_back(p->fclass[a]);
+  std::sort(c.begin(), c.end());
+  return c;
+}
+template <typename F>
+std::vector<KTerm> class_terms(const std::vector<KTerm>& all, const gpfvm_problem* p, int cls, F term_of) {
+  std::vector<KTerm> out;
+  for (size_t t = 0; t < all.size(); ++t)
+    if (p->fclass[term_of(t)] == cls) out.push_back(all[t]);
+  return out;
+}
+// G_PP pairs (a, b) with field classes (P, Q)
+std::vector<KTerm> pp_terms_pq(const gpfvm_problem* p, int P, int Q) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b) {
+      if (p->fclass[a] != P || p->fclass[b] != Q) continue;
+      KTerm t{};
+      t.c = p->coef[a] * p->coef[b];
+      for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 0, p->alpha[b][i], false);
+      ts.push_back(t);
+    }
+  return ts;
+}
+
 std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s, bool fold = false) {
   const bool q = fold && s == 0 && p->sicbc;
   KTerm t{};
@@ -454,10 +499,134 @@ struct Builder {
     peak = std::max(peak, scr.used);
   }
 
+  // ---- variable coefficients (App. C.4): a term's cell-side factor carries
+  // diag(f_a); products are grouped by field class and combined elementwise
+  bool varcoef() const { return p->nfield > 0; }
+  const void* field_ptr(int cls) const {
+    if (cls < 0) return nullptr;
+    return f32 ? (const void*)(p->f_field + (i64)cls * p->N) : (const void*)(p->d_field + (i64)cls * p->N);
+  }
+  void combine(Plan& plan, double* out, const std::vector<std::pair<const double*, int>>& ys, double scale,
+               const double* D, double gamma, double beta) {
+    FieldTerms t{};
+    t.nt = (int)ys.size();
+    if (t.nt > FIELD_MAXT) throw CudaError{cudaErrorInvalidValue, "too many field classes"};
+    for (int k = 0; k < t.nt; ++k) {
+      t.y[k] = ys[k].first;
+      t.f[k] = field_ptr(ys[k].second);
+      t.scale[k] = scale;
+    }
+    const bool F = f32;
+    const i64 n = p->N;
+    plan.func([=](cudaStream_t st) { field_combine(out, n, t, D, gamma, beta, F, st); });
+  }
+  // w_Q = f_Q .* in for every class (the constant class reads in itself)
+  std::vector<const double*> vc_inputs(Plan& plan, const double* in, const std::vector<int>& cls) {
+    std::vector<const double*> w;
+    for (int c : cls) {
+      if (c < 0) { w.push_back(in); continue; }
+      double* x = take(p->N);
+      combine(plan, x, {{in, c}}, 1.0, nullptr, 0.0, 0.0);
+      w.push_back(x);
+    }
+    return w;
+  }
+  // sum over classes Q of kron(terms of class Q) applied to w_Q into out (din -> dout)
+  void vc_sum_in(Plan& plan, const int* din, const int* dout, const std::vector<KTerm>& all,
+                 const std::vector<int>& cls, const std::vector<const double*>& w, double scale, double* out,
+                 bool accumulate) {
+    bool first = !accumulate;
+    for (size_t q = 0; q < cls.size(); ++q) {
+      const std::vector<KTerm> ts = class_terms(all, p, cls[q], [](size_t t) { return (int)t; });
+      if (ts.empty()) continue;
+      kron(plan, din, dout, 1, ts, scale, w[q], out, first ? 0.0 : 1.0, nullptr, 0.0);
+      first = false;
+    }
+  }
+  // out (+)= scale * sum_P f_P .* kron(terms of class P) in  (din -> cells)
+  void vc_sum_out(Plan& plan, const int* din, const std::vector<KTerm>& all, const std::vector<int>& cls,
+                  const double* in, double scale, double* out, bool accumulate) {
+    int dc[3];
+    dims_cells(p, dc);
+    std::vector<std::pair<const double*, int>> ys;
+    for (int c : cls) {
+      const std::vector<KTerm> ts = class_terms(all, p, c, [](size_t t) { return (int)t; });
+      if (ts.empty()) continue;
+      double* y = take(p->N);
+      kron(plan, din, dc, 1, ts, scale, in, y, 0.0, nullptr, 0.0);
+      ys.push_back({y, c});
+    }
+    combine(plan, out, ys, 1.0, nullptr, 0.0, accumulate ? 1.0 : 0.0);
+  }
+  // G_PP in (+ G_PB / L k(X*) parts): the variable-coefficient operator,
+  // sequential (no face sets, no tensor cores, no background chain)
+  void vc_ghat(Plan& plan, const double* in, double* out, double* g, double* w, double* u, bool with_icbc) {
+    stage_begin();
+    int dc[3], ds[3], dp[3];
+    dims_cells(p, dc);
+    dims_pred(p, dp);
+    const std::vector<int> cls = field_classes(p);
+    const std::vector<const double*> win = vc_inputs(plan, in, cls);
+    std::vector<std::pair<const double*, int>> ys;
+    std::vector<double*> y(cls.size());
+    for (size_t P = 0; P < cls.size(); ++P) {
+      y[P] = take(p->N);
+      bool first = true;
+      for (size_t Q = 0; Q < cls.size(); ++Q) {
+        const std::vector<KTerm> ts = pp_terms_pq(p, cls[P], cls[Q]);
+        if (ts.empty()) continue;
+        kron(plan, dc, dc, 1, ts, p->s2, win[Q], y[P], first ? 0.0 : 1.0, nullptr, 0.0);
+        first = false;
+      }
+      if (!first) ys.push_back({y[P], cls[P]});
+    }
+    if (with_icbc && p->M > 0) {
+      for (int s = 0; s < p->nsets; ++s) {
+        dims_set(p, s, ds);
+        vc_sum_in(plan, dc, ds, pb_terms(p, s, true, true), cls, win, p->s2, at(g, p->sets[s].off), false);
+      }
+      Plan H;
+      int ready[2];
+      hsolve_chain(H, g, w, ready);
+      plan.zip({&H});
+      for (size_t P = 0; P < cls.size(); ++P) {
+        bool has = false;
+        for (auto& e : ys) has = has || e.second == cls[P];
+        for (int s = 0; s < p->nsets; ++s) {
+          dims_set(p, s, ds);
+          const std::vector<KTerm> ts =
+              class_terms(pb_terms(p, s, false, true), p, cls[P], [](size_t t) { return (int)t; });
+          if (ts.empty()) continue;
+          kron(plan, ds, dc, 1, ts, -p->s2, at(w, p->sets[s].off), y[P], has ? 1.0 : 0.0, nullptr, 0.0);
+          if (!has) ys.push_back({y[P], cls[P]});
+          has = true;
+        }
+      }
+    }
+    combine(plan, out, ys, 1.0, in, p->jitter, 0.0);  // + jitter in (G_PP)
+    if (u) {
+      vc_sum_in(plan, dc, dp, ppred_terms(p), cls, win, p->s2, u, false);
+      if (with_icbc && p->M > 0) to_pred_sets(plan, w, u, -1.0, true, true);
+    }
+    stage_end();
+  }
+
   // out = G_BP in (cells -> all sets), into g (M); fold: set 0 in its eigenbasis
   void bp(Plan& plan, const double* in, double* g, bool fold = false) {
     int dc[3], ds[3];
     dims_cells(p, dc);
+    if (varcoef()) {
+      const bool k0 = keep;
+      if (!k0) stage_begin();
+      const std::vector<int> cls = field_classes(p);
+      const std::vector<const double*> win = vc_inputs(plan, in, cls);
+      for (int s = 0; s < p->nsets; ++s) {
+        dims_set(p, s, ds);
+        vc_sum_in(plan, dc, ds, pb_terms(p, s, true, fold), cls, win, p->s2, at(g, p->sets[s].off), false);
+      }
+      if (!k0) stage_end();
+      return;
+    }
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
       kron(plan, dc, ds, 1, pb_terms(p, s, true, fold), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
@@ -467,6 +636,28 @@ struct Builder {
   void pb(Plan& plan, const double* w, double* out, double scale, bool accumulate, bool fold = false) {
     int dc[3], ds[3];
     dims_cells(p, dc);
+    if (varcoef()) {
+      const bool k0 = keep;
+      if (!k0) stage_begin();
+      const std::vector<int> cls = field_classes(p);
+      std::vector<std::pair<const double*, int>> ys;
+      for (int c : cls) {
+        double* y = take(p->N);
+        bool first = true;
+        for (int s = 0; s < p->nsets; ++s) {
+          dims_set(p, s, ds);
+          const std::vector<KTerm> ts =
+              class_terms(pb_terms(p, s, false, fold), p, c, [](size_t t) { return (int)t; });
+          if (ts.empty()) continue;
+          kron(plan, ds, dc, 1, ts, scale * p->s2, at(w, p->sets[s].off), y, first ? 0.0 : 1.0, nullptr, 0.0);
+          first = false;
+        }
+        if (!first) ys.push_back({y, c});
+      }
+      combine(plan, out, ys, 1.0, nullptr, 0.0, accumulate ? 1.0 : 0.0);
+      if (!k0) stage_end();
+      return;
+    }
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
       kron(plan, ds, dc, 1, pb_terms(p, s, false, fold), scale * p->s2, at(w, p->sets[s].off), out,
@@ -804,6 +995,10 @@ struct Builder {
   // background chain.
   void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
                    Plan* pp_chain = nullptr) {
+    if (varcoef()) {
+      vc_ghat(plan, in, out, g, w, u, true);
+      return;
+    }
     int dc[3], ds[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
@@ -919,6 +1114,10 @@ struct Builder {
   }
 
   void pp(Plan& plan, const double* in, double* out, int* count) {
+    if (varcoef()) {
+      vc_ghat(plan, in, out, nullptr, nullptr, nullptr, false);
+      return;
+    }
     int dc[3];
     dims_cells(p, dc);
     kron(plan, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
@@ -928,6 +1127,15 @@ struct Builder {
     int dc[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
+    if (varcoef()) {
+      const bool k0 = keep;
+      if (!k0) stage_begin();
+      const std::vector<int> cls = field_classes(p);
+      const std::vector<const double*> win = vc_inputs(plan, v, cls);
+      vc_sum_in(plan, dc, dp, ppred_terms(p), cls, win, scale * p->s2, u, acc);
+      if (!k0) stage_end();
+      return;
+    }
     kron(plan, dc, dp, 1, ppred_terms(p), scale * p->s2, v, u, acc ? 1.0 : 0.0, nullptr, 0.0);
   }
   // out = scale * L_PDE k(X*) beta (prediction grid -> cells)
@@ -935,6 +1143,13 @@ struct Builder {
     int dc[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
+    if (varcoef()) {
+      const bool k0 = keep;
+      if (!k0) stage_begin();
+      vc_sum_out(plan, dp, predp_terms(p), field_classes(p), beta, scale * p->s2, out, false);
+      if (!k0) stage_end();
+      return;
+    }
     kron(plan, dp, dc, 1, predp_terms(p), scale * p->s2, beta, out, 0.0, nullptr, 0.0);
   }
   // g = L_IC,BC k(X*) beta (prediction grid -> all sets; fold: set 0 in its eigenbasis)
@@ -1182,6 +1397,8 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   for (int k = 0; k < 4; ++k) p->p_op[k] = Plan();
   B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
   B.ghat_phased(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
+  p->p_res = Plan();
+  B.ghat_phased(p->p_res, p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
   if (M > 0) {
     B.bp(p->p_op[2], p->d_vin, p->d_wout);
     B.pb(p->p_op[3], p->d_win, p->d_vout, 1.0, false);
@@ -1424,7 +1641,12 @@ void build_plans32(gpfvm_problem* p, Builder& B) {
   p->p_pp32 = Plan();
   B.pp(p->p_pp32, D(p->f_vin), D(p->f_vout), nullptr);
   // tensor-core variants of G_PP, one pair of instances per operand format
-  {
+  // (not for variable coefficients: their products run on the SIMT plans)
+  if (p->nfield > 0) {
+    p->tc_ok = false;
+    p->tc_split_total = 0;
+    p->tc_ops_total = 0;
+  } else {
     TcBuild T{p};
     for (int m = 0; m < 3; ++m) {
       build_tc_instance(p, T, p->f_p, p->f_q, 2 * m, m);
@@ -1471,9 +1693,10 @@ void finalize_plans(gpfvm_problem* p) {
   p->p_var32.skip = &p->d_st32->done;
   std::vector<Plan*> all = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
                             &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
-                            &p->p_mvv_cg, &p->p_mvv32, &p->p_tgt};
+                            &p->p_mvv_cg, &p->p_mvv32, &p->p_tgt, &p->p_res};
   std::vector<std::string> names = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2",
-                                    "op3", "mv32", "var32", "pp32", "mvv_cg", "mvv32", "tgt"};
+                                    "op3", "mv32", "var32", "pp32", "mvv_cg", "mvv32", "tgt", "res"};
+  p->p_res.skip = &p->d_mctl->first;
   for (int m = 0; m < 3; ++m) {
     all.push_back(&p->p_mv32tc[m]);
     all.push_back(&p->p_mvv32tc[m]);
@@ -1554,6 +1777,12 @@ int validate(const gpfvm_desc* D) {
   if (D->rhs)
     for (i64 j = 0; j < N; ++j)
       if (!std::isfinite(D->rhs[j])) return GPFVM_ERR_INVALID_ARG;
+  for (int k = 0; k < D->n_terms; ++k)
+    if (D->coef_field[k])
+      for (i64 j = 0; j < N; ++j)
+        if (!std::isfinite(D->coef_field[k][j])) return GPFVM_ERR_INVALID_ARG;
+  for (int k = D->n_terms; k < GPFVM_MAX_TERMS; ++k)
+    if (D->coef_field[k]) return GPFVM_ERR_INVALID_ARG;
   return GPFVM_OK;
 }
 
@@ -1723,6 +1952,13 @@ void alloc_all(gpfvm_problem* p) {
     p->d_rhs = m.alloc<double>(N);
     GPFVM_CUDA(cudaMemcpy(p->d_rhs, p->rhs.data(), N * sizeof(double), cudaMemcpyHostToDevice));
   }
+  if (p->nfield > 0) {
+    p->d_field = m.alloc<double>((i64)p->nfield * N);
+    p->f_field = m.alloc<float>((i64)p->nfield * N);
+    GPFVM_CUDA(cudaMemcpy(p->d_field, p->fields.data(), sizeof(double) * p->nfield * N, cudaMemcpyHostToDevice));
+    std::vector<float> f32(p->fields.begin(), p->fields.end());
+    GPFVM_CUDA(cudaMemcpy(p->f_field, f32.data(), sizeof(float) * p->nfield * N, cudaMemcpyHostToDevice));
+  }
   p->d_b = m.alloc<double>(N);
   p->d_x = m.alloc<double>(N);
   p->d_r = m.alloc<double>(N);
@@ -1772,12 +2008,16 @@ void alloc_all(gpfvm_problem* p) {
   p->d_eta32 = m.alloc<double>(cap);
   p->d_st = m.alloc<CGState>(1);
   p->d_st32 = m.alloc<CGState>(1);
+  p->d_mctl = m.alloc<MixedCtl>(1);
   p->d_psync = m.alloc<unsigned int>(2);
   GPFVM_CUDA(cudaMemset(p->d_psync, 0, 2 * sizeof(unsigned int)));
   GPFVM_CUDA(cudaMemset(p->d_st, 0, sizeof(CGState)));
   GPFVM_CUDA(cudaMemset(p->d_st32, 0, sizeof(CGState)));
   GPFVM_CUDA(cudaMallocHost(&p->h_st, sizeof(CGState)));
   GPFVM_CUDA(cudaMallocHost(&p->h_st32, sizeof(CGState)));
+  GPFVM_CUDA(cudaMallocHost(&p->h_mctl, sizeof(MixedCtl)));
+  std::memset(p->h_mctl, 0, sizeof(MixedCtl));
+  GPFVM_CUDA(cudaMemset(p->d_mctl, 0, sizeof(MixedCtl)));
   std::memset(p->h_st, 0, sizeof(CGState));
   std::memset(p->h_st32, 0, sizeof(CGState));
   GPFVM_CUDA(cudaMemset(p->d_down, 0, P * sizeof(double)));
@@ -2478,6 +2718,25 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
   p->jitter = D->jitter;
   p->colloc = D->observe == 1;
   p->nterms = D->n_terms;
+  {
+    std::vector<const double*> seen;
+    for (int k = 0; k < D->n_terms; ++k) {
+      const double* f = D->coef_field[k];
+      if (!f) continue;
+      int c = -1;
+      for (size_t j = 0; j < seen.size(); ++j)
+        if (seen[j] == f) c = (int)j;
+      if (c < 0) {
+        c = (int)seen.size();
+        seen.push_back(f);
+        i64 n = 1;
+        for (int i = 0; i < D->ndim; ++i) n *= D->n_cells[i];
+        p->fields.insert(p->fields.end(), f, f + n);
+      }
+      p->fclass[k] = c;
+    }
+    p->nfield = (int)seen.size();
+  }
   for (int k = 0; k < p->nterms; ++k) {
     p->coef[k] = D->coef[k];
     for (int i = 0; i < p->d; ++i) p->alpha[k][i] = D->alpha[k][i];
@@ -3053,6 +3312,283 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
     if (!progressed) std::this_thread::yield();
   }
   cudaEventDestroy(ev);
+  return worst;
+  GPFVM_GUARD_END
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves as ONE graph launch.  Every problem's whole solve is a
+// device-driven loop: a WHILE node whose body computes the FP64 residual,
+// takes the refinement decision on the device (mixed_ctl), runs the inner CG
+// as a nested WHILE node and applies the correction (mixed_post); an FP64
+// problem's body is its CG iteration.  All problems' loops are independent
+// branches of one graph, launched once; the host only sets them up before
+// and reads their states after.  The direction stores cannot grow inside a
+// graph, so they are allocated up front: every run's directions with reorth 1
+// (up to max_iter), one run's with reorth 0 or 2.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CaptureGuard {  // ends a failed capture so that the stream stays usable
+  cudaStream_t st;
+  bool active = true;
+  ~CaptureGuard() {
+    if (active) {
+      cudaGraph_t dummy = nullptr;
+      cudaStreamEndCapture(st, &dummy);
+      if (dummy) cudaGraphDestroy(dummy);
+      cudaGetLastError();
+    }
+  }
+};
+
+// Adds to `g` the WHILE node of one problem's device-driven solve (handle
+// created on g); *k_outer / *k_inner receive the kernels of one outer / inner
+// pass (for the launch count).
+void add_solve_loop(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaGraph_t g, cudaStream_t st, cudaStream_t st2,
+                    long long* k_outer, long long* k_inner) {
+  const i64 N = p->N;
+  const bool mixed = o->precision != GPFVM_FP64;
+  cudaGraphConditionalHandle ho;
+  GPFVM_CUDA(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = ho;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wo;
+  GPFVM_CUDA(cudaGraphAddNode(&wo, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const int unroll = loop_unroll();
+  if (!mixed) {  // FP64: the CG iteration itself, as in make_loop_graph
+    const bool reorth = o->reorth != 0, want_var = o->want_var != 0;
+    const long long before = g_launches.load();
+    GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    {
+      CaptureGuard cg{st};
+      for (int u = 0; u < unroll; ++u) cg_iteration(p, reorth, want_var, st);
+      loop_ctl(p->d_st, ho, st);
+      cudaGraph_t out;
+      cg.active = false;
+      GPFVM_CUDA(cudaStreamEndCapture(st, &out));
+    }
+    *k_inner = g_launches.load() - before;
+    g_launches.fetch_sub(*k_inner);
+    *k_outer = 0;
+    return;
+  }
+  MixedCtl* c = p->d_mctl;
+  const bool reorth = o->reorth != 0, cont = o->reorth == 1, want_var = o->want_var != 0;
+  // segment A: FP64 residual, decision, start of the next run
+  const long long before = g_launches.load();
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  std::vector<cudaGraphNode_t> tail;
+  cudaGraphConditionalHandle hi;
+  GPFVM_CUDA(cudaGraphConditionalHandleCreate(&hi, body, 0, 0));
+  GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  {
+    CaptureGuard cg{st};
+    axpby(p->d_x, p->d_x, p->d_vin, 1.0, 0.0, N, st);  // vin = x (a kernel node)
+    p->p_res.run(st);  // skipped on the first pass (x = 0)
+    mixed_resid(p->d_b, p->d_vout, p->d_r, N, c, st);
+    norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
+    mixed_ctl(c, p->d_st, p->d_st32, ho, hi, st);
+    cg_init<double, float>(p->d_r, p->f_d, p->f_r, p->f_p, N, p->d_st32, st, &p->d_st->aux[0], &c->stop);
+    if (cont)
+      cg_project<float>(p->f_S, p->f_Q, p->f_r, p->f_d, p->f_p, N, p->cap32, p->d_st32, p->d_part2, p->d_coef,
+                        p->d_eta32, st);
+    cudaStreamCaptureStatus cs;
+    GPFVM_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    tail.assign(deps, deps + ndeps);
+    cudaGraph_t out;
+    cg.active = false;
+    GPFVM_CUDA(cudaStreamEndCapture(st, &out));
+  }
+  // the inner CG run: a nested WHILE node after segment A
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hi;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  cudaGraphNode_t wi;
+  GPFVM_CUDA(cudaGraphAddNode(&wi, body, tail.data(), nullptr, tail.size(), &ip));
+  cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+  const long long mid = g_launches.load();
+  GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  {
+    CaptureGuard cg{st2};
+    for (int u = 0; u < unroll; ++u) cg_iteration32(p, want_var, reorth, st2);
+    loop_ctl(p->d_st32, hi, st2);
+    cudaGraph_t out;
+    cg.active = false;
+    GPFVM_CUDA(cudaStreamEndCapture(st2, &out));
+  }
+  *k_inner = g_launches.load() - mid;
+  // segment B: bookkeeping and the correction, after the inner loop
+  const long long mid2 = g_launches.load();
+  GPFVM_CUDA(cudaStreamBeginCaptureToGraph(st, body, &wi, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  {
+    CaptureGuard cg{st};
+    mixed_post(c, p->d_st32, p->d_x, p->f_d, N, ho, st);
+    cudaGraph_t out;
+    cg.active = false;
+    GPFVM_CUDA(cudaStreamEndCapture(st, &out));
+  }
+  *k_outer = (mid - before) + (g_launches.load() - mid2);
+  g_launches.fetch_sub(g_launches.load() - before);
+}
+
+// Host-side set-up of one problem's device-driven solve (enqueued on st).
+int graph_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
+  if (!p->assembled) return GPFVM_ERR_STATE;
+  if (!o || o->max_iter < 1 || !(o->rtol >= 0) || o->reorth < 0 || o->reorth > 2) return GPFVM_ERR_INVALID_ARG;
+  if (o->precision == GPFVM_FP64) {
+    const int b = solve_begin(p, o, st);  // stores, scalar header, x = 0, r = p = b
+    if (b != GPFVM_OK) return b;
+    runs()[p].launched = o->max_iter;  // the graph is launched by the batch
+    return GPFVM_OK;
+  }
+  if (o->precision < GPFVM_MIXED_FP32 || o->precision > GPFVM_MIXED_BF16) return GPFVM_ERR_INVALID_ARG;
+  if (o->reorth == 1 && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
+  const int want_tc = o->precision == GPFVM_MIXED_TF32X3 ? TC_TF32X3
+                      : o->precision == GPFVM_MIXED_BF16X3 ? TC_BF16X3
+                      : o->precision == GPFVM_MIXED_BF16  ? TC_BF16
+                                                          : -1;
+  if (want_tc >= 0 && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (want_tc != p->tc_mode) {
+    p->tc_mode = want_tc;
+    if (p->graph32) cudaGraphExecDestroy(p->graph32);
+    p->graph32 = nullptr;
+    p->graph32_key = -1;
+  }
+  const int icap = std::min(p->cap, o->inner_max_iter > 0 ? o->inner_max_iter : p->cap);
+  ensure_store32(p, o->reorth == 1 ? std::min(o->max_iter, p->cap) : icap);
+  MixedCtl& h = *p->h_mctl;
+  std::memset(&h, 0, sizeof(MixedCtl));
+  h.rtol = o->rtol;
+  h.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
+  h.max_iter = o->max_iter;
+  h.icap_opt = icap;
+  h.cap32 = p->cap32;
+  h.cont = o->reorth == 1;
+  h.want_var = o->want_var != 0;
+  h.max_outer = o->max_iter + 4;
+  h.rel = h.rel_prev = 1.0;
+  h.tscale = 1.0;
+  h.first = 1;
+  GPFVM_CUDA(cudaMemcpyAsync(p->d_mctl, &h, sizeof(MixedCtl), cudaMemcpyHostToDevice, st));
+  GPFVM_CUDA(cudaMemsetAsync(&p->d_st->status, 0, sizeof(int), st));
+  GPFVM_CUDA(cudaMemsetAsync(&p->d_st32->pad[1], 0, sizeof(int), st));
+  GPFVM_CUDA(cudaMemsetAsync(p->d_x, 0, sizeof(double) * p->N, st));
+  if (o->want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  norm2(p->d_b, p->N, &p->d_st->aux[1], p->d_st, st);
+  return GPFVM_OK;
+}
+
+// Reads the final state of one problem's device-driven solve.
+int graph_end(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, long long k_outer,
+              long long k_inner, cudaStream_t st) {
+  if (o->precision == GPFVM_FP64) {
+    copy_header_to_host(p, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    p->graph_kernels = k_inner;
+    return solve_end(p, info, st);
+  }
+  GPFVM_CUDA(cudaMemcpyAsync(p->h_mctl, p->d_mctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, st));
+  GPFVM_CUDA(cudaStreamSynchronize(st));
+  const MixedCtl& h = *p->h_mctl;
+  count_launch((long long)(h.outer + 1) * k_outer + h.inner_passes * k_inner);
+  int status = h.stop ? h.status : GPFVM_NOT_CONVERGED;
+  gpfvm_solve_info I = p->last;
+  I.iterations = h.total;
+  I.status = status;
+  I.rel_residual = h.rel;
+  I.true_rel_residual = h.rel;
+  I.t_solve_ms = 0.0;
+  p->last = I;
+  p->last_outer = h.outer;
+  if (info) *info = I;
+  p->solved = status >= 0;
+  p->want_var_last = o->want_var != 0;
+  p->last_store = o->reorth == 1 ? 2 : 0;
+  p->last_kstore = o->reorth == 1 ? h.kstore : 0;
+  return status;
+}
+
+}  // namespace
+
+extern "C" int gpfvm_solve_batch_graph(gpfvm_problem** ps, int n, const gpfvm_solve_opts* opts,
+                                       gpfvm_solve_info* infos, void* stream, int64_t* launches_out) {
+  if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (ps[i] == ps[j]) return GPFVM_ERR_INVALID_ARG;  // one loop per problem
+  GPFVM_GUARD_BEGIN
+  // set-up and launch on a stream of our own (capture is not possible on the
+  // legacy default stream), ordered after the caller's stream
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  GPFVM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  struct StreamOwner {
+    cudaStream_t s;
+    cudaEvent_t& e;
+    ~StreamOwner() {
+      if (e) cudaEventDestroy(e);
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } owner{st, ev};
+  GPFVM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  GPFVM_CUDA(cudaEventRecord(ev, (cudaStream_t)stream));
+  GPFVM_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  std::vector<int> ok(n, 0);
+  int worst = GPFVM_OK;
+  for (int i = 0; i < n; ++i) {
+    const int b = graph_begin(ps[i], opts, st);
+    ok[i] = b == GPFVM_OK;
+    if (!ok[i]) {
+      worst = std::min(worst, b);
+      if (infos) infos[i].status = b;
+    }
+  }
+  cudaStream_t cap_st = nullptr, cap_st2 = nullptr;
+  GPFVM_CUDA(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+  if (cudaStreamCreateWithFlags(&cap_st2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(cap_st);
+    throw CudaError{cudaErrorUnknown, "stream"};
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  std::vector<long long> ko(n, 0), ki(n, 0);
+  const long long l0 = g_launches.load();
+  try {
+    GPFVM_CUDA(cudaGraphCreate(&g, 0));
+    for (int i = 0; i < n; ++i)
+      if (ok[i]) add_solve_loop(ps[i], opts, g, cap_st, cap_st2, &ko[i], &ki[i]);
+    GPFVM_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    GPFVM_CUDA(cudaGraphLaunch(ex, st));  // the whole batch
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap_st);
+    cudaStreamDestroy(cap_st2);
+    throw;
+  }
+  cudaGraphExecDestroy(ex);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cap_st);
+  cudaStreamDestroy(cap_st2);
+  for (int i = 0; i < n; ++i) {
+    if (!ok[i]) continue;
+    const int r = graph_end(ps[i], opts, infos ? &infos[i] : nullptr, ko[i], ki[i], st);
+    if (r < 0) worst = std::min(worst, r);
+    else if (r == GPFVM_NOT_CONVERGED && worst == GPFVM_OK) worst = r;
+  }
+  if (launches_out) *launches_out = g_launches.load() - l0;
   return worst;
   GPFVM_GUARD_END
 }

@@ -38,8 +38,10 @@ __device__ double sum_partials(const double* part, int n, double* smem) {
 
 template <typename TB, typename T>
 __global__ void __launch_bounds__(RT) k_init(const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                                              T* __restrict__ p, i64 n, CGState* st, const double* nrm2) {
+                                              T* __restrict__ p, i64 n, CGState* st, const double* nrm2,
+                                              const int* skip) {
   pdl_wait();
+  if (skip && *skip) return;
   __shared__ double red[32];
   // optional normalisation to a unit right-hand side (x0 = 0): b / ||b||
   double sc = 1.0;
@@ -103,7 +105,7 @@ template <typename T>
 __global__ void __launch_bounds__(RT) k_downdate(const T* __restrict__ u, double* __restrict__ down, i64 n,
                                                   const CGState* st) {
   pdl_wait();
-  if (st->done) return;
+  if (st->done || st->nodown) return;
   const double inv = 1.0 / st->eta;
   for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
     const double v = (double)u[i];
@@ -228,23 +230,29 @@ __global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) part2[(i64)j * nchunk + c] = sum;
   }
-  // the last block to finish forms the coefficients (one warp per direction)
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(&st->ticket[4], 1u) == gridDim.x * gridDim.y - 1);
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  for (int j = warp; j < k; j += RT / 32) {
-    const volatile double* row = part2 + (i64)j * nchunk;
-    double sum = 0.0;
-    for (int cc = lane; cc < nchunk; cc += 32) sum += row[cc];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) coef[j] = sum / eta_hist[j];
+}
+
+// coef_j = (sum over chunks of part2[j][.]) / eta_j, one block per direction
+// (the chunk sums are added in a fixed order: deterministic)
+__global__ void __launch_bounds__(RT) k_reorth_coef(const CGState* st, int nchunk, const double* __restrict__ part2,
+                                                     const double* __restrict__ eta_hist, double* __restrict__ coef) {
+  pdl_wait();
+  if (st->done) return;
+  const int j = blockIdx.x;
+  if (j >= min(st->k, st->cap)) return;
+  __shared__ double red[32];
+  const double* __restrict__ row = part2 + (i64)j * nchunk;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int cc = threadIdx.x;
+  for (; cc + 3 * RT < nchunk; cc += 4 * RT) {
+    a0 += row[cc];
+    a1 += row[cc + RT];
+    a2 += row[cc + 2 * RT];
+    a3 += row[cc + 3 * RT];
   }
-  if (threadIdx.x == 0) st->ticket[4] = 0;
+  for (; cc < nchunk; cc += RT) a0 += row[cc];
+  const double sum = block_sum<RT>((a0 + a1) + (a2 + a3), red);
+  if (threadIdx.x == 0) coef[j] = sum / eta_hist[j];
 }
 
 template <typename T>
@@ -305,8 +313,9 @@ int reduce_grid(i64 n) {
 }
 
 template <typename TB, typename T>
-void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2) {
-  launch_pdl(k_init<TB, T>, reduce_grid(n), RT, 0, s, b, x, r, p, n, st, nrm2);
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2,
+             const int* skip) {
+  launch_pdl(k_init<TB, T>, reduce_grid(n), RT, 0, s, b, x, r, p, n, st, nrm2, skip);
 }
 template <typename T>
 void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s) {
@@ -368,10 +377,7 @@ template <typename T>
 void cg_residual_wrt(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
                      const double* eta_hist, cudaStream_t s) {
   const i64 ld = store_ld(n);
-  const int nchunk = reorth_chunks(n);
-  int gy = (4 * 152 + nchunk - 1) / nchunk;
-  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
-  launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, S, ld, p, n, st, part2, eta_hist, coef);
+  reorth_coefs(S, (const T*)p, n, cap, st, part2, coef, eta_hist, s);
   launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, Q, ld, p, n, st, coef, 1.0);
 }
 template <typename T>
@@ -383,15 +389,24 @@ int reorth_chunks(i64 n) {
   const i64 c = (n + RCH - 1) / RCH;
   return c < 1 ? 1 : (int)c;
 }
+// partial dots Q^T p per chunk, then the coefficients (one block per direction)
 template <typename T>
-void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
-               const double* eta_hist, cudaStream_t s) {
+void reorth_coefs(const T* Q, const T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
+                  const double* eta_hist, cudaStream_t s) {
   const i64 ld = store_ld(n);
   const int nchunk = reorth_chunks(n);
   // split the directions over blockIdx.y until about four CTAs per SM are busy
   int gy = (4 * 152 + nchunk - 1) / nchunk;
   gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
   launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, Q, ld, p, n, st, part2, eta_hist, coef);
+  if (cap > 0) launch_pdl(k_reorth_coef, cap, RT, 0, s, (const CGState*)st, nchunk, (const double*)part2, eta_hist, coef);
+}
+
+template <typename T>
+void cg_reorth(const T* S, const T* Q, T* p, i64 n, int cap, CGState* st, double* part2, double* coef,
+               const double* eta_hist, cudaStream_t s) {
+  const i64 ld = store_ld(n);
+  reorth_coefs(Q, (const T*)p, n, cap, st, part2, coef, eta_hist, s);
   launch_pdl(k_reorth_apply<T>, ceil_div(n, RT * (16 / (int)sizeof(T))), RT, 0, s, S, ld, p, n, st, coef, 1.0);
 }
 
@@ -430,12 +445,9 @@ template <typename T>
 void cg_project(const T* S, const T* Q, T* r, T* d, T* p, i64 n, int cap, CGState* st, double* part2,
                 double* coef, const double* eta_hist, cudaStream_t s) {
   const i64 ld = store_ld(n);
-  const int nchunk = reorth_chunks(n);
-  int gy = (4 * 152 + nchunk - 1) / nchunk;
-  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
   const int ga = ceil_div(n, RT * (16 / (int)sizeof(T)));
-  // c_j = s_j . r / eta_j  (the dots kernel with the directions in place of Q)
-  launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, S, ld, r, n, st, part2, eta_hist, coef);
+  // c_j = s_j . r / eta_j  (the dots with the directions in place of Q)
+  reorth_coefs(S, (const T*)r, n, cap, st, part2, coef, eta_hist, s);
   launch_pdl(k_reorth_apply<T>, ga, RT, 0, s, Q, ld, r, n, st, coef, 1.0);   // r -= Q c
   launch_pdl(k_reorth_apply<T>, ga, RT, 0, s, S, ld, d, n, st, coef, -1.0);  // d += S c
   launch_pdl(k_restart<T>, reduce_grid(n), RT, 0, s, r, p, n, st);
@@ -457,9 +469,9 @@ void cg_project(const T* S, const T* Q, T* r, T* d, T* p, i64 n, int cap, CGStat
 GPFVM_CG_INST(double)
 GPFVM_CG_INST(float)
 template void cg_init<double, double>(const double*, double*, double*, double*, i64, CGState*, cudaStream_t,
-                                      const double*);
+                                      const double*, const int*);
 template void cg_init<double, float>(const double*, float*, float*, float*, i64, CGState*, cudaStream_t,
-                                     const double*);
+                                     const double*, const int*);
 
 // ---- small vector helpers -------------------------------------------------
 __global__ void k_axpby(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
@@ -580,6 +592,134 @@ void transpose(const double* A, double* B, int m, int n, cudaStream_t s) {
   if (m <= 0 || n <= 0) return;
   k_transpose<<<dim3(ceil_div(n, 32), ceil_div(m, 32)), dim3(32, 8), 0, s>>>(A, B, m, n);
   GPFVM_LAUNCH_CHECK();
+}
+
+// ---- variable coefficients ------------------------------------------------
+template <typename T>
+__global__ void k_field_combine(T* __restrict__ out, i64 n, const FieldTerms t, const T* __restrict__ D,
+                                double gamma, double beta) {
+  pdl_wait();
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    double v = beta != 0.0 ? beta * (double)out[i] : 0.0;
+    for (int k = 0; k < t.nt; ++k) {
+      const double y = (double)((const T*)t.y[k])[i];
+      const double f = t.f[k] ? (double)((const T*)t.f[k])[i] : 1.0;
+      v = fma(t.scale[k] * f, y, v);
+    }
+    if (D) v = fma(gamma, (double)D[i], v);
+    out[i] = (T)v;
+  }
+}
+void field_combine(void* out, i64 n, const FieldTerms& t, const void* D, double gamma, double beta, bool f32,
+                   cudaStream_t s) {
+  if (n <= 0) return;
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  if (f32) launch_pdl(k_field_combine<float>, g, RT, 0, s, (float*)out, n, t, (const float*)D, gamma, beta);
+  else launch_pdl(k_field_combine<double>, g, RT, 0, s, (double*)out, n, t, (const double*)D, gamma, beta);
+}
+
+// ---- device-driven mixed refinement --------------------------------------
+__global__ void k_mixed_ctl(MixedCtl* c, const CGState* s64, CGState* s32, cudaGraphConditionalHandle ho,
+                            cudaGraphConditionalHandle hi) {
+  pdl_wait();
+  if (c->stop) {  // never reached with a live loop; keeps a stray pass inert
+    cudaGraphSetConditional(hi, 0u);
+    cudaGraphSetConditional(ho, 0u);
+    return;
+  }
+  const double b2 = s64->aux[1];
+  double rel = b2 > 0.0 ? sqrt(s64->aux[0] / b2) : 0.0;
+  int stop = 0, status = 0;
+  if (s32->pad[1] & DEV_TIMEOUT) {
+    stop = 1; status = -6;
+  } else if (!isfinite(rel)) {
+    stop = 1; status = -4;
+  } else if (c->outer > 0 && rel > 10.0 * c->rel_prev) {  // divergence: undo the last correction
+    stop = 1; status = 1;
+    c->undo = 1;
+    rel = c->rel_prev;
+  } else {
+    c->rel_prev = rel;
+    if (rel <= c->rtol || (c->cont && c->outer > 0 && c->tscale >= 1.0 && rel <= 2.0 * c->rtol)) {
+      stop = 1; status = 0;
+    } else if (c->total >= c->max_iter || c->idle >= 3 || c->outer >= c->max_outer) {
+      stop = 1; status = 1;
+    } else {
+      if (c->outer > 0 && rel <= 2.0 * c->rtol) c->tscale *= 0.5;
+      const int kbase = c->cont ? c->kstore : 0;
+      const int run_cap = min(c->icap_opt, c->max_iter - c->total);
+      const int icap = max(1, min(c->cap32 - kbase, run_cap));
+      const double itol = fmax(c->itol, rel > 0.0 ? c->tscale * c->rtol / rel : c->itol);
+      s32->rtol2 = itol * itol;
+      s32->max_iter = kbase + icap;
+      s32->cap = c->cap32;
+      s32->kbase = kbase;
+      s32->nodown = (c->want_var && (c->cont || c->outer == 0)) ? 0 : 1;
+      s32->pad[1] = 0;
+      c->kbase = kbase;
+    }
+  }
+  c->rel = rel;
+  c->stop = stop;
+  if (stop) {
+    c->status = status == 0 ? 0 : (status == 1 ? 1 : status);
+    s32->done = 1;
+  }
+  cudaGraphSetConditional(hi, stop ? 0u : 1u);
+  cudaGraphSetConditional(ho, stop ? 0u : 1u);
+}
+void mixed_ctl(MixedCtl* c, const CGState* s64, CGState* s32, cudaGraphConditionalHandle h_outer,
+               cudaGraphConditionalHandle h_inner, cudaStream_t s) {
+  launch_pdl(k_mixed_ctl, 1, 1, 0, s, c, s64, s32, h_outer, h_inner);
+}
+
+__global__ void k_mixed_resid(const double* __restrict__ b, const double* __restrict__ gx, double* __restrict__ r,
+                              i64 n, const MixedCtl* c) {
+  pdl_wait();
+  if (c->stop) return;
+  const bool first = c->first != 0;
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT)
+    r[i] = first ? b[i] : b[i] - gx[i];
+}
+void mixed_resid(const double* b, const double* gx, double* r, i64 n, const MixedCtl* c, cudaStream_t s) {
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  launch_pdl(k_mixed_resid, g, RT, 0, s, b, gx, r, n, c);
+}
+
+// one thread: bookkeeping of the finished run (before the x update)
+__global__ void k_mixed_count(MixedCtl* c, CGState* s32, cudaGraphConditionalHandle ho) {
+  c->first = 0;
+  if (c->stop) return;
+  const int k = s32->k - s32->kbase;
+  c->total += k;
+  c->inner_passes += s32->loops;
+  if (c->cont) c->kstore = min(s32->k, c->cap32);
+  if (k == 0 && !s32->converged) {  // not even one inner step
+    c->stop = 1;
+    c->status = -4;
+    cudaGraphSetConditional(ho, 0u);
+    return;
+  }
+  c->idle = k == 0 ? c->idle + 1 : 0;
+  c->outer += 1;
+}
+__global__ void k_mixed_xupd(const MixedCtl* c, const CGState* s32, double* __restrict__ x,
+                             const float* __restrict__ d, i64 n) {
+  pdl_wait();
+  if (c->stop && !c->undo) return;
+  const double a = (c->undo ? -1.0 : 1.0) * s32->aux[7];
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) x[i] = fma(a, (double)d[i], x[i]);
+}
+void mixed_post(MixedCtl* c, CGState* s32, double* x, const float* d, i64 n, cudaGraphConditionalHandle h_outer,
+                cudaStream_t s) {
+  // a plain launch: its predecessor in the graph is the inner loop's conditional node
+  k_mixed_count<<<1, 1, 0, s>>>(c, s32, h_outer);
+  GPFVM_LAUNCH_CHECK();
+  int g = ceil_div(n, RT);
+  if (g > 4096) g = 4096;
+  launch_pdl(k_mixed_xupd, g, RT, 0, s, (const MixedCtl*)c, (const CGState*)s32, x, d, n);
 }
 
 }  // namespace gpfvm

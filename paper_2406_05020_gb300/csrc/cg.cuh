@@ -13,6 +13,7 @@ struct CGState {
   int pad[2];
   int loops;  // passes of the device-side iteration loop (reset by cg_init)
   int kbase;  // directions already stored when a run starts: cg_init sets k = kbase
+  int nodown, pad3;  // nodown: the variance downdate of this run is skipped
   unsigned int ticket[8];
   double part[CG_MAX_PART];
 };
@@ -25,7 +26,8 @@ i64 store_ld(i64 n);
 // r = p = b (scaled by 1/sqrt(*nrm2) when nrm2 is given; st->aux[7] keeps the
 // inverse factor), x = 0, and the scalar header reset for a new run.
 template <typename TB, typename T>
-void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2 = nullptr);
+void cg_init(const TB* b, T* x, T* r, T* p, i64 n, CGState* st, cudaStream_t s, const double* nrm2 = nullptr,
+             const int* skip = nullptr);
 template <typename T>
 void cg_dot_eta(const T* p, const T* q, i64 n, CGState* st, double* eta_hist, cudaStream_t s);
 template <typename T>
@@ -64,5 +66,42 @@ void norm2(const double* v, i64 n, double* out, CGState* st, cudaStream_t s);
 void var_final(const double* vB, const double* down, double* var, double s2, i64 n, cudaStream_t s);
 void colsumsq(const double* Y, int rows, i64 cols, double* acc, cudaStream_t s);
 void transpose(const double* A, double* B, int m, int n, cudaStream_t s);
+
+// ---- variable coefficients: out = beta out + sum_t scale_t (f_t .* y_t) + gamma D
+// (f_t null: 1); FP64 or FP32 (f32) data
+constexpr int FIELD_MAXT = 8;
+struct FieldTerms {
+  const void* y[FIELD_MAXT];
+  const void* f[FIELD_MAXT];
+  double scale[FIELD_MAXT];
+  int nt;
+};
+void field_combine(void* out, i64 n, const FieldTerms& t, const void* D, double gamma, double beta, bool f32,
+                   cudaStream_t s);
+
+// ---- device-driven mixed refinement (one graph per solve, see api.cu) ----
+// The refinement decisions of the host-driven solver (residual test,
+// divergence guard, run tolerance, conjugate continuation bookkeeping) taken
+// on the device between the runs of an outer graph loop.
+struct MixedCtl {
+  // options
+  double rtol, itol;
+  int max_iter, icap_opt, cap32, cont, want_var, max_outer;
+  // state
+  double rel, rel_prev, tscale;
+  int outer, total, kstore, idle, kbase;
+  int first, stop, undo, status;  // status: 0 running, else a gpfvm_status
+  long long inner_passes;
+};
+// control step after the FP64 residual (r, with ||r||^2 in s64->aux[0] and
+// ||b||^2 in s64->aux[1]): decides stop / next run, writes the inner state
+void mixed_ctl(MixedCtl* c, const CGState* s64, CGState* s32, cudaGraphConditionalHandle h_outer,
+               cudaGraphConditionalHandle h_inner, cudaStream_t s);
+// r = b - (first ? 0 : Gx), skipped once the solve stopped
+void mixed_resid(const double* b, const double* gx, double* r, i64 n, const MixedCtl* c, cudaStream_t s);
+// after a run: bookkeeping (iterations, stores, breakdown), then x += |r| d
+// (or the undo of the last correction after a divergence)
+void mixed_post(MixedCtl* c, CGState* s32, double* x, const float* d, i64 n, cudaGraphConditionalHandle h_outer,
+                cudaStream_t s);
 
 }  // namespace gpfvm

@@ -47,7 +47,8 @@ class Desc(C.Structure):
                 ("alpha", (C.c_int * MAX_DIM) * MAX_TERMS), ("coef", C.c_double * MAX_TERMS),
                 ("rhs", C.POINTER(C.c_double)), ("jitter", C.c_double), ("n_sets", C.c_int),
                 ("sets", PointSet * MAX_SETS), ("n_pred", C.c_int * MAX_DIM),
-                ("pred", C.POINTER(C.c_double) * MAX_DIM), ("observe", C.c_int)]
+                ("pred", C.POINTER(C.c_double) * MAX_DIM), ("observe", C.c_int),
+                ("coef_field", C.POINTER(C.c_double) * MAX_TERMS)]
 
 
 class SolveOpts(C.Structure):
@@ -87,6 +88,8 @@ SIGNATURES = {
     "gpfvm_export": (C.c_int64, [P, C.c_int, D, C.c_int64, P]),
     "gpfvm_factor": (C.c_int64, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, D, C.c_int64, P]),
     "gpfvm_solve_batch": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "gpfvm_solve_batch_graph": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P,
+                                          C.POINTER(C.c_int64)]),
     "gpfvm_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(P)]),
     "gpfvm_server_submit": (C.c_int, [P, C.POINTER(Desc), C.POINTER(C.c_int64)]),
     "gpfvm_server_step": (C.c_int, [P]),
@@ -185,6 +188,15 @@ def make_desc(prob):
         d.coef[k] = float(c)
     d.rhs = arr(np.ravel(prob.rhs)) if prob.rhs is not None else None
     d.observe = 1 if getattr(prob, "observe", "fvm") == "collocation" else 0
+    fields = getattr(prob, "fields", None)
+    if fields is not None:
+        shared = {}  # terms sharing one array share one pointer (one field on the device)
+        for k, f in enumerate(fields):
+            if f is None:
+                continue
+            if id(f) not in shared:
+                shared[id(f)] = arr(np.ravel(f))
+            d.coef_field[k] = shared[id(f)]
     d.jitter = float(prob.jitter)
     if len(prob.sets) > MAX_SETS:
         raise ValueError("too many point sets")
@@ -325,6 +337,16 @@ def solve_batch(problems, opts: SolveOpts, stream=None):
     code = _check(lib().gpfvm_solve_batch(arr, len(problems), C.byref(opts), infos, _stream(stream)),
                   "gpfvm_solve_batch")
     return code, list(infos)
+
+
+def solve_batch_graph(problems, opts: SolveOpts, stream=None):
+    """The batch as one graph launch (gpfvm_solve_batch_graph): (code, infos, kernels executed)."""
+    arr = (P * len(problems))(*[p.h for p in problems])
+    infos = (SolveInfo * len(problems))()
+    nl = C.c_int64(0)
+    code = _check(lib().gpfvm_solve_batch_graph(arr, len(problems), C.byref(opts), infos, _stream(stream),
+                                                C.byref(nl)), "gpfvm_solve_batch_graph")
+    return code, list(infos), int(nl.value)
 
 
 def kron_matvec_noalloc(dims, terms, scale, diag, v, out, stream=None):

@@ -115,3 +115,56 @@ def test_server_isolates_bad_and_oversized_requests():
     m, _ = O.dense_posterior(good)
     assert relerr(mean, m) < 1e-6
     srv.close()
+
+
+@pytest.mark.parametrize("precision,reorth", [(0, 1), (2, 1), (2, 2)])
+def test_batch_graph_at_c4_sizes_equals_individual_solves(precision, reorth):
+    """The uneven heat batch at its own sizes (axis sizes 16..64) as ONE graph
+    launch (device-driven refinement in every problem's loop) gives every
+    problem's individual, host-driven solve: same iterations, mean and variance
+    to 1e-14."""
+    import torch
+
+    from paper_2406_05020_gb300 import gpfvm
+    probs = W.batch_heat(256, lo=16, hi=64, seed=0)[:5]
+    opts = gpfvm.solve_opts(max_iter=3000, rtol=1e-10, precision=precision, reorth=reorth, want_var=True,
+                            inner_max_iter=400, inner_rtol=1e-2)
+    alone = [_alone(p, opts) for p in probs]
+    pbs = [gpfvm.Problem(p, max_iter=3000) for p in probs]
+    for pb in pbs:
+        pb.assemble()
+    code, infos, launches = gpfvm.solve_batch_graph(pbs, opts)
+    assert code == 0, [i.as_dict() for i in infos]
+    assert launches > 0
+    for pb, prob, ref, info in zip(pbs, probs, alone, infos):
+        mean = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+        var = torch.empty_like(mean)
+        pb.query(mean, var)
+        assert ref[0] == 0 and info.status == 0
+        assert info.iterations == ref[3]
+        assert relerr(mean.cpu().numpy(), ref[1]) < 1e-14
+        np.testing.assert_allclose(var.cpu().numpy(), ref[2], rtol=0, atol=1e-14)
+        pb.close()
+
+
+def test_server_at_c5_sizes_same_result_alone_and_in_the_mix():
+    """Served wave requests from the lower end of the serving size range
+    (axis sizes 32..40), bounded-memory refinement (reorth 2): each result is
+    the same alone and in the mix."""
+    from paper_2406_05020_gb300 import gpfvm
+    reqs = W.serving_wave_stream(rate=500.0, duration=1.0, lo=32, hi=40, seed=7, n_max=3)
+    kw = dict(max_iter=12000, rtol=1e-10, precision=2, reorth=2, want_var=True, inner_max_iter=400)
+    srv = gpfvm.Server(max_slots=3, **kw)
+    tickets = [srv.submit(p) for _, p in reqs]
+    guard = 0
+    while srv.step() > 0:
+        guard += 1
+        assert guard < 10000000
+    opts = gpfvm.solve_opts(**kw)
+    for t, (_, prob) in zip(tickets, reqs):
+        code, mean, var, info = srv.poll(t)
+        ref = _alone(prob, opts)
+        assert code == ref[0] and code in (0, 1), info.as_dict()
+        assert relerr(mean, ref[1]) < 1e-14
+        np.testing.assert_allclose(var, ref[2], rtol=0, atol=1e-14)
+    srv.close()
