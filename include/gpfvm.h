@@ -159,6 +159,13 @@ typedef struct {
   double inner_rtol;   /* mixed: residual reduction of one inner CG run (<= 0: 1e-2) */
   int inner_reorth_first; /* unused (kept for layout): with reorth every inner run continues one
                              G^-conjugate direction set (see gpfvm_solve) */
+  int coarse;          /* FP64 with reorth: multigrid warm start (appendix "Multigrid
+                          preconditioners") on coarse cells of coarse^ndim fine cells (every
+                          n_cells divisible by it, at most 4096 coarse cells): the coarse FVM
+                          observations are conditioned on exactly (Cholesky of W^T G^ W) and
+                          become the first stored actions, before CG on the fine cells;
+                          0 or 1 = off.  max_iter counts CG iterations only, and the problem's
+                          direction capacity must hold both. */
 } gpfvm_solve_opts;
 
 typedef struct {

@@ -2299,6 +2299,86 @@ std::map<const gpfvm_problem*, SolveRun>& runs() {
   return m;
 }
 
+// Multigrid warm start (appendix "Multigrid preconditioners"): the coarse FVM
+// observations W^T y (a coarse volume is the union of f^d fine ones) are
+// conditioned on exactly before CG.  With A_c = W^T G^ W = L_c L_c^T the
+// columns of W L_c^-T are G^-orthonormal actions; they are written as the
+// first n_c stored directions (eta = 1, their images G^ W L_c^-T beside them)
+// with their downdate, so that the Galerkin projection at the start of the CG
+// run is the exact coarse solve and every CG direction is made conjugate to
+// them by the usual reorthogonalisation.  Two passes of n_c operator
+// applications (A_c, then the directions); returns n_c or an error.
+int multigrid_setup(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
+  const int f = o->coarse;
+  CoarseGeom g{};
+  g.d = p->d;
+  g.f = f;
+  i64 nc = 1;
+  for (int i = 0; i < p->d; ++i) {
+    if (p->nc[i] % f) return GPFVM_ERR_INVALID_ARG;
+    g.n[i] = p->nc[i];
+    g.nc[i] = p->nc[i] / f;
+    nc *= g.nc[i];
+  }
+  if (nc > 4096 || nc + o->max_iter > p->cap64) return GPFVM_ERR_INVALID_ARG;
+  const int n = (int)nc;
+  const i64 N = p->N, ld = store_ld(N);
+  double *Ac = nullptr, *Lc = nullptr, *Li = nullptr, *scr = nullptr;
+  auto release = [&] {
+    if (Ac) cudaFree(Ac);
+    if (Lc) cudaFree(Lc);
+    if (Li) cudaFree(Li);
+    if (scr) cudaFree(scr);
+  };
+  try {
+    GPFVM_CUDA(cudaMalloc(&Ac, sizeof(double) * nc * nc));
+    GPFVM_CUDA(cudaMalloc(&Lc, sizeof(double) * nc * nc));
+    GPFVM_CUDA(cudaMalloc(&Li, sizeof(double) * nc * nc));
+    GPFVM_CUDA(cudaMalloc(&scr, sizeof(double) * (nc * nc / 4 + 64 * nc + 64)));
+    GPFVM_CUDA(cudaMemsetAsync(&p->d_st->done, 0, sizeof(int), st));  // the operator plans run
+    // pass 1: column c of A_c = W^T G^ (W e_c)
+    for (int c = 0; c < n; ++c) {
+      coarse_gather(p->d_p, N, g, nullptr, c, st);
+      p->p_mv_cg.run(st);
+      coarse_restrict(p->d_q, g, Ac + c, nc, st);
+    }
+    GPFVM_CUDA(cudaMemsetAsync(Lc, 0, sizeof(double) * nc * nc, st));
+    GPFVM_CUDA(cudaMemsetAsync(Li, 0, sizeof(double) * nc * nc, st));
+    GPFVM_CUDA(cudaMemsetAsync(&p->d_st->pad[0], 0, sizeof(int), st));
+    {
+      Plan ch;
+      plan_chol_inverse(ch, Ac, Lc, Li, n, nc, scr, &p->d_st->pad[0]);
+      ch.finalize();
+      ch.fan = &p->fan;
+      ch.run(st);
+    }
+    copy_header_to_host(p, st);
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+    if (p->h_st->pad[0] & DEV_NOT_SPD) {
+      release();
+      return GPFVM_ERR_NOT_SPD;
+    }
+    // pass 2: s_c = W L_c^-T e_c (row c of L_c^-1 spread over the fine cells),
+    // its image and its downdate (eta = 1)
+    const bool want_var = o->want_var != 0;
+    for (int c = 0; c < n; ++c) {
+      coarse_gather(p->d_S + (i64)c * ld, N, g, Li + (i64)c * nc, -1, st);
+      GPFVM_CUDA(cudaMemcpyAsync(p->d_p, p->d_S + (i64)c * ld, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      (want_var ? p->p_mvv_cg : p->p_mv_cg).run(st);
+      GPFVM_CUDA(cudaMemcpyAsync(p->d_Q + (i64)c * ld, p->d_q, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      if (want_var) add_squares(p->d_down, p->d_u, p->P, st);
+    }
+    std::vector<double> ones((size_t)n, 1.0);
+    GPFVM_CUDA(cudaMemcpyAsync(p->d_eta, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    GPFVM_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    release();
+    throw;
+  }
+  release();
+  return n;
+}
+
 int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
@@ -2314,14 +2394,32 @@ int solve_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
     GPFVM_CUDA(cudaEventCreate(&R.e1));
   }
   GPFVM_CUDA(cudaEventRecord(R.e0, st));
-  if (reorth) ensure_store64(p, o->max_iter);
+  // multigrid warm start: coarse actions stored ahead of the CG directions
+  i64 ncoarse = 0;
+  if (o->coarse > 1) {
+    if (!reorth) return GPFVM_ERR_INVALID_ARG;
+    ncoarse = 1;
+    for (int i = 0; i < p->d; ++i) ncoarse *= p->nc[i] / o->coarse;
+    if (ncoarse + o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
+  }
+  if (reorth) ensure_store64(p, (int)(o->max_iter + ncoarse));
+  if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  int kb = 0;
+  if (o->coarse > 1) {
+    kb = multigrid_setup(p, o, st);
+    if (kb < 0) return kb;
+  }
   p->h_st->rtol2 = o->rtol * o->rtol;
-  p->h_st->max_iter = o->max_iter;
+  p->h_st->max_iter = o->max_iter + kb;  // the CG budget excludes the coarse actions
   p->h_st->cap = reorth ? p->cap64 : 0;
+  p->h_st->kbase = kb;
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->rtol2, &p->h_st->rtol2, sizeof(double), cudaMemcpyHostToDevice, st));
   GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->max_iter, &p->h_st->max_iter, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
-  if (want_var) GPFVM_CUDA(cudaMemsetAsync(p->d_down, 0, sizeof(double) * p->P, st));
+  GPFVM_CUDA(cudaMemcpyAsync(&p->d_st->kbase, &p->h_st->kbase, sizeof(int), cudaMemcpyHostToDevice, st));
   cg_init(p->d_b, p->d_x, p->d_r, p->d_p, p->N, p->d_st, st);
+  if (kb > 0)  // x = the exact coarse solve, r and p projected
+    cg_project<double>(p->d_S, p->d_Q, p->d_r, p->d_x, p->d_p, p->N, p->cap64, p->d_st, p->d_part2, p->d_coef,
+                       p->d_eta, st);
   const int key = (reorth ? 1 : 0) + (want_var ? 2 : 0);
   if (!p->graph || p->graph_key != key) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -2381,7 +2479,7 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
   else if (h.status & DEV_BREAKDOWN) status = GPFVM_ERR_BREAKDOWN;
   else if (h.converged) status = GPFVM_OK;
   gpfvm_solve_info I = p->last;
-  I.iterations = h.k;
+  I.iterations = h.k - h.kbase;  // CG iterations (coarse actions of a multigrid start excluded)
   I.status = status;
   I.rel_residual = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
   I.t_solve_ms = ms;
@@ -2472,6 +2570,7 @@ int mixed_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
   if (!p->assembled) return GPFVM_ERR_STATE;
   if (!o || o->max_iter < 1 || !(o->rtol >= 0)) return GPFVM_ERR_INVALID_ARG;
   if (o->precision < GPFVM_MIXED_FP32 || o->precision > GPFVM_MIXED_BF16) return GPFVM_ERR_INVALID_ARG;
+  if (o->coarse > 1) return GPFVM_ERR_INVALID_ARG;  // the multigrid start is an FP64-path option
   MixedRun& R = mruns()[p];
   R.o = *o;
   R.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-2;
@@ -3450,6 +3549,7 @@ int graph_begin(gpfvm_problem* p, const gpfvm_solve_opts* o, cudaStream_t st) {
     return GPFVM_OK;
   }
   if (o->precision < GPFVM_MIXED_FP32 || o->precision > GPFVM_MIXED_BF16) return GPFVM_ERR_INVALID_ARG;
+  if (o->coarse > 1) return GPFVM_ERR_INVALID_ARG;  // the multigrid start is an FP64-path option
   if (o->reorth == 1 && o->max_iter > p->cap) return GPFVM_ERR_INVALID_ARG;
   const int want_tc = o->precision == GPFVM_MIXED_TF32X3 ? TC_TF32X3
                       : o->precision == GPFVM_MIXED_BF16X3 ? TC_BF16X3

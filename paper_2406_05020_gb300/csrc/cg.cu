@@ -619,6 +619,69 @@ void field_combine(void* out, i64 n, const FieldTerms& t, const void* D, double 
   else launch_pdl(k_field_combine<double>, g, RT, 0, s, (double*)out, n, t, (const double*)D, gamma, beta);
 }
 
+// ---- multigrid warm start --------------------------------------------------
+__device__ __forceinline__ i64 coarse_index(i64 i, const CoarseGeom& g) {
+  i64 c = 0, mul = 1;
+  for (int a = g.d - 1; a >= 0; --a) {
+    const i64 k = i % g.n[a];
+    i /= g.n[a];
+    c += (k / g.f) * mul;
+    mul *= g.nc[a];
+  }
+  return c;
+}
+__global__ void k_coarse_gather(double* __restrict__ p, i64 n, const CoarseGeom g, const double* __restrict__ row,
+                                i64 c) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) {
+    const i64 ci = coarse_index(i, g);
+    p[i] = row ? row[ci] : (ci == c ? 1.0 : 0.0);
+  }
+}
+void coarse_gather(double* p, i64 n, const CoarseGeom& g, const double* row, i64 c, cudaStream_t s) {
+  int gr = ceil_div(n, RT);
+  if (gr > 4096) gr = 4096;
+  k_coarse_gather<<<gr, RT, 0, s>>>(p, n, g, row, c);
+  GPFVM_LAUNCH_CHECK();
+}
+// one thread per coarse cell, its f^d fine cells summed in a fixed order
+__global__ void k_coarse_restrict(const double* __restrict__ v, const CoarseGeom g, double* __restrict__ out,
+                                  i64 stride, i64 nc) {
+  const i64 c = (i64)blockIdx.x * RT + threadIdx.x;
+  if (c >= nc) return;
+  int cc[3] = {0, 0, 0};
+  i64 r = c;
+  for (int a = g.d - 1; a >= 0; --a) {
+    cc[a] = (int)(r % g.nc[a]);
+    r /= g.nc[a];
+  }
+  const int f0 = g.f, f1 = g.d > 1 ? g.f : 1, f2 = g.d > 2 ? g.f : 1;
+  double acc = 0.0;
+  for (int a = 0; a < f0; ++a)
+    for (int b = 0; b < f1; ++b)
+      for (int e = 0; e < f2; ++e) {
+        int k[3] = {cc[0] * g.f + a, g.d > 1 ? cc[1] * g.f + b : 0, g.d > 2 ? cc[2] * g.f + e : 0};
+        i64 i = 0;
+        for (int ax = 0; ax < g.d; ++ax) i = i * g.n[ax] + k[ax];
+        acc += v[i];
+      }
+  out[c * stride] = acc;
+}
+void coarse_restrict(const double* v, const CoarseGeom& g, double* out, i64 stride, cudaStream_t s) {
+  i64 nc = 1;
+  for (int a = 0; a < g.d; ++a) nc *= g.nc[a];
+  k_coarse_restrict<<<ceil_div(nc, RT), RT, 0, s>>>(v, g, out, stride, nc);
+  GPFVM_LAUNCH_CHECK();
+}
+__global__ void k_add_squares(double* __restrict__ down, const double* __restrict__ u, i64 n) {
+  for (i64 i = (i64)blockIdx.x * RT + threadIdx.x; i < n; i += (i64)gridDim.x * RT) down[i] = fma(u[i], u[i], down[i]);
+}
+void add_squares(double* down, const double* u, i64 n, cudaStream_t s) {
+  int gr = ceil_div(n, RT);
+  if (gr > 4096) gr = 4096;
+  k_add_squares<<<gr, RT, 0, s>>>(down, u, n);
+  GPFVM_LAUNCH_CHECK();
+}
+
 // ---- device-driven mixed refinement --------------------------------------
 __global__ void k_mixed_ctl(MixedCtl* c, const CGState* s64, CGState* s32, cudaGraphConditionalHandle ho,
                             cudaGraphConditionalHandle hi) {

@@ -79,6 +79,18 @@ struct FieldTerms {
 void field_combine(void* out, i64 n, const FieldTerms& t, const void* D, double gamma, double beta, bool f32,
                    cudaStream_t s);
 
+// ---- multigrid warm start: coarse cells of `f`^d fine cells (row-major axes)
+struct CoarseGeom {
+  int d, f;
+  int n[3], nc[3];
+};
+// p[i] = row[coarse(i)] (row != null) or the indicator of coarse cell c
+void coarse_gather(double* p, i64 n, const CoarseGeom& g, const double* row, i64 c, cudaStream_t s);
+// out[c' * stride] = sum of v over the fine cells of coarse cell c' (the restriction W^T v)
+void coarse_restrict(const double* v, const CoarseGeom& g, double* out, i64 stride, cudaStream_t s);
+// down += u .* u
+void add_squares(double* down, const double* u, i64 n, cudaStream_t s);
+
 // ---- device-driven mixed refinement (one graph per solve, see api.cu) ----
 // The refinement decisions of the host-driven solver (residual test,
 // divergence guard, run tolerance, conjugate continuation bookkeeping) taken

@@ -54,7 +54,7 @@ class Desc(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("precision", C.c_int), ("reorth", C.c_int),
                 ("want_var", C.c_int), ("check_every", C.c_int), ("inner_max_iter", C.c_int),
-                ("inner_rtol", C.c_double), ("inner_reorth_first", C.c_int)]
+                ("inner_rtol", C.c_double), ("inner_reorth_first", C.c_int), ("coarse", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -212,12 +212,13 @@ def make_desc(prob):
 
 
 def solve_opts(max_iter=2000, rtol=1e-10, precision=FP64, reorth=True, want_var=True, check_every=16,
-               inner_max_iter=0, inner_rtol=1e-2, inner_reorth_first=False):
+               inner_max_iter=0, inner_rtol=1e-2, inner_reorth_first=False, coarse=0):
     o = SolveOpts()
     o.max_iter, o.rtol, o.precision = int(max_iter), float(rtol), int(precision)
     o.reorth, o.want_var, o.check_every = int(reorth), int(want_var), int(check_every)
     o.inner_max_iter, o.inner_rtol = int(inner_max_iter), float(inner_rtol)
     o.inner_reorth_first = int(inner_reorth_first)
+    o.coarse = int(coarse)
     return o
 
 
