@@ -111,7 +111,13 @@ typedef struct {
  *                  Hadamard product with the rank-one matrix of the two terms'
  *                  coefficients, applied as diagonal scalings.  Terms passing
  *                  the same pointer share one field.  Such problems run the
- *                  FP64 and FP32 SIMT operators (no tensor-core precisions). */
+ *                  FP64 and FP32 SIMT operators (no tensor-core precisions).
+ *   fp64_products  0: the FP64 CG iteration and the FP64 residual of the mixed
+ *                  solves apply G_PP on the tensor cores by exact digit
+ *                  products (FP64 matrix-product accuracy; every axis <= 128
+ *                  cells and constant coefficients, else FP64 FMA); 1: always
+ *                  FP64 FMA (SIMT) mode products.  Ops 0/1 of gpfvm_gram_matvec
+ *                  are FP64 FMA and ops 12/13 the digit-product form either way. */
 typedef struct {
   int ndim;
   int n_cells[GPFVM_MAX_DIM];
@@ -129,6 +135,7 @@ typedef struct {
   const double* pred[GPFVM_MAX_DIM];
   int observe;
   const double* coef_field[GPFVM_MAX_TERMS];
+  int fp64_products;
 } gpfvm_desc;
 
 /* Precision of the CG iteration. */
@@ -211,6 +218,13 @@ int gpfvm_assemble(gpfvm_problem* p, void* stream);
  *   op 7: out = G^ v, the inner operator of GPFVM_MIXED_TF32X3 (FP64 in/out)
  *   op 8 / op 9: G_PP / G^ (inner operator) in split bf16 (GPFVM_MIXED_BF16X3)
  *   op 10 / op 11: G_PP / G^ (inner operator) in one bf16 product (GPFVM_MIXED_BF16)
+ *   op 12 / op 13: G_PP / G^ in FP64 with the G_PP mode products computed on
+ *                  the bf16 tensor cores by exact digit products (every row of
+ *                  an operand split into 8 balanced 7-bit digits, the digit
+ *                  products accumulated exactly in FP32 and recombined in
+ *                  64-bit integers; the splitting of Ozaki et al. 2012):
+ *                  GPFVM_ERR_INVALID_ARG where an axis has more than 128 cells
+ *                  or a coefficient field is given
  * Ops 6, 7, 9 and 11 use the mixed solver's FP32 work vectors: not between the
  * begin and end of a solve on the same problem.  Requires gpfvm_assemble.  v and out must not overlap. */
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream);

@@ -23,6 +23,7 @@
 
 #include "cg.cuh"
 #include "kron.cuh"
+#include "oz.cuh"
 #include "tc.cuh"
 
 using namespace gpfvm;
@@ -261,6 +262,23 @@ struct gpfvm_problem {
   std::vector<TcLevel> tc_levels[6];  // instance 2 m + 0: f_p -> f_q, 2 m + 1: f_vin -> f_vout (TcMode m)
   i64 tc_split_total = 0, tc_ops_total = 0;
   int tc_nu = 0, tc_nw = 0;
+  // FP64 G_PP on the tensor cores by exact digit products (oz.cu): factor digit
+  // images, rotated FP64 intermediates, row exponents, op tables per instance
+  // (0: d_p -> d_q of the CG plans, 1: d_vin -> d_vout, 2: the same for the
+  // refinement residual, skipped with it)
+  bool oz_ok = false;   // every axis <= 128 cells, constant coefficients
+  bool oz_on = true;    // the FP64 CG and residual plans use it (desc fp64_products == 0)
+  struct OzJob { i64 fac_off; int n; double alpha; i64 img_off, fexp_off; };
+  std::vector<OzJob> oz_jobs;
+  struct OzLevel { int off, nops; i64 tiles; OzExpJobs jobs; };
+  std::vector<OzLevel> oz_levels[3];
+  OzOp* d_ozops = nullptr;
+  unsigned char* d_ozimg = nullptr;
+  int* d_ozfexp = nullptr;
+  int* d_ozexp = nullptr;
+  double *d_ozY = nullptr, *d_ozZ = nullptr;
+  i64 oz_ops_total = 0, oz_img_total = 0, oz_fexp_total = 0, oz_exp_total = 0;
+  int oz_nu = 0, oz_nw = 0;
   int cap64 = 0, cap32 = 0;  // directions the allocated stores hold
   CGState* d_st32 = nullptr;
   CGState* h_st32 = nullptr;
@@ -277,7 +295,7 @@ struct gpfvm_problem {
   // ---- plans
   Plan p_setup, p_chol, p_rhs, p_mv_cg, p_var_cg, p_mean, p_vB, p_tgt;
   Plan p_res;  // G^ x for the FP64 residual of the device-driven refinement (skipped on its first pass)
-  Plan p_op[4];
+  Plan p_op[6];  // ops 0-3, then 12 / 13 (G_PP / G^ with the digit-product G_PP)
   Plan p_mv32, p_var32, p_pp32, p_mvv_cg, p_mvv32;
   Plan p_mv32tc[3], p_mvv32tc[3], p_pp32tc[3];  // per TcMode
   int modeprods_pp = 0;
@@ -1322,6 +1340,212 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
   }
 }
 
+// FP64 G_PP on the tensor cores by exact digit products (oz.cu): the shared
+// three-level form with rotating axes of the tensor-core FP32 form, with FP64
+// tensors, a row-exponent pass before every level and factor digit images
+// sliced once per assembly.
+struct OzBuild {
+  gpfvm_problem* p;
+  std::vector<OzOp> ops;
+  std::map<std::pair<i64, double>, std::pair<i64, i64>> img;  // (factor offset, alpha) -> (image bytes, exponents)
+  i64 img_n = 0, fexp_n = 0, exp_n = 0;
+  bool ok = true;
+  std::pair<const unsigned char*, const int*> image(i64 fo, int n, double alpha) {
+    auto key = std::make_pair(fo, alpha);
+    auto it = img.find(key);
+    if (it == img.end()) {
+      it = img.emplace(key, std::make_pair(img_n, fexp_n)).first;
+      p->oz_jobs.push_back({fo, n, alpha, img_n, fexp_n});
+      img_n += oz_image_bytes(n, n);
+      fexp_n += (n + 31) / 32 * 32;
+    }
+    return {p->d_ozimg ? p->d_ozimg + it->second.first : nullptr,
+            p->d_ozfexp ? p->d_ozfexp + it->second.second : nullptr};
+  }
+};
+
+void build_oz_instance(gpfvm_problem* p, OzBuild& O, const double* in, double* out, int inst, const int* skip) {
+  const int d = p->d;
+  int n[3] = {1, 1, 1};
+  i64 Ntot = 1;
+  for (int i = 0; i < d; ++i) {
+    n[i] = p->nc[i];
+    Ntot *= n[i];
+    if (n[i] > OZ_KMAX) O.ok = false;
+  }
+  struct Term { double c; i64 f[3]; };
+  std::vector<Term> terms;
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b) {
+      Term t{p->coef[a] * p->coef[b], {0, 0, 0}};
+      for (int i = 0; i < d; ++i) t.f[i] = p->fac_off.at(FKey(i, 0, p->alpha[a][i], 0, p->alpha[b][i]));
+      terms.push_back(t);
+    }
+  auto& levels = p->oz_levels[inst];
+  levels.clear();
+  i64 exo = 0;  // exponent ints of this instance
+  auto begin_level = [&](i64 R, int K) {
+    gpfvm_problem::OzLevel L{};
+    L.off = (int)O.ops.size();
+    L.jobs.R = (int)R;
+    L.jobs.K = K;
+    L.jobs.skip = skip;
+    levels.push_back(L);
+  };
+  // row exponents of source tensor `A` (index `src` of the level's jobs)
+  auto job = [&](int src, const double* A) -> const int* {
+    auto& J = levels.back().jobs;
+    if (src >= OZ_MAXSEG) { O.ok = false; return nullptr; }
+    while (J.n <= src) {
+      J.A[J.n] = nullptr;
+      J.ex[J.n] = p->d_ozexp ? p->d_ozexp + exo : nullptr;
+      exo += ((i64)J.R + 31) / 32 * 32;
+      J.n++;
+    }
+    J.A[src] = A;
+    return J.ex[src];
+  };
+  auto blank = [&](i64 R, int K, int N, double* o) {
+    OzOp op{};
+    op.R = (int)R; op.K = K; op.N = N; op.out = o;
+    op.skip = skip;
+    return op;
+  };
+  auto seg = [&](OzOp& op, const double* A, const int* ex, i64 fo, int nf, double alpha) {
+    if (op.nseg >= OZ_MAXSEG) { O.ok = false; return; }
+    auto im = O.image(fo, nf, alpha);
+    op.A[op.nseg] = A;
+    op.Aexp[op.nseg] = ex;
+    op.Bimg[op.nseg] = im.first;
+    op.Bexp[op.nseg] = im.second;
+    op.nseg++;
+  };
+  auto add_op = [&](OzOp op) {
+    auto& L = levels.back();
+    op.tile_begin = L.tiles;
+    L.tiles += oz_tiles(op.R, op.N);
+    L.nops++;
+    if (op.N > 128 || op.K > OZ_KMAX) O.ok = false;
+    O.ops.push_back(op);
+  };
+  if (d == 1) {
+    begin_level(1, n[0]);
+    const int* ex = job(0, in);
+    OzOp op = blank(1, n[0], n[0], out);
+    for (auto& t : terms) seg(op, in, ex, t.f[0], n[0], p->s2 * t.c);
+    op.D = in;
+    op.gamma = p->jitter;
+    add_op(op);
+    O.exp_n = std::max(O.exp_n, exo);
+    return;
+  }
+  std::vector<i64> U, Wf;
+  std::vector<int> uo(terms.size()), wo(terms.size());
+  for (size_t k = 0; k < terms.size(); ++k) {
+    if (d == 3) {
+      auto it = std::find(U.begin(), U.end(), terms[k].f[2]);
+      uo[k] = (int)(it - U.begin());
+      if (it == U.end()) U.push_back(terms[k].f[2]);
+    }
+    auto jt = std::find(Wf.begin(), Wf.end(), terms[k].f[0]);
+    wo[k] = (int)(jt - Wf.begin());
+    if (jt == Wf.end()) Wf.push_back(terms[k].f[0]);
+  }
+  p->oz_nu = std::max(p->oz_nu, (int)U.size());
+  p->oz_nw = std::max(p->oz_nw, (int)Wf.size());
+  auto Y = [&](int u) { return p->d_ozY ? p->d_ozY + (i64)u * Ntot : nullptr; };
+  auto Z = [&](int w) { return p->d_ozZ ? p->d_ozZ + (i64)w * Ntot : nullptr; };
+  if (d == 3) {
+    begin_level((i64)n[0] * n[1], n[2]);
+    const int* ex = job(0, in);
+    for (size_t u = 0; u < U.size(); ++u) {
+      OzOp op = blank((i64)n[0] * n[1], n[2], n[2], Y((int)u));
+      seg(op, in, ex, U[u], n[2], 1.0);
+      add_op(op);
+    }
+  }
+  begin_level(d == 3 ? (i64)n[2] * n[0] : (i64)n[0], n[1]);
+  std::vector<const int*> exY;
+  if (d == 3)
+    for (size_t u = 0; u < U.size(); ++u) exY.push_back(job((int)u, Y((int)u)));
+  else
+    exY.push_back(job(0, in));
+  for (size_t w = 0; w < Wf.size(); ++w) {
+    OzOp op = blank(d == 3 ? (i64)n[2] * n[0] : (i64)n[0], n[1], n[1], Z((int)w));
+    std::vector<std::pair<std::pair<int, i64>, double>> acc;  // merged (source, factor) pairs
+    for (size_t k = 0; k < terms.size(); ++k) {
+      if (wo[k] != (int)w) continue;
+      const int src = (d == 3) ? uo[k] : 0;
+      bool merged = false;
+      for (auto& a : acc)
+        if (a.first.first == src && a.first.second == terms[k].f[1]) { a.second += terms[k].c; merged = true; }
+      if (!merged) acc.push_back({{src, terms[k].f[1]}, terms[k].c});
+    }
+    for (auto& a : acc) seg(op, d == 3 ? Y(a.first.first) : in, exY[a.first.first], a.first.second, n[1], a.second);
+    add_op(op);
+  }
+  begin_level(Ntot / n[0], n[0]);
+  OzOp op = blank(Ntot / n[0], n[0], n[0], out);
+  for (size_t w = 0; w < Wf.size(); ++w) seg(op, Z((int)w), job((int)w, Z((int)w)), Wf[w], n[0], p->s2);
+  op.D = in;
+  op.gamma = p->jitter;
+  add_op(op);
+  O.exp_n = std::max(O.exp_n, exo);
+}
+
+// The three instances and their op tables (counting pass: null buffers).
+void build_oz(gpfvm_problem* p) {
+  p->oz_jobs.clear();
+  for (auto& L : p->oz_levels) L.clear();
+  if (p->nfield > 0 || p->d < 2) {  // (one axis: a single row of up to 128 cells, FMA form)
+    p->oz_ok = false;
+    return;
+  }
+  OzBuild O{p};
+  build_oz_instance(p, O, p->d_p, p->d_q, 0, p->d_st ? &p->d_st->done : nullptr);
+  build_oz_instance(p, O, p->d_vin, p->d_vout, 1, nullptr);
+  build_oz_instance(p, O, p->d_vin, p->d_vout, 2, p->d_mctl ? &p->d_mctl->first : nullptr);
+  p->oz_ok = O.ok;
+  p->oz_ops_total = (i64)O.ops.size();
+  p->oz_img_total = O.img_n;
+  p->oz_fexp_total = O.fexp_n;
+  p->oz_exp_total = O.exp_n;
+  if (!p->d_ozops || !O.ok) return;
+  // host-side bounds check of every operand before any launch
+  for (const OzOp& op : O.ops) {
+    bool ok = p->mem.contains(op.out, 8LL * op.N * op.R) && (!op.D || p->mem.contains(op.D, 8LL * op.N * op.R));
+    ok = ok && op.nseg >= 1 && op.K >= 1 && op.K <= OZ_KMAX && op.N >= 1 && op.N <= 128;
+    for (int s = 0; s < op.nseg; ++s)
+      ok = ok && p->mem.contains(op.A[s], 8LL * op.R * op.K) && p->mem.contains(op.Aexp[s], 4LL * op.R) &&
+           p->mem.contains(op.Bimg[s], oz_image_bytes(op.N, op.K)) && p->mem.contains(op.Bexp[s], 4LL * op.N) &&
+           ((uintptr_t)op.Bimg[s] & 15) == 0;
+    if (!ok) throw CudaError{cudaErrorInvalidValue, "digit-product operand out of bounds"};
+  }
+  for (auto& lv : p->oz_levels)
+    for (auto& L : lv)
+      for (int j = 0; j < L.jobs.n; ++j)
+        if (!p->mem.contains(L.jobs.A[j], 8LL * L.jobs.R * L.jobs.K) || !p->mem.contains(L.jobs.ex[j], 4LL * L.jobs.R))
+          throw CudaError{cudaErrorInvalidValue, "digit-product exponent job out of bounds"};
+  GPFVM_CUDA(cudaMemcpy(p->d_ozops, O.ops.data(), sizeof(OzOp) * O.ops.size(), cudaMemcpyHostToDevice));
+}
+
+// G_PP of instance `inst` as FUNC ops (one per level: exponent pass + mode products).
+Plan oz_chain(gpfvm_problem* p, int inst) {
+  Plan c;
+  for (const auto& L : p->oz_levels[inst]) {
+    const OzExpJobs J = L.jobs;
+    const OzOp* ops = p->d_ozops + L.off;
+    const int nops = L.nops;
+    const i64 tiles = L.tiles;
+    int* status = &p->d_st->status;
+    c.func([=](cudaStream_t st) {
+      oz_row_exponents(J, st);
+      launch_oz_modes(ops, nops, tiles, status, st);
+    });
+  }
+  return c;
+}
+
 void build_plans(gpfvm_problem* p, Builder& B) {
   const i64 N = p->N, M = p->M, P = p->P;
   gpfvm_problem* pp_ = p;
@@ -1384,21 +1608,38 @@ void build_plans(gpfvm_problem* p, Builder& B) {
       B.pb(p->p_rhs, p->d_w, b, -1.0, true);
     }
   }
-  // ---- CG iteration plans (phased: independent mode products share launches)
+  // ---- CG iteration plans (phased: independent mode products share launches);
+  // G_PP by digit products on the tensor cores where available and chosen
+  build_oz(p);
+  const bool oz = p->oz_ok && p->oz_on && p->d_ozops;
   p->p_mv_cg = Plan();
   p->modeprods_pp = 0;
-  B.ghat_phased(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_w, nullptr, &p->modeprods_pp);
+  {
+    Plan c = oz ? oz_chain(p, 0) : Plan();
+    B.ghat_phased(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_w, nullptr, &p->modeprods_pp, oz ? &c : nullptr);
+  }
   p->p_mvv_cg = Plan();
-  B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr);
+  {
+    Plan c = oz ? oz_chain(p, 0) : Plan();
+    B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr, oz ? &c : nullptr);
+  }
   p->p_var_cg = Plan();
   B.to_pred_cells(p->p_var_cg, p->d_p, p->d_u, 1.0, false);
   if (M > 0) B.to_pred_sets(p->p_var_cg, p->d_w, p->d_u, -1.0, true, true);
   // ---- operator plans for gpfvm_gram_matvec / true residual
-  for (int k = 0; k < 4; ++k) p->p_op[k] = Plan();
+  for (int k = 0; k < 6; ++k) p->p_op[k] = Plan();
   B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
   B.ghat_phased(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
+  if (p->oz_ok && p->d_ozops) {
+    p->p_op[4] = oz_chain(p, 1);
+    Plan c = oz_chain(p, 1);
+    B.ghat_phased(p->p_op[5], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr, &c);
+  }
   p->p_res = Plan();
-  B.ghat_phased(p->p_res, p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
+  {
+    Plan c = oz ? oz_chain(p, 2) : Plan();
+    B.ghat_phased(p->p_res, p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr, oz ? &c : nullptr);
+  }
   if (M > 0) {
     B.bp(p->p_op[2], p->d_vin, p->d_wout);
     B.pb(p->p_op[3], p->d_win, p->d_vout, 1.0, false);
@@ -1693,9 +1934,9 @@ void finalize_plans(gpfvm_problem* p) {
   p->p_var32.skip = &p->d_st32->done;
   std::vector<Plan*> all = {&p->p_setup, &p->p_chol, &p->p_rhs, &p->p_mv_cg, &p->p_var_cg, &p->p_mean, &p->p_vB,
                             &p->p_op[0], &p->p_op[1], &p->p_op[2], &p->p_op[3], &p->p_mv32, &p->p_var32, &p->p_pp32,
-                            &p->p_mvv_cg, &p->p_mvv32, &p->p_tgt, &p->p_res};
+                            &p->p_mvv_cg, &p->p_mvv32, &p->p_tgt, &p->p_res, &p->p_op[4], &p->p_op[5]};
   std::vector<std::string> names = {"setup", "chol", "rhs", "mv_cg", "var_cg", "mean", "vB", "op0", "op1", "op2",
-                                    "op3", "mv32", "var32", "pp32", "mvv_cg", "mvv32", "tgt", "res"};
+                                    "op3", "mv32", "var32", "pp32", "mvv_cg", "mvv32", "tgt", "res", "op12", "op13"};
   p->p_res.skip = &p->d_mctl->first;
   for (int m = 0; m < 3; ++m) {
     all.push_back(&p->p_mv32tc[m]);
@@ -1735,6 +1976,7 @@ int validate(const gpfvm_desc* D) {
   if (!(D->outputscale > 0) || !(D->jitter >= 0) || !std::isfinite(D->outputscale) || !std::isfinite(D->jitter))
     return GPFVM_ERR_INVALID_ARG;
   if (D->observe != 0 && D->observe != 1) return GPFVM_ERR_INVALID_ARG;
+  if (D->fp64_products != 0 && D->fp64_products != 1) return GPFVM_ERR_INVALID_ARG;
   i64 N = 1, P = 1;
   for (int i = 0; i < D->ndim; ++i) {
     if (D->n_cells[i] < 1 || D->n_cells[i] > 65536 || !D->edges[i]) return GPFVM_ERR_INVALID_ARG;
@@ -2033,6 +2275,14 @@ void alloc_all(gpfvm_problem* p) {
   p->f_tcpart = m.alloc<float>(std::max<i64>(p->tc_part_total, 64));
   p->d_tcops = m.alloc<TcOp>(std::max<i64>(p->tc_ops_total, 1));
   p->tc_jobs.clear();
+  if (p->oz_ok) {
+    p->d_ozops = m.alloc<OzOp>(std::max<i64>(p->oz_ops_total, 1));
+    p->d_ozimg = m.alloc<unsigned char>(std::max<i64>(p->oz_img_total, 256));
+    p->d_ozfexp = m.alloc<int>(std::max<i64>(p->oz_fexp_total, 64));
+    p->d_ozexp = m.alloc<int>(std::max<i64>(p->oz_exp_total, 64));
+    p->d_ozY = m.alloc<double>(std::max<i64>((i64)p->oz_nu * N, 64));
+    p->d_ozZ = m.alloc<double>(std::max<i64>((i64)p->oz_nw * N, 64));
+  }
   p->scratch_cap = std::max<i64>(B0.peak, 64);
   p->d_scratch = m.alloc<double>(p->scratch_cap);
   Builder B{p};
@@ -2083,6 +2333,9 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
     if (p->h_st->pad[0] & DEV_NOT_SPD) return GPFVM_ERR_NOT_SPD;
   }
   p->p_rhs.run(st);
+  if (p->oz_ok && p->d_ozimg)
+    for (const auto& j : p->oz_jobs)
+      oz_split_factor(p->d_fac + j.fac_off, j.n, j.n, j.alpha, p->d_ozimg + j.img_off, p->d_ozfexp + j.fexp_off, st);
   convert_d2f(p->d_fac, p->f_fac, p->nfac, st);
   for (auto& j : p->tc_jobs) {
     const i64 n = std::get<2>(j), off = std::get<3>(j);
@@ -2197,9 +2450,13 @@ void cg_iteration(gpfvm_problem* p, bool reorth, bool want_var, cudaStream_t st)
   if (reorth) cg_reorth(p->d_S, p->d_Q, p->d_p, N, p->cap64, p->d_st, p->d_part2, p->d_coef, p->d_eta, st);
 }
 
+// The FP64 G^ of residuals and refinement: with the digit-product G_PP when the
+// CG plans use it (the same operator as the captured refinement's p_res).
+Plan& fp64_ghat(gpfvm_problem* p) { return (p->oz_ok && p->oz_on && p->d_ozops) ? p->p_op[5] : p->p_op[1]; }
+
 double true_rel_residual(gpfvm_problem* p, const double* x, cudaStream_t st) {
   GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, x, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, st));
-  p->p_op[1].run(st);
+  fp64_ghat(p).run(st);
   axpby(p->d_b, p->d_vout, p->d_vout, 1.0, -1.0, p->N, st);
   norm2(p->d_vout, p->N, &p->d_st->aux[0], p->d_st, st);
   copy_header_to_host(p, st);
@@ -2622,7 +2879,7 @@ void mixed_launch(gpfvm_problem* p, int, cudaStream_t st) {
       GPFVM_CUDA(cudaMemcpyAsync(p->d_r, p->d_b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     } else {
       GPFVM_CUDA(cudaMemcpyAsync(p->d_vin, p->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      p->p_op[1].run(st);
+      fp64_ghat(p).run(st);
       axpby(p->d_b, p->d_vout, p->d_r, 1.0, -1.0, N, st);
     }
     norm2(p->d_r, N, &p->d_st->aux[0], p->d_st, st);
@@ -2816,6 +3073,7 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
   p->s2 = D->outputscale;
   p->jitter = D->jitter;
   p->colloc = D->observe == 1;
+  p->oz_on = D->fp64_products == 0;
   p->nterms = D->n_terms;
   {
     std::vector<const double*> seen;
@@ -2965,10 +3223,11 @@ bool op_uses_tc(int op) { return op == 5 || op >= 7; }
 extern "C" {
 
 int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, void* stream) {
-  if (!p || !v || !out || op < 0 || op > 11) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || op < 0 || op > 13) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
   if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (op >= 12 && !p->oz_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
   bool inner = false;
@@ -2990,19 +3249,23 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
   double* in = (op == 3) ? p->d_win : p->d_vin;
   double* res = (op == 2) ? p->d_wout : p->d_vout;
   GPFVM_CUDA(cudaMemcpyAsync(in, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
-  p->p_op[op].run(st);
+  if (op >= 12) GPFVM_CUDA(cudaMemsetAsync(&p->d_st->status, 0, sizeof(int), st));
+  p->p_op[op >= 12 ? op - 8 : op].run(st);
   GPFVM_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * nout, cudaMemcpyDeviceToDevice, st));
+  if (op >= 12) GPFVM_CUDA(cudaMemcpyAsync(p->h_st, p->d_st, offsetof(CGState, part), cudaMemcpyDeviceToHost, st));
   GPFVM_CUDA(cudaStreamSynchronize(st));
+  if (op >= 12 && (p->h_st->status & DEV_TIMEOUT)) return GPFVM_ERR_TIMEOUT;
   return GPFVM_OK;
   GPFVM_GUARD_END
 }
 
 int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* out, int reps, void* stream,
                             double* ms_per_application) {
-  if (!p || !v || !out || !ms_per_application || reps < 1 || op < 0 || op > 11) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !v || !out || !ms_per_application || reps < 1 || op < 0 || op > 13) return GPFVM_ERR_INVALID_ARG;
   if (!p->assembled) return GPFVM_ERR_STATE;
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
   if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
+  if (op >= 12 && !p->oz_ok) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
   bool inner = false;
@@ -3019,9 +3282,9 @@ int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* o
     convert_d2f(v, inner ? p->f_p : p->f_vin, p->N, st);
   } else {
     GPFVM_CUDA(cudaMemcpyAsync(op == 3 ? p->d_win : p->d_vin, v, sizeof(double) * nin, cudaMemcpyDeviceToDevice, st));
-    plan = &p->p_op[op];
+    plan = &p->p_op[op >= 12 ? op - 8 : op];
   }
-  const bool is32 = op >= 4;
+  const bool is32 = op >= 4 && op <= 11;
   // one application as a CUDA graph, replayed reps times between events
   cudaGraph_t g = nullptr;
   const long long before = g_launches.load();

@@ -1,0 +1,460 @@
+// FP64 Kronecker mode products on the 5th-generation tensor cores by exact
+// digit products.
+//
+// Method: the error-free splitting of a matrix product into exactly computed
+// partial products (Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012),
+// in the fixed-point form of its integer-unit variant (Ootomo, Ozaki and
+// Yokota, IJHPCA 2024).  Every row of an FP64 operand is scaled by a power of
+// two, taken from the row's largest exponent, into a 55-bit integer
+//   X = sum_j d_j 2^(49 - 7 j),   j = 0..7,
+// with balanced digits d_j in [-64, 64].  A digit is exact in bf16, a product
+// of two digits is exact in FP32 (|d d'| <= 2^12), and for K <= 128 each of
+// the 8 "diagonals"
+//   acc_d[r][c] = sum_k sum_{a + b = d} dA_a[r][k] dB_b[c][k]        (d = 0..7)
+// (at most 8 products per k) stays within 2^22, so tcgen05.mma (kind::f16,
+// bf16 inputs, FP32 accumulators in TMEM) computes it exactly.  The diagonals
+// are recombined in 64-bit fixed point (the least significant through
+// truncating shifts), the segments of a sum are aligned on the grid of the
+// largest segment scale max_s 2^(E_s + F_s) of each output (row and column
+// exponents of different segments do not add up), and the total is rounded
+// once to FP64.  Pairs with a + b >= 8 are dropped;
+// with the digit truncation the error of one output stays near 2^-54 of
+// K max_k|A[r][k]| max_k|B[c][k]| summed over the segments (FP64
+// matrix-product accuracy).  The FP64 FMA rate of this part is about 1/70 of
+// its dense bf16 tensor rate.
+//
+// Per CTA (256 threads; one CTA per SM: its 512 TMEM columns hold 8 diagonals
+// x 64 output columns): one tile = 128 tensor rows x 64 output columns of one
+// op.  For every (segment, 32-wide K block) stage, thread 0 starts a bulk copy
+// (cp.async.bulk, mbarrier transaction count) of the stage's pre-sliced factor
+// digit planes into shared memory, all threads slice the FP64 tensor rows into
+// 8 bf16 digit planes (64-byte-swizzled K-major rows), and thread 0 issues
+// 2 x 36 MMAs (M = 128, N = 64, K = 16) into the 8 diagonal accumulators.  Two
+// operand sets: the next stage is sliced while the MMAs of the current one
+// run.  After the last K block of a segment the accumulators are drained into
+// per-thread 64-bit sums.  All waits are bounded; a timeout sets *status and
+// the kernel returns after its outstanding copies and MMAs and freeing TMEM.
+#include <algorithm>
+
+#include "oz.cuh"
+#include "tc_tile.cuh"
+
+namespace gpfvm {
+
+constexpr int OZ_THREADS = 256;
+constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
+constexpr int OZ_DYN_SMEM = 2 * OZ_SET + 1024;
+
+i64 oz_image_bytes(int N, int K) {
+  const int nh = (N + OZ_COLS - 1) / OZ_COLS, nkb = (K + OZ_KB - 1) / OZ_KB;
+  return (i64)nkb * nh * OZ_IMG_STAGE;
+}
+
+i64 oz_tiles(int R, int N) { return (i64)((R + OZ_ROWS - 1) / OZ_ROWS) * ((N + OZ_COLS - 1) / OZ_COLS); }
+
+__device__ __forceinline__ int oz_field(unsigned long long bits) { return (int)((bits >> 52) & 0x7ff); }
+
+// |a| (bit pattern `bits`) as a 55-bit integer on the grid of a row whose
+// largest exponent field is emax (zero, subnormal and tiny values give 0)
+__device__ __forceinline__ unsigned long long oz_fix(unsigned long long bits, int emax) {
+  const int e = oz_field(bits);
+  const int sh = max(emax - e, 0);
+  if (e == 0 || sh > 54) return 0ull;
+  return (((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2) >> sh;
+}
+
+// balanced base-128 digits of X < 2^55: X = sum_j d_j 2^(49 - 7 j), d_j in [-64, 64]
+__device__ __forceinline__ void oz_digits(unsigned long long X, int d[OZ_DIGITS]) {
+  const uint32_t hi = (uint32_t)(X >> 32), lo = (uint32_t)X;
+  uint32_t raw[OZ_DIGITS];
+  raw[0] = hi >> 17;
+  raw[1] = (hi >> 10) & 127u;
+  raw[2] = (hi >> 3) & 127u;
+  raw[3] = ((hi & 7u) << 4) | (lo >> 28);
+  raw[4] = (lo >> 21) & 127u;
+  raw[5] = (lo >> 14) & 127u;
+  raw[6] = (lo >> 7) & 127u;
+  raw[7] = lo & 127u;
+  int carry = 0;
+#pragma unroll
+  for (int j = OZ_DIGITS - 1; j >= 1; --j) {
+    const int t = (int)raw[j] + carry;
+    carry = t >= 64 ? 1 : 0;
+    d[j] = t - (carry << 7);
+  }
+  d[0] = (int)raw[0] + carry;
+}
+
+// FP32 bit pattern of the integer v (|v| <= 2^22) with the sign bit flipped
+// by negbit; its upper half is the bf16 pattern of the same value
+__device__ __forceinline__ uint32_t oz_f32bits(int v, uint32_t negbit) {
+  return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f) ^ negbit;
+}
+
+// integer value of an FP32 accumulator holding an integer of magnitude <= 2^22
+__device__ __forceinline__ int oz_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
+// S * 2^T rounded to nearest FP64 (S != 0 assumed small enough: |S| < 2^62)
+__device__ __forceinline__ double oz_to_double(long long S, int T) {
+  if (S == 0) return 0.0;
+  const unsigned long long neg = S < 0 ? 1ull : 0ull;
+  const unsigned long long u = neg ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int p = 63 - __clzll((long long)u);
+  unsigned long long mant;
+  int ex = p + T;
+  if (p <= 52) {
+    mant = u << (52 - p);
+  } else {
+    const int sh = p - 52;
+    mant = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++ex;
+      }
+    }
+  }
+  const int biased = ex + 1023;
+  if (biased <= 0) return neg ? -0.0 : 0.0;  // below the normal range
+  if (biased >= 2047) return __longlong_as_double((long long)((neg << 63) | (0x7FFull << 52)));
+  return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ void oz_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void oz_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// largest exponent field of every row of the jobs' R x K tensors (one warp per row)
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(const __grid_constant__ OzExpJobs J) {
+  pdl_wait();
+  if (J.skip && *J.skip) return;
+  const int lane = threadIdx.x & 31;
+  const i64 total = (i64)J.n * J.R, nwarps = (i64)gridDim.x * 8;
+  for (i64 w = (i64)blockIdx.x * 8 + (threadIdx.x >> 5); w < total; w += nwarps) {
+    const int job = (int)(w / J.R);
+    const i64 r = w - (i64)job * J.R;
+    const double* __restrict__ row = J.A[job] + r * J.K;
+    int e = 0;
+    for (int k = lane; k < J.K; k += 32) e = max(e, oz_field((unsigned long long)__double_as_longlong(__ldg(row + k))));
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0) J.ex[job][r] = e;
+  }
+}
+
+void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st) {
+  const i64 rows = (i64)jobs.n * jobs.R;
+  if (rows <= 0) return;
+  const int grid = (int)std::min<i64>((rows + 7) / 8, 8 * 152);
+  launch_pdl(oz_rowexp_kernel, grid, 256, 0, st, jobs);
+}
+
+// digit image of alpha F (one warp per row j): plane l of (K block kb, column
+// half h) at img + ((kb * nh + h) * 8 + l) * OZ_B_PLANE, 64-byte-swizzled rows
+__global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ F, int N, int K, double alpha,
+                                                       unsigned char* __restrict__ img, int* __restrict__ fexp) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= N) return;  // whole warps
+  const int nh = (N + OZ_COLS - 1) / OZ_COLS;
+  int e = 0;
+  for (int k = lane; k < K; k += 32) e = max(e, oz_field((unsigned long long)__double_as_longlong(alpha * F[(i64)j * K + k])));
+  e = __reduce_max_sync(0xffffffffu, e);
+  if (lane == 0) fexp[j] = e;
+  for (int k = lane; k < K; k += 32) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(alpha * F[(i64)j * K + k]);
+    int d[OZ_DIGITS];
+    oz_digits(oz_fix(bits, e), d);
+    const uint32_t neg = (uint32_t)(bits >> 63) << 31;
+    unsigned char* blk = img + ((i64)(k / OZ_KB) * nh + j / OZ_COLS) * OZ_IMG_STAGE;
+    const uint32_t off = sw64(j % OZ_COLS, k % OZ_KB);
+#pragma unroll
+    for (int l = 0; l < OZ_DIGITS; ++l)
+      *(unsigned short*)(blk + l * OZ_B_PLANE + off) = (unsigned short)(oz_f32bits(d[l], neg) >> 16);
+  }
+}
+
+void oz_split_factor(const double* F, int N, int K, double alpha, unsigned char* img, int* fexp, cudaStream_t st) {
+  if (N <= 0 || K <= 0) return;
+  GPFVM_CUDA(cudaMemsetAsync(img, 0, oz_image_bytes(N, K), st));
+  oz_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(F, N, K, alpha, img, fexp);
+  GPFVM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __restrict__ ops, int nops, i64 total,
+                                                               int* status) {
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t mma_bar[2], full_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int s_es[OZ_MAXSEG][OZ_ROWS], s_fs[OZ_MAXSEG][OZ_COLS];
+  __shared__ int s_emax[OZ_ROWS], s_fmax[OZ_COLS];
+  // per output: how far the largest segment scale 2^(E_s + F_s) lies below 2^(emax + fmax)
+  __shared__ unsigned char s_del[OZ_ROWS][OZ_COLS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(OZ_DIGITS * OZ_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[b])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  pdl_wait();  // TMEM and the barriers are set up while the previous kernel drains
+
+  // per-set pipeline state (the same in every thread)
+  uint32_t mph0 = 0, mph1 = 0, fph0 = 0, fph1 = 0;
+  int mpend0 = 0, mpend1 = 0, fpend0 = 0, fpend1 = 0;
+  auto wait_mma = [&](int b) {
+    const bool ok = b ? mbar_wait(&mma_bar[1], mph1) : mbar_wait(&mma_bar[0], mph0);
+    if (b) { mph1 ^= 1u; mpend1 = 0; } else { mph0 ^= 1u; mpend0 = 0; }
+    if (!ok) {
+      atomicOr(status, (int)DEV_TIMEOUT);
+      abort_flag = 1;
+    }
+  };
+  const uint32_t idesc = idesc_bf16(OZ_COLS);
+  const int q = warp & 3, ch = warp >> 2;     // drain / epilogue: TMEM lane quadrant, 32-column half
+  const int srow = tid >> 1, kh = tid & 1;    // staging: tile row, 16-wide half of the K block
+
+  for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
+    if (abort_flag) break;
+    int lo = 0, hi = nops - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ops[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const OzOp& op = ops[lo];
+    if (op.skip && *op.skip) continue;
+    const int R = op.R, K = op.K, N = op.N, nseg = op.nseg;
+    const int nh = (N + OZ_COLS - 1) / OZ_COLS;
+    const i64 local = t - op.tile_begin;
+    const int h = (int)(local % nh);
+    const int row0 = (int)(local / nh) * OZ_ROWS;
+    for (int i = tid; i < nseg * OZ_ROWS; i += OZ_THREADS) {
+      const int s = i / OZ_ROWS, r = i % OZ_ROWS;
+      s_es[s][r] = (row0 + r < R) ? op.Aexp[s][row0 + r] : 0;
+    }
+    for (int i = tid; i < nseg * OZ_COLS; i += OZ_THREADS) {
+      const int s = i / OZ_COLS, c = i % OZ_COLS, j = h * OZ_COLS + c;
+      s_fs[s][c] = (j < N) ? op.Bexp[s][j] : 0;
+    }
+    __syncthreads();
+    if (tid < OZ_ROWS) {
+      int m = 0;
+      for (int s = 0; s < nseg; ++s) m = max(m, s_es[s][tid]);
+      s_emax[tid] = m;
+    } else if (tid < OZ_ROWS + OZ_COLS) {
+      int m = 0;
+      for (int s = 0; s < nseg; ++s) m = max(m, s_fs[s][tid - OZ_ROWS]);
+      s_fmax[tid - OZ_ROWS] = m;
+    }
+    if (nseg > 1) {
+      // the sums are kept on the grid of max_s (E_s + F_s), not of emax + fmax:
+      // segments with the largest row and column exponents need not coincide
+      __syncthreads();
+      for (int i = tid; i < OZ_ROWS * OZ_COLS; i += OZ_THREADS) {
+        const int r = i / OZ_COLS, c = i % OZ_COLS;
+        int tmax = 0;
+        for (int s = 0; s < nseg; ++s) tmax = max(tmax, s_es[s][r] + s_fs[s][c]);
+        s_del[r][c] = (unsigned char)min(s_emax[r] + s_fmax[c] - tmax, 255);
+      }
+    }
+    const int nkb = (K + OZ_KB - 1) / OZ_KB;
+    const int nstage = nseg * nkb;
+    // fixed point of the sums: value = S * 2^(EA + EB - 2056 - G); |one segment's
+    // sum| < 1.02 * 2^(19 + G), so G = 43 - ceil(log2 nseg) keeps |S| < 2^62.1
+    const int G = 43 - (nseg > 1 ? 32 - __clz(nseg - 1) : 0);
+    long long S[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) S[i] = 0;
+    double ra[16];
+    auto load_stage = [&](int st2) {
+      const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * 16;
+      const double* __restrict__ A = op.A[s];
+      const int gr = row0 + srow;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = k0 + i;
+        ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
+      }
+    };
+    load_stage(0);
+    for (int st = 0; st < nstage; ++st) {
+      const int s = st / nkb, kb = st % nkb, b = st & 1;
+      if (b ? mpend1 : mpend0) wait_mma(b);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* sA = base + b * OZ_SET;
+      unsigned char* sB = sA + OZ_DIGITS * OZ_A_PLANE;
+      if (tid == 0) {
+        uint64_t* fb = b ? &full_bar[1] : &full_bar[0];
+        oz_expect_tx(fb, OZ_IMG_STAGE);
+        oz_bulk_copy(sB, op.Bimg[s] + ((i64)kb * nh + h) * OZ_IMG_STAGE, OZ_IMG_STAGE, fb);
+      }
+      if (b) fpend1 = 1; else fpend0 = 1;
+      // slice this thread's 16 values of its row into the 8 digit planes
+      const int emax = s_es[s][srow];
+#pragma unroll
+      for (int q2 = 0; q2 < 2; ++q2) {
+        uint32_t w[OZ_DIGITS][4];
+#pragma unroll
+        for (int p2 = 0; p2 < 4; ++p2) {
+          const unsigned long long b0 = (unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2]);
+          const unsigned long long b1 = (unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2 + 1]);
+          int d0[OZ_DIGITS], d1[OZ_DIGITS];
+          oz_digits(oz_fix(b0, emax), d0);
+          oz_digits(oz_fix(b1, emax), d1);
+          const uint32_t n0 = (uint32_t)(b0 >> 63) << 31, n1 = (uint32_t)(b1 >> 63) << 31;
+#pragma unroll
+          for (int j = 0; j < OZ_DIGITS; ++j) w[j][p2] = __byte_perm(oz_f32bits(d0[j], n0), oz_f32bits(d1[j], n1), 0x7632);
+        }
+        const uint32_t off = sw64(srow, kh * 16 + q2 * 8);
+#pragma unroll
+        for (int j = 0; j < OZ_DIGITS; ++j)
+          *(uint4*)(sA + j * OZ_A_PLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (abort_flag) break;
+      if (tid == 0) {
+        const bool ok = b ? mbar_wait(&full_bar[1], fph1) : mbar_wait(&full_bar[0], fph0);
+        if (!ok) {
+          atomicOr(status, (int)DEV_TIMEOUT);
+          abort_flag = 1;
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int ksteps = (min(OZ_KB, K - kb * OZ_KB) + 15) / 16;
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t koff = ks * 32;  // 16 bf16 = 32 bytes inside the 64-byte row
+#pragma unroll
+            for (int d = 0; d < OZ_DIGITS; ++d) {
+#pragma unroll
+              for (int a = 0; a <= d; ++a) {
+                const uint64_t da = desc_sw64(smem_u32(sA + a * OZ_A_PLANE) + koff);
+                const uint64_t db = desc_sw64(smem_u32(sB + (d - a) * OZ_B_PLANE) + koff);
+                mma_bf16(tmem + d * OZ_COLS, da, db, idesc, (kb > 0 || ks > 0 || a > 0) ? 1u : 0u);
+              }
+            }
+          }
+        }
+        mma_commit(b ? &mma_bar[1] : &mma_bar[0]);
+      }
+      if (b) { fph1 ^= 1u; fpend1 = 0; mpend1 = 1; } else { fph0 ^= 1u; fpend0 = 0; mpend0 = 1; }
+      if (st + 1 < nstage) load_stage(st + 1);  // overlaps the MMAs
+      if (kb == nkb - 1) {
+        // segment s complete: add its diagonals, aligned to the tile's exponents, to S
+        if (mpend0) wait_mma(0);
+        if (mpend1) wait_mma(1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = q * 32 + lane;
+        const int shA = s_emax[row] - s_es[s][row];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          long long V[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) V[i] = 0;
+#pragma unroll
+          for (int d = 0; d < OZ_DIGITS; ++d) {
+            uint32_t v[8];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * OZ_COLS + ch * 32 + cc * 8);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const long long a = (long long)oz_int(v[i]);
+              V[i] += 7 * d <= G ? (a << (G - 7 * d)) : (a >> (7 * d - G));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int col = ch * 32 + cc * 8 + i;
+            const int sh = shA + s_fmax[col] - s_fs[s][col] - (nseg > 1 ? (int)s_del[row][col] : 0);
+            if (sh < 62) S[cc * 8 + i] += V[i] >> sh;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // the next segment's MMAs overwrite the accumulators
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+    }
+    if (!abort_flag) {
+      const int row = q * 32 + lane, gr = row0 + row;
+      if (gr < R) {
+        const int EA = s_emax[row];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ch * 32 + i, j = h * OZ_COLS + col;
+          if (j < N) {
+            const int EB = s_fmax[col];
+            const int del = nseg > 1 ? (int)s_del[row][col] : 0;
+            double val = (EA == 2047 || EB == 2047) ? __longlong_as_double(0x7FF8000000000000LL)
+                                                    : oz_to_double(S[i], EA + EB - del - 2056 - G);
+            const i64 o = (i64)j * R + gr;
+            if (op.D) val = fma(op.gamma, op.D[o], val);
+            if (op.beta != 0.0) val = fma(op.beta, op.out[o], val);
+            op.out[o] = val;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // after a timeout: let the outstanding copies and MMAs land (bounded) before freeing TMEM
+  if (tid == 0) {
+    if (fpend0) mbar_wait(&full_bar[0], fph0);
+    if (fpend1) mbar_wait(&full_bar[1], fph1);
+  }
+  if (mpend0) mbar_wait(&mma_bar[0], mph0);
+  if (mpend1) mbar_wait(&mma_bar[1], mph1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_DIGITS * OZ_COLS)
+                 : "memory");
+  }
+}
+
+void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, cudaStream_t st) {
+  if (nops <= 0 || total_tiles <= 0) return;
+  static int sms = 0;
+  static bool attr = false;
+  if (!attr) {
+    int dev = 0;
+    GPFVM_CUDA(cudaGetDevice(&dev));
+    GPFVM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GPFVM_CUDA(cudaFuncSetAttribute(oz_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_DYN_SMEM));
+    attr = true;
+  }
+  const int grid = (int)std::min<i64>(total_tiles, std::max(sms, 1));
+  launch_pdl(oz_mode_kernel, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+}
+
+}  // namespace gpfvm

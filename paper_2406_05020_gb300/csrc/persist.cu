@@ -176,8 +176,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) persist_kernel(PProgDev prog) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  TcCtx cx{sm, sm + TC_A_BYTES, sm + 2 * TC_A_BYTES, sm + 2 * TC_A_BYTES + prog.tc_cols * 128,
-           &bar, prog.tc_cols > 0 ? tmem_slot : 0u, 0u, &abort_flag, prog.status};
+  TcCtx cx{};
+  for (int b = 0; b < 2; ++b) {  // one operand set (the persistent kernel's shared memory budget)
+    cx.sAhi[b] = sm;
+    cx.sAlo[b] = sm + TC_A_BYTES;
+    cx.sBhi[b] = sm + 2 * TC_A_BYTES;
+    cx.sBlo[b] = sm + 2 * TC_A_BYTES + prog.tc_cols * 128;
+    cx.bar[b] = &bar;
+    cx.phase[b] = 0u;
+  }
+  cx.nbuf = 1;
+  cx.tmem = prog.tc_cols > 0 ? tmem_slot : 0u;
+  cx.abort_flag = &abort_flag;
+  cx.status = prog.status;
   // a converged CG (the plan's skip flag, written before this launch) runs nothing
   const bool skip_all = prog.skip && *prog.skip;
   for (int ph = 0; ph < prog.nphases && !skip_all; ++ph) {

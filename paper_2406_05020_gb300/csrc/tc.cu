@@ -24,16 +24,19 @@
 // tcgen05.ld (one row per thread) and stores it transposed (coalesced).
 // All mbarrier waits are bounded; a timeout sets *status and the kernel
 // drains and frees its TMEM before returning.
+#include <cstdlib>
+
 #include "tc_tile.cuh"
 
 namespace gpfvm {
 
 __global__ void __launch_bounds__(128, 1) tc_mode_kernel(const TcOp* __restrict__ ops, int nops, i64 total,
-                                                         int ncols, int* status) {
+                                                         int ncols, int nbuf, int* status) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  // carve: A_hi, A_lo (16 KB each), B_hi, B_lo (npad x 128 B each), aligned to 1024
+  // carve, twice: A_hi, A_lo (16 KB each), B_hi, B_lo (ncols x 128 B each), aligned to 1024
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t bar;
+  const int set_bytes = 2 * TC_A_BYTES + 2 * ncols * 128;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -45,14 +48,27 @@ __global__ void __launch_bounds__(128, 1) tc_mode_kernel(const TcOp* __restrict_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
     abort_flag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  TcCtx cx{base, base + TC_A_BYTES, base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + ncols * 128,
-           &bar, tmem_slot, 0u, &abort_flag, status};
+  TcCtx cx{};
+  for (int b = 0; b < 2; ++b) {
+    unsigned char* sb = base + (nbuf == 2 ? b : 0) * set_bytes;
+    cx.sAhi[b] = sb;
+    cx.sAlo[b] = sb + TC_A_BYTES;
+    cx.sBhi[b] = sb + 2 * TC_A_BYTES;
+    cx.sBlo[b] = sb + 2 * TC_A_BYTES + ncols * 128;
+    cx.bar[b] = &bar[b];
+    cx.phase[b] = 0u;
+  }
+  cx.nbuf = nbuf;
+  cx.tmem = tmem_slot;
+  cx.abort_flag = &abort_flag;
+  cx.status = status;
   pdl_wait();  // TMEM and the barrier are set up while the previous kernel drains
   for (i64 t = blockIdx.x; t < total && !abort_flag; t += gridDim.x) tc_tile(ops, nops, t, cx);
   __syncthreads();
@@ -76,7 +92,22 @@ __global__ void __launch_bounds__(256) tc_sum_kernel(const TcOp* __restrict__ op
   }
 }
 
-int tc_smem_bytes(int ncols) { return 2 * TC_A_BYTES + 2 * ncols * 128 + 1024; }
+int tc_smem_bytes(int ncols, int nbuf) { return nbuf * (2 * TC_A_BYTES + 2 * ncols * 128) + 1024; }
+
+// GPFVM_TC_NBUF=1 or 2 forces the number of operand sets (for timing both).
+static int tc_env_nbuf() {
+  static const int v = [] {
+    const char* e = std::getenv("GPFVM_TC_NBUF");
+    const int n = e ? std::atoi(e) : 0;
+    return (n == 1 || n == 2) ? n : 0;
+  }();
+  return v;
+}
+
+// Two operand sets (staging overlapped with the MMAs of the previous stage)
+// where two CTAs still fit on an SM with them; one set otherwise, so that
+// two CTAs overlap each other instead.
+static int tc_nbuf(int ncols) { return 2 * tc_smem_bytes(ncols, 2) <= 227 * 1024 ? 2 : 1; }
 
 void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, int* status, cudaStream_t st,
                      int any_split) {
@@ -85,14 +116,15 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
   int ncols = 32;
   while (ncols < npad) ncols <<= 1;
   if (npad > 4 * TC_BREG) throw CudaError{cudaErrorInvalidValue, "tc: output size above 128"};
-  const int smem = tc_smem_bytes(ncols);
+  const int nbuf = tc_env_nbuf() ? tc_env_nbuf() : tc_nbuf(ncols);
+  const int smem = tc_smem_bytes(ncols, nbuf);
   static int attr_set = 0;
   if (attr_set < smem) {
-    GPFVM_CUDA(cudaFuncSetAttribute(tc_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(256)));
-    attr_set = tc_smem_bytes(256);
+    GPFVM_CUDA(cudaFuncSetAttribute(tc_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(128, 2)));
+    attr_set = tc_smem_bytes(128, 2);
   }
   const int grid = (int)std::min<i64>(total_tiles, 2 * 152);
-  launch_pdl(tc_mode_kernel, grid, 128, smem, st, d_ops, nops, total_tiles, ncols, status);
+  launch_pdl(tc_mode_kernel, grid, 128, smem, st, d_ops, nops, total_tiles, ncols, nbuf, status);
   if (any_split) launch_pdl(tc_sum_kernel, dim3(2 * 152, nops), 256, 0, st, d_ops);
 }
 

@@ -43,6 +43,6 @@ void launch_tc_modes(const TcOp* d_ops, int nops, i64 total_tiles, int max_n, in
 // hi / lo parts of alpha * F for the given TcMode (kept as FP32 values that
 // are exactly representable in the mode's operand type)
 void tc_split(const float* F, i64 n, float alpha, float* hi, float* lo, cudaStream_t st, int mode = TC_TF32X3);
-int tc_smem_bytes(int ncols);
+int tc_smem_bytes(int ncols, int nbuf);
 
 }  // namespace gpfvm

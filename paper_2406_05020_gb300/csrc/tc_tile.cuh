@@ -108,17 +108,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// Per-CTA state for running tensor-core tiles (set up by the kernel: shared
-// operand buffers, the MMA-completion mbarrier, the TMEM accumulator, the
-// barrier phase, an abort flag in shared memory and the status word).
+// Per-CTA state for running tensor-core tiles (set up by the kernel: one or
+// two sets of shared operand buffers, one MMA-completion mbarrier per set,
+// the TMEM accumulator, the barrier phases, an abort flag in shared memory
+// and the status word).  With two sets, stage s + 1 is written into the other
+// set while the MMAs of stage s run; a set is rewritten only after its own
+// MMAs have completed.
 struct TcCtx {
-  unsigned char *sAhi, *sAlo, *sBhi, *sBlo;
-  uint64_t* bar;
+  unsigned char *sAhi[2], *sAlo[2], *sBhi[2], *sBlo[2];
+  uint64_t* bar[2];
   uint32_t tmem;
-  uint32_t phase;
+  uint32_t phase[2];
+  int nbuf;
   int* abort_flag;
   int* status;
 };
+
+// Waits for the MMAs committed to operand set b (bounded; a timeout sets the
+// status and the CTA's abort flag) and flips that set's barrier phase.
+__device__ __forceinline__ void tc_wait_set(TcCtx& cx, int b) {
+  const bool ok = b ? mbar_wait(cx.bar[1], cx.phase[1]) : mbar_wait(cx.bar[0], cx.phase[0]);
+  if (b) cx.phase[1] ^= 1u; else cx.phase[0] ^= 1u;
+  if (!ok) {
+    atomicOr(cx.status, (int)DEV_TIMEOUT);
+    *cx.abort_flag = 1;
+  }
+}
 
 // One 128-row output tile t of the op table.  Every thread of the CTA calls
 // it (it synchronises the CTA); threads 0..127 stage the operands and read
@@ -171,25 +186,36 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
     }
   };
   load_stage(0);
-  for (int st = 0; st < nstage && !*cx.abort_flag; ++st) {
+  int st = 0;
+  for (; st < nstage; ++st) {
+    const int b = cx.nbuf == 2 ? (st & 1) : 0;
     const int k0 = (st % nkb) * TC_KB;
-    // registers -> shared (split A into hi / lo), previous MMAs have completed
+    // the set's previous MMAs (stage st - nbuf) must be done before it is rewritten
+    if (st >= cx.nbuf) {
+      tc_wait_set(cx, b);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    unsigned char* sAhi = b ? cx.sAhi[1] : cx.sAhi[0];
+    unsigned char* sAlo = b ? cx.sAlo[1] : cx.sAlo[0];
+    unsigned char* sBhi = b ? cx.sBhi[1] : cx.sBhi[0];
+    unsigned char* sBlo = b ? cx.sBlo[1] : cx.sBlo[0];
+    // registers -> shared (split A into hi / lo)
     if (act && mode == TC_TF32X3) {
 #pragma unroll
       for (int q = 0; q < TC_ROWS * TC_KB / 128; ++q) {
         const int r = rb + 4 * q;
         const float v = ra[q], vh = tf32_rna(v);
         const uint32_t off = sw128(r, c);
-        *(float*)(cx.sAhi + off) = vh;
-        *(float*)(cx.sAlo + off) = v - vh;
+        *(float*)(sAhi + off) = vh;
+        *(float*)(sAlo + off) = v - vh;
       }
 #pragma unroll
       for (int q = 0; q < TC_BREG; ++q) {
         const int r = rb + 4 * q;
         if (r < npad) {
           const uint32_t off = sw128(r, c);
-          *(float*)(cx.sBhi + off) = rbh[q];
-          *(float*)(cx.sBlo + off) = rbl[q];
+          *(float*)(sBhi + off) = rbh[q];
+          *(float*)(sBlo + off) = rbl[q];
         }
       }
     } else if (act) {  // bf16 operands in 64-byte rows (the B parts are exact bf16 values)
@@ -198,21 +224,22 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
         const int r = rb + 4 * q;
         const float v = ra[q], vh = bf16_rn(v);
         const uint32_t off = sw64(r, c);
-        *(unsigned short*)(cx.sAhi + off) = bf16_bits(vh);
-        if (mode == TC_BF16X3) *(unsigned short*)(cx.sAlo + off) = bf16_bits(v - vh);
+        *(unsigned short*)(sAhi + off) = bf16_bits(vh);
+        if (mode == TC_BF16X3) *(unsigned short*)(sAlo + off) = bf16_bits(v - vh);
       }
 #pragma unroll
       for (int q = 0; q < TC_BREG; ++q) {
         const int r = rb + 4 * q;
         if (r < npad) {
           const uint32_t off = sw64(r, c);
-          *(unsigned short*)(cx.sBhi + off) = bf16_bits(rbh[q]);
-          if (mode == TC_BF16X3) *(unsigned short*)(cx.sBlo + off) = bf16_bits(rbl[q]);
+          *(unsigned short*)(sBhi + off) = bf16_bits(rbh[q]);
+          if (mode == TC_BF16X3) *(unsigned short*)(sBlo + off) = bf16_bits(rbl[q]);
         }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (*cx.abort_flag) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int kk = min(TC_KB, K - k0);
@@ -220,8 +247,8 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
         const int ksteps = (kk + 7) / 8;
         for (int ks = 0; ks < ksteps; ++ks) {
           const uint32_t koff = ks * 32;  // 8 tf32 = 32 bytes inside the 128-byte row
-          const uint64_t ah = desc_sw128(smem_u32(cx.sAhi) + koff), al = desc_sw128(smem_u32(cx.sAlo) + koff);
-          const uint64_t bh = desc_sw128(smem_u32(cx.sBhi) + koff), bl = desc_sw128(smem_u32(cx.sBlo) + koff);
+          const uint64_t ah = desc_sw128(smem_u32(sAhi) + koff), al = desc_sw128(smem_u32(sAlo) + koff);
+          const uint64_t bh = desc_sw128(smem_u32(sBhi) + koff), bl = desc_sw128(smem_u32(sBlo) + koff);
           mma_tf32(cx.tmem, ah, bh, idesc, acc);
           acc = 1;
           mma_tf32(cx.tmem, ah, bl, idesc, 1);
@@ -231,28 +258,26 @@ __device__ __forceinline__ void tc_tile(const TcOp* __restrict__ ops, int nops, 
         const int ksteps = (kk + 15) / 16;
         for (int ks = 0; ks < ksteps; ++ks) {
           const uint32_t koff = ks * 32;  // 16 bf16 = 32 bytes inside the 64-byte row
-          const uint64_t ah = desc_sw64(smem_u32(cx.sAhi) + koff), bh = desc_sw64(smem_u32(cx.sBhi) + koff);
+          const uint64_t ah = desc_sw64(smem_u32(sAhi) + koff), bh = desc_sw64(smem_u32(sBhi) + koff);
           mma_bf16(cx.tmem, ah, bh, idesc, acc);
           acc = 1;
           if (mode == TC_BF16X3) {
-            const uint64_t al = desc_sw64(smem_u32(cx.sAlo) + koff), bl = desc_sw64(smem_u32(cx.sBlo) + koff);
+            const uint64_t al = desc_sw64(smem_u32(sAlo) + koff), bl = desc_sw64(smem_u32(sBlo) + koff);
             mma_bf16(cx.tmem, ah, bl, idesc, 1);
             mma_bf16(cx.tmem, al, bh, idesc, 1);
           }
         }
       }
-      mma_commit(cx.bar);
+      mma_commit(b ? cx.bar[1] : cx.bar[0]);
     }
     if (st + 1 < nstage) load_stage(st + 1);  // overlaps the MMAs
-    const bool ok = mbar_wait(cx.bar, cx.phase);
-    cx.phase ^= 1;
-    if (!ok && tid == 0) {
-      atomicOr(cx.status, (int)DEV_TIMEOUT);
-      *cx.abort_flag = 1;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
   }
+  if (!*cx.abort_flag) {
+    // drain: the last nbuf stages have not been waited for
+    for (int s2 = max(0, nstage - cx.nbuf); s2 < nstage; ++s2) tc_wait_set(cx, cx.nbuf == 2 ? (s2 & 1) : 0);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
   if (*cx.abort_flag) return;
   // epilogue: row = row0 + tid, columns j < N, rotated store out[j * R + row]
   // (a partial sum of a segment group goes to its slice of op.part)

@@ -48,7 +48,7 @@ class Desc(C.Structure):
                 ("rhs", C.POINTER(C.c_double)), ("jitter", C.c_double), ("n_sets", C.c_int),
                 ("sets", PointSet * MAX_SETS), ("n_pred", C.c_int * MAX_DIM),
                 ("pred", C.POINTER(C.c_double) * MAX_DIM), ("observe", C.c_int),
-                ("coef_field", C.POINTER(C.c_double) * MAX_TERMS)]
+                ("coef_field", C.POINTER(C.c_double) * MAX_TERMS), ("fp64_products", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -225,9 +225,12 @@ def solve_opts(max_iter=2000, rtol=1e-10, precision=FP64, reorth=True, want_var=
 class Problem:
     """One GP-FVM problem resident on the GPU (create/assemble/solve/query)."""
 
-    def __init__(self, prob, max_iter: int = 2000):
+    def __init__(self, prob, max_iter: int = 2000, fp64_products: int = 0):
+        """fp64_products: 0 = FP64 G_PP by exact digit products on the tensor
+        cores where the problem allows it, 1 = FP64 FMA (gpfvm_desc)."""
         self.prob = prob
         self.desc, self._keep = make_desc(prob)
+        self.desc.fp64_products = int(fp64_products)
         h = P()
         _check(lib().gpfvm_create(C.byref(self.desc), int(max_iter), C.byref(h)), "gpfvm_create")
         self.h = h
@@ -251,7 +254,7 @@ class Problem:
         return _check(lib().gpfvm_assemble(self.h, _stream(stream)), "gpfvm_assemble")
 
     def _op_sizes(self, op: int):
-        if not 0 <= op <= 11:
+        if not 0 <= op <= 13:
             raise ValueError(f"unknown operator {op}")
         if op == 2:
             return self.N, self.M
