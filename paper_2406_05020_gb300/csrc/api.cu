@@ -279,6 +279,16 @@ struct gpfvm_problem {
   double *d_ozY = nullptr, *d_ozZ = nullptr;
   i64 oz_ops_total = 0, oz_img_total = 0, oz_fexp_total = 0, oz_exp_total = 0;
   int oz_nu = 0, oz_nw = 0;
+  // digit-product forms of other FP64 Kronecker chains (Builder::kron_digits):
+  // op tables, factor images (strided views) and their slicing jobs
+  struct OzxJob { const double* F; i64 rs, cs; int N, K; double alpha; i64 img_off, fexp_off; };
+  std::vector<OzxJob> ozx_jobs;
+  std::map<std::tuple<const double*, i64, i64, int, int, double>, std::pair<i64, i64>> ozx_img;
+  std::vector<OzOp> ozx_ops;
+  OzOp* d_ozxops = nullptr;
+  unsigned char* d_ozximg = nullptr;
+  int* d_ozxfexp = nullptr;
+  i64 ozx_ops_cap = 0, ozx_img_n = 0, ozx_fexp_n = 0;
   int cap64 = 0, cap32 = 0;  // directions the allocated stores hold
   CGState* d_st32 = nullptr;
   CGState* h_st32 = nullptr;
@@ -504,6 +514,7 @@ struct Builder {
     return (P)((FP)base + n);
   }
   bool keep = false;  // inside a stage of zipped chains: intermediates must not overlap
+  bool fma_only = false;  // kron_digits declines (the FP64 FMA operators)
   void stage_begin() {
     scr.used = 0;
     keep = true;
@@ -515,6 +526,153 @@ struct Builder {
     if (!keep) scr.used = 0;
     plan_kron(plan, scr, dd > 0 ? dd : p->d, din, dout, batch, terms, scale, in, out, beta, D, gamma, count, f32);
     peak = std::max(peak, scr.used);
+  }
+
+  // out = scale * sum_t c_t (F_t0 (x) F_t1 (x) F_t2) in + beta out + gamma D in
+  // FP64 by exact digit products on the tensor cores (oz.cu), in the shared
+  // rotating-axes three-level form (contract the last axis, write the new axis
+  // first); false, with nothing added, where that form does not apply (FP32
+  // plans, one axis, an axis above 128, the FMA form chosen).  Intermediates
+  // and row exponents come from the stage's scratch.
+  bool kron_digits(Plan& plan, const int* din, const int* dout, const std::vector<KTerm>& terms, double scale,
+                   const double* in, double* out, double beta, const double* D, double gamma, const int* skip) {
+    const int d = p->d;
+    if (f32 || fma_only || !p->oz_ok || !p->oz_on || d < 2 || terms.empty()) return false;
+    for (int i = 0; i < d; ++i)
+      if (din[i] < 1 || dout[i] < 1 || din[i] > OZ_KMAX || dout[i] > 128) return false;
+    if (!keep) scr.used = 0;
+    auto same = [](const MatRef& a, const MatRef& b) { return a.p == b.p && a.rs == b.rs && a.cs == b.cs; };
+    auto image = [&](const MatRef& f, int N, int K, double alpha) {
+      const auto key = std::make_tuple(f.p, f.rs, f.cs, N, K, alpha);
+      auto it = p->ozx_img.find(key);
+      if (it == p->ozx_img.end()) {
+        it = p->ozx_img.emplace(key, std::make_pair(p->ozx_img_n, p->ozx_fexp_n)).first;
+        p->ozx_jobs.push_back({f.p, f.rs, f.cs, N, K, alpha, p->ozx_img_n, p->ozx_fexp_n});
+        p->ozx_img_n += oz_image_bytes(N, K);
+        p->ozx_fexp_n += (N + 31) / 32 * 32;
+      }
+      return std::make_pair(p->d_ozximg ? (const unsigned char*)(p->d_ozximg + it->second.first) : nullptr,
+                            p->d_ozxfexp ? (const int*)(p->d_ozxfexp + it->second.second) : nullptr);
+    };
+    struct Lv { int off, nops; i64 tiles; OzExpJobs jobs; };
+    std::vector<Lv> lv;
+    bool ok = true;
+    const size_t first_op = p->ozx_ops.size();
+    auto begin_level = [&](i64 R, int K) {
+      Lv L{};
+      L.off = (int)p->ozx_ops.size();
+      L.jobs.R = (int)R;
+      L.jobs.K = K;
+      L.jobs.skip = skip;
+      lv.push_back(L);
+    };
+    auto job = [&](const double* A, i64 R) -> const int* {
+      auto& J = lv.back().jobs;
+      if (J.n >= OZ_MAXSEG) { ok = false; return nullptr; }
+      J.A[J.n] = A;
+      J.ex[J.n] = (int*)take((R + 1) / 2);
+      return J.ex[J.n++];
+    };
+    auto blank = [&](i64 R, int K, int N, double* o) {
+      OzOp op{};
+      op.R = (int)R; op.K = K; op.N = N; op.out = o;
+      op.skip = skip;
+      return op;
+    };
+    auto seg = [&](OzOp& op, const double* A, const int* ex, const MatRef& f, int N, int K, double alpha) {
+      if (op.nseg >= OZ_MAXSEG) { ok = false; return; }
+      const auto im = image(f, N, K, alpha);
+      op.A[op.nseg] = A;
+      op.Aexp[op.nseg] = ex;
+      op.Bimg[op.nseg] = im.first;
+      op.Bexp[op.nseg] = im.second;
+      op.nseg++;
+    };
+    auto add_op = [&](OzOp op) {
+      auto& L = lv.back();
+      op.tile_begin = L.tiles;
+      L.tiles += oz_tiles(op.R, op.N);
+      L.nops++;
+      p->ozx_ops.push_back(op);
+    };
+    const i64 n0 = din[0], n1 = din[1], n2 = d == 3 ? din[2] : 1;
+    const i64 m0 = dout[0], m1 = dout[1], m2 = d == 3 ? dout[2] : 1;
+    std::vector<MatRef> U, Wf;
+    std::vector<int> uo(terms.size()), wo(terms.size());
+    for (size_t k = 0; k < terms.size(); ++k) {
+      if (d == 3) {
+        int f = -1;
+        for (size_t u = 0; u < U.size(); ++u) if (same(U[u], terms[k].f[2])) f = (int)u;
+        if (f < 0) { f = (int)U.size(); U.push_back(terms[k].f[2]); }
+        uo[k] = f;
+      }
+      int w = -1;
+      for (size_t j = 0; j < Wf.size(); ++j) if (same(Wf[j], terms[k].f[0])) w = (int)j;
+      if (w < 0) { w = (int)Wf.size(); Wf.push_back(terms[k].f[0]); }
+      wo[k] = w;
+    }
+    std::vector<const double*> Y;
+    std::vector<const int*> exY;
+    if (d == 3) {  // contract axis 2: (n0 n1) x n2 -> Y_u (m2, n0, n1)
+      begin_level(n0 * n1, (int)n2);
+      const int* ex = job(in, n0 * n1);
+      for (size_t u = 0; u < U.size(); ++u) {
+        double* y = take(m2 * n0 * n1);
+        Y.push_back(y);
+        OzOp op = blank(n0 * n1, (int)n2, (int)m2, y);
+        seg(op, in, ex, U[u], (int)m2, (int)n2, 1.0);
+        add_op(op);
+      }
+    }
+    // contract axis 1: rows (m2, n0) (or n0) x n1 -> Z_w (m1, m2, n0)
+    const i64 R2 = m2 * n0;
+    begin_level(R2, (int)n1);
+    if (d == 3) for (size_t u = 0; u < U.size(); ++u) exY.push_back(job(Y[u], R2));
+    else exY.push_back(job(in, R2));
+    std::vector<const double*> Z;
+    for (size_t w = 0; w < Wf.size(); ++w) {
+      double* z = take(m1 * R2);
+      Z.push_back(z);
+      OzOp op = blank(R2, (int)n1, (int)m1, z);
+      std::vector<std::pair<std::pair<int, MatRef>, double>> acc;  // merged (source, factor) pairs
+      for (size_t k = 0; k < terms.size(); ++k) {
+        if (wo[k] != (int)w) continue;
+        const int src = d == 3 ? uo[k] : 0;
+        bool merged = false;
+        for (auto& a : acc)
+          if (a.first.first == src && same(a.first.second, terms[k].f[1])) { a.second += terms[k].c; merged = true; }
+        if (!merged) acc.push_back({{src, terms[k].f[1]}, terms[k].c});
+      }
+      for (auto& a : acc)
+        seg(op, d == 3 ? Y[a.first.first] : in, exY[a.first.first], a.first.second, (int)m1, (int)n1, a.second);
+      add_op(op);
+    }
+    // contract axis 0: rows (m1, m2) x n0 -> out (m0, m1, m2)
+    const i64 R3 = m1 * m2;
+    begin_level(R3, (int)n0);
+    OzOp op = blank(R3, (int)n0, (int)m0, out);
+    for (size_t w = 0; w < Wf.size(); ++w) seg(op, Z[w], job(Z[w], R3), Wf[w], (int)m0, (int)n0, scale);
+    op.D = D;
+    op.gamma = gamma;
+    op.beta = beta;
+    add_op(op);
+    peak = std::max(peak, scr.used);
+    if (!ok) {
+      p->ozx_ops.resize(first_op);
+      return false;
+    }
+    for (const Lv& L : lv) {
+      const OzExpJobs J = L.jobs;
+      const OzOp* ops = p->d_ozxops ? p->d_ozxops + L.off : nullptr;
+      const int nops = L.nops;
+      const i64 tiles = L.tiles;
+      int* status = &p->d_st->status;
+      plan.func([=](cudaStream_t st) {
+        oz_row_exponents(J, st);
+        launch_oz_modes(ops, nops, tiles, status, st);
+      });
+    }
+    return true;
   }
 
   // ---- variable coefficients (App. C.4): a term's cell-side factor carries
@@ -1011,8 +1169,9 @@ struct Builder {
   // launches per direction instead of three); the others take Kronecker chains
   // into separate buffers.  With IC/BC sets, G_PP runs beside all of it as a
   // background chain.
+  // `skip` is the plan's skip flag (the digit-product chains honour it too).
   void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
-                   Plan* pp_chain = nullptr) {
+                   Plan* pp_chain = nullptr, const int* skip = nullptr) {
     if (varcoef()) {
       vc_ghat(plan, in, out, g, w, u, true);
       return;
@@ -1025,7 +1184,12 @@ struct Builder {
     Plan PP, PR;
     if (pp_chain) PP = std::move(*pp_chain);
     else kron(PP, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
-    if (u) kron(PR, dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
+    // the variance product (outside the CG recurrence) by digit products; the
+    // IC/BC chains stay in FP64 FMA: their factor rows decay over many orders
+    // of magnitude, where the fixed-point digit error (relative to a row's
+    // largest entry) exceeds FMA rounding enough to break CG run to 1e-13
+    if (u && !kron_digits(PR, dc, dp, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0, skip))
+      kron(PR, dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
     std::vector<const Plan*> cs;
     std::vector<int> st;
     auto put = [&](const Plan& c, int s0) {
@@ -1534,7 +1698,7 @@ Plan oz_chain(gpfvm_problem* p, int inst) {
   Plan c;
   for (const auto& L : p->oz_levels[inst]) {
     const OzExpJobs J = L.jobs;
-    const OzOp* ops = p->d_ozops + L.off;
+    const OzOp* ops = p->d_ozops ? p->d_ozops + L.off : nullptr;
     const int nops = L.nops;
     const i64 tiles = L.tiles;
     int* status = &p->d_st->status;
@@ -1546,8 +1710,32 @@ Plan oz_chain(gpfvm_problem* p, int inst) {
   return c;
 }
 
+// The op table of the digit-product chains built by Builder::kron_digits:
+// bounds-checked on the host and copied once the buffers exist (real pass).
+void finish_ozx(gpfvm_problem* p) {
+  if (!p->d_ozxops || p->ozx_ops.empty()) return;
+  if ((i64)p->ozx_ops.size() > p->ozx_ops_cap) throw CudaError{cudaErrorInvalidValue, "digit-product op table"};
+  for (const OzOp& op : p->ozx_ops) {
+    bool ok = p->mem.contains(op.out, 8LL * op.N * op.R) && (!op.D || p->mem.contains(op.D, 8LL * op.N * op.R));
+    ok = ok && op.nseg >= 1 && op.K >= 1 && op.K <= OZ_KMAX && op.N >= 1 && op.N <= 128;
+    for (int s = 0; s < op.nseg; ++s)
+      ok = ok && p->mem.contains(op.A[s], 8LL * op.R * op.K) && p->mem.contains(op.Aexp[s], 4LL * op.R) &&
+           p->mem.contains(op.Bimg[s], oz_image_bytes(op.N, op.K)) && p->mem.contains(op.Bexp[s], 4LL * op.N) &&
+           ((uintptr_t)op.Bimg[s] & 15) == 0;
+    if (!ok) throw CudaError{cudaErrorInvalidValue, "digit-product operand out of bounds"};
+  }
+  for (const auto& j : p->ozx_jobs)
+    if (!p->mem.contains(j.F, 8LL * (1 + (j.N - 1) * j.rs + (j.K - 1) * j.cs)))
+      throw CudaError{cudaErrorInvalidValue, "digit-product factor out of bounds"};
+  GPFVM_CUDA(cudaMemcpy(p->d_ozxops, p->ozx_ops.data(), sizeof(OzOp) * p->ozx_ops.size(), cudaMemcpyHostToDevice));
+}
+
 void build_plans(gpfvm_problem* p, Builder& B) {
   const i64 N = p->N, M = p->M, P = p->P;
+  p->ozx_ops.clear();
+  p->ozx_jobs.clear();
+  p->ozx_img.clear();
+  p->ozx_img_n = p->ozx_fexp_n = 0;
   gpfvm_problem* pp_ = p;
   // ---- setup: factors + G_BB
   p->p_setup = Plan();
@@ -1616,12 +1804,13 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   p->modeprods_pp = 0;
   {
     Plan c = oz ? oz_chain(p, 0) : Plan();
-    B.ghat_phased(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_w, nullptr, &p->modeprods_pp, oz ? &c : nullptr);
+    B.ghat_phased(p->p_mv_cg, p->d_p, p->d_q, p->d_g, p->d_w, nullptr, &p->modeprods_pp, oz ? &c : nullptr,
+                  &p->d_st->done);
   }
   p->p_mvv_cg = Plan();
   {
     Plan c = oz ? oz_chain(p, 0) : Plan();
-    B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr, oz ? &c : nullptr);
+    B.ghat_phased(p->p_mvv_cg, p->d_p, p->d_q, p->d_g, p->d_w, p->d_u, nullptr, oz ? &c : nullptr, &p->d_st->done);
   }
   p->p_var_cg = Plan();
   B.to_pred_cells(p->p_var_cg, p->d_p, p->d_u, 1.0, false);
@@ -1629,8 +1818,10 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   // ---- operator plans for gpfvm_gram_matvec / true residual
   for (int k = 0; k < 6; ++k) p->p_op[k] = Plan();
   B.pp(p->p_op[0], p->d_vin, p->d_vout, nullptr);
+  B.fma_only = true;  // op 1: every product in FP64 FMA
   B.ghat_phased(p->p_op[1], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr);
-  if (p->oz_ok && p->d_ozops) {
+  B.fma_only = false;
+  if (p->oz_ok) {  // (in the counting pass too: the digit chains of G^ need op-table room)
     p->p_op[4] = oz_chain(p, 1);
     Plan c = oz_chain(p, 1);
     B.ghat_phased(p->p_op[5], p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr, &c);
@@ -1638,7 +1829,8 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   p->p_res = Plan();
   {
     Plan c = oz ? oz_chain(p, 2) : Plan();
-    B.ghat_phased(p->p_res, p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr, oz ? &c : nullptr);
+    B.ghat_phased(p->p_res, p->d_vin, p->d_vout, p->d_g2, p->d_wout, nullptr, nullptr, oz ? &c : nullptr,
+                  &p->d_mctl->first);
   }
   if (M > 0) {
     B.bp(p->p_op[2], p->d_vin, p->d_wout);
@@ -1696,6 +1888,7 @@ void build_plans(gpfvm_problem* p, Builder& B) {
       p->p_vB.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
     }
   }
+  finish_ozx(p);
 }
 
 // Tensor-core G_PP: the shared three-level form with rotating axes
@@ -2275,6 +2468,12 @@ void alloc_all(gpfvm_problem* p) {
   p->f_tcpart = m.alloc<float>(std::max<i64>(p->tc_part_total, 64));
   p->d_tcops = m.alloc<TcOp>(std::max<i64>(p->tc_ops_total, 1));
   p->tc_jobs.clear();
+  if (!p->ozx_ops.empty()) {
+    p->ozx_ops_cap = (i64)p->ozx_ops.size();
+    p->d_ozxops = m.alloc<OzOp>(p->ozx_ops_cap);
+    p->d_ozximg = m.alloc<unsigned char>(std::max<i64>(p->ozx_img_n, 256));
+    p->d_ozxfexp = m.alloc<int>(std::max<i64>(p->ozx_fexp_n, 64));
+  }
   if (p->oz_ok) {
     p->d_ozops = m.alloc<OzOp>(std::max<i64>(p->oz_ops_total, 1));
     p->d_ozimg = m.alloc<unsigned char>(std::max<i64>(p->oz_img_total, 256));
@@ -2335,7 +2534,11 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
   p->p_rhs.run(st);
   if (p->oz_ok && p->d_ozimg)
     for (const auto& j : p->oz_jobs)
-      oz_split_factor(p->d_fac + j.fac_off, j.n, j.n, j.alpha, p->d_ozimg + j.img_off, p->d_ozfexp + j.fexp_off, st);
+      oz_split_factor(p->d_fac + j.fac_off, j.n, 1, j.n, j.n, j.alpha, p->d_ozimg + j.img_off, p->d_ozfexp + j.fexp_off,
+                      st);
+  if (p->d_ozximg)
+    for (const auto& j : p->ozx_jobs)
+      oz_split_factor(j.F, j.rs, j.cs, j.N, j.K, j.alpha, p->d_ozximg + j.img_off, p->d_ozxfexp + j.fexp_off, st);
   convert_d2f(p->d_fac, p->f_fac, p->nfac, st);
   for (auto& j : p->tc_jobs) {
     const i64 n = std::get<2>(j), off = std::get<3>(j);

@@ -42,6 +42,7 @@
 namespace gpfvm {
 
 constexpr int OZ_THREADS = 256;
+constexpr int OZ_G = 43;  // binary point of one segment's 64-bit sum (see the drain)
 constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
 constexpr int OZ_DYN_SMEM = 2 * OZ_SET + 1024;
 
@@ -63,32 +64,43 @@ __device__ __forceinline__ unsigned long long oz_fix(unsigned long long bits, in
   return (((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2) >> sh;
 }
 
-// balanced base-128 digits of X < 2^55: X = sum_j d_j 2^(49 - 7 j), d_j in [-64, 64]
-__device__ __forceinline__ void oz_digits(unsigned long long X, int d[OZ_DIGITS]) {
-  const uint32_t hi = (uint32_t)(X >> 32), lo = (uint32_t)X;
-  uint32_t raw[OZ_DIGITS];
-  raw[0] = hi >> 17;
-  raw[1] = (hi >> 10) & 127u;
-  raw[2] = (hi >> 3) & 127u;
-  raw[3] = ((hi & 7u) << 4) | (lo >> 28);
-  raw[4] = (lo >> 21) & 127u;
-  raw[5] = (lo >> 14) & 127u;
-  raw[6] = (lo >> 7) & 127u;
-  raw[7] = lo & 127u;
-  int carry = 0;
-#pragma unroll
-  for (int j = OZ_DIGITS - 1; j >= 1; --j) {
-    const int t = (int)raw[j] + carry;
-    carry = t >= 64 ? 1 : 0;
-    d[j] = t - (carry << 7);
-  }
-  d[0] = (int)raw[0] + carry;
+// Balanced digits by an offset: with C = 64 sum_j 2^(49 - 7 j), the plain
+// base-128 digits e_j of Y = X + C (X < 2^55, so e_0 <= 128) give
+// X = sum_j (e_j - 64) 2^(49 - 7 j): d_j = e_j - 64 in [-64, 64], no carries.
+constexpr unsigned long long OZ_C = 64ull * ((1ull << 49) + (1ull << 42) + (1ull << 35) + (1ull << 28) +
+                                             (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+
+// digit field j of Y, or-ed into the FP32 pattern of 1.5 * 2^23 (the value 12582912 + e_j)
+template <int J>
+__device__ __forceinline__ uint32_t oz_field_f32(uint32_t yhi, uint32_t ylo) {
+  uint32_t e;
+  if (J == 0) e = yhi >> 17;
+  else if (J == 1) e = (yhi >> 10) & 127u;
+  else if (J == 2) e = (yhi >> 3) & 127u;
+  else if (J == 3) e = __funnelshift_r(ylo, yhi, 28) & 127u;
+  else if (J == 4) e = (ylo >> 21) & 127u;
+  else if (J == 5) e = (ylo >> 14) & 127u;
+  else if (J == 6) e = (ylo >> 7) & 127u;
+  else e = ylo & 127u;
+  return 0x4B400000u | e;
 }
 
-// FP32 bit pattern of the integer v (|v| <= 2^22) with the sign bit flipped
-// by negbit; its upper half is the bf16 pattern of the same value
-__device__ __forceinline__ uint32_t oz_f32bits(int v, uint32_t negbit) {
-  return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f) ^ negbit;
+// FP32 bit pattern of sgn * d_j (sgn = +-1, the element's sign): its upper
+// half is the bf16 pattern of the same integer
+template <int J>
+__device__ __forceinline__ uint32_t oz_digit_f32(uint32_t yhi, uint32_t ylo, float sgn, float off) {
+  return __float_as_uint(fmaf(__uint_as_float(oz_field_f32<J>(yhi, ylo)), sgn, off));
+}
+
+// (hi, lo) words of Y = X + C for the element with bit pattern `bits`, and
+// its sign factor / offset for oz_digit_f32 (off = -sgn (12582912 + 64))
+__device__ __forceinline__ void oz_prep(unsigned long long bits, int emax, uint32_t& yhi, uint32_t& ylo, float& sgn,
+                                        float& off) {
+  const unsigned long long Y = oz_fix(bits, emax) + OZ_C;
+  yhi = (uint32_t)(Y >> 32);
+  ylo = (uint32_t)Y;
+  sgn = (bits >> 63) ? -1.0f : 1.0f;
+  off = (bits >> 63) ? 12582976.0f : -12582976.0f;
 }
 
 // integer value of an FP32 accumulator holding an integer of magnitude <= 2^22
@@ -162,33 +174,43 @@ void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st) {
 
 // digit image of alpha F (one warp per row j): plane l of (K block kb, column
 // half h) at img + ((kb * nh + h) * 8 + l) * OZ_B_PLANE, 64-byte-swizzled rows
-__global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ F, int N, int K, double alpha,
-                                                       unsigned char* __restrict__ img, int* __restrict__ fexp) {
+__global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ F, i64 rs, i64 cs, int N, int K,
+                                                       double alpha, unsigned char* __restrict__ img,
+                                                       int* __restrict__ fexp) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= N) return;  // whole warps
   const int nh = (N + OZ_COLS - 1) / OZ_COLS;
   int e = 0;
-  for (int k = lane; k < K; k += 32) e = max(e, oz_field((unsigned long long)__double_as_longlong(alpha * F[(i64)j * K + k])));
+  for (int k = lane; k < K; k += 32) e = max(e, oz_field((unsigned long long)__double_as_longlong(alpha * F[j * rs + k * cs])));
   e = __reduce_max_sync(0xffffffffu, e);
   if (lane == 0) fexp[j] = e;
   for (int k = lane; k < K; k += 32) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(alpha * F[(i64)j * K + k]);
-    int d[OZ_DIGITS];
-    oz_digits(oz_fix(bits, e), d);
-    const uint32_t neg = (uint32_t)(bits >> 63) << 31;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(alpha * F[j * rs + k * cs]);
+    uint32_t yh, yl;
+    float sg, of;
+    oz_prep(bits, e, yh, yl, sg, of);
+    uint32_t f[OZ_DIGITS];
+    f[0] = oz_digit_f32<0>(yh, yl, sg, of);
+    f[1] = oz_digit_f32<1>(yh, yl, sg, of);
+    f[2] = oz_digit_f32<2>(yh, yl, sg, of);
+    f[3] = oz_digit_f32<3>(yh, yl, sg, of);
+    f[4] = oz_digit_f32<4>(yh, yl, sg, of);
+    f[5] = oz_digit_f32<5>(yh, yl, sg, of);
+    f[6] = oz_digit_f32<6>(yh, yl, sg, of);
+    f[7] = oz_digit_f32<7>(yh, yl, sg, of);
     unsigned char* blk = img + ((i64)(k / OZ_KB) * nh + j / OZ_COLS) * OZ_IMG_STAGE;
     const uint32_t off = sw64(j % OZ_COLS, k % OZ_KB);
 #pragma unroll
-    for (int l = 0; l < OZ_DIGITS; ++l)
-      *(unsigned short*)(blk + l * OZ_B_PLANE + off) = (unsigned short)(oz_f32bits(d[l], neg) >> 16);
+    for (int l = 0; l < OZ_DIGITS; ++l) *(unsigned short*)(blk + l * OZ_B_PLANE + off) = (unsigned short)(f[l] >> 16);
   }
 }
 
-void oz_split_factor(const double* F, int N, int K, double alpha, unsigned char* img, int* fexp, cudaStream_t st) {
+void oz_split_factor(const double* F, i64 rs, i64 cs, int N, int K, double alpha, unsigned char* img, int* fexp,
+                     cudaStream_t st) {
   if (N <= 0 || K <= 0) return;
   GPFVM_CUDA(cudaMemsetAsync(img, 0, oz_image_bytes(N, K), st));
-  oz_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(F, N, K, alpha, img, fexp);
+  oz_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(F, rs, cs, N, K, alpha, img, fexp);
   GPFVM_LAUNCH_CHECK();
 }
 
@@ -286,9 +308,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     }
     const int nkb = (K + OZ_KB - 1) / OZ_KB;
     const int nstage = nseg * nkb;
-    // fixed point of the sums: value = S * 2^(EA + EB - 2056 - G); |one segment's
-    // sum| < 1.02 * 2^(19 + G), so G = 43 - ceil(log2 nseg) keeps |S| < 2^62.1
-    const int G = 43 - (nseg > 1 ? 32 - __clz(nseg - 1) : 0);
+    // fixed point: one segment's sum V = sum_d acc_d 2^(OZ_G - 7 d) stays below
+    // 1.02 * 2^(19 + OZ_G) = 2^62.03 (one unit: 2^-55 of max|a| max|b|); with
+    // more segments each is shifted down by guard = ceil(log2 nseg) bits, so
+    // |S| < 2^62.03 and value = S * 2^(E + F - 2056 - OZ_G + guard)
+    const int guard = nseg > 1 ? 32 - __clz(nseg - 1) : 0;
     long long S[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) S[i] = 0;
@@ -297,10 +321,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
       const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * 16;
       const double* __restrict__ A = op.A[s];
       const int gr = row0 + srow;
+      if (gr < R && (K & 1) == 0 && k0 + 16 <= K) {  // 16-byte aligned pairs
+        const double2* src = (const double2*)(A + (i64)gr * K + k0);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int k = k0 + i;
-        ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
+        for (int i = 0; i < 8; ++i) {
+          const double2 t2 = __ldg(src + i);
+          ra[2 * i] = t2.x;
+          ra[2 * i + 1] = t2.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int k = k0 + i;
+          ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
+        }
       }
     };
     load_stage(0);
@@ -323,14 +357,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         uint32_t w[OZ_DIGITS][4];
 #pragma unroll
         for (int p2 = 0; p2 < 4; ++p2) {
-          const unsigned long long b0 = (unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2]);
-          const unsigned long long b1 = (unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2 + 1]);
-          int d0[OZ_DIGITS], d1[OZ_DIGITS];
-          oz_digits(oz_fix(b0, emax), d0);
-          oz_digits(oz_fix(b1, emax), d1);
-          const uint32_t n0 = (uint32_t)(b0 >> 63) << 31, n1 = (uint32_t)(b1 >> 63) << 31;
-#pragma unroll
-          for (int j = 0; j < OZ_DIGITS; ++j) w[j][p2] = __byte_perm(oz_f32bits(d0[j], n0), oz_f32bits(d1[j], n1), 0x7632);
+          uint32_t h0, l0, h1, l1;
+          float s0, o0, s1, o1;
+          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2]), emax, h0, l0, s0, o0);
+          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2 + 1]), emax, h1, l1, s1, o1);
+#define OZ_PAIR(J) w[J][p2] = __byte_perm(oz_digit_f32<J>(h0, l0, s0, o0), oz_digit_f32<J>(h1, l1, s1, o1), 0x7632)
+          OZ_PAIR(0); OZ_PAIR(1); OZ_PAIR(2); OZ_PAIR(3); OZ_PAIR(4); OZ_PAIR(5); OZ_PAIR(6); OZ_PAIR(7);
+#undef OZ_PAIR
         }
         const uint32_t off = sw64(srow, kh * 16 + q2 * 8);
 #pragma unroll
@@ -348,16 +381,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int ksteps = (min(OZ_KB, K - kb * OZ_KB) + 15) / 16;
+          // descriptors differ only in the start address field (16-byte units)
+          const uint64_t da0 = desc_sw64(smem_u32(sA)), db0 = desc_sw64(smem_u32(sB));
           for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t koff = ks * 32;  // 16 bf16 = 32 bytes inside the 64-byte row
+            const uint64_t dak = da0 + (uint64_t)(ks * 2), dbk = db0 + (uint64_t)(ks * 2);  // 32 bytes per K step
 #pragma unroll
             for (int d = 0; d < OZ_DIGITS; ++d) {
 #pragma unroll
-              for (int a = 0; a <= d; ++a) {
-                const uint64_t da = desc_sw64(smem_u32(sA + a * OZ_A_PLANE) + koff);
-                const uint64_t db = desc_sw64(smem_u32(sB + (d - a) * OZ_B_PLANE) + koff);
-                mma_bf16(tmem + d * OZ_COLS, da, db, idesc, (kb > 0 || ks > 0 || a > 0) ? 1u : 0u);
-              }
+              for (int a = 0; a <= d; ++a)
+                mma_bf16(tmem + d * OZ_COLS, dak + (uint64_t)(a * (OZ_A_PLANE >> 4)),
+                         dbk + (uint64_t)((d - a) * (OZ_B_PLANE >> 4)), idesc, (kb > 0 || ks > 0 || a > 0) ? 1u : 0u);
             }
           }
         }
@@ -374,29 +407,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         const int shA = s_emax[row] - s_es[s][row];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          long long V[8];
+          uint32_t v[OZ_DIGITS][8];
+          const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32 + cc * 8);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) V[i] = 0;
-#pragma unroll
-          for (int d = 0; d < OZ_DIGITS; ++d) {
-            uint32_t v[8];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * OZ_COLS + ch * 32 + cc * 8);
+          for (int d = 0; d < OZ_DIGITS; ++d)
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const long long a = (long long)oz_int(v[i]);
-              V[i] += 7 * d <= G ? (a << (G - 7 * d)) : (a >> (7 * d - G));
-            }
-          }
+                : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                  "=r"(v[d][6]), "=r"(v[d][7])
+                : "r"(tb + (uint32_t)(d * OZ_COLS)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
+            // sum_d acc_d 2^(OZ_G - 7 d) (the last diagonal through a truncating shift)
+            const long long V = ((long long)oz_int(v[0][i]) << OZ_G) + ((long long)oz_int(v[1][i]) << (OZ_G - 7)) +
+                                ((long long)oz_int(v[2][i]) << (OZ_G - 14)) +
+                                ((long long)oz_int(v[3][i]) << (OZ_G - 21)) +
+                                ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
+                                ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
+                                ((long long)oz_int(v[6][i]) << (OZ_G - 42)) + ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
             const int col = ch * 32 + cc * 8 + i;
-            const int sh = shA + s_fmax[col] - s_fs[s][col] - (nseg > 1 ? (int)s_del[row][col] : 0);
-            if (sh < 62) S[cc * 8 + i] += V[i] >> sh;
+            const int sh = guard + shA + s_fmax[col] - s_fs[s][col] - (nseg > 1 ? (int)s_del[row][col] : 0);
+            if (sh < 62) S[cc * 8 + i] += V >> sh;
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -415,7 +447,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
             const int EB = s_fmax[col];
             const int del = nseg > 1 ? (int)s_del[row][col] : 0;
             double val = (EA == 2047 || EB == 2047) ? __longlong_as_double(0x7FF8000000000000LL)
-                                                    : oz_to_double(S[i], EA + EB - del - 2056 - G);
+                                                    : oz_to_double(S[i], EA + EB - del - 2056 - OZ_G + guard);
             const i64 o = (i64)j * R + gr;
             if (op.D) val = fma(op.gamma, op.D[o], val);
             if (op.beta != 0.0) val = fma(op.beta, op.out[o], val);

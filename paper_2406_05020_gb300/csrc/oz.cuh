@@ -43,8 +43,10 @@ struct OzExpJobs {
 
 // bytes of the digit image of an N x K factor (zero padded to 64-row halves and 32-wide K blocks)
 i64 oz_image_bytes(int N, int K);
-// digit image and per-row exponent fields of alpha * F (F: N x K row-major FP64)
-void oz_split_factor(const double* F, int N, int K, double alpha, unsigned char* img, int* fexp, cudaStream_t st);
+// digit image and per-row exponent fields of alpha * F (F: N x K FP64, element
+// (j, k) at F[j * rs + k * cs])
+void oz_split_factor(const double* F, i64 rs, i64 cs, int N, int K, double alpha, unsigned char* img, int* fexp,
+                     cudaStream_t st);
 void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st);
 // tiles of one op (row tiles x column halves)
 i64 oz_tiles(int R, int N);
