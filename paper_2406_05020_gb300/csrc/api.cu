@@ -279,6 +279,8 @@ struct gpfvm_problem {
   double *d_ozY = nullptr, *d_ozZ = nullptr;
   i64 oz_ops_total = 0, oz_img_total = 0, oz_fexp_total = 0, oz_exp_total = 0;
   int oz_nu = 0, oz_nw = 0;
+  int* d_ozgexp = nullptr;  // window exponents of the digit-product dense GEMMs (2 x ozg_cap ints)
+  i64 ozg_cap = 0;
   // digit-product forms of other FP64 Kronecker chains (Builder::kron_digits):
   // op tables, factor images (strided views) and their slicing jobs
   struct OzxJob { const double* F; i64 rs, cs; int N, K; double alpha; i64 img_off, fexp_off; };
@@ -1354,6 +1356,17 @@ struct Builder {
   }
 };
 
+// Exponent scratch of the digit-product dense GEMMs (null Aexp: FMA GEMMs).
+OzChol ozchol(gpfvm_problem* p, int* status) {
+  OzChol o{};
+  if (!p->oz_on || !p->d_ozgexp) return o;
+  o.Aexp = p->d_ozgexp;
+  o.Bexp = p->d_ozgexp + p->ozg_cap;
+  o.cap = p->ozg_cap;
+  o.status = status;
+  return o;
+}
+
 // Structured IC/BC assembly (see icbc.cu): eigen-decompose set 0's 1D
 // factors, form the Schur complement of the other sets and factorise it.
 void build_sicbc(gpfvm_problem* p, Builder& B) {
@@ -1424,6 +1437,9 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
       const int ms = (int)p->sets[s].size;
       pl.func([=](cudaStream_t st) { axpy_block(pp->d_Sc + offR, MR, pp->d_Tsc, ms, MR, ms, -1.0, st); });
     }
+    // (FP64 FMA: the factorisation of these decaying, ill-conditioned Gram
+    // matrices needs errors relative to sum |a_k b_k|, which the fixed-point
+    // digit products, relative to max |a| max |b| per window, do not give)
     plan_chol_inverse(pl, p->d_Sc, p->d_LS, p->d_LSinv, MR, MR, p->d_sscr, p->d_st ? &p->d_st->pad[0] : nullptr);
     pl.func([=](cudaStream_t st) { transpose(pp->d_LSinv, pp->d_LSinvT, MR, MR, st); });
   }
@@ -1469,7 +1485,9 @@ void build_sicbc_var(gpfvm_problem* p, Builder& B) {
     g.m = MR; g.n = MK; g.k = MR;
     g.a_rs = MR; g.a_cs = 1; g.b_rs = MK; g.b_cs = 1; g.c_rs = MK;
     g.batch = 1; g.tri = TRI_A_LOWER; g.tile = dense_tile(MR, MK);
-    pl.gemm(g, {{GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, {GemmSeg{p->d_LSinv, p->d_Et, 1.0}}}});
+    OzChol ozc = ozchol(p, &p->d_st->status);
+    plan_dense_gemm(pl, g, GemmGroup{p->d_R, nullptr, 0.0, 0.0, 0, 0}, GemmSeg{p->d_LSinv, p->d_Et, 1.0},
+                    ozc.Aexp ? &ozc : nullptr);
   }
   const int Rrows = p->vb_rows;
   double* vB = p->d_vB;
@@ -2372,6 +2390,11 @@ void alloc_all(gpfvm_problem* p) {
       p->d_LinvT = m.alloc<double>(M * M);
       p->d_cscr = m.alloc<double>(M * M / 4 + 64 * M + 64);
     }
+    if (p->oz_on) {  // window exponents of the digit-product dense GEMMs (rows x windows, per operand)
+      const i64 big = std::max<i64>(M, p->MR);
+      p->ozg_cap = big * ((big + OZ_KMAX - 1) / OZ_KMAX);
+      p->d_ozgexp = m.alloc<int>(2 * p->ozg_cap);
+    }
     p->d_yB = m.alloc<double>(M);
     p->d_g = m.alloc<double>(M);
     p->d_t = m.alloc<double>(M);
@@ -2530,6 +2553,7 @@ int run_assemble(gpfvm_problem* p, cudaStream_t st) {
     copy_header_to_host(p, st);
     GPFVM_CUDA(cudaStreamSynchronize(st));
     if (p->h_st->pad[0] & DEV_NOT_SPD) return GPFVM_ERR_NOT_SPD;
+    if (p->h_st->pad[0] & DEV_TIMEOUT) return GPFVM_ERR_TIMEOUT;
   }
   p->p_rhs.run(st);
   if (p->oz_ok && p->d_ozimg)

@@ -10,6 +10,7 @@
 //   L22, L22^-1 = chol_inv(A22)
 //   (L^-1)21 = -L22^-1 (L21 L11^-1)
 // The base case (n <= 64) runs in one CTA from shared memory.
+#include "oz.cuh"
 #include "plan.cuh"
 
 namespace gpfvm {
@@ -93,8 +94,30 @@ static GemmDesc gdesc(int m, int n, int k, i64 a_rs, i64 a_cs, i64 b_rs, i64 b_c
   return g;
 }
 
+// One dense FP64 GEMM (one group, one segment): digit products for the large
+// ones (both sizes >= 128 and a contraction of at least 128) when `oz` is
+// given, else the FP64 FMA kernel.
+void plan_dense_gemm(Plan& plan, const GemmDesc& g, const GemmGroup& G, const GemmSeg& S, const OzChol* oz) {
+  const i64 nwin = (g.k + OZ_KMAX - 1) / OZ_KMAX;
+  if (oz && g.m >= 128 && g.n >= 128 && g.k >= 128 && g.a_cs == 1 && (g.b_rs == 1 || g.b_cs == 1) &&
+      (i64)g.m * nwin <= oz->cap && (i64)g.n * nwin <= oz->cap) {
+    OzGemm o{};
+    o.m = g.m; o.n = g.n; o.k = g.k;
+    o.A = S.A; o.a_rs = g.a_rs;
+    o.B = S.B; o.b_rs = g.b_rs; o.b_cs = g.b_cs;
+    o.C = G.C; o.c_rs = g.c_rs;
+    o.D = G.D; o.d_rs = g.d_rs;
+    o.alpha = S.alpha; o.beta = G.beta; o.gamma = G.gamma;
+    o.tri = g.tri;
+    int *ea = oz->Aexp, *eb = oz->Bexp, *st = oz->status;
+    plan.func([=](cudaStream_t s) { oz_gemm(o, ea, eb, st, s); });
+  } else {
+    plan.gemm(g, {{G, {S}}});
+  }
+}
+
 void plan_chol_inverse(Plan& plan, double* A, double* L, double* Linv, int n, i64 lda,
-                       double* scratch, int* status) {
+                       double* scratch, int* status, const OzChol* oz) {
   if (n <= 0) return;
   if (n <= 64) {
     plan.func([=](cudaStream_t st) { launch_chol_base(A, L, Linv, n, lda, status, st); });
@@ -109,28 +132,20 @@ void plan_chol_inverse(Plan& plan, double* A, double* L, double* Linv, int n, i6
   double* L22 = L21 + n1;
   double* Li21 = Linv + (i64)n1 * lda;
   double* Li22 = Li21 + n1;
-  plan_chol_inverse(plan, A, L, Linv, n1, lda, scratch, status);
+  plan_chol_inverse(plan, A, L, Linv, n1, lda, scratch, status, oz);
   // L21 = A21 * Linv11^T ; B(kk, j) = Linv11[j][kk] is upper triangular in (kk, j)
-  {
-    GemmGroup G{L21, nullptr, 0.0, 0.0, 0, 0};
-    plan.gemm(gdesc(n2, n1, n1, lda, 1, 1, lda, lda, TRI_B_UPPER), {{G, {GemmSeg{A21, Linv, 1.0}}}});
-  }
+  plan_dense_gemm(plan, gdesc(n2, n1, n1, lda, 1, 1, lda, lda, TRI_B_UPPER), GemmGroup{L21, nullptr, 0.0, 0.0, 0, 0},
+            GemmSeg{A21, Linv, 1.0}, oz);
   // A22 -= L21 * L21^T (lower tiles)
-  {
-    GemmGroup G{A22, nullptr, 1.0, 0.0, 0, 0};
-    plan.gemm(gdesc(n2, n2, n1, lda, 1, 1, lda, lda, TRI_C_LOWER), {{G, {GemmSeg{L21, L21, -1.0}}}});
-  }
-  plan_chol_inverse(plan, A22, L22, Li22, n2, lda, scratch, status);
+  plan_dense_gemm(plan, gdesc(n2, n2, n1, lda, 1, 1, lda, lda, TRI_C_LOWER), GemmGroup{A22, nullptr, 1.0, 0.0, 0, 0},
+            GemmSeg{L21, L21, -1.0}, oz);
+  plan_chol_inverse(plan, A22, L22, Li22, n2, lda, scratch, status, oz);
   // T = L21 * Linv11 (Linv11 lower: B(kk, j) = 0 for kk < j)
-  {
-    GemmGroup G{scratch, nullptr, 0.0, 0.0, 0, 0};
-    plan.gemm(gdesc(n2, n1, n1, lda, 1, lda, 1, n1, TRI_B_LOWER), {{G, {GemmSeg{L21, Linv, 1.0}}}});
-  }
+  plan_dense_gemm(plan, gdesc(n2, n1, n1, lda, 1, lda, 1, n1, TRI_B_LOWER), GemmGroup{scratch, nullptr, 0.0, 0.0, 0, 0},
+            GemmSeg{L21, Linv, 1.0}, oz);
   // Linv21 = -Linv22 * T (Linv22 lower: A(i, kk) = 0 for kk > i)
-  {
-    GemmGroup G{Li21, nullptr, 0.0, 0.0, 0, 0};
-    plan.gemm(gdesc(n2, n1, n2, lda, 1, n1, 1, lda, TRI_A_LOWER), {{G, {GemmSeg{Li22, scratch, -1.0}}}});
-  }
+  plan_dense_gemm(plan, gdesc(n2, n1, n2, lda, 1, n1, 1, lda, TRI_A_LOWER), GemmGroup{Li21, nullptr, 0.0, 0.0, 0, 0},
+            GemmSeg{Li22, scratch, -1.0}, oz);
 }
 
 }  // namespace gpfvm

@@ -43,6 +43,7 @@ namespace gpfvm {
 
 constexpr int OZ_THREADS = 256;
 constexpr int OZ_G = 43;  // binary point of one segment's 64-bit sum (see the drain)
+constexpr int OZ_NONFINITE = 0x7fffffff;  // block exponent of a sum that met a NaN or infinity
 constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
 constexpr int OZ_DYN_SMEM = 2 * OZ_SET + 1024;
 
@@ -487,6 +488,316 @@ void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, 
   }
   const int grid = (int)std::min<i64>(total_tiles, std::max(sms, 1));
   launch_pdl(oz_mode_kernel, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM by digit products for long K (the dense FP64 work of the IC/BC
+// Cholesky stage): C = beta C + gamma D + alpha A B.  K is cut into windows of
+// OZ_KMAX with their own row / column exponents (oz_gemm_exponents); every
+// window's 8 diagonals are exact as above, and are added into per-output
+// block-floating 64-bit sums: S with exponent eS, rescaled when a window with
+// a larger scale arrives, each window shifted down by `guard` bits so that up
+// to 2^guard windows cannot overflow.
+
+// largest exponent field of every (row, window) of a K-major (sk == 1, warp per
+// row) or row-major-across-rows (sr == 1, thread per row) operand; `tri`
+// zeroes (kk > row) for 1 and (kk < row) for 2
+__global__ void __launch_bounds__(256) oz_winexp_kernel(const double* __restrict__ X, i64 sr, i64 sk, int rows, int K,
+                                                        int nwin, int tri, int* __restrict__ ex, const int* skip) {
+  pdl_wait();
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  if (sk == 1) {
+    const i64 total = (i64)rows * nwin, nw = (i64)gridDim.x * 8;
+    for (i64 w = (i64)blockIdx.x * 8 + (threadIdx.x >> 5); w < total; w += nw) {
+      const int r = (int)(w / nwin), win = (int)(w % nwin);
+      int e = 0;
+      for (int k = win * OZ_KMAX + lane; k < min(K, (win + 1) * OZ_KMAX); k += 32) {
+        if ((tri == 1 && k > r) || (tri == 2 && k < r)) continue;
+        e = max(e, oz_field((unsigned long long)__double_as_longlong(__ldg(X + r * sr + k))));
+      }
+      e = __reduce_max_sync(0xffffffffu, e);
+      if (lane == 0) ex[(i64)r * nwin + win] = e;
+    }
+  } else {
+    const i64 total = (i64)rows * nwin;
+    for (i64 w = (i64)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (i64)gridDim.x * blockDim.x) {
+      const int win = (int)(w / rows), r = (int)(w % rows);  // consecutive threads: consecutive rows
+      int e = 0;
+      for (int k = win * OZ_KMAX; k < min(K, (win + 1) * OZ_KMAX); ++k) {
+        if ((tri == 1 && k > r) || (tri == 2 && k < r)) continue;
+        e = max(e, oz_field((unsigned long long)__double_as_longlong(__ldg(X + r * sr + k * sk))));
+      }
+      ex[(i64)r * nwin + win] = e;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzGemm g, int* status) {
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t mma_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int s_ea[OZ_ROWS], s_eb[OZ_COLS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(OZ_DIGITS * OZ_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  pdl_wait();
+  if (g.skip && *g.skip) goto done;
+  {
+    uint32_t mph0 = 0, mph1 = 0;
+    int mpend0 = 0, mpend1 = 0;
+    auto wait_mma = [&](int b) {
+      const bool ok = b ? mbar_wait(&mma_bar[1], mph1) : mbar_wait(&mma_bar[0], mph0);
+      if (b) { mph1 ^= 1u; mpend1 = 0; } else { mph0 ^= 1u; mpend0 = 0; }
+      if (!ok) {
+        atomicOr(status, (int)DEV_TIMEOUT);
+        abort_flag = 1;
+      }
+    };
+    const uint32_t idesc = idesc_bf16(OZ_COLS);
+    const int q = warp & 3, ch = warp >> 2;
+    const int srow = tid >> 1, kh = tid & 1;
+    const bool bk = g.b_rs == 1;  // B K-major (rows of B^T contiguous)
+    const int bj = bk ? (tid >> 2) : (tid & 63), bq = bk ? (tid & 3) : (tid >> 6);
+    const int tiles_n = (g.n + OZ_COLS - 1) / OZ_COLS;
+    const i64 total = (i64)((g.m + OZ_ROWS - 1) / OZ_ROWS) * tiles_n;
+    for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
+      if (abort_flag) break;
+      const int row0 = (int)(t / tiles_n) * OZ_ROWS, col0 = (int)(t % tiles_n) * OZ_COLS;
+      if ((g.tri & TRI_C_LOWER) && col0 > row0 + OZ_ROWS - 1) continue;
+      // windows that can be nonzero for this tile
+      int w_lo = 0, w_hi = g.nwin - 1;
+      if (g.tri & TRI_A_LOWER) w_hi = min(w_hi, (row0 + OZ_ROWS - 1) / OZ_KMAX);
+      if (g.tri & TRI_A_UPPER) w_lo = max(w_lo, row0 / OZ_KMAX);
+      if (g.tri & TRI_B_UPPER) w_hi = min(w_hi, (col0 + OZ_COLS - 1) / OZ_KMAX);
+      if (g.tri & TRI_B_LOWER) w_lo = max(w_lo, col0 / OZ_KMAX);
+      const int nw = w_hi - w_lo + 1;
+      const int guard = nw > 1 ? 32 - __clz(nw - 1) : 0;
+      long long S[32];
+      int eS[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) { S[i] = 0; eS[i] = -1000000; }
+      const int nstage = nw > 0 ? nw * (OZ_KMAX / OZ_KB) : 0;
+      double ra[16], rb[8];
+      auto load_stage = [&](int st2) {
+        const int kk0 = (w_lo + st2 / (OZ_KMAX / OZ_KB)) * OZ_KMAX + (st2 % (OZ_KMAX / OZ_KB)) * OZ_KB;
+        const int gr = row0 + srow, ka = kk0 + kh * 16;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int k = ka + i;
+          const bool z = gr >= g.m || k >= g.k || ((g.tri & TRI_A_LOWER) && k > gr) || ((g.tri & TRI_A_UPPER) && k < gr);
+          ra[i] = z ? 0.0 : __ldg(g.A + (i64)gr * g.a_rs + k);
+        }
+        const int gj = col0 + bj, kb2 = kk0 + bq * 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = kb2 + i;
+          const bool z = gj >= g.n || k >= g.k || ((g.tri & TRI_B_UPPER) && k > gj) || ((g.tri & TRI_B_LOWER) && k < gj);
+          rb[i] = z ? 0.0 : __ldg(g.B + (i64)k * g.b_rs + (i64)gj * g.b_cs);
+        }
+      };
+      if (nstage > 0) load_stage(0);
+      for (int st = 0; st < nstage; ++st) {
+        const int kb = st % (OZ_KMAX / OZ_KB), win = w_lo + st / (OZ_KMAX / OZ_KB), b = st & 1;
+        if (kb == 0) {  // this window's exponents (the previous window is drained)
+          if (tid < OZ_ROWS) s_ea[tid] = row0 + tid < g.m ? g.Aexp[(i64)(row0 + tid) * g.nwin + win] : 0;
+          else if (tid < OZ_ROWS + OZ_COLS) {
+            const int j = col0 + tid - OZ_ROWS;
+            s_eb[tid - OZ_ROWS] = j < g.n ? g.Bexp[(i64)j * g.nwin + win] : 0;
+          }
+          __syncthreads();
+        }
+        if (b ? mpend1 : mpend0) wait_mma(b);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* sA = base + b * OZ_SET;
+        unsigned char* sB = sA + OZ_DIGITS * OZ_A_PLANE;
+        {  // A: 16 values of row srow
+          const int emax = s_ea[srow];
+#pragma unroll
+          for (int q2 = 0; q2 < 2; ++q2) {
+            uint32_t w[OZ_DIGITS][4];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+              uint32_t h0, l0, h1, l1;
+              float s0, o0, s1, o1;
+              oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2]), emax, h0, l0, s0, o0);
+              oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2 + 1]), emax, h1, l1, s1, o1);
+#define OZ_PAIR(J) w[J][p2] = __byte_perm(oz_digit_f32<J>(h0, l0, s0, o0), oz_digit_f32<J>(h1, l1, s1, o1), 0x7632)
+              OZ_PAIR(0); OZ_PAIR(1); OZ_PAIR(2); OZ_PAIR(3); OZ_PAIR(4); OZ_PAIR(5); OZ_PAIR(6); OZ_PAIR(7);
+#undef OZ_PAIR
+            }
+            const uint32_t off = sw64(srow, kh * 16 + q2 * 8);
+#pragma unroll
+            for (int j = 0; j < OZ_DIGITS; ++j)
+              *(uint4*)(sA + j * OZ_A_PLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+          }
+        }
+        {  // B: 8 values of B^T row bj (K-block chunk bq)
+          const int emax = s_eb[bj];
+          uint32_t w[OZ_DIGITS][4];
+#pragma unroll
+          for (int p2 = 0; p2 < 4; ++p2) {
+            uint32_t h0, l0, h1, l1;
+            float s0, o0, s1, o1;
+            oz_prep((unsigned long long)__double_as_longlong(rb[2 * p2]), emax, h0, l0, s0, o0);
+            oz_prep((unsigned long long)__double_as_longlong(rb[2 * p2 + 1]), emax, h1, l1, s1, o1);
+#define OZ_PAIR(J) w[J][p2] = __byte_perm(oz_digit_f32<J>(h0, l0, s0, o0), oz_digit_f32<J>(h1, l1, s1, o1), 0x7632)
+            OZ_PAIR(0); OZ_PAIR(1); OZ_PAIR(2); OZ_PAIR(3); OZ_PAIR(4); OZ_PAIR(5); OZ_PAIR(6); OZ_PAIR(7);
+#undef OZ_PAIR
+          }
+          const uint32_t off = sw64(bj, bq * 8);
+#pragma unroll
+          for (int j = 0; j < OZ_DIGITS; ++j)
+            *(uint4*)(sB + j * OZ_B_PLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da0 = desc_sw64(smem_u32(sA)), db0 = desc_sw64(smem_u32(sB));
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t dak = da0 + (uint64_t)(ks * 2), dbk = db0 + (uint64_t)(ks * 2);
+#pragma unroll
+            for (int d = 0; d < OZ_DIGITS; ++d) {
+#pragma unroll
+              for (int a = 0; a <= d; ++a)
+                mma_bf16(tmem + d * OZ_COLS, dak + (uint64_t)(a * (OZ_A_PLANE >> 4)),
+                         dbk + (uint64_t)((d - a) * (OZ_B_PLANE >> 4)), idesc, (kb > 0 || ks > 0 || a > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(b ? &mma_bar[1] : &mma_bar[0]);
+        }
+        if (b) mpend1 = 1; else mpend0 = 1;
+        if (st + 1 < nstage) load_stage(st + 1);
+        if (kb == OZ_KMAX / OZ_KB - 1) {
+          // window complete: fold its diagonals into the block-floating sums
+          if (mpend0) wait_mma(0);
+          if (mpend1) wait_mma(1);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int row = q * 32 + lane;
+          const int ea = s_ea[row];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            uint32_t v[OZ_DIGITS][8];
+            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32 + cc * 8);
+#pragma unroll
+            for (int d = 0; d < OZ_DIGITS; ++d)
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                  : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                    "=r"(v[d][6]), "=r"(v[d][7])
+                  : "r"(tb + (uint32_t)(d * OZ_COLS)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const long long V = ((long long)oz_int(v[0][i]) << OZ_G) + ((long long)oz_int(v[1][i]) << (OZ_G - 7)) +
+                                  ((long long)oz_int(v[2][i]) << (OZ_G - 14)) +
+                                  ((long long)oz_int(v[3][i]) << (OZ_G - 21)) +
+                                  ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
+                                  ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
+                                  ((long long)oz_int(v[6][i]) << (OZ_G - 42)) +
+                                  ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
+              const int k = cc * 8 + i;
+              const int eb = s_eb[ch * 32 + k];
+              const int ew = ea + eb;
+              if (ea == 2047 || eb == 2047) eS[k] = OZ_NONFINITE;  // a NaN or infinity in this window
+              if (V != 0 && eS[k] != OZ_NONFINITE) {
+                if (ew > eS[k]) {  // rescale the sum to the new, larger scale
+                  const int dsh = ew - eS[k];
+                  S[k] = dsh < 62 ? (S[k] >> dsh) : 0;
+                  eS[k] = ew;
+                }
+                const int sh = guard + eS[k] - ew;
+                if (sh < 62) S[k] += V >> sh;
+              }
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncthreads();
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+      }
+      if (!abort_flag) {
+        const int row = q * 32 + lane, gr = row0 + row;
+        if (gr < g.m) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int j = col0 + ch * 32 + i;
+            if (j < g.n) {
+              double val = eS[i] == OZ_NONFINITE ? __longlong_as_double(0x7FF8000000000000LL)
+                           : S[i] == 0                ? 0.0
+                                                      : oz_to_double(S[i], eS[i] - 2056 - OZ_G + guard);
+              val *= g.alpha;
+              double* c = g.C + (i64)gr * g.c_rs + j;
+              if (g.beta != 0.0) val = fma(g.beta, *c, val);
+              if (g.D) val = fma(g.gamma, g.D[(i64)gr * g.d_rs + j], val);
+              *c = val;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (mpend0) mbar_wait(&mma_bar[0], mph0);
+    if (mpend1) mbar_wait(&mma_bar[1], mph1);
+  }
+done:
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_DIGITS * OZ_COLS)
+                 : "memory");
+  }
+}
+
+void oz_gemm(const OzGemm& g0, int* Aexp, int* Bexp, int* status, cudaStream_t st) {
+  if (g0.m <= 0 || g0.n <= 0) return;
+  OzGemm g = g0;
+  g.nwin = (g.k + OZ_KMAX - 1) / OZ_KMAX;
+  g.Aexp = Aexp;
+  g.Bexp = Bexp;
+  const int triA = (g.tri & TRI_A_LOWER) ? 1 : (g.tri & TRI_A_UPPER) ? 2 : 0;
+  const int triB = (g.tri & TRI_B_UPPER) ? 1 : (g.tri & TRI_B_LOWER) ? 2 : 0;
+  if (g.k > 0) {
+    const i64 ra = (i64)g.m * g.nwin, rb = (i64)g.n * g.nwin;
+    launch_pdl(oz_winexp_kernel, (int)std::min<i64>((ra + 7) / 8, 8 * 152), 256, 0, st, g.A, g.a_rs, (i64)1, g.m, g.k,
+               g.nwin, triA, Aexp, g.skip);
+    if (g.b_rs == 1)
+      launch_pdl(oz_winexp_kernel, (int)std::min<i64>((rb + 7) / 8, 8 * 152), 256, 0, st, g.B, g.b_cs, (i64)1, g.n,
+                 g.k, g.nwin, triB, Bexp, g.skip);
+    else
+      launch_pdl(oz_winexp_kernel, (int)std::min<i64>((rb + 255) / 256, 8 * 152), 256, 0, st, g.B, g.b_cs, g.b_rs,
+                 g.n, g.k, g.nwin, triB, Bexp, g.skip);
+  }
+  static int sms = 0;
+  static bool attr = false;
+  if (!attr) {
+    int dev = 0;
+    GPFVM_CUDA(cudaGetDevice(&dev));
+    GPFVM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GPFVM_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_DYN_SMEM));
+    attr = true;
+  }
+  const i64 tiles = (i64)((g.m + OZ_ROWS - 1) / OZ_ROWS) * ((g.n + OZ_COLS - 1) / OZ_COLS);
+  launch_pdl(oz_gemm_kernel, (int)std::min<i64>(tiles, std::max(sms, 1)), OZ_THREADS, OZ_DYN_SMEM, st, g, status);
 }
 
 }  // namespace gpfvm

@@ -52,4 +52,28 @@ void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st);
 i64 oz_tiles(int R, int N);
 void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, cudaStream_t st);
 
+// C = beta C + gamma D + alpha A B in FP64 by digit products for long K:
+// A(i, kk) = A[i a_rs + kk] (m x k), B(kk, j) = B[kk b_rs + j b_cs] with
+// b_rs == 1 or b_cs == 1, C(i, j) = C[i c_rs + j], D likewise with d_rs;
+// tri: GemmTri flags (zero triangles of A / B are masked, TRI_C_LOWER skips
+// the tiles above the diagonal).  Aexp / Bexp: device scratch of m and n
+// times ceil(k / 128) ints (the per-window exponents, written here).
+struct OzGemm {
+  int m, n, k, nwin;
+  const double* A;
+  i64 a_rs;
+  const double* B;
+  i64 b_rs, b_cs;
+  double* C;
+  i64 c_rs;
+  const double* D;
+  i64 d_rs;
+  double alpha, beta, gamma;
+  int tri;
+  const int* Aexp;
+  const int* Bexp;
+  const int* skip;
+};
+void oz_gemm(const OzGemm& g, int* Aexp, int* Bexp, int* status, cudaStream_t st);
+
 }  // namespace gpfvm

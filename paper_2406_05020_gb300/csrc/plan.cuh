@@ -580,8 +580,20 @@ class Plan {
 // Builds the recursive Cholesky + inverse of an n x n SPD matrix A (lower
 // triangle read, lda) into L and Linv (lower, row-major, lda); scratch must
 // hold n*n/4 + 64 doubles.  status receives DEV_NOT_SPD on a pivot <= 0.
+// Dense FP64 GEMMs of the factorisation by digit products on the tensor cores
+// (oz_gemm) when given: exponent scratch for m and n rows of ceil(k / 128)
+// windows each (rows x windows <= cap) and the status word of bounded waits.
+struct OzChol {
+  int* Aexp;
+  int* Bexp;
+  i64 cap;
+  int* status;
+};
 void plan_chol_inverse(Plan& plan, double* A, double* L, double* Linv, int n, i64 lda,
-                       double* scratch, int* status);
+                       double* scratch, int* status, const OzChol* oz = nullptr);
+// One dense FP64 GEMM (one group, one segment; a_cs == 1): by digit products
+// when `oz` is given and it is large, else the FP64 FMA kernel.
+void plan_dense_gemm(Plan& plan, const GemmDesc& g, const GemmGroup& G, const GemmSeg& S, const OzChol* oz);
 int dense_tile(int m, int n);
 
 }  // namespace gpfvm
