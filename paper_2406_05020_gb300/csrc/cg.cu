@@ -211,24 +211,33 @@ __global__ void __launch_bounds__(RT) k_reorth_dots(const T* __restrict__ Q, i64
   T pv[NV][W];
 #pragma unroll
   for (int v = 0; v < NV; ++v) ldv(p, base + (i64)(v * 32 + lane) * W, n, pv[v]);
+  // four directions per warp at a time: eight independent FMA chains per lane
+  // (the FP64 FMA pipe, not HBM, bounds this kernel on parts with a low FP64 rate)
   const int wstride = gridDim.y * (RT / 32);
-  for (int j = blockIdx.y * (RT / 32) + warp; j < k; j += wstride) {
-    const T* __restrict__ qj = Q + (i64)j * ld;
-    T a0 = T(0), a1 = T(0);
+  for (int j0 = (blockIdx.y * (RT / 32) + warp) * 4; j0 < k; j0 += wstride * 4) {
+    const T* __restrict__ qj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) qj[u] = Q + (i64)min(j0 + u, k - 1) * ld;
+    T a[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u][0] = a[u][1] = T(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      T qv[W];
-      ldv(qj, base + (i64)(v * 32 + lane) * W, n, qv);
+      T qv[4][W];
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        if (w & 1) a1 = fma(qv[w], pv[v][w], a1);
-        else a0 = fma(qv[w], pv[v][w], a0);
-      }
+      for (int u = 0; u < 4; ++u) ldv(qj[u], base + (i64)(v * 32 + lane) * W, n, qv[u]);
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u][w & 1] = fma(qv[u][w], pv[v][w], a[u][w & 1]);
     }
-    double sum = (double)a0 + (double)a1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) part2[(i64)j * nchunk + c] = sum;
+    for (int u = 0; u < 4; ++u) {
+      double sum = (double)a[u][0] + (double)a[u][1];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0 && j0 + u < k) part2[(i64)(j0 + u) * nchunk + c] = sum;
+    }
   }
 }
 
@@ -395,9 +404,10 @@ void reorth_coefs(const T* Q, const T* p, i64 n, int cap, CGState* st, double* p
                   const double* eta_hist, cudaStream_t s) {
   const i64 ld = store_ld(n);
   const int nchunk = reorth_chunks(n);
-  // split the directions over blockIdx.y until about four CTAs per SM are busy
+  // split the directions (in groups of four per warp) over blockIdx.y until
+  // about four CTAs per SM are busy
   int gy = (4 * 152 + nchunk - 1) / nchunk;
-  gy = std::max(1, std::min(gy, ceil_div(cap, RT / 32)));
+  gy = std::max(1, std::min(gy, ceil_div(cap, 4 * (RT / 32))));
   launch_pdl(k_reorth_dots<T>, dim3(nchunk, gy), RT, 0, s, Q, ld, p, n, st, part2, eta_hist, coef);
   if (cap > 0) launch_pdl(k_reorth_coef, cap, RT, 0, s, (const CGState*)st, nchunk, (const double*)part2, eta_hist, coef);
 }
