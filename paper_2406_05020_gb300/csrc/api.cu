@@ -1186,10 +1186,8 @@ struct Builder {
     Plan PP, PR;
     if (pp_chain) PP = std::move(*pp_chain);
     else kron(PP, dc, dc, 1, pp_terms(p), p->s2, in, out, 0.0, in, p->jitter, count);
-    // the variance product (outside the CG recurrence) by digit products; the
-    // IC/BC chains stay in FP64 FMA: their factor rows decay over many orders
-    // of magnitude, where the fixed-point digit error (relative to a row's
-    // largest entry) exceeds FMA rounding enough to break CG run to 1e-13
+    // the Kronecker chains of G_PR (variance) and of the IC/BC sets off the
+    // box faces run as digit products when the FP64 form is chosen
     if (u && !kron_digits(PR, dc, dp, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0, skip))
       kron(PR, dc, dp, 1, ppred_terms(p), p->s2, in, u, 0.0, nullptr, 0.0);
     std::vector<const Plan*> cs;
@@ -1219,7 +1217,9 @@ struct Builder {
             lbp = std::max(lbp, lv[k - f0] + 1);
           }
         } else {
-          kron(BP[s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
+          if (!kron_digits(BP[s], dc, ds, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr,
+                           0.0, skip))
+            kron(BP[s], dc, ds, 1, pb_terms(p, s, true, true), p->s2, in, at(g, p->sets[s].off), 0.0, nullptr, 0.0);
           lbp = std::max(lbp, (int)BP[s].ops.size());
           put(BP[s], 0);
         }
@@ -1253,15 +1253,19 @@ struct Builder {
       for (size_t k = 0; k < gen_o.size(); ++k) {
         const int s = gen_o[k];
         dims_set(p, s, ds);
-        kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), at(T, (i64)k * sN), 0.0,
-             nullptr, 0.0);
+        if (!kron_digits(PB[s], ds, dc, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off),
+                         at(T, (i64)k * sN), 0.0, nullptr, 0.0, skip))
+          kron(PB[s], ds, dc, 1, pb_terms(p, s, false, true), -p->s2, at(w, p->sets[s].off), at(T, (i64)k * sN), 0.0,
+               nullptr, 0.0);
         put(PB[s], r_of[s]);
       }
       for (size_t k = 0; k < gen_u.size(); ++k) {
         const int s = gen_u[k];
         dims_set(p, s, ds);
-        kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, (i64)k * sP), 0.0,
-             nullptr, 0.0);
+        if (!kron_digits(VS[s], ds, dp, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, (i64)k * sP),
+                         0.0, nullptr, 0.0, skip))
+          kron(VS[s], ds, dp, 1, bpred_terms(p, s, true), -p->s2, at(w, p->sets[s].off), at(V, (i64)k * sP), 0.0,
+               nullptr, 0.0);
         put(VS[s], r_of[s]);
       }
       auto expadd = [&](Plan& pl, double* dst, i64 n, const int* dt, const double* parts, int np, i64 stride,
