@@ -270,7 +270,7 @@ struct gpfvm_problem {
   bool oz_on = true;    // the FP64 CG and residual plans use it (desc fp64_products == 0)
   struct OzJob { i64 fac_off; int n; double alpha; i64 img_off, fexp_off; };
   std::vector<OzJob> oz_jobs;
-  struct OzLevel { int off, nops; i64 tiles; OzExpJobs jobs; };
+  struct OzLevel { int off, nops; i64 tiles; OzExpJobs jobs; int n; };  // n: the level's outputs per row (uniform)
   std::vector<OzLevel> oz_levels[3];
   OzOp* d_ozops = nullptr;
   unsigned char* d_ozimg = nullptr;
@@ -556,7 +556,7 @@ struct Builder {
       return std::make_pair(p->d_ozximg ? (const unsigned char*)(p->d_ozximg + it->second.first) : nullptr,
                             p->d_ozxfexp ? (const int*)(p->d_ozxfexp + it->second.second) : nullptr);
     };
-    struct Lv { int off, nops; i64 tiles; OzExpJobs jobs; };
+    struct Lv { int off, nops; i64 tiles; OzExpJobs jobs; int n; };
     std::vector<Lv> lv;
     bool ok = true;
     const size_t first_op = p->ozx_ops.size();
@@ -593,6 +593,8 @@ struct Builder {
     auto add_op = [&](OzOp op) {
       auto& L = lv.back();
       op.tile_begin = L.tiles;
+      if (L.nops > 0 && L.n != op.N) ok = false;  // one tiling per launch
+      L.n = op.N;
       L.tiles += oz_tiles(op.R, op.N);
       L.nops++;
       p->ozx_ops.push_back(op);
@@ -668,10 +670,11 @@ struct Builder {
       const OzOp* ops = p->d_ozxops ? p->d_ozxops + L.off : nullptr;
       const int nops = L.nops;
       const i64 tiles = L.tiles;
+      const int nl = L.n;
       int* status = &p->d_st->status;
       plan.func([=](cudaStream_t st) {
         oz_row_exponents(J, st);
-        launch_oz_modes(ops, nops, tiles, status, st);
+        launch_oz_modes(ops, nops, tiles, nl, status, st);
       });
     }
     return true;
@@ -1609,6 +1612,8 @@ void build_oz_instance(gpfvm_problem* p, OzBuild& O, const double* in, double* o
   auto add_op = [&](OzOp op) {
     auto& L = levels.back();
     op.tile_begin = L.tiles;
+    if (L.nops > 0 && L.n != op.N) O.ok = false;  // one tiling per launch
+    L.n = op.N;
     L.tiles += oz_tiles(op.R, op.N);
     L.nops++;
     if (op.N > 128 || op.K > OZ_KMAX) O.ok = false;
@@ -1723,10 +1728,11 @@ Plan oz_chain(gpfvm_problem* p, int inst) {
     const OzOp* ops = p->d_ozops ? p->d_ozops + L.off : nullptr;
     const int nops = L.nops;
     const i64 tiles = L.tiles;
+    const int nl = L.n;
     int* status = &p->d_st->status;
     c.func([=](cudaStream_t st) {
       oz_row_exponents(J, st);
-      launch_oz_modes(ops, nops, tiles, status, st);
+      launch_oz_modes(ops, nops, tiles, nl, status, st);
     });
   }
   return c;

@@ -47,12 +47,25 @@ constexpr int OZ_NONFINITE = 0x7fffffff;  // block exponent of a sum that met a 
 constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
 constexpr int OZ_DYN_SMEM = 2 * OZ_SET + 1024;
 
+// Outputs of 64 < N <= 128 take the "tall" tiling: the factor (128 rows, all
+// outputs) is the MMA's M side and 64 tensor rows its N side, so every tensor
+// element is sliced once; otherwise the factor is the N side (64 outputs per
+// tile) and 128 tensor rows the M side.
+bool oz_tall(int N) { return N > OZ_COLS && N <= 2 * OZ_COLS; }
+
+// rows of one factor digit-image block: 128 for the tall tiling, else 64
+static int oz_img_rows(int N) { return oz_tall(N) ? 2 * OZ_COLS : OZ_COLS; }
+
 i64 oz_image_bytes(int N, int K) {
-  const int nh = (N + OZ_COLS - 1) / OZ_COLS, nkb = (K + OZ_KB - 1) / OZ_KB;
-  return (i64)nkb * nh * OZ_IMG_STAGE;
+  const int rb = oz_img_rows(N);
+  const int nh = (N + rb - 1) / rb, nkb = (K + OZ_KB - 1) / OZ_KB;
+  return (i64)nkb * nh * OZ_DIGITS * rb * 64;
 }
 
-i64 oz_tiles(int R, int N) { return (i64)((R + OZ_ROWS - 1) / OZ_ROWS) * ((N + OZ_COLS - 1) / OZ_COLS); }
+i64 oz_tiles(int R, int N) {
+  if (oz_tall(N)) return (R + OZ_COLS - 1) / OZ_COLS;
+  return (i64)((R + OZ_ROWS - 1) / OZ_ROWS) * ((N + OZ_COLS - 1) / OZ_COLS);
+}
 
 __device__ __forceinline__ int oz_field(unsigned long long bits) { return (int)((bits >> 52) & 0x7ff); }
 
@@ -173,15 +186,15 @@ void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st) {
   launch_pdl(oz_rowexp_kernel, grid, 256, 0, st, jobs);
 }
 
-// digit image of alpha F (one warp per row j): plane l of (K block kb, column
-// half h) at img + ((kb * nh + h) * 8 + l) * OZ_B_PLANE, 64-byte-swizzled rows
+// digit image of alpha F (one warp per row j): plane l of (K block kb, row
+// block h of rb rows) at img + ((kb * nh + h) * 8 + l) * rb * 64, 64-byte-swizzled rows
 __global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ F, i64 rs, i64 cs, int N, int K,
-                                                       double alpha, unsigned char* __restrict__ img,
+                                                       int rb, double alpha, unsigned char* __restrict__ img,
                                                        int* __restrict__ fexp) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= N) return;  // whole warps
-  const int nh = (N + OZ_COLS - 1) / OZ_COLS;
+  const int nh = (N + rb - 1) / rb;
   int e = 0;
   for (int k = lane; k < K; k += 32) e = max(e, oz_field((unsigned long long)__double_as_longlong(alpha * F[j * rs + k * cs])));
   e = __reduce_max_sync(0xffffffffu, e);
@@ -200,10 +213,10 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict_
     f[5] = oz_digit_f32<5>(yh, yl, sg, of);
     f[6] = oz_digit_f32<6>(yh, yl, sg, of);
     f[7] = oz_digit_f32<7>(yh, yl, sg, of);
-    unsigned char* blk = img + ((i64)(k / OZ_KB) * nh + j / OZ_COLS) * OZ_IMG_STAGE;
-    const uint32_t off = sw64(j % OZ_COLS, k % OZ_KB);
+    unsigned char* blk = img + ((i64)(k / OZ_KB) * nh + j / rb) * (OZ_DIGITS * rb * 64);
+    const uint32_t off = sw64(j % rb, k % OZ_KB);
 #pragma unroll
-    for (int l = 0; l < OZ_DIGITS; ++l) *(unsigned short*)(blk + l * OZ_B_PLANE + off) = (unsigned short)(f[l] >> 16);
+    for (int l = 0; l < OZ_DIGITS; ++l) *(unsigned short*)(blk + l * rb * 64 + off) = (unsigned short)(f[l] >> 16);
   }
 }
 
@@ -211,22 +224,29 @@ void oz_split_factor(const double* F, i64 rs, i64 cs, int N, int K, double alpha
                      cudaStream_t st) {
   if (N <= 0 || K <= 0) return;
   GPFVM_CUDA(cudaMemsetAsync(img, 0, oz_image_bytes(N, K), st));
-  oz_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(F, rs, cs, N, K, alpha, img, fexp);
+  oz_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(F, rs, cs, N, K, oz_img_rows(N), alpha, img, fexp);
   GPFVM_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------------------
+// TALL: see oz_tall.  TR tensor rows and TC outputs per tile; the M side of
+// the MMA (128 rows: TMEM lanes) is the factor when TALL, else the tensor.
+template <bool TALL>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __restrict__ ops, int nops, i64 total,
                                                                int* status) {
+  constexpr int TR = TALL ? OZ_COLS : OZ_ROWS, TC = TALL ? 2 * OZ_COLS : OZ_COLS;
+  constexpr int TPLANE = TR * 64, FPLANE = TC * 64;      // digit plane bytes: tensor, factor
+  constexpr int FIMG = OZ_DIGITS * FPLANE;               // one factor image block
+  constexpr int EPT = TALL ? 8 : 16, PARTS = OZ_KB / EPT;  // tensor elements per thread and stage
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t mma_bar[2], full_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ int s_es[OZ_MAXSEG][OZ_ROWS], s_fs[OZ_MAXSEG][OZ_COLS];
-  __shared__ int s_emax[OZ_ROWS], s_fmax[OZ_COLS];
+  __shared__ int s_es[OZ_MAXSEG][TR], s_fs[OZ_MAXSEG][TC];
+  __shared__ int s_emax[TR], s_fmax[TC];
   // per output: how far the largest segment scale 2^(E_s + F_s) lies below 2^(emax + fmax)
-  __shared__ unsigned char s_del[OZ_ROWS][OZ_COLS];
+  __shared__ unsigned char s_del[TR][TC];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -262,7 +282,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
   };
   const uint32_t idesc = idesc_bf16(OZ_COLS);
   const int q = warp & 3, ch = warp >> 2;     // drain / epilogue: TMEM lane quadrant, 32-column half
-  const int srow = tid >> 1, kh = tid & 1;    // staging: tile row, 16-wide half of the K block
+  const int srow = tid / PARTS, kh = tid % PARTS;  // staging: tensor row, EPT-wide part of the K block
 
   for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
     if (abort_flag) break;
@@ -274,34 +294,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     const OzOp& op = ops[lo];
     if (op.skip && *op.skip) continue;
     const int R = op.R, K = op.K, N = op.N, nseg = op.nseg;
-    const int nh = (N + OZ_COLS - 1) / OZ_COLS;
+    const int nh = TALL ? 1 : (N + TC - 1) / TC;
     const i64 local = t - op.tile_begin;
     const int h = (int)(local % nh);
-    const int row0 = (int)(local / nh) * OZ_ROWS;
-    for (int i = tid; i < nseg * OZ_ROWS; i += OZ_THREADS) {
-      const int s = i / OZ_ROWS, r = i % OZ_ROWS;
+    const int row0 = (int)(local / nh) * TR;
+    for (int i = tid; i < nseg * TR; i += OZ_THREADS) {
+      const int s = i / TR, r = i % TR;
       s_es[s][r] = (row0 + r < R) ? op.Aexp[s][row0 + r] : 0;
     }
-    for (int i = tid; i < nseg * OZ_COLS; i += OZ_THREADS) {
-      const int s = i / OZ_COLS, c = i % OZ_COLS, j = h * OZ_COLS + c;
+    for (int i = tid; i < nseg * TC; i += OZ_THREADS) {
+      const int s = i / TC, c = i % TC, j = h * TC + c;
       s_fs[s][c] = (j < N) ? op.Bexp[s][j] : 0;
     }
     __syncthreads();
-    if (tid < OZ_ROWS) {
+    if (tid < TR) {
       int m = 0;
       for (int s = 0; s < nseg; ++s) m = max(m, s_es[s][tid]);
       s_emax[tid] = m;
-    } else if (tid < OZ_ROWS + OZ_COLS) {
+    } else if (tid < TR + TC) {
       int m = 0;
-      for (int s = 0; s < nseg; ++s) m = max(m, s_fs[s][tid - OZ_ROWS]);
-      s_fmax[tid - OZ_ROWS] = m;
+      for (int s = 0; s < nseg; ++s) m = max(m, s_fs[s][tid - TR]);
+      s_fmax[tid - TR] = m;
     }
     if (nseg > 1) {
       // the sums are kept on the grid of max_s (E_s + F_s), not of emax + fmax:
       // segments with the largest row and column exponents need not coincide
       __syncthreads();
-      for (int i = tid; i < OZ_ROWS * OZ_COLS; i += OZ_THREADS) {
-        const int r = i / OZ_COLS, c = i % OZ_COLS;
+      for (int i = tid; i < TR * TC; i += OZ_THREADS) {
+        const int r = i / TC, c = i % TC;
         int tmax = 0;
         for (int s = 0; s < nseg; ++s) tmax = max(tmax, s_es[s][r] + s_fs[s][c]);
         s_del[r][c] = (unsigned char)min(s_emax[r] + s_fmax[c] - tmax, 255);
@@ -317,22 +337,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     long long S[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) S[i] = 0;
-    double ra[16];
+    double ra[EPT];
     auto load_stage = [&](int st2) {
-      const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * 16;
+      const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * EPT;
       const double* __restrict__ A = op.A[s];
       const int gr = row0 + srow;
-      if (gr < R && (K & 1) == 0 && k0 + 16 <= K) {  // 16-byte aligned pairs
+      if (gr < R && (K & 1) == 0 && k0 + EPT <= K) {  // 16-byte aligned pairs
         const double2* src = (const double2*)(A + (i64)gr * K + k0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < EPT / 2; ++i) {
           const double2 t2 = __ldg(src + i);
           ra[2 * i] = t2.x;
           ra[2 * i + 1] = t2.y;
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < EPT; ++i) {
           const int k = k0 + i;
           ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
         }
@@ -343,18 +363,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
       const int s = st / nkb, kb = st % nkb, b = st & 1;
       if (b ? mpend1 : mpend0) wait_mma(b);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char* sA = base + b * OZ_SET;
-      unsigned char* sB = sA + OZ_DIGITS * OZ_A_PLANE;
+      unsigned char* sA = base + b * OZ_SET;            // tensor digit planes
+      unsigned char* sB = sA + OZ_DIGITS * TPLANE;       // factor digit planes
       if (tid == 0) {
         uint64_t* fb = b ? &full_bar[1] : &full_bar[0];
-        oz_expect_tx(fb, OZ_IMG_STAGE);
-        oz_bulk_copy(sB, op.Bimg[s] + ((i64)kb * nh + h) * OZ_IMG_STAGE, OZ_IMG_STAGE, fb);
+        oz_expect_tx(fb, FIMG);
+        oz_bulk_copy(sB, op.Bimg[s] + ((i64)kb * nh + h) * FIMG, FIMG, fb);
       }
       if (b) fpend1 = 1; else fpend0 = 1;
-      // slice this thread's 16 values of its row into the 8 digit planes
+      // slice this thread's EPT values of its row into the 8 digit planes
       const int emax = s_es[s][srow];
 #pragma unroll
-      for (int q2 = 0; q2 < 2; ++q2) {
+      for (int q2 = 0; q2 < EPT / 8; ++q2) {
         uint32_t w[OZ_DIGITS][4];
 #pragma unroll
         for (int p2 = 0; p2 < 4; ++p2) {
@@ -366,10 +386,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
           OZ_PAIR(0); OZ_PAIR(1); OZ_PAIR(2); OZ_PAIR(3); OZ_PAIR(4); OZ_PAIR(5); OZ_PAIR(6); OZ_PAIR(7);
 #undef OZ_PAIR
         }
-        const uint32_t off = sw64(srow, kh * 16 + q2 * 8);
+        const uint32_t off = sw64(srow, kh * EPT + q2 * 8);
 #pragma unroll
         for (int j = 0; j < OZ_DIGITS; ++j)
-          *(uint4*)(sA + j * OZ_A_PLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+          *(uint4*)(sA + j * TPLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -382,8 +402,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int ksteps = (min(OZ_KB, K - kb * OZ_KB) + 15) / 16;
-          // descriptors differ only in the start address field (16-byte units)
-          const uint64_t da0 = desc_sw64(smem_u32(sA)), db0 = desc_sw64(smem_u32(sB));
+          // descriptors differ only in the start address field (16-byte units);
+          // the M side (128 rows, 8 KB planes) is the factor when TALL
+          const uint64_t da0 = desc_sw64(smem_u32(TALL ? sB : sA)), db0 = desc_sw64(smem_u32(TALL ? sA : sB));
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint64_t dak = da0 + (uint64_t)(ks * 2), dbk = db0 + (uint64_t)(ks * 2);  // 32 bytes per K step
 #pragma unroll
@@ -404,8 +425,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         if (mpend0) wait_mma(0);
         if (mpend1) wait_mma(1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = q * 32 + lane;
-        const int shA = s_emax[row] - s_es[s][row];
+        const int L = q * 32 + lane;  // TMEM lane: tensor row (else) / output (TALL)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           uint32_t v[OZ_DIGITS][8];
@@ -427,8 +447,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
                                 ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
                                 ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
                                 ((long long)oz_int(v[6][i]) << (OZ_G - 42)) + ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
-            const int col = ch * 32 + cc * 8 + i;
-            const int sh = guard + shA + s_fmax[col] - s_fs[s][col] - (nseg > 1 ? (int)s_del[row][col] : 0);
+            const int cidx = ch * 32 + cc * 8 + i;  // TMEM column
+            const int row = TALL ? cidx : L, col = TALL ? L : cidx;
+            const int sh = guard + s_emax[row] - s_es[s][row] + s_fmax[col] - s_fs[s][col] -
+                           (nseg > 1 ? (int)s_del[row][col] : 0);
             if (sh < 62) S[cc * 8 + i] += V >> sh;
           }
         }
@@ -438,13 +460,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
       }
     }
     if (!abort_flag) {
-      const int row = q * 32 + lane, gr = row0 + row;
-      if (gr < R) {
-        const int EA = s_emax[row];
+      const int L = q * 32 + lane;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = ch * 32 + i, j = h * OZ_COLS + col;
-          if (j < N) {
+      for (int i = 0; i < 32; ++i) {
+        const int row = TALL ? ch * 32 + i : L, col = TALL ? L : ch * 32 + i;
+        const int gr = row0 + row, j = h * TC + col;
+        if (gr < R && j < N) {
+          const int EA = s_emax[row];
+          {
             const int EB = s_fmax[col];
             const int del = nseg > 1 ? (int)s_del[row][col] : 0;
             double val = (EA == 2047 || EB == 2047) ? __longlong_as_double(0x7FF8000000000000LL)
@@ -475,7 +498,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
   }
 }
 
-void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, cudaStream_t st) {
+void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int n, int* status, cudaStream_t st) {
   if (nops <= 0 || total_tiles <= 0) return;
   static int sms = 0;
   static bool attr = false;
@@ -483,11 +506,15 @@ void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, 
     int dev = 0;
     GPFVM_CUDA(cudaGetDevice(&dev));
     GPFVM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GPFVM_CUDA(cudaFuncSetAttribute(oz_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_DYN_SMEM));
+    GPFVM_CUDA(cudaFuncSetAttribute(oz_mode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_DYN_SMEM));
+    GPFVM_CUDA(cudaFuncSetAttribute(oz_mode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_DYN_SMEM));
     attr = true;
   }
   const int grid = (int)std::min<i64>(total_tiles, std::max(sms, 1));
-  launch_pdl(oz_mode_kernel, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+  if (oz_tall(n))
+    launch_pdl(oz_mode_kernel<true>, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+  else
+    launch_pdl(oz_mode_kernel<false>, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
 }
 
 // ---------------------------------------------------------------------------

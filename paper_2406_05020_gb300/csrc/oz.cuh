@@ -48,9 +48,12 @@ i64 oz_image_bytes(int N, int K);
 void oz_split_factor(const double* F, i64 rs, i64 cs, int N, int K, double alpha, unsigned char* img, int* fexp,
                      cudaStream_t st);
 void oz_row_exponents(const OzExpJobs& jobs, cudaStream_t st);
-// tiles of one op (row tiles x column halves)
+// the tall tiling (all outputs of a tile on the MMA's M side) for 64 < N <= 128
+bool oz_tall(int N);
+// tiles of one op (row tiles x column halves, or row tiles of 64 when tall)
 i64 oz_tiles(int R, int N);
-void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int* status, cudaStream_t st);
+// one level of ops, all with N outputs (the same tiling for the whole launch)
+void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int n, int* status, cudaStream_t st);
 
 // C = beta C + gamma D + alpha A B in FP64 by digit products for long K:
 // A(i, kk) = A[i a_rs + kk] (m x k), B(kk, j) = B[kk b_rs + j b_cs] with
