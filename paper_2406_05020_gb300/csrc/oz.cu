@@ -23,16 +23,17 @@
 // matrix-product accuracy).  The FP64 FMA rate of this part is about 1/70 of
 // its dense bf16 tensor rate.
 //
-// Per CTA (256 threads; one CTA per SM: its 512 TMEM columns hold 8 diagonals
-// x 64 output columns): one tile = 128 tensor rows x 64 output columns of one
+// Per CTA (512 threads; one CTA per SM: its 512 TMEM columns hold 8 diagonals
+// x 64 columns): one tile = 128 tensor rows x 64 output columns of one
 // op.  For every (segment, 32-wide K block) stage, thread 0 starts a bulk copy
 // (cp.async.bulk, mbarrier transaction count) of the stage's pre-sliced factor
 // digit planes into shared memory, all threads slice the FP64 tensor rows into
 // 8 bf16 digit planes (64-byte-swizzled K-major rows), and thread 0 issues
 // 2 x 36 MMAs (M = 128, N = 64, K = 16) into the 8 diagonal accumulators.  Two
 // operand sets: the next stage is sliced while the MMAs of the current one
-// run.  After the last K block of a segment the accumulators are drained into
-// per-thread 64-bit sums.  All waits are bounded; a timeout sets *status and
+// run; the warps hand a stage to the issuing thread through an mbarrier (no
+// CTA barrier per stage).  After the last K block of a segment the
+// accumulators are drained into per-thread 64-bit sums.  All waits are bounded; a timeout sets *status and
 // the kernel returns after its outstanding copies and MMAs and freeing TMEM.
 #include <algorithm>
 
@@ -41,7 +42,8 @@
 
 namespace gpfvm {
 
-constexpr int OZ_THREADS = 256;
+constexpr int OZ_THREADS = 256;   // the long-K GEMM kernel
+constexpr int OZ_MTHREADS = 512;  // the mode-product kernel: 16 warps, 4 per TMEM lane quadrant
 constexpr int OZ_G = 43;  // binary point of one segment's 64-bit sum (see the drain)
 constexpr int OZ_NONFINITE = 0x7fffffff;  // block exponent of a sum that met a NaN or infinity
 constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
@@ -232,15 +234,16 @@ void oz_split_factor(const double* F, i64 rs, i64 cs, int N, int K, double alpha
 // TALL: see oz_tall.  TR tensor rows and TC outputs per tile; the M side of
 // the MMA (128 rows: TMEM lanes) is the factor when TALL, else the tensor.
 template <bool TALL>
-__global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __restrict__ ops, int nops, i64 total,
+__global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __restrict__ ops, int nops, i64 total,
                                                                int* status) {
   constexpr int TR = TALL ? OZ_COLS : OZ_ROWS, TC = TALL ? 2 * OZ_COLS : OZ_COLS;
   constexpr int TPLANE = TR * 64, FPLANE = TC * 64;      // digit plane bytes: tensor, factor
   constexpr int FIMG = OZ_DIGITS * FPLANE;               // one factor image block
-  constexpr int EPT = TALL ? 8 : 16, PARTS = OZ_KB / EPT;  // tensor elements per thread and stage
+  constexpr int EPT = TALL ? 4 : 8, PARTS = OZ_KB / EPT;  // tensor elements per thread and stage
+  constexpr int CW = EPT < 8 ? EPT : 8, NCH = EPT / CW;   // elements per smem store, stores per plane
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t mma_bar[2], full_bar[2];
+  __shared__ uint64_t mma_bar[2], full_bar[2], ready_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int s_es[OZ_MAXSEG][TR], s_fs[OZ_MAXSEG][TC];
@@ -259,6 +262,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[b])) : "memory");
+      // every warp arrives once its part of a stage's digit planes is written
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&ready_bar[b])), "r"(OZ_MTHREADS / 32)
+                   : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
   pdl_wait();  // TMEM and the barriers are set up while the previous kernel drains
 
   // per-set pipeline state (the same in every thread)
-  uint32_t mph0 = 0, mph1 = 0, fph0 = 0, fph1 = 0;
+  uint32_t mph0 = 0, mph1 = 0, fph0 = 0, fph1 = 0, rph0 = 0, rph1 = 0;
   int mpend0 = 0, mpend1 = 0, fpend0 = 0, fpend1 = 0;
   auto wait_mma = [&](int b) {
     const bool ok = b ? mbar_wait(&mma_bar[1], mph1) : mbar_wait(&mma_bar[0], mph0);
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     }
   };
   const uint32_t idesc = idesc_bf16(OZ_COLS);
-  const int q = warp & 3, ch = warp >> 2;     // drain / epilogue: TMEM lane quadrant, 32-column half
+  const int q = warp & 3, ch = warp >> 2;     // drain / epilogue: TMEM lane quadrant, 16-column quarter
   const int srow = tid / PARTS, kh = tid % PARTS;  // staging: tensor row, EPT-wide part of the K block
 
   for (i64 t = blockIdx.x; t < total; t += gridDim.x) {
@@ -298,11 +304,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     const i64 local = t - op.tile_begin;
     const int h = (int)(local % nh);
     const int row0 = (int)(local / nh) * TR;
-    for (int i = tid; i < nseg * TR; i += OZ_THREADS) {
+    for (int i = tid; i < nseg * TR; i += OZ_MTHREADS) {
       const int s = i / TR, r = i % TR;
       s_es[s][r] = (row0 + r < R) ? op.Aexp[s][row0 + r] : 0;
     }
-    for (int i = tid; i < nseg * TC; i += OZ_THREADS) {
+    for (int i = tid; i < nseg * TC; i += OZ_MTHREADS) {
       const int s = i / TC, c = i % TC, j = h * TC + c;
       s_fs[s][c] = (j < N) ? op.Bexp[s][j] : 0;
     }
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
       // the sums are kept on the grid of max_s (E_s + F_s), not of emax + fmax:
       // segments with the largest row and column exponents need not coincide
       __syncthreads();
-      for (int i = tid; i < TR * TC; i += OZ_THREADS) {
+      for (int i = tid; i < TR * TC; i += OZ_MTHREADS) {
         const int r = i / TC, c = i % TC;
         int tmax = 0;
         for (int s = 0; s < nseg; ++s) tmax = max(tmax, s_es[s][r] + s_fs[s][c]);
@@ -334,9 +340,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     // more segments each is shifted down by guard = ceil(log2 nseg) bits, so
     // |S| < 2^62.03 and value = S * 2^(E + F - 2056 - OZ_G + guard)
     const int guard = nseg > 1 ? 32 - __clz(nseg - 1) : 0;
-    long long S[32];
+    long long S[16];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) S[i] = 0;
+    for (int i = 0; i < 16; ++i) S[i] = 0;
     double ra[EPT];
     auto load_stage = [&](int st2) {
       const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * EPT;
@@ -374,28 +380,37 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
       // slice this thread's EPT values of its row into the 8 digit planes
       const int emax = s_es[s][srow];
 #pragma unroll
-      for (int q2 = 0; q2 < EPT / 8; ++q2) {
-        uint32_t w[OZ_DIGITS][4];
+      for (int q2 = 0; q2 < NCH; ++q2) {
+        uint32_t w[OZ_DIGITS][CW / 2];
 #pragma unroll
-        for (int p2 = 0; p2 < 4; ++p2) {
+        for (int p2 = 0; p2 < CW / 2; ++p2) {
           uint32_t h0, l0, h1, l1;
           float s0, o0, s1, o1;
-          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2]), emax, h0, l0, s0, o0);
-          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * 8 + 2 * p2 + 1]), emax, h1, l1, s1, o1);
+          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * CW + 2 * p2]), emax, h0, l0, s0, o0);
+          oz_prep((unsigned long long)__double_as_longlong(ra[q2 * CW + 2 * p2 + 1]), emax, h1, l1, s1, o1);
 #define OZ_PAIR(J) w[J][p2] = __byte_perm(oz_digit_f32<J>(h0, l0, s0, o0), oz_digit_f32<J>(h1, l1, s1, o1), 0x7632)
           OZ_PAIR(0); OZ_PAIR(1); OZ_PAIR(2); OZ_PAIR(3); OZ_PAIR(4); OZ_PAIR(5); OZ_PAIR(6); OZ_PAIR(7);
 #undef OZ_PAIR
         }
-        const uint32_t off = sw64(srow, kh * EPT + q2 * 8);
+        const uint32_t off = sw64(srow, kh * EPT + q2 * CW);
 #pragma unroll
-        for (int j = 0; j < OZ_DIGITS; ++j)
-          *(uint4*)(sA + j * TPLANE + off) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+        for (int j = 0; j < OZ_DIGITS; ++j) {
+          if constexpr (CW == 8)
+            *(uint4*)(sA + j * TPLANE + off) = make_uint4(w[j][0], w[j][CW / 2 - 3], w[j][CW / 2 - 2], w[j][CW / 2 - 1]);
+          else
+            *(uint2*)(sA + j * TPLANE + off) = make_uint2(w[j][0], w[j][CW / 2 - 1]);
+        }
       }
+      // hand the stage to the MMA issuer without a CTA barrier: the other warps
+      // go on to the next stage's loads while thread 0 issues this one
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (abort_flag) break;
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b ? &ready_bar[1] : &ready_bar[0]))
+                     : "memory");
       if (tid == 0) {
-        const bool ok = b ? mbar_wait(&full_bar[1], fph1) : mbar_wait(&full_bar[0], fph0);
+        const bool ok = (b ? mbar_wait(&ready_bar[1], rph1) : mbar_wait(&ready_bar[0], rph0)) &&
+                        (b ? mbar_wait(&full_bar[1], fph1) : mbar_wait(&full_bar[0], fph0));
         if (!ok) {
           atomicOr(status, (int)DEV_TIMEOUT);
           abort_flag = 1;
@@ -418,7 +433,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         }
         mma_commit(b ? &mma_bar[1] : &mma_bar[0]);
       }
-      if (b) { fph1 ^= 1u; fpend1 = 0; mpend1 = 1; } else { fph0 ^= 1u; fpend0 = 0; mpend0 = 1; }
+      if (b) { fph1 ^= 1u; rph1 ^= 1u; fpend1 = 0; mpend1 = 1; } else { fph0 ^= 1u; rph0 ^= 1u; fpend0 = 0; mpend0 = 1; }
       if (st + 1 < nstage) load_stage(st + 1);  // overlaps the MMAs
       if (kb == nkb - 1) {
         // segment s complete: add its diagonals, aligned to the tile's exponents, to S
@@ -427,9 +442,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int L = q * 32 + lane;  // TMEM lane: tensor row (else) / output (TALL)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
+        for (int cc = 0; cc < 2; ++cc) {
           uint32_t v[OZ_DIGITS][8];
-          const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32 + cc * 8);
+          const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 16 + cc * 8);
 #pragma unroll
           for (int d = 0; d < OZ_DIGITS; ++d)
             asm volatile(
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
                                 ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
                                 ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
                                 ((long long)oz_int(v[6][i]) << (OZ_G - 42)) + ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
-            const int cidx = ch * 32 + cc * 8 + i;  // TMEM column
+            const int cidx = ch * 16 + cc * 8 + i;  // TMEM column
             const int row = TALL ? cidx : L, col = TALL ? L : cidx;
             const int sh = guard + s_emax[row] - s_es[s][row] + s_fmax[col] - s_fs[s][col] -
                            (nseg > 1 ? (int)s_del[row][col] : 0);
@@ -462,8 +477,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_mode_kernel(const OzOp* __re
     if (!abort_flag) {
       const int L = q * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int row = TALL ? ch * 32 + i : L, col = TALL ? L : ch * 32 + i;
+      for (int i = 0; i < 16; ++i) {
+        const int row = TALL ? ch * 16 + i : L, col = TALL ? L : ch * 16 + i;
         const int gr = row0 + row, j = h * TC + col;
         if (gr < R && j < N) {
           const int EA = s_emax[row];
@@ -512,9 +527,9 @@ void launch_oz_modes(const OzOp* d_ops, int nops, i64 total_tiles, int n, int* s
   }
   const int grid = (int)std::min<i64>(total_tiles, std::max(sms, 1));
   if (oz_tall(n))
-    launch_pdl(oz_mode_kernel<true>, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+    launch_pdl(oz_mode_kernel<true>, grid, OZ_MTHREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
   else
-    launch_pdl(oz_mode_kernel<false>, grid, OZ_THREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
+    launch_pdl(oz_mode_kernel<false>, grid, OZ_MTHREADS, OZ_DYN_SMEM, st, d_ops, nops, total_tiles, status);
 }
 
 // ---------------------------------------------------------------------------
