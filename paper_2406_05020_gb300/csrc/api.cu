@@ -35,8 +35,20 @@ void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relax
 
 namespace {
 
+// An IC/BC point set: a tensor grid of points observing the derivative of
+// the given order on each axis.  Two given sets that differ only in the order
+// on axis 0, where both sit at one common coordinate (u and u_t at t = 0 of a
+// second-order-in-time problem), are held as one "stacked" set with two
+// axis-0 points at that coordinate: point 0 with order[0] and noise, point 1
+// with order2 and noise2.  Their joint covariance is then one Kronecker
+// product (the axis-0 factor becomes 2 x 2), so the structured IC/BC stage
+// inverts both through one eigenbasis instead of placing the second in the
+// Schur complement.  Layouts agree: axis 0 is the slowest, so the stacked
+// set's values are the first set's followed by the second's.
 struct SetC {
   int order[3] = {0, 0, 0};
+  int order2 = -1;      // axis-0 order of point 1 of a stacked set (else -1)
+  double noise2 = 0.0;  // its noise variance
   int n[3] = {1, 1, 1};
   std::vector<double> coords[3];
   std::vector<double> values;
@@ -188,6 +200,10 @@ struct gpfvm_problem {
   std::vector<double> rhs;
   int nsets = 0;
   SetC sets[GPFVM_MAX_SETS];
+  // the caller's sets: set u is internal set uset[u], and with uslice[u] >= 0
+  // the axis-0 point uslice[u] of that stacked set
+  int nusets = 0;
+  int uset[GPFVM_MAX_SETS] = {}, uslice[GPFVM_MAX_SETS] = {};
   int npred[3] = {1, 1, 1};
   std::vector<double> pred[3];
   bool colloc = false;  // PDE observed at the cell centres (collocation) instead of cell integrals
@@ -355,6 +371,47 @@ i64 fam_n(const gpfvm_problem* p, int ax, int kind, int arg) {
   return p->npred[ax];
 }
 
+// Stack consecutive given sets s, s + 1 that differ only in the derivative
+// order on axis 0 and sit at one common axis-0 coordinate (see SetC), unless
+// GPFVM_STACK_SETS=0.  Offsets and the order of the M values are unchanged.
+void stack_sets(gpfvm_problem* p) {
+  const char* env = std::getenv("GPFVM_STACK_SETS");
+  if ((env && std::atoi(env) == 0) || p->d < 2) return;
+  auto stackable = [&](const SetC& a, const SetC& b) {
+    if (a.n[0] != 1 || b.n[0] != 1 || a.coords[0][0] != b.coords[0][0] || a.order[0] == b.order[0]) return false;
+    for (int i = 1; i < p->d; ++i)
+      if (a.n[i] != b.n[i] || a.order[i] != b.order[i] || a.coords[i] != b.coords[i]) return false;
+    return true;
+  };
+  int ns = 0;
+  for (int u = 0; u < p->nusets;) {
+    SetC& out = p->sets[ns];
+    if (u + 1 < p->nusets && stackable(p->sets[u], p->sets[u + 1])) {
+      SetC a = p->sets[u];
+      const SetC& b = p->sets[u + 1];
+      a.n[0] = 2;
+      a.coords[0] = {a.coords[0][0], a.coords[0][0]};
+      a.order2 = b.order[0];
+      a.noise2 = b.noise;
+      a.values.insert(a.values.end(), b.values.begin(), b.values.end());
+      a.size *= 2;
+      p->uset[u] = p->uset[u + 1] = ns;
+      p->uslice[u] = 0;
+      p->uslice[u + 1] = 1;
+      out = std::move(a);
+      u += 2;
+    } else {
+      if (&out != &p->sets[u]) out = std::move(p->sets[u]);
+      p->uset[u] = ns;
+      p->uslice[u] = -1;
+      u += 1;
+    }
+    ++ns;
+  }
+  for (int s = ns; s < p->nsets; ++s) p->sets[s] = SetC();
+  p->nsets = ns;
+}
+
 void need_factor(gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab) {
   FKey key(ax, ka, aa, kb, ab);
   if (p->fac_off.count(key)) return;
@@ -365,6 +422,14 @@ void need_factor(gpfvm_problem* p, int ax, int ka, int aa, int kb, int ab) {
   J.kind_b = (kb == 0 && !p->colloc) ? 0 : 1;
   J.ord_a = ka == 0 ? aa : (ka == 1 ? p->sets[aa].order[ax] : 0);
   J.ord_b = kb == 0 ? ab : (kb == 1 ? p->sets[ab].order[ax] : 0);
+  if (ka == 1 && ax == 0 && p->sets[aa].order2 >= 0) {
+    J.has2_a = 1;
+    J.ord2_a = p->sets[aa].order2;
+  }
+  if (kb == 1 && ax == 0 && p->sets[ab].order2 >= 0) {
+    J.has2_b = 1;
+    J.ord2_b = p->sets[ab].order2;
+  }
   J.n_a = (int)fam_n(p, ax, ka, aa);
   J.n_b = (int)fam_n(p, ax, kb, ab);
   J.ell = p->ell[ax];
@@ -1385,7 +1450,8 @@ void build_sicbc(gpfvm_problem* p, Builder& B) {
   pl.func([=](cudaStream_t st) {
     launch_jacobi(pp->d_jac, pp->d, maxn, st);
     lambda_tensor(pp->d_lam[0], d >= 2 ? pp->d_lam[1] : nullptr, d >= 3 ? pp->d_lam[2] : nullptr, pp->nK[0],
-                  d >= 2 ? pp->nK[1] : 1, d >= 3 ? pp->nK[2] : 1, pp->s2, pp->sets[0].noise, pp->d_lt, st);
+                  d >= 2 ? pp->nK[1] : 1, d >= 3 ? pp->nK[2] : 1, pp->s2, pp->sets[0].noise,
+                  pp->sets[0].order2 >= 0 ? pp->d_QK[0] : nullptr, pp->sets[0].noise2, pp->d_lt, st);
     recip(pp->d_lt, pp->d_ltinv, MK, st);
   });
   // fold the eigenbasis into set 0's factors: cells (F_i Q_i), prediction
@@ -1781,6 +1847,7 @@ void build_plans(gpfvm_problem* p, Builder& B) {
       for (int s = 0; s < p->nsets; ++s) {
         G.off[s] = (int)p->sets[s].off;
         G.noise[s] = p->sets[s].noise;
+        G.noise2[s] = p->sets[s].order2 >= 0 ? p->sets[s].noise2 : p->sets[s].noise;
         for (int i = 0; i < p->d; ++i) G.dims[s][i] = p->sets[s].n[i];
         for (int s2 = 0; s2 < p->nsets; ++s2)
           for (int i = 0; i < p->d; ++i)
@@ -2327,7 +2394,8 @@ void alloc_all(gpfvm_problem* p) {
   p->sicbc = false;
   if (M > 0) {
     const char* env = getenv("GPFVM_ICBC");
-    bool ok = !(env && std::strcmp(env, "dense") == 0) && p->sets[0].noise > 0;
+    bool ok = !(env && std::strcmp(env, "dense") == 0) && p->sets[0].noise > 0 &&
+              (p->sets[0].order2 < 0 || p->sets[0].noise2 > 0);
     for (int s = 1; s < p->nsets; ++s) ok = ok && p->sets[s].size <= p->sets[0].size;
     for (int i = 0; i < p->d; ++i) ok = ok && p->sets[0].n[i] <= 96;
     p->sicbc = ok;
@@ -3352,8 +3420,12 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
     S.noise = D->sets[s].noise_var;
     S.off = off;
     off += S.size;
+    p->uset[s] = s;
+    p->uslice[s] = -1;
   }
+  p->nusets = p->nsets;
   p->M = off;
+  stack_sets(p.get());
   p->cap = max_iter > 0 ? max_iter : 2000;
   // register the 1D factors the problem needs
   for (int a = 0; a < p->nterms; ++a)
@@ -3806,16 +3878,34 @@ int64_t gpfvm_export(gpfvm_problem* p, int what, double* host_out, int64_t capac
 int64_t gpfvm_factor(gpfvm_problem* p, int axis, int kind_a, int arg_a, int kind_b, int arg_b, double* host_out,
                      int64_t capacity, void* stream) {
   if (!p || !host_out || axis < 0 || axis >= p->d) return GPFVM_ERR_INVALID_ARG;
-  auto it = p->fac_off.find(FKey(axis, kind_a, arg_a, kind_b, arg_b));
+  // the caller's set numbers -> internal sets (and the axis-0 point of a stacked set)
+  int ia = arg_a, ib = arg_b, sa = -1, sb = -1;
+  if (kind_a == 1) {
+    if (arg_a < 0 || arg_a >= p->nusets) return GPFVM_ERR_NOT_FOUND;
+    ia = p->uset[arg_a];
+    if (axis == 0) sa = p->uslice[arg_a];
+  }
+  if (kind_b == 1) {
+    if (arg_b < 0 || arg_b >= p->nusets) return GPFVM_ERR_NOT_FOUND;
+    ib = p->uset[arg_b];
+    if (axis == 0) sb = p->uslice[arg_b];
+  }
+  auto it = p->fac_off.find(FKey(axis, kind_a, ia, kind_b, ib));
   if (it == p->fac_off.end()) return GPFVM_ERR_NOT_FOUND;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
-  const i64 n = fam_n(p, axis, kind_a, arg_a) * fam_n(p, axis, kind_b, arg_b);
-  if (n > capacity) return GPFVM_ERR_INVALID_ARG;
+  const i64 na = fam_n(p, axis, kind_a, ia), nb = fam_n(p, axis, kind_b, ib);
+  const i64 ra = sa >= 0 ? 1 : na, rb = sb >= 0 ? 1 : nb;
+  if (ra * rb > capacity) return GPFVM_ERR_INVALID_ARG;
   p->p_setup.run(st);
-  GPFVM_CUDA(cudaMemcpyAsync(host_out, p->d_fac + it->second, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  std::vector<double> full(sa >= 0 || sb >= 0 ? na * nb : 0);
+  double* dst = full.empty() ? host_out : full.data();
+  GPFVM_CUDA(cudaMemcpyAsync(dst, p->d_fac + it->second, sizeof(double) * na * nb, cudaMemcpyDeviceToHost, st));
   GPFVM_CUDA(cudaStreamSynchronize(st));
-  return n;
+  if (!full.empty())
+    for (i64 i = 0; i < ra; ++i)
+      for (i64 j = 0; j < rb; ++j) host_out[i * rb + j] = full[(sa >= 0 ? sa : i) * nb + (sb >= 0 ? sb : j)];
+  return ra * rb;
   GPFVM_GUARD_END
 }
 

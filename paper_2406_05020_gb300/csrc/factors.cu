@@ -56,12 +56,12 @@ __device__ double factor_entry(const FactorJob& J, int i, int j) {
   if (J.kind_a == 0) {
     xa[0] = J.ca[i + 1]; wa[0] = 1.0; xa[1] = J.ca[i]; wa[1] = -1.0; na = 2; ma = J.ord_a - 1;
   } else {
-    xa[0] = J.ca[i]; wa[0] = 1.0; na = 1; ma = J.ord_a;
+    xa[0] = J.ca[i]; wa[0] = 1.0; na = 1; ma = (J.has2_a && i == 1) ? J.ord2_a : J.ord_a;
   }
   if (J.kind_b == 0) {
     xb[0] = J.cb[j + 1]; wb[0] = 1.0; xb[1] = J.cb[j]; wb[1] = -1.0; nb = 2; mb = J.ord_b - 1;
   } else {
-    xb[0] = J.cb[j]; wb[0] = 1.0; nb = 1; mb = J.ord_b;
+    xb[0] = J.cb[j]; wb[0] = 1.0; nb = 1; mb = (J.has2_b && j == 1) ? J.ord2_b : J.ord_b;
   }
   const int order = ma + mb;
   const double sign_n = (mb & 1) ? -1.0 : 1.0;  // (-1)^n, n may be -1
@@ -155,14 +155,16 @@ __global__ void gbb_kernel(GbbParams P, double* __restrict__ G) {
     while (s2 + 1 < P.n_sets && o2 >= P.off[s2 + 1]) ++s2;
     int l1 = o1 - P.off[s1], l2 = o2 - P.off[s2];
     double v = P.outputscale;
+    int i0 = 0;  // axis-0 index of point o1
     for (int ax = P.ndim - 1; ax >= 0; --ax) {
       const int n1 = P.dims[s1][ax], n2 = P.dims[s2][ax];
       const int i1 = l1 % n1, i2 = l2 % n2;
       l1 /= n1;
       l2 /= n2;
       v *= P.fac[s1][s2][ax][(i64)i1 * n2 + i2];
+      i0 = i1;
     }
-    if (o1 == o2) v += P.noise[s1];
+    if (o1 == o2) v += i0 > 0 ? P.noise2[s1] : P.noise[s1];
     G[e] = v;
   }
 }

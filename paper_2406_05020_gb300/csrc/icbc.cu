@@ -229,20 +229,29 @@ void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t 
 }
 
 // lt[m] = sigma^2 prod_i lam_i[m_i] + nu  over the row-major multi-index m of (n0, n1, n2)
+// With two stacked sets (axis 0 = two points at one coordinate, carrying the
+// two sets' noise levels nu and nu_b) the noise is diag(nu, nu_b) on axis 0;
+// in the eigenbasis it stays diagonal when the axis-0 factor is (the
+// cross-covariance of orders 0 and 1 at one point is an odd derivative of the
+// even kernel at 0, so Q0 is the identity), and its diagonal is
+// sum_i Q0[i][j]^2 nu_i.
 __global__ void k_lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2,
-                                double s2, double nu, double* __restrict__ lt) {
+                                double s2, double nu, const double* __restrict__ q0, double nu_b,
+                                double* __restrict__ lt) {
   const i64 tot = (i64)n0 * n1 * n2;
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (i64)gridDim.x * blockDim.x) {
     const int i2 = (int)(e % n2), i1 = (int)((e / n2) % n1), i0 = (int)(e / ((i64)n1 * n2));
-    lt[e] = s2 * (l0 ? l0[i0] : 1.0) * (l1 ? l1[i1] : 1.0) * (l2 ? l2[i2] : 1.0) + nu;
+    const double nz = q0 ? nu * q0[i0] * q0[i0] + nu_b * q0[n0 + i0] * q0[n0 + i0] : nu;
+    lt[e] = s2 * (l0 ? l0[i0] : 1.0) * (l1 ? l1[i1] : 1.0) * (l2 ? l2[i2] : 1.0) + nz;
   }
 }
 void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,
-                   double* lt, cudaStream_t st) {
+                   const double* q0, double nu_b, double* lt, cudaStream_t st) {
+  if (q0 && n0 != 2) throw CudaError{cudaErrorInvalidValue, "lambda_tensor: a stacked axis has two points"};
   const i64 tot = (i64)n0 * n1 * n2;
   int g = ceil_div(tot, 256);
   if (g > 2048) g = 2048;
-  k_lambda_tensor<<<g, 256, 0, st>>>(l0, l1, l2, n0, n1, n2, s2, nu, lt);
+  k_lambda_tensor<<<g, 256, 0, st>>>(l0, l1, l2, n0, n1, n2, s2, nu, q0, nu_b, lt);
   GPFVM_LAUNCH_CHECK();
 }
 

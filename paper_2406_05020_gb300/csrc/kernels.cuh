@@ -7,9 +7,12 @@ namespace gpfvm {
 // ---- 1D factor assembly (factors.cu) -------------------------------------
 // kind 0: cell family over edges ca[0..n] with derivative order ord (0..2);
 // kind 1: point family at ca[0..n) with derivative order ord (0..1).
+// A point family made of two stacked sets (two points at one coordinate of
+// axis 0, see SetC in api.cu) gives its point 1 the order ord2 when has2 is set.
 struct FactorJob {
   int kind_a, ord_a, n_a;
   int kind_b, ord_b, n_b;
+  int has2_a, ord2_a, has2_b, ord2_b;
   const double* ca;
   const double* cb;
   double ell;
@@ -22,6 +25,7 @@ struct GbbParams {
   int off[GPFVM_MAX_SETS + 1];
   int dims[GPFVM_MAX_SETS][GPFVM_MAX_DIM];
   double noise[GPFVM_MAX_SETS];
+  double noise2[GPFVM_MAX_SETS];  // noise of the points with axis-0 index >= 1 (stacked sets)
   double outputscale;
   const double* fac[GPFVM_MAX_SETS][GPFVM_MAX_SETS][GPFVM_MAX_DIM];
 };
@@ -119,8 +123,11 @@ struct JacobiJob {
   int* sweeps;      // out: sweeps of the FP32 and of the FP64 phase (may be null)
 };
 void launch_jacobi(const JacobiJob* d_jobs, int n_jobs, int max_n, cudaStream_t st);
+// lt[i0, i1, i2] = s2 l0[i0] l1[i1] l2[i2] + noise, the noise of eigenvector
+// i0 of axis 0 being nu, or with q0 (the n0 = 2 eigenvectors of a stacked
+// axis 0, row-major) nu q0[0][i0]^2 + nu_b q0[1][i0]^2
 void lambda_tensor(const double* l0, const double* l1, const double* l2, int n0, int n1, int n2, double s2, double nu,
-                   double* lt, cudaStream_t st);
+                   const double* q0, double nu_b, double* lt, cudaStream_t st);
 // One launch of a merged table of face-set ops (face.cuh): kind 0 ContrOp,
 // 1 BilOp, 2 ExpAddOp; `items` CTAs in total, `smem` dynamic shared bytes.
 void launch_face(int kind, const void* table, int nops, i64 items, int f32, int smem, cudaStream_t st);
