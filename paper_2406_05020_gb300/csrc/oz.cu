@@ -119,9 +119,26 @@ __device__ __forceinline__ void oz_prep(unsigned long long bits, int emax, uint3
   off = (bits >> 63) ? 12582976.0f : -12582976.0f;
 }
 
-// integer value of an FP32 accumulator holding an integer of magnitude <= 2^22
-__device__ __forceinline__ int oz_int(uint32_t f) {
-  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+// acc_a 2^7 + acc_b for two FP32 accumulators holding integers of magnitude
+// <= 2^22 (< 2^30: exact in 32 bits).  Adding 1.5 * 2^23 puts an integer into
+// the low mantissa bits (offset 0x4B400000 in the bit pattern); the two
+// offsets are removed as one constant, mod 2^32.
+__device__ __forceinline__ int oz_pair(uint32_t fa, uint32_t fb) {
+  const uint32_t ia = __float_as_uint(__uint_as_float(fa) + 12582912.0f);
+  const uint32_t ib = __float_as_uint(__uint_as_float(fb) + 12582912.0f);
+  return (int)(ia * 128u + ib - 129u * 0x4B400000u);
+}
+
+// sum_d acc_d 2^(OZ_G - 7 d) of the 8 diagonals, the last through a
+// truncating shift: pairs (2e, 2e + 1) are formed in 32 bits and weighted
+// 2^(OZ_G - 14 e - 7); truncating the last pair by 49 - OZ_G bits gives the
+// same value as truncating acc_7 alone (acc_6 2^7 is a multiple of 2^(49 - OZ_G))
+__device__ __forceinline__ long long oz_diagonals(const uint32_t (&v)[OZ_DIGITS][8], int i) {
+  static_assert(OZ_G >= 35 && OZ_G <= 49, "pair weights need 35 <= OZ_G <= 49");
+  const int p0 = oz_pair(v[0][i], v[1][i]), p1 = oz_pair(v[2][i], v[3][i]);
+  const int p2 = oz_pair(v[4][i], v[5][i]), p3 = oz_pair(v[6][i], v[7][i]);
+  return ((long long)p0 << (OZ_G - 7)) + ((long long)p1 << (OZ_G - 21)) + ((long long)p2 << (OZ_G - 35)) +
+         (long long)(p3 >> (49 - OZ_G));
 }
 
 // S * 2^T rounded to nearest FP64 (S != 0 assumed small enough: |S| < 2^62)
@@ -453,18 +470,15 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
                   "=r"(v[d][6]), "=r"(v[d][7])
                 : "r"(tb + (uint32_t)(d * OZ_COLS)));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // the shift of segment s's sum: guard + (emax - E_s) + (fmax - F_s) - del,
+          // the lane's own part (its output, or its row) taken once
+          const int own = guard + (TALL ? s_fmax[L] - s_fs[s][L] : s_emax[L] - s_es[s][L]);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            // sum_d acc_d 2^(OZ_G - 7 d) (the last diagonal through a truncating shift)
-            const long long V = ((long long)oz_int(v[0][i]) << OZ_G) + ((long long)oz_int(v[1][i]) << (OZ_G - 7)) +
-                                ((long long)oz_int(v[2][i]) << (OZ_G - 14)) +
-                                ((long long)oz_int(v[3][i]) << (OZ_G - 21)) +
-                                ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
-                                ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
-                                ((long long)oz_int(v[6][i]) << (OZ_G - 42)) + ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
+            const long long V = oz_diagonals(v, i);
             const int cidx = ch * 16 + cc * 8 + i;  // TMEM column
             const int row = TALL ? cidx : L, col = TALL ? L : cidx;
-            const int sh = guard + s_emax[row] - s_es[s][row] + s_fmax[col] - s_fs[s][col] -
+            const int sh = own + (TALL ? s_emax[row] - s_es[s][row] : s_fmax[col] - s_fs[s][col]) -
                            (nseg > 1 ? (int)s_del[row][col] : 0);
             if (sh < 62) S[cc * 8 + i] += V >> sh;
           }
@@ -749,13 +763,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const long long V = ((long long)oz_int(v[0][i]) << OZ_G) + ((long long)oz_int(v[1][i]) << (OZ_G - 7)) +
-                                  ((long long)oz_int(v[2][i]) << (OZ_G - 14)) +
-                                  ((long long)oz_int(v[3][i]) << (OZ_G - 21)) +
-                                  ((long long)oz_int(v[4][i]) << (OZ_G - 28)) +
-                                  ((long long)oz_int(v[5][i]) << (OZ_G - 35)) +
-                                  ((long long)oz_int(v[6][i]) << (OZ_G - 42)) +
-                                  ((long long)(oz_int(v[7][i]) >> (49 - OZ_G)));
+              const long long V = oz_diagonals(v, i);
               const int k = cc * 8 + i;
               const int eb = s_eb[ch * 32 + k];
               const int ew = ea + eb;

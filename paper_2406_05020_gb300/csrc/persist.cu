@@ -491,6 +491,9 @@ void persist_free(PersistProg* prog) {
 
 bool persist_run(const PersistProg* prog, cudaStream_t st) {
   if (!prog || prog->grid <= 0) return false;
+  // the grid-barrier words start from zero on every launch (a launch that gave
+  // up at a barrier leaves its arrival count behind)
+  GPFVM_CUDA(cudaMemsetAsync(prog->dev.sync, 0, 2 * sizeof(unsigned int), st));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(prog->grid);
   cfg.blockDim = dim3(P_THREADS);
