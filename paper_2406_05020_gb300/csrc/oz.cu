@@ -48,6 +48,8 @@ constexpr int OZ_G = 43;  // binary point of one segment's 64-bit sum (see the d
 constexpr int OZ_NONFINITE = 0x7fffffff;  // block exponent of a sum that met a NaN or infinity
 constexpr int OZ_SET = OZ_DIGITS * OZ_A_PLANE + OZ_IMG_STAGE;  // 96 KB: one operand set
 constexpr int OZ_DYN_SMEM = 2 * OZ_SET + 1024;
+constexpr int OZ_SOPS = 16;  // op tables up to this size are read from shared memory
+static_assert(sizeof(OzOp) % 16 == 0, "op table copied in 16-byte words");
 
 // Outputs of 64 < N <= 128 take the "tall" tiling: the factor (128 rows, all
 // outputs) is the MMA's M side and 64 tensor rows its N side, so every tensor
@@ -265,6 +267,8 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
   __shared__ int abort_flag;
   __shared__ int s_es[OZ_MAXSEG][TR], s_fs[OZ_MAXSEG][TC];
   __shared__ int s_emax[TR], s_fmax[TC];
+  __shared__ __align__(16) OzOp s_ops[OZ_SOPS];  // the op table (nops <= OZ_SOPS)
+  __shared__ int s_skip[OZ_SOPS];                // ... and the ops' skip flags
   // per output: how far the largest segment scale 2^(E_s + F_s) lies below 2^(emax + fmax)
   __shared__ unsigned char s_del[TR][TC];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -291,6 +295,17 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   pdl_wait();  // TMEM and the barriers are set up while the previous kernel drains
+  // small op tables (and their skip flags, fixed for the launch) go to shared
+  // memory once, so a tile's prologue reads no op field from global memory
+  const bool stab = nops <= OZ_SOPS;
+  if (stab) {
+    const int words = nops * (int)(sizeof(OzOp) / 16);
+    for (int i = tid; i < words; i += OZ_MTHREADS) ((uint4*)s_ops)[i] = ((const uint4*)ops)[i];
+    __syncthreads();
+    if (tid < nops) s_skip[tid] = s_ops[tid].skip ? *s_ops[tid].skip : 0;
+    __syncthreads();
+  }
+  const OzOp* tab = stab ? s_ops : ops;
 
   // per-set pipeline state (the same in every thread)
   uint32_t mph0 = 0, mph1 = 0, fph0 = 0, fph1 = 0, rph0 = 0, rph1 = 0;
@@ -312,15 +327,39 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
     int lo = 0, hi = nops - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (ops[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+      if (tab[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
-    const OzOp& op = ops[lo];
-    if (op.skip && *op.skip) continue;
+    const OzOp& op = tab[lo];
+    if (stab ? s_skip[lo] != 0 : (op.skip && *op.skip)) continue;
     const int R = op.R, K = op.K, N = op.N, nseg = op.nseg;
     const int nh = TALL ? 1 : (N + TC - 1) / TC;
     const i64 local = t - op.tile_begin;
     const int h = (int)(local % nh);
     const int row0 = (int)(local / nh) * TR;
+    const int nkb = (K + OZ_KB - 1) / OZ_KB;
+    const int nstage = nseg * nkb;
+    double ra[EPT];
+    auto load_stage = [&](int st2) {
+      const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * EPT;
+      const double* __restrict__ A = op.A[s];
+      const int gr = row0 + srow;
+      if (gr < R && (K & 1) == 0 && k0 + EPT <= K) {  // 16-byte aligned pairs
+        const double2* src = (const double2*)(A + (i64)gr * K + k0);
+#pragma unroll
+        for (int i = 0; i < EPT / 2; ++i) {
+          const double2 t2 = __ldg(src + i);
+          ra[2 * i] = t2.x;
+          ra[2 * i + 1] = t2.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          const int k = k0 + i;
+          ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
+        }
+      }
+    };
+    load_stage(0);  // in flight during the exponent prologue
     for (int i = tid; i < nseg * TR; i += OZ_MTHREADS) {
       const int s = i / TR, r = i % TR;
       s_es[s][r] = (row0 + r < R) ? op.Aexp[s][row0 + r] : 0;
@@ -350,8 +389,6 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
         s_del[r][c] = (unsigned char)min(s_emax[r] + s_fmax[c] - tmax, 255);
       }
     }
-    const int nkb = (K + OZ_KB - 1) / OZ_KB;
-    const int nstage = nseg * nkb;
     // fixed point: one segment's sum V = sum_d acc_d 2^(OZ_G - 7 d) stays below
     // 1.02 * 2^(19 + OZ_G) = 2^62.03 (one unit: 2^-55 of max|a| max|b|); with
     // more segments each is shifted down by guard = ceil(log2 nseg) bits, so
@@ -360,28 +397,6 @@ __global__ void __launch_bounds__(OZ_MTHREADS, 1) oz_mode_kernel(const OzOp* __r
     long long S[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) S[i] = 0;
-    double ra[EPT];
-    auto load_stage = [&](int st2) {
-      const int s = st2 / nkb, k0 = (st2 % nkb) * OZ_KB + kh * EPT;
-      const double* __restrict__ A = op.A[s];
-      const int gr = row0 + srow;
-      if (gr < R && (K & 1) == 0 && k0 + EPT <= K) {  // 16-byte aligned pairs
-        const double2* src = (const double2*)(A + (i64)gr * K + k0);
-#pragma unroll
-        for (int i = 0; i < EPT / 2; ++i) {
-          const double2 t2 = __ldg(src + i);
-          ra[2 * i] = t2.x;
-          ra[2 * i + 1] = t2.y;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-          const int k = k0 + i;
-          ra[i] = (gr < R && k < K) ? __ldg(A + (i64)gr * K + k) : 0.0;
-        }
-      }
-    };
-    load_stage(0);
     for (int st = 0; st < nstage; ++st) {
       const int s = st / nkb, kb = st % nkb, b = st & 1;
       if (b ? mpend1 : mpend0) wait_mma(b);
