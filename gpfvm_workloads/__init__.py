@@ -30,18 +30,20 @@ import numpy as np
 __all__ = [
     "PointSet", "Problem", "heat_1d", "heat_2d", "wave_2d", "wave_2d_sine",
     "toy_cos", "batch_heat", "serving_wave_stream", "uniform_edges",
-    "gaussian_bumps",
+    "gaussian_bumps", "wave_1d_system", "shallow_water_2d",
 ]
 
 
 @dataclass
 class PointSet:
-    """A tensor grid of point functionals  d^order u (x)  (one per grid point)."""
+    """A tensor grid of point functionals  d^order u (x)  (one per grid point);
+    with several outputs, of the component u_out."""
     order: Tuple[int, ...]
     coords: List[np.ndarray]
     values: np.ndarray
     noise_var: float
     name: str = ""
+    out: int = 0
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -72,6 +74,15 @@ class Problem:
     # over n_cells) multiplying the term's coefficient -- a piecewise-constant
     # variable coefficient such as a bathymetry-dependent wave speed
     fields: Optional[List[Optional[np.ndarray]]] = None
+    # several outputs (Sec. 3.3, multi-dimensional codomains): u = (u_0 .. u_{n_out-1})
+    # with independent tensor-product priors of the same hyperparameters; term k
+    # belongs to equation term_eq[k] and differentiates component term_out[k]
+    # (None: one equation, one output).  Every cell yields one observation per
+    # equation; PDE observations are ordered equation-major, predictions
+    # output-major.
+    n_out: int = 1
+    term_eq: Optional[List[int]] = None
+    term_out: Optional[List[int]] = None
 
     @property
     def ndim(self) -> int:
@@ -82,8 +93,13 @@ class Problem:
         return tuple(len(e) - 1 for e in self.edges)
 
     @property
+    def n_eq(self) -> int:
+        return 1 if self.term_eq is None else int(max(self.term_eq)) + 1
+
+    @property
     def N(self) -> int:
-        return int(np.prod(self.n_cells))
+        """PDE observations: one per cell and equation."""
+        return self.n_eq * int(np.prod(self.n_cells))
 
     @property
     def M(self) -> int:
@@ -91,7 +107,8 @@ class Problem:
 
     @property
     def P(self) -> int:
-        return int(np.prod([len(p) for p in self.pred]))
+        """Prediction points: the grid for every output."""
+        return self.n_out * int(np.prod([len(p) for p in self.pred]))
 
 
 def uniform_edges(lo: float, hi: float, n: int) -> np.ndarray:
@@ -342,3 +359,63 @@ def serving_wave_stream(rate: float = 500.0, duration: float = 1.0, lo: int = 32
                     pred=(nt // 2, nx // 2, ny // 2), ic_noise=0.0, ell=ell, jitter=jitter)
         reqs.append((t, p))
     return reqs
+
+
+def wave_1d_system(nt: int = 8, nx: int = 8, pred=(9, 9), ell=(0.5, 0.3), jitter: float = 1e-10,
+                   n_ic: Optional[int] = None) -> Problem:
+    """The 1D wave equation as a first-order system in two outputs (u, v):
+        u_t + v_x = 0,   v_t + u_x = 0   on [0,1]^2,
+    u(0, x) = sin(pi x), v(0, x) = 0, u(t, 0) = u(t, 1) = 0, solved by
+    u = sin(pi x) cos(pi t), v = -cos(pi x) sin(pi t).  Each equation couples
+    both components (Sec. 3.3: operators sum_alpha sum_i c_{alpha,i} D^alpha u_i)."""
+    te, xe = uniform_edges(0, 1, nt), uniform_edges(0, 1, nx)
+    n_ic = nx + 1 if n_ic is None else n_ic
+    xs = np.linspace(0, 1, n_ic)
+    t0 = np.array([0.0])
+    ic_u = PointSet((0, 0), [t0, xs], np.sin(np.pi * xs), jitter, "ic_u", out=0)
+    ic_v = PointSet((0, 0), [t0, xs], np.zeros(n_ic), jitter, "ic_v", out=1)
+    tb = np.linspace(0, 1, nt + 1)[1:]
+    bc = PointSet((0, 0), [tb, np.array([0.0, 1.0])], np.zeros(2 * nt), jitter, "bc_u", out=0)
+    terms = [((1, 0), 1.0), ((0, 1), 1.0), ((1, 0), 1.0), ((0, 1), 1.0)]
+    grid = [np.linspace(0, 1, pred[0]), np.linspace(0, 1, pred[1])]
+    return Problem([te, xe], tuple(ell), 1.0, terms, jitter, [ic_u, ic_v, bc], grid,
+                   name=f"wave1d_system_{nt}x{nx}", n_out=2, term_eq=[0, 0, 1, 1], term_out=[0, 1, 1, 0])
+
+
+def shallow_water_2d(nt: int = 8, nx: int = 8, ny: int = 8, H: float = 1.0, g: float = 1.0, f: float = 0.5,
+                     k: float = 0.1, n_ic=(8, 8), n_bc=(4, 4), pred=(4, 5, 5), ell=(0.4, 0.3, 0.3),
+                     width: float = 0.15, jitter: float = 1e-8, seed: int = 0) -> Problem:
+    """Linearised 2D shallow-water equations with constant depth H (App. C.4's
+    system without its variable bathymetry), outputs (h, u, v):
+        h_t + H (u_x + v_y) = 0,   u_t - f v + g h_x + k u = 0,   v_t + f u + g h_y + k v = 0
+    on [0,1]^3.  IC: a Gaussian bump of the given width (centre U(0.35,0.65)^2) in h, zero
+    velocities; walls: u = 0 at x = 0, 1 and v = 0 at y = 0, 1 on n_bc (time x tangential)
+    midpoint grids."""
+    rng = np.random.default_rng(seed)
+    cx, cy = rng.uniform(0.35, 0.65, 2)
+    edges = [uniform_edges(0, 1, nt), uniform_edges(0, 1, nx), uniform_edges(0, 1, ny)]
+    xs, ys = np.linspace(0, 1, n_ic[0]), np.linspace(0, 1, n_ic[1])
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    h0 = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width)).ravel()
+    t0 = np.array([0.0])
+    ic_h = PointSet((0, 0, 0), [t0, xs, ys], h0, jitter, "ic_h", out=0)
+    ic_u = PointSet((0, 0, 0), [t0, xs, ys], np.zeros(h0.size), jitter, "ic_u", out=1)
+    ic_v = PointSet((0, 0, 0), [t0, xs, ys], np.zeros(h0.size), jitter, "ic_v", out=2)
+    tb, sb = _mid(0, 1, n_bc[0]), _mid(0, 1, n_bc[1])
+    two = np.array([0.0, 1.0])
+    wall_u = PointSet((0, 0, 0), [tb, two, sb], np.zeros(n_bc[0] * 2 * n_bc[1]), jitter, "wall_u", out=1)
+    wall_v = PointSet((0, 0, 0), [tb, sb, two], np.zeros(n_bc[0] * 2 * n_bc[1]), jitter, "wall_v", out=2)
+    terms, eq, out = [], [], []
+
+    def add(alpha, c, e, o):
+        if c != 0.0:
+            terms.append((alpha, float(c)))
+            eq.append(e)
+            out.append(o)
+    add((1, 0, 0), 1.0, 0, 0); add((0, 1, 0), H, 0, 1); add((0, 0, 1), H, 0, 2)
+    add((1, 0, 0), 1.0, 1, 1); add((0, 0, 0), -f, 1, 2); add((0, 1, 0), g, 1, 0); add((0, 0, 0), k, 1, 1)
+    add((1, 0, 0), 1.0, 2, 2); add((0, 0, 0), f, 2, 1); add((0, 0, 1), g, 2, 0); add((0, 0, 0), k, 2, 2)
+    grid = [np.linspace(0, 1, p) for p in pred]
+    return Problem(edges, tuple(ell), 1.0, terms, jitter, [ic_h, ic_u, ic_v, wall_u, wall_v], grid,
+                   name=f"swe2d_{nt}x{nx}x{ny}", meta={"H": H, "g": g, "f": f, "k": k, "centre": (cx, cy)},
+                   n_out=3, term_eq=eq, term_out=out)

@@ -175,47 +175,75 @@ class Block:
     (row-major); term t contributes c_t times the product over axes of the
     1D functional family F_{t,i} evaluated at that index.  c_t is a scalar or,
     for a piecewise-constant variable coefficient (one value per functional,
-    App. C.4 "Variable bathymetry"), an array over the block."""
+    App. C.4 "Variable bathymetry"), an array over the block.  With several
+    outputs (Sec. 3.3), term t acts on the component outs[t]."""
 
-    def __init__(self, shape: Sequence[int], terms: List[Tuple[float, list]], name: str = ""):
+    def __init__(self, shape: Sequence[int], terms: List[Tuple[float, list]], name: str = "",
+                 outs: Sequence[int] = None):
         self.shape = tuple(int(n) for n in shape)
         self.terms = terms
         self.name = name
+        self.outs = [0] * len(terms) if outs is None else [int(o) for o in outs]
 
     @property
     def size(self) -> int:
         return int(np.prod(self.shape))
 
 
-def pde_block(prob) -> Block:
+def pde_blocks(prob) -> List[Block]:
     """L_PDE of a factorized box scheme (Sec. 4.1): one volume per cell,
     L_V[u] = sum_alpha c_alpha int_V D^alpha u  (Eq. linop-def, Eq. multi-input-fv).
     With collocation observations (Sec. 3: the collocation operator
     L_x[u] = D[u](x)) the functional of a cell is instead D[u] at its centre:
-    sum_alpha c_alpha D^alpha u (x_V), point families of order alpha_i."""
-    terms = []
+    sum_alpha c_alpha D^alpha u (x_V), point families of order alpha_i.
+    With several outputs (Sec. 3.3) equation e is sum over its terms
+    c_{alpha,i} D^alpha u_i: one block per equation, in equation order."""
     colloc = getattr(prob, "observe", "fvm") == "collocation"
     fields = getattr(prob, "fields", None)
-    for k, (alpha, c) in enumerate(prob.terms):
-        if fields is not None and fields[k] is not None:
-            c = float(c) * np.asarray(fields[k], np.float64).ravel()
-        if colloc:
-            fams = [point_family(0.5 * (e[:-1] + e[1:]), a) for e, a in zip(prob.edges, alpha)]
-        else:
-            fams = [cell_family(e[:-1], e[1:], a) for e, a in zip(prob.edges, alpha)]
-        terms.append((c if isinstance(c, np.ndarray) else float(c), fams))
-    return Block(prob.n_cells, terms, "pde")
+    eqs = getattr(prob, "term_eq", None) or [0] * len(prob.terms)
+    outs = getattr(prob, "term_out", None) or [0] * len(prob.terms)
+    blocks = []
+    for e in range(max(eqs) + 1):
+        terms, touts = [], []
+        for k, (alpha, c) in enumerate(prob.terms):
+            if eqs[k] != e:
+                continue
+            if fields is not None and fields[k] is not None:
+                c = float(c) * np.asarray(fields[k], np.float64).ravel()
+            if colloc:
+                fams = [point_family(0.5 * (ed[:-1] + ed[1:]), a) for ed, a in zip(prob.edges, alpha)]
+            else:
+                fams = [cell_family(ed[:-1], ed[1:], a) for ed, a in zip(prob.edges, alpha)]
+            terms.append((c if isinstance(c, np.ndarray) else float(c), fams))
+            touts.append(outs[k])
+        blocks.append(Block(prob.n_cells, terms, f"pde{e}", touts))
+    return blocks
+
+
+def pde_block(prob) -> Block:
+    """The PDE block of a one-equation problem (see pde_blocks)."""
+    blocks = pde_blocks(prob)
+    if len(blocks) != 1:
+        raise ValueError("several equations: use pde_blocks")
+    return blocks[0]
 
 
 def point_block(ps) -> Block:
-    """A tensor grid of point functionals d^m u (x) (initial/boundary data)."""
+    """A tensor grid of point functionals d^m u (x) (initial/boundary data) of
+    the component ps.out."""
     return Block(ps.shape, [(1.0, [point_family(x, m) for x, m in zip(ps.coords, ps.order)])],
-                 ps.name)
+                 ps.name, [getattr(ps, "out", 0)])
+
+
+def pred_blocks(prob) -> List[Block]:
+    """Point evaluations u_j(x) on the prediction grid, one block per output j."""
+    return [Block([len(p) for p in prob.pred], [(1.0, [point_family(p, 0) for p in prob.pred])], f"pred{j}",
+                  [j]) for j in range(getattr(prob, "n_out", 1))]
 
 
 def pred_block(prob) -> Block:
     """Point evaluations u(x) on the prediction grid."""
-    return Block([len(p) for p in prob.pred], [(1.0, [point_family(p, 0) for p in prob.pred])], "pred")
+    return pred_blocks(prob)[0]
 
 
 def block_cov(X: Block, Y: Block, ell: Sequence[float], outputscale: float) -> np.ndarray:
@@ -224,8 +252,10 @@ def block_cov(X: Block, Y: Block, ell: Sequence[float], outputscale: float) -> n
     I = np.unravel_index(np.arange(X.size), X.shape)
     J = np.unravel_index(np.arange(Y.size), Y.shape)
     out = np.zeros((X.size, Y.size))
-    for c1, F in X.terms:
-        for c2, G in Y.terms:
+    for (c1, F), o1 in zip(X.terms, X.outs):
+        for (c2, G), o2 in zip(Y.terms, Y.outs):
+            if o1 != o2:  # outputs are a priori uncorrelated (Eq. multioutput-cov-def)
+                continue
             # a variable coefficient makes the term pair a Hadamard product with
             # the rank-one matrix c1 c2^T (App. C.4)
             prod = np.outer(np.broadcast_to(c1, (X.size,)), np.broadcast_to(c2, (Y.size,))).copy()
@@ -241,7 +271,7 @@ def block_cov(X: Block, Y: Block, ell: Sequence[float], outputscale: float) -> n
 # ----------------------------------------------------------------------------
 def ibvp_blocks(prob):
     """Observation blocks in the order of L_IBVP = (L_IC,BC ; L_PDE) (Sec. 2.2)."""
-    return [point_block(s) for s in prob.sets] + [pde_block(prob)]
+    return [point_block(s) for s in prob.sets] + pde_blocks(prob)
 
 
 def noise_diag(prob) -> np.ndarray:
@@ -273,8 +303,9 @@ def dense_posterior(prob, return_gram: bool = False):
     (zero prior mean, zero noise mean; G is positive definite so G^+ = G^-1)."""
     G = dense_gram(prob)
     y = observations(prob)
-    pb = pred_block(prob)
-    Kx = np.vstack([block_cov(X, pb, prob.lengthscale, prob.outputscale) for X in ibvp_blocks(prob)])
+    pbs = pred_blocks(prob)  # one per output: the grid output-major
+    Kx = np.vstack([np.hstack([block_cov(X, pb, prob.lengthscale, prob.outputscale) for pb in pbs])
+                    for X in ibvp_blocks(prob)])
     L = sla.cholesky(G, lower=True)
     alpha = sla.cho_solve((L, True), y)
     mean = Kx.T @ alpha
@@ -309,6 +340,8 @@ class KronIBVP:
     c_a c_b^T (App. C.4), applied as diag(c_a) (x)A diag(c_b)."""
 
     def __init__(self, prob):
+        if getattr(prob, "n_out", 1) != 1 or getattr(prob, "term_eq", None) is not None:
+            raise NotImplementedError("KronIBVP: one output; use dense_posterior for systems")
         self.prob = prob
         self.ell = prob.lengthscale
         self.s2 = prob.outputscale
@@ -700,4 +733,8 @@ PINS = {
     "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
                                       "on one point is the Cauchy-Schwarz-optimal single-action reduction; "
                                       "repeated targeted actions reach the exact (Cholesky) variance there",
+    "multi-output (pde_blocks / pred_blocks / block_cov outs)": "two decoupled equations == the pair of one-output "
+                                                                "posteriors; an unobserved output keeps its prior; "
+                                                                "the first-order 1D wave system converges to its "
+                                                                "analytic solution (and not with swapped components)",
 }

@@ -1,0 +1,89 @@
+"""Pins of the oracle's multi-output posterior (Sec. 3.3, multi-dimensional
+codomains: independent priors per output, operators summing derivatives of
+several components), against things other than itself:
+
+* a system of two decoupled equations is the pair of one-output posteriors;
+* an output that no observation touches keeps its prior;
+* the first-order form of the 1D wave equation (u_t + v_x = 0, v_t + u_x = 0)
+  converges to its analytic solution under refinement, which fails if a term
+  acts on the wrong component."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import gpfvm_workloads as W
+import oracle as O
+
+
+def _system_of(a, b):
+    """The two one-output problems a, b (same cells, kernel, grid) as one
+    two-output system: equation 0 = a's PDE on u_0, equation 1 = b's on u_1."""
+    sets = [replace(s, out=0) for s in a.sets] + [replace(s, out=1) for s in b.sets]
+    terms = list(a.terms) + list(b.terms)
+    eq = [0] * len(a.terms) + [1] * len(b.terms)
+    return replace(a, terms=terms, sets=sets, n_out=2, term_eq=eq, term_out=list(eq), name="pair")
+
+
+def test_decoupled_system_is_the_pair_of_single_posteriors():
+    a = W.heat_1d(5, 6, nu=0.05, n_ic=5, n_bc=3, pred=5)
+    b = W.heat_1d(5, 6, nu=0.2, n_ic=5, n_bc=3, pred=5)
+    b = replace(b, sets=[replace(s, values=np.cos(np.arange(s.size))) for s in b.sets])
+    ma, va = O.dense_posterior(a)
+    mb, vb = O.dense_posterior(b)
+    sysp = _system_of(a, b)
+    assert sysp.N == a.N + b.N and sysp.P == a.P + b.P
+    m, v = O.dense_posterior(sysp)
+    P = a.P
+    np.testing.assert_allclose(m[:P], ma, rtol=0, atol=1e-10 * max(1.0, np.abs(ma).max()))
+    np.testing.assert_allclose(m[P:], mb, rtol=0, atol=1e-10 * max(1.0, np.abs(mb).max()))
+    np.testing.assert_allclose(v[:P], va, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(v[P:], vb, rtol=0, atol=1e-10)
+
+
+def test_unobserved_output_keeps_its_prior():
+    a = W.heat_1d(5, 6, nu=0.1, n_ic=5, n_bc=3, pred=5)
+    sysp = replace(a, n_out=2, term_eq=[0] * len(a.terms), term_out=[0] * len(a.terms))
+    m, v = O.dense_posterior(sysp)
+    ma, va = O.dense_posterior(a)
+    P = a.P
+    np.testing.assert_allclose(m[:P], ma, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(v[:P], va, rtol=0, atol=1e-12)
+    assert np.all(m[P:] == 0.0)
+    np.testing.assert_allclose(v[P:], a.outputscale, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("swap", [False, True])
+def test_first_order_wave_system_converges_to_the_analytic_solution(swap):
+    """u = sin(pi x) cos(pi t), v = -cos(pi x) sin(pi t).  With the components of
+    equation 1 swapped (a plausible indexing mistake) the posterior does not
+    approach that solution."""
+    errs = []
+    for n in (4, 8, 16):
+        p = W.wave_1d_system(n, n, pred=(9, 9), ell=(0.5, 0.3))
+        if swap:
+            p = replace(p, term_out=[0, 1, 0, 1])
+        m, _ = O.dense_posterior(p)
+        T, X = np.meshgrid(p.pred[0], p.pred[1], indexing="ij")
+        u = np.sin(np.pi * X) * np.cos(np.pi * T)
+        v = -np.cos(np.pi * X) * np.sin(np.pi * T)
+        P = T.size
+        errs.append(max(np.abs(m[:P] - u.ravel()).max(), np.abs(m[P:] - v.ravel()).max()))
+    if swap:
+        assert errs[-1] > 0.1
+    else:
+        assert errs[0] > errs[1] > errs[2]
+        assert errs[2] < 1e-3
+
+
+def test_multi_output_blocks_zero_across_components():
+    """Cross-covariances between observations of different outputs vanish
+    (Eq. multioutput-cov-def); within one output they are the one-output ones."""
+    p = W.wave_1d_system(4, 5)
+    ic_u, ic_v = (O.point_block(s) for s in p.sets[:2])
+    assert np.all(O.block_cov(ic_u, ic_v, p.lengthscale, p.outputscale) == 0.0)
+    K = O.block_cov(ic_u, ic_u, p.lengthscale, p.outputscale)
+    K1 = O.block_cov(O.point_block(replace(p.sets[0], out=1)), ic_v, p.lengthscale, p.outputscale)
+    np.testing.assert_array_equal(K, K1)
+    eq0, eq1 = O.pde_blocks(p)
+    assert eq0.outs == [0, 1] and eq1.outs == [1, 0]
