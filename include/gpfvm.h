@@ -55,6 +55,7 @@ extern "C" {
 #define GPFVM_MAX_DIM 3
 #define GPFVM_MAX_TERMS 8
 #define GPFVM_MAX_SETS 8
+#define GPFVM_MAX_OUTPUTS 4
 
 enum gpfvm_status {
   GPFVM_OK = 0,
@@ -117,7 +118,25 @@ typedef struct {
  *                  products (FP64 matrix-product accuracy; every axis <= 128
  *                  cells and constant coefficients, else FP64 FMA); 1: always
  *                  FP64 FMA (SIMT) mode products.  Ops 0/1 of gpfvm_gram_matvec
- *                  are FP64 FMA and ops 12/13 the digit-product form either way. */
+ *                  are FP64 FMA and ops 12/13 the digit-product form either way.
+ *   n_outputs      0: one equation on one output u (term_eq, term_out and
+ *                  set_out are not read).  >= 1 (at most GPFVM_MAX_OUTPUTS): a
+ *                  system in u = (u_0 .. u_{n_outputs-1}) with independent
+ *                  priors of the same hyperparameters (Sec. 3.3, Eq.
+ *                  multioutput-cov-def).  Term k belongs to equation
+ *                  term_eq[k] and differentiates component term_out[k]
+ *                  (Sec. 3.3: an operator sum_alpha sum_i c_{alpha,i} D^alpha
+ *                  u_i); the equations are numbered 0 .. n_eq - 1 without
+ *                  gaps, and every cell yields one observation per equation.
+ *                  Set s observes component set_out[s].  With n_outputs = 1
+ *                  and one equation this is the one-output problem.  Vectors over the PDE
+ *                  observations (rhs, gram_matvec, the CG directions) hold
+ *                  n_eq blocks of prod n_cells, equation-major; the prediction
+ *                  grid is evaluated for every output, output-major (P =
+ *                  n_outputs prod n_pred).  Such systems are solved in FP64
+ *                  with FMA mode products and the dense IC/BC stage (no
+ *                  mixed precisions, coefficient fields, multigrid start,
+ *                  targeted actions, batches or server). */
 typedef struct {
   int ndim;
   int n_cells[GPFVM_MAX_DIM];
@@ -136,6 +155,10 @@ typedef struct {
   int observe;
   const double* coef_field[GPFVM_MAX_TERMS];
   int fp64_products;
+  int n_outputs;
+  int term_eq[GPFVM_MAX_TERMS];
+  int term_out[GPFVM_MAX_TERMS];
+  int set_out[GPFVM_MAX_SETS];
 } gpfvm_desc;
 
 /* Precision of the CG iteration. */

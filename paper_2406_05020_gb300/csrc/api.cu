@@ -46,6 +46,7 @@ namespace {
 // Schur complement.  Layouts agree: axis 0 is the slowest, so the stacked
 // set's values are the first set's followed by the second's.
 struct SetC {
+  int comp = 0;         // the output component observed (systems, Sec. 3.3)
   int order[3] = {0, 0, 0};
   int order2 = -1;      // axis-0 order of point 1 of a stacked set (else -1)
   double noise2 = 0.0;  // its noise variance
@@ -200,6 +201,13 @@ struct gpfvm_problem {
   std::vector<double> rhs;
   int nsets = 0;
   SetC sets[GPFVM_MAX_SETS];
+  // systems (Sec. 3.3): neq equations over nout independent outputs; term a
+  // belongs to equation teq[a] and differentiates output tout[a].  PDE vectors
+  // hold neq blocks of Nc cells, predictions nout blocks of Pp points.
+  bool multi = false;
+  int neq = 1, nout = 1;
+  int teq[GPFVM_MAX_TERMS] = {}, tout[GPFVM_MAX_TERMS] = {};
+  i64 Nc = 0, Pp = 0;
   // the caller's sets: set u is internal set uset[u], and with uslice[u] >= 0
   // the axis-0 point uslice[u] of that stacked set
   int nusets = 0;
@@ -379,6 +387,7 @@ void stack_sets(gpfvm_problem* p) {
   if ((env && std::atoi(env) == 0) || p->d < 2) return;
   auto stackable = [&](const SetC& a, const SetC& b) {
     if (a.n[0] != 1 || b.n[0] != 1 || a.coords[0][0] != b.coords[0][0] || a.order[0] == b.order[0]) return false;
+    if (a.comp != b.comp) return false;
     for (int i = 1; i < p->d; ++i)
       if (a.n[i] != b.n[i] || a.order[i] != b.order[i] || a.coords[i] != b.coords[i]) return false;
     return true;
@@ -557,6 +566,47 @@ std::vector<KTerm> bpred_terms(const gpfvm_problem* p, int s, bool fold = false)
   t.c = 1.0;
   for (int i = 0; i < p->d; ++i) t.f[i] = q ? facq_ref(p, i, 1, s, 2, 0, true) : fac_ref(p, i, 1, s, 2, 0, true);
   return {t};
+}
+
+// ---- systems (Sec. 3.3): the terms of one block.  Outputs are a priori
+// uncorrelated (Eq. multioutput-cov-def), so a pair of terms contributes only
+// where both act on the same output.
+// G_PP block (equation e, equation e2): pairs a in e, b in e2 on one output
+std::vector<KTerm> pp_terms_mo(const gpfvm_problem* p, int e, int e2) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a)
+    for (int b = 0; b < p->nterms; ++b) {
+      if (p->teq[a] != e || p->teq[b] != e2 || p->tout[a] != p->tout[b]) continue;
+      KTerm t{};
+      t.c = p->coef[a] * p->coef[b];
+      for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 0, p->alpha[b][i], false);
+      ts.push_back(t);
+    }
+  return ts;
+}
+// cells of equation e -> set s (to_set) or back: the terms of e on the set's output
+std::vector<KTerm> pb_terms_mo(const gpfvm_problem* p, int s, int e, bool to_set) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a) {
+    if (p->teq[a] != e || p->tout[a] != p->sets[s].comp) continue;
+    KTerm t{};
+    t.c = p->coef[a];
+    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 1, s, to_set);
+    ts.push_back(t);
+  }
+  return ts;
+}
+// cells of equation e -> prediction grid of output j
+std::vector<KTerm> ppred_terms_mo(const gpfvm_problem* p, int e, int j) {
+  std::vector<KTerm> ts;
+  for (int a = 0; a < p->nterms; ++a) {
+    if (p->teq[a] != e || p->tout[a] != j) continue;
+    KTerm t{};
+    t.c = p->coef[a];
+    for (int i = 0; i < p->d; ++i) t.f[i] = fac_ref(p, i, 0, p->alpha[a][i], 2, 0, true);
+    ts.push_back(t);
+  }
+  return ts;
 }
 
 void dims_cells(const gpfvm_problem* p, int* o) { for (int i = 0; i < p->d; ++i) o[i] = p->nc[i]; }
@@ -859,6 +909,10 @@ struct Builder {
 
   // out = G_BP in (cells -> all sets), into g (M); fold: set 0 in its eigenbasis
   void bp(Plan& plan, const double* in, double* g, bool fold = false) {
+    if (p->multi) {
+      mo_bp(plan, in, g);
+      return;
+    }
     int dc[3], ds[3];
     dims_cells(p, dc);
     if (varcoef()) {
@@ -880,6 +934,10 @@ struct Builder {
   }
   // out (+)= scale * G_PB w; fold: the set-0 part of w in its eigenbasis
   void pb(Plan& plan, const double* w, double* out, double scale, bool accumulate, bool fold = false) {
+    if (p->multi) {
+      mo_pb(plan, w, out, scale, accumulate);
+      return;
+    }
     int dc[3], ds[3];
     dims_cells(p, dc);
     if (varcoef()) {
@@ -986,7 +1044,7 @@ struct Builder {
   // faces), when its other dimensions and those of the grid dt fit the
   // bilinear kernel; else -1.
   int face_axis(int s, const int* dt) const {
-    if (p->d != 3 || p->nterms > FACE_MAXT) return -1;
+    if (p->d != 3 || p->nterms > FACE_MAXT || p->multi) return -1;
     int a = 0;
     for (int i = 1; i < 3; ++i)
       if (p->sets[s].n[i] < p->sets[s].n[a]) a = i;
@@ -1242,6 +1300,10 @@ struct Builder {
   // `skip` is the plan's skip flag (the digit-product chains honour it too).
   void ghat_phased(Plan& plan, const double* in, double* out, double* g, double* w, double* u, int* count,
                    Plan* pp_chain = nullptr, const int* skip = nullptr) {
+    if (p->multi) {
+      mo_ghat(plan, in, out, g, w, u);
+      return;
+    }
     if (varcoef()) {
       vc_ghat(plan, in, out, g, w, u, true);
       return;
@@ -1370,6 +1432,10 @@ struct Builder {
   }
 
   void pp(Plan& plan, const double* in, double* out, int* count) {
+    if (p->multi) {
+      mo_pp(plan, in, out);
+      return;
+    }
     if (varcoef()) {
       vc_ghat(plan, in, out, nullptr, nullptr, nullptr, false);
       return;
@@ -1380,6 +1446,10 @@ struct Builder {
   }
   // u (+)= scale * (L_PDE k(X*))^T v
   void to_pred_cells(Plan& plan, const double* v, double* u, double scale, bool acc) {
+    if (p->multi) {
+      mo_to_pred_cells(plan, v, u, scale, acc);
+      return;
+    }
     int dc[3], dp[3];
     dims_cells(p, dc);
     dims_pred(p, dp);
@@ -1418,12 +1488,117 @@ struct Builder {
     }
   }
   void to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc, bool fold = false) {
+    if (p->multi) {
+      mo_to_pred_sets(plan, w, u, scale, acc);
+      return;
+    }
     int ds[3], dp[3];
     dims_pred(p, dp);
     for (int s = 0; s < p->nsets; ++s) {
       dims_set(p, s, ds);
       kron(plan, ds, dp, 1, bpred_terms(p, s, fold), scale * p->s2, at(w, p->sets[s].off), u,
            (acc || s > 0) ? 1.0 : 0.0, nullptr, 0.0);
+    }
+  }
+
+  // ---- systems (Sec. 3.3): block by block, sequential FP64 Kronecker chains
+  // (no face forms, digit products, tensor cores or structured IC/BC stage).
+  // PDE vectors: neq blocks of Nc cells; predictions: nout blocks of Pp points.
+  void zero(Plan& plan, double* x, i64 n) {
+    plan.func([=](cudaStream_t st) { GPFVM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st)); });
+  }
+  // out_e = sum_e2 G_PP[e, e2] in_e2 + jitter in_e (the diagonal block first: it carries the jitter)
+  void mo_pp(Plan& plan, const double* in, double* out) {
+    int dc[3];
+    dims_cells(p, dc);
+    const i64 Nc = p->Nc;
+    for (int e = 0; e < p->neq; ++e) {
+      bool first = true;
+      for (int k = 0; k < p->neq; ++k) {
+        const int e2 = (e + k) % p->neq;
+        const std::vector<KTerm> ts = pp_terms_mo(p, e, e2);
+        if (ts.empty()) continue;
+        kron(plan, dc, dc, 1, ts, p->s2, in + e2 * Nc, out + e * Nc, first ? 0.0 : 1.0, first ? in + e * Nc : nullptr,
+             first ? p->jitter : 0.0);
+        first = false;
+      }
+    }
+  }
+  // g_s = sum_e G_BP[s, e] in_e for every set s
+  void mo_bp(Plan& plan, const double* in, double* g) {
+    int dc[3], ds[3];
+    dims_cells(p, dc);
+    for (int s = 0; s < p->nsets; ++s) {
+      dims_set(p, s, ds);
+      bool first = true;
+      for (int e = 0; e < p->neq; ++e) {
+        const std::vector<KTerm> ts = pb_terms_mo(p, s, e, true);
+        if (ts.empty()) continue;
+        kron(plan, dc, ds, 1, ts, p->s2, in + e * p->Nc, g + p->sets[s].off, first ? 0.0 : 1.0, nullptr, 0.0);
+        first = false;
+      }
+      if (first) zero(plan, g + p->sets[s].off, p->sets[s].size);  // no equation involves its output
+    }
+  }
+  // out_e (+)= scale sum_s G_PB[e, s] w_s
+  void mo_pb(Plan& plan, const double* w, double* out, double scale, bool accumulate) {
+    int dc[3], ds[3];
+    dims_cells(p, dc);
+    for (int e = 0; e < p->neq; ++e) {
+      bool first = !accumulate;
+      for (int s = 0; s < p->nsets; ++s) {
+        const std::vector<KTerm> ts = pb_terms_mo(p, s, e, false);
+        if (ts.empty()) continue;
+        dims_set(p, s, ds);
+        kron(plan, ds, dc, 1, ts, scale * p->s2, w + p->sets[s].off, out + e * p->Nc, first ? 0.0 : 1.0, nullptr, 0.0);
+        first = false;
+      }
+      if (first) zero(plan, out + e * p->Nc, p->Nc);
+    }
+  }
+  // u_j (+)= scale sum_e (L_e k(X*_j))^T v_e for every output j
+  void mo_to_pred_cells(Plan& plan, const double* v, double* u, double scale, bool acc) {
+    int dc[3], dp[3];
+    dims_cells(p, dc);
+    dims_pred(p, dp);
+    for (int j = 0; j < p->nout; ++j) {
+      bool first = !acc;
+      for (int e = 0; e < p->neq; ++e) {
+        const std::vector<KTerm> ts = ppred_terms_mo(p, e, j);
+        if (ts.empty()) continue;
+        kron(plan, dc, dp, 1, ts, scale * p->s2, v + e * p->Nc, u + j * p->Pp, first ? 0.0 : 1.0, nullptr, 0.0);
+        first = false;
+      }
+      if (first) zero(plan, u + j * p->Pp, p->Pp);
+    }
+  }
+  // u_j (+)= scale sum over the sets s observing output j of k_s(X*_j)^T w_s
+  void mo_to_pred_sets(Plan& plan, const double* w, double* u, double scale, bool acc) {
+    int ds[3], dp[3];
+    dims_pred(p, dp);
+    for (int j = 0; j < p->nout; ++j) {
+      bool first = !acc;
+      for (int s = 0; s < p->nsets; ++s) {
+        if (p->sets[s].comp != j) continue;
+        dims_set(p, s, ds);
+        kron(plan, ds, dp, 1, bpred_terms(p, s), scale * p->s2, w + p->sets[s].off, u + j * p->Pp,
+             first ? 0.0 : 1.0, nullptr, 0.0);
+        first = false;
+      }
+      if (first) zero(plan, u + j * p->Pp, p->Pp);
+    }
+  }
+  // out = G^ in = G_PP in - G_PB G_BB^-1 G_BP in; with u also u = Lhat k(X*)^T in
+  void mo_ghat(Plan& plan, const double* in, double* out, double* g, double* w, double* u) {
+    mo_pp(plan, in, out);
+    if (p->M > 0) {
+      mo_bp(plan, in, g);
+      hsolve(plan, g, w);
+      mo_pb(plan, w, out, -1.0, true);
+    }
+    if (u) {
+      mo_to_pred_cells(plan, in, u, 1.0, false);
+      if (p->M > 0) mo_to_pred_sets(plan, w, u, -1.0, true);
     }
   }
 };
@@ -1754,7 +1929,7 @@ void build_oz_instance(gpfvm_problem* p, OzBuild& O, const double* in, double* o
 void build_oz(gpfvm_problem* p) {
   p->oz_jobs.clear();
   for (auto& L : p->oz_levels) L.clear();
-  if (p->nfield > 0 || p->d < 2) {  // (one axis: a single row of up to 128 cells, FMA form)
+  if (p->nfield > 0 || p->d < 2 || p->multi) {  // (one axis: a single row of up to 128 cells, FMA form)
     p->oz_ok = false;
     return;
   }
@@ -1848,6 +2023,7 @@ void build_plans(gpfvm_problem* p, Builder& B) {
         G.off[s] = (int)p->sets[s].off;
         G.noise[s] = p->sets[s].noise;
         G.noise2[s] = p->sets[s].order2 >= 0 ? p->sets[s].noise2 : p->sets[s].noise;
+        G.comp[s] = p->sets[s].comp;
         for (int i = 0; i < p->d; ++i) G.dims[s][i] = p->sets[s].n[i];
         for (int s2 = 0; s2 < p->nsets; ++s2)
           for (int i = 0; i < p->d; ++i)
@@ -1946,11 +2122,13 @@ void build_plans(gpfvm_problem* p, Builder& B) {
   // ---- targeted actions (appendix "Targeted uncertainty reduction"):
   // p = Lhat k(X*) beta = L_PDE k(X*) beta - G_PB G_BB^-1 L_IC,BC k(X*) beta
   p->p_tgt = Plan();
-  B.from_pred_cells(p->p_tgt, p->d_tbeta, p->d_p, 1.0);
-  if (M > 0) {
-    B.from_pred_sets(p->p_tgt, p->d_tbeta, p->d_g2, p->sicbc);
-    B.hsolve(p->p_tgt, p->d_g2, p->d_wout);
-    B.pb(p->p_tgt, p->d_wout, p->d_p, -1.0, true, p->sicbc);
+  if (!p->multi) {  // (targeted actions: one-output problems)
+    B.from_pred_cells(p->p_tgt, p->d_tbeta, p->d_p, 1.0);
+    if (M > 0) {
+      B.from_pred_sets(p->p_tgt, p->d_tbeta, p->d_g2, p->sicbc);
+      B.hsolve(p->p_tgt, p->d_g2, p->d_wout);
+      B.pb(p->p_tgt, p->d_wout, p->d_p, -1.0, true, p->sicbc);
+    }
   }
   // ---- Cholesky-stage variance term vB[p] = || L^-1 k_B(x_p) ||^2 in row chunks
   p->p_vB = Plan();
@@ -1962,25 +2140,31 @@ void build_plans(gpfvm_problem* p, Builder& B) {
     const int R = p->vb_rows;
     int dp[3], ds[3];
     dims_pred(p, dp);
+    const i64 Pp = p->Pp;
     for (i64 m0 = 0; m0 < M && R > 0; m0 += R) {
       const int rows = (int)std::min<i64>(R, M - m0);
-      bool first = true;
-      for (int s = 0; s < p->nsets; ++s) {
-        const i64 off = p->sets[s].off, ms = p->sets[s].size;
-        if (off > m0 + rows - 1) continue;  // L^-1 is lower triangular: these columns are zero
-        const double* src = p->d_Linv + m0 * M + off;
-        double* dst = p->d_vbchunk;
-        p->p_vB.func([=](cudaStream_t st) {
-          GPFVM_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ms, src, sizeof(double) * M, sizeof(double) * ms, rows,
-                                       cudaMemcpyDeviceToDevice, st));
-        });
-        dims_set(p, s, ds);
-        B.kron(p->p_vB, ds, dp, rows, bpred_terms(p, s), p->s2, p->d_vbchunk, p->d_vbY, first ? 0.0 : 1.0, nullptr,
-               0.0);
-        first = false;
+      for (int j = 0; j < p->nout; ++j) {  // (systems: the sets of output j give its grid's term)
+        bool first = true;
+        for (int s = 0; s < p->nsets; ++s) {
+          const i64 off = p->sets[s].off, ms = p->sets[s].size;
+          if (p->sets[s].comp != j) continue;
+          if (off > m0 + rows - 1) continue;  // L^-1 is lower triangular: these columns are zero
+          const double* src = p->d_Linv + m0 * M + off;
+          double* dst = p->d_vbchunk;
+          p->p_vB.func([=](cudaStream_t st) {
+            GPFVM_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ms, src, sizeof(double) * M, sizeof(double) * ms, rows,
+                                         cudaMemcpyDeviceToDevice, st));
+          });
+          dims_set(p, s, ds);
+          B.kron(p->p_vB, ds, dp, rows, bpred_terms(p, s), p->s2, p->d_vbchunk, p->d_vbY, first ? 0.0 : 1.0, nullptr,
+                 0.0);
+          first = false;
+        }
+        if (first) continue;
+        const double* Y = p->d_vbY;
+        double* vBj = vB + j * Pp;
+        p->p_vB.func([=](cudaStream_t st) { colsumsq(Y, rows, Pp, vBj, st); });
       }
-      const double* Y = p->d_vbY;
-      p->p_vB.func([=](cudaStream_t st) { colsumsq(Y, rows, P, vB, st); });
     }
   }
   finish_ozx(p);
@@ -2157,6 +2341,10 @@ Plan tc_chain(gpfvm_problem* p, int inst) {
 
 // FP32 plans of the mixed solver's inner operator.
 void build_plans32(gpfvm_problem* p, Builder& B) {
+  if (p->multi) {  // systems are solved in FP64 only
+    p->tc_ok = false;
+    return;
+  }
   B.f32 = true;
   p->building_f32 = true;
   auto D = [](float* f) { return (double*)f; };
@@ -2265,7 +2453,27 @@ int validate(const gpfvm_desc* D) {
     return GPFVM_ERR_INVALID_ARG;
   if (D->observe != 0 && D->observe != 1) return GPFVM_ERR_INVALID_ARG;
   if (D->fp64_products != 0 && D->fp64_products != 1) return GPFVM_ERR_INVALID_ARG;
-  i64 N = 1, P = 1;
+  if (D->n_outputs < 0 || D->n_outputs > GPFVM_MAX_OUTPUTS) return GPFVM_ERR_INVALID_ARG;
+  int neq = 1;
+  const int nout = D->n_outputs > 0 ? D->n_outputs : 1;
+  if (D->n_outputs > 0) {  // term_eq / term_out / set_out are read (0: one equation, one output)
+    bool used[GPFVM_MAX_TERMS] = {};
+    neq = 0;
+    for (int k = 0; k < D->n_terms; ++k) {
+      if (D->term_eq[k] < 0 || D->term_eq[k] >= GPFVM_MAX_TERMS) return GPFVM_ERR_INVALID_ARG;
+      if (D->term_out[k] < 0 || D->term_out[k] >= nout) return GPFVM_ERR_INVALID_ARG;
+      used[D->term_eq[k]] = true;
+      neq = std::max(neq, D->term_eq[k] + 1);
+    }
+    for (int e = 0; e < neq; ++e)
+      if (!used[e]) return GPFVM_ERR_INVALID_ARG;  // equations numbered without gaps
+    for (int s = 0; s < D->n_sets; ++s)
+      if (D->set_out[s] < 0 || D->set_out[s] >= nout) return GPFVM_ERR_INVALID_ARG;
+    if (nout > 1 || neq > 1)
+      for (int k = 0; k < D->n_terms; ++k)
+        if (D->coef_field[k]) return GPFVM_ERR_INVALID_ARG;  // systems take constant coefficients
+  }
+  i64 N = neq, P = nout;
   for (int i = 0; i < D->ndim; ++i) {
     if (D->n_cells[i] < 1 || D->n_cells[i] > 65536 || !D->edges[i]) return GPFVM_ERR_INVALID_ARG;
     if (!(D->lengthscale[i] > 0) || !std::isfinite(D->lengthscale[i])) return GPFVM_ERR_INVALID_ARG;
@@ -2395,7 +2603,7 @@ void alloc_all(gpfvm_problem* p) {
   if (M > 0) {
     const char* env = getenv("GPFVM_ICBC");
     bool ok = !(env && std::strcmp(env, "dense") == 0) && p->sets[0].noise > 0 &&
-              (p->sets[0].order2 < 0 || p->sets[0].noise2 > 0);
+              (p->sets[0].order2 < 0 || p->sets[0].noise2 > 0) && !p->multi;
     for (int s = 1; s < p->nsets; ++s) ok = ok && p->sets[s].size <= p->sets[0].size;
     for (int i = 0; i < p->d; ++i) ok = ok && p->sets[0].n[i] <= 96;
     p->sicbc = ok;
@@ -3056,6 +3264,7 @@ int solve_end(gpfvm_problem* p, gpfvm_solve_info* info, cudaStream_t st) {
 }
 
 int run_solve(gpfvm_problem* p, const gpfvm_solve_opts* o, gpfvm_solve_info* info, cudaStream_t st) {
+  if (p->multi && o && (o->precision != GPFVM_FP64 || o->coarse > 1)) return GPFVM_ERR_INVALID_ARG;
   if (o && o->precision != GPFVM_FP64) return mixed_solve(p, o, info, st);
   const int b = solve_begin(p, o, st);
   if (b != GPFVM_OK) return b;
@@ -3375,6 +3584,25 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
     p->N *= p->nc[i];
     p->P *= p->npred[i];
   }
+  p->Nc = p->N;
+  p->Pp = p->P;
+  if (D->n_outputs > 0) {
+    p->nout = D->n_outputs;
+    p->neq = 0;
+    for (int k = 0; k < D->n_terms; ++k) {
+      p->teq[k] = D->term_eq[k];
+      p->tout[k] = D->term_out[k];
+      p->neq = std::max(p->neq, p->teq[k] + 1);
+    }
+    p->multi = p->nout > 1 || p->neq > 1;
+  }
+  if (p->multi) {
+    p->N = p->Nc * p->neq;
+    p->P = p->Pp * p->nout;
+  } else {
+    p->neq = p->nout = 1;
+    for (int k = 0; k < D->n_terms; ++k) p->teq[k] = p->tout[k] = 0;
+  }
   p->s2 = D->outputscale;
   p->jitter = D->jitter;
   p->colloc = D->observe == 1;
@@ -3418,6 +3646,7 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
     if (D->sets[s].values) S.values.assign(D->sets[s].values, D->sets[s].values + S.size);
     else S.values.assign(S.size, 0.0);
     S.noise = D->sets[s].noise_var;
+    S.comp = p->multi ? D->set_out[s] : 0;
     S.off = off;
     off += S.size;
     p->uset[s] = s;
@@ -3537,6 +3766,7 @@ int gpfvm_gram_matvec(gpfvm_problem* p, int op, const double* v, double* out, vo
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
   if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   if (op >= 12 && !p->oz_ok) return GPFVM_ERR_INVALID_ARG;
+  if (p->multi && op > 3) return GPFVM_ERR_INVALID_ARG;  // systems: the FP64 operators 0-3
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
   bool inner = false;
@@ -3575,6 +3805,7 @@ int gpfvm_gram_matvec_bench(gpfvm_problem* p, int op, const double* v, double* o
   if ((op == 2 || op == 3) && p->M == 0) return GPFVM_ERR_INVALID_ARG;
   if (op_uses_tc(op) && !p->tc_ok) return GPFVM_ERR_INVALID_ARG;
   if (op >= 12 && !p->oz_ok) return GPFVM_ERR_INVALID_ARG;
+  if (p->multi && op > 3) return GPFVM_ERR_INVALID_ARG;  // systems: the FP64 operators 0-3
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
   bool inner = false;
@@ -3733,7 +3964,7 @@ int gpfvm_autotune(gpfvm_problem* p, int precision, void* stream, double* report
 }
 
 int gpfvm_target(gpfvm_problem* p, const double* beta, int n_actions, void* stream) {
-  if (!p || !beta || n_actions < 1) return GPFVM_ERR_INVALID_ARG;
+  if (!p || !beta || n_actions < 1 || p->multi) return GPFVM_ERR_INVALID_ARG;
   GPFVM_GUARD_BEGIN
   cudaStream_t st = pick_stream(p, stream);
   if (!p->solved || p->last_store != 1 || !p->want_var_last) return GPFVM_ERR_STATE;
@@ -3954,7 +4185,7 @@ extern "C" int gpfvm_solve_batch(gpfvm_problem** ps, int n, const gpfvm_solve_op
                                  void* stream) {
   if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
-    if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
+    if (!ps[i] || ps[i]->multi) return GPFVM_ERR_INVALID_ARG;  // (systems: one at a time)
   GPFVM_GUARD_BEGIN
   cudaEvent_t ev;
   GPFVM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -4212,7 +4443,7 @@ extern "C" int gpfvm_solve_batch_graph(gpfvm_problem** ps, int n, const gpfvm_so
                                        gpfvm_solve_info* infos, void* stream, int64_t* launches_out) {
   if (!ps || n < 0 || !opts) return GPFVM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
-    if (!ps[i]) return GPFVM_ERR_INVALID_ARG;
+    if (!ps[i] || ps[i]->multi) return GPFVM_ERR_INVALID_ARG;  // (systems: one at a time)
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j)
       if (ps[i] == ps[j]) return GPFVM_ERR_INVALID_ARG;  // one loop per problem
@@ -4342,6 +4573,11 @@ extern "C" int gpfvm_server_submit(gpfvm_server* s, const gpfvm_desc* d, int64_t
   if (!s || !d || !ticket) return GPFVM_ERR_INVALID_ARG;
   const int v = validate(d);
   if (v != GPFVM_OK) return v;
+  if (d->n_outputs > 0) {  // (systems: one at a time, FP64)
+    for (int k = 0; k < d->n_terms; ++k)
+      if (d->term_eq[k] != 0 || d->term_out[k] != 0) return GPFVM_ERR_INVALID_ARG;
+    if (d->n_outputs > 1) return GPFVM_ERR_INVALID_ARG;
+  }
   auto R = std::make_unique<Request>();
   R->desc = *d;
   R->store.reserve(4 + 3 * GPFVM_MAX_SETS + 8);

@@ -145,7 +145,8 @@ void launch_factors(const FactorJob* d_jobs, int n_jobs, i64 max_entries, cudaSt
 }
 
 // Dense IC/BC Gram: entry (o1, o2) of G_BB = sigma^2 prod_i D_i^{s s'}[l_i, l'_i]
-// (+ noise variance on the diagonal), sets enumerated by their offsets.
+// (+ noise variance on the diagonal), sets enumerated by their offsets; zero
+// between sets observing different outputs of a system (Eq. multioutput-cov-def).
 __global__ void gbb_kernel(GbbParams P, double* __restrict__ G) {
   const i64 M = P.M;
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < M * M; e += (i64)gridDim.x * blockDim.x) {
@@ -154,7 +155,7 @@ __global__ void gbb_kernel(GbbParams P, double* __restrict__ G) {
     while (s1 + 1 < P.n_sets && o1 >= P.off[s1 + 1]) ++s1;
     while (s2 + 1 < P.n_sets && o2 >= P.off[s2 + 1]) ++s2;
     int l1 = o1 - P.off[s1], l2 = o2 - P.off[s2];
-    double v = P.outputscale;
+    double v = P.comp[s1] == P.comp[s2] ? P.outputscale : 0.0;  // outputs are a priori uncorrelated
     int i0 = 0;  // axis-0 index of point o1
     for (int ax = P.ndim - 1; ax >= 0; --ax) {
       const int n1 = P.dims[s1][ax], n2 = P.dims[s2][ax];

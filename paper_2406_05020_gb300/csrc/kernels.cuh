@@ -26,6 +26,7 @@ struct GbbParams {
   int dims[GPFVM_MAX_SETS][GPFVM_MAX_DIM];
   double noise[GPFVM_MAX_SETS];
   double noise2[GPFVM_MAX_SETS];  // noise of the points with axis-0 index >= 1 (stacked sets)
+  int comp[GPFVM_MAX_SETS];       // output component of each set (different: uncorrelated)
   double outputscale;
   const double* fac[GPFVM_MAX_SETS][GPFVM_MAX_SETS][GPFVM_MAX_DIM];
 };

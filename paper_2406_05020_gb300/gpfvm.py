@@ -48,7 +48,9 @@ class Desc(C.Structure):
                 ("rhs", C.POINTER(C.c_double)), ("jitter", C.c_double), ("n_sets", C.c_int),
                 ("sets", PointSet * MAX_SETS), ("n_pred", C.c_int * MAX_DIM),
                 ("pred", C.POINTER(C.c_double) * MAX_DIM), ("observe", C.c_int),
-                ("coef_field", C.POINTER(C.c_double) * MAX_TERMS), ("fp64_products", C.c_int)]
+                ("coef_field", C.POINTER(C.c_double) * MAX_TERMS), ("fp64_products", C.c_int),
+                ("n_outputs", C.c_int), ("term_eq", C.c_int * MAX_TERMS), ("term_out", C.c_int * MAX_TERMS),
+                ("set_out", C.c_int * MAX_SETS)]
 
 
 class SolveOpts(C.Structure):
@@ -208,6 +210,16 @@ def make_desc(prob):
             d.sets[s].coords[i] = arr(ps.coords[i])
         d.sets[s].values = arr(np.ravel(ps.values))
         d.sets[s].noise_var = float(ps.noise_var)
+    n_out = int(getattr(prob, "n_out", 1))
+    term_eq = getattr(prob, "term_eq", None)
+    if n_out > 1 or (term_eq is not None and max(term_eq) > 0):  # a system (Sec. 3.3)
+        d.n_outputs = n_out
+        term_out = getattr(prob, "term_out", None)
+        for k in range(len(prob.terms)):
+            d.term_eq[k] = int(term_eq[k]) if term_eq is not None else 0
+            d.term_out[k] = int(term_out[k]) if term_out is not None else 0
+        for s, ps in enumerate(prob.sets):
+            d.set_out[s] = int(getattr(ps, "out", 0))
     return d, keep
 
 
