@@ -53,7 +53,7 @@ extern "C" {
 #endif
 
 #define GPFVM_MAX_DIM 3
-#define GPFVM_MAX_TERMS 8
+#define GPFVM_MAX_TERMS 16
 #define GPFVM_MAX_SETS 8
 #define GPFVM_MAX_OUTPUTS 4
 

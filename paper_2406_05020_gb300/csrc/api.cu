@@ -218,7 +218,7 @@ struct gpfvm_problem {
   // variable coefficients: term a's coefficient is coef[a] * field[fclass[a]] per cell (fclass -1:
   // constant); the distinct fields live in d_field / f_field (nfield x N)
   int nfield = 0;
-  int fclass[GPFVM_MAX_TERMS] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int fclass[GPFVM_MAX_TERMS];  // set to -1 for every term at creation
   std::vector<double> fields;
   double* d_field = nullptr;
   float* f_field = nullptr;
@@ -3608,6 +3608,7 @@ int gpfvm_create(const gpfvm_desc* D, int max_iter, gpfvm_problem** out) {
   p->colloc = D->observe == 1;
   p->oz_on = D->fp64_products == 0;
   p->nterms = D->n_terms;
+  for (int k = 0; k < GPFVM_MAX_TERMS; ++k) p->fclass[k] = -1;
   {
     std::vector<const double*> seen;
     for (int k = 0; k < D->n_terms; ++k) {

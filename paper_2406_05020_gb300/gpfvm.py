@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgpfvm.so")
 
-MAX_DIM, MAX_TERMS, MAX_SETS = 3, 8, 8
+MAX_DIM, MAX_TERMS, MAX_SETS = 3, 16, 8
 OK, NOT_CONVERGED = 0, 1
 FP64, MIXED_FP32, MIXED_TF32X3, MIXED_BF16X3, MIXED_BF16 = 0, 1, 2, 3, 4
 

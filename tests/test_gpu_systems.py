@@ -32,6 +32,9 @@ PROBS = {
     "wave1d_system": lambda: W.wave_1d_system(6, 7, pred=(5, 6)),
     "wave1d_system_colloc": lambda: W.collocation(W.wave_1d_system(6, 7, pred=(5, 6))),
     "swe2d": lambda: W.shallow_water_2d(4, 5, 6, f=0.0, k=0.0, n_ic=(4, 5), n_bc=(2, 3), pred=(3, 4, 3)),
+    # with Coriolis and drag: 11 terms in 3 equations (App. C.4's system at constant depth)
+    "swe2d_coriolis_drag": lambda: W.shallow_water_2d(4, 5, 6, f=0.5, k=0.1, n_ic=(4, 5), n_bc=(2, 3),
+                                                      pred=(3, 4, 3)),
     "swe2d_ragged": lambda: W.shallow_water_2d(3, 6, 4, H=0.7, g=1.3, f=0.0, k=0.0, n_ic=(5, 3), n_bc=(2, 2),
                                                pred=(2, 3, 4), ell=(0.5, 0.35, 0.3)),
     # one output observed by two equations (an overdetermined pair on u)
