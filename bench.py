@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpfvm", choices=["gpfvm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the measurements of targeted actions, coefficient fields, systems, multigrid, "
+                         "collocation")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--batch", type=int, default=256, help="problems of the uneven heat batch (0: skip)")
     ap.add_argument("--batch-fp64", type=int, default=16, help="problems of the batch also solved in FP64")
@@ -733,6 +736,7 @@ def run_gpfvm(args):
         batch = bench_batch(gpfvm, torch, args.batch, args.batch_fp64)
     if rank == 0 and args.serve > 0:
         serving = bench_serving(gpfvm, torch, args.serve, args.slots)
+    rows_f = bench_next_rows(gpfvm, torch) if rank == 0 and not args.no_next_rows else None
 
     cpu = c1 = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -766,6 +770,7 @@ def run_gpfvm(args):
                                  if any(paths2[k].get("meets_1e-6") for k in paths2 if k != "fp64") else None},
             "batch": batch,
             "serving": serving,
+            "next_rows": rows_f,
             "clocks": clk,
             "fp64_gemm_peak_tflops_measured": fp64_peak,
             "cpu_baseline": cpu,
@@ -775,6 +780,84 @@ def run_gpfvm(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_next_rows(gpfvm, torch):
+    """The rows beyond the hot path, each as FP64 full steps (assemble, solve,
+    query) on one GB300: targeted actions after the converged heat 64^3 solve,
+    a coefficient field (heat 64^3 with nu(x, y)), a system in three outputs
+    (linearised shallow water 32^3 with Coriolis and drag), the multigrid warm
+    start (heat 64^3 on 8^3 coarse cells) and collocation (heat 64^3, 300 CG
+    iterations).  One untimed warm-up step each, then 2 timed steps (CUDA events)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.Stream(device=dev)
+    sp = st.cuda_stream
+
+    def steps(prob, opts, nsteps=2):
+        # (a multigrid start keeps its coarse actions in the direction stores too)
+        pb = gpfvm.Problem(prob, max_iter=opts.max_iter + (4096 if opts.coarse > 1 else 0))
+        mean = torch.empty(pb.P, dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+        ms, info = [], None
+        for k in range(1 + nsteps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            pb.assemble(stream=sp)
+            code, info = pb.solve(opts, stream=sp)
+            pb.query(mean, var if opts.want_var else None, stream=sp)
+            e1.record(st)
+            st.synchronize()
+            if k > 0:
+                ms.append(e0.elapsed_time(e1))
+        d = {"solves_per_s": 1e3 * nsteps / sum(ms), "ms_per_step": sum(ms) / nsteps, "status": int(code),
+             "iterations": int(info.iterations), "true_rel_residual": float(info.true_rel_residual),
+             "N": pb.N, "M": pb.M, "P": pb.P}
+        return pb, d, mean, var
+
+    out = {}
+    o10 = dict(max_iter=MAX_ITER, rtol=RTOL, precision=gpfvm.FP64, reorth=True, want_var=True)
+    # f1: 16 targeted actions (Dirichlet weights over 32 grid points) continuing the converged state
+    pb, d, mean, var = steps(c2_workload(0), gpfvm.solve_opts(**o10))
+    rng = np.random.default_rng(5)
+    pts = rng.choice(pb.P, 32, replace=False)
+    betas = np.zeros((16, pb.P))
+    betas[:, pts] = rng.dirichlet(np.ones(32), size=16)
+    v0 = var.cpu().numpy()[pts]
+    bt = torch.as_tensor(betas, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    pb.target(bt, stream=sp)
+    pb.query(mean, var, stream=sp)
+    e1.record(st)
+    st.synchronize()
+    out["f1_targeted_heat64"] = {"solve": d, "actions": 16, "ms_for_actions_and_query": e0.elapsed_time(e1),
+                                 "var_ratio_at_targets_mean": float(np.mean(var.cpu().numpy()[pts] / v0))}
+    pb.close()
+    # f2: coefficient field; system in three outputs
+    pb, d, _, _ = steps(W.heat_2d_varcoef(64, 64, 64), gpfvm.solve_opts(**o10))
+    out["f2_varcoef_heat64"] = d
+    pb.close()
+    swe = W.shallow_water_2d(32, 32, 32, n_ic=(16, 16), n_bc=(8, 8), pred=(16, 16, 16))
+    pb, d, _, _ = steps(swe, gpfvm.solve_opts(max_iter=3000, rtol=1e-8, precision=gpfvm.FP64, reorth=True,
+                                              want_var=True))
+    d["workload"] = "linearised shallow water (h, u, v), 32^3 cells, H = g = 1, f = 0.5, k = 0.1, rtol 1e-8"
+    out["f2_system_swe32"] = d
+    pb.close()
+    # f3: multigrid start on 8^3 coarse cells
+    pb, d, _, _ = steps(c2_workload(0), gpfvm.solve_opts(coarse=8, **o10))
+    out["f3_multigrid_heat64"] = d
+    pb.close()
+    # f4: collocation at the cell centres, a fixed 300-iteration computation-aware posterior
+    # (collocating the second-order operator needs the fourth kernel derivative and leaves CG far
+    # from 1e-10: measured relative residuals 1e-5 at 32^3 and 2.6e-4 at 64^3 after 3000
+    # reorthogonalised iterations)
+    pb, d, _, _ = steps(W.collocation(c2_workload(0)),
+                        gpfvm.solve_opts(max_iter=300, rtol=0.0, precision=gpfvm.FP64, reorth=True, want_var=True))
+    d["cg"] = "300 iterations (fixed)"
+    out["f4_collocation_heat64"] = d
+    pb.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def profile_workload(args, seed):
