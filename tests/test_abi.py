@@ -68,3 +68,38 @@ def test_non_increasing_edges_rejected(lib):
     p.edges[1] = np.array([0.0, 0.5, 0.5, 0.7, 1.0])
     d, keep = gpfvm.make_desc(p)
     assert _create(d) == -1
+
+
+def test_system_descriptor_fields(lib):
+    """A system (Sec. 3.3) is passed with the equation and output of every term
+    and the output of every set; a one-output problem leaves them unread."""
+    from paper_2406_05020_gb300 import gpfvm
+    d, keep = gpfvm.make_desc(W.shallow_water_2d(3, 4, 4, n_ic=(3, 3), n_bc=(2, 2), pred=(2, 2, 2)))
+    assert d.n_outputs == 3 and d.n_terms == 11
+    assert list(d.term_eq)[:11] == [0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 2]
+    assert list(d.term_out)[:11] == [0, 1, 2, 1, 2, 0, 1, 2, 1, 0, 2]
+    assert list(d.set_out)[:5] == [0, 1, 2, 1, 2]
+    d1, keep1 = gpfvm.make_desc(W.heat_2d(4, 4, 4, n_ic=(3, 3), n_bc=(2, 2), pred=(2, 2, 2)))
+    assert d1.n_outputs == 0
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda d: setattr(d, "n_outputs", 5),                    # above GPFVM_MAX_OUTPUTS
+    lambda d: d.term_out.__setitem__(0, 3),                  # no such output
+    lambda d: d.term_eq.__setitem__(3, 5),                   # a gap in the equation numbers
+    lambda d: d.set_out.__setitem__(1, -1),                  # no such output for a set
+])
+def test_invalid_system_descriptors_rejected(lib, mutate):
+    from paper_2406_05020_gb300 import gpfvm
+    d, keep = gpfvm.make_desc(W.shallow_water_2d(3, 4, 4, n_ic=(3, 3), n_bc=(2, 2), pred=(2, 2, 2)))
+    mutate(d)
+    assert _create(d) == -1
+
+
+def test_system_with_coefficient_field_rejected(lib):
+    """Systems take constant coefficients: a coefficient field is refused."""
+    from paper_2406_05020_gb300 import gpfvm
+    p = W.wave_1d_system(3, 4, pred=(2, 2))
+    p.fields = [None, np.ones(p.N // 2), None, None]
+    d, keep = gpfvm.make_desc(p)
+    assert _create(d) == -1
