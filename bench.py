@@ -236,7 +236,7 @@ class OracleSampler:
       the Cholesky-stage variance of kron_posterior on 1/sub of the grid
         points (same geometry, every sub-th y coordinate), scaled by sub."""
 
-    def __init__(self, n_fit=10, sub=64):
+    def __init__(self, n_fit=12, sub=64):
         import oracle as O
         self.O = O
         self.n_fit, self.sub = n_fit, sub
@@ -261,8 +261,17 @@ class OracleSampler:
     def fit(self):
         d = self._iters(self.n_fit)
         k = np.arange(d.size)
-        self.b, self.a = (np.polyfit(k[1:], d[1:], 1) if d.size > 2 else (0.0, float(d.mean())))
-        self.b = max(float(self.b), 0.0)
+        # Theil-Sen (median of the pairwise slopes, then the median intercept):
+        # the reorthogonalisation's few ms per stored direction sit under the
+        # timing noise of ~2 s iterations, which a least-squares slope does not
+        # resist (the first iteration, with first-use set-up, is left out)
+        kk, dd = k[1:], d[1:]
+        if dd.size > 2:
+            sl = [(dd[j] - dd[i]) / (kk[j] - kk[i]) for i in range(dd.size) for j in range(i + 1, dd.size)]
+            self.b = max(float(np.median(sl)), 0.0)
+            self.a = float(np.median(dd - self.b * kk))
+        else:
+            self.b, self.a = 0.0, float(d.mean())
         t0 = time.perf_counter()
         self.O.kron_posterior(self.sub_prob, max_iter=0, K=self.K_sub)
         self.t_var = (time.perf_counter() - t0) * (self.prob.P / self.P_sub)
