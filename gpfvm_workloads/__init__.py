@@ -384,19 +384,21 @@ def wave_1d_system(nt: int = 8, nx: int = 8, pred=(9, 9), ell=(0.5, 0.3), jitter
 
 def shallow_water_2d(nt: int = 8, nx: int = 8, ny: int = 8, H: float = 1.0, g: float = 1.0, f: float = 0.5,
                      k: float = 0.1, n_ic=(8, 8), n_bc=(4, 4), pred=(4, 5, 5), ell=(0.4, 0.3, 0.3),
-                     width: float = 0.15, jitter: float = 1e-8, seed: int = 0) -> Problem:
+                     width: float = 0.15, jitter: float = 1e-8, seed: int = 0, standing: bool = False) -> Problem:
     """Linearised 2D shallow-water equations with constant depth H (App. C.4's
     system without its variable bathymetry), outputs (h, u, v):
         h_t + H (u_x + v_y) = 0,   u_t - f v + g h_x + k u = 0,   v_t + f u + g h_y + k v = 0
     on [0,1]^3.  IC: a Gaussian bump of the given width (centre U(0.35,0.65)^2) in h, zero
     velocities; walls: u = 0 at x = 0, 1 and v = 0 at y = 0, 1 on n_bc (time x tangential)
-    midpoint grids."""
+    midpoint grids.  With standing=True the IC is h = cos(pi x) instead: for f = k = 0 the
+    solution is the standing wave h = cos(pi x) cos(w t), u = sqrt(g/H) sin(pi x) sin(w t),
+    v = 0 with w = pi sqrt(g H)."""
     rng = np.random.default_rng(seed)
     cx, cy = rng.uniform(0.35, 0.65, 2)
     edges = [uniform_edges(0, 1, nt), uniform_edges(0, 1, nx), uniform_edges(0, 1, ny)]
     xs, ys = np.linspace(0, 1, n_ic[0]), np.linspace(0, 1, n_ic[1])
     X, Y = np.meshgrid(xs, ys, indexing="ij")
-    h0 = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width)).ravel()
+    h0 = (np.cos(np.pi * X) if standing else np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width))).ravel()
     t0 = np.array([0.0])
     ic_h = PointSet((0, 0, 0), [t0, xs, ys], h0, jitter, "ic_h", out=0)
     ic_u = PointSet((0, 0, 0), [t0, xs, ys], np.zeros(h0.size), jitter, "ic_u", out=1)

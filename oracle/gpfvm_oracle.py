@@ -735,6 +735,7 @@ PINS = {
                                       "repeated targeted actions reach the exact (Cholesky) variance there",
     "multi-output (pde_blocks / pred_blocks / block_cov outs)": "two decoupled equations == the pair of one-output "
                                                                 "posteriors; an unobserved output keeps its prior; "
-                                                                "the first-order 1D wave system converges to its "
-                                                                "analytic solution (and not with swapped components)",
+                                                                "the first-order 1D wave system and the linearised "
+                                                                "shallow-water standing wave converge to their analytic "
+                                                                "solutions (and not with a term on the wrong component)",
 }

@@ -87,3 +87,33 @@ def test_multi_output_blocks_zero_across_components():
     np.testing.assert_array_equal(K, K1)
     eq0, eq1 = O.pde_blocks(p)
     assert eq0.outs == [0, 1] and eq1.outs == [1, 0]
+
+
+@pytest.mark.parametrize("swap", [False, True])
+def test_shallow_water_standing_wave(swap):
+    """Three outputs, three equations (linearised shallow water, f = k = 0):
+    the posterior approaches h = cos(pi x) cos(w t), u = sqrt(g/H) sin(pi x)
+    sin(w t), v = 0 (w = pi sqrt(g H)) under refinement; with the pressure
+    term g h_x made to act on v instead of h it does not."""
+    H, g = 1.0, 1.0
+    errs = []
+    for n in (4, 6, 8):
+        p = W.shallow_water_2d(n, n, n, H=H, g=g, f=0.0, k=0.0, n_ic=(n + 1, n + 1), n_bc=(n, n), pred=(5, 5, 3),
+                               ell=(0.4, 0.3, 0.5), jitter=1e-10, standing=True)
+        if swap:
+            outs = list(p.term_out)
+            k = next(i for i, (a, c) in enumerate(p.terms) if a == (0, 1, 0) and p.term_eq[i] == 1)
+            assert outs[k] == 0  # g h_x in the u equation
+            outs[k] = 2
+            p = replace(p, term_out=outs)
+        m, _ = O.dense_posterior(p)
+        T, X, Y = np.meshgrid(*p.pred, indexing="ij")
+        w = np.pi * np.sqrt(g * H)
+        exact = np.concatenate([(np.cos(np.pi * X) * np.cos(w * T)).ravel(),
+                                (np.sqrt(g / H) * np.sin(np.pi * X) * np.sin(w * T)).ravel(), np.zeros(T.size)])
+        errs.append(np.abs(m - exact).max())
+    if swap:
+        assert errs[-1] > 0.05
+    else:
+        assert errs[0] > errs[1] > errs[2]
+        assert errs[2] < 1e-2
