@@ -337,34 +337,46 @@ class KronIBVP:
     rectangular 1D factors; G_BB is assembled densely entrywise.  A
     piecewise-constant variable coefficient c_a (one value per cell) turns
     each Kronecker term into its Hadamard product with the rank-one matrix
-    c_a c_b^T (App. C.4), applied as diag(c_a) (x)A diag(c_b)."""
+    c_a c_b^T (App. C.4), applied as diag(c_a) (x)A diag(c_b).  For a system
+    (Sec. 3.3) G_PP has a block per pair of equations, holding the pairs of
+    their terms that act on one output, and every set or prediction block meets
+    only the terms on its own output."""
 
     def __init__(self, prob):
-        if getattr(prob, "n_out", 1) != 1 or getattr(prob, "term_eq", None) is not None:
-            raise NotImplementedError("KronIBVP: one output; use dense_posterior for systems")
         self.prob = prob
         self.ell = prob.lengthscale
         self.s2 = prob.outputscale
-        self.pde = pde_block(prob)
+        eqs = pde_blocks(prob)
+        self.neq = len(eqs)
+        self.nout = int(getattr(prob, "n_out", 1))
+        self.pde = eqs[0] if self.neq == 1 else None  # the one-equation block
         self.sets = [point_block(s) for s in prob.sets]
-        self.pred = pred_block(prob)
+        self.pred = pred_blocks(prob)[0]  # the grid (every output is evaluated on it)
         self.shape = prob.n_cells
+        self.Nc = int(np.prod(self.shape))
+        self.Pp = self.pred.size
+        self.P = self.Pp * self.nout
         d = prob.ndim
-        # PDE x PDE pairs (coefficients kept apart: scalars or per-cell arrays)
+        # PDE x PDE: (equation e, equation e2, coefficients, factors) for every pair
+        # of terms acting on one output (Sec. 3.3: outputs are a priori uncorrelated)
         self.pp = []
-        for c1, F in self.pde.terms:
-            for c2, G in self.pde.terms:
-                self.pp.append(((c1, c2), [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)]))
-        # PDE x set s (N_i x n_{s,i} factors per term)
+        for e, X in enumerate(eqs):
+            for e2, Y in enumerate(eqs):
+                for (c1, F), o1 in zip(X.terms, X.outs):
+                    for (c2, G), o2 in zip(Y.terms, Y.outs):
+                        if o1 == o2:
+                            self.pp.append((e, e2, (c1, c2), [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)]))
+        # PDE x set s (N_i x n_{s,i} factors per term of an equation on the set's output)
         self.pb = []
         for sb in self.sets:
             (_, G), = sb.terms
-            self.pb.append([(c, [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)])
-                            for c, F in self.pde.terms])
-        # PDE x prediction grid and set x prediction grid
+            self.pb.append([(e, c, [cov_1d(F[i], G[i], self.ell[i]) for i in range(d)])
+                            for e, X in enumerate(eqs) for (c, F), o in zip(X.terms, X.outs) if o == sb.outs[0]])
+        # PDE x prediction grid of output j, and set x prediction grid (of the set's output)
         (_, Pf), = self.pred.terms
-        self.pp_pred = [(c, [cov_1d(F[i], Pf[i], self.ell[i]) for i in range(d)])
-                        for c, F in self.pde.terms]
+        self.pp_pred = [[(e, c, [cov_1d(F[i], Pf[i], self.ell[i]) for i in range(d)])
+                         for e, X in enumerate(eqs) for (c, F), o in zip(X.terms, X.outs) if o == j]
+                        for j in range(self.nout)]
         self.b_pred = []
         for sb in self.sets:
             (_, G), = sb.terms
@@ -385,35 +397,40 @@ class KronIBVP:
         self.offsets = np.cumsum([0] + [s.size for s in self.sets])
 
     # --- blocks -------------------------------------------------------------
+    # Vectors over the PDE observations hold the equations one after another,
+    # vectors over the prediction grid the outputs one after another.
     def _cells(self, c):
         """A term coefficient as a scalar or a tensor over the cells."""
         return c.reshape(self.shape) if isinstance(c, np.ndarray) else c
 
+    def _eq(self, v):
+        return v.reshape((self.neq,) + tuple(self.shape))
+
     def Gpp(self, v: np.ndarray) -> np.ndarray:
-        V = v.reshape(self.shape)
-        out = np.zeros(self.shape)
-        for (c1, c2), mats in self.pp:
-            out += self._cells(c1) * mode_apply(mats, self._cells(c2) * V)
+        V = self._eq(v)
+        out = np.zeros_like(V)
+        for e, e2, (c1, c2), mats in self.pp:
+            out[e] += self._cells(c1) * mode_apply(mats, self._cells(c2) * V[e2])
         return self.s2 * out.ravel() + self.prob.jitter * v
 
     def Gbp(self, v: np.ndarray) -> np.ndarray:
         """G_BP v: PDE volumes -> point sets."""
-        V = v.reshape(self.shape)
+        V = self._eq(v)
         parts = []
         for sb, terms in zip(self.sets, self.pb):
             acc = np.zeros(sb.shape)
-            for c, mats in terms:
-                acc += mode_apply([A.T for A in mats], self._cells(c) * V)
+            for e, c, mats in terms:
+                acc += mode_apply([A.T for A in mats], self._cells(c) * V[e])
             parts.append(self.s2 * acc.ravel())
         return np.concatenate(parts) if parts else np.zeros(0)
 
     def Gpb(self, w: np.ndarray) -> np.ndarray:
         """G_PB w: point sets -> PDE volumes."""
-        out = np.zeros(self.shape)
+        out = np.zeros((self.neq,) + tuple(self.shape))
         for k, (sb, terms) in enumerate(zip(self.sets, self.pb)):
             W = w[self.offsets[k]:self.offsets[k + 1]].reshape(sb.shape)
-            for c, mats in terms:
-                out += self._cells(c) * mode_apply(mats, W)
+            for e, c, mats in terms:
+                out[e] += self._cells(c) * mode_apply(mats, W)
         return self.s2 * out.ravel()
 
     def Hsolve(self, w: np.ndarray) -> np.ndarray:
@@ -433,34 +450,39 @@ class KronIBVP:
         return self.yP - self.Gpb(self.Hsolve(self.yB))
 
     # --- prediction-side products --------------------------------------------
+    def _out(self, b):
+        return b.reshape((self.nout,) + tuple(self.pred.shape))
+
     def KPx(self, x: np.ndarray) -> np.ndarray:
-        """L_PDE k(X*)^T x (volumes -> prediction grid)."""
-        X = x.reshape(self.shape)
-        out = np.zeros(self.pred.shape)
-        for c, mats in self.pp_pred:
-            out += mode_apply([A.T for A in mats], self._cells(c) * X)
+        """L_PDE k(X*)^T x (volumes -> prediction grid of every output)."""
+        X = self._eq(x)
+        out = np.zeros((self.nout,) + tuple(self.pred.shape))
+        for j, terms in enumerate(self.pp_pred):
+            for e, c, mats in terms:
+                out[j] += mode_apply([A.T for A in mats], self._cells(c) * X[e])
         return self.s2 * out.ravel()
 
     def KBx(self, w: np.ndarray) -> np.ndarray:
-        """L_IC,BC k(X*)^T w (point sets -> prediction grid)."""
-        out = np.zeros(self.pred.shape)
+        """L_IC,BC k(X*)^T w (point sets -> prediction grid of their outputs)."""
+        out = np.zeros((self.nout,) + tuple(self.pred.shape))
         for k, (sb, mats) in enumerate(zip(self.sets, self.b_pred)):
             W = w[self.offsets[k]:self.offsets[k + 1]].reshape(sb.shape)
-            out += mode_apply([A.T for A in mats], W)
+            out[sb.outs[0]] += mode_apply([A.T for A in mats], W)
         return self.s2 * out.ravel()
 
     def KPxT(self, beta: np.ndarray) -> np.ndarray:
         """L_PDE k(X*) beta (prediction grid -> volumes): the adjoint of KPx."""
-        B = beta.reshape(self.pred.shape)
-        out = np.zeros(self.shape)
-        for c, mats in self.pp_pred:
-            out += self._cells(c) * mode_apply(mats, B)
+        B = self._out(beta)
+        out = np.zeros((self.neq,) + tuple(self.shape))
+        for j, terms in enumerate(self.pp_pred):
+            for e, c, mats in terms:
+                out[e] += self._cells(c) * mode_apply(mats, B[j])
         return self.s2 * out.ravel()
 
     def KBxT(self, beta: np.ndarray) -> np.ndarray:
         """L_IC,BC k(X*) beta (prediction grid -> point sets): the adjoint of KBx."""
-        B = beta.reshape(self.pred.shape)
-        parts = [self.s2 * mode_apply(mats, B).ravel() for mats in self.b_pred]
+        B = self._out(beta)
+        parts = [self.s2 * mode_apply(mats, B[sb.outs[0]]).ravel() for sb, mats in zip(self.sets, self.b_pred)]
         return np.concatenate(parts) if parts else np.zeros(0)
 
     def Lhat_k(self, beta: np.ndarray) -> np.ndarray:
@@ -470,10 +492,11 @@ class KronIBVP:
         return self.KPxT(beta) - self.Gpb(self.Hsolve(self.KBxT(beta)))
 
     def KB_dense(self) -> np.ndarray:
-        """L_IC,BC k(X*) as a dense M x P matrix (entrywise)."""
+        """L_IC,BC k(X*) as a dense M x P matrix (entrywise), outputs one after another."""
         if not self.sets:
-            return np.zeros((0, self.pred.size))
-        return np.vstack([block_cov(X, self.pred, self.ell, self.s2) for X in self.sets])
+            return np.zeros((0, self.P))
+        preds = pred_blocks(self.prob)
+        return np.vstack([np.hstack([block_cov(X, Pj, self.ell, self.s2) for Pj in preds]) for X in self.sets])
 
 
 def cg_itergp(K: KronIBVP, max_iter: int, rtol: float = 0.0, want_var: bool = True,
@@ -496,7 +519,7 @@ def cg_itergp(K: KronIBVP, max_iter: int, rtol: float = 0.0, want_var: bool = Tr
     p = r.copy()
     rr = float(r @ r)
     bnorm = math.sqrt(rr)
-    down = np.zeros(K.pred.size)
+    down = np.zeros(K.P)
     it = 0
     hist = [1.0]
     S, Q, etas = [], [], []
@@ -657,7 +680,7 @@ def multigrid_itergp(K: KronIBVP, factor: int, max_iter: int, rtol: float = 0.0,
     Lc = sla.cholesky(0.5 * (Ac + Ac.T), lower=True)
     x = W @ sla.cho_solve((Lc, True), W.T @ b)
     r = b - K.Ghat(x)
-    down = np.zeros(K.pred.size)
+    down = np.zeros(K.P)
     if want_var:
         U = np.column_stack([K.KPx(W[:, c]) - K.KBx(K.Hsolve(K.Gbp(W[:, c]))) for c in range(W.shape[1])])
         Z = sla.solve_triangular(Lc, U.T, lower=True)
@@ -733,6 +756,8 @@ PINS = {
     "targeted_itergp/posterior_from": "equals itergp_actions on [CG directions | targeted actions]; one action "
                                       "on one point is the Cauchy-Schwarz-optimal single-action reduction; "
                                       "repeated targeted actions reach the exact (Cholesky) variance there",
+    "KronIBVP for systems": "every block product equals the dense entrywise blocks (block_cov) of the same "
+                            "system; the converged kron_posterior equals dense_posterior",
     "multi-output (pde_blocks / pred_blocks / block_cov outs)": "two decoupled equations == the pair of one-output "
                                                                 "posteriors; an unobserved output keeps its prior; "
                                                                 "the first-order 1D wave system and the linearised "

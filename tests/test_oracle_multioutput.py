@@ -117,3 +117,38 @@ def test_shallow_water_standing_wave(swap):
     else:
         assert errs[0] > errs[1] > errs[2]
         assert errs[2] < 1e-2
+
+
+@pytest.mark.parametrize("make", [lambda: W.wave_1d_system(5, 6, pred=(4, 5)),
+                                  lambda: W.shallow_water_2d(3, 4, 5, n_ic=(3, 4), n_bc=(2, 2), pred=(2, 3, 3)),
+                                  lambda: W.collocation(W.wave_1d_system(4, 5, pred=(3, 4)))])
+def test_kron_operator_of_systems_equals_dense_blocks(make):
+    p = make()
+    K = O.KronIBVP(p)
+    cov = lambda X, Y: O.block_cov(X, Y, p.lengthscale, p.outputscale)  # noqa: E731
+    eqs = O.pde_blocks(p)
+    sets = [O.point_block(s) for s in p.sets]
+    preds = O.pred_blocks(p)
+    Gpp = np.vstack([np.hstack([cov(X, Y) for Y in eqs]) for X in eqs])
+    Gbp = np.vstack([np.hstack([cov(S, Y) for Y in eqs]) for S in sets])
+    Kp = np.vstack([np.hstack([cov(X, Q) for Q in preds]) for X in eqs])
+    Kb = np.vstack([np.hstack([cov(S, Q) for Q in preds]) for S in sets])
+    rng = np.random.default_rng(3)
+    v, w, b = rng.normal(size=p.N), rng.normal(size=p.M), rng.normal(size=p.P)
+    close = lambda a, ref: np.testing.assert_allclose(a, ref, rtol=0, atol=1e-12 * np.abs(ref).max())  # noqa: E731
+    close(K.Gpp(v), Gpp @ v + p.jitter * v)
+    close(K.Gbp(v), Gbp @ v)
+    close(K.Gpb(w), Gbp.T @ w)
+    close(K.KPx(v), Kp.T @ v)
+    close(K.KBx(w), Kb.T @ w)
+    close(K.KPxT(b), Kp @ b)
+    close(K.KBxT(b), Kb @ b)
+    close(K.KB_dense(), Kb)
+
+
+def test_kron_posterior_of_a_system_equals_the_dense_posterior():
+    p = W.shallow_water_2d(3, 4, 5, n_ic=(3, 4), n_bc=(2, 2), pred=(2, 3, 3))
+    m, v = O.dense_posterior(p)
+    r = O.kron_posterior(p, rtol=1e-13)
+    assert np.linalg.norm(r["mean"] - m) / np.linalg.norm(m) < 1e-9
+    assert np.all(r["var"] >= v - 1e-9)
