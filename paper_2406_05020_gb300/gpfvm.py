@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgpfvm.so")
 
-MAX_DIM, MAX_TERMS, MAX_SETS = 3, 16, 8
+MAX_DIM, MAX_TERMS, MAX_SETS, MAX_OUTPUTS = 3, 16, 8, 4
 OK, NOT_CONVERGED = 0, 1
 FP64, MIXED_FP32, MIXED_TF32X3, MIXED_BF16X3, MIXED_BF16 = 0, 1, 2, 3, 4
 
@@ -212,9 +212,14 @@ def make_desc(prob):
         d.sets[s].noise_var = float(ps.noise_var)
     n_out = int(getattr(prob, "n_out", 1))
     term_eq = getattr(prob, "term_eq", None)
+    term_out = getattr(prob, "term_out", None)
+    if n_out < 1 or n_out > MAX_OUTPUTS:
+        raise ValueError(f"n_out must be 1..{MAX_OUTPUTS}")
+    for name, lst in (("term_eq", term_eq), ("term_out", term_out)):
+        if lst is not None and len(lst) != len(prob.terms):
+            raise ValueError(f"{name}: one entry per operator term")
     if n_out > 1 or (term_eq is not None and max(term_eq) > 0):  # a system (Sec. 3.3)
         d.n_outputs = n_out
-        term_out = getattr(prob, "term_out", None)
         for k in range(len(prob.terms)):
             d.term_eq[k] = int(term_eq[k]) if term_eq is not None else 0
             d.term_out[k] = int(term_out[k]) if term_out is not None else 0

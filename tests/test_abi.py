@@ -103,3 +103,15 @@ def test_system_with_coefficient_field_rejected(lib):
     p.fields = [None, np.ones(p.N // 2), None, None]
     d, keep = gpfvm.make_desc(p)
     assert _create(d) == -1
+
+
+def test_binding_checks_system_lists():
+    """The binding refuses per-term lists of the wrong length and too many outputs."""
+    from dataclasses import replace
+
+    from paper_2406_05020_gb300 import gpfvm
+    p = W.wave_1d_system(3, 4, pred=(2, 2))
+    with pytest.raises(ValueError):
+        gpfvm.make_desc(replace(p, term_out=[0, 1, 1]))
+    with pytest.raises(ValueError):
+        gpfvm.make_desc(replace(p, n_out=5))
