@@ -745,7 +745,14 @@ def run_gpfvm(args):
         batch = bench_batch(gpfvm, torch, args.batch, args.batch_fp64)
     if rank == 0 and args.serve > 0:
         serving = bench_serving(gpfvm, torch, args.serve, args.slots)
-    rows_f = bench_next_rows(gpfvm, torch) if rank == 0 and not args.no_next_rows else None
+    rows_f = None
+    if rank == 0 and not args.no_next_rows:
+        try:  # secondary measurements: a failure here is reported, the headline line still prints
+            rows_f = bench_next_rows(gpfvm, torch)
+        except Exception as e:  # noqa: BLE001
+            rows_f = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
 
     cpu = c1 = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
