@@ -751,8 +751,11 @@ def run_gpfvm(args):
             rows_f = bench_next_rows(gpfvm, torch)
         except Exception as e:  # noqa: BLE001
             rows_f = {"error": f"{type(e).__name__}: {e}"}
-            torch.cuda.synchronize()
-            torch.cuda.empty_cache()
+            try:
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+            except Exception:  # noqa: BLE001
+                pass
 
     cpu = c1 = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
