@@ -384,7 +384,8 @@ def wave_1d_system(nt: int = 8, nx: int = 8, pred=(9, 9), ell=(0.5, 0.3), jitter
 
 def shallow_water_2d(nt: int = 8, nx: int = 8, ny: int = 8, H: float = 1.0, g: float = 1.0, f: float = 0.5,
                      k: float = 0.1, n_ic=(8, 8), n_bc=(4, 4), pred=(4, 5, 5), ell=(0.4, 0.3, 0.3),
-                     width: float = 0.15, jitter: float = 1e-8, seed: int = 0, standing: bool = False) -> Problem:
+                     width: float = 0.15, jitter: float = 1e-8, seed: int = 0, standing: bool = False,
+                     depth: Optional[np.ndarray] = None) -> Problem:
     """Linearised 2D shallow-water equations with constant depth H (App. C.4's
     system without its variable bathymetry), outputs (h, u, v):
         h_t + H (u_x + v_y) = 0,   u_t - f v + g h_x + k u = 0,   v_t + f u + g h_y + k v = 0
@@ -392,7 +393,9 @@ def shallow_water_2d(nt: int = 8, nx: int = 8, ny: int = 8, H: float = 1.0, g: f
     velocities; walls: u = 0 at x = 0, 1 and v = 0 at y = 0, 1 on n_bc (time x tangential)
     midpoint grids.  With standing=True the IC is h = cos(pi x) instead: for f = k = 0 the
     solution is the standing wave h = cos(pi x) cos(w t), u = sqrt(g/H) sin(pi x) sin(w t),
-    v = 0 with w = pi sqrt(g H)."""
+    v = 0 with w = pi sqrt(g H).  depth: an (nx, ny) array of per-cell depths H(x, y)
+    (App. C.4's bathymetry, piecewise constant per cell and constant in time) multiplying
+    the two velocity terms of the h equation instead of the constant H."""
     rng = np.random.default_rng(seed)
     cx, cy = rng.uniform(0.35, 0.65, 2)
     edges = [uniform_edges(0, 1, nt), uniform_edges(0, 1, nx), uniform_edges(0, 1, ny)]
@@ -414,10 +417,15 @@ def shallow_water_2d(nt: int = 8, nx: int = 8, ny: int = 8, H: float = 1.0, g: f
             terms.append((alpha, float(c)))
             eq.append(e)
             out.append(o)
-    add((1, 0, 0), 1.0, 0, 0); add((0, 1, 0), H, 0, 1); add((0, 0, 1), H, 0, 2)
+    add((1, 0, 0), 1.0, 0, 0); add((0, 1, 0), 1.0 if depth is not None else H, 0, 1)
+    add((0, 0, 1), 1.0 if depth is not None else H, 0, 2)
     add((1, 0, 0), 1.0, 1, 1); add((0, 0, 0), -f, 1, 2); add((0, 1, 0), g, 1, 0); add((0, 0, 0), k, 1, 1)
     add((1, 0, 0), 1.0, 2, 2); add((0, 0, 0), f, 2, 1); add((0, 0, 1), g, 2, 0); add((0, 0, 0), k, 2, 2)
     grid = [np.linspace(0, 1, p) for p in pred]
+    fields = None
+    if depth is not None:
+        field = np.broadcast_to(np.asarray(depth, np.float64), (nt, nx, ny)).ravel().copy()
+        fields = [field if (e == 0 and o in (1, 2)) else None for e, o in zip(eq, out)]
     return Problem(edges, tuple(ell), 1.0, terms, jitter, [ic_h, ic_u, ic_v, wall_u, wall_v], grid,
                    name=f"swe2d_{nt}x{nx}x{ny}", meta={"H": H, "g": g, "f": f, "k": k, "centre": (cx, cy)},
-                   n_out=3, term_eq=eq, term_out=out)
+                   fields=fields, n_out=3, term_eq=eq, term_out=out)

@@ -152,3 +152,29 @@ def test_kron_posterior_of_a_system_equals_the_dense_posterior():
     r = O.kron_posterior(p, rtol=1e-13)
     assert np.linalg.norm(r["mean"] - m) / np.linalg.norm(m) < 1e-9
     assert np.all(r["var"] >= v - 1e-9)
+
+
+def test_system_with_a_constant_depth_field_equals_constant_depth():
+    """App. C.4's bathymetry enters the h equation as a per-cell field on its two
+    velocity terms; a field equal to H everywhere gives the constant-depth system
+    (dense and Kronecker oracles), a varying one a different posterior."""
+    kw = dict(n_ic=(3, 4), n_bc=(2, 2), pred=(2, 3, 3), H=0.8)
+    p = W.shallow_water_2d(3, 4, 5, **kw)
+    q = W.shallow_water_2d(3, 4, 5, depth=np.full((4, 5), 0.8), **kw)
+    assert sum(f is not None for f in q.fields) == 2
+    m, v = O.dense_posterior(p)
+    mq, vq = O.dense_posterior(q)
+    np.testing.assert_allclose(mq, m, rtol=0, atol=1e-12 * np.abs(m).max())
+    np.testing.assert_allclose(vq, v, rtol=0, atol=1e-12)
+    K, Kq = O.KronIBVP(p), O.KronIBVP(q)
+    x = np.random.default_rng(1).normal(size=p.N)
+    np.testing.assert_allclose(Kq.Ghat(x), K.Ghat(x), rtol=0, atol=1e-12 * np.abs(K.Ghat(x)).max())
+    X, Y = np.meshgrid(np.linspace(0, 1, 4), np.linspace(0, 1, 5), indexing="ij")
+    r = W.shallow_water_2d(3, 4, 5, depth=0.5 + 0.5 * X * Y, **kw)
+    mr, _ = O.dense_posterior(r)
+    assert np.abs(mr - m).max() > 1e-4
+    # Kronecker-with-diagonals == entrywise dense blocks for the varying field too
+    Kr = O.KronIBVP(r)
+    eqs = O.pde_blocks(r)
+    Gpp = np.vstack([np.hstack([O.block_cov(A, B, r.lengthscale, r.outputscale) for B in eqs]) for A in eqs])
+    np.testing.assert_allclose(Kr.Gpp(x), Gpp @ x + r.jitter * x, rtol=0, atol=1e-12 * np.abs(Gpp @ x).max())
